@@ -1,0 +1,250 @@
+"""One step of the improved Yau--Yau filter in float64, in the paper's order.
+
+Per step k (Section 2.2, "Procedure"; log-domain forms of Section 7):
+  1. prediction  ell_pred(i) = log( sum_j c_j e^{L_j(i)} + c_{N+1} e^{ell(i)} ), the N-scale
+     kernel of eq. general_kernel applied to the weights (Sections 4.1-4.3), with
+     L_j(i) = LSE over unmasked sources of log K_{dt/s_j}(x_i, x_s) + log w_q + ell(s)
+     (computed by the C core, see csrc/yyo_kernel.c); the identity term carries no
+     quadrature factor.  Targets on the Dirichlet boundary get -inf (Section 4.2, step 3).
+     Negative coefficients are handled by a signed log-sum-exp; a non-positive total
+     gives -inf and is counted.
+  2. correction  ell'(i) = ell_pred(i) + h(x_i).dy_k - dt/2 |h(x_i)|^2 (Section 2.2
+     "Online stage", Section 7 "Observation Update").
+  3. normalisation  Lambda_k = LSE_i ell'(i), ell_hat = ell' - Lambda_k (Section 7
+     "Normalization"); running log-normaliser Z_k = Z_{k-1} + Lambda_k.
+  4. estimate  x_hat = sum w_hat x (Section 2.2, step 4); variance
+     v_hat = sum w_hat (x - x_hat)^2; ESS = 1 / sum w_hat^2.
+  5. restart  (Section 5): when ESS < rho n, or iota >= 2 and k mod iota == 0, the box is
+     re-centred at x_hat, the reference nodes are translated (the same u), and the
+     weights are re-initialised from N(x_hat, diag(max(v_hat, v_min))), v_min = (R/4)^2,
+     or uniformly.  Z is left unchanged by a restart.
+
+Nodes are held as float32 box coordinates u (what both implementations store) and
+float64 centre c; positions are x = c + u in float64.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import _lib, coeffs, model as mdl
+
+
+@dataclass
+class Problem:
+    model: str
+    r: int
+    n: int
+    dt: float
+    R: np.ndarray                 # [r] half-widths
+    n_scales: int
+    model_a: float = -0.5
+    restart_interval: int = 0
+    ess_frac: float = 0.0
+    prior_mean: float = 0.0
+    prior_var: float = 1.0
+    restart_init: str = "gauss"   # "gauss" | "uniform"
+
+    @property
+    def taus(self) -> np.ndarray:
+        return self.dt / coeffs.scales(self.n_scales)
+
+    @property
+    def log_wq(self) -> float:
+        return float(np.sum(np.log(2.0 * self.R)) - np.log(self.n))
+
+    @property
+    def coef(self) -> np.ndarray:
+        return coeffs.kernel_coefficients(self.n_scales)
+
+
+@dataclass
+class Prepared:
+    x: np.ndarray      # [n][r] float64
+    f: np.ndarray      # [n][r]
+    divf: np.ndarray   # [n]
+    mask: np.ndarray   # [n] bool
+
+
+def boundary_mask(u: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """Nodes within omega = 1e-12 R of a face of [-R, R]^r (Section 4.2, step 3)."""
+    uu = np.abs(u.astype(np.float64))
+    return np.any(uu >= R[None, :] - 1e-12 * R[None, :], axis=1)
+
+
+def prepare(p: Problem, u: np.ndarray, centre: np.ndarray) -> Prepared:
+    x = centre[None, :].astype(np.float64) + u.astype(np.float64)
+    return Prepared(x=x, f=mdl.drift(p.model, x, p.model_a),
+                    divf=mdl.divergence(p.model, x, p.model_a),
+                    mask=boundary_mask(u, p.R))
+
+
+def log_sum_exp(a: np.ndarray) -> float:
+    m = np.max(a)
+    if np.isinf(m):
+        return float(m)
+    return float(m + np.log(np.sum(np.exp(a - m))))
+
+
+def normalise(logw: np.ndarray) -> tuple[float, np.ndarray]:
+    lam = log_sum_exp(logw)
+    return lam, logw - lam
+
+
+def prior_logw(p: Problem, x: np.ndarray) -> np.ndarray:
+    """log sigma_0(x_i) for x_0 ~ N(mu0, s0^2 I) (Section 4.2, step 4)."""
+    d = x - p.prior_mean
+    return -0.5 * np.sum(d * d, axis=1) / p.prior_var - 0.5 * p.r * np.log(2 * np.pi * p.prior_var)
+
+
+def kernel_lse(p: Problem, prep: Prepared, logw: np.ndarray, t0: int = 0, t1: int | None = None,
+               n_threads: int = 0) -> np.ndarray:
+    """L_j(i) for targets t0 <= i < t1 and every scale j: [(t1 - t0)][N]."""
+    t1 = p.n if t1 is None else t1
+    L = _lib.lib()
+    x = np.ascontiguousarray(prep.x, dtype=np.float64)
+    f = np.ascontiguousarray(prep.f, dtype=np.float64)
+    dv = np.ascontiguousarray(prep.divf, dtype=np.float64)
+    lw = np.ascontiguousarray(logw, dtype=np.float64)
+    mk = np.ascontiguousarray(prep.mask, dtype=np.uint8)
+    tau = np.ascontiguousarray(p.taus, dtype=np.float64)
+    out = np.empty((t1 - t0, p.n_scales), dtype=np.float64)
+    ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    L.yyo_kernel_lse(p.n, p.r, ptr(x), ptr(f), ptr(dv), ptr(lw), ptr(mk), p.n_scales,
+                     ptr(tau), p.log_wq, t0, t1, ptr(out), n_threads)
+    return out
+
+
+def combine(p: Problem, Lj: np.ndarray, logw_t: np.ndarray, mask_t: np.ndarray) -> tuple[np.ndarray, int]:
+    """Signed log-sum-exp of sum_j c_j e^{L_j} + c_{N+1} e^{ell}; returns (ell_pred, clamps)."""
+    c = p.coef
+    n_t = Lj.shape[0]
+    out = np.empty(n_t)
+    clamps = 0
+    for i in range(n_t):
+        if mask_t[i]:
+            out[i] = -np.inf
+            continue
+        terms, signs = [], []
+        for j in range(p.n_scales + 1):
+            if c[j] == 0.0:
+                continue
+            val = Lj[i, j] if j < p.n_scales else logw_t[i]
+            if np.isinf(val) and val < 0:
+                continue
+            terms.append(np.log(abs(c[j])) + val)
+            signs.append(1.0 if c[j] > 0 else -1.0)
+        if not terms:
+            out[i] = -np.inf
+            continue
+        m = max(terms)
+        s = sum(sg * np.exp(t - m) for sg, t in zip(signs, terms))
+        if s > 0.0:
+            out[i] = m + np.log(s)
+        else:
+            out[i] = -np.inf
+            clamps += 1
+    return out, clamps
+
+
+def predict(p: Problem, prep: Prepared, logw: np.ndarray, t0: int = 0, t1: int | None = None,
+            n_threads: int = 0) -> tuple[np.ndarray, int]:
+    t1 = p.n if t1 is None else t1
+    Lj = kernel_lse(p, prep, logw, t0, t1, n_threads)
+    return combine(p, Lj, logw[t0:t1], prep.mask[t0:t1])
+
+
+def log_likelihood(p: Problem, x: np.ndarray, dy: np.ndarray) -> np.ndarray:
+    """h(x_i).dy - dt/2 |h(x_i)|^2, the Ito-corrected log update factor."""
+    h = mdl.sensor(p.model, x)
+    return h @ dy - 0.5 * p.dt * np.sum(h * h, axis=1)
+
+
+def estimate(x: np.ndarray, logw_hat: np.ndarray) -> tuple[np.ndarray, np.ndarray, float]:
+    w = np.exp(logw_hat)
+    mean = w @ x
+    d = x - mean[None, :]
+    var = w @ (d * d)
+    ess = 1.0 / float(np.sum(w * w))
+    return mean, var, ess
+
+
+def restart_due(p: Problem, ess: float, k: int) -> bool:
+    by_ess = p.ess_frac > 0.0 and ess < p.ess_frac * p.n
+    by_interval = p.restart_interval >= 2 and k % p.restart_interval == 0
+    return bool(by_ess or by_interval)
+
+
+def restart_logw(p: Problem, x: np.ndarray, mean: np.ndarray, var: np.ndarray) -> np.ndarray:
+    """Fresh normalised log-weights after a restart centred at the estimate."""
+    if p.restart_init == "uniform":
+        return np.full(p.n, -np.log(p.n))
+    v = np.maximum(var, (p.R / 4.0) ** 2)
+    d = x - mean[None, :]
+    lw = -0.5 * np.sum(d * d / v[None, :], axis=1) - 0.5 * np.sum(np.log(2 * np.pi * v))
+    return normalise(lw)[1]
+
+
+@dataclass
+class State:
+    u: np.ndarray          # [n][r] float32 reference nodes (box coordinates)
+    centre: np.ndarray     # [r] float64
+    logw: np.ndarray       # [n] float64, normalised
+    lognorm: float = 0.0   # Z
+    k: int = 0
+
+
+@dataclass
+class StepRecord:
+    mean: np.ndarray
+    var: np.ndarray
+    ess: float
+    lam: float
+    lognorm: float
+    restarted: bool
+    clamps: int
+    logw_pred: np.ndarray = field(repr=False, default=None)
+    logw_hat: np.ndarray = field(repr=False, default=None)
+
+
+def init_state(p: Problem, u: np.ndarray, centre: np.ndarray) -> State:
+    prep = prepare(p, u, centre)
+    lw = prior_logw(p, prep.x)
+    lw[prep.mask] = -np.inf
+    lam, lw_hat = normalise(lw)
+    return State(u=u, centre=centre.astype(np.float64).copy(), logw=lw_hat, lognorm=lam, k=0)
+
+
+def step(p: Problem, st: State, dy: np.ndarray, n_threads: int = 0,
+         keep_logw: bool = False) -> tuple[StepRecord, State]:
+    prep = prepare(p, st.u, st.centre)
+    lw_pred, clamps = predict(p, prep, st.logw, n_threads=n_threads)
+    lw_upd = lw_pred + log_likelihood(p, prep.x, dy)
+    lam, lw_hat = normalise(lw_upd)
+    if np.isinf(lam):
+        raise FloatingPointError("all weights vanished")
+    mean, var, ess = estimate(prep.x, lw_hat)
+    k = st.k + 1
+    Z = st.lognorm + lam
+    rec = StepRecord(mean=mean, var=var, ess=ess, lam=lam, lognorm=Z, restarted=False,
+                     clamps=clamps, logw_pred=lw_pred if keep_logw else None,
+                     logw_hat=lw_hat if keep_logw else None)
+    new = State(u=st.u, centre=st.centre, logw=lw_hat, lognorm=Z, k=k)
+    if restart_due(p, ess, k):
+        rec.restarted = True
+        centre = mean.copy()
+        prep2 = prepare(p, st.u, centre)
+        lw0 = restart_logw(p, prep2.x, mean, var)
+        lw0[prep2.mask] = -np.inf
+        new = State(u=st.u, centre=centre, logw=lw0, lognorm=Z, k=k)
+    return rec, new
+
+
+def run(p: Problem, st: State, dys: np.ndarray, n_threads: int = 0) -> list[StepRecord]:
+    recs = []
+    for k in range(dys.shape[0]):
+        rec, st = step(p, st, dys[k], n_threads=n_threads)
+        recs.append(rec)
+    return recs

@@ -1,0 +1,69 @@
+"""Named synthetic workloads.
+
+Each workload is a seeded cubic-sensor (f = cos x, h = x^3) or linear-Gaussian
+(f = -0.5 x, h = x) problem with m = r, unit noise, x_0 ~ N(0, I), dt = 0.01, run by the
+filter over n scrambled-Sobol nodes in a box of half-width R.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+
+import numpy as np
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    model: str            # "cubic" | "linear"
+    r: int
+    n: int
+    steps: int
+    dt: float = 0.01
+    R: float = 0.3        # box half-width
+    n_scales: int = 2     # N, bandwidths dt/s_j with s_j = 2^(j-1)
+    restart_interval: int = 2   # iota; <= 1 disables interval restarts
+    ess_frac: float = 0.5       # restart when ESS < ess_frac * n; 0 disables
+    seed: int = 1
+    precision: str = "f32"      # "f64" | "f32" | "bf16"
+    model_a: float = -0.5
+    prior_mean: float = 0.0
+    prior_var: float = 1.0
+    restart_rule: str = "plain"  # "plain" | "learned"
+
+    def with_(self, **kw) -> "Workload":
+        return replace(self, **kw)
+
+
+WORKLOADS: dict[str, Workload] = {
+    # plain method in FP64, one global box, no restart
+    "cubic_r2_n1024": Workload("cubic_r2_n1024", "cubic", r=2, n=1024, steps=100, R=4.0,
+                               n_scales=2, restart_interval=0, ess_frac=0.0, seed=1,
+                               precision="f64"),
+    # r = 100: FP32 form against the BF16 Gram form
+    "cubic_r100_n16384": Workload("cubic_r100_n16384", "cubic", r=100, n=16384, steps=200,
+                                  n_scales=2, seed=2, precision="bf16"),
+    # headline: r = 1000, three bandwidths
+    "cubic_r1000_n65536": Workload("cubic_r1000_n65536", "cubic", r=1000, n=65536, steps=100,
+                                   n_scales=3, seed=3, precision="bf16"),
+    # learned restart proposal
+    "cubic_r50_n8192": Workload("cubic_r50_n8192", "cubic", r=50, n=8192, steps=500,
+                                n_scales=2, seed=5, precision="bf16"),
+}
+
+
+def get_workload(name: str) -> Workload:
+    return WORKLOADS[name]
+
+
+def batched_workloads(count: int = 256, seed: int = 4, steps: int = 200) -> list[Workload]:
+    """Ragged batch: r ~ U{10..200}, n log-uniform in [2048, 32768] (not rounded),
+    even members cubic sensor, odd members linear-Gaussian (a = -0.5)."""
+    rng = np.random.Generator(np.random.Philox(key=np.uint64(seed) ^ np.uint64(0xBA7C4)))
+    out = []
+    for b in range(count):
+        r = int(rng.integers(10, 201))
+        n = int(round(float(np.exp(rng.uniform(np.log(2048.0), np.log(32768.0))))))
+        model = "cubic" if b % 2 == 0 else "linear"
+        out.append(Workload(f"batch{b}", model, r=r, n=n, steps=steps, n_scales=2,
+                            seed=seed + b, precision="bf16"))
+    return out
