@@ -1,0 +1,359 @@
+#!/usr/bin/env python3
+"""Throughput of the improved Yau--Yau filter's online stage on GB300.
+
+One step = prediction (multi-scale kernel sum) + correction + normalisation + estimate
++ restart test (and a restart when it fires), for one trajectory of the workload.
+Prints ONE JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+                    [--precision bf16|f32|f64] [--impl yy|reference]
+
+Under torchrun (N > 1) every rank runs an independent trajectory of the same workload
+(different seed); the path shards by trajectory with no collective, so the value is the
+sum of trajectory-steps per second over ranks (weak scaling).  --impl reference times the
+FP64 CPU oracle on a bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from synth import WORKLOADS, simulate, sobol_poly_params, sobol_scramble_params  # noqa: E402
+
+DEFAULT_WORKLOAD = "cubic_r1000_n65536"
+METRIC = "filter steps/s & kernel pair-evals/s at r=1000: mixed vs FP32, same RMSE"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, ValueError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, 0, None
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    dist.init_process_group("nccl")
+    return rank, ws, local, dist
+
+
+def _make_filter(w, precision, seed, device):
+    from paper_2509_16896_gb300 import binding
+    cfg = binding.config_from_workload(w, precision=precision)
+    flt = binding.Filter(cfg, device=device)
+    flt.init_nodes(sobol_poly_params(w.r, seed), sobol_scramble_params(w.r, seed), np.zeros(w.r))
+    return flt
+
+
+def _algorithmic_flops(w, precision):
+    """Per prediction launch: BF16 path -> the Gram screen U U^T (2 n^2 r flops);
+    FP32/FP64 path -> difference form, 3 flops per coordinate per pair."""
+    if precision == "bf16":
+        return 2.0 * w.n * w.n * w.r, "tensor"
+    return 3.0 * w.n * w.n * w.r, "alu"
+
+
+def run_yy(args):
+    import torch
+    rank, ws, local, dist = _dist()
+    device = f"cuda:{local}"
+    torch.cuda.set_device(device)
+    w = WORKLOADS[args.workload]
+    prec = args.precision or w.precision
+    seed = w.seed + 1000 * rank
+    steps_total = args.warmup + args.steps
+    tr = simulate(w.model, w.r, max(steps_total, 1), w.dt, seed=seed)
+    flt = _make_filter(w, prec, seed, device)
+    stream = flt.stream
+    dys = torch.tensor(tr.dy, dtype=torch.float64, device=device)
+
+    def step(k):
+        flt.predict()
+        flt.update(dys[k % dys.shape[0]])
+        flt.restart(mode=0)
+
+    with torch.cuda.stream(stream):
+        for k in range(args.warmup):
+            step(k)
+    torch.cuda.synchronize()
+    # ---- device-resident timed region --------------------------------------------
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    l0 = flt.launches()
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for k in range(args.steps):
+            step(args.warmup + k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    launches = flt.launches() - l0
+    ms = e0.elapsed_time(e1)
+    t_max = ms
+    if dist is not None:
+        t = torch.tensor([ms], device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    mean, var, ess, z = flt.estimate()
+    # ---- dominant kernel: prediction launches timed alone on the filter's stream ----
+    flops, bound = _algorithmic_flops(w, prec)
+    n_pred = max(3, min(20, args.steps))
+    pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    pe0.record(stream)
+    for _ in range(n_pred):
+        flt.predict()
+    pe1.record(stream)
+    torch.cuda.synchronize()
+    pred_ms = pe0.elapsed_time(pe1) / n_pred
+    flt.update(dys[0])   # leave the handle in a consistent state
+    # ---- end to end through the C ABI with host buffers ---------------------------
+    n_e2e = max(3, min(args.steps, 50))
+    dy_host = torch.tensor(tr.dy, dtype=torch.float64).pin_memory()
+    dy_dev = torch.empty(w.r, dtype=torch.float64, device=device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        with torch.cuda.stream(stream):
+            dy_dev.copy_(dy_host[k % dy_host.shape[0]], non_blocking=True)
+        flt.predict()
+        flt.update(dy_dev)
+        flt.estimate()
+        flt.restart(mode=0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = n_e2e / e2e_s
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=device, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = n_e2e * ws / float(t.item())
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    peaks, src = _peaks()
+    steps_per_s = args.steps * ws / (t_max / 1e3)
+    if bound == "tensor":
+        peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        unit = "TFLOP/s"
+        achieved = flops / (pred_ms / 1e3) / 1e12
+    else:
+        # float32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        unit = "TFLOP/s"
+        achieved = flops / (pred_ms / 1e3) / 1e12
+    out = {
+        "metric": METRIC,
+        "value": round(steps_per_s, 4),
+        "unit": "filter steps/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(t_max / args.steps, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"bf16": "bf16", "f32": "f32", "f64": "f64"}[prec],
+        "data": "synthetic (seeded Euler-Maruyama cubic sensor, scrambled Sobol nodes)",
+        "config": {"workload": w.name, "r": w.r, "n": w.n, "n_scales": w.n_scales, "dt": w.dt,
+                   "R": w.R, "restart_interval": w.restart_interval, "ess_frac": w.ess_frac,
+                   "precision": prec, "trajectories_per_gpu": 1,
+                   "l2": f"inputs larger than L2 (u is {w.n * w.r * 4 / 1e6:.0f} MB)"},
+        "pair_evals_per_s": round(steps_per_s * w.n_scales * w.n * w.n, 1),
+        "clocks": clk.summary(),
+        "e2e": {"value": round(e2e_val, 4), "unit": "filter steps/s",
+                "h2d_bytes_per_step": 8 * w.r, "d2h_bytes_per_step": 8 * (2 * w.r + 2 + 6)},
+        "gpu_launches": int(launches),
+        "roofline": {"bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": unit,
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "kernel": "prediction (kernel sum)", "kernel_ms": round(pred_ms, 4),
+                     "peak_source": src if bound == "tensor" else "derived: 152 SMs x 128 FP32 lanes x 2 x max clock"},
+        "estimate_check": {"ess": ess, "mean_abs": float(np.mean(np.abs(mean))), "finite": bool(np.all(np.isfinite(mean)))},
+    }
+    if args.fp32_steps > 0 and prec == "bf16":
+        out["fp32_comparator"] = _time_precision(w, "f32", args.fp32_steps, tr, device)
+    if args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def _time_precision(w, prec, steps, tr, device):
+    """Steps/s of another precision of the same path (the plain FP32 form)."""
+    import torch
+    flt = _make_filter(w, prec, w.seed, device)
+    dys = torch.tensor(tr.dy, dtype=torch.float64, device=device)
+    with torch.cuda.stream(flt.stream):
+        flt.predict(); flt.update(dys[0]); flt.restart(mode=0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(flt.stream)
+    for k in range(steps):
+        flt.predict(); flt.update(dys[(k + 1) % dys.shape[0]]); flt.restart(mode=0)
+    e1.record(flt.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    m, v, e, z = flt.estimate()
+    return {"precision": prec, "steps": steps, "ms_per_step": round(ms, 3),
+            "value": round(1e3 / ms, 4), "unit": "filter steps/s"}
+
+
+def cpu_baseline(w, seconds: float):
+    """The FP64 oracle as it stands, timed on this host's cores on a bounded sample: the
+    prediction for a sample of target rows against all n sources plus the O(n r)
+    correction, scaled to one full step."""
+    from oracle import filter as F, sobol
+    cores = os.cpu_count() or 1
+    p = F.Problem(model=w.model, r=w.r, n=w.n, dt=w.dt, R=np.full(w.r, w.R), n_scales=w.n_scales,
+                  model_a=w.model_a)
+    _, u = sobol.nodes(sobol_poly_params(w.r, w.seed), sobol_scramble_params(w.r, w.seed), w.n, w.R)
+    st = F.init_state(p, u, np.zeros(w.r))
+    prep = F.prepare(p, u, st.centre)
+    tr = simulate(w.model, w.r, 1, w.dt, seed=w.seed)
+    # calibrate rows so that the sample takes about `seconds`
+    t0 = time.perf_counter()
+    F.predict(p, prep, st.logw, 0, cores, n_threads=cores)
+    t_cal = max(time.perf_counter() - t0, 1e-6)
+    rows = int(min(w.n, max(cores, cores * math.floor(seconds / t_cal))))
+    t0 = time.perf_counter()
+    F.predict(p, prep, st.logw, 0, rows, n_threads=cores)
+    t_pred = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    lw = F.log_likelihood(p, prep.x, tr.dy[0]) + st.logw
+    lam, lh = F.normalise(lw)
+    F.estimate(prep.x, lh)
+    t_upd = time.perf_counter() - t0
+    step_s = t_pred * (w.n / rows) + t_upd
+    return {"value": round(1.0 / step_s, 6), "unit": "filter steps/s", "cores": cores,
+            "kind": "oracle",
+            "sample": f"prediction of {rows} of {w.n} target rows (all sources, {w.n_scales} scales) "
+                      f"+ one full correction/estimate, scaled to one step; {t_pred + t_upd:.1f} s of CPU work"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = WORKLOADS[args.workload]
+    prec = args.precision or w.precision
+    vals = []
+    for _ in range(args.warmup):
+        cpu_baseline(w, seconds=2.0)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(w, seconds=args.cpu_seconds / max(args.steps, 1)))
+    v = statistics.median([x["value"] for x in vals])
+    out = {"metric": METRIC, "impl": "reference", "value": v, "unit": "filter steps/s", "n_gpus": 1,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / v, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded Euler-Maruyama cubic sensor, scrambled Sobol nodes)",
+           "config": {"workload": w.name, "r": w.r, "n": w.n, "n_scales": w.n_scales, "precision": prec},
+           "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"], "value": v},
+           "e2e": {"value": v, "unit": "filter steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": round(time.perf_counter() - t0, 2)}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default=None, choices=["bf16", "f32", "f64"])
+    ap.add_argument("--impl", default="yy", choices=["yy", "reference"])
+    ap.add_argument("--fp32-steps", type=int, default=3, help="steps of the plain FP32 comparator")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "yy":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_yy(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * yy.h -- C ABI of libyy, the GB300 (sm_103a) online stage of the improved Yau--Yau
+ * filter (arXiv 2509.16896).
+ *
+ * The filtering problem (Section 2.1, eq. NonlinearFilter) is
+ *     dX = f(X) dt + dV,   dY = h(X) dt + dW,   X in R^r, Y in R^m,
+ * with unit-covariance Brownian motions.  The library carries the unnormalised
+ * conditional density as log-weights on n scrambled-Sobol nodes in a box
+ * [c - R, c + R]^r and advances it one observation step at a time:
+ *     yy_predict   prediction by the N-scale kernel operator (Sections 4.1-4.3,
+ *                  eq. general_kernel) in log-sum-exp form (Section 7, Prediction Step)
+ *     yy_update    Ito-corrected likelihood update (Section 2.2, Online stage), log-domain
+ *                  normalisation (Section 7, Normalization), posterior mean (Section 2.2,
+ *                  step 4), variance and effective sample size
+ *     yy_estimate  copies the estimates to the host
+ *     yy_restart   local resampling-restart (Section 5)
+ *
+ * Conventions shared by every entry point
+ *   - Memory.  Device memory is owned by the caller: it passes one device workspace of at
+ *     least yy_workspace_bytes() bytes (256-byte aligned) to yy_create and keeps it alive
+ *     until yy_destroy.  The library never allocates or frees device memory.  The opaque
+ *     yy_filter handle (host memory) is owned by the library.
+ *   - Streams.  Every call is stream-ordered on the CUDA stream given to yy_create (a
+ *     cudaStream_t passed as void*, NULL = legacy default stream).  Only the calls that
+ *     return host data (yy_estimate, yy_get_*, yy_restart with a non-NULL report
+ *     pointer) synchronise that stream; none calls cudaDeviceSynchronize.
+ *   - Errors.  Every call returns a yy_status and never aborts.  Arguments are checked
+ *     before any launch (YY_ERR_ARG).  Device-side conditions (non-finite normaliser,
+ *     every weight zero, a wait that timed out) set a sticky status word that
+ *     yy_estimate returns.
+ *   - Models.  m = r; h is componentwise.  YY_MODEL_CUBIC: f(x) = cos x, h(x) = x^3.
+ *     YY_MODEL_LINEAR: f(x) = a x, h(x) = x.
+ *   - Layout.  Node coordinates are float32 box coordinates u (x = c + u), rows of
+ *     r values, row-major; host arrays passed in or out are dense [n][r].
+ */
+#ifndef YY_H
+#define YY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define YY_EXPORT __attribute__((visibility("default")))
+#else
+#define YY_EXPORT
+#endif
+
+#define YY_API_VERSION 1
+#define YY_MAX_SCALES 4
+#define YY_MAX_DIM 1024
+#define YY_SOBOL_POLY_WORDS 16
+#define YY_SOBOL_SCRAMBLE_WORDS 33
+
+typedef struct yy_filter yy_filter;
+
+typedef enum {
+    YY_OK = 0,
+    YY_ERR_ARG = 1,          /* invalid argument; nothing was launched */
+    YY_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    YY_ERR_WORKSPACE = 3,    /* workspace missing, misaligned or too small */
+    YY_ERR_NONFINITE = 4,    /* the log-normaliser or an estimate is NaN or infinite */
+    YY_ERR_DEGENERATE = 5,   /* every log-weight is -inf after an update */
+    YY_ERR_TIMEOUT = 6,      /* a device-side wait gave up (bounded spin) */
+    YY_ERR_STATE = 7,        /* call out of order (e.g. predict before init_nodes) */
+    YY_ERR_UNSUPPORTED = 8   /* configuration not supported by this build */
+} yy_status;
+
+typedef enum { YY_MODEL_CUBIC = 0, YY_MODEL_LINEAR = 1 } yy_model;
+
+/* Arithmetic of the prediction step.  FP64: every step in float64.  FP32: exact
+ * float32 differences.  BF16: a tcgen05 BF16 Gram product screens out pairs whose
+ * kernel term is provably negligible, and the remaining pairs are evaluated exactly in
+ * float32 (results agree with FP32 within float32 rounding). */
+typedef enum { YY_PREC_FP64 = 0, YY_PREC_FP32 = 1, YY_PREC_BF16 = 2 } yy_precision;
+
+/* Log-weights after a restart (Section 5 only says the filter restarts at x_hat):
+ * GAUSS = log N(x; x_hat, diag(max(v_hat, (R/4)^2))), UNIFORM = equal weights. */
+typedef enum { YY_RESTART_INIT_GAUSS = 0, YY_RESTART_INIT_UNIFORM = 1 } yy_restart_init;
+
+/* yy_restart modes: AUTO applies the device-side test computed by the last yy_update
+ * (ESS < ess_frac * n, or restart_interval >= 2 and step % restart_interval == 0);
+ * FORCE restarts unconditionally; NEVER only reports the test. */
+typedef enum { YY_RESTART_AUTO = 0, YY_RESTART_FORCE = 1, YY_RESTART_NEVER = 2 } yy_restart_mode;
+
+typedef struct {
+    int32_t r;                 /* state dimension, 1..YY_MAX_DIM */
+    int32_t m;                 /* observation dimension; must equal r */
+    int64_t n;                 /* nodes, >= 2 */
+    double dt;                 /* step, > 0 */
+    double R;                  /* default box half-width, > 0 */
+    int32_t n_scales;          /* N of eq. general_kernel, 1..YY_MAX_SCALES; s_j = 2^(j-1) */
+    int32_t model;             /* yy_model */
+    double model_a;            /* drift slope of YY_MODEL_LINEAR */
+    int32_t precision;         /* yy_precision */
+    int32_t restart_interval;  /* iota; <= 1: no interval restart */
+    double ess_frac;           /* restart when ESS < ess_frac * n; 0 disables */
+    int32_t restart_init;      /* yy_restart_init */
+    double prior_mean;         /* x_0 ~ N(prior_mean, prior_var I) */
+    double prior_var;          /* > 0 */
+} yy_config;
+
+/* Bytes of device workspace that yy_create needs for cfg (0 if cfg is invalid). */
+YY_EXPORT size_t yy_workspace_bytes(const yy_config* cfg);
+
+/* Creates a filter on the current CUDA device.  d_workspace: device pointer,
+ * 256-byte aligned, >= yy_workspace_bytes(cfg) bytes, owned by the caller.
+ * stream: cudaStream_t or NULL.  *out receives the handle. */
+YY_EXPORT yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t bytes, void* stream,
+                    yy_filter** out);
+
+/* Releases the host handle (the workspace stays the caller's). NULL is accepted. */
+YY_EXPORT yy_status yy_destroy(yy_filter* f);
+
+/* Node generation (Appendix A, Sobol Sequence; Section 2.2, step 1): generates the n
+ * scrambled Sobol points on the device and maps them to the box, then evaluates the
+ * prior log-weights log sigma_0 (Section 4.2, step 4) and the Dirichlet mask (Section
+ * 4.2, step 3).
+ *   h_poly      host uint32 [r][YY_SOBOL_POLY_WORDS]: per dimension the degree s of its
+ *               primitive polynomial (0 = identity dimension), the inner coefficients a
+ *               (a_1 most significant), then m_1..m_s.
+ *   h_scramble  host uint32 [r][YY_SOBOL_SCRAMBLE_WORDS] or NULL (no scramble): rows
+ *               1..32 of a lower-triangular unit-diagonal GF(2) matrix (row k acts on
+ *               output digit k, stored at bit 32-k), then the digital shift.
+ *   h_center    host double [r], box centre c.
+ *   h_halfwidth host double [r] or NULL (all equal to cfg.R).
+ * Coordinates: u = R_d (2 (y + 1/2) 2^-32 - 1) in float64, rounded to float32, where y is
+ * the scrambled 32-bit integer of point i (indices 0..n-1, Gray-code order). */
+YY_EXPORT yy_status yy_init_nodes(yy_filter* f, const uint32_t* h_poly, const uint32_t* h_scramble,
+                        const double* h_center, const double* h_halfwidth);
+
+/* Writes the scrambled Sobol integers of points first..first+count-1 to d_bits
+ * (device uint32 [count][r], caller-owned).  Same generator as yy_init_nodes. */
+YY_EXPORT yy_status yy_sobol_bits(yy_filter* f, uint32_t* d_bits, int64_t first, int64_t count);
+
+/* Prediction (Section 4, eq. general_kernel; Section 7, Prediction Step):
+ *   ell_pred(i) = log( sum_j c_j e^{L_j(i)} + c_{N+1} e^{ell(i)} ),
+ *   L_j(i) = log sum_{s unmasked} K_{dt/s_j}(x_i, x_s) w_q e^{ell(s)},
+ * K the first-order kernel of eq. kernel, w_q = prod_d 2 R_d / n, c the solution of the
+ * generalised Vandermonde system.  Boundary nodes get -inf.  A non-positive combination
+ * gives -inf and is counted.  Asynchronous. */
+YY_EXPORT yy_status yy_predict(yy_filter* f);
+
+/* Correction and estimate (Section 2.2 Online stage and step 4; Section 7):
+ *   ell'(i) = ell_pred(i) + h(x_i).dy - dt/2 |h(x_i)|^2,  Lambda = LSE ell',
+ *   normalised weights, x_hat = sum w x, v_hat = sum w (x - x_hat)^2, ESS = 1/sum w^2,
+ *   Z += Lambda, then the restart test.
+ * d_dy: device double [m], the observation increment y(tau_k) - y(tau_{k-1}).
+ * Asynchronous. */
+YY_EXPORT yy_status yy_update(yy_filter* f, const double* d_dy);
+
+/* Copies the last step's estimate to the host (any pointer may be NULL):
+ * h_mean, h_var double [r]; h_ess, h_lognorm (Z_k) double.  Synchronises the stream
+ * and returns the sticky device status. */
+YY_EXPORT yy_status yy_estimate(yy_filter* f, double* h_mean, double* h_var, double* h_ess,
+                      double* h_lognorm);
+
+/* Local resampling-restart (Section 5): re-centres the box at x_hat, keeps the reference
+ * node set (translation), re-evaluates the drift at the new nodes and re-initialises the
+ * log-weights (cfg.restart_init).  mode: yy_restart_mode.  h_did_restart: NULL (stay
+ * asynchronous) or a host int32 that receives 1 if a restart happened (synchronises). */
+YY_EXPORT yy_status yy_restart(yy_filter* f, int32_t mode, int32_t* h_did_restart);
+
+/* Copies node coordinates u (host float [n][r]) and/or the Dirichlet mask (host uint8
+ * [n]); either pointer may be NULL.  Synchronises. */
+YY_EXPORT yy_status yy_get_nodes(yy_filter* f, float* h_u, uint8_t* h_mask);
+
+/* Copies the current log-weights: after yy_update (or init/restart) the normalised
+ * ell_hat; after yy_predict the predicted ell_pred minus *h_offset.  h_logw is host float
+ * [n] (FP32/BF16 precision) or double [n] (FP64 precision).  Synchronises. */
+YY_EXPORT yy_status yy_get_log_weights(yy_filter* f, void* h_logw, double* h_offset);
+
+/* Overwrites the filter state: box centre (host double [r]), normalised log-weights
+ * (host float or double [n], as for yy_get_log_weights), running log-normaliser Z and
+ * step counter.  Re-evaluates the drift at the nodes.  Used for checkpoint/resume. */
+YY_EXPORT yy_status yy_set_state(yy_filter* f, const double* h_center, const void* h_logw,
+                       double lognorm, int64_t step);
+
+/* Reads the box centre (host double [r]), Z and step counter. Synchronises. */
+YY_EXPORT yy_status yy_get_state(yy_filter* f, double* h_center, double* h_lognorm, int64_t* h_step);
+
+/* Number of targets whose multi-scale combination was non-positive (set to -inf) in the
+ * last yy_predict.  Synchronises. */
+YY_EXPORT yy_status yy_get_clamps(yy_filter* f, int64_t* h_clamps);
+
+/* Kernel launches issued by this handle so far (for launch accounting). */
+YY_EXPORT int64_t yy_launch_count(const yy_filter* f);
+
+/* Human-readable name of a status code (static storage). */
+YY_EXPORT const char* yy_status_str(yy_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* YY_H */

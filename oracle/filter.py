@@ -11,7 +11,8 @@ Per step k (Section 2.2, "Procedure"; log-domain forms of Section 7):
   2. correction  ell'(i) = ell_pred(i) + h(x_i).dy_k - dt/2 |h(x_i)|^2 (Section 2.2
      "Online stage", Section 7 "Observation Update").
   3. normalisation  Lambda_k = LSE_i ell'(i), ell_hat = ell' - Lambda_k (Section 7
-     "Normalization"); running log-normaliser Z_k = Z_{k-1} + Lambda_k.
+     "Normalization"); running log-normaliser Z_k = Z_{k-1} + Lambda_k, Z_0 = 0 (the prior
+     weights are normalised at initialisation).
   4. estimate  x_hat = sum w_hat x (Section 2.2, step 4); variance
      v_hat = sum w_hat (x - x_hat)^2; ESS = 1 / sum w_hat^2.
   5. restart  (Section 5): when ESS < rho n, or iota >= 2 and k mod iota == 0, the box is
@@ -213,8 +214,8 @@ def init_state(p: Problem, u: np.ndarray, centre: np.ndarray) -> State:
     prep = prepare(p, u, centre)
     lw = prior_logw(p, prep.x)
     lw[prep.mask] = -np.inf
-    lam, lw_hat = normalise(lw)
-    return State(u=u, centre=centre.astype(np.float64).copy(), logw=lw_hat, lognorm=lam, k=0)
+    _, lw_hat = normalise(lw)
+    return State(u=u, centre=centre.astype(np.float64).copy(), logw=lw_hat, lognorm=0.0, k=0)
 
 
 def step(p: Problem, st: State, dy: np.ndarray, n_threads: int = 0,

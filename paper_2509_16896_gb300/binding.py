@@ -1,0 +1,234 @@
+"""Thin Python binding of libyy (include/yy.h): argument marshalling only.
+
+Every step of the filter runs in the library's CUDA kernels.  PyTorch provides the
+device workspace, the device buffers of the observation increments and the CUDA stream.
+There is no fallback: if the library cannot be loaded the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "lib", "libyy.so")
+_lock = threading.Lock()
+_lib = None
+
+YY_OK = 0
+STATUS_NAMES = {0: "YY_OK", 1: "YY_ERR_ARG", 2: "YY_ERR_CUDA", 3: "YY_ERR_WORKSPACE",
+                4: "YY_ERR_NONFINITE", 5: "YY_ERR_DEGENERATE", 6: "YY_ERR_TIMEOUT",
+                7: "YY_ERR_STATE", 8: "YY_ERR_UNSUPPORTED"}
+MODELS = {"cubic": 0, "linear": 1}
+PRECISIONS = {"f64": 0, "f32": 1, "bf16": 2}
+RESTART_INIT = {"gauss": 0, "uniform": 1}
+RESTART_AUTO, RESTART_FORCE, RESTART_NEVER = 0, 1, 2
+SOBOL_POLY_WORDS = 16
+SOBOL_SCRAMBLE_WORDS = 33
+
+# every symbol include/yy.h declares
+EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy_sobol_bits",
+           "yy_predict", "yy_update", "yy_estimate", "yy_restart", "yy_get_nodes",
+           "yy_get_log_weights", "yy_set_state", "yy_get_state", "yy_get_clamps",
+           "yy_launch_count", "yy_status_str")
+
+
+class YYError(RuntimeError):
+    def __init__(self, fn: str, code: int):
+        super().__init__(f"{fn} failed: {STATUS_NAMES.get(code, code)}")
+        self.code = code
+
+
+class YYConfig(ctypes.Structure):
+    _fields_ = [("r", ctypes.c_int32), ("m", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("dt", ctypes.c_double), ("R", ctypes.c_double), ("n_scales", ctypes.c_int32),
+                ("model", ctypes.c_int32), ("model_a", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("restart_interval", ctypes.c_int32),
+                ("ess_frac", ctypes.c_double), ("restart_init", ctypes.c_int32),
+                ("prior_mean", ctypes.c_double), ("prior_var", ctypes.c_double)]
+
+
+def _declare(L: ctypes.CDLL) -> None:
+    P, I32, I64, D, S = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    sig = {
+        "yy_workspace_bytes": (S, [P]),
+        "yy_create": (I32, [P, P, S, P, P]),
+        "yy_destroy": (I32, [P]),
+        "yy_init_nodes": (I32, [P, P, P, P, P]),
+        "yy_sobol_bits": (I32, [P, P, I64, I64]),
+        "yy_predict": (I32, [P]),
+        "yy_update": (I32, [P, P]),
+        "yy_estimate": (I32, [P, P, P, P, P]),
+        "yy_restart": (I32, [P, I32, P]),
+        "yy_get_nodes": (I32, [P, P, P]),
+        "yy_get_log_weights": (I32, [P, P, P]),
+        "yy_set_state": (I32, [P, P, P, D, I64]),
+        "yy_get_state": (I32, [P, P, P, P]),
+        "yy_get_clamps": (I32, [P, P]),
+        "yy_launch_count": (I64, [P]),
+        "yy_status_str": (ctypes.c_char_p, [I32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Loads lib/libyy.so, compiling it first if it is missing; raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_LIB_PATH):
+                if not build_if_missing:
+                    raise FileNotFoundError(f"{_LIB_PATH} is missing; run build()")
+                from . import build as _b
+                _b.build()
+            L = ctypes.CDLL(_LIB_PATH)
+            _declare(L)
+            _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _check(fn: str, code: int) -> None:
+    if code != YY_OK:
+        raise YYError(fn, code)
+
+
+def make_config(model: str, r: int, n: int, dt: float, R: float, n_scales: int,
+                precision: str, restart_interval: int = 0, ess_frac: float = 0.0,
+                model_a: float = -0.5, restart_init: str = "gauss", prior_mean: float = 0.0,
+                prior_var: float = 1.0) -> YYConfig:
+    return YYConfig(r=r, m=r, n=n, dt=dt, R=R, n_scales=n_scales, model=MODELS[model],
+                    model_a=model_a, precision=PRECISIONS[precision],
+                    restart_interval=restart_interval, ess_frac=ess_frac,
+                    restart_init=RESTART_INIT[restart_init], prior_mean=prior_mean,
+                    prior_var=prior_var)
+
+
+def config_from_workload(w, precision: str | None = None, **over) -> YYConfig:
+    kw = dict(model=w.model, r=w.r, n=w.n, dt=w.dt, R=w.R, n_scales=w.n_scales,
+              precision=precision or w.precision, restart_interval=w.restart_interval,
+              ess_frac=w.ess_frac, model_a=w.model_a, prior_mean=w.prior_mean,
+              prior_var=w.prior_var)
+    kw.update(over)
+    return make_config(**kw)
+
+
+class Filter:
+    """One filter handle on one CUDA device (torch allocates its workspace)."""
+
+    def __init__(self, cfg: YYConfig, device: str = "cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.cfg = cfg
+        self.device = torch.device(device)
+        nbytes = self.lib.yy_workspace_bytes(ctypes.byref(cfg))
+        if nbytes == 0:
+            raise YYError("yy_workspace_bytes", 1)
+        self.ws_bytes = int(nbytes)
+        self.ws = torch.empty(self.ws_bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.ws.data_ptr()
+        self.ws_ptr = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check("yy_create", self.lib.yy_create(ctypes.byref(cfg), ctypes.c_void_p(self.ws_ptr),
+                                               self.ws_bytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                               ctypes.byref(h)))
+        self.h = h
+        self.r, self.n = cfg.r, cfg.n
+        self.fp64 = cfg.precision == PRECISIONS["f64"]
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.yy_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- calls -------------------------------------------------------------------
+    def init_nodes(self, poly: np.ndarray, scramble: np.ndarray | None, center: np.ndarray,
+                   halfwidth: np.ndarray | None = None) -> None:
+        poly = np.ascontiguousarray(poly, dtype=np.uint32)
+        scr = None if scramble is None else np.ascontiguousarray(scramble, dtype=np.uint32)
+        cen = np.ascontiguousarray(center, dtype=np.float64)
+        hw = None if halfwidth is None else np.ascontiguousarray(halfwidth, dtype=np.float64)
+        assert poly.shape == (self.r, SOBOL_POLY_WORDS) and cen.shape == (self.r,)
+        _check("yy_init_nodes", self.lib.yy_init_nodes(
+            self.h, _ptr(poly), None if scr is None else _ptr(scr), _ptr(cen),
+            None if hw is None else _ptr(hw)))
+
+    def sobol_bits(self, first: int, count: int):
+        out = self.torch.empty((count, self.r), dtype=self.torch.int32, device=self.device)
+        _check("yy_sobol_bits", self.lib.yy_sobol_bits(self.h, ctypes.c_void_p(out.data_ptr()),
+                                                       first, count))
+        return out
+
+    def predict(self) -> None:
+        _check("yy_predict", self.lib.yy_predict(self.h))
+
+    def update(self, dy_dev) -> None:
+        """dy_dev: torch float64 tensor [r] on the device."""
+        assert dy_dev.dtype == self.torch.float64 and dy_dev.is_cuda and dy_dev.numel() == self.r
+        _check("yy_update", self.lib.yy_update(self.h, ctypes.c_void_p(dy_dev.data_ptr())))
+
+    def estimate(self):
+        mean = np.empty(self.r)
+        var = np.empty(self.r)
+        ess = ctypes.c_double()
+        z = ctypes.c_double()
+        _check("yy_estimate", self.lib.yy_estimate(self.h, _ptr(mean), _ptr(var), ctypes.byref(ess),
+                                                   ctypes.byref(z)))
+        return mean, var, ess.value, z.value
+
+    def restart(self, mode: int = RESTART_AUTO, report: bool = False):
+        did = ctypes.c_int32(0)
+        _check("yy_restart", self.lib.yy_restart(self.h, mode, ctypes.byref(did) if report else None))
+        return bool(did.value) if report else None
+
+    def get_nodes(self):
+        u = np.empty((self.n, self.r), dtype=np.float32)
+        mask = np.empty(self.n, dtype=np.uint8)
+        _check("yy_get_nodes", self.lib.yy_get_nodes(self.h, _ptr(u), _ptr(mask)))
+        return u, mask.astype(bool)
+
+    def get_log_weights(self):
+        out = np.empty(self.n, dtype=np.float64 if self.fp64 else np.float32)
+        off = ctypes.c_double()
+        _check("yy_get_log_weights", self.lib.yy_get_log_weights(self.h, _ptr(out), ctypes.byref(off)))
+        return out, off.value
+
+    def set_state(self, center: np.ndarray, logw: np.ndarray, lognorm: float = 0.0, step: int = 0):
+        cen = np.ascontiguousarray(center, dtype=np.float64)
+        lw = np.ascontiguousarray(logw, dtype=np.float64 if self.fp64 else np.float32)
+        _check("yy_set_state", self.lib.yy_set_state(self.h, _ptr(cen), _ptr(lw), lognorm, step))
+
+    def get_state(self):
+        cen = np.empty(self.r)
+        z = ctypes.c_double()
+        k = ctypes.c_int64()
+        _check("yy_get_state", self.lib.yy_get_state(self.h, _ptr(cen), ctypes.byref(z), ctypes.byref(k)))
+        return cen, z.value, k.value
+
+    def clamps(self) -> int:
+        c = ctypes.c_int64()
+        _check("yy_get_clamps", self.lib.yy_get_clamps(self.h, ctypes.byref(c)))
+        return c.value
+
+    def launches(self) -> int:
+        return int(self.lib.yy_launch_count(self.h))

@@ -1,0 +1,466 @@
+// C ABI of libyy (declared in include/yy.h): argument checks, workspace carving, host
+// constants (multi-scale coefficients, offsets) and the launch sequences.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "yy_internal.cuh"
+
+using namespace yy;
+
+struct yy_filter {
+    yy_config cfg;
+    int r_pad;
+    long long n_pad;
+    cudaStream_t stream;
+    char* ws;
+    size_t ws_bytes;
+    bool fp64;
+    Bufs<float> bf;
+    Bufs<double> bd;
+    Consts<float> kf;
+    Consts<double> kd;
+    bool nodes_ready;
+    bool predicted;     // logw_pred holds the last prediction
+    long long launches;
+    double coef[kMaxScales + 1];
+    double log_wq;
+    double c_ref;
+};
+
+namespace {
+
+long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+bool cfg_valid(const yy_config* c) {
+    if (!c) return false;
+    if (c->r < 1 || c->r > YY_MAX_DIM || c->m != c->r) return false;
+    if (c->n < 2 || c->n > (1LL << 31)) return false;
+    if (!(c->dt > 0.0) || !(c->R > 0.0) || !(c->prior_var > 0.0)) return false;
+    if (c->n_scales < 1 || c->n_scales > YY_MAX_SCALES) return false;
+    if (c->model != YY_MODEL_CUBIC && c->model != YY_MODEL_LINEAR) return false;
+    if (c->precision < YY_PREC_FP64 || c->precision > YY_PREC_BF16) return false;
+    if (c->restart_init != YY_RESTART_INIT_GAUSS && c->restart_init != YY_RESTART_INIT_UNIFORM) return false;
+    if (!(c->ess_frac >= 0.0) || c->ess_frac > 1.0) return false;
+    return true;
+}
+
+// Sequential carve of the workspace with 256-byte alignment.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    template <typename P>
+    P* take(size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        P* p = base ? reinterpret_cast<P*>(base + off) : nullptr;
+        off += bytes;
+        return p;
+    }
+};
+
+template <typename T>
+size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
+    const long long n_pad = round_up(c->n, kRowAlign);
+    const int r_pad = (int)round_up(c->r, kColAlign);
+    Carver cv{base};
+    Bufs<T> b{};
+    const size_t nr = (size_t)n_pad * r_pad;
+    b.u = cv.take<float>(nr * sizeof(float));
+    b.f = cv.take<T>(nr * sizeof(T));
+    b.ubf = (c->precision == YY_PREC_BF16) ? cv.take<__nv_bfloat16>(nr * sizeof(__nv_bfloat16)) : nullptr;
+    b.divf = cv.take<T>(n_pad * sizeof(T));
+    b.nu = cv.take<T>(n_pad * sizeof(T));
+    b.nf = cv.take<T>(n_pad * sizeof(T));
+    b.mask = cv.take<uint8_t>(n_pad);
+    b.logw = cv.take<T>(n_pad * sizeof(T));
+    b.logw_pred = cv.take<T>(n_pad * sizeof(T));
+    b.centre = cv.take<double>(r_pad * sizeof(double));
+    b.halfwidth = cv.take<double>(r_pad * sizeof(double));
+    b.mean = cv.take<double>(r_pad * sizeof(double));
+    b.var = cv.take<double>(r_pad * sizeof(double));
+    b.dirs = cv.take<uint32_t>((size_t)c->r * 33 * sizeof(uint32_t));
+    b.params = cv.take<uint32_t>((size_t)c->r * (YY_SOBOL_POLY_WORDS + YY_SOBOL_SCRAMBLE_WORDS) * sizeof(uint32_t));
+    b.obs_g = cv.take<T>(r_pad * sizeof(T));
+    b.obs_c = cv.take<T>(r_pad * sizeof(T));
+    b.part = cv.take<double>(part_bytes(r_pad));
+    b.stats = cv.take<DevStats>(sizeof(DevStats));
+    if (c->precision == YY_PREC_BF16) {
+        const size_t tc = tc_scratch_bytes(n_pad, c->n_scales);
+        char* t = cv.take<char>(tc);
+        b.cand_count = reinterpret_cast<int*>(t);
+        b.row_state = t ? reinterpret_cast<float*>(t + 256) : nullptr;
+        const size_t rs = (size_t)n_pad * 2 * c->n_scales * sizeof(float);
+        const size_t rs_al = (rs + 255) & ~(size_t)255;
+        b.cand = t ? reinterpret_cast<int2*>(t + 256 + rs_al) : nullptr;
+        b.cand_cap = (long long)((tc - 256 - rs_al) / sizeof(int2));
+    }
+    if (out) *out = b;
+    return cv.off + 256;
+}
+
+// Coefficients of eq. general_kernel: V c = d with rows (1..1 | 1), (s_j^-1 | 0),
+// (s_j^-mu_k | 0), mu_k = 3/2, 2, ..., solved by Gaussian elimination with partial pivoting.
+void multiscale_coefficients(int N, double* c) {
+    const int M = N + 1;
+    double A[kMaxScales + 1][kMaxScales + 2];
+    for (int row = 0; row < M; ++row)
+        for (int col = 0; col <= M; ++col) A[row][col] = 0.0;
+    for (int j = 0; j < M; ++j) A[0][j] = 1.0;
+    A[0][M] = 1.0;
+    for (int j = 0; j < N; ++j) A[1][j] = 1.0 / ldexp(1.0, j);
+    A[1][M] = 1.0;
+    for (int k = 0; k + 2 < M; ++k) {
+        const double mu = 1.5 + 0.5 * k;
+        for (int j = 0; j < N; ++j) A[2 + k][j] = pow(ldexp(1.0, j), -mu);
+    }
+    for (int col = 0; col < M; ++col) {
+        int piv = col;
+        for (int row = col + 1; row < M; ++row)
+            if (fabs(A[row][col]) > fabs(A[piv][col])) piv = row;
+        if (piv != col)
+            for (int q = 0; q <= M; ++q) { double t = A[col][q]; A[col][q] = A[piv][q]; A[piv][q] = t; }
+        for (int row = col + 1; row < M; ++row) {
+            const double f = A[row][col] / A[col][col];
+            for (int q = col; q <= M; ++q) A[row][q] -= f * A[col][q];
+        }
+    }
+    for (int row = M - 1; row >= 0; --row) {
+        double s = A[row][M];
+        for (int q = row + 1; q < M; ++q) s -= A[row][q] * c[q];
+        c[row] = s / A[row][row];
+    }
+    if (N == 1) c[1] = 0.0;  // exact: the identity term vanishes for the first-order kernel
+}
+
+template <typename T>
+void fill_consts(yy_filter* f, Consts<T>* k, const double* halfwidth) {
+    const yy_config& c = f->cfg;
+    k->n = c.n;
+    k->n_pad = f->n_pad;
+    k->r = c.r;
+    k->r_pad = f->r_pad;
+    k->N = c.n_scales;
+    k->model = c.model;
+    k->model_a = (T)c.model_a;
+    k->dt = (T)c.dt;
+    double log_vol = 0.0;
+    for (int d = 0; d < c.r; ++d) log_vol += log(2.0 * (halfwidth ? halfwidth[d] : c.R));
+    f->log_wq = log_vol - log((double)c.n);
+    double Cj[kMaxScales];
+    double cref = -INFINITY;
+    for (int j = 0; j < c.n_scales; ++j) {
+        const double tau = c.dt / ldexp(1.0, j);
+        Cj[j] = -0.5 * c.r * log(2.0 * M_PI * tau) + f->log_wq;
+        cref = fmax(cref, Cj[j]);
+        k->tau[j] = (T)tau;
+        k->inv2tau[j] = (T)(0.5 / tau);
+    }
+    for (int j = 0; j < c.n_scales; ++j) k->cj_off[j] = (T)(Cj[j] - cref);
+    for (int j = c.n_scales; j < kMaxScales; ++j) { k->tau[j] = T(0); k->inv2tau[j] = T(0); k->cj_off[j] = T(0); }
+    for (int j = 0; j <= kMaxScales; ++j) { k->logabs_c[j] = T(0); k->sign_c[j] = T(0); }
+    for (int j = 0; j <= c.n_scales; ++j) {
+        const double cj = f->coef[j];
+        k->sign_c[j] = (cj > 0.0) ? T(1) : (cj < 0.0 ? T(-1) : T(0));
+        k->logabs_c[j] = (cj != 0.0) ? (T)log(fabs(cj)) : T(0);
+    }
+    k->c_ref = cref;
+    f->c_ref = cref;
+}
+
+yy_status cuda_status(cudaError_t e) { return e == cudaSuccess ? YY_OK : YY_ERR_CUDA; }
+
+__global__ void k_set_stats(DevStats* st, double lognorm, long long step) {
+    st->lognorm = lognorm;
+    st->step = step;
+}
+
+template <typename T>
+yy_status do_init_nodes(yy_filter* f, Bufs<T>& b, Consts<T>& k, const uint32_t* h_poly,
+                        const uint32_t* h_scr, const double* h_center, const double* h_half) {
+    const yy_config& c = f->cfg;
+    const int W = YY_SOBOL_POLY_WORDS + YY_SOBOL_SCRAMBLE_WORDS;
+    uint32_t* staging = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)c.r * W);
+    double* cen = (double*)calloc(f->r_pad, sizeof(double));
+    double* half = (double*)calloc(f->r_pad, sizeof(double));
+    if (!staging || !cen || !half) { free(staging); free(cen); free(half); return YY_ERR_ARG; }
+    for (int d = 0; d < c.r; ++d) {
+        memcpy(staging + (size_t)d * W, h_poly + (size_t)d * YY_SOBOL_POLY_WORDS,
+               sizeof(uint32_t) * YY_SOBOL_POLY_WORDS);
+        uint32_t* L = staging + (size_t)d * W + YY_SOBOL_POLY_WORDS;
+        if (h_scr) {
+            memcpy(L, h_scr + (size_t)d * YY_SOBOL_SCRAMBLE_WORDS, sizeof(uint32_t) * YY_SOBOL_SCRAMBLE_WORDS);
+        } else {
+            for (int q = 1; q <= 32; ++q) L[q - 1] = 1u << (32 - q);
+            L[32] = 0u;
+        }
+        cen[d] = h_center[d];
+        half[d] = h_half ? h_half[d] : c.R;
+    }
+    fill_consts<T>(f, &k, half);
+    cudaStream_t s = f->stream;
+    cudaError_t e = cudaMemcpyAsync(b.params, staging, sizeof(uint32_t) * (size_t)c.r * W, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.centre, cen, sizeof(double) * f->r_pad, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(b.halfwidth, half, sizeof(double) * f->r_pad, cudaMemcpyHostToDevice, s);
+    // pageable copies are staged before return, but keep the host buffers until the stream drains
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    free(staging); free(cen); free(half);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    if ((e = launch_sobol_dirs<T>(b.params, b.dirs, c.r, s)) != cudaSuccess) return YY_ERR_CUDA;
+    if ((e = launch_sobol_points(b.dirs, c.r, f->r_pad, 0, c.n, b.u, nullptr, b.halfwidth, s)) != cudaSuccess)
+        return YY_ERR_CUDA;
+    if ((e = launch_prep<T>(k, b, true, true, c.prior_mean, c.prior_var, s)) != cudaSuccess) return YY_ERR_CUDA;
+    int l = 0;
+    if ((e = launch_normalise_only<T>(k, b, s, &l)) != cudaSuccess) return YY_ERR_CUDA;
+    k_set_stats<<<1, 1, 0, s>>>(b.stats, 0.0, 0);
+    f->launches += 5 + l;
+    f->nodes_ready = true;
+    f->predicted = false;
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t yy_workspace_bytes(const yy_config* cfg) {
+    if (!cfg_valid(cfg)) return 0;
+    if (cfg->precision == YY_PREC_FP64) return carve<double>(cfg, nullptr, nullptr);
+    return carve<float>(cfg, nullptr, nullptr);
+}
+
+yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t bytes, void* stream,
+                    yy_filter** out) {
+    if (!out) return YY_ERR_ARG;
+    *out = nullptr;
+    if (!cfg_valid(cfg)) return YY_ERR_ARG;
+    const size_t need = yy_workspace_bytes(cfg);
+    if (!d_workspace || ((uintptr_t)d_workspace & 255u) || bytes < need) return YY_ERR_WORKSPACE;
+    yy_filter* f = new (std::nothrow) yy_filter();
+    if (!f) return YY_ERR_ARG;
+    f->cfg = *cfg;
+    f->r_pad = (int)round_up(cfg->r, kColAlign);
+    f->n_pad = round_up(cfg->n, kRowAlign);
+    f->stream = (cudaStream_t)stream;
+    f->ws = (char*)d_workspace;
+    f->ws_bytes = bytes;
+    f->fp64 = (cfg->precision == YY_PREC_FP64);
+    multiscale_coefficients(cfg->n_scales, f->coef);
+    if (f->fp64) carve<double>(cfg, f->ws, &f->bd);
+    else carve<float>(cfg, f->ws, &f->bf);
+    cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, f->stream);
+    if (e != cudaSuccess) { delete f; return YY_ERR_CUDA; }
+    *out = f;
+    return YY_OK;
+}
+
+yy_status yy_destroy(yy_filter* f) {
+    delete f;
+    return YY_OK;
+}
+
+yy_status yy_init_nodes(yy_filter* f, const uint32_t* h_poly, const uint32_t* h_scramble,
+                        const double* h_center, const double* h_halfwidth) {
+    if (!f || !h_poly || !h_center) return YY_ERR_ARG;
+    for (int d = 0; d < f->cfg.r; ++d) {
+        const uint32_t s = h_poly[(size_t)d * YY_SOBOL_POLY_WORDS];
+        if (s > YY_SOBOL_POLY_WORDS - 2) return YY_ERR_ARG;
+        if (h_halfwidth && !(h_halfwidth[d] > 0.0)) return YY_ERR_ARG;
+        if (!isfinite(h_center[d])) return YY_ERR_ARG;
+    }
+    if (f->fp64) return do_init_nodes<double>(f, f->bd, f->kd, h_poly, h_scramble, h_center, h_halfwidth);
+    return do_init_nodes<float>(f, f->bf, f->kf, h_poly, h_scramble, h_center, h_halfwidth);
+}
+
+yy_status yy_sobol_bits(yy_filter* f, uint32_t* d_bits, int64_t first, int64_t count) {
+    if (!f || !d_bits || first < 0 || count < 0) return YY_ERR_ARG;
+    if (!f->nodes_ready) return YY_ERR_STATE;
+    const uint32_t* dirs = f->fp64 ? f->bd.dirs : f->bf.dirs;
+    f->launches += 1;
+    return cuda_status(launch_sobol_points(dirs, f->cfg.r, f->r_pad, first, count, nullptr, d_bits,
+                                           nullptr, f->stream));
+}
+
+yy_status yy_predict(yy_filter* f) {
+    if (!f) return YY_ERR_ARG;
+    if (!f->nodes_ready) return YY_ERR_STATE;
+    cudaError_t e;
+    if (f->fp64) {
+        e = cudaMemsetAsync(&f->bd.stats->clamps, 0, sizeof(unsigned), f->stream);
+        if (e == cudaSuccess) e = launch_ksum_simt<double>(f->kd, f->bd, f->stream);
+        f->launches += 1;
+    } else if (f->cfg.precision == YY_PREC_FP32) {
+        e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
+        if (e == cudaSuccess) e = launch_ksum_simt<float>(f->kf, f->bf, f->stream);
+        f->launches += 1;
+    } else {
+        e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
+        int l = 0;
+        if (e == cudaSuccess) e = launch_ksum_tc(f->kf, f->bf, f->stream, &l);
+        f->launches += l;
+        if (e == cudaErrorNotSupported) return YY_ERR_UNSUPPORTED;
+    }
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    f->predicted = true;
+    return YY_OK;
+}
+
+yy_status yy_update(yy_filter* f, const double* d_dy) {
+    if (!f || !d_dy) return YY_ERR_ARG;
+    if (!f->nodes_ready || !f->predicted) return YY_ERR_STATE;
+    int l = 0;
+    cudaError_t e = f->fp64
+        ? launch_update<double>(f->kd, f->bd, d_dy, f->cfg.restart_interval, f->cfg.ess_frac, f->stream, &l)
+        : launch_update<float>(f->kf, f->bf, d_dy, f->cfg.restart_interval, f->cfg.ess_frac, f->stream, &l);
+    f->launches += l;
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    f->predicted = false;
+    return YY_OK;
+}
+
+static yy_status status_from_word(unsigned w) {
+    if (w & kStatusTimeout) return YY_ERR_TIMEOUT;
+    if (w & kStatusDegenerate) return YY_ERR_DEGENERATE;
+    if (w & kStatusNonFinite) return YY_ERR_NONFINITE;
+    return YY_OK;
+}
+
+yy_status yy_estimate(yy_filter* f, double* h_mean, double* h_var, double* h_ess, double* h_lognorm) {
+    if (!f) return YY_ERR_ARG;
+    if (!f->nodes_ready) return YY_ERR_STATE;
+    DevStats* st = f->fp64 ? f->bd.stats : f->bf.stats;
+    double* mean = f->fp64 ? f->bd.mean : f->bf.mean;
+    double* var = f->fp64 ? f->bd.var : f->bf.var;
+    DevStats hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, st, sizeof(DevStats), cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess && h_mean) e = cudaMemcpyAsync(h_mean, mean, sizeof(double) * f->cfg.r, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess && h_var) e = cudaMemcpyAsync(h_var, var, sizeof(double) * f->cfg.r, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    if (h_ess) *h_ess = hs.ess;
+    if (h_lognorm) *h_lognorm = hs.lognorm;
+    return status_from_word(hs.status);
+}
+
+yy_status yy_restart(yy_filter* f, int32_t mode, int32_t* h_did_restart) {
+    if (!f) return YY_ERR_ARG;
+    if (mode != YY_RESTART_AUTO && mode != YY_RESTART_FORCE && mode != YY_RESTART_NEVER) return YY_ERR_ARG;
+    if (!f->nodes_ready || f->predicted) return YY_ERR_STATE;
+    int l = 0;
+    cudaError_t e = f->fp64
+        ? launch_restart<double>(f->kd, f->bd, mode, f->cfg.restart_init, f->stream, &l)
+        : launch_restart<float>(f->kf, f->bf, mode, f->cfg.restart_init, f->stream, &l);
+    f->launches += l;
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    if (h_did_restart) {
+        DevStats* st = f->fp64 ? f->bd.stats : f->bf.stats;
+        if (mode == YY_RESTART_NEVER) {
+            int flag = 0;
+            e = cudaMemcpyAsync(&flag, &st->restart_flag, sizeof(int), cudaMemcpyDeviceToHost, f->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+            *h_did_restart = flag;
+        } else {
+            int did = 0;
+            e = cudaMemcpyAsync(&did, &st->last_restarted, sizeof(int), cudaMemcpyDeviceToHost, f->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+            *h_did_restart = did;
+        }
+        if (e != cudaSuccess) return YY_ERR_CUDA;
+    }
+    return YY_OK;
+}
+
+yy_status yy_get_nodes(yy_filter* f, float* h_u, uint8_t* h_mask) {
+    if (!f) return YY_ERR_ARG;
+    if (!f->nodes_ready) return YY_ERR_STATE;
+    const float* u = f->fp64 ? f->bd.u : f->bf.u;
+    const uint8_t* mk = f->fp64 ? f->bd.mask : f->bf.mask;
+    cudaError_t e = cudaSuccess;
+    if (h_u)
+        e = cudaMemcpy2DAsync(h_u, sizeof(float) * f->cfg.r, u, sizeof(float) * f->r_pad,
+                              sizeof(float) * f->cfg.r, (size_t)f->cfg.n, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess && h_mask) e = cudaMemcpyAsync(h_mask, mk, (size_t)f->cfg.n, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    return cuda_status(e);
+}
+
+yy_status yy_get_log_weights(yy_filter* f, void* h_logw, double* h_offset) {
+    if (!f || !h_logw) return YY_ERR_ARG;
+    if (!f->nodes_ready) return YY_ERR_STATE;
+    const size_t es = f->fp64 ? sizeof(double) : sizeof(float);
+    const void* src = f->predicted ? (f->fp64 ? (void*)f->bd.logw_pred : (void*)f->bf.logw_pred)
+                                   : (f->fp64 ? (void*)f->bd.logw : (void*)f->bf.logw);
+    cudaError_t e = cudaMemcpyAsync(h_logw, src, es * (size_t)f->cfg.n, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (h_offset) *h_offset = f->predicted ? f->c_ref : 0.0;
+    return cuda_status(e);
+}
+
+yy_status yy_set_state(yy_filter* f, const double* h_center, const void* h_logw, double lognorm,
+                       int64_t step) {
+    if (!f || !h_center || !h_logw || step < 0) return YY_ERR_ARG;
+    if (!f->nodes_ready) return YY_ERR_STATE;
+    for (int d = 0; d < f->cfg.r; ++d)
+        if (!isfinite(h_center[d])) return YY_ERR_ARG;
+    const size_t es = f->fp64 ? sizeof(double) : sizeof(float);
+    double* cen = f->fp64 ? f->bd.centre : f->bf.centre;
+    void* lw = f->fp64 ? (void*)f->bd.logw : (void*)f->bf.logw;
+    DevStats* st = f->fp64 ? f->bd.stats : f->bf.stats;
+    cudaError_t e = cudaMemcpyAsync(cen, h_center, sizeof(double) * f->cfg.r, cudaMemcpyHostToDevice, f->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lw, h_logw, es * (size_t)f->cfg.n, cudaMemcpyHostToDevice, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    k_set_stats<<<1, 1, 0, f->stream>>>(st, lognorm, step);
+    e = f->fp64 ? launch_prep<double>(f->kd, f->bd, false, false, 0.0, 1.0, f->stream)
+                : launch_prep<float>(f->kf, f->bf, false, false, 0.0, 1.0, f->stream);
+    f->launches += 2;
+    f->predicted = false;
+    return cuda_status(e);
+}
+
+yy_status yy_get_state(yy_filter* f, double* h_center, double* h_lognorm, int64_t* h_step) {
+    if (!f) return YY_ERR_ARG;
+    if (!f->nodes_ready) return YY_ERR_STATE;
+    double* cen = f->fp64 ? f->bd.centre : f->bf.centre;
+    DevStats* st = f->fp64 ? f->bd.stats : f->bf.stats;
+    DevStats hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, st, sizeof(DevStats), cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess && h_center)
+        e = cudaMemcpyAsync(h_center, cen, sizeof(double) * f->cfg.r, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    if (h_lognorm) *h_lognorm = hs.lognorm;
+    if (h_step) *h_step = hs.step;
+    return YY_OK;
+}
+
+yy_status yy_get_clamps(yy_filter* f, int64_t* h_clamps) {
+    if (!f || !h_clamps) return YY_ERR_ARG;
+    DevStats* st = f->fp64 ? f->bd.stats : f->bf.stats;
+    DevStats hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, st, sizeof(DevStats), cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    *h_clamps = hs.clamps;
+    return YY_OK;
+}
+
+int64_t yy_launch_count(const yy_filter* f) { return f ? f->launches : 0; }
+
+const char* yy_status_str(yy_status s) {
+    switch (s) {
+        case YY_OK: return "YY_OK";
+        case YY_ERR_ARG: return "YY_ERR_ARG: invalid argument";
+        case YY_ERR_CUDA: return "YY_ERR_CUDA: CUDA runtime error";
+        case YY_ERR_WORKSPACE: return "YY_ERR_WORKSPACE: workspace missing, misaligned or too small";
+        case YY_ERR_NONFINITE: return "YY_ERR_NONFINITE: non-finite normaliser or estimate";
+        case YY_ERR_DEGENERATE: return "YY_ERR_DEGENERATE: every log-weight is -inf";
+        case YY_ERR_TIMEOUT: return "YY_ERR_TIMEOUT: a device-side wait gave up";
+        case YY_ERR_STATE: return "YY_ERR_STATE: call out of order";
+        case YY_ERR_UNSUPPORTED: return "YY_ERR_UNSUPPORTED: configuration not supported";
+    }
+    return "unknown yy_status";
+}
+
+}  // extern "C"

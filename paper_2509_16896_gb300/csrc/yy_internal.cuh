@@ -1,0 +1,118 @@
+// Internal declarations of libyy (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <math.h>
+
+#include "yy.h"
+
+namespace yy {
+
+constexpr int kMaxScales = YY_MAX_SCALES;
+constexpr int kRowAlign = 256;       // node rows are padded to a multiple of this
+constexpr int kColAlign = 64;        // coordinates per row are padded to a multiple of this
+constexpr int kNumPartBlocks = 304;  // blocks of the reduction passes (2 per SM)
+
+// Device status word bits (sticky until the handle is recreated).
+constexpr uint32_t kStatusNonFinite = 1u << 0;
+constexpr uint32_t kStatusDegenerate = 1u << 1;
+constexpr uint32_t kStatusTimeout = 1u << 2;
+constexpr uint32_t kStatusCandOverflow = 1u << 3;
+
+// Device-side per-filter scalars.
+struct DevStats {
+    double lam_rel;      // log-sum-exp of the unnormalised log-weights, relative to offsets
+    double lam;          // Lambda_k (absolute)
+    double lognorm;      // Z_k
+    double lam_c;        // Ito-corrected log-likelihood at the box centre
+    double ess;
+    double wsum, wsq;    // sum of normalised weights and of their squares
+    long long step;      // k
+    int restart_flag;    // test result of the last update (or forced)
+    int restarts;        // restarts so far
+    unsigned int status; // kStatus* bits
+    unsigned int clamps; // non-positive combinations in the last predict
+    unsigned long long candidates;  // exact pair evaluations in the last BF16 predict
+    int last_restarted;  // 1 if the last yy_restart call re-centred the box
+};
+
+// Constants of one filter handed to kernels by value.
+template <typename T>
+struct Consts {
+    long long n, n_pad;
+    int r, r_pad;
+    int N;
+    int model;           // yy_model
+    T model_a;
+    T dt;
+    T tau[kMaxScales];
+    T inv2tau[kMaxScales];   // 1 / (2 tau_j)
+    T cj_off[kMaxScales];    // C_j - C_ref, C_j = -(r/2) log(2 pi tau_j) + log w_q
+    T logabs_c[kMaxScales + 1];
+    T sign_c[kMaxScales + 1];  // 0 for a zero coefficient
+    double c_ref;
+};
+
+// Pointers into the caller's workspace.
+template <typename T>
+struct Bufs {
+    float* u;             // [n_pad][r_pad] box coordinates
+    T* f;                 // [n_pad][r_pad] drift at x = c + u
+    __nv_bfloat16* ubf;   // [n_pad][r_pad] bf16 copy of u (BF16 precision only)
+    T* divf;              // [n_pad]
+    T* nu;                // [n_pad] |u_i|^2
+    T* nf;                // [n_pad] |f_i|^2
+    uint8_t* mask;        // [n_pad] Dirichlet boundary
+    T* logw;              // [n_pad] current (normalised or unnormalised) log-weights
+    T* logw_pred;         // [n_pad] predicted log-weights minus c_ref
+    double* centre;       // [r_pad]
+    double* halfwidth;    // [r_pad]
+    uint32_t* dirs;       // [r][33] scrambled direction numbers + shift
+    uint32_t* params;     // [r][16 + 33] staging of the Sobol parameters
+    double* mean;         // [r_pad] x_hat
+    double* var;          // [r_pad] v_hat
+    T* obs_g;             // [r_pad] dy - dt h(c)
+    T* obs_c;             // [r_pad] centre in T
+    double* part;         // reduction partials
+    DevStats* stats;
+    // BF16 path scratch
+    int* cand_count;      // [1]
+    int2* cand;           // [cand_cap] (target, source) pairs
+    float* row_state;     // [n_pad][2 * N] online (max, sum) per target and scale
+    long long cand_cap;
+};
+
+// Launch helpers (defined in the .cu files).
+template <typename T>
+cudaError_t launch_sobol_dirs(const uint32_t* params, uint32_t* dirs, int r, cudaStream_t s);
+cudaError_t launch_sobol_points(const uint32_t* dirs, int r, int r_pad, long long first,
+                                long long count, float* u, uint32_t* bits, const double* halfwidth,
+                                cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_prep(const Consts<T>& k, const Bufs<T>& b, bool init_weights, bool first,
+                        double prior_mean, double prior_var, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s);
+cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s,
+                           int* launches);
+size_t tc_scratch_bytes(long long n_pad, int N);
+
+template <typename T>
+cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy,
+                          int restart_interval, double ess_frac, cudaStream_t s, int* launches);
+
+template <typename T>
+cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind,
+                           cudaStream_t s, int* launches);
+
+template <typename T>
+cudaError_t launch_normalise_only(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s,
+                                  int* launches);
+
+size_t part_bytes(int r_pad);
+
+}  // namespace yy

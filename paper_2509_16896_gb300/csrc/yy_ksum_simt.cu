@@ -1,0 +1,202 @@
+// Prediction step, plain form on the FMA pipes (float32 or float64).
+//
+// For every target i and scale j (tau_j = dt / 2^(j-1)), in units relative to c_ref:
+//   L_j(i) - c_ref = (C_j - c_ref) - tau_j div f(x_i)
+//                    + LSE_s [ -|u_i - tau_j f_i - u_s|^2 / (2 tau_j) + ell_s ],
+//   C_j = -(r/2) log(2 pi tau_j) + log w_q,
+// which is log sum_s K_{tau_j}(x_i, x_s) w_q e^{ell_s} for the first-order kernel of
+// eq. kernel (Section 4.3.1) after completing the square:
+//   -|x-y|^2/(2 tau) - (y-x).f(x) - tau(div f + |f|^2/2) = -|x - tau f(x) - y|^2/(2 tau) - tau div f.
+// Differences are formed first: with D = u_i - u_s, S1 = |D|^2 and S2 = D.f_i,
+//   |u_i - tau f_i - u_s|^2 = S1 - 2 tau S2 + tau^2 |f_i|^2,
+// so one pass over the coordinates serves all N scales.  The N terms are combined with
+// the identity term of eq. general_kernel by a signed log-sum-exp; a non-positive total
+// gives -inf (counted).
+//
+// Tiling: a CTA owns 64 targets and sweeps all sources in tiles of 64, staging 16
+// coordinates of the target rows, their drift and the source rows in shared memory per
+// step; each of the 256 threads holds a 4x4 block of (S1, S2) accumulators and, per
+// target and scale, an online (max, sum) of the exponentials, merged across the 16
+// threads of a target group at the end.
+#include "yy_internal.cuh"
+
+namespace yy {
+
+namespace {
+constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
+
+template <typename T> __device__ __forceinline__ T exp_fast(T x);
+template <> __device__ __forceinline__ float exp_fast<float>(float x) { return exp2f(x * 1.4426950408889634f); }
+template <> __device__ __forceinline__ double exp_fast<double>(double x) { return exp(x); }
+template <typename T> __device__ __forceinline__ T log_t(T x);
+template <> __device__ __forceinline__ float log_t<float>(float x) { return logf(x); }
+template <> __device__ __forceinline__ double log_t<double>(double x) { return log(x); }
+}  // namespace
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int rk) {
+    __shared__ T At[BK][BM];   // u of targets
+    __shared__ T Ft[BK][BM];   // f of targets
+    __shared__ T Bt[BK][BN];   // u of sources
+    __shared__ T lsrc[BN];
+
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const long long i0 = (long long)blockIdx.x * BM;
+
+    T rowc[TM][N];          // -(tau_j / 2) |f_i|^2
+    T mx[TM][N], sm[TM][N];
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+        const long long i = i0 + ty * TM + a;
+        const T nf = (i < k.n) ? b.nf[i] : T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            rowc[a][j] = -T(0.5) * k.tau[j] * nf;
+            mx[a][j] = T(-INFINITY);
+            sm[a][j] = T(0);
+        }
+    }
+
+    for (long long s0 = 0; s0 < k.n; s0 += BN) {
+        T S1[TM][TN], S2[TM][TN];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int c = 0; c < TN; ++c) { S1[a][c] = T(0); S2[a][c] = T(0); }
+        if (tid < BN) {
+            const long long s = s0 + tid;
+            lsrc[tid] = (s < k.n && !b.mask[s]) ? b.logw[s] : T(-INFINITY);
+        }
+        for (int d0 = 0; d0 < rk; d0 += BK) {
+            __syncthreads();
+            // 64 rows x 16 coordinates per operand; 256 threads x 4 values
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int e = tid + 256 * q;
+                const int row = e >> 4, col = e & 15;
+                const size_t ti = (size_t)(i0 + row) * k.r_pad + d0 + col;
+                const size_t si = (size_t)(s0 + row) * k.r_pad + d0 + col;
+                At[col][row] = (T)b.u[ti];
+                Ft[col][row] = b.f[ti];
+                Bt[col][row] = (T)b.u[si];
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < BK; ++kk) {
+                T av[TM], fv[TM], bv[TN];
+#pragma unroll
+                for (int a = 0; a < TM; ++a) { av[a] = At[kk][ty * TM + a]; fv[a] = Ft[kk][ty * TM + a]; }
+#pragma unroll
+                for (int c = 0; c < TN; ++c) bv[c] = Bt[kk][tx * TN + c];
+#pragma unroll
+                for (int a = 0; a < TM; ++a)
+#pragma unroll
+                    for (int c = 0; c < TN; ++c) {
+                        const T dlt = av[a] - bv[c];
+                        S1[a][c] = fma(dlt, dlt, S1[a][c]);
+                        S2[a][c] = fma(dlt, fv[a], S2[a][c]);
+                    }
+            }
+        }
+        // scores and online log-sum-exp for this source tile
+        T ls[TN];
+#pragma unroll
+        for (int c = 0; c < TN; ++c) ls[c] = lsrc[tx * TN + c];
+#pragma unroll
+        for (int a = 0; a < TM; ++a)
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                T sc[TN];
+                T tmax = T(-INFINITY);
+#pragma unroll
+                for (int c = 0; c < TN; ++c) {
+                    sc[c] = fma(-S1[a][c], k.inv2tau[j], S2[a][c]) + (rowc[a][j] + ls[c]);
+                    tmax = fmax(tmax, sc[c]);
+                }
+                if (tmax == T(-INFINITY)) continue;
+                if (tmax > mx[a][j]) {
+                    sm[a][j] = (mx[a][j] == T(-INFINITY)) ? T(0) : sm[a][j] * exp_fast<T>(mx[a][j] - tmax);
+                    mx[a][j] = tmax;
+                }
+#pragma unroll
+                for (int c = 0; c < TN; ++c) sm[a][j] += exp_fast<T>(sc[c] - mx[a][j]);
+            }
+        __syncthreads();
+    }
+
+    // merge the 16 threads that share a target group (lanes differing in the low 4 bits)
+#pragma unroll
+    for (int a = 0; a < TM; ++a)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            T m = mx[a][j], s = sm[a][j];
+#pragma unroll
+            for (int o = 1; o < 16; o <<= 1) {
+                const T m2 = __shfl_xor_sync(0xffffffffu, m, o);
+                const T s2 = __shfl_xor_sync(0xffffffffu, s, o);
+                if (m2 != T(-INFINITY)) {
+                    if (m == T(-INFINITY)) { m = m2; s = s2; }
+                    else if (m2 > m) { s = s * exp_fast<T>(m - m2) + s2; m = m2; }
+                    else { s += s2 * exp_fast<T>(m2 - m); }
+                }
+            }
+            mx[a][j] = m;
+            sm[a][j] = s;
+        }
+    if (tx != 0) return;
+#pragma unroll
+    for (int a = 0; a < TM; ++a) {
+        const long long i = i0 + ty * TM + a;
+        if (i >= k.n) continue;
+        if (b.mask[i]) { b.logw_pred[i] = T(-INFINITY); continue; }
+        const T divf = b.divf[i];
+        T term[N + 1], sg[N + 1];
+        T M = T(-INFINITY);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const T L = (mx[a][j] == T(-INFINITY))
+                            ? T(-INFINITY)
+                            : k.cj_off[j] - k.tau[j] * divf + mx[a][j] + log_t<T>(sm[a][j]);
+            sg[j] = k.sign_c[j];
+            term[j] = (sg[j] == T(0) || L == T(-INFINITY)) ? T(-INFINITY) : k.logabs_c[j] + L;
+            M = fmax(M, term[j]);
+        }
+        {
+            const T li = b.logw[i];
+            sg[N] = k.sign_c[N];
+            term[N] = (sg[N] == T(0) || li == T(-INFINITY))
+                          ? T(-INFINITY)
+                          : k.logabs_c[N] + (T)((double)li - k.c_ref);
+            M = fmax(M, term[N]);
+        }
+        T out = T(-INFINITY);
+        if (M != T(-INFINITY)) {
+            T S = T(0);
+#pragma unroll
+            for (int j = 0; j <= N; ++j)
+                if (term[j] != T(-INFINITY)) S += sg[j] * exp_fast<T>(term[j] - M);
+            if (S > T(0)) out = M + log_t<T>(S);
+            else atomicAdd(&b.stats->clamps, 1u);
+        }
+        b.logw_pred[i] = out;
+    }
+}
+
+template <typename T>
+cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s) {
+    const int rk = ((k.r + BK - 1) / BK) * BK;
+    const unsigned grid = (unsigned)(k.n_pad / BM);
+    switch (k.N) {
+        case 1: k_ksum_simt<T, 1><<<grid, 256, 0, s>>>(k, b, rk); break;
+        case 2: k_ksum_simt<T, 2><<<grid, 256, 0, s>>>(k, b, rk); break;
+        case 3: k_ksum_simt<T, 3><<<grid, 256, 0, s>>>(k, b, rk); break;
+        case 4: k_ksum_simt<T, 4><<<grid, 256, 0, s>>>(k, b, rk); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+template cudaError_t launch_ksum_simt<float>(const Consts<float>&, const Bufs<float>&, cudaStream_t);
+template cudaError_t launch_ksum_simt<double>(const Consts<double>&, const Bufs<double>&, cudaStream_t);
+
+}  // namespace yy

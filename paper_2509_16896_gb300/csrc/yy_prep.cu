@@ -1,0 +1,134 @@
+// Per-node preparation: drift, divergence and norms at x = c + u, Dirichlet mask, bf16
+// copy of u, and the initial or restart log-weights.
+//
+//   f(x)      cubic: cos x (componentwise); linear: a x              (Section 9.1 / 9.3)
+//   div f(x)  cubic: -sum_d sin x_d;       linear: a r
+//   mask      |u_d| >= R_d - 1e-12 R_d for some d (Section 4.2, step 3), tested in float64
+//   prior     log sigma_0(x) = -|x - mu0|^2 / (2 s0^2) + const (Section 4.2, step 4)
+//   restart   log N(x; x_hat, diag(max(v_hat, (R/4)^2))) + const, or uniform
+//             (Section 5; the density is this library's reading of "re-initialise")
+// Constants that cancel in the normalisation that follows are dropped.
+//
+// One warp per node row; lanes stride over coordinates.  x = c + u is formed in float64,
+// the model is evaluated in the working precision T.
+#include "yy_internal.cuh"
+
+namespace yy {
+
+enum PrepMode { kPrepOnly = 0, kPrepInit = 1, kPrepRestart = 2 };
+
+template <typename T>
+__device__ __forceinline__ void sincos_t(T x, T* s, T* c);
+template <>
+__device__ __forceinline__ void sincos_t<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+template <>
+__device__ __forceinline__ void sincos_t<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, int first,
+                                              double prior_mean, double prior_var, int init_kind) {
+    if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const double* cen = (mode == kPrepRestart) ? b.mean : b.centre;
+    for (long long i = warp; i < k.n_pad; i += nwarps) {
+        const float* ui = b.u + (size_t)i * k.r_pad;
+        T* fi = b.f + (size_t)i * k.r_pad;
+        if (i >= k.n) {  // padding rows: inert
+            for (int d = lane; d < k.r_pad; d += 32) fi[d] = T(0);
+            if (lane == 0) {
+                b.divf[i] = T(0);
+                b.nf[i] = T(0);
+                b.logw[i] = T(-INFINITY);
+                if (first) { b.nu[i] = T(0); b.mask[i] = 1; }
+            }
+            continue;
+        }
+        T div = T(0), nf = T(0), nu = T(0), lw = T(0);
+        int on_face = 0;
+        for (int d = lane; d < k.r_pad; d += 32) {
+            T fv = T(0);
+            if (d < k.r) {
+                const float uf = ui[d];
+                const double xd = cen[d] + (double)uf;
+                const T x = (T)xd;
+                if (k.model == YY_MODEL_CUBIC) {
+                    T s, c;
+                    sincos_t<T>(x, &s, &c);
+                    fv = c;
+                    div -= s;
+                } else {
+                    fv = k.model_a * x;
+                    div += k.model_a;
+                }
+                nf += fv * fv;
+                nu += (T)uf * (T)uf;
+                const double R = b.halfwidth[d];
+                if (fabs((double)uf) >= R - 1e-12 * R) on_face = 1;
+                if (mode == kPrepInit) {
+                    const double z = xd - prior_mean;
+                    lw -= (T)(0.5 * z * z / prior_var);
+                } else if (mode == kPrepRestart && init_kind == YY_RESTART_INIT_GAUSS) {
+                    const double R4 = 0.25 * R;
+                    const double v = fmax(b.var[d], R4 * R4);
+                    lw -= (T)(0.5 * (double)uf * (double)uf / v);
+                }
+                if (first && b.ubf) b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(uf);
+            } else if (first && b.ubf) {
+                b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(0.0f);
+            }
+            fi[d] = fv;
+        }
+        div = warp_sum(div);
+        nf = warp_sum(nf);
+        nu = warp_sum(nu);
+        lw = warp_sum(lw);
+        on_face = __any_sync(0xffffffffu, on_face);
+        if (lane == 0) {
+            b.divf[i] = div;
+            b.nf[i] = nf;
+            if (first) {
+                b.nu[i] = nu;
+                b.mask[i] = (uint8_t)on_face;
+            }
+            if (mode != kPrepOnly) b.logw[i] = b.mask[i] ? T(-INFINITY) : lw;
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, bool first,
+                             double prior_mean, double prior_var, int init_kind, cudaStream_t s) {
+    long long warps = k.n_pad;
+    long long blocks = (warps * 32 + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_prep<T><<<(unsigned)blocks, 256, 0, s>>>(k, b, mode, first ? 1 : 0, prior_mean, prior_var,
+                                                init_kind);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prep(const Consts<T>& k, const Bufs<T>& b, bool init_weights, bool first,
+                        double prior_mean, double prior_var, cudaStream_t s) {
+    return launch_prep_mode<T>(k, b, init_weights ? kPrepInit : kPrepOnly, first, prior_mean,
+                               prior_var, 0, s);
+}
+template cudaError_t launch_prep<float>(const Consts<float>&, const Bufs<float>&, bool, bool,
+                                        double, double, cudaStream_t);
+template cudaError_t launch_prep<double>(const Consts<double>&, const Bufs<double>&, bool, bool,
+                                         double, double, cudaStream_t);
+
+template cudaError_t launch_prep_mode<float>(const Consts<float>&, const Bufs<float>&, int, bool,
+                                             double, double, int, cudaStream_t);
+template cudaError_t launch_prep_mode<double>(const Consts<double>&, const Bufs<double>&, int,
+                                              bool, double, double, int, cudaStream_t);
+
+}  // namespace yy

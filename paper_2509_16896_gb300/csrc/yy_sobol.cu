@@ -1,0 +1,93 @@
+// Scrambled Sobol nodes on the device (Appendix A, "Sobol Sequence"; scrambling as in
+// "Practical considerations" there).
+//
+// k_sobol_dirs: one thread per dimension turns the generator parameters (primitive
+// polynomial x^s + a_1 x^{s-1} + ... + a_{s-1} x + 1 and initial m_1..m_s) into the 32
+// direction integers V_k = m_k 2^{32-k}, continued for k > s by
+//     V_k = V_{k-s} ^ (V_{k-s} >> s) ^ XOR_{i<s, a_i = 1} V_{k-i},
+// and pre-multiplies them by the scramble matrix (the scramble y -> L y ^ e is linear in
+// the XOR of direction integers, so L can be applied once per direction integer).
+//
+// k_sobol_points: thread per (point, dimension): XOR of the scrambled direction integers
+// selected by the Gray code g = i ^ (i >> 1), XOR the digital shift, then the box map
+// u = R (2 (y + 1/2) 2^-32 - 1) in float64 with explicit round-to-nearest operations
+// (no contraction), rounded once more to float32.
+#include "yy_internal.cuh"
+
+namespace yy {
+
+__global__ void k_sobol_dirs(const uint32_t* __restrict__ params, uint32_t* __restrict__ dirs,
+                             int r) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= r) return;
+    const uint32_t* p = params + (size_t)d * (YY_SOBOL_POLY_WORDS + YY_SOBOL_SCRAMBLE_WORDS);
+    const uint32_t* L = p + YY_SOBOL_POLY_WORDS;
+    uint32_t V[33];
+    const int s = (int)p[0];
+    const uint32_t a = p[1];
+    if (s == 0) {
+        for (int k = 1; k <= 32; ++k) V[k] = 1u << (32 - k);
+    } else {
+        for (int k = 1; k <= s && k <= 32; ++k) V[k] = p[1 + k] << (32 - k);
+        for (int k = s + 1; k <= 32; ++k) {
+            uint32_t v = V[k - s] ^ (V[k - s] >> s);
+            for (int i = 1; i < s; ++i)
+                if ((a >> (s - 1 - i)) & 1u) v ^= V[k - i];
+            V[k] = v;
+        }
+    }
+    uint32_t* out = dirs + (size_t)d * 33;
+    for (int b = 1; b <= 32; ++b) {
+        uint32_t w = 0;
+        for (int k = 1; k <= 32; ++k) w |= (uint32_t)(__popc(L[k - 1] & V[b]) & 1) << (32 - k);
+        out[b - 1] = w;
+    }
+    out[32] = L[32];
+}
+
+__global__ void k_sobol_points(const uint32_t* __restrict__ dirs, int r, int r_pad,
+                               long long first, long long count, float* __restrict__ u,
+                               uint32_t* __restrict__ bits, const double* __restrict__ halfwidth) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= r) return;
+    const uint32_t* V = dirs + (size_t)d * 33;
+    const double R = halfwidth ? halfwidth[d] : 0.0;
+    for (long long i = blockIdx.y * (long long)blockDim.y + threadIdx.y; i < count;
+         i += (long long)gridDim.y * blockDim.y) {
+        const unsigned long long idx = (unsigned long long)(first + i);
+        const uint32_t g = (uint32_t)(idx ^ (idx >> 1));
+        uint32_t y = V[32];
+#pragma unroll 8
+        for (int b = 0; b < 32; ++b)
+            if ((g >> b) & 1u) y ^= V[b];
+        if (bits) bits[(size_t)i * r + d] = y;
+        if (u) {
+            double t = __dadd_rn((double)y, 0.5);
+            t = __dmul_rn(t, 0x1p-31);      // 2 (y + 1/2) 2^-32, exact
+            t = __dsub_rn(t, 1.0);          // exact
+            u[(size_t)(first + i) * r_pad + d] = __double2float_rn(__dmul_rn(R, t));
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_sobol_dirs(const uint32_t* params, uint32_t* dirs, int r, cudaStream_t s) {
+    k_sobol_dirs<<<(r + 63) / 64, 64, 0, s>>>(params, dirs, r);
+    return cudaGetLastError();
+}
+template cudaError_t launch_sobol_dirs<float>(const uint32_t*, uint32_t*, int, cudaStream_t);
+template cudaError_t launch_sobol_dirs<double>(const uint32_t*, uint32_t*, int, cudaStream_t);
+
+cudaError_t launch_sobol_points(const uint32_t* dirs, int r, int r_pad, long long first,
+                                long long count, float* u, uint32_t* bits, const double* halfwidth,
+                                cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    dim3 block(64, 4);
+    long long gy = (count + 3) / 4;
+    if (gy > 65535) gy = 65535;
+    dim3 grid((r + 63) / 64, (unsigned)gy);
+    k_sobol_points<<<grid, block, 0, s>>>(dirs, r, r_pad, first, count, u, bits, halfwidth);
+    return cudaGetLastError();
+}
+
+}  // namespace yy

@@ -1,0 +1,362 @@
+// Correction, normalisation, estimate and restart test (Section 2.2 "Online stage" and
+// step 4, Section 7 "Observation Update" and "Normalization", Section 5).
+//
+// The Ito-corrected log-likelihood h(x).dy - dt/2 |h(x)|^2 is split as
+//     lambda(c) + sum_d dh_d (g_d - dt/2 dh_d),   dh_d = h(c_d + u_d) - h(c_d),
+//     g_d = dy_d - dt h(c_d),
+// which is an exact rewrite: lambda(c) (float64, once per step) absorbs the large common
+// part, and the per-node sum has no cancellation (cubic: dh = u (3c^2 + 3cu + u^2)).
+// The log-weights kept in T are therefore relative to c_ref + lambda(c); the absolute
+// normaliser Lambda_k = c_ref + lambda(c) + LSE(relative) is accumulated in float64.
+//
+// Passes (all coalesced, one warp per node row or one thread per coordinate):
+//   k_obs_prep     g, centre in T, lambda(c)                       (1 block)
+//   k_loglik       ell' = ell_pred + sum_d ..., per-block (max, sum) (HBM pass over u)
+//   k_lse_merge    Lambda_rel                                       (1 block, float64)
+//   k_moments      ell_hat = ell' - Lambda_rel, w = e^ell_hat; per block the weight sum,
+//                  sum of squares, weighted mean and centred second moment of u over
+//                  32-row chunks merged with Chan's update          (HBM pass over u)
+//   k_finalize     merge of the block moments (Chan, float64): x_hat = c + mean,
+//                  v_hat, ESS = W^2 / sum w^2, Z += Lambda, restart test (1 block)
+#include "yy_internal.cuh"
+
+namespace yy {
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_u(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T exp_t(T x);
+template <>
+__device__ __forceinline__ float exp_t<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
+
+// merge (m, s) pairs of a log-sum-exp: value = m + log s
+__device__ __forceinline__ void lse_merge(double& m, double& s, double m2, double s2) {
+    if (m2 == -INFINITY) return;
+    if (m == -INFINITY) { m = m2; s = s2; return; }
+    if (m2 > m) { s = s * exp(m - m2) + s2; m = m2; }
+    else { s += s2 * exp(m2 - m); }
+}
+
+size_t part_bytes(int r_pad) {
+    return (size_t)kNumPartBlocks * (size_t)(4 + 2 * r_pad) * sizeof(double);
+}
+
+template <typename T>
+__global__ void k_obs_prep(Consts<T> k, Bufs<T> b, const double* __restrict__ dy) {
+    __shared__ double red[32];
+    double acc = 0.0;
+    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
+        if (d < k.r) {
+            const double c = b.centre[d];
+            const double hc = (k.model == YY_MODEL_CUBIC) ? c * c * c : c;
+            const double y = dy[d];
+            b.obs_g[d] = (T)(y - (double)k.dt * hc);
+            b.obs_c[d] = (T)c;
+            acc += hc * y - 0.5 * (double)k.dt * hc * hc;
+        } else {
+            b.obs_g[d] = T(0);
+            b.obs_c[d] = T(0);
+        }
+    }
+    acc = warp_sum_u(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        v = warp_sum_u(v);
+        if (threadIdx.x == 0) b.stats->lam_c = v;
+    }
+}
+
+// ell'(i) = ell_pred(i) + sum_d dh_d (g_d - dt/2 dh_d); per-block (max, sum) partials.
+template <typename T>
+__global__ void __launch_bounds__(256) k_loglik(Consts<T> k, Bufs<T> b) {
+    __shared__ double sm[8], ss[8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const T half_dt = T(0.5) * k.dt;
+    double m = -INFINITY, s = 0.0;
+    for (long long i = warp; i < k.n; i += nwarps) {
+        const T p = b.logw_pred[i];
+        const float* ui = b.u + (size_t)i * k.r_pad;
+        T acc = T(0);
+        for (int d = lane; d < k.r; d += 32) {
+            const T u = (T)ui[d];
+            const T c = b.obs_c[d];
+            const T dh = (k.model == YY_MODEL_CUBIC) ? u * (T(3) * c * c + T(3) * c * u + u * u) : u;
+            acc += dh * (b.obs_g[d] - half_dt * dh);
+        }
+        acc = warp_sum_u(acc);
+        const T lw = (p == T(-INFINITY)) ? T(-INFINITY) : p + acc;
+        if (lane == 0) b.logw[i] = lw;
+        lse_merge(m, s, (double)lw, 1.0);
+    }
+    if (lane == 0) { sm[wib] = m; ss[wib] = s; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double M = -INFINITY, S = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge(M, S, sm[w], ss[w]);
+        b.part[2 * blockIdx.x] = M;
+        b.part[2 * blockIdx.x + 1] = S;
+    }
+}
+
+// LSE partials of b.logw (used after init / restart weights).
+template <typename T>
+__global__ void __launch_bounds__(256) k_lse_partials(Consts<T> k, Bufs<T> b, int conditional) {
+    if (conditional && b.stats->restart_flag == 0) return;
+    __shared__ double sm[8], ss[8];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    double m = -INFINITY, s = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.n;
+         i += (long long)gridDim.x * blockDim.x)
+        lse_merge(m, s, (double)b.logw[i], 1.0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double m2 = __shfl_xor_sync(0xffffffffu, m, o);
+        const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        lse_merge(m, s, m2, s2);
+    }
+    if (lane == 0) { sm[wib] = m; ss[wib] = s; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double M = -INFINITY, S = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge(M, S, sm[w], ss[w]);
+        b.part[2 * blockIdx.x] = M;
+        b.part[2 * blockIdx.x + 1] = S;
+    }
+}
+
+__global__ void k_lse_merge(const double* __restrict__ part, int nb, DevStats* st, int conditional) {
+    if (conditional && st->restart_flag == 0) return;
+    __shared__ double sm[32], ss[32];
+    double m = -INFINITY, s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) lse_merge(m, s, part[2 * i], part[2 * i + 1]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double m2 = __shfl_xor_sync(0xffffffffu, m, o);
+        const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
+        lse_merge(m, s, m2, s2);
+    }
+    if ((threadIdx.x & 31) == 0) { sm[threadIdx.x >> 5] = m; ss[threadIdx.x >> 5] = s; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double M = -INFINITY, S = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge(M, S, sm[w], ss[w]);
+        if (M == -INFINITY) {
+            st->status |= kStatusDegenerate;
+            st->lam_rel = 0.0;
+        } else {
+            st->lam_rel = M + log(S);
+            if (!isfinite(st->lam_rel)) { st->status |= kStatusNonFinite; st->lam_rel = 0.0; }
+        }
+    }
+}
+
+template <typename T>
+__global__ void k_subtract(Consts<T> k, Bufs<T> b, int conditional) {
+    if (conditional && b.stats->restart_flag == 0) return;
+    const T lam = (T)b.stats->lam_rel;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.n;
+         i += (long long)gridDim.x * blockDim.x)
+        b.logw[i] = b.logw[i] - lam;
+}
+
+constexpr int kMomDims = YY_MAX_DIM / 256;   // coordinates per thread in k_moments
+
+// Normalises ell' and accumulates per-block weighted moments of u.
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments(Consts<T> k, Bufs<T> b) {
+    __shared__ T w_s[32];
+    __shared__ double wc_s[2];
+    const int tid = threadIdx.x;
+    const long long rows_per = (k.n + gridDim.x - 1) / gridDim.x;
+    const long long i0 = blockIdx.x * rows_per;
+    const long long i1 = min(k.n, i0 + rows_per);
+    const T lam = (T)b.stats->lam_rel;
+    double W = 0.0, Q = 0.0;
+    double mu[kMomDims], M2[kMomDims];
+#pragma unroll
+    for (int q = 0; q < kMomDims; ++q) { mu[q] = 0.0; M2[q] = 0.0; }
+    for (long long c0 = i0; c0 < i1; c0 += 32) {
+        const int cn = (int)min((long long)32, i1 - c0);
+        if (tid < 32) {
+            T w = T(0);
+            if (tid < cn) {
+                const T lh = b.logw[c0 + tid] - lam;
+                b.logw[c0 + tid] = lh;
+                w = exp_t<T>(lh);
+            }
+            w_s[tid] = w;
+            const double wsum = warp_sum_u((double)w);
+            const double wsq = warp_sum_u((double)w * (double)w);
+            if (tid == 0) { wc_s[0] = wsum; wc_s[1] = wsq; }
+        }
+        __syncthreads();
+        const double Wc = wc_s[0];
+        if (Wc > 0.0) {
+#pragma unroll
+            for (int q = 0; q < kMomDims; ++q) {
+                const int d = tid + 256 * q;
+                if (d < k.r) {
+                    T S = T(0);
+                    for (int l = 0; l < cn; ++l) S += w_s[l] * (T)b.u[(size_t)(c0 + l) * k.r_pad + d];
+                    const T muc = S / (T)Wc;
+                    T m2 = T(0);
+                    for (int l = 0; l < cn; ++l) {
+                        const T dv = (T)b.u[(size_t)(c0 + l) * k.r_pad + d] - muc;
+                        m2 += w_s[l] * dv * dv;
+                    }
+                    const double delta = (double)muc - mu[q];
+                    const double Wn = W + Wc;
+                    mu[q] += delta * (Wc / Wn);
+                    M2[q] += (double)m2 + delta * delta * (W * Wc / Wn);
+                }
+            }
+            W += Wc;
+            Q += wc_s[1];
+        }
+        __syncthreads();
+    }
+    double* p = b.part + (size_t)blockIdx.x * (4 + 2 * k.r_pad);
+    if (tid == 0) { p[0] = W; p[1] = Q; }
+#pragma unroll
+    for (int q = 0; q < kMomDims; ++q) {
+        const int d = tid + 256 * q;
+        if (d < k.r_pad) { p[4 + d] = mu[q]; p[4 + k.r_pad + d] = M2[q]; }
+    }
+}
+
+template <typename T>
+__global__ void k_finalize(Consts<T> k, Bufs<T> b, int nb, int restart_interval, double ess_frac) {
+    __shared__ double Wtot_s, Q_s;
+    DevStats* st = b.stats;
+    if (threadIdx.x == 0) {
+        double W = 0.0, Q = 0.0;
+        for (int j = 0; j < nb; ++j) {
+            const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
+            W += p[0];
+            Q += p[1];
+        }
+        Wtot_s = W;
+        Q_s = Q;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < k.r; d += blockDim.x) {
+        double W = 0.0, mu = 0.0, M2 = 0.0;
+        for (int j = 0; j < nb; ++j) {
+            const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
+            const double Wc = p[0];
+            if (!(Wc > 0.0)) continue;
+            const double delta = p[4 + d] - mu;
+            const double Wn = W + Wc;
+            mu += delta * (Wc / Wn);
+            M2 += p[4 + k.r_pad + d] + delta * delta * (W * Wc / Wn);
+            W = Wn;
+        }
+        const double mean = b.centre[d] + mu;
+        const double var = (W > 0.0) ? M2 / W : 0.0;
+        b.mean[d] = mean;
+        b.var[d] = var;
+        if (!isfinite(mean) || !isfinite(var)) atomicOr(&st->status, kStatusNonFinite);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double W = Wtot_s, Q = Q_s;
+        st->wsum = W;
+        st->wsq = Q;
+        const double ess = (Q > 0.0) ? W * W / Q : 0.0;
+        st->ess = ess;
+        const double lam = k.c_ref + st->lam_c + st->lam_rel;
+        st->lam = lam;
+        st->lognorm += lam;
+        if (!isfinite(lam)) st->status |= kStatusNonFinite;
+        st->step += 1;
+        const bool by_ess = ess_frac > 0.0 && ess < ess_frac * (double)k.n;
+        const bool by_int = restart_interval >= 2 && (st->step % restart_interval) == 0;
+        st->restart_flag = (by_ess || by_int) ? 1 : 0;
+    }
+}
+
+template <typename T>
+cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy,
+                          int restart_interval, double ess_frac, cudaStream_t s, int* launches) {
+    const int nb = kNumPartBlocks;
+    k_obs_prep<T><<<1, 256, 0, s>>>(k, b, dy);
+    k_loglik<T><<<nb, 256, 0, s>>>(k, b);
+    k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 0);
+    k_moments<T><<<nb, 256, 0, s>>>(k, b);
+    k_finalize<T><<<1, 256, 0, s>>>(k, b, nb, restart_interval, ess_frac);
+    if (launches) *launches += 5;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_normalise_only(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s,
+                                  int* launches) {
+    const int nb = kNumPartBlocks;
+    k_lse_partials<T><<<nb, 256, 0, s>>>(k, b, 0);
+    k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 0);
+    k_subtract<T><<<nb, 256, 0, s>>>(k, b, 0);
+    if (launches) *launches += 3;
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void k_restart_begin(DevStats* st, int mode) {
+    if (mode == YY_RESTART_FORCE) st->restart_flag = 1;
+    st->last_restarted = 0;
+}
+
+template <typename T>
+__global__ void k_restart_commit(Consts<T> k, Bufs<T> b) {
+    if (b.stats->restart_flag == 0) return;
+    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) b.centre[d] = (d < k.r) ? b.mean[d] : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        b.stats->restarts += 1;
+        b.stats->restart_flag = 0;
+        b.stats->last_restarted = 1;
+    }
+}
+
+template <typename T>
+cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, bool first,
+                             double prior_mean, double prior_var, int init_kind, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind,
+                           cudaStream_t s, int* launches) {
+    if (mode == YY_RESTART_NEVER) return cudaSuccess;
+    const int nb = kNumPartBlocks;
+    k_restart_begin<T><<<1, 1, 0, s>>>(b.stats, mode);
+    cudaError_t e = launch_prep_mode<T>(k, b, 2 /*restart*/, false, 0.0, 1.0, init_kind, s);
+    if (e != cudaSuccess) return e;
+    k_lse_partials<T><<<nb, 256, 0, s>>>(k, b, 1);
+    k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 1);
+    k_subtract<T><<<nb, 256, 0, s>>>(k, b, 1);
+    k_restart_commit<T><<<1, 256, 0, s>>>(k, b);
+    if (launches) *launches += 6;
+    return cudaGetLastError();
+}
+
+#define YY_INST(T)                                                                             \
+    template cudaError_t launch_update<T>(const Consts<T>&, const Bufs<T>&, const double*, int, \
+                                          double, cudaStream_t, int*);                         \
+    template cudaError_t launch_normalise_only<T>(const Consts<T>&, const Bufs<T>&,             \
+                                                  cudaStream_t, int*);                          \
+    template cudaError_t launch_restart<T>(const Consts<T>&, const Bufs<T>&, int, int,          \
+                                           cudaStream_t, int*);
+YY_INST(float)
+YY_INST(double)
+#undef YY_INST
+
+}  // namespace yy

@@ -1,0 +1,80 @@
+"""The C-ABI library loads and exports every symbol include/yy.h declares; argument
+checks that return before any CUDA call.  No GPU needed."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2509_16896_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "yy.h")).read()
+    return sorted(set(re.findall(r"YY_EXPORT\s+[\w\s\*]+?\b(yy_\w+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    try:
+        return binding.load()
+    except FileNotFoundError as e:   # no nvcc on this machine
+        pytest.skip(str(e))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared_symbols()
+    assert len(declared) >= 16
+    assert sorted(binding.EXPORTS) == sorted(declared)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def _cfg(**kw):
+    base = dict(model="cubic", r=8, n=100, dt=0.01, R=0.3, n_scales=2, precision="f32")
+    base.update(kw)
+    return binding.make_config(**base)
+
+
+def test_workspace_bytes_and_invalid_configs(lib):
+    good = _cfg()
+    assert lib.yy_workspace_bytes(ctypes.byref(good)) > 0
+    bad = [_cfg(r=0), _cfg(n=1), _cfg(dt=0.0), _cfg(R=-1.0), _cfg(n_scales=0), _cfg(n_scales=5),
+           _cfg(r=1025), _cfg(ess_frac=1.5)]
+    for c in bad:
+        assert lib.yy_workspace_bytes(ctypes.byref(c)) == 0
+        h = ctypes.c_void_p()
+        assert lib.yy_create(ctypes.byref(c), ctypes.c_void_p(1 << 20), 1 << 30, None,
+                             ctypes.byref(h)) == 1   # YY_ERR_ARG
+    c = _cfg()
+    c.m = 3
+    assert lib.yy_workspace_bytes(ctypes.byref(c)) == 0
+
+
+def test_workspace_checks_before_any_launch(lib):
+    c = _cfg()
+    need = lib.yy_workspace_bytes(ctypes.byref(c))
+    h = ctypes.c_void_p()
+    # misaligned, too small, missing: rejected without touching the device
+    assert lib.yy_create(ctypes.byref(c), ctypes.c_void_p((1 << 20) + 8), need, None, ctypes.byref(h)) == 3
+    assert lib.yy_create(ctypes.byref(c), ctypes.c_void_p(1 << 20), need - 1, None, ctypes.byref(h)) == 3
+    assert lib.yy_create(ctypes.byref(c), None, need, None, ctypes.byref(h)) == 3
+
+
+def test_null_handle_calls_return_arg_error(lib):
+    assert lib.yy_predict(None) == 1
+    assert lib.yy_update(None, None) == 1
+    assert lib.yy_estimate(None, None, None, None, None) == 1
+    assert lib.yy_restart(None, 0, None) == 1
+    assert lib.yy_destroy(None) == 0
+    assert lib.yy_launch_count(None) == 0
+    assert lib.yy_status_str(3).startswith(b"YY_ERR_WORKSPACE")
+
+
+def test_workspace_grows_with_problem(lib):
+    small = lib.yy_workspace_bytes(ctypes.byref(_cfg(n=1000, r=10)))
+    big = lib.yy_workspace_bytes(ctypes.byref(_cfg(n=65536, r=1000, precision="bf16", n_scales=3)))
+    # u, f (float32) and the bf16 copy: >= 10 bytes per padded coordinate
+    assert big >= 65536 * 1024 * 10 > small

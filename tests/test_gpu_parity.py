@@ -1,0 +1,213 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same seeded inputs.
+
+Bars: node integers, float32 coordinates, the boundary mask and -inf patterns bit-exact;
+FP64 path within 1e-10 relative; FP32 path within 1e-5 relative (max(1, |value|) for
+log-weights and the normaliser, |value| for variances, n-relative for ESS).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from synth import simulate
+
+from ._helpers import oracle_problem, rel_err, sobol_inputs
+
+pytestmark = pytest.mark.gpu
+
+# id: (model, r, n, R, N, precision, seed)
+CASES = {
+    "c1_f64": ("cubic", 2, 1024, 4.0, 2, "f64", 1),
+    "c1_f32": ("cubic", 2, 1024, 4.0, 2, "f32", 1),
+    "ragged_f32": ("cubic", 17, 1000, 0.3, 3, "f32", 2),
+    "linear_f32": ("linear", 3, 777, 2.0, 1, "f32", 3),
+    "r100_f32": ("cubic", 100, 2048, 0.3, 2, "f32", 4),
+    "r1_f64_N4": ("linear", 1, 300, 5.0, 4, "f64", 5),
+    "wide_f32": ("cubic", 130, 513, 0.3, 2, "f32", 6),
+}
+TOL = {"f64": 1e-10, "f32": 1e-5}
+
+
+def _make(case, restart_interval=0, ess_frac=0.0, scrambled=True, restart_init="gauss"):
+    from paper_2509_16896_gb300 import binding
+    model, r, n, R, N, prec, seed = case
+    cfg = binding.make_config(model=model, r=r, n=n, dt=0.01, R=R, n_scales=N, precision=prec,
+                              restart_interval=restart_interval, ess_frac=ess_frac,
+                              restart_init=restart_init)
+    flt = binding.Filter(cfg)
+    poly, scr = sobol_inputs(r, seed, scrambled)
+    flt.init_nodes(poly, scr, np.zeros(r))
+    p = oracle_problem(model, r, n, 0.01, R, N, restart_interval, ess_frac, restart_init=restart_init)
+    return flt, p, poly, scr
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_nodes_bit_exact(yy_lib, name):
+    from oracle import filter as F, sobol
+    flt, p, poly, scr = _make(CASES[name])
+    y_or, u_or = sobol.nodes(poly, scr, p.n, p.R[0])
+    u, mask = flt.get_nodes()
+    assert u.dtype == np.float32 and np.array_equal(u.view(np.uint32), u_or.view(np.uint32))
+    bits = flt.sobol_bits(0, p.n).cpu().numpy().view(np.uint32)
+    assert np.array_equal(bits, y_or)
+    assert np.array_equal(mask, F.boundary_mask(u_or, p.R))
+
+
+def test_unscrambled_corner_node_is_masked(yy_lib):
+    """Unscrambled point 0 maps to R (2^-32 - 1), which rounds to -R in float32: on the
+    face, so it is masked as source and target (Section 4.2, step 3)."""
+    from oracle import filter as F
+    flt, p, poly, scr = _make(CASES["ragged_f32"], scrambled=False)
+    u, mask = flt.get_nodes()
+    assert mask[0] and mask.sum() >= 1
+    st = F.init_state(p, u, np.zeros(p.r))
+    flt.set_state(np.zeros(p.r), st.logw.astype(np.float32), 0.0, 0)
+    flt.predict()
+    lw, off = flt.get_log_weights()
+    assert np.isneginf(lw[0])
+    prep = F.prepare(p, u, np.zeros(p.r))
+    ref, _ = F.predict(p, prep, st.logw)
+    assert rel_err(lw.astype(np.float64) + off, ref) <= TOL["f32"]
+
+
+def _oracle_state(p, u, steps, seed):
+    """Runs the oracle a few steps from the prior to get a non-trivial state."""
+    from oracle import filter as F
+    tr = simulate(p.model, p.r, steps + 1, p.dt, seed=seed + 100)
+    st = F.init_state(p, u, np.zeros(p.r))
+    for k in range(steps):
+        _, st = F.step(p, st, tr.dy[k])
+    return st, tr.dy[steps]
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_step_local_parity(yy_lib, name):
+    import torch
+    from oracle import filter as F
+    case = CASES[name]
+    prec = case[5]
+    tol = TOL[prec]
+    flt, p, poly, scr = _make(case)
+    u, _ = flt.get_nodes()
+    st, dy = _oracle_state(p, u, 2, case[6])
+    T = np.float64 if prec == "f64" else np.float32
+    flt.set_state(st.centre, st.logw.astype(T), st.lognorm, st.k)
+    # prediction
+    flt.predict()
+    lw_pred, off = flt.get_log_weights()
+    prep = F.prepare(p, u, st.centre)
+    ref_pred, ref_clamps = F.predict(p, prep, st.logw.astype(T).astype(np.float64))
+    assert rel_err(lw_pred.astype(np.float64) + off, ref_pred) <= tol
+    assert flt.clamps() == ref_clamps
+    # correction, normalisation, estimate
+    flt.update(torch.tensor(dy, dtype=torch.float64, device="cuda"))
+    mean, var, ess, z = flt.estimate()
+    lw_hat, off2 = flt.get_log_weights()
+    assert off2 == 0.0
+    st_in = F.State(u=u, centre=st.centre, logw=st.logw.astype(T).astype(np.float64),
+                    lognorm=st.lognorm, k=st.k)
+    rec, _ = F.step(p, st_in, dy, keep_logw=True)
+    assert rel_err(lw_hat, rec.logw_hat) <= tol
+    assert np.max(np.abs(mean - rec.mean) / np.maximum(1.0, np.abs(rec.mean))) <= tol
+    assert np.all(np.abs(var - rec.var) <= tol * np.abs(rec.var) + 1e-12)
+    assert abs(ess - rec.ess) <= tol * rec.ess
+    assert abs(z - rec.lognorm) <= tol * max(1.0, abs(rec.lognorm))
+
+
+@pytest.mark.parametrize("name", ["ragged_f32", "c1_f64", "linear_f32"])
+@pytest.mark.parametrize("init", ["gauss", "uniform"])
+def test_restart_parity(yy_lib, name, init):
+    import torch
+    from oracle import filter as F
+    case = CASES[name]
+    prec = case[5]
+    tol = TOL[prec]
+    flt, p, poly, scr = _make(case, restart_init=init)
+    u, _ = flt.get_nodes()
+    st, dy = _oracle_state(p, u, 1, case[6])
+    T = np.float64 if prec == "f64" else np.float32
+    flt.set_state(st.centre, st.logw.astype(T), st.lognorm, st.k)
+    flt.predict()
+    flt.update(torch.tensor(dy, dtype=torch.float64, device="cuda"))
+    mean, var, ess, z = flt.estimate()
+    assert flt.restart(mode=1, report=True) is True   # FORCE
+    cen, z2, k2 = flt.get_state()
+    assert np.array_equal(cen, mean) and z2 == z and k2 == st.k + 1
+    lw, _ = flt.get_log_weights()
+    # oracle restart from the GPU's own estimate: the comparison isolates the restart
+    prep2 = F.prepare(p, u, mean)
+    ref = F.restart_logw(p, prep2.x, mean, var)
+    ref[prep2.mask] = -np.inf
+    assert rel_err(lw, ref) <= tol
+    assert flt.restart(mode=2, report=True) in (False, True)   # NEVER: report only
+
+
+def test_whole_run_fp64_matches_oracle(yy_lib):
+    """Plain method in FP64, r = 2, n = 1024, R = 4, N = 2, 100 steps, no restart."""
+    import torch
+    from oracle import filter as F, metrics
+    case = CASES["c1_f64"]
+    flt, p, poly, scr = _make(case)
+    u, _ = flt.get_nodes()
+    tr = simulate("cubic", 2, 100, 0.01, seed=1)
+    recs = F.run(p, F.init_state(p, u, np.zeros(2)), tr.dy)
+    dys = torch.tensor(tr.dy, dtype=torch.float64, device="cuda")
+    est = []
+    for k in range(100):
+        flt.predict()
+        flt.update(dys[k])
+        m, v, e, z = flt.estimate()
+        est.append(m)
+    est = np.array(est)
+    ref = np.array([q.mean for q in recs])
+    assert np.max(np.abs(est - ref)) <= 1e-9
+    assert abs(metrics.rmse(est, tr.x) - metrics.rmse(ref, tr.x)) <= 1e-9
+
+
+def test_whole_run_fp32_with_restarts(yy_lib):
+    """r = 17, n = 1000, interval restarts every 2 steps: trajectories stay together."""
+    import torch
+    from oracle import filter as F, metrics
+    case = CASES["ragged_f32"]
+    flt, p, poly, scr = _make(case, restart_interval=2)
+    u, _ = flt.get_nodes()
+    K = 20
+    tr = simulate("cubic", 17, K, 0.01, seed=7)
+    recs = F.run(p, F.init_state(p, u, np.zeros(17)), tr.dy)
+    dys = torch.tensor(tr.dy, dtype=torch.float64, device="cuda")
+    est = []
+    for k in range(K):
+        flt.predict()
+        flt.update(dys[k])
+        est.append(flt.estimate()[0])
+        flt.restart(mode=0)
+    est = np.array(est)
+    ref = np.array([q.mean for q in recs])
+    assert np.max(np.abs(est - ref)) <= 1e-4
+    assert abs(metrics.rmse(est, tr.x) - metrics.rmse(ref, tr.x)) <= 1e-3 * float(np.sqrt(np.mean(tr.x ** 2)))
+
+
+def test_degenerate_weights_are_reported(yy_lib):
+    import torch
+    from paper_2509_16896_gb300 import binding
+    flt, p, poly, scr = _make(CASES["linear_f32"])
+    flt.set_state(np.zeros(p.r), np.full(p.n, -np.inf, dtype=np.float32), 0.0, 0)
+    flt.predict()
+    flt.update(torch.zeros(p.r, dtype=torch.float64, device="cuda"))
+    with pytest.raises(binding.YYError) as ei:
+        flt.estimate()
+    assert ei.value.code == 5   # YY_ERR_DEGENERATE
+
+
+def test_call_order_is_checked(yy_lib):
+    import torch
+    from paper_2509_16896_gb300 import binding
+    cfg = binding.make_config(model="cubic", r=4, n=64, dt=0.01, R=0.3, n_scales=2, precision="f32")
+    flt = binding.Filter(cfg)
+    with pytest.raises(binding.YYError) as ei:
+        flt.predict()
+    assert ei.value.code == 7
+    poly, scr = sobol_inputs(4, 1)
+    flt.init_nodes(poly, scr, np.zeros(4))
+    with pytest.raises(binding.YYError):
+        flt.update(torch.zeros(4, dtype=torch.float64, device="cuda"))   # no predict yet
