@@ -87,14 +87,9 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.part = cv.take<double>(part_bytes(r_pad));
     b.stats = cv.take<DevStats>(sizeof(DevStats));
     if (c->precision == YY_PREC_BF16) {
-        const size_t tc = tc_scratch_bytes(n_pad, c->n_scales);
-        char* t = cv.take<char>(tc);
-        b.cand_count = reinterpret_cast<int*>(t);
-        b.row_state = t ? reinterpret_cast<float*>(t + 256) : nullptr;
-        const size_t rs = (size_t)n_pad * 2 * c->n_scales * sizeof(float);
-        const size_t rs_al = (rs + 255) & ~(size_t)255;
-        b.cand = t ? reinterpret_cast<int2*>(t + 256 + rs_al) : nullptr;
-        b.cand_cap = (long long)((tc - 256 - rs_al) / sizeof(int2));
+        b.tc_q = cv.take<float>((size_t)n_pad * sizeof(float));
+        b.tc_tile_lmax = cv.take<float>((size_t)(n_pad / 256) * sizeof(float));
+        b.tc_tile_numax = cv.take<float>((size_t)(n_pad / 256) * sizeof(float));
     }
     if (out) *out = b;
     return cv.off + 256;

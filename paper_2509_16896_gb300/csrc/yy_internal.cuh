@@ -78,10 +78,9 @@ struct Bufs {
     double* part;         // reduction partials
     DevStats* stats;
     // BF16 path scratch
-    int* cand_count;      // [1]
-    int2* cand;           // [cand_cap] (target, source) pairs
-    float* row_state;     // [n_pad][2 * N] online (max, sum) per target and scale
-    long long cand_cap;
+    float* tc_q;          // [n_pad] |u_s|^2 of live sources, 3e38 for dead ones
+    float* tc_tile_lmax;  // [n_pad / 256] max live log-weight per source tile
+    float* tc_tile_numax; // [n_pad / 256] max |u_s|^2 per source tile
 };
 
 // Launch helpers (defined in the .cu files).
@@ -99,7 +98,7 @@ template <typename T>
 cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s);
 cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s,
                            int* launches);
-size_t tc_scratch_bytes(long long n_pad, int N);
+size_t tc_scratch_bytes(long long n_pad);
 
 template <typename T>
 cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy,

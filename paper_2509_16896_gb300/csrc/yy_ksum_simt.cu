@@ -18,7 +18,7 @@
 // step; each of the 256 threads holds a 4x4 block of (S1, S2) accumulators and, per
 // target and scale, an online (max, sum) of the exponentials, merged across the 16
 // threads of a target group at the end.
-#include "yy_internal.cuh"
+#include "yy_combine.cuh"
 
 namespace yy {
 
@@ -28,9 +28,6 @@ constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
 template <typename T> __device__ __forceinline__ T exp_fast(T x);
 template <> __device__ __forceinline__ float exp_fast<float>(float x) { return exp2f(x * 1.4426950408889634f); }
 template <> __device__ __forceinline__ double exp_fast<double>(double x) { return exp(x); }
-template <typename T> __device__ __forceinline__ T log_t(T x);
-template <> __device__ __forceinline__ float log_t<float>(float x) { return logf(x); }
-template <> __device__ __forceinline__ double log_t<double>(double x) { return log(x); }
 }  // namespace
 
 template <typename T, int N>
@@ -150,36 +147,7 @@ __global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int r
         const long long i = i0 + ty * TM + a;
         if (i >= k.n) continue;
         if (b.mask[i]) { b.logw_pred[i] = T(-INFINITY); continue; }
-        const T divf = b.divf[i];
-        T term[N + 1], sg[N + 1];
-        T M = T(-INFINITY);
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const T L = (mx[a][j] == T(-INFINITY))
-                            ? T(-INFINITY)
-                            : k.cj_off[j] - k.tau[j] * divf + mx[a][j] + log_t<T>(sm[a][j]);
-            sg[j] = k.sign_c[j];
-            term[j] = (sg[j] == T(0) || L == T(-INFINITY)) ? T(-INFINITY) : k.logabs_c[j] + L;
-            M = fmax(M, term[j]);
-        }
-        {
-            const T li = b.logw[i];
-            sg[N] = k.sign_c[N];
-            term[N] = (sg[N] == T(0) || li == T(-INFINITY))
-                          ? T(-INFINITY)
-                          : k.logabs_c[N] + (T)((double)li - k.c_ref);
-            M = fmax(M, term[N]);
-        }
-        T out = T(-INFINITY);
-        if (M != T(-INFINITY)) {
-            T S = T(0);
-#pragma unroll
-            for (int j = 0; j <= N; ++j)
-                if (term[j] != T(-INFINITY)) S += sg[j] * exp_fast<T>(term[j] - M);
-            if (S > T(0)) out = M + log_t<T>(S);
-            else atomicAdd(&b.stats->clamps, 1u);
-        }
-        b.logw_pred[i] = out;
+        b.logw_pred[i] = combine_scales<T, N>(k, mx[a], sm[a], b.divf[i], b.logw[i], &b.stats->clamps);
     }
 }
 

@@ -1,14 +1,490 @@
-// Prediction step, BF16 tensor-core screening + exact float32 evaluation (placeholder).
-#include "yy_internal.cuh"
+// Prediction step on the 5th-generation tensor cores (sm_103a): BF16 Gram screening on
+// tcgen05 + exact float32 evaluation of the surviving pairs.
+//
+// The kernel sum of the prediction (Section 4, eq. general_kernel; Section 7) is, per
+// target i and scale j, a log-sum-exp over sources s of
+//     score_j(i, s) = -|u_i - tau_j f_i - u_s|^2 / (2 tau_j) + ell_s.
+// In high dimension almost every term is smaller than the largest one by hundreds of
+// nats, so it is computed as a flash-attention-style tile loop that never materialises the
+// n x n matrix and only spends exponentials where they matter:
+//
+//  1. G = U_t U_s^T on tcgen05 (BF16 operands staged by TMA in 128-byte-swizzled shared
+//     memory, FP32 accumulators in TMEM, double-buffered so the MMA of source tile t+1
+//     overlaps the screening of tile t);
+//  2. |u_i - u_s|^2 ~= |u_i|^2 + |u_s|^2 - 2 G with a rigorous error bound
+//     (|dG| <= 2^-6 |u_i||u_s| for BF16 operands with FP32 accumulation, plus float32
+//     rounding);
+//  3. by the triangle inequality |u_i - tau f_i - u_s| >= |u_i - u_s| - tau |f_i|, a pair
+//     whose distance exceeds rho_i = max_j [tau_j |f_i| + sqrt(2 tau_j max(0, lmax - M_j(i)
+//     + T))] has score_j < M_j(i) - T for every scale, where M_j(i) is the running maximum
+//     of exact scores (a lower bound of the row maximum; it starts at the exact self term)
+//     and lmax the largest source log-weight of the tile.  With T = ln n + 20 the skipped
+//     terms add at most e^-20 relative mass;
+//  4. pairs that survive the screen are evaluated exactly in float32 from the float32
+//     node coordinates (difference form, warp-cooperative over the coordinates) and fed
+//     to the online log-sum-exp of their target row.
+//
+// CTA = one tile of 128 targets over all sources (source tiles of 256).  Warp roles:
+// warp 0 issues TMA loads, warp 1 allocates TMEM and issues tcgen05.mma (one thread),
+// warps 2-5 read the accumulators with tcgen05.ld (each warp its TMEM lane quarter, one
+// target row per thread) and screen.  Every wait is bounded (%globaltimer); on expiry the
+// kernel records YY_ERR_TIMEOUT in the status word, drains its own copies and MMAs with a
+// bounded wait, frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "yy_combine.cuh"
 
 namespace yy {
 
-size_t tc_scratch_bytes(long long n_pad, int N) {
-    return 256 + (size_t)n_pad * 2 * N * sizeof(float) + 256 + (size_t)n_pad * 16 * sizeof(int2);
+namespace tc {
+constexpr int BM = 128;      // targets per CTA (UMMA M)
+constexpr int BN = 256;      // sources per tile (UMMA N)
+constexpr int BK = 64;       // coordinates per stage: 64 bf16 = one 128-byte swizzle row
+constexpr int UK = 16;       // K of one tcgen05.mma kind::f16
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int NUM_THREADS = 192;
+constexpr int EPI_WARPS = 4;
+constexpr uint32_t TMEM_COLS = 512;   // two accumulators of BN fp32 columns
+constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_WARPS * BN * 4 + 256;
+// kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1),
+// B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+constexpr unsigned long long kTimeoutNs = 4000000000ull;
+constexpr float kEpsGram = 0.015625f;   // 2^-6
+constexpr float kDeadQ = 3.0e38f;
+constexpr float kThetaMax = 1.0e30f;
+}  // namespace tc
+
+namespace {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false when the limit expired (status recorded) or another role aborted.
+__device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                             unsigned int* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > tc::kTimeoutNs) {
+            *abort_flag = 1;
+            atomicOr(status, kStatusTimeout);
+            return false;
+        }
+    }
+}
+// Bounded wait used while draining after an abort (ignores the abort flag).
+__device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer() - t0 > tc::kTimeoutNs) return;
+}
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle: start address,
+// leading byte offset 16 (unused for this layout), stride byte offset 1024 (8 rows of 128
+// bytes), descriptor version 1, layout SWIZZLE_128B (2) in bits 61-63.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(tc::IDESC), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Screening threshold on |u_s|^2 - 2 G for one target row (see the file comment).
+template <int N>
+__device__ __forceinline__ float screen_theta(const Consts<float>& k, bool live, float nu_i, float Fi,
+                                              const float (&mx)[N], float lmax, float numax, float T) {
+    if (!live || lmax == -INFINITY) return -INFINITY;
+    float rho = 0.f;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        if (mx[j] == -INFINITY) return tc::kThetaMax;
+        const float gap = fmaxf(lmax - mx[j] + T, 0.f);
+        rho = fmaxf(rho, k.tau[j] * Fi + sqrtf(2.f * k.tau[j] * gap));
+    }
+    const float err = 2.f * tc::kEpsGram * sqrtf(nu_i * numax) + 1e-6f * (nu_i + numax + rho * rho);
+    return fminf(rho * rho + err - nu_i, tc::kThetaMax);
 }
 
-cudaError_t launch_ksum_tc(const Consts<float>&, const Bufs<float>&, cudaStream_t, int*) {
-    return cudaErrorNotSupported;
+}  // namespace
+
+// Per source tile: |u_s|^2 of live sources (kDeadQ for masked, padded or -inf ones), the
+// largest live log-weight and the largest live |u_s|^2.
+__global__ void __launch_bounds__(256) k_tc_colprep(Consts<float> k, Bufs<float> b) {
+    __shared__ float red_l[8], red_n[8];
+    const long long s = (long long)blockIdx.x * 256 + threadIdx.x;
+    float lw = -INFINITY, nu = 0.f;
+    bool live = false;
+    if (s < k.n) {
+        lw = b.logw[s];
+        nu = b.nu[s];
+        live = !b.mask[s] && lw != -INFINITY;
+    }
+    b.tc_q[s] = live ? nu : tc::kDeadQ;
+    float lm = live ? lw : -INFINITY, nm = live ? nu : 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+        nm = fmaxf(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+    }
+    if ((threadIdx.x & 31) == 0) { red_l[threadIdx.x >> 5] = lm; red_n[threadIdx.x >> 5] = nm; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) { lm = fmaxf(lm, red_l[w]); nm = fmaxf(nm, red_n[w]); }
+        lm = fmaxf(red_l[0], lm);
+        nm = fmaxf(red_n[0], nm);
+        b.tc_tile_lmax[blockIdx.x] = lm;
+        b.tc_tile_numax[blockIdx.x] = nm;
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(tc::NUM_THREADS, 1)
+    k_ksum_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              Consts<float> k, Bufs<float> b, float T, int nk, int n_src_tiles) {
+    using namespace tc;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    float* qs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(qs + EPI_WARPS * BN);
+    uint64_t* full = bars;
+    uint64_t* empty = bars + STAGES;
+    uint64_t* tfull = bars + 2 * STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* drain = tempty + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    unsigned int* status = &b.stats->status;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long i0 = (long long)blockIdx.x * BM;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+        for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], EPI_WARPS); }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        mbar_fence_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer -------------------------------------------------------
+            int last_phase[STAGES];
+            for (int s = 0; s < STAGES; ++s) last_phase[s] = -1;
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = 0; t < n_src_tiles && ok; ++t) {
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = (int)(it % STAGES);
+                    const uint32_t ph = (it / STAGES) & 1u;
+                    if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, status)) { ok = false; break; }
+                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    uint8_t* dA = smem + s * STAGE_BYTES;
+                    tma_load_2d(&tmA, &full[s], dA, kb * BK, (int)i0);
+                    tma_load_2d(&tmB, &full[s], dA + A_BYTES, kb * BK, t * BN);
+                    last_phase[s] = (int)ph;
+                }
+            }
+            if (!ok)   // let our own copies land before shared memory is released
+                for (int s = 0; s < STAGES; ++s)
+                    if (last_phase[s] >= 0) wait_drain(&full[s], (uint32_t)last_phase[s]);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer -----------------------------------------------------------
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = 0; t < n_src_tiles && ok; ++t) {
+                const int acc = t & 1;
+                const uint32_t aph = (uint32_t)(t >> 1) & 1u;
+                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < nk; ++kb, ++it) {
+                    const int s = (int)(it % STAGES);
+                    const uint32_t ph = (it / STAGES) & 1u;
+                    if (!wait_bounded(&full[s], ph, abort_flag, status)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t b0 = a0 + A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / UK; ++kk)
+                        mma_bf16(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0 + kk * UK * 2),
+                                 (kb | kk) != 0 ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                if (ok) mma_commit(&tfull[acc]);
+            }
+            // all MMAs issued by this thread have completed once drain fires
+            mma_commit(drain);
+            wait_drain(drain, 0);
+        }
+    } else {
+        // ---- epilogue: screening + exact evaluation --------------------------------------
+        const int q = warp & 3;
+        const int row_t = q * 32 + lane;
+        const long long i = i0 + row_t;
+        const bool in_range = i < k.n;
+        const bool live = in_range && !b.mask[i];
+        float nu_i = 0.f, nf_i = 0.f, li = -INFINITY;
+        if (in_range) { nu_i = b.nu[i]; nf_i = b.nf[i]; li = b.logw[i]; }
+        const float Fi = sqrtf(nf_i);
+        float rowc[N], mx[N], sm[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            rowc[j] = -0.5f * k.tau[j] * nf_i;
+            const bool self = live && li != -INFINITY;
+            mx[j] = self ? rowc[j] + li : -INFINITY;   // exact self term (u_i - u_i = 0)
+            sm[j] = self ? 1.f : 0.f;
+        }
+        float* qw = qs + (warp - 2) * BN;
+        unsigned long long ncand = 0;
+        bool ok = true;
+        for (int t = 0; t < n_src_tiles; ++t) {
+            const int acc = t & 1;
+            const uint32_t aph = (uint32_t)(t >> 1) & 1u;
+            __syncwarp();
+            for (int c = lane; c < BN; c += 32) qw[c] = b.tc_q[(size_t)t * BN + c];
+            __syncwarp();
+            const float lmax = b.tc_tile_lmax[t], numax = b.tc_tile_numax[t];
+            float theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
+            if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+            for (int ch = 0; ch < BN / 32; ++ch) {
+                uint32_t v[32];
+                __syncwarp();
+                tmem_ld32(tbase + (uint32_t)(ch * 32), v);
+                tmem_ld_wait();
+                uint32_t cm = 0;
+#pragma unroll
+                for (int c = 0; c < 32; ++c) {
+                    const float dd = fmaf(-2.f, __uint_as_float(v[c]), qw[ch * 32 + c]);
+                    cm |= (dd <= theta ? 1u : 0u) << c;
+                }
+                const long long sb = (long long)t * BN + ch * 32;
+                if (i >= sb && i < sb + 32) cm &= ~(1u << (int)(i - sb));   // self term already counted
+                while (true) {
+                    const uint32_t who = __ballot_sync(0xffffffffu, cm != 0u);
+                    if (who == 0u) break;
+                    const int leader = __ffs(who) - 1;
+                    const int c = __shfl_sync(0xffffffffu, __ffs(cm) - 1, leader);
+                    const long long src = sb + c;
+                    const long long tgt = i0 + q * 32 + leader;
+                    const float* ut = b.u + (size_t)tgt * k.r_pad;
+                    const float* us = b.u + (size_t)src * k.r_pad;
+                    const float* ft = b.f + (size_t)tgt * k.r_pad;
+                    float s1 = 0.f, s2 = 0.f;
+                    for (int d = lane; d < k.r; d += 32) {
+                        const float dl = ut[d] - us[d];
+                        s1 = fmaf(dl, dl, s1);
+                        s2 = fmaf(dl, ft[d], s2);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                    }
+                    if (lane == leader) {
+                        const float ls = b.mask[src] ? -INFINITY : b.logw[src];
+                        if (ls != -INFINITY) {
+#pragma unroll
+                            for (int j = 0; j < N; ++j) {
+                                const float sc = fmaf(-s1, k.inv2tau[j], s2) + (rowc[j] + ls);
+                                if (sc > mx[j]) {
+                                    sm[j] = (mx[j] == -INFINITY) ? 1.f : sm[j] * expf(mx[j] - sc) + 1.f;
+                                    mx[j] = sc;
+                                } else {
+                                    sm[j] += expf(sc - mx[j]);
+                                }
+                            }
+                        }
+                        cm &= cm - 1u;
+                        ++ncand;
+                        theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+        if (ok && in_range)
+            b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li, &b.stats->clamps)
+                                  : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
+        if (lane == 0 && ncand) atomicAdd(&b.stats->candidates, ncand);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) {
+        __syncwarp();
+        tmem_dealloc(tmem, TMEM_COLS);
+    }
+}
+
+size_t tc_scratch_bytes(long long n_pad) {
+    return (size_t)n_pad * sizeof(float) + 2 * (size_t)(n_pad / 256) * sizeof(float) + 1024;
+}
+
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int N>
+cudaError_t launch_n(const CUtensorMap& a, const CUtensorMap& bm, const Consts<float>& k, const Bufs<float>& b,
+                     float T, cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_ksum_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int nk = k.r_pad / tc::BK;
+    const int nst = (int)(k.n_pad / tc::BN);
+    k_ksum_tc<N><<<(unsigned)(k.n_pad / tc::BM), tc::NUM_THREADS, tc::SMEM_BYTES, s>>>(a, bm, k, b, T, nk, nst);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s, int* launches) {
+    if (!b.ubf || k.n_pad % tc::BN != 0 || k.r_pad % tc::BK != 0) return cudaErrorInvalidValue;
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, b.ubf, k.n_pad, k.r_pad, tc::BM) || !make_map(&mb, b.ubf, k.n_pad, k.r_pad, tc::BN))
+        return cudaErrorNotSupported;
+    cudaError_t e = cudaMemsetAsync(&b.stats->candidates, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_tc_colprep<<<(unsigned)(k.n_pad / 256), 256, 0, s>>>(k, b);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const float T = (float)(log((double)k.n) + 20.0);
+    switch (k.N) {
+        case 1: e = launch_n<1>(ma, mb, k, b, T, s); break;
+        case 2: e = launch_n<2>(ma, mb, k, b, T, s); break;
+        case 3: e = launch_n<3>(ma, mb, k, b, T, s); break;
+        case 4: e = launch_n<4>(ma, mb, k, b, T, s); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (launches) *launches += 2;
+    return e;
 }
 
 }  // namespace yy

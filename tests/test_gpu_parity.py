@@ -24,8 +24,15 @@ CASES = {
     "r100_f32": ("cubic", 100, 2048, 0.3, 2, "f32", 4),
     "r1_f64_N4": ("linear", 1, 300, 5.0, 4, "f64", 5),
     "wide_f32": ("cubic", 130, 513, 0.3, 2, "f32", 6),
+    # tcgen05 BF16 screening + exact float32 evaluation
+    "tc_r64_bf16": ("cubic", 64, 1024, 0.3, 2, "bf16", 7),
+    "tc_ragged_bf16": ("cubic", 100, 1000, 0.3, 3, "bf16", 8),
+    "tc_r300_bf16": ("cubic", 300, 2048, 0.3, 2, "bf16", 9),
+    "tc_lowr_bf16": ("cubic", 2, 1024, 4.0, 2, "bf16", 1),
+    "tc_linear_bf16": ("linear", 8, 777, 1.0, 1, "bf16", 3),
+    "tc_N4_bf16": ("cubic", 33, 1500, 0.5, 4, "bf16", 10),
 }
-TOL = {"f64": 1e-10, "f32": 1e-5}
+TOL = {"f64": 1e-10, "f32": 1e-5, "bf16": 1e-5}
 
 
 def _make(case, restart_interval=0, ess_frac=0.0, scrambled=True, restart_init="gauss"):
@@ -80,7 +87,7 @@ def _oracle_state(p, u, steps, seed):
     return st, tr.dy[steps]
 
 
-@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("name", sorted(CASES, key=lambda n: (not n.startswith("tc_r64"), n)))
 def test_step_local_parity(yy_lib, name):
     import torch
     from oracle import filter as F
@@ -211,3 +218,26 @@ def test_call_order_is_checked(yy_lib):
     flt.init_nodes(poly, scr, np.zeros(4))
     with pytest.raises(binding.YYError):
         flt.update(torch.zeros(4, dtype=torch.float64, device="cuda"))   # no predict yet
+
+
+@pytest.mark.parametrize("r,n,N", [(64, 2048, 2), (200, 3000, 3), (1000, 1024, 3)])
+def test_bf16_screen_matches_fp32_path(yy_lib, r, n, N):
+    """Same state through both prediction kernels: the BF16 screen only drops terms below
+    e^-(ln n + 20) of the row maximum, so the two agree to float32 rounding."""
+    import torch
+    from paper_2509_16896_gb300 import binding
+    poly, scr = sobol_inputs(r, 21)
+    tr = simulate("cubic", r, 3, 0.01, seed=21)
+    out = {}
+    for prec in ("f32", "bf16"):
+        cfg = binding.make_config(model="cubic", r=r, n=n, dt=0.01, R=0.3, n_scales=N, precision=prec)
+        flt = binding.Filter(cfg)
+        flt.init_nodes(poly, scr, np.zeros(r))
+        for k in range(2):
+            flt.predict()
+            flt.update(torch.tensor(tr.dy[k], dtype=torch.float64, device="cuda"))
+        flt.predict()
+        out[prec] = flt.get_log_weights()
+    a = out["f32"][0].astype(np.float64) + out["f32"][1]
+    b = out["bf16"][0].astype(np.float64) + out["bf16"][1]
+    assert rel_err(b, a) <= 2e-6
