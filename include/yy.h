@@ -54,6 +54,7 @@ extern "C" {
 #define YY_MAX_DIM 1024
 #define YY_SOBOL_POLY_WORDS 16
 #define YY_SOBOL_SCRAMBLE_WORDS 33
+#define YY_NOALLOC_MAX_DIM 1024
 
 typedef struct yy_filter yy_filter;
 
@@ -185,6 +186,27 @@ YY_EXPORT yy_status yy_get_state(yy_filter* f, double* h_center, double* h_logno
 /* Number of targets whose multi-scale combination was non-positive (set to -inf) in the
  * last yy_predict.  Synchronises. */
 YY_EXPORT yy_status yy_get_clamps(yy_filter* f, int64_t* h_clamps);
+
+/* Weighted moments of node rows without any device allocation.  The paper has no
+ * counterpart: this is a library service for callers that cannot allocate device memory
+ * when they need the result (inside host callbacks or stream work where cudaMalloc is not
+ * allowed, plug-ins whose host owns every device buffer and passes only inputs and
+ * outputs, real-time loops that forbid allocation after start-up).  It computes what
+ * yy_update's normalisation and estimate compute, for caller-supplied rows:
+ *   w_i = exp(logw_i - LSE(logw)),  mean_d = sum_i w_i u_id,
+ *   var_d = sum_i w_i (u_id - mean_d)^2,  ESS = (sum w)^2 / sum w^2.
+ *   d_u     device float [n][ld], rows of r coordinates (ld >= r)
+ *   d_logw  device float [n], log-weights with any common offset (-inf allowed)
+ *   d_out   device double [2r + 3]: mean[r], var[r], ESS, LSE(logw), sum of weights
+ *   stream  cudaStream_t or NULL
+ * Limits: 1 <= r <= YY_NOALLOC_MAX_DIM and n >= 1; anything else returns YY_ERR_ARG
+ * before any launch.  Scratch lives in a fixed device array of about 2 MB inside the
+ * library, held by every GPU that loads it until the process exits.  The first call on a
+ * device looks up that array's device address; make it before any stream capture.  All
+ * calls share the array: calls that overlap on the GPU race and must be serialised by
+ * the caller.  Asynchronous; no device memory is allocated or freed. */
+YY_EXPORT yy_status yy_weighted_moments_static(const float* d_u, int64_t n, int32_t r, int64_t ld,
+                                               const float* d_logw, double* d_out, void* stream);
 
 /* Kernel launches issued by this handle so far (for launch accounting). */
 YY_EXPORT int64_t yy_launch_count(const yy_filter* f);

@@ -32,7 +32,7 @@ SOBOL_SCRAMBLE_WORDS = 33
 EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy_sobol_bits",
            "yy_predict", "yy_update", "yy_estimate", "yy_restart", "yy_get_nodes",
            "yy_get_log_weights", "yy_set_state", "yy_get_state", "yy_get_clamps",
-           "yy_launch_count", "yy_status_str")
+           "yy_launch_count", "yy_status_str", "yy_weighted_moments_static")
 
 
 class YYError(RuntimeError):
@@ -69,6 +69,7 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_get_clamps": (I32, [P, P]),
         "yy_launch_count": (I64, [P]),
         "yy_status_str": (ctypes.c_char_p, [I32]),
+        "yy_weighted_moments_static": (I32, [P, I64, I32, I64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -232,3 +233,20 @@ class Filter:
 
     def launches(self) -> int:
         return int(self.lib.yy_launch_count(self.h))
+
+
+def weighted_moments_static(u_dev, logw_dev, out_dev, stream=None) -> None:
+    """Calls yy_weighted_moments_static, which allocates no device memory: u_dev is a
+    float32 [n][ld] device tensor (row stride ld >= r = u_dev.shape[1] when 2-D), logw_dev
+    float32 [n], out_dev float64 [2r + 3] (mean, var, ESS, LSE, weight sum)."""
+    import torch
+    L = load()
+    n, r = u_dev.shape
+    ld = u_dev.stride(0)
+    assert u_dev.dtype == torch.float32 and u_dev.stride(1) == 1
+    assert logw_dev.dtype == torch.float32 and logw_dev.numel() == n
+    assert out_dev.dtype == torch.float64 and out_dev.numel() >= 2 * r + 3
+    s = stream if stream is not None else torch.cuda.current_stream(u_dev.device)
+    _check("yy_weighted_moments_static", L.yy_weighted_moments_static(
+        ctypes.c_void_p(u_dev.data_ptr()), n, r, ld, ctypes.c_void_p(logw_dev.data_ptr()),
+        ctypes.c_void_p(out_dev.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
