@@ -112,10 +112,10 @@ def _dist():
     return rank, ws, local, dist
 
 
-def _make_filter(w, precision, seed, device):
+def _make_filter(w, precision, seed, device, stream=None):
     from paper_2509_16896_gb300 import binding
     cfg = binding.config_from_workload(w, precision=precision)
-    flt = binding.Filter(cfg, device=device)
+    flt = binding.Filter(cfg, device=device, stream=stream)
     flt.init_nodes(sobol_poly_params(w.r, seed), sobol_scramble_params(w.r, seed), np.zeros(w.r))
     return flt
 
@@ -128,6 +128,11 @@ def _algorithmic_flops(w, precision):
     return 3.0 * w.n * w.n * w.r, "alu"
 
 
+def _rmse(est, truth):
+    K, r = truth.shape
+    return float(np.sqrt(np.sum((est - truth) ** 2) / (K * r)))
+
+
 def run_yy(args):
     import torch
     rank, ws, local, dist = _dist()
@@ -136,20 +141,17 @@ def run_yy(args):
     w = WORKLOADS[args.workload]
     prec = args.precision or w.precision
     seed = w.seed + 1000 * rank
-    steps_total = args.warmup + args.steps
-    tr = simulate(w.model, w.r, max(steps_total, 1), w.dt, seed=seed)
-    flt = _make_filter(w, prec, seed, device)
-    stream = flt.stream
+    W, K = args.warmup, args.steps
+    tr = simulate(w.model, w.r, W + K, w.dt, seed=seed)
+    stream = torch.cuda.Stream(device)
+    flt = _make_filter(w, prec, seed, device, stream)
     dys = torch.tensor(tr.dy, dtype=torch.float64, device=device)
-
-    def step(k):
-        flt.predict()
-        flt.update(dys[k % dys.shape[0]])
-        flt.restart(mode=0)
-
+    hist = torch.zeros((K, 2 * w.r + 4), dtype=torch.float64, device=device)
     with torch.cuda.stream(stream):
-        for k in range(args.warmup):
-            step(k)
+        if W:
+            flt.run_steps(dys[:W])
+        # the K timed steps as one CUDA graph (captured, not executed, here)
+        flt.graph_capture(dys[W:W + K], hist)
     torch.cuda.synchronize()
     # ---- device-resident timed region --------------------------------------------
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -159,8 +161,7 @@ def run_yy(args):
     l0 = flt.launches()
     with ClockSampler(local) as clk:
         e0.record(stream)
-        for k in range(args.steps):
-            step(args.warmup + k)
+        flt.graph_launch()
         e1.record(stream)
         torch.cuda.synchronize()
     if dist is not None:
@@ -172,10 +173,14 @@ def run_yy(args):
         t = torch.tensor([ms], device=device)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
+    h = hist.cpu().numpy()
+    est = h[:, :w.r]
+    rmse = _rmse(est, tr.x[W:W + K])
+    restarts = int(h[:, 2 * w.r + 3].sum())
     mean, var, ess, z = flt.estimate()
     # ---- dominant kernel: prediction launches timed alone on the filter's stream ----
     flops, bound = _algorithmic_flops(w, prec)
-    n_pred = max(3, min(20, args.steps))
+    n_pred = max(3, min(20, K))
     pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     pe0.record(stream)
@@ -184,9 +189,10 @@ def run_yy(args):
     pe1.record(stream)
     torch.cuda.synchronize()
     pred_ms = pe0.elapsed_time(pe1) / n_pred
-    flt.update(dys[0])   # leave the handle in a consistent state
+    with torch.cuda.stream(stream):
+        flt.update(dys[0])   # leave the handle in a consistent state
     # ---- end to end through the C ABI with host buffers ---------------------------
-    n_e2e = max(3, min(args.steps, 50))
+    n_e2e = max(3, min(K, 50))
     dy_host = torch.tensor(tr.dy, dtype=torch.float64).pin_memory()
     dy_dev = torch.empty(w.r, dtype=torch.float64, device=device)
     torch.cuda.synchronize()
@@ -211,24 +217,24 @@ def run_yy(args):
             dist.destroy_process_group()
         return
     peaks, src = _peaks()
-    steps_per_s = args.steps * ws / (t_max / 1e3)
+    steps_per_s = K * ws / (t_max / 1e3)
     if bound == "tensor":
         peak = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
-        unit = "TFLOP/s"
         achieved = flops / (pred_ms / 1e3) / 1e12
+        peak_note = f"{src}: bf16_tflops_sustained (kernel timed inside the step loop)"
     else:
         # float32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        unit = "TFLOP/s"
         achieved = flops / (pred_ms / 1e3) / 1e12
+        peak_note = "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"
     out = {
         "metric": METRIC,
         "value": round(steps_per_s, 4),
         "unit": "filter steps/s",
         "n_gpus": ws,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": round(t_max / args.steps, 4),
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": round(t_max / K, 4),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -236,21 +242,24 @@ def run_yy(args):
         "data": "synthetic (seeded Euler-Maruyama cubic sensor, scrambled Sobol nodes)",
         "config": {"workload": w.name, "r": w.r, "n": w.n, "n_scales": w.n_scales, "dt": w.dt,
                    "R": w.R, "restart_interval": w.restart_interval, "ess_frac": w.ess_frac,
-                   "precision": prec, "trajectories_per_gpu": 1,
+                   "precision": prec, "trajectories_per_gpu": 1, "time_loop": "one CUDA graph of K steps",
                    "l2": f"inputs larger than L2 (u is {w.n * w.r * 4 / 1e6:.0f} MB)"},
         "pair_evals_per_s": round(steps_per_s * w.n_scales * w.n * w.n, 1),
+        "rmse": rmse,
+        "restarts": restarts,
         "clocks": clk.summary(),
         "e2e": {"value": round(e2e_val, 4), "unit": "filter steps/s",
-                "h2d_bytes_per_step": 8 * w.r, "d2h_bytes_per_step": 8 * (2 * w.r + 2 + 6)},
+                "h2d_bytes_per_step": 8 * w.r, "d2h_bytes_per_step": 8 * (2 * w.r + 2) + 56},
         "gpu_launches": int(launches),
-        "roofline": {"bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": unit,
+        "roofline": {"bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4), "traffic": None,
                      "kernel": "prediction (kernel sum)", "kernel_ms": round(pred_ms, 4),
-                     "peak_source": src if bound == "tensor" else "derived: 152 SMs x 128 FP32 lanes x 2 x max clock"},
-        "estimate_check": {"ess": ess, "mean_abs": float(np.mean(np.abs(mean))), "finite": bool(np.all(np.isfinite(mean)))},
+                     "peak_source": peak_note},
     }
     if args.fp32_steps > 0 and prec == "bf16":
-        out["fp32_comparator"] = _time_precision(w, "f32", args.fp32_steps, tr, device)
+        S = min(args.fp32_steps, K)
+        out["fp32_comparator"] = _time_precision(w, "f32", S, W, tr, device)
+        out["fp32_comparator"]["rmse_mixed_same_steps"] = _rmse(est[:S], tr.x[W:W + S])
     if args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     print(json.dumps(out), flush=True)
@@ -259,24 +268,29 @@ def run_yy(args):
         dist.destroy_process_group()
 
 
-def _time_precision(w, prec, steps, tr, device):
-    """Steps/s of another precision of the same path (the plain FP32 form)."""
+def _time_precision(w, prec, steps, warmup, tr, device):
+    """Steps/s and RMSE of another precision of the same path (the plain FP32 form) over
+    the first `steps` timed steps of the same trajectory."""
     import torch
-    flt = _make_filter(w, prec, w.seed, device)
+    stream = torch.cuda.Stream(device)
+    flt = _make_filter(w, prec, w.seed, device, stream)
     dys = torch.tensor(tr.dy, dtype=torch.float64, device=device)
-    with torch.cuda.stream(flt.stream):
-        flt.predict(); flt.update(dys[0]); flt.restart(mode=0)
+    hist = torch.zeros((steps, 2 * w.r + 4), dtype=torch.float64, device=device)
+    with torch.cuda.stream(stream):
+        if warmup:
+            flt.run_steps(dys[:warmup])
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(flt.stream)
-    for k in range(steps):
-        flt.predict(); flt.update(dys[(k + 1) % dys.shape[0]]); flt.restart(mode=0)
-    e1.record(flt.stream)
+    e0.record(stream)
+    with torch.cuda.stream(stream):
+        flt.run_steps(dys[warmup:warmup + steps], hist)
+    e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    m, v, e, z = flt.estimate()
+    est = hist.cpu().numpy()[:, :w.r]
     return {"precision": prec, "steps": steps, "ms_per_step": round(ms, 3),
-            "value": round(1e3 / ms, 4), "unit": "filter steps/s"}
+            "value": round(1e3 / ms, 4), "unit": "filter steps/s",
+            "rmse": _rmse(est, tr.x[warmup:warmup + steps])}
 
 
 def cpu_baseline(w, seconds: float):
@@ -343,7 +357,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default=None, choices=["bf16", "f32", "f64"])
     ap.add_argument("--impl", default="yy", choices=["yy", "reference"])
-    ap.add_argument("--fp32-steps", type=int, default=3, help="steps of the plain FP32 comparator")
+    ap.add_argument("--fp32-steps", type=int, default=10, help="steps of the plain FP32 comparator")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()

@@ -165,6 +165,28 @@ YY_EXPORT yy_status yy_estimate(yy_filter* f, double* h_mean, double* h_var, dou
  * asynchronous) or a host int32 that receives 1 if a restart happened (synchronises). */
 YY_EXPORT yy_status yy_restart(yy_filter* f, int32_t mode, int32_t* h_did_restart);
 
+/* Runs K filter steps back to back on the handle's stream, without host round trips:
+ * for each k, yy_predict, yy_update with d_dy_all + k m, an optional record of the
+ * estimate, and yy_restart(YY_RESTART_AUTO).
+ *   d_dy_all  device double [K][m], observation increments of the K steps
+ *   d_hist    device double [K][2r + 4] or NULL; row k receives x_hat[r], v_hat[r], ESS,
+ *             Lambda_k, Z_k and 1.0 if the restart test fired at step k (else 0.0)
+ * Asynchronous. */
+YY_EXPORT yy_status yy_run_steps(yy_filter* f, const double* d_dy_all, int64_t K, double* d_hist);
+
+/* Captures yy_run_steps(f, d_dy_all, K, d_hist) into a CUDA graph owned by the handle
+ * (replacing any earlier one); nothing is executed.  The handle's stream must be a
+ * created stream (not NULL / the legacy default stream).  The pointers are baked into the
+ * graph: their contents may change between replays, the buffers must stay alive. */
+YY_EXPORT yy_status yy_graph_capture(yy_filter* f, const double* d_dy_all, int64_t K, double* d_hist);
+
+/* Replays the captured K-step graph on the handle's stream (asynchronous).  Returns
+ * YY_ERR_STATE if nothing was captured. */
+YY_EXPORT yy_status yy_graph_launch(yy_filter* f);
+
+/* Number of kernel launches one replay of the captured graph performs (0 if none). */
+YY_EXPORT int64_t yy_graph_kernel_count(const yy_filter* f);
+
 /* Copies node coordinates u (host float [n][r]) and/or the Dirichlet mask (host uint8
  * [n]); either pointer may be NULL.  Synchronises. */
 YY_EXPORT yy_status yy_get_nodes(yy_filter* f, float* h_u, uint8_t* h_mask);

@@ -32,7 +32,8 @@ SOBOL_SCRAMBLE_WORDS = 33
 EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy_sobol_bits",
            "yy_predict", "yy_update", "yy_estimate", "yy_restart", "yy_get_nodes",
            "yy_get_log_weights", "yy_set_state", "yy_get_state", "yy_get_clamps",
-           "yy_launch_count", "yy_status_str", "yy_weighted_moments_static")
+           "yy_launch_count", "yy_status_str", "yy_weighted_moments_static",
+           "yy_run_steps", "yy_graph_capture", "yy_graph_launch", "yy_graph_kernel_count")
 
 
 class YYError(RuntimeError):
@@ -70,6 +71,10 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_launch_count": (I64, [P]),
         "yy_status_str": (ctypes.c_char_p, [I32]),
         "yy_weighted_moments_static": (I32, [P, I64, I32, I64, P, P, P]),
+        "yy_run_steps": (I32, [P, P, I64, P]),
+        "yy_graph_capture": (I32, [P, P, I64, P]),
+        "yy_graph_launch": (I32, [P]),
+        "yy_graph_kernel_count": (I64, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -233,6 +238,25 @@ class Filter:
 
     def launches(self) -> int:
         return int(self.lib.yy_launch_count(self.h))
+
+    def run_steps(self, dy_all_dev, hist_dev=None) -> None:
+        """dy_all_dev: float64 [K][r] device tensor; hist_dev: float64 [K][2r + 4] or None."""
+        K = dy_all_dev.shape[0]
+        _check("yy_run_steps", self.lib.yy_run_steps(
+            self.h, ctypes.c_void_p(dy_all_dev.data_ptr()), K,
+            None if hist_dev is None else ctypes.c_void_p(hist_dev.data_ptr())))
+
+    def graph_capture(self, dy_all_dev, hist_dev=None) -> None:
+        K = dy_all_dev.shape[0]
+        _check("yy_graph_capture", self.lib.yy_graph_capture(
+            self.h, ctypes.c_void_p(dy_all_dev.data_ptr()), K,
+            None if hist_dev is None else ctypes.c_void_p(hist_dev.data_ptr())))
+
+    def graph_launch(self) -> None:
+        _check("yy_graph_launch", self.lib.yy_graph_launch(self.h))
+
+    def graph_kernels(self) -> int:
+        return int(self.lib.yy_graph_kernel_count(self.h))
 
 
 def weighted_moments_static(u_dev, logw_dev, out_dev, stream=None) -> None:

@@ -28,6 +28,9 @@ struct yy_filter {
     double coef[kMaxScales + 1];
     double log_wq;
     double c_ref;
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    long long graph_kernels;
 };
 
 namespace {
@@ -84,6 +87,7 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.params = cv.take<uint32_t>((size_t)c->r * (YY_SOBOL_POLY_WORDS + YY_SOBOL_SCRAMBLE_WORDS) * sizeof(uint32_t));
     b.obs_g = cv.take<T>(r_pad * sizeof(T));
     b.obs_c = cv.take<T>(r_pad * sizeof(T));
+    b.dimc = cv.take<T>(3 * (size_t)r_pad * sizeof(T));
     b.part = cv.take<double>(part_bytes(r_pad));
     b.stats = cv.take<DevStats>(sizeof(DevStats));
     if (c->precision == YY_PREC_BF16) {
@@ -244,13 +248,19 @@ yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t bytes, void*
     multiscale_coefficients(cfg->n_scales, f->coef);
     if (f->fp64) carve<double>(cfg, f->ws, &f->bd);
     else carve<float>(cfg, f->ws, &f->bf);
-    cudaError_t e = cudaMemsetAsync(d_workspace, 0, need, f->stream);
+    cudaError_t e = cudaSuccess;
+    if (cfg->precision == YY_PREC_BF16) e = prepare_ksum_tc();
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_workspace, 0, need, f->stream);
     if (e != cudaSuccess) { delete f; return YY_ERR_CUDA; }
     *out = f;
     return YY_OK;
 }
 
 yy_status yy_destroy(yy_filter* f) {
+    if (f) {
+        if (f->gexec) cudaGraphExecDestroy(f->gexec);
+        if (f->graph) cudaGraphDestroy(f->graph);
+    }
     delete f;
     return YY_OK;
 }
@@ -366,6 +376,60 @@ yy_status yy_restart(yy_filter* f, int32_t mode, int32_t* h_did_restart) {
     return YY_OK;
 }
 
+yy_status yy_run_steps(yy_filter* f, const double* d_dy_all, int64_t K, double* d_hist) {
+    if (!f || !d_dy_all || K < 0) return YY_ERR_ARG;
+    if (!f->nodes_ready || f->predicted) return YY_ERR_STATE;
+    const int r = f->cfg.r;
+    for (int64_t k = 0; k < K; ++k) {
+        yy_status st = yy_predict(f);
+        if (st != YY_OK) return st;
+        if ((st = yy_update(f, d_dy_all + (size_t)k * f->cfg.m)) != YY_OK) return st;
+        if (d_hist) {
+            double* row = d_hist + (size_t)k * (2 * r + 4);
+            cudaError_t e = f->fp64 ? launch_record<double>(f->kd, f->bd, row, f->stream)
+                                    : launch_record<float>(f->kf, f->bf, row, f->stream);
+            if (e != cudaSuccess) return YY_ERR_CUDA;
+            f->launches += 1;
+        }
+        if ((st = yy_restart(f, YY_RESTART_AUTO, nullptr)) != YY_OK) return st;
+    }
+    return YY_OK;
+}
+
+yy_status yy_graph_capture(yy_filter* f, const double* d_dy_all, int64_t K, double* d_hist) {
+    if (!f || !d_dy_all || K < 1) return YY_ERR_ARG;
+    if (!f->stream) return YY_ERR_STATE;
+    if (!f->nodes_ready || f->predicted) return YY_ERR_STATE;
+    if (f->gexec) { cudaGraphExecDestroy(f->gexec); f->gexec = nullptr; }
+    if (f->graph) { cudaGraphDestroy(f->graph); f->graph = nullptr; }
+    const long long l0 = f->launches;
+    cudaError_t e = cudaStreamBeginCapture(f->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    const yy_status st = yy_run_steps(f, d_dy_all, K, d_hist);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(f->stream, &g);
+    f->graph_kernels = f->launches - l0;
+    f->launches = l0;   // capture launches nothing
+    f->predicted = false;
+    if (st != YY_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return YY_ERR_CUDA; }
+    f->graph = g;
+    f->gexec = ex;
+    return YY_OK;
+}
+
+yy_status yy_graph_launch(yy_filter* f) {
+    if (!f) return YY_ERR_ARG;
+    if (!f->gexec) return YY_ERR_STATE;
+    f->launches += f->graph_kernels;
+    return cuda_status(cudaGraphLaunch(f->gexec, f->stream));
+}
+
+int64_t yy_graph_kernel_count(const yy_filter* f) { return (f && f->gexec) ? f->graph_kernels : 0; }
+
 yy_status yy_get_nodes(yy_filter* f, float* h_u, uint8_t* h_mask) {
     if (!f) return YY_ERR_ARG;
     if (!f->nodes_ready) return YY_ERR_STATE;
@@ -409,7 +473,7 @@ yy_status yy_set_state(yy_filter* f, const double* h_center, const void* h_logw,
     k_set_stats<<<1, 1, 0, f->stream>>>(st, lognorm, step);
     e = f->fp64 ? launch_prep<double>(f->kd, f->bd, false, false, 0.0, 1.0, f->stream)
                 : launch_prep<float>(f->kf, f->bf, false, false, 0.0, 1.0, f->stream);
-    f->launches += 2;
+    f->launches += 3;
     f->predicted = false;
     return cuda_status(e);
 }

@@ -75,6 +75,7 @@ struct Bufs {
     double* var;          // [r_pad] v_hat
     T* obs_g;             // [r_pad] dy - dt h(c)
     T* obs_c;             // [r_pad] centre in T
+    T* dimc;              // [3][r_pad] per-dimension constants of the preparation pass
     double* part;         // reduction partials
     DevStats* stats;
     // BF16 path scratch
@@ -99,6 +100,10 @@ cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t 
 cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s,
                            int* launches);
 size_t tc_scratch_bytes(long long n_pad);
+cudaError_t prepare_ksum_tc();
+
+template <typename T>
+cudaError_t launch_record(const Consts<T>& k, const Bufs<T>& b, double* hist_row, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy,

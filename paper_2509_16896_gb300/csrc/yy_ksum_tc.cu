@@ -452,12 +452,6 @@ bool make_map(CUtensorMap* map, const void* base, long long rows, int cols, int 
 template <int N>
 cudaError_t launch_n(const CUtensorMap& a, const CUtensorMap& bm, const Consts<float>& k, const Bufs<float>& b,
                      float T, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_ksum_tc<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
     const int nk = k.r_pad / tc::BK;
     const int nst = (int)(k.n_pad / tc::BN);
     k_ksum_tc<N><<<(unsigned)(k.n_pad / tc::BM), tc::NUM_THREADS, tc::SMEM_BYTES, s>>>(a, bm, k, b, T, nk, nst);
@@ -465,6 +459,16 @@ cudaError_t launch_n(const CUtensorMap& a, const CUtensorMap& bm, const Consts<f
 }
 
 }  // namespace
+
+// Opts the prediction kernels into their shared-memory size on the current device (called
+// when a BF16 handle is created, so that no attribute call happens during stream capture).
+cudaError_t prepare_ksum_tc() {
+    cudaError_t e = cudaFuncSetAttribute(k_ksum_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    return e;
+}
 
 cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s, int* launches) {
     if (!b.ubf || k.n_pad % tc::BN != 0 || k.r_pad % tc::BK != 0) return cudaErrorInvalidValue;

@@ -9,8 +9,9 @@
 //             (Section 5; the density is this library's reading of "re-initialise")
 // Constants that cancel in the normalisation that follows are dropped.
 //
-// One warp per node row; lanes stride over coordinates.  x = c + u is formed in float64,
-// the model is evaluated in the working precision T.
+// One warp per node row; lanes stride over coordinates.  x = c + u is formed as
+// c_hi + (u + c_lo) with the float64 centre split into a head and a tail in the working
+// precision T (k_prep_dims), and the model is evaluated in T.
 #include "yy_internal.cuh"
 
 namespace yy {
@@ -31,10 +32,41 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// Per-dimension constants of one preparation pass: the centre split into a T-precision
+// head and tail (x = c_hi + (u + c_lo) loses only the final rounding), and for a Gaussian
+// restart 1 / (2 max(v_hat_d, (R_d / 4)^2)).
+template <typename T>
+__global__ void k_prep_dims(Consts<T> k, Bufs<T> b, int mode, int init_kind) {
+    if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
+    const double* cen = (mode == kPrepRestart) ? b.mean : b.centre;
+    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
+        T hi = T(0), lo = T(0), iv = T(0);
+        if (d < k.r) {
+            const double c = cen[d];
+            hi = (T)c;
+            lo = (T)(c - (double)hi);
+            if (mode == kPrepRestart && init_kind == YY_RESTART_INIT_GAUSS) {
+                const double R4 = 0.25 * b.halfwidth[d];
+                iv = (T)(0.5 / fmax(b.var[d], R4 * R4));
+            }
+        }
+        b.dimc[d] = hi;
+        b.dimc[k.r_pad + d] = lo;
+        b.dimc[2 * k.r_pad + d] = iv;
+    }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, int first,
-                                              double prior_mean, double prior_var, int init_kind) {
+                                              double prior_mean, double prior_var) {
     if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
+    __shared__ T s_hi[YY_MAX_DIM], s_lo[YY_MAX_DIM], s_iv[YY_MAX_DIM];
+    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
+        s_hi[d] = b.dimc[d];
+        s_lo[d] = b.dimc[k.r_pad + d];
+        s_iv[d] = b.dimc[2 * k.r_pad + d];
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -58,30 +90,28 @@ __global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, 
             T fv = T(0);
             if (d < k.r) {
                 const float uf = ui[d];
-                const double xd = cen[d] + (double)uf;
-                const T x = (T)xd;
+                const T x = s_hi[d] + ((T)uf + s_lo[d]);
                 if (k.model == YY_MODEL_CUBIC) {
-                    T s, c;
-                    sincos_t<T>(x, &s, &c);
-                    fv = c;
-                    div -= s;
+                    T sn, cs;
+                    sincos_t<T>(x, &sn, &cs);
+                    fv = cs;
+                    div -= sn;
                 } else {
                     fv = k.model_a * x;
                     div += k.model_a;
                 }
                 nf += fv * fv;
-                nu += (T)uf * (T)uf;
-                const double R = b.halfwidth[d];
-                if (fabs((double)uf) >= R - 1e-12 * R) on_face = 1;
-                if (mode == kPrepInit) {
-                    const double z = xd - prior_mean;
-                    lw -= (T)(0.5 * z * z / prior_var);
-                } else if (mode == kPrepRestart && init_kind == YY_RESTART_INIT_GAUSS) {
-                    const double R4 = 0.25 * R;
-                    const double v = fmax(b.var[d], R4 * R4);
-                    lw -= (T)(0.5 * (double)uf * (double)uf / v);
+                if (mode == kPrepRestart) lw -= (T)uf * (T)uf * s_iv[d];
+                if (first) {
+                    nu += (T)uf * (T)uf;
+                    const double R = b.halfwidth[d];
+                    if (fabs((double)uf) >= R - 1e-12 * R) on_face = 1;
+                    if (b.ubf) b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(uf);
                 }
-                if (first && b.ubf) b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(uf);
+                if (mode == kPrepInit) {
+                    const double z = cen[d] + (double)uf - prior_mean;
+                    lw -= (T)(0.5 * z * z / prior_var);
+                }
             } else if (first && b.ubf) {
                 b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(0.0f);
             }
@@ -89,9 +119,11 @@ __global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, 
         }
         div = warp_sum(div);
         nf = warp_sum(nf);
-        nu = warp_sum(nu);
         lw = warp_sum(lw);
-        on_face = __any_sync(0xffffffffu, on_face);
+        if (first) {
+            nu = warp_sum(nu);
+            on_face = __any_sync(0xffffffffu, on_face);
+        }
         if (lane == 0) {
             b.divf[i] = div;
             b.nf[i] = nf;
@@ -107,11 +139,11 @@ __global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, 
 template <typename T>
 cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, bool first,
                              double prior_mean, double prior_var, int init_kind, cudaStream_t s) {
+    k_prep_dims<T><<<1, 256, 0, s>>>(k, b, mode, init_kind);
     long long warps = k.n_pad;
     long long blocks = (warps * 32 + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_prep<T><<<(unsigned)blocks, 256, 0, s>>>(k, b, mode, first ? 1 : 0, prior_mean, prior_var,
-                                                init_kind);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_prep<T><<<(unsigned)blocks, 256, 0, s>>>(k, b, mode, first ? 1 : 0, prior_mean, prior_var);
     return cudaGetLastError();
 }
 

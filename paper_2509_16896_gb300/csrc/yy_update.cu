@@ -16,8 +16,8 @@
 //   k_moments      ell_hat = ell' - Lambda_rel, w = e^ell_hat; per block the weight sum,
 //                  sum of squares, weighted mean and centred second moment of u over
 //                  32-row chunks merged with Chan's update          (HBM pass over u)
-//   k_finalize     merge of the block moments (Chan, float64): x_hat = c + mean,
-//                  v_hat, ESS = W^2 / sum w^2, Z += Lambda, restart test (1 block)
+//   k_finalize_*   merge of the block moments (Chan, float64): x_hat = c + mean,
+//                  v_hat, ESS = W^2 / sum w^2, Z += Lambda, restart test
 #include "yy_internal.cuh"
 
 namespace yy {
@@ -44,8 +44,13 @@ __device__ __forceinline__ void lse_merge(double& m, double& s, double m2, doubl
     else { s += s2 * exp(m2 - m); }
 }
 
+// Moment partials (4 + 2 r_pad doubles per block) followed by the Chan merge coefficients
+// (2 doubles per block).
 size_t part_bytes(int r_pad) {
-    return (size_t)kNumPartBlocks * (size_t)(4 + 2 * r_pad) * sizeof(double);
+    return ((size_t)kNumPartBlocks * (size_t)(4 + 2 * r_pad) + 2 * (size_t)kNumPartBlocks + 8) * sizeof(double);
+}
+__device__ __forceinline__ double* coef_area(double* part, int r_pad) {
+    return part + (size_t)kNumPartBlocks * (size_t)(4 + 2 * r_pad);
 }
 
 template <typename T>
@@ -76,26 +81,48 @@ __global__ void k_obs_prep(Consts<T> k, Bufs<T> b, const double* __restrict__ dy
 }
 
 // ell'(i) = ell_pred(i) + sum_d dh_d (g_d - dt/2 dh_d); per-block (max, sum) partials.
+// One warp per row, two coordinates per lane per load (float2), four loads in flight;
+// the per-step vectors g and c sit in shared memory.  Coordinates r..r_pad-1 are zero in
+// u and in g, so they add nothing.
 template <typename T>
 __global__ void __launch_bounds__(256) k_loglik(Consts<T> k, Bufs<T> b) {
     __shared__ double sm[8], ss[8];
+    __shared__ T s_g[YY_MAX_DIM], s_c[YY_MAX_DIM];
+    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) { s_g[d] = b.obs_g[d]; s_c[d] = b.obs_c[d]; }
+    __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
     const T half_dt = T(0.5) * k.dt;
+    const bool cubic = k.model == YY_MODEL_CUBIC;
     double m = -INFINITY, s = 0.0;
     for (long long i = warp; i < k.n; i += nwarps) {
         const T p = b.logw_pred[i];
-        const float* ui = b.u + (size_t)i * k.r_pad;
-        T acc = T(0);
-        for (int d = lane; d < k.r; d += 32) {
-            const T u = (T)ui[d];
-            const T c = b.obs_c[d];
-            const T dh = (k.model == YY_MODEL_CUBIC) ? u * (T(3) * c * c + T(3) * c * u + u * u) : u;
-            acc += dh * (b.obs_g[d] - half_dt * dh);
+        const float2* ui = reinterpret_cast<const float2*>(b.u + (size_t)i * k.r_pad);
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        const int nv = k.r_pad >> 1;   // float2 per row (r_pad is a multiple of 64)
+        for (int v0 = lane; v0 < nv; v0 += 128) {
+            float2 uu[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int v = v0 + 32 * q;
+                uu[q] = (v < nv) ? ui[v] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int d = 2 * (v0 + 32 * q);
+                if (d < k.r_pad) {
+                    const T u0 = (T)uu[q].x, u1 = (T)uu[q].y;
+                    const T c0 = s_c[d], c1 = s_c[d + 1];
+                    const T h0 = cubic ? u0 * (T(3) * c0 * c0 + T(3) * c0 * u0 + u0 * u0) : u0;
+                    const T h1 = cubic ? u1 * (T(3) * c1 * c1 + T(3) * c1 * u1 + u1 * u1) : u1;
+                    acc[q] += h0 * (s_g[d] - half_dt * h0) + h1 * (s_g[d + 1] - half_dt * h1);
+                }
+            }
         }
-        acc = warp_sum_u(acc);
-        const T lw = (p == T(-INFINITY)) ? T(-INFINITY) : p + acc;
+        T tot = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        tot = warp_sum_u(tot);
+        const T lw = (p == T(-INFINITY)) ? T(-INFINITY) : p + tot;
         if (lane == 0) b.logw[i] = lw;
         lse_merge(m, s, (double)lw, 1.0);
     }
@@ -235,55 +262,70 @@ __global__ void __launch_bounds__(256) k_moments(Consts<T> k, Bufs<T> b) {
     }
 }
 
+// Scalars of the step and the coefficients of the sequential Chan merge of the block
+// moments (they depend on the block weights only): alpha_j = W_j / W_(<=j),
+// beta_j = W_(<j) W_j / W_(<=j).  ESS = W^2 / Q, Lambda = c_ref + lambda(c) + Lambda_rel,
+// Z += Lambda, step k += 1, restart test.
 template <typename T>
-__global__ void k_finalize(Consts<T> k, Bufs<T> b, int nb, int restart_interval, double ess_frac) {
-    __shared__ double Wtot_s, Q_s;
+__global__ void k_finalize_scalars(Consts<T> k, Bufs<T> b, int nb, int restart_interval, double ess_frac) {
+    if (threadIdx.x != 0) return;
     DevStats* st = b.stats;
-    if (threadIdx.x == 0) {
-        double W = 0.0, Q = 0.0;
-        for (int j = 0; j < nb; ++j) {
-            const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
-            W += p[0];
-            Q += p[1];
-        }
-        Wtot_s = W;
-        Q_s = Q;
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < k.r; d += blockDim.x) {
-        double W = 0.0, mu = 0.0, M2 = 0.0;
-        for (int j = 0; j < nb; ++j) {
-            const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
-            const double Wc = p[0];
-            if (!(Wc > 0.0)) continue;
-            const double delta = p[4 + d] - mu;
+    double* coef = coef_area(b.part, k.r_pad);
+    double W = 0.0, Q = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
+        const double Wc = p[0];
+        Q += p[1];
+        if (Wc > 0.0) {
             const double Wn = W + Wc;
-            mu += delta * (Wc / Wn);
-            M2 += p[4 + k.r_pad + d] + delta * delta * (W * Wc / Wn);
+            coef[2 * j] = Wc / Wn;
+            coef[2 * j + 1] = W * Wc / Wn;
             W = Wn;
+        } else {
+            coef[2 * j] = 0.0;
+            coef[2 * j + 1] = 0.0;
         }
-        const double mean = b.centre[d] + mu;
-        const double var = (W > 0.0) ? M2 / W : 0.0;
-        b.mean[d] = mean;
-        b.var[d] = var;
-        if (!isfinite(mean) || !isfinite(var)) atomicOr(&st->status, kStatusNonFinite);
     }
+    coef[2 * nb] = W;
+    st->wsum = W;
+    st->wsq = Q;
+    const double ess = (Q > 0.0) ? W * W / Q : 0.0;
+    st->ess = ess;
+    const double lam = k.c_ref + st->lam_c + st->lam_rel;
+    st->lam = lam;
+    st->lognorm += lam;
+    if (!isfinite(lam)) st->status |= kStatusNonFinite;
+    st->step += 1;
+    const bool by_ess = ess_frac > 0.0 && ess < ess_frac * (double)k.n;
+    const bool by_int = restart_interval >= 2 && (st->step % restart_interval) == 0;
+    st->restart_flag = (by_ess || by_int) ? 1 : 0;
+}
+
+// Per coordinate: mean and variance from the block partials with the precomputed merge
+// coefficients (float64 fused multiply-adds only); x_hat = c + mean.
+template <typename T>
+__global__ void __launch_bounds__(128) k_finalize_dims(Consts<T> k, Bufs<T> b, int nb) {
+    __shared__ double s_coef[2 * kNumPartBlocks + 1];
+    const double* coef = coef_area(b.part, k.r_pad);
+    for (int j = threadIdx.x; j <= 2 * nb; j += blockDim.x) s_coef[j] = coef[j];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const double W = Wtot_s, Q = Q_s;
-        st->wsum = W;
-        st->wsq = Q;
-        const double ess = (Q > 0.0) ? W * W / Q : 0.0;
-        st->ess = ess;
-        const double lam = k.c_ref + st->lam_c + st->lam_rel;
-        st->lam = lam;
-        st->lognorm += lam;
-        if (!isfinite(lam)) st->status |= kStatusNonFinite;
-        st->step += 1;
-        const bool by_ess = ess_frac > 0.0 && ess < ess_frac * (double)k.n;
-        const bool by_int = restart_interval >= 2 && (st->step % restart_interval) == 0;
-        st->restart_flag = (by_ess || by_int) ? 1 : 0;
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= k.r) return;
+    double mu = 0.0, M2 = 0.0;
+    for (int j = 0; j < nb; ++j) {
+        const double a = s_coef[2 * j];
+        if (a == 0.0) continue;
+        const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
+        const double delta = p[4 + d] - mu;
+        mu = fma(delta, a, mu);
+        M2 += p[4 + k.r_pad + d] + delta * delta * s_coef[2 * j + 1];
     }
+    const double W = s_coef[2 * nb];
+    const double mean = b.centre[d] + mu;
+    const double var = (W > 0.0) ? M2 / W : 0.0;
+    b.mean[d] = mean;
+    b.var[d] = var;
+    if (!isfinite(mean) || !isfinite(var)) atomicOr(&b.stats->status, kStatusNonFinite);
 }
 
 template <typename T>
@@ -294,8 +336,9 @@ cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy
     k_loglik<T><<<nb, 256, 0, s>>>(k, b);
     k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 0);
     k_moments<T><<<nb, 256, 0, s>>>(k, b);
-    k_finalize<T><<<1, 256, 0, s>>>(k, b, nb, restart_interval, ess_frac);
-    if (launches) *launches += 5;
+    k_finalize_scalars<T><<<1, 32, 0, s>>>(k, b, nb, restart_interval, ess_frac);
+    k_finalize_dims<T><<<(k.r + 127) / 128, 128, 0, s>>>(k, b, nb);
+    if (launches) *launches += 6;
     return cudaGetLastError();
 }
 
@@ -344,11 +387,33 @@ cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int i
     k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 1);
     k_subtract<T><<<nb, 256, 0, s>>>(k, b, 1);
     k_restart_commit<T><<<1, 256, 0, s>>>(k, b);
-    if (launches) *launches += 6;
+    if (launches) *launches += 7;
+    return cudaGetLastError();
+}
+
+// Row of the estimate history: x_hat[r], v_hat[r], ESS, Lambda, Z, restart test result.
+template <typename T>
+__global__ void k_record(Consts<T> k, Bufs<T> b, double* __restrict__ row) {
+    for (int d = threadIdx.x; d < k.r; d += blockDim.x) {
+        row[d] = b.mean[d];
+        row[k.r + d] = b.var[d];
+    }
+    if (threadIdx.x == 0) {
+        row[2 * k.r] = b.stats->ess;
+        row[2 * k.r + 1] = b.stats->lam;
+        row[2 * k.r + 2] = b.stats->lognorm;
+        row[2 * k.r + 3] = b.stats->restart_flag ? 1.0 : 0.0;
+    }
+}
+
+template <typename T>
+cudaError_t launch_record(const Consts<T>& k, const Bufs<T>& b, double* hist_row, cudaStream_t s) {
+    k_record<T><<<1, 256, 0, s>>>(k, b, hist_row);
     return cudaGetLastError();
 }
 
 #define YY_INST(T)                                                                             \
+    template cudaError_t launch_record<T>(const Consts<T>&, const Bufs<T>&, double*, cudaStream_t); \
     template cudaError_t launch_update<T>(const Consts<T>&, const Bufs<T>&, const double*, int, \
                                           double, cudaStream_t, int*);                         \
     template cudaError_t launch_normalise_only<T>(const Consts<T>&, const Bufs<T>&,             \
