@@ -86,36 +86,52 @@ __global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, 
         }
         T div = T(0), nf = T(0), nu = T(0), lw = T(0);
         int on_face = 0;
-        for (int d = lane; d < k.r_pad; d += 32) {
-            T fv = T(0);
-            if (d < k.r) {
-                const float uf = ui[d];
-                const T x = s_hi[d] + ((T)uf + s_lo[d]);
-                if (k.model == YY_MODEL_CUBIC) {
-                    T sn, cs;
-                    sincos_t<T>(x, &sn, &cs);
-                    fv = cs;
-                    div -= sn;
-                } else {
-                    fv = k.model_a * x;
-                    div += k.model_a;
-                }
-                nf += fv * fv;
-                if (mode == kPrepRestart) lw -= (T)uf * (T)uf * s_iv[d];
-                if (first) {
-                    nu += (T)uf * (T)uf;
-                    const double R = b.halfwidth[d];
-                    if (fabs((double)uf) >= R - 1e-12 * R) on_face = 1;
-                    if (b.ubf) b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(uf);
-                }
-                if (mode == kPrepInit) {
-                    const double z = cen[d] + (double)uf - prior_mean;
-                    lw -= (T)(0.5 * z * z / prior_var);
-                }
-            } else if (first && b.ubf) {
-                b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(0.0f);
+        // two coordinates per lane per load, four loads in flight (r_pad is a multiple of 64)
+        const int nv = k.r_pad >> 1;
+        const float2* ui2 = reinterpret_cast<const float2*>(ui);
+        for (int v0 = lane; v0 < nv; v0 += 128) {
+            float2 uu[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int v = v0 + 32 * q;
+                uu[q] = (v < nv) ? ui2[v] : make_float2(0.f, 0.f);
             }
-            fi[d] = fv;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int dq = 2 * (v0 + 32 * q);
+                if (dq >= k.r_pad) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int d = dq + e;
+                    const float uf = e ? uu[q].y : uu[q].x;
+                    T fv = T(0);
+                    if (d < k.r) {
+                        const T x = s_hi[d] + ((T)uf + s_lo[d]);
+                        if (k.model == YY_MODEL_CUBIC) {
+                            T sn, cs;
+                            sincos_t<T>(x, &sn, &cs);
+                            fv = cs;
+                            div -= sn;
+                        } else {
+                            fv = k.model_a * x;
+                            div += k.model_a;
+                        }
+                        nf += fv * fv;
+                        if (mode == kPrepRestart) lw -= (T)uf * (T)uf * s_iv[d];
+                        if (first) {
+                            nu += (T)uf * (T)uf;
+                            const double R = b.halfwidth[d];
+                            if (fabs((double)uf) >= R - 1e-12 * R) on_face = 1;
+                        }
+                        if (mode == kPrepInit) {
+                            const double z = cen[d] + (double)uf - prior_mean;
+                            lw -= (T)(0.5 * z * z / prior_var);
+                        }
+                    }
+                    if (first && b.ubf) b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(d < k.r ? uf : 0.0f);
+                    fi[d] = fv;
+                }
+            }
         }
         div = warp_sum(div);
         nf = warp_sum(nf);

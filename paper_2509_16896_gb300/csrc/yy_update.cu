@@ -44,13 +44,10 @@ __device__ __forceinline__ void lse_merge(double& m, double& s, double m2, doubl
     else { s += s2 * exp(m2 - m); }
 }
 
-// Moment partials (4 + 2 r_pad doubles per block) followed by the Chan merge coefficients
-// (2 doubles per block).
+// Moment partials: 4 + 2 r_pad doubles per block (the log-sum-exp partials reuse the
+// first 2 kNumPartBlocks doubles earlier in the step).
 size_t part_bytes(int r_pad) {
-    return ((size_t)kNumPartBlocks * (size_t)(4 + 2 * r_pad) + 2 * (size_t)kNumPartBlocks + 8) * sizeof(double);
-}
-__device__ __forceinline__ double* coef_area(double* part, int r_pad) {
-    return part + (size_t)kNumPartBlocks * (size_t)(4 + 2 * r_pad);
+    return (size_t)kNumPartBlocks * (size_t)(4 + 2 * r_pad) * sizeof(double);
 }
 
 template <typename T>
@@ -123,8 +120,15 @@ __global__ void __launch_bounds__(256) k_loglik(Consts<T> k, Bufs<T> b) {
         T tot = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         tot = warp_sum_u(tot);
         const T lw = (p == T(-INFINITY)) ? T(-INFINITY) : p + tot;
-        if (lane == 0) b.logw[i] = lw;
-        lse_merge(m, s, (double)lw, 1.0);
+        if (lane == 0) {
+            b.logw[i] = lw;
+            // running (max, sum) of this warp's rows; float exponentials, float64 sums
+            const double l = (double)lw;
+            if (l != -INFINITY) {
+                if (l > m) { s = s * (double)expf((float)(m - l)) + 1.0; m = l; }
+                else s += (double)expf((float)(l - m));
+            }
+        }
     }
     if (lane == 0) { sm[wib] = m; ss[wib] = s; }
     __syncthreads();
@@ -164,20 +168,37 @@ __global__ void __launch_bounds__(256) k_lse_partials(Consts<T> k, Bufs<T> b, in
 
 __global__ void k_lse_merge(const double* __restrict__ part, int nb, DevStats* st, int conditional) {
     if (conditional && st->restart_flag == 0) return;
-    __shared__ double sm[32], ss[32];
-    double m = -INFINITY, s = 0.0;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) lse_merge(m, s, part[2 * i], part[2 * i + 1]);
+    __shared__ double red[32];
+    __shared__ double s_max;
+    // phase 1: the largest block maximum
+    double m = -INFINITY;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) m = fmax(m, part[2 * i]);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const double m2 = __shfl_xor_sync(0xffffffffu, m, o);
-        const double s2 = __shfl_xor_sync(0xffffffffu, s, o);
-        lse_merge(m, s, m2, s2);
-    }
-    if ((threadIdx.x & 31) == 0) { sm[threadIdx.x >> 5] = m; ss[threadIdx.x >> 5] = s; }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double M = -INFINITY, S = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge(M, S, sm[w], ss[w]);
+        double M = -INFINITY;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) M = fmax(M, red[w]);
+        s_max = M;
+    }
+    __syncthreads();
+    const double M = s_max;
+    // phase 2: sum of the block sums rescaled to M
+    double s = 0.0;
+    if (M != -INFINITY)
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            const double mb = part[2 * i];
+            if (mb != -INFINITY) s += part[2 * i + 1] * exp(mb - M);
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double S = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) S += red[w];
         if (M == -INFINITY) {
             st->status |= kStatusDegenerate;
             st->lam_rel = 0.0;
@@ -266,66 +287,91 @@ __global__ void __launch_bounds__(256) k_moments(Consts<T> k, Bufs<T> b) {
 // moments (they depend on the block weights only): alpha_j = W_j / W_(<=j),
 // beta_j = W_(<j) W_j / W_(<=j).  ESS = W^2 / Q, Lambda = c_ref + lambda(c) + Lambda_rel,
 // Z += Lambda, step k += 1, restart test.
+// Scalars of the step: weight sum W and sum of squares Q over the block partials,
+// ESS = W^2 / Q, Lambda = c_ref + lambda(c) + Lambda_rel, Z += Lambda, step k += 1 and the
+// restart test.
 template <typename T>
-__global__ void k_finalize_scalars(Consts<T> k, Bufs<T> b, int nb, int restart_interval, double ess_frac) {
-    if (threadIdx.x != 0) return;
+__global__ void __launch_bounds__(512) k_finalize_scalars(Consts<T> k, Bufs<T> b, int nb, int restart_interval,
+                                                          double ess_frac) {
+    __shared__ double red_w[16], red_q[16];
     DevStats* st = b.stats;
-    double* coef = coef_area(b.part, k.r_pad);
-    double W = 0.0, Q = 0.0;
-    for (int j = 0; j < nb; ++j) {
+    const int t = threadIdx.x;
+    double w = 0.0, q = 0.0;
+    for (int j = t; j < nb; j += blockDim.x) {
         const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
-        const double Wc = p[0];
-        Q += p[1];
-        if (Wc > 0.0) {
-            const double Wn = W + Wc;
-            coef[2 * j] = Wc / Wn;
-            coef[2 * j + 1] = W * Wc / Wn;
-            W = Wn;
-        } else {
-            coef[2 * j] = 0.0;
-            coef[2 * j + 1] = 0.0;
-        }
+        if (p[0] > 0.0) w += p[0];
+        q += p[1];
     }
-    coef[2 * nb] = W;
-    st->wsum = W;
-    st->wsq = Q;
-    const double ess = (Q > 0.0) ? W * W / Q : 0.0;
-    st->ess = ess;
-    const double lam = k.c_ref + st->lam_c + st->lam_rel;
-    st->lam = lam;
-    st->lognorm += lam;
-    if (!isfinite(lam)) st->status |= kStatusNonFinite;
-    st->step += 1;
-    const bool by_ess = ess_frac > 0.0 && ess < ess_frac * (double)k.n;
-    const bool by_int = restart_interval >= 2 && (st->step % restart_interval) == 0;
-    st->restart_flag = (by_ess || by_int) ? 1 : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        w += __shfl_xor_sync(0xffffffffu, w, o);
+        q += __shfl_xor_sync(0xffffffffu, q, o);
+    }
+    if ((t & 31) == 0) { red_w[t >> 5] = w; red_q[t >> 5] = q; }
+    __syncthreads();
+    if (t == 0) {
+        double W = 0.0, Q = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { W += red_w[i]; Q += red_q[i]; }
+        st->wsum = W;
+        st->wsq = Q;
+        const double ess = (Q > 0.0) ? W * W / Q : 0.0;
+        st->ess = ess;
+        const double lam = k.c_ref + st->lam_c + st->lam_rel;
+        st->lam = lam;
+        st->lognorm += lam;
+        if (!isfinite(lam)) st->status |= kStatusNonFinite;
+        st->step += 1;
+        const bool by_ess = ess_frac > 0.0 && ess < ess_frac * (double)k.n;
+        const bool by_int = restart_interval >= 2 && (st->step % restart_interval) == 0;
+        st->restart_flag = (by_ess || by_int) ? 1 : 0;
+    }
 }
 
-// Per coordinate: mean and variance from the block partials with the precomputed merge
-// coefficients (float64 fused multiply-adds only); x_hat = c + mean.
+// Per coordinate: mean and variance merged from the block partials with Chan's rule;
+// x_hat = c + mean.  32 coordinates per block; the 8 warps take 8 contiguous groups of
+// partials and their group results are merged at the end.
 template <typename T>
-__global__ void __launch_bounds__(128) k_finalize_dims(Consts<T> k, Bufs<T> b, int nb) {
-    __shared__ double s_coef[2 * kNumPartBlocks + 1];
-    const double* coef = coef_area(b.part, k.r_pad);
-    for (int j = threadIdx.x; j <= 2 * nb; j += blockDim.x) s_coef[j] = coef[j];
-    __syncthreads();
-    const int d = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= k.r) return;
-    double mu = 0.0, M2 = 0.0;
-    for (int j = 0; j < nb; ++j) {
-        const double a = s_coef[2 * j];
-        if (a == 0.0) continue;
-        const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
-        const double delta = p[4 + d] - mu;
-        mu = fma(delta, a, mu);
-        M2 += p[4 + k.r_pad + d] + delta * delta * s_coef[2 * j + 1];
+__global__ void __launch_bounds__(256) k_finalize_dims(Consts<T> k, Bufs<T> b, int nb) {
+    __shared__ double g_w[8][32], g_mu[8][32], g_m2[8][32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int d = blockIdx.x * 32 + lane;
+    const int per = (nb + 7) / 8;
+    const int j0 = g * per, j1 = min(nb, j0 + per);
+    double W = 0.0, mu = 0.0, M2 = 0.0;
+    if (d < k.r) {
+        for (int j = j0; j < j1; ++j) {
+            const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
+            const double wc = p[0];
+            if (!(wc > 0.0)) continue;
+            const double Wn = W + wc;
+            const double a = wc / Wn, bcoef = W * wc / Wn;
+            const double delta = p[4 + d] - mu;
+            mu = fma(delta, a, mu);
+            M2 += p[4 + k.r_pad + d] + delta * delta * bcoef;
+            W = Wn;
+        }
     }
-    const double W = s_coef[2 * nb];
-    const double mean = b.centre[d] + mu;
-    const double var = (W > 0.0) ? M2 / W : 0.0;
-    b.mean[d] = mean;
-    b.var[d] = var;
-    if (!isfinite(mean) || !isfinite(var)) atomicOr(&b.stats->status, kStatusNonFinite);
+    g_w[g][lane] = W;
+    g_mu[g][lane] = mu;
+    g_m2[g][lane] = M2;
+    __syncthreads();
+    if (g == 0 && d < k.r) {
+        double Wt = 0.0, mt = 0.0, Mt = 0.0;
+        for (int q = 0; q < 8; ++q) {
+            const double wc = g_w[q][lane];
+            if (!(wc > 0.0)) continue;
+            const double Wn = Wt + wc;
+            const double delta = g_mu[q][lane] - mt;
+            mt += delta * (wc / Wn);
+            Mt += g_m2[q][lane] + delta * delta * (Wt * wc / Wn);
+            Wt = Wn;
+        }
+        const double mean = b.centre[d] + mt;
+        const double var = (Wt > 0.0) ? Mt / Wt : 0.0;
+        b.mean[d] = mean;
+        b.var[d] = var;
+        if (!isfinite(mean) || !isfinite(var)) atomicOr(&b.stats->status, kStatusNonFinite);
+    }
 }
 
 template <typename T>
@@ -336,8 +382,8 @@ cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy
     k_loglik<T><<<nb, 256, 0, s>>>(k, b);
     k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 0);
     k_moments<T><<<nb, 256, 0, s>>>(k, b);
-    k_finalize_scalars<T><<<1, 32, 0, s>>>(k, b, nb, restart_interval, ess_frac);
-    k_finalize_dims<T><<<(k.r + 127) / 128, 128, 0, s>>>(k, b, nb);
+    k_finalize_scalars<T><<<1, 512, 0, s>>>(k, b, nb, restart_interval, ess_frac);
+    k_finalize_dims<T><<<(k.r + 31) / 32, 256, 0, s>>>(k, b, nb);
     if (launches) *launches += 6;
     return cudaGetLastError();
 }
