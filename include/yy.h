@@ -187,6 +187,57 @@ YY_EXPORT yy_status yy_graph_launch(yy_filter* f);
 /* Number of kernel launches one replay of the captured graph performs (0 if none). */
 YY_EXPORT int64_t yy_graph_kernel_count(const yy_filter* f);
 
+/* ---- batches of independent filters ------------------------------------------------
+ * B filters with their own r, n, model, box and restart settings (same precision, FP32 or
+ * BF16, and same n_scales) advance together: every pass of a step is one launch for the
+ * whole batch, the BF16 prediction is one persistent tcgen05 launch over a work list of
+ * (filter, 128-target tile) items balanced longest-first across the SMs, and the K-step
+ * loop can be captured as one CUDA graph.  Memory: one caller-owned device workspace of
+ * yy_batch_workspace_bytes(cfgs, B) bytes (256-byte aligned) holds the descriptors and
+ * every filter's workspace. */
+typedef struct yy_batch yy_batch;
+
+YY_EXPORT size_t yy_batch_workspace_bytes(const yy_config* cfgs, int32_t B);
+
+/* Creates the batch and its B filter handles (owned by the batch). */
+YY_EXPORT yy_status yy_batch_create(const yy_config* cfgs, int32_t B, void* d_workspace, size_t bytes,
+                                    void* stream, yy_batch** out);
+YY_EXPORT yy_status yy_batch_destroy(yy_batch* bt);
+
+/* Borrows filter b (0 <= b < B) for yy_init_nodes, yy_estimate, yy_get_* and yy_set_state.
+ * Every filter must have had yy_init_nodes before the first batched step. */
+YY_EXPORT yy_status yy_batch_filter(yy_batch* bt, int32_t b, yy_filter** out);
+
+/* K batched steps (prediction, correction, estimate, automatic restart of every filter).
+ *   d_dy_all  device double [K][M], M = sum_b m_b; filter b's increments at offset
+ *             sum_{b' < b} m_b' of each row
+ *   d_hist    device double [K][H] or NULL, H = sum_b (2 r_b + 4); filter b's record
+ *             (x_hat, v_hat, ESS, Lambda, Z, restart flag) at offset sum_{b' < b} (2 r_b' + 4)
+ * Asynchronous (the first call uploads the descriptors and synchronises once). */
+YY_EXPORT yy_status yy_batch_run_steps(yy_batch* bt, const double* d_dy_all, int64_t K, double* d_hist);
+
+/* One batched prediction (all filters), for timing; leaves every filter "predicted". */
+YY_EXPORT yy_status yy_batch_predict(yy_batch* bt);
+
+/* Captures yy_batch_run_steps(bt, d_dy_all, K, d_hist) as a CUDA graph (needs a created
+ * stream); yy_batch_graph_launch replays it. */
+YY_EXPORT yy_status yy_batch_graph_capture(yy_batch* bt, const double* d_dy_all, int64_t K, double* d_hist);
+YY_EXPORT yy_status yy_batch_graph_launch(yy_batch* bt);
+
+/* Schedule of the batched BF16 prediction: source-tile width bn (128 or 256) and the
+ * number of persistent CTAs (1..1024).  yy_batch_autotune times the candidates bn x
+ * {1, 2, 4} x SM count on the batch itself (reps predictions each), keeps the fastest and,
+ * if cache_path is not NULL, records it there keyed by the batch's shape (and reuses a
+ * recorded choice instead of timing). */
+YY_EXPORT yy_status yy_batch_set_schedule(yy_batch* bt, int32_t bn, int32_t grid);
+YY_EXPORT yy_status yy_batch_get_schedule(const yy_batch* bt, int32_t* h_bn, int32_t* h_grid);
+YY_EXPORT yy_status yy_batch_autotune(yy_batch* bt, const char* cache_path, int32_t reps, int32_t* h_bn,
+                                      int32_t* h_grid);
+
+/* Kernel launches issued so far, and per replay of the captured graph. */
+YY_EXPORT int64_t yy_batch_launch_count(const yy_batch* bt);
+YY_EXPORT int64_t yy_batch_graph_kernel_count(const yy_batch* bt);
+
 /* Copies node coordinates u (host float [n][r]) and/or the Dirichlet mask (host uint8
  * [n]); either pointer may be NULL.  Synchronises. */
 YY_EXPORT yy_status yy_get_nodes(yy_filter* f, float* h_u, uint8_t* h_mask);

@@ -33,7 +33,11 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_predict", "yy_update", "yy_estimate", "yy_restart", "yy_get_nodes",
            "yy_get_log_weights", "yy_set_state", "yy_get_state", "yy_get_clamps",
            "yy_launch_count", "yy_status_str", "yy_weighted_moments_static",
-           "yy_run_steps", "yy_graph_capture", "yy_graph_launch", "yy_graph_kernel_count")
+           "yy_run_steps", "yy_graph_capture", "yy_graph_launch", "yy_graph_kernel_count",
+           "yy_batch_workspace_bytes", "yy_batch_create", "yy_batch_destroy", "yy_batch_filter",
+           "yy_batch_run_steps", "yy_batch_predict", "yy_batch_graph_capture", "yy_batch_graph_launch",
+           "yy_batch_set_schedule", "yy_batch_get_schedule", "yy_batch_autotune",
+           "yy_batch_launch_count", "yy_batch_graph_kernel_count")
 
 
 class YYError(RuntimeError):
@@ -75,6 +79,19 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_graph_capture": (I32, [P, P, I64, P]),
         "yy_graph_launch": (I32, [P]),
         "yy_graph_kernel_count": (I64, [P]),
+        "yy_batch_workspace_bytes": (S, [P, I32]),
+        "yy_batch_create": (I32, [P, I32, P, S, P, P]),
+        "yy_batch_destroy": (I32, [P]),
+        "yy_batch_filter": (I32, [P, I32, P]),
+        "yy_batch_run_steps": (I32, [P, P, I64, P]),
+        "yy_batch_predict": (I32, [P]),
+        "yy_batch_graph_capture": (I32, [P, P, I64, P]),
+        "yy_batch_graph_launch": (I32, [P]),
+        "yy_batch_set_schedule": (I32, [P, I32, I32]),
+        "yy_batch_get_schedule": (I32, [P, P, P]),
+        "yy_batch_autotune": (I32, [P, ctypes.c_char_p, I32, P, P]),
+        "yy_batch_launch_count": (I64, [P]),
+        "yy_batch_graph_kernel_count": (I64, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -257,6 +274,110 @@ class Filter:
 
     def graph_kernels(self) -> int:
         return int(self.lib.yy_graph_kernel_count(self.h))
+
+
+class _BorrowedFilter(Filter):
+    """A filter handle owned by a Batch (no workspace of its own)."""
+
+    def __init__(self, batch, b, cfg):
+        self.torch = batch.torch
+        self.lib = batch.lib
+        self.cfg = cfg
+        self.device = batch.device
+        self.stream = batch.stream
+        h = ctypes.c_void_p()
+        _check("yy_batch_filter", self.lib.yy_batch_filter(batch.h, b, ctypes.byref(h)))
+        self.h = h
+        self.r, self.n = cfg.r, cfg.n
+        self.fp64 = False
+
+    def close(self) -> None:   # owned by the batch
+        self.h = None
+
+
+class Batch:
+    """B independent filters advanced together (include/yy.h, batch section)."""
+
+    def __init__(self, cfgs, device: str = "cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.device = torch.device(device)
+        self.cfgs = list(cfgs)
+        self.B = len(self.cfgs)
+        arr = (YYConfig * self.B)(*self.cfgs)
+        self._arr = arr
+        nbytes = self.lib.yy_batch_workspace_bytes(arr, self.B)
+        if nbytes == 0:
+            raise YYError("yy_batch_workspace_bytes", 1)
+        self.ws = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=self.device)
+        ptr = (self.ws.data_ptr() + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        h = ctypes.c_void_p()
+        _check("yy_batch_create", self.lib.yy_batch_create(arr, self.B, ctypes.c_void_p(ptr), int(nbytes),
+                                                           ctypes.c_void_p(self.stream.cuda_stream),
+                                                           ctypes.byref(h)))
+        self.h = h
+        self.filters = [_BorrowedFilter(self, b, self.cfgs[b]) for b in range(self.B)]
+        self.dy_off = np.cumsum([0] + [c.m for c in self.cfgs])
+        self.hist_off = np.cumsum([0] + [2 * c.r + 4 for c in self.cfgs])
+
+    @property
+    def M(self) -> int:
+        return int(self.dy_off[-1])
+
+    @property
+    def H(self) -> int:
+        return int(self.hist_off[-1])
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.yy_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run_steps(self, dy_all_dev, hist_dev=None) -> None:
+        K = dy_all_dev.shape[0]
+        _check("yy_batch_run_steps", self.lib.yy_batch_run_steps(
+            self.h, ctypes.c_void_p(dy_all_dev.data_ptr()), K,
+            None if hist_dev is None else ctypes.c_void_p(hist_dev.data_ptr())))
+
+    def predict(self) -> None:
+        _check("yy_batch_predict", self.lib.yy_batch_predict(self.h))
+
+    def graph_capture(self, dy_all_dev, hist_dev=None) -> None:
+        K = dy_all_dev.shape[0]
+        _check("yy_batch_graph_capture", self.lib.yy_batch_graph_capture(
+            self.h, ctypes.c_void_p(dy_all_dev.data_ptr()), K,
+            None if hist_dev is None else ctypes.c_void_p(hist_dev.data_ptr())))
+
+    def graph_launch(self) -> None:
+        _check("yy_batch_graph_launch", self.lib.yy_batch_graph_launch(self.h))
+
+    def set_schedule(self, bn: int, grid: int) -> None:
+        _check("yy_batch_set_schedule", self.lib.yy_batch_set_schedule(self.h, bn, grid))
+
+    def schedule(self):
+        bn, grid = ctypes.c_int32(), ctypes.c_int32()
+        _check("yy_batch_get_schedule", self.lib.yy_batch_get_schedule(self.h, ctypes.byref(bn), ctypes.byref(grid)))
+        return bn.value, grid.value
+
+    def autotune(self, cache_path: str | None = None, reps: int = 3):
+        bn, grid = ctypes.c_int32(), ctypes.c_int32()
+        _check("yy_batch_autotune", self.lib.yy_batch_autotune(
+            self.h, None if cache_path is None else cache_path.encode(), reps, ctypes.byref(bn), ctypes.byref(grid)))
+        return bn.value, grid.value
+
+    def launches(self) -> int:
+        return int(self.lib.yy_batch_launch_count(self.h))
+
+    def graph_kernels(self) -> int:
+        return int(self.lib.yy_batch_graph_kernel_count(self.h))
 
 
 def weighted_moments_static(u_dev, logw_dev, out_dev, stream=None) -> None:

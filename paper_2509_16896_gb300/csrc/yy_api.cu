@@ -6,32 +6,9 @@
 
 #include <new>
 
-#include "yy_internal.cuh"
+#include "yy_handle.cuh"
 
 using namespace yy;
-
-struct yy_filter {
-    yy_config cfg;
-    int r_pad;
-    long long n_pad;
-    cudaStream_t stream;
-    char* ws;
-    size_t ws_bytes;
-    bool fp64;
-    Bufs<float> bf;
-    Bufs<double> bd;
-    Consts<float> kf;
-    Consts<double> kd;
-    bool nodes_ready;
-    bool predicted;     // logw_pred holds the last prediction
-    long long launches;
-    double coef[kMaxScales + 1];
-    double log_wq;
-    double c_ref;
-    cudaGraph_t graph;
-    cudaGraphExec_t gexec;
-    long long graph_kernels;
-};
 
 namespace {
 
@@ -92,8 +69,8 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.stats = cv.take<DevStats>(sizeof(DevStats));
     if (c->precision == YY_PREC_BF16) {
         b.tc_q = cv.take<float>((size_t)n_pad * sizeof(float));
-        b.tc_tile_lmax = cv.take<float>((size_t)(n_pad / 256) * sizeof(float));
-        b.tc_tile_numax = cv.take<float>((size_t)(n_pad / 256) * sizeof(float));
+        b.tc_tile_lmax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
+        b.tc_tile_numax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
     }
     if (out) *out = b;
     return cv.off + 256;

@@ -1,0 +1,424 @@
+// Batches of independent filters with ragged n and r: one launch per pass covers every
+// trajectory, the prediction is one persistent tcgen05 launch over a longest-processing-
+// time-first work list, and the K-step loop can be captured as one CUDA graph.  A small
+// autotuner picks the source-tile width and the persistent grid by timing the batch's own
+// prediction.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <functional>
+#include <new>
+#include <queue>
+#include <string>
+#include <vector>
+
+#include "yy_handle.cuh"
+
+using namespace yy;
+
+struct yy_batch {
+    int B;
+    int precision;
+    int N;
+    cudaStream_t stream;
+    char* ws;
+    size_t ws_bytes;
+    std::vector<yy_filter*> filters;
+    std::vector<long long> dy_off, hist_off;
+    long long M, H;                 // row lengths of the increment and history buffers
+    int r_max;
+    long long n_pad_max;
+    int nbu;                        // reduction blocks per trajectory
+    // device descriptors (inside the workspace)
+    Traj<float>* d_traj;
+    void* d_maps;                   // CUtensorMap[2B]
+    int2* d_items;
+    int* d_cta_start;
+    int max_items, max_grid;
+    // schedule
+    int bn, grid, n_items;
+    bool uploaded;
+    long long launches;
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    long long graph_kernels;
+    alignas(64) unsigned char map_any[128];
+};
+
+namespace {
+
+constexpr int kBatchRedBlocks = 16;
+constexpr int kMaxGrid = 1024;
+constexpr size_t kMapBytes = 128;
+
+size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+bool batch_cfg_ok(const yy_config* cfgs, int B) {
+    if (!cfgs || B < 1) return false;
+    for (int b = 0; b < B; ++b) {
+        if (yy_workspace_bytes(&cfgs[b]) == 0) return false;
+        if (cfgs[b].precision != cfgs[0].precision || cfgs[b].n_scales != cfgs[0].n_scales) return false;
+        if (cfgs[b].precision == YY_PREC_FP64) return false;
+    }
+    return true;
+}
+
+long long total_items(const yy_config* cfgs, int B) {
+    long long t = 0;
+    for (int b = 0; b < B; ++b) t += (cfgs[b].n + 255) / 256 * 2;   // 128-row target tiles
+    return t;
+}
+
+size_t header_bytes(const yy_config* cfgs, int B) {
+    size_t s = 0;
+    s += al256(sizeof(Traj<float>) * (size_t)B);
+    s += al256(kMapBytes * 2 * (size_t)B);
+    s += al256(sizeof(int2) * (size_t)total_items(cfgs, B));
+    s += al256(sizeof(int) * (kMaxGrid + 1));
+    return s;
+}
+
+int sm_count() {
+    int dev = 0, n = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+}
+
+// Longest-processing-time-first: items sorted by cost, each given to the least-loaded CTA;
+// returns the concatenated per-CTA lists and their offsets.
+void lpt_schedule(const yy_batch* bt, int grid, int bn, std::vector<int2>& items, std::vector<int>& start) {
+    struct It { double cost; int b, t; };
+    std::vector<It> all;
+    for (int b = 0; b < bt->B; ++b) {
+        const yy_filter* f = bt->filters[b];
+        const long long tiles = f->n_pad / 128;
+        const double src_tiles = (double)(f->n_pad / bn);
+        const double cost = src_tiles * ((double)(f->r_pad / 64) + 1.0);
+        for (long long t = 0; t < tiles; ++t) all.push_back({cost, b, (int)t});
+    }
+    std::stable_sort(all.begin(), all.end(), [](const It& a, const It& c) { return a.cost > c.cost; });
+    using Load = std::pair<double, int>;
+    std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+    for (int c = 0; c < grid; ++c) heap.push({0.0, c});
+    std::vector<std::vector<int2>> per(grid);
+    for (const It& it : all) {
+        Load l = heap.top();
+        heap.pop();
+        per[l.second].push_back(make_int2(it.b, it.t));
+        heap.push({l.first + it.cost, l.second});
+    }
+    items.clear();
+    start.assign(grid + 1, 0);
+    for (int c = 0; c < grid; ++c) {
+        start[c] = (int)items.size();
+        items.insert(items.end(), per[c].begin(), per[c].end());
+    }
+    start[grid] = (int)items.size();
+}
+
+// Builds and uploads the descriptors (trajectory constants and buffers, TMA maps, work
+// lists).  Synchronous; never called during stream capture.
+yy_status upload(yy_batch* bt) {
+    for (int b = 0; b < bt->B; ++b)
+        if (!bt->filters[b]->nodes_ready) return YY_ERR_STATE;
+    std::vector<Traj<float>> tr(bt->B);
+    std::vector<unsigned char> maps(kMapBytes * 2 * (size_t)bt->B, 0);
+    for (int b = 0; b < bt->B; ++b) {
+        yy_filter* f = bt->filters[b];
+        tr[b].k = f->kf;
+        tr[b].b = f->bf;
+        tr[b].dy_off = bt->dy_off[b];
+        tr[b].hist_off = bt->hist_off[b];
+        tr[b].restart_interval = f->cfg.restart_interval;
+        tr[b].ess_frac = f->cfg.ess_frac;
+        tr[b].restart_init = f->cfg.restart_init;
+        if (bt->precision == YY_PREC_BF16) {
+            if (!make_tc_map(&maps[kMapBytes * 2 * b], f->bf.ubf, f->n_pad, f->r_pad, 128) ||
+                !make_tc_map(&maps[kMapBytes * (2 * b + 1)], f->bf.ubf, f->n_pad, f->r_pad, bt->bn))
+                return YY_ERR_UNSUPPORTED;
+            if (b == 0) memcpy(bt->map_any, &maps[0], kMapBytes);
+        }
+    }
+    std::vector<int2> items;
+    std::vector<int> start;
+    lpt_schedule(bt, bt->grid, bt->bn, items, start);
+    if ((int)items.size() > bt->max_items) return YY_ERR_ARG;
+    cudaError_t e = cudaMemcpyAsync(bt->d_traj, tr.data(), sizeof(Traj<float>) * tr.size(), cudaMemcpyHostToDevice,
+                                    bt->stream);
+    if (e == cudaSuccess && bt->precision == YY_PREC_BF16)
+        e = cudaMemcpyAsync(bt->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice, bt->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bt->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, bt->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bt->d_cta_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice,
+                            bt->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(bt->stream);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    bt->n_items = (int)items.size();
+    bt->uploaded = true;
+    return YY_OK;
+}
+
+yy_status batch_predict(yy_batch* bt) {
+    int l = 0;
+    cudaError_t e = launch_reset_batch<float>(bt->d_traj, bt->B, bt->stream, &l);
+    if (e == cudaSuccess) {
+        if (bt->precision == YY_PREC_BF16)
+            e = launch_ksum_tc_batch(bt->d_traj, bt->B, bt->N, bt->n_pad_max, bt->d_maps, bt->d_items,
+                                     bt->d_cta_start, bt->grid, bt->bn, bt->filters[0]->kf, bt->filters[0]->bf,
+                                     bt->map_any, bt->stream, &l);
+        else
+            e = launch_ksum_simt_batch<float>(bt->d_traj, bt->B, bt->N, bt->n_pad_max, bt->r_max, bt->stream, &l);
+    }
+    bt->launches += l;
+    return e == cudaSuccess ? YY_OK : YY_ERR_CUDA;
+}
+
+yy_status batch_steps(yy_batch* bt, const double* d_dy_all, int64_t K, double* d_hist) {
+    for (int64_t k = 0; k < K; ++k) {
+        yy_status st = batch_predict(bt);
+        if (st != YY_OK) return st;
+        int l = 0;
+        cudaError_t e = launch_update_batch<float>(bt->d_traj, bt->B, bt->r_max, d_dy_all + (size_t)k * bt->M,
+                                                   bt->nbu, bt->stream, &l);
+        if (e == cudaSuccess && d_hist)
+            e = launch_record_batch<float>(bt->d_traj, bt->B, d_hist + (size_t)k * bt->H, bt->stream, &l);
+        if (e == cudaSuccess)
+            e = launch_restart_batch<float>(bt->d_traj, bt->B, bt->r_max, bt->n_pad_max, bt->nbu, bt->stream, &l);
+        bt->launches += l;
+        if (e != cudaSuccess) return YY_ERR_CUDA;
+    }
+    return YY_OK;
+}
+
+uint64_t batch_signature(const yy_batch* bt) {
+    uint64_t h = 1469598103934665603ull;
+    auto mix = [&](uint64_t v) { h ^= v; h *= 1099511628211ull; };
+    mix((uint64_t)bt->B);
+    mix((uint64_t)bt->N);
+    mix((uint64_t)bt->precision);
+    for (const yy_filter* f : bt->filters) { mix((uint64_t)f->cfg.n); mix((uint64_t)f->cfg.r); }
+    return h;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t yy_batch_workspace_bytes(const yy_config* cfgs, int32_t B) {
+    if (!batch_cfg_ok(cfgs, B)) return 0;
+    size_t s = header_bytes(cfgs, B);
+    for (int b = 0; b < B; ++b) s += al256(yy_workspace_bytes(&cfgs[b]));
+    return s + 256;
+}
+
+yy_status yy_batch_create(const yy_config* cfgs, int32_t B, void* d_workspace, size_t bytes, void* stream,
+                          yy_batch** out) {
+    if (!out) return YY_ERR_ARG;
+    *out = nullptr;
+    if (!batch_cfg_ok(cfgs, B)) return YY_ERR_ARG;
+    const size_t need = yy_batch_workspace_bytes(cfgs, B);
+    if (!d_workspace || ((uintptr_t)d_workspace & 255u) || bytes < need) return YY_ERR_WORKSPACE;
+    yy_batch* bt = new (std::nothrow) yy_batch();
+    if (!bt) return YY_ERR_ARG;
+    bt->B = B;
+    bt->precision = cfgs[0].precision;
+    bt->N = cfgs[0].n_scales;
+    bt->stream = (cudaStream_t)stream;
+    bt->ws = (char*)d_workspace;
+    bt->ws_bytes = bytes;
+    bt->nbu = kBatchRedBlocks;
+    bt->bn = 256;
+    bt->grid = sm_count();
+    bt->max_grid = kMaxGrid;
+    bt->max_items = (int)total_items(cfgs, B);
+    char* p = bt->ws;
+    bt->d_traj = reinterpret_cast<Traj<float>*>(p);
+    p += al256(sizeof(Traj<float>) * (size_t)B);
+    bt->d_maps = p;
+    p += al256(kMapBytes * 2 * (size_t)B);
+    bt->d_items = reinterpret_cast<int2*>(p);
+    p += al256(sizeof(int2) * (size_t)bt->max_items);
+    bt->d_cta_start = reinterpret_cast<int*>(p);
+    p += al256(sizeof(int) * (kMaxGrid + 1));
+    long long M = 0, H = 0;
+    bt->r_max = 0;
+    bt->n_pad_max = 0;
+    for (int b = 0; b < B; ++b) {
+        const size_t wb = yy_workspace_bytes(&cfgs[b]);
+        yy_filter* f = nullptr;
+        const yy_status st = yy_create(&cfgs[b], p, wb, stream, &f);
+        if (st != YY_OK) {
+            for (yy_filter* g : bt->filters) yy_destroy(g);
+            delete bt;
+            return st;
+        }
+        bt->filters.push_back(f);
+        p += al256(wb);
+        bt->dy_off.push_back(M);
+        bt->hist_off.push_back(H);
+        M += cfgs[b].m;
+        H += 2 * cfgs[b].r + 4;
+        bt->r_max = std::max(bt->r_max, cfgs[b].r);
+        bt->n_pad_max = std::max(bt->n_pad_max, f->n_pad);
+    }
+    bt->M = M;
+    bt->H = H;
+    *out = bt;
+    return YY_OK;
+}
+
+yy_status yy_batch_destroy(yy_batch* bt) {
+    if (!bt) return YY_OK;
+    if (bt->gexec) cudaGraphExecDestroy(bt->gexec);
+    if (bt->graph) cudaGraphDestroy(bt->graph);
+    for (yy_filter* f : bt->filters) yy_destroy(f);
+    delete bt;
+    return YY_OK;
+}
+
+yy_status yy_batch_filter(yy_batch* bt, int32_t b, yy_filter** out) {
+    if (!bt || !out || b < 0 || b >= bt->B) return YY_ERR_ARG;
+    *out = bt->filters[b];
+    bt->uploaded = false;   // the caller may re-initialise this filter
+    return YY_OK;
+}
+
+yy_status yy_batch_set_schedule(yy_batch* bt, int32_t bn, int32_t grid) {
+    if (!bt || (bn != 128 && bn != 256) || grid < 1 || grid > kMaxGrid) return YY_ERR_ARG;
+    bt->bn = bn;
+    bt->grid = grid;
+    bt->uploaded = false;
+    return YY_OK;
+}
+
+yy_status yy_batch_get_schedule(const yy_batch* bt, int32_t* h_bn, int32_t* h_grid) {
+    if (!bt) return YY_ERR_ARG;
+    if (h_bn) *h_bn = bt->bn;
+    if (h_grid) *h_grid = bt->grid;
+    return YY_OK;
+}
+
+yy_status yy_batch_predict(yy_batch* bt) {
+    if (!bt) return YY_ERR_ARG;
+    if (!bt->uploaded) {
+        const yy_status st = upload(bt);
+        if (st != YY_OK) return st;
+    }
+    return batch_predict(bt);
+}
+
+yy_status yy_batch_run_steps(yy_batch* bt, const double* d_dy_all, int64_t K, double* d_hist) {
+    if (!bt || !d_dy_all || K < 0) return YY_ERR_ARG;
+    if (!bt->uploaded) {
+        const yy_status st = upload(bt);
+        if (st != YY_OK) return st;
+    }
+    return batch_steps(bt, d_dy_all, K, d_hist);
+}
+
+yy_status yy_batch_graph_capture(yy_batch* bt, const double* d_dy_all, int64_t K, double* d_hist) {
+    if (!bt || !d_dy_all || K < 1) return YY_ERR_ARG;
+    if (!bt->stream) return YY_ERR_STATE;
+    if (!bt->uploaded) {
+        const yy_status st = upload(bt);
+        if (st != YY_OK) return st;
+    }
+    if (bt->gexec) { cudaGraphExecDestroy(bt->gexec); bt->gexec = nullptr; }
+    if (bt->graph) { cudaGraphDestroy(bt->graph); bt->graph = nullptr; }
+    const long long l0 = bt->launches;
+    cudaError_t e = cudaStreamBeginCapture(bt->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    const yy_status st = batch_steps(bt, d_dy_all, K, d_hist);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(bt->stream, &g);
+    bt->graph_kernels = bt->launches - l0;
+    bt->launches = l0;
+    if (st != YY_OK) { if (g) cudaGraphDestroy(g); return st; }
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    if (e != cudaSuccess) { cudaGraphDestroy(g); return YY_ERR_CUDA; }
+    bt->graph = g;
+    bt->gexec = ex;
+    return YY_OK;
+}
+
+yy_status yy_batch_graph_launch(yy_batch* bt) {
+    if (!bt) return YY_ERR_ARG;
+    if (!bt->gexec) return YY_ERR_STATE;
+    bt->launches += bt->graph_kernels;
+    return cudaGraphLaunch(bt->gexec, bt->stream) == cudaSuccess ? YY_OK : YY_ERR_CUDA;
+}
+
+int64_t yy_batch_launch_count(const yy_batch* bt) { return bt ? bt->launches : 0; }
+int64_t yy_batch_graph_kernel_count(const yy_batch* bt) { return (bt && bt->gexec) ? bt->graph_kernels : 0; }
+
+yy_status yy_batch_autotune(yy_batch* bt, const char* cache_path, int32_t reps, int32_t* h_bn, int32_t* h_grid) {
+    if (!bt || reps < 1) return YY_ERR_ARG;
+    if (bt->precision != YY_PREC_BF16) {   // only the tensor-core path has a schedule to tune
+        if (h_bn) *h_bn = bt->bn;
+        if (h_grid) *h_grid = bt->grid;
+        return YY_OK;
+    }
+    const uint64_t sig = batch_signature(bt);
+    if (cache_path) {
+        if (FILE* fh = fopen(cache_path, "r")) {
+            unsigned long long s;
+            int bn, grid;
+            bool hit = false;
+            while (fscanf(fh, "%llx %d %d", &s, &bn, &grid) == 3)
+                if (s == sig) { hit = true; bt->bn = bn; bt->grid = grid; }
+            fclose(fh);
+            if (hit) {
+                bt->uploaded = false;
+                if (h_bn) *h_bn = bt->bn;
+                if (h_grid) *h_grid = bt->grid;
+                return YY_OK;
+            }
+        }
+    }
+    const int sms = sm_count();
+    const int cand_bn[2] = {256, 128};
+    const int cand_mul[3] = {1, 2, 4};
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return YY_ERR_CUDA;
+    float best = INFINITY;
+    int best_bn = bt->bn, best_grid = bt->grid;
+    for (int bn : cand_bn)
+        for (int mul : cand_mul) {
+            const int grid = std::min(kMaxGrid, sms * mul);
+            bt->bn = bn;
+            bt->grid = grid;
+            bt->uploaded = false;
+            yy_status st = upload(bt);
+            if (st != YY_OK) continue;
+            if ((st = batch_predict(bt)) != YY_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+            cudaEventRecord(e0, bt->stream);
+            for (int r = 0; r < reps; ++r) batch_predict(bt);
+            cudaEventRecord(e1, bt->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return YY_ERR_CUDA; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_bn = bn; best_grid = grid; }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bt->bn = best_bn;
+    bt->grid = best_grid;
+    bt->uploaded = false;
+    if (cache_path) {
+        if (FILE* fh = fopen(cache_path, "a")) {
+            fprintf(fh, "%llx %d %d\n", (unsigned long long)sig, best_bn, best_grid);
+            fclose(fh);
+        }
+    }
+    if (h_bn) *h_bn = best_bn;
+    if (h_grid) *h_grid = best_grid;
+    return YY_OK;
+}
+
+}  // extern "C"

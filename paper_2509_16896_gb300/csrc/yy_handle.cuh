@@ -1,0 +1,27 @@
+// Host-side handle of one filter (shared by the single-filter and batch entry points).
+#pragma once
+
+#include "yy_internal.cuh"
+
+struct yy_filter {
+    yy_config cfg;
+    int r_pad;
+    long long n_pad;
+    cudaStream_t stream;
+    char* ws;
+    size_t ws_bytes;
+    bool fp64;
+    yy::Bufs<float> bf;
+    yy::Bufs<double> bd;
+    yy::Consts<float> kf;
+    yy::Consts<double> kd;
+    bool nodes_ready;
+    bool predicted;     // logw_pred holds the last prediction
+    long long launches;
+    double coef[yy::kMaxScales + 1];
+    double log_wq;
+    double c_ref;
+    cudaGraph_t graph;
+    cudaGraphExec_t gexec;
+    long long graph_kernels;
+};

@@ -80,8 +80,20 @@ struct Bufs {
     DevStats* stats;
     // BF16 path scratch
     float* tc_q;          // [n_pad] |u_s|^2 of live sources, 3e38 for dead ones
-    float* tc_tile_lmax;  // [n_pad / 256] max live log-weight per source tile
-    float* tc_tile_numax; // [n_pad / 256] max |u_s|^2 per source tile
+    float* tc_tile_lmax;  // [n_pad / 128] max live log-weight per chunk of 128 sources
+    float* tc_tile_numax; // [n_pad / 128] max |u_s|^2 per chunk of 128 sources
+};
+
+// Device-side descriptor of one trajectory of a batch (kernels index it by blockIdx.y).
+template <typename T>
+struct Traj {
+    Consts<T> k;
+    Bufs<T> b;
+    long long dy_off;      // offset of this trajectory's increments within a step row
+    long long hist_off;    // offset of its record within a history row
+    int restart_interval;
+    double ess_frac;
+    int restart_init;
 };
 
 // Launch helpers (defined in the .cu files).
@@ -118,5 +130,26 @@ cudaError_t launch_normalise_only(const Consts<T>& k, const Bufs<T>& b, cudaStre
                                   int* launches);
 
 size_t part_bytes(int r_pad);
+
+// Batched launches: one launch covers every trajectory (grid.y = trajectory).
+template <typename T>
+cudaError_t launch_update_batch(const Traj<T>* d_traj, int B, int r_max, const double* dy_row,
+                                int nbu, cudaStream_t s, int* launches);
+template <typename T>
+cudaError_t launch_restart_batch(const Traj<T>* d_traj, int B, int r_max, long long n_pad_max,
+                                 int nbu, cudaStream_t s, int* launches);
+template <typename T>
+cudaError_t launch_record_batch(const Traj<T>* d_traj, int B, double* hist_row, cudaStream_t s, int* launches);
+template <typename T>
+cudaError_t launch_reset_batch(const Traj<T>* d_traj, int B, cudaStream_t s, int* launches);
+bool make_tc_map(void* map /* CUtensorMap */, const void* base, long long rows, int cols, int box_rows);
+cudaError_t launch_ksum_tc_batch(const Traj<float>* d_traj, int B, int N, long long n_pad_max,
+                                 const void* d_maps /* CUtensorMap[2B] */, const int2* d_items,
+                                 const int* d_cta_start, int grid, int bn, const Consts<float>& k_any,
+                                 const Bufs<float>& b_any, const void* map_any, cudaStream_t s, int* launches);
+
+template <typename T>
+cudaError_t launch_ksum_simt_batch(const Traj<T>* d_traj, int B, int N, long long n_pad_max, int r_max,
+                                   cudaStream_t s, int* launches);
 
 }  // namespace yy

@@ -31,7 +31,7 @@ template <> __device__ __forceinline__ double exp_fast<double>(double x) { retur
 }  // namespace
 
 template <typename T, int N>
-__global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int rk) {
+__device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>& b, int rk, int bid) {
     __shared__ T At[BK][BM];   // u of targets
     __shared__ T Ft[BK][BM];   // f of targets
     __shared__ T Bt[BK][BN];   // u of sources
@@ -39,7 +39,7 @@ __global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int r
 
     const int tid = threadIdx.x;
     const int tx = tid & 15, ty = tid >> 4;
-    const long long i0 = (long long)blockIdx.x * BM;
+    const long long i0 = (long long)bid * BM;
 
     T rowc[TM][N];          // -(tau_j / 2) |f_i|^2
     T mx[TM][N], sm[TM][N];
@@ -150,6 +150,38 @@ __global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int r
         b.logw_pred[i] = combine_scales<T, N>(k, mx[a], sm[a], b.divf[i], b.logw[i], &b.stats->clamps);
     }
 }
+
+template <typename T, int N>
+__global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int rk) {
+    ksum_simt_body<T, N>(k, b, rk, blockIdx.x);
+}
+
+// batched: trajectory = blockIdx.y; blocks past a trajectory's rows return at once
+template <typename T, int N>
+__global__ void __launch_bounds__(256) kb_ksum_simt(const Traj<T>* __restrict__ tr) {
+    const Traj<T>& t = tr[blockIdx.y];
+    if ((long long)blockIdx.x * BM >= t.k.n_pad) return;
+    const int rk = ((t.k.r + BK - 1) / BK) * BK;
+    ksum_simt_body<T, N>(t.k, t.b, rk, blockIdx.x);
+}
+
+template <typename T>
+cudaError_t launch_ksum_simt_batch(const Traj<T>* d_traj, int B, int N, long long n_pad_max, int r_max,
+                                   cudaStream_t s, int* launches) {
+    (void)r_max;
+    const dim3 grid((unsigned)(n_pad_max / BM), B);
+    switch (N) {
+        case 1: kb_ksum_simt<T, 1><<<grid, 256, 0, s>>>(d_traj); break;
+        case 2: kb_ksum_simt<T, 2><<<grid, 256, 0, s>>>(d_traj); break;
+        case 3: kb_ksum_simt<T, 3><<<grid, 256, 0, s>>>(d_traj); break;
+        case 4: kb_ksum_simt<T, 4><<<grid, 256, 0, s>>>(d_traj); break;
+        default: return cudaErrorInvalidValue;
+    }
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+template cudaError_t launch_ksum_simt_batch<float>(const Traj<float>*, int, int, long long, int, cudaStream_t, int*);
+template cudaError_t launch_ksum_simt_batch<double>(const Traj<double>*, int, int, long long, int, cudaStream_t, int*);
 
 template <typename T>
 cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s) {

@@ -24,7 +24,11 @@
 //     node coordinates (difference form, warp-cooperative over the coordinates) and fed
 //     to the online log-sum-exp of their target row.
 //
-// CTA = one tile of 128 targets over all sources (source tiles of 256).  Warp roles:
+// Work item = one tile of 128 targets of one filter over all of that filter's sources
+// (source tiles of BN = 256 or 128).  A single filter launches one CTA per item; a batch
+// of ragged filters launches a persistent grid in which every CTA walks its own list of
+// (filter, target tile) items, prepared on the host by a longest-processing-time-first
+// assignment, with the TMA descriptors of every filter in global memory.  Warp roles:
 // warp 0 issues TMA loads, warp 1 allocates TMEM and issues tcgen05.mma (one thread),
 // warps 2-5 read the accumulators with tcgen05.ld (each warp its TMEM lane quarter, one
 // target row per thread) and screen.  Every wait is bounded (%globaltimer); on expiry the
@@ -38,26 +42,32 @@
 namespace yy {
 
 namespace tc {
-constexpr int BM = 128;      // targets per CTA (UMMA M)
-constexpr int BN = 256;      // sources per tile (UMMA N)
+constexpr int BM = 128;      // targets per item (UMMA M)
 constexpr int BK = 64;       // coordinates per stage: 64 bf16 = one 128-byte swizzle row
 constexpr int UK = 16;       // K of one tcgen05.mma kind::f16
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int NUM_THREADS = 192;
 constexpr int EPI_WARPS = 4;
-constexpr uint32_t TMEM_COLS = 512;   // two accumulators of BN fp32 columns
-constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_WARPS * BN * 4 + 256;
-// kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1),
-// B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+constexpr int A_BYTES = BM * BK * 2;
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
 constexpr float kEpsGram = 0.015625f;   // 2^-6
 constexpr float kDeadQ = 3.0e38f;
 constexpr float kThetaMax = 1.0e30f;
+
+// Shape-dependent constants.  BN = 256: 4 stages, 512 TMEM columns, one CTA per SM.
+// BN = 128: 3 stages (96 KB), 256 TMEM columns, so two CTAs fit on one SM.
+template <int BN>
+struct Cfg {
+    static constexpr int STAGES = (BN == 256) ? 4 : 3;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators of BN fp32 columns
+    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_WARPS * BN * 4 + 256;
+    // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1),
+    // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                                      ((uint32_t)(BM >> 4) << 24);
+};
+
 }  // namespace tc
 
 namespace {
@@ -146,12 +156,13 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     d |= (uint64_t)2 << 61;
     return d;
 }
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
         "setp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(tc::IDESC), "r"(accumulate)
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -192,11 +203,11 @@ __device__ __forceinline__ float screen_theta(const Consts<float>& k, bool live,
 
 }  // namespace
 
-// Per source tile: |u_s|^2 of live sources (kDeadQ for masked, padded or -inf ones), the
-// largest live log-weight and the largest live |u_s|^2.
-__global__ void __launch_bounds__(256) k_tc_colprep(Consts<float> k, Bufs<float> b) {
-    __shared__ float red_l[8], red_n[8];
-    const long long s = (long long)blockIdx.x * 256 + threadIdx.x;
+// Per source chunk of 128: |u_s|^2 of live sources (kDeadQ for masked, padded or -inf
+// ones), the largest live log-weight and the largest live |u_s|^2.
+__device__ __forceinline__ void colprep_body(const Consts<float>& k, const Bufs<float>& b, int chunk) {
+    __shared__ float red_l[4], red_n[4];
+    const long long s = (long long)chunk * 128 + threadIdx.x;
     float lw = -INFINITY, nu = 0.f;
     bool live = false;
     if (s < k.n) {
@@ -214,19 +225,39 @@ __global__ void __launch_bounds__(256) k_tc_colprep(Consts<float> k, Bufs<float>
     if ((threadIdx.x & 31) == 0) { red_l[threadIdx.x >> 5] = lm; red_n[threadIdx.x >> 5] = nm; }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < 8; ++w) { lm = fmaxf(lm, red_l[w]); nm = fmaxf(nm, red_n[w]); }
-        lm = fmaxf(red_l[0], lm);
-        nm = fmaxf(red_n[0], nm);
-        b.tc_tile_lmax[blockIdx.x] = lm;
-        b.tc_tile_numax[blockIdx.x] = nm;
+        for (int w = 1; w < 4; ++w) { lm = fmaxf(lm, red_l[w]); nm = fmaxf(nm, red_n[w]); }
+        b.tc_tile_lmax[chunk] = lm;
+        b.tc_tile_numax[chunk] = nm;
     }
 }
 
-template <int N>
+__global__ void __launch_bounds__(128) k_tc_colprep(Consts<float> k, Bufs<float> b) { colprep_body(k, b, blockIdx.x); }
+
+__global__ void __launch_bounds__(128) kb_tc_colprep(const Traj<float>* __restrict__ tr) {
+    const Traj<float>& t = tr[blockIdx.y];
+    if ((long long)blockIdx.x * 128 >= t.k.n_pad) return;
+    colprep_body(t.k, t.b, blockIdx.x);
+}
+
+// Work list of a launch.  items == nullptr: one item per CTA, target tile blockIdx.x of
+// the filter passed by value.  Otherwise CTA c processes items[cta_start[c] ..
+// cta_start[c + 1]), each (filter index, target tile), with descriptors tr[filter] and
+// TMA maps maps[2 filter] (A, 128-row box) and maps[2 filter + 1] (B, BN-row box).
+struct TcWork {
+    const Traj<float>* tr;
+    const CUtensorMap* maps;
+    const int2* items;
+    const int* cta_start;
+};
+
+template <int N, int BN>
 __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     k_ksum_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              Consts<float> k, Bufs<float> b, float T, int nk, int n_src_tiles) {
+              const __grid_constant__ Consts<float> k0, const __grid_constant__ Bufs<float> b0, TcWork w) {
     using namespace tc;
+    using C = Cfg<BN>;
+    constexpr int STAGES = C::STAGES;
+    constexpr int STAGE_BYTES = C::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     float* qs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
@@ -238,10 +269,14 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     uint64_t* drain = tempty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    unsigned int* status = &b.stats->status;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long i0 = (long long)blockIdx.x * BM;
+    const bool batched = (w.items != nullptr);
+    const int it_begin = batched ? w.cta_start[blockIdx.x] : 0;
+    const int it_end = batched ? w.cta_start[blockIdx.x + 1] : 1;
+    // status word for timeouts: the first filter of this CTA (or the single filter)
+    unsigned int* status = batched ? (it_end > it_begin ? &w.tr[w.items[it_begin].x].b.stats->status : nullptr)
+                                   : &b0.stats->status;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -251,7 +286,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         mbar_fence_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, TMEM_COLS);
+        tmem_alloc(tmem_slot, C::TMEM_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -259,23 +294,44 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    // per-item view: descriptors, maps, first target row, K stages, source tiles
+    auto item_kb = [&](int idx, const Consts<float>*& kp, const Bufs<float>*& bp, const CUtensorMap*& ma,
+                       const CUtensorMap*& mb, long long& i0) {
+        if (!batched) {
+            kp = &k0; bp = &b0; ma = &tmA; mb = &tmB;
+            i0 = (long long)blockIdx.x * BM;
+        } else {
+            const int2 it = w.items[idx];
+            kp = &w.tr[it.x].k; bp = &w.tr[it.x].b;
+            ma = &w.maps[2 * it.x]; mb = &w.maps[2 * it.x + 1];
+            i0 = (long long)it.y * BM;
+        }
+    };
+
     if (warp == 0) {
-        if (lane == 0) {
+        if (lane == 0 && status) {
             // ---- TMA producer -------------------------------------------------------
             int last_phase[STAGES];
             for (int s = 0; s < STAGES; ++s) last_phase[s] = -1;
             uint32_t it = 0;
             bool ok = true;
-            for (int t = 0; t < n_src_tiles && ok; ++t) {
-                for (int kb = 0; kb < nk; ++kb, ++it) {
-                    const int s = (int)(it % STAGES);
-                    const uint32_t ph = (it / STAGES) & 1u;
-                    if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, status)) { ok = false; break; }
-                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                    uint8_t* dA = smem + s * STAGE_BYTES;
-                    tma_load_2d(&tmA, &full[s], dA, kb * BK, (int)i0);
-                    tma_load_2d(&tmB, &full[s], dA + A_BYTES, kb * BK, t * BN);
-                    last_phase[s] = (int)ph;
+            for (int idx = it_begin; idx < it_end && ok; ++idx) {
+                const Consts<float>* kp; const Bufs<float>* bp; const CUtensorMap* ma; const CUtensorMap* mb;
+                long long i0;
+                item_kb(idx, kp, bp, ma, mb, i0);
+                const int nk = kp->r_pad / BK;
+                const int nst = (int)(kp->n_pad / BN);
+                for (int t = 0; t < nst && ok; ++t) {
+                    for (int kb = 0; kb < nk; ++kb, ++it) {
+                        const int s = (int)(it % STAGES);
+                        const uint32_t ph = (it / STAGES) & 1u;
+                        if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, status)) { ok = false; break; }
+                        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                        uint8_t* dA = smem + s * STAGE_BYTES;
+                        tma_load_2d(ma, &full[s], dA, kb * BK, (int)i0);
+                        tma_load_2d(mb, &full[s], dA + A_BYTES, kb * BK, t * BN);
+                        last_phase[s] = (int)ph;
+                    }
                 }
             }
             if (!ok)   // let our own copies land before shared memory is released
@@ -283,143 +339,163 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     if (last_phase[s] >= 0) wait_drain(&full[s], (uint32_t)last_phase[s]);
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && status) {
             // ---- MMA issuer -----------------------------------------------------------
-            uint32_t it = 0;
+            uint32_t it = 0, tcount = 0;
             bool ok = true;
-            for (int t = 0; t < n_src_tiles && ok; ++t) {
-                const int acc = t & 1;
-                const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
-                for (int kb = 0; kb < nk; ++kb, ++it) {
-                    const int s = (int)(it % STAGES);
-                    const uint32_t ph = (it / STAGES) & 1u;
-                    if (!wait_bounded(&full[s], ph, abort_flag, status)) { ok = false; break; }
+            for (int idx = it_begin; idx < it_end && ok; ++idx) {
+                const Consts<float>* kp; const Bufs<float>* bp; const CUtensorMap* ma; const CUtensorMap* mb;
+                long long i0;
+                item_kb(idx, kp, bp, ma, mb, i0);
+                const int nk = kp->r_pad / BK;
+                const int nst = (int)(kp->n_pad / BN);
+                for (int t = 0; t < nst && ok; ++t, ++tcount) {
+                    const int acc = (int)(tcount & 1u);
+                    const uint32_t aph = (tcount >> 1) & 1u;
+                    if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-                    const uint32_t b0 = a0 + A_BYTES;
+                    const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
+                    for (int kb = 0; kb < nk; ++kb, ++it) {
+                        const int s = (int)(it % STAGES);
+                        const uint32_t ph = (it / STAGES) & 1u;
+                        if (!wait_bounded(&full[s], ph, abort_flag, status)) { ok = false; break; }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+                        const uint32_t b0a = a0 + A_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BK / UK; ++kk)
-                        mma_bf16(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0 + kk * UK * 2),
-                                 (kb | kk) != 0 ? 1u : 0u);
-                    mma_commit(&empty[s]);
+                        for (int kk = 0; kk < BK / UK; ++kk)
+                            mma_bf16(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0a + kk * UK * 2), C::IDESC,
+                                     (kb | kk) != 0 ? 1u : 0u);
+                        mma_commit(&empty[s]);
+                    }
+                    if (ok) mma_commit(&tfull[acc]);
                 }
-                if (ok) mma_commit(&tfull[acc]);
             }
             // all MMAs issued by this thread have completed once drain fires
             mma_commit(drain);
             wait_drain(drain, 0);
         }
-    } else {
+    } else if (status) {
         // ---- epilogue: screening + exact evaluation --------------------------------------
         const int q = warp & 3;
-        const int row_t = q * 32 + lane;
-        const long long i = i0 + row_t;
-        const bool in_range = i < k.n;
-        const bool live = in_range && !b.mask[i];
-        float nu_i = 0.f, nf_i = 0.f, li = -INFINITY;
-        if (in_range) { nu_i = b.nu[i]; nf_i = b.nf[i]; li = b.logw[i]; }
-        const float Fi = sqrtf(nf_i);
-        float rowc[N], mx[N], sm[N];
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            rowc[j] = -0.5f * k.tau[j] * nf_i;
-            const bool self = live && li != -INFINITY;
-            mx[j] = self ? rowc[j] + li : -INFINITY;   // exact self term (u_i - u_i = 0)
-            sm[j] = self ? 1.f : 0.f;
-        }
         float* qw = qs + (warp - 2) * BN;
-        unsigned long long ncand = 0;
+        uint32_t tcount = 0;
         bool ok = true;
-        for (int t = 0; t < n_src_tiles; ++t) {
-            const int acc = t & 1;
-            const uint32_t aph = (uint32_t)(t >> 1) & 1u;
-            __syncwarp();
-            for (int c = lane; c < BN; c += 32) qw[c] = b.tc_q[(size_t)t * BN + c];
-            __syncwarp();
-            const float lmax = b.tc_tile_lmax[t], numax = b.tc_tile_numax[t];
-            float theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
-            if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) { ok = false; break; }
-            tc_fence_after();
-            const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
-            for (int ch = 0; ch < BN / 32; ++ch) {
-                uint32_t v[32];
+        for (int idx = it_begin; idx < it_end && ok; ++idx) {
+            const Consts<float>* kp; const Bufs<float>* bp; const CUtensorMap* ma; const CUtensorMap* mb;
+            long long i0;
+            item_kb(idx, kp, bp, ma, mb, i0);
+            const Consts<float>& k = *kp;
+            const Bufs<float>& b = *bp;
+            const int nst = (int)(k.n_pad / BN);
+            const float T = logf((float)k.n) + 20.0f;
+            const long long i = i0 + q * 32 + lane;
+            const bool in_range = i < k.n;
+            const bool live = in_range && !b.mask[i];
+            float nu_i = 0.f, nf_i = 0.f, li = -INFINITY;
+            if (in_range) { nu_i = b.nu[i]; nf_i = b.nf[i]; li = b.logw[i]; }
+            const float Fi = sqrtf(nf_i);
+            float rowc[N], mx[N], sm[N];
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                rowc[j] = -0.5f * k.tau[j] * nf_i;
+                const bool self = live && li != -INFINITY;
+                mx[j] = self ? rowc[j] + li : -INFINITY;   // exact self term (u_i - u_i = 0)
+                sm[j] = self ? 1.f : 0.f;
+            }
+            unsigned long long ncand = 0;
+            for (int t = 0; t < nst; ++t, ++tcount) {
+                const int acc = (int)(tcount & 1u);
+                const uint32_t aph = (tcount >> 1) & 1u;
                 __syncwarp();
-                tmem_ld32(tbase + (uint32_t)(ch * 32), v);
-                tmem_ld_wait();
-                uint32_t cm = 0;
-#pragma unroll
-                for (int c = 0; c < 32; ++c) {
-                    const float dd = fmaf(-2.f, __uint_as_float(v[c]), qw[ch * 32 + c]);
-                    cm |= (dd <= theta ? 1u : 0u) << c;
+                for (int c = lane; c < BN; c += 32) qw[c] = b.tc_q[(size_t)t * BN + c];
+                __syncwarp();
+                float lmax = b.tc_tile_lmax[t * (BN / 128)], numax = b.tc_tile_numax[t * (BN / 128)];
+                if (BN == 256) {
+                    lmax = fmaxf(lmax, b.tc_tile_lmax[2 * t + 1]);
+                    numax = fmaxf(numax, b.tc_tile_numax[2 * t + 1]);
                 }
-                const long long sb = (long long)t * BN + ch * 32;
-                if (i >= sb && i < sb + 32) cm &= ~(1u << (int)(i - sb));   // self term already counted
-                while (true) {
-                    const uint32_t who = __ballot_sync(0xffffffffu, cm != 0u);
-                    if (who == 0u) break;
-                    const int leader = __ffs(who) - 1;
-                    const int c = __shfl_sync(0xffffffffu, __ffs(cm) - 1, leader);
-                    const long long src = sb + c;
-                    const long long tgt = i0 + q * 32 + leader;
-                    const float* ut = b.u + (size_t)tgt * k.r_pad;
-                    const float* us = b.u + (size_t)src * k.r_pad;
-                    const float* ft = b.f + (size_t)tgt * k.r_pad;
-                    float s1 = 0.f, s2 = 0.f;
-                    for (int d = lane; d < k.r; d += 32) {
-                        const float dl = ut[d] - us[d];
-                        s1 = fmaf(dl, dl, s1);
-                        s2 = fmaf(dl, ft[d], s2);
-                    }
+                float theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
+                if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+                for (int ch = 0; ch < BN / 32; ++ch) {
+                    uint32_t v[32];
+                    __syncwarp();
+                    tmem_ld32(tbase + (uint32_t)(ch * 32), v);
+                    tmem_ld_wait();
+                    uint32_t cm = 0;
 #pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                    for (int c = 0; c < 32; ++c) {
+                        const float dd = fmaf(-2.f, __uint_as_float(v[c]), qw[ch * 32 + c]);
+                        cm |= (dd <= theta ? 1u : 0u) << c;
                     }
-                    if (lane == leader) {
-                        const float ls = b.mask[src] ? -INFINITY : b.logw[src];
-                        if (ls != -INFINITY) {
+                    const long long sb = (long long)t * BN + ch * 32;
+                    if (i >= sb && i < sb + 32) cm &= ~(1u << (int)(i - sb));   // self term already counted
+                    while (true) {
+                        const uint32_t who = __ballot_sync(0xffffffffu, cm != 0u);
+                        if (who == 0u) break;
+                        const int leader = __ffs(who) - 1;
+                        const int c = __shfl_sync(0xffffffffu, __ffs(cm) - 1, leader);
+                        const long long src = sb + c;
+                        const long long tgt = i0 + q * 32 + leader;
+                        const float* ut = b.u + (size_t)tgt * k.r_pad;
+                        const float* us = b.u + (size_t)src * k.r_pad;
+                        const float* ft = b.f + (size_t)tgt * k.r_pad;
+                        float s1 = 0.f, s2 = 0.f;
+                        for (int d = lane; d < k.r; d += 32) {
+                            const float dl = ut[d] - us[d];
+                            s1 = fmaf(dl, dl, s1);
+                            s2 = fmaf(dl, ft[d], s2);
+                        }
 #pragma unroll
-                            for (int j = 0; j < N; ++j) {
-                                const float sc = fmaf(-s1, k.inv2tau[j], s2) + (rowc[j] + ls);
-                                if (sc > mx[j]) {
-                                    sm[j] = (mx[j] == -INFINITY) ? 1.f : sm[j] * expf(mx[j] - sc) + 1.f;
-                                    mx[j] = sc;
-                                } else {
-                                    sm[j] += expf(sc - mx[j]);
+                        for (int o = 16; o > 0; o >>= 1) {
+                            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                        }
+                        if (lane == leader) {
+                            const float ls = b.mask[src] ? -INFINITY : b.logw[src];
+                            if (ls != -INFINITY) {
+#pragma unroll
+                                for (int j = 0; j < N; ++j) {
+                                    const float sc = fmaf(-s1, k.inv2tau[j], s2) + (rowc[j] + ls);
+                                    if (sc > mx[j]) {
+                                        sm[j] = (mx[j] == -INFINITY) ? 1.f : sm[j] * expf(mx[j] - sc) + 1.f;
+                                        mx[j] = sc;
+                                    } else {
+                                        sm[j] += expf(sc - mx[j]);
+                                    }
                                 }
                             }
+                            cm &= cm - 1u;
+                            ++ncand;
+                            theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
                         }
-                        cm &= cm - 1u;
-                        ++ncand;
-                        theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[acc]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[acc]);
-        }
-        if (ok && in_range)
-            b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li, &b.stats->clamps)
-                                  : -INFINITY;
+            if (ok && in_range)
+                b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li, &b.stats->clamps)
+                                      : -INFINITY;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
-        if (lane == 0 && ncand) atomicAdd(&b.stats->candidates, ncand);
+            for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
+            if (lane == 0 && ncand) atomicAdd(&b.stats->candidates, ncand);
+        }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     if (warp == 1) {
         __syncwarp();
-        tmem_dealloc(tmem, TMEM_COLS);
+        tmem_dealloc(tmem, C::TMEM_COLS);
     }
 }
 
 size_t tc_scratch_bytes(long long n_pad) {
-    return (size_t)n_pad * sizeof(float) + 2 * (size_t)(n_pad / 256) * sizeof(float) + 1024;
+    return (size_t)n_pad * sizeof(float) + 2 * (size_t)(n_pad / 128) * sizeof(float) + 1024;
 }
 
 namespace {
@@ -437,7 +513,38 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-bool make_map(CUtensorMap* map, const void* base, long long rows, int cols, int box_rows) {
+template <int N, int BN>
+void* kernel_ptr() { return reinterpret_cast<void*>(k_ksum_tc<N, BN>); }
+
+template <int BN>
+cudaError_t set_attr_all() {
+    cudaError_t e = cudaSuccess;
+    const int sm = tc::Cfg<BN>::SMEM_BYTES;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<1, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<2, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<3, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<4, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
+}
+
+template <int BN>
+cudaError_t launch_bn(int N, unsigned grid, const CUtensorMap& a, const CUtensorMap& bm, const Consts<float>& k,
+                      const Bufs<float>& b, const TcWork& w, cudaStream_t s) {
+    const int sm = tc::Cfg<BN>::SMEM_BYTES;
+    switch (N) {
+        case 1: k_ksum_tc<1, BN><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
+        case 2: k_ksum_tc<2, BN><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
+        case 3: k_ksum_tc<3, BN><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
+        case 4: k_ksum_tc<4, BN><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool make_tc_map(void* map_out, const void* base, long long rows, int cols, int box_rows) {
+    CUtensorMap* map = static_cast<CUtensorMap*>(map_out);
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
@@ -449,44 +556,43 @@ bool make_map(CUtensorMap* map, const void* base, long long rows, int cols, int 
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int N>
-cudaError_t launch_n(const CUtensorMap& a, const CUtensorMap& bm, const Consts<float>& k, const Bufs<float>& b,
-                     float T, cudaStream_t s) {
-    const int nk = k.r_pad / tc::BK;
-    const int nst = (int)(k.n_pad / tc::BN);
-    k_ksum_tc<N><<<(unsigned)(k.n_pad / tc::BM), tc::NUM_THREADS, tc::SMEM_BYTES, s>>>(a, bm, k, b, T, nk, nst);
-    return cudaGetLastError();
-}
-
-}  // namespace
-
 // Opts the prediction kernels into their shared-memory size on the current device (called
-// when a BF16 handle is created, so that no attribute call happens during stream capture).
+// when a BF16 handle or batch is created, so that no attribute call happens during
+// stream capture).
 cudaError_t prepare_ksum_tc() {
-    cudaError_t e = cudaFuncSetAttribute(k_ksum_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
+    cudaError_t e = set_attr_all<256>();
+    if (e == cudaSuccess) e = set_attr_all<128>();
     return e;
 }
 
 cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s, int* launches) {
-    if (!b.ubf || k.n_pad % tc::BN != 0 || k.r_pad % tc::BK != 0) return cudaErrorInvalidValue;
+    if (!b.ubf || k.n_pad % 256 != 0 || k.r_pad % tc::BK != 0) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, b.ubf, k.n_pad, k.r_pad, tc::BM) || !make_map(&mb, b.ubf, k.n_pad, k.r_pad, tc::BN))
+    if (!make_tc_map(&ma, b.ubf, k.n_pad, k.r_pad, tc::BM) || !make_tc_map(&mb, b.ubf, k.n_pad, k.r_pad, 256))
         return cudaErrorNotSupported;
     cudaError_t e = cudaMemsetAsync(&b.stats->candidates, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    k_tc_colprep<<<(unsigned)(k.n_pad / 256), 256, 0, s>>>(k, b);
+    k_tc_colprep<<<(unsigned)(k.n_pad / 128), 128, 0, s>>>(k, b);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const float T = (float)(log((double)k.n) + 20.0);
-    switch (k.N) {
-        case 1: e = launch_n<1>(ma, mb, k, b, T, s); break;
-        case 2: e = launch_n<2>(ma, mb, k, b, T, s); break;
-        case 3: e = launch_n<3>(ma, mb, k, b, T, s); break;
-        case 4: e = launch_n<4>(ma, mb, k, b, T, s); break;
-        default: return cudaErrorInvalidValue;
-    }
+    const TcWork w{nullptr, nullptr, nullptr, nullptr};
+    e = launch_bn<256>(k.N, (unsigned)(k.n_pad / tc::BM), ma, mb, k, b, w, s);
+    if (launches) *launches += 2;
+    return e;
+}
+
+// Batched prediction: column preparation for every filter, then one persistent launch
+// over the precomputed item lists.  bn selects the source-tile width (256 or 128).
+cudaError_t launch_ksum_tc_batch(const Traj<float>* d_traj, int B, int N, long long n_pad_max,
+                                 const void* d_maps, const int2* d_items, const int* d_cta_start,
+                                 int grid, int bn, const Consts<float>& k_any, const Bufs<float>& b_any,
+                                 const void* map_any_v, cudaStream_t s, int* launches) {
+    kb_tc_colprep<<<dim3((unsigned)(n_pad_max / 128), B), 128, 0, s>>>(d_traj);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const CUtensorMap& map_any = *static_cast<const CUtensorMap*>(map_any_v);
+    const TcWork w{d_traj, static_cast<const CUtensorMap*>(d_maps), d_items, d_cta_start};
+    e = (bn == 128) ? launch_bn<128>(N, (unsigned)grid, map_any, map_any, k_any, b_any, w, s)
+                    : launch_bn<256>(N, (unsigned)grid, map_any, map_any, k_any, b_any, w, s);
     if (launches) *launches += 2;
     return e;
 }

@@ -36,7 +36,7 @@ __device__ __forceinline__ T warp_sum(T v) {
 // head and tail (x = c_hi + (u + c_lo) loses only the final rounding), and for a Gaussian
 // restart 1 / (2 max(v_hat_d, (R_d / 4)^2)).
 template <typename T>
-__global__ void k_prep_dims(Consts<T> k, Bufs<T> b, int mode, int init_kind) {
+__device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind) {
     if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
     const double* cen = (mode == kPrepRestart) ? b.mean : b.centre;
     for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
@@ -57,8 +57,8 @@ __global__ void k_prep_dims(Consts<T> k, Bufs<T> b, int mode, int init_kind) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, int first,
-                                              double prior_mean, double prior_var) {
+__device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, int mode, int first,
+                                          double prior_mean, double prior_var, int bid, int nblk) {
     if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
     __shared__ T s_hi[YY_MAX_DIM], s_lo[YY_MAX_DIM], s_iv[YY_MAX_DIM];
     for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
@@ -68,8 +68,8 @@ __global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, 
     }
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long warp = (bid * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)nblk * blockDim.x) >> 5;
     const double* cen = (mode == kPrepRestart) ? b.mean : b.centre;
     for (long long i = warp; i < k.n_pad; i += nwarps) {
         const float* ui = b.u + (size_t)i * k.r_pad;
@@ -151,6 +151,36 @@ __global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, 
         }
     }
 }
+
+template <typename T>
+__global__ void k_prep_dims(Consts<T> k, Bufs<T> b, int mode, int init_kind) { prep_dims_body<T>(k, b, mode, init_kind); }
+template <typename T>
+__global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, int first, double prior_mean,
+                                              double prior_var) {
+    prep_body<T>(k, b, mode, first, prior_mean, prior_var, blockIdx.x, gridDim.x);
+}
+// batched restart preparation: trajectory = blockIdx.y
+template <typename T>
+__global__ void kb_prep_dims(const Traj<T>* __restrict__ tr) {
+    const Traj<T>& t = tr[blockIdx.y];
+    prep_dims_body<T>(t.k, t.b, kPrepRestart, t.restart_init);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) kb_prep(const Traj<T>* __restrict__ tr) {
+    const Traj<T>& t = tr[blockIdx.y];
+    prep_body<T>(t.k, t.b, kPrepRestart, 0, 0.0, 1.0, blockIdx.x, gridDim.x);
+}
+
+template <typename T>
+cudaError_t launch_prep_restart_batch(const Traj<T>* d_traj, int B, long long n_pad_max, cudaStream_t s) {
+    kb_prep_dims<T><<<dim3(1, B), 256, 0, s>>>(d_traj);
+    long long blocks = (n_pad_max * 32 + 255) / 256;
+    if (blocks > 64) blocks = 64;
+    kb_prep<T><<<dim3((unsigned)blocks, B), 256, 0, s>>>(d_traj);
+    return cudaGetLastError();
+}
+template cudaError_t launch_prep_restart_batch<float>(const Traj<float>*, int, long long, cudaStream_t);
+template cudaError_t launch_prep_restart_batch<double>(const Traj<double>*, int, long long, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, bool first,

@@ -10,14 +10,19 @@
 // normaliser Lambda_k = c_ref + lambda(c) + LSE(relative) is accumulated in float64.
 //
 // Passes (all coalesced, one warp per node row or one thread per coordinate):
-//   k_obs_prep     g, centre in T, lambda(c)                       (1 block)
-//   k_loglik       ell' = ell_pred + sum_d ..., per-block (max, sum) (HBM pass over u)
-//   k_lse_merge    Lambda_rel                                       (1 block, float64)
-//   k_moments      ell_hat = ell' - Lambda_rel, w = e^ell_hat; per block the weight sum,
-//                  sum of squares, weighted mean and centred second moment of u over
-//                  32-row chunks merged with Chan's update          (HBM pass over u)
-//   k_finalize_*   merge of the block moments (Chan, float64): x_hat = c + mean,
-//                  v_hat, ESS = W^2 / sum w^2, Z += Lambda, restart test
+//   obs_prep        g, centre in T, lambda(c)                             (1 block)
+//   loglik          ell' = ell_pred + sum_d ..., per-block (max, sum)     (HBM pass over u)
+//   lse_merge       Lambda_rel                                            (1 block, float64)
+//   moments         ell_hat = ell' - Lambda_rel, w = e^ell_hat; per block the weight sum,
+//                   sum of squares, weighted mean and centred second moment of u over
+//                   32-row chunks merged with Chan's update                (HBM pass over u)
+//   finalize_*      merge of the block moments (Chan, float64): x_hat = c + mean,
+//                   v_hat, ESS = W^2 / sum w^2, Z += Lambda, restart test
+//
+// Every pass is a __device__ body taking the block index and block count explicitly;
+// a single-filter __global__ wrapper runs it over blockIdx.x, and a batched wrapper
+// (prefix kb_) runs it for trajectory blockIdx.y of a Traj array, so that one launch
+// covers a whole batch of ragged filters.
 #include "yy_internal.cuh"
 
 namespace yy {
@@ -50,8 +55,12 @@ size_t part_bytes(int r_pad) {
     return (size_t)kNumPartBlocks * (size_t)(4 + 2 * r_pad) * sizeof(double);
 }
 
+// ---------------------------------------------------------------------------------------
+// bodies
+// ---------------------------------------------------------------------------------------
+
 template <typename T>
-__global__ void k_obs_prep(Consts<T> k, Bufs<T> b, const double* __restrict__ dy) {
+__device__ __forceinline__ void obs_prep_body(const Consts<T>& k, const Bufs<T>& b, const double* __restrict__ dy) {
     __shared__ double red[32];
     double acc = 0.0;
     for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
@@ -82,14 +91,14 @@ __global__ void k_obs_prep(Consts<T> k, Bufs<T> b, const double* __restrict__ dy
 // the per-step vectors g and c sit in shared memory.  Coordinates r..r_pad-1 are zero in
 // u and in g, so they add nothing.
 template <typename T>
-__global__ void __launch_bounds__(256) k_loglik(Consts<T> k, Bufs<T> b) {
+__device__ __forceinline__ void loglik_body(const Consts<T>& k, const Bufs<T>& b, int bid, int nblk) {
     __shared__ double sm[8], ss[8];
     __shared__ T s_g[YY_MAX_DIM], s_c[YY_MAX_DIM];
     for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) { s_g[d] = b.obs_g[d]; s_c[d] = b.obs_c[d]; }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const long long warp = (bid * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)nblk * blockDim.x) >> 5;
     const T half_dt = T(0.5) * k.dt;
     const bool cubic = k.model == YY_MODEL_CUBIC;
     double m = -INFINITY, s = 0.0;
@@ -135,20 +144,20 @@ __global__ void __launch_bounds__(256) k_loglik(Consts<T> k, Bufs<T> b) {
     if (threadIdx.x == 0) {
         double M = -INFINITY, S = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge(M, S, sm[w], ss[w]);
-        b.part[2 * blockIdx.x] = M;
-        b.part[2 * blockIdx.x + 1] = S;
+        b.part[2 * bid] = M;
+        b.part[2 * bid + 1] = S;
     }
 }
 
 // LSE partials of b.logw (used after init / restart weights).
 template <typename T>
-__global__ void __launch_bounds__(256) k_lse_partials(Consts<T> k, Bufs<T> b, int conditional) {
+__device__ __forceinline__ void lse_partials_body(const Consts<T>& k, const Bufs<T>& b, int conditional, int bid,
+                                                  int nblk) {
     if (conditional && b.stats->restart_flag == 0) return;
     __shared__ double sm[8], ss[8];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     double m = -INFINITY, s = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.n;
-         i += (long long)gridDim.x * blockDim.x)
+    for (long long i = bid * (long long)blockDim.x + threadIdx.x; i < k.n; i += (long long)nblk * blockDim.x)
         lse_merge(m, s, (double)b.logw[i], 1.0);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -161,12 +170,12 @@ __global__ void __launch_bounds__(256) k_lse_partials(Consts<T> k, Bufs<T> b, in
     if (threadIdx.x == 0) {
         double M = -INFINITY, S = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) lse_merge(M, S, sm[w], ss[w]);
-        b.part[2 * blockIdx.x] = M;
-        b.part[2 * blockIdx.x + 1] = S;
+        b.part[2 * bid] = M;
+        b.part[2 * bid + 1] = S;
     }
 }
 
-__global__ void k_lse_merge(const double* __restrict__ part, int nb, DevStats* st, int conditional) {
+__device__ __forceinline__ void lse_merge_body(const double* __restrict__ part, int nb, DevStats* st, int conditional) {
     if (conditional && st->restart_flag == 0) return;
     __shared__ double red[32];
     __shared__ double s_max;
@@ -210,24 +219,24 @@ __global__ void k_lse_merge(const double* __restrict__ part, int nb, DevStats* s
 }
 
 template <typename T>
-__global__ void k_subtract(Consts<T> k, Bufs<T> b, int conditional) {
+__device__ __forceinline__ void subtract_body(const Consts<T>& k, const Bufs<T>& b, int conditional, int bid,
+                                              int nblk) {
     if (conditional && b.stats->restart_flag == 0) return;
     const T lam = (T)b.stats->lam_rel;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < k.n;
-         i += (long long)gridDim.x * blockDim.x)
+    for (long long i = bid * (long long)blockDim.x + threadIdx.x; i < k.n; i += (long long)nblk * blockDim.x)
         b.logw[i] = b.logw[i] - lam;
 }
 
-constexpr int kMomDims = YY_MAX_DIM / 256;   // coordinates per thread in k_moments
+constexpr int kMomDims = YY_MAX_DIM / 256;   // coordinates per thread in the moments pass
 
 // Normalises ell' and accumulates per-block weighted moments of u.
 template <typename T>
-__global__ void __launch_bounds__(256) k_moments(Consts<T> k, Bufs<T> b) {
+__device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& b, int bid, int nblk) {
     __shared__ T w_s[32];
     __shared__ double wc_s[2];
     const int tid = threadIdx.x;
-    const long long rows_per = (k.n + gridDim.x - 1) / gridDim.x;
-    const long long i0 = blockIdx.x * rows_per;
+    const long long rows_per = (k.n + nblk - 1) / nblk;
+    const long long i0 = bid * rows_per;
     const long long i1 = min(k.n, i0 + rows_per);
     const T lam = (T)b.stats->lam_rel;
     double W = 0.0, Q = 0.0;
@@ -274,7 +283,7 @@ __global__ void __launch_bounds__(256) k_moments(Consts<T> k, Bufs<T> b) {
         }
         __syncthreads();
     }
-    double* p = b.part + (size_t)blockIdx.x * (4 + 2 * k.r_pad);
+    double* p = b.part + (size_t)bid * (4 + 2 * k.r_pad);
     if (tid == 0) { p[0] = W; p[1] = Q; }
 #pragma unroll
     for (int q = 0; q < kMomDims; ++q) {
@@ -283,17 +292,13 @@ __global__ void __launch_bounds__(256) k_moments(Consts<T> k, Bufs<T> b) {
     }
 }
 
-// Scalars of the step and the coefficients of the sequential Chan merge of the block
-// moments (they depend on the block weights only): alpha_j = W_j / W_(<=j),
-// beta_j = W_(<j) W_j / W_(<=j).  ESS = W^2 / Q, Lambda = c_ref + lambda(c) + Lambda_rel,
-// Z += Lambda, step k += 1, restart test.
 // Scalars of the step: weight sum W and sum of squares Q over the block partials,
 // ESS = W^2 / Q, Lambda = c_ref + lambda(c) + Lambda_rel, Z += Lambda, step k += 1 and the
 // restart test.
 template <typename T>
-__global__ void __launch_bounds__(512) k_finalize_scalars(Consts<T> k, Bufs<T> b, int nb, int restart_interval,
-                                                          double ess_frac) {
-    __shared__ double red_w[16], red_q[16];
+__device__ __forceinline__ void finalize_scalars_body(const Consts<T>& k, const Bufs<T>& b, int nb,
+                                                      int restart_interval, double ess_frac) {
+    __shared__ double red_w[32], red_q[32];
     DevStats* st = b.stats;
     const int t = threadIdx.x;
     double w = 0.0, q = 0.0;
@@ -331,10 +336,10 @@ __global__ void __launch_bounds__(512) k_finalize_scalars(Consts<T> k, Bufs<T> b
 // x_hat = c + mean.  32 coordinates per block; the 8 warps take 8 contiguous groups of
 // partials and their group results are merged at the end.
 template <typename T>
-__global__ void __launch_bounds__(256) k_finalize_dims(Consts<T> k, Bufs<T> b, int nb) {
+__device__ __forceinline__ void finalize_dims_body(const Consts<T>& k, const Bufs<T>& b, int nb, int bid) {
     __shared__ double g_w[8][32], g_mu[8][32], g_m2[8][32];
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int d = blockIdx.x * 32 + lane;
+    const int d = bid * 32 + lane;
     const int per = (nb + 7) / 8;
     const int j0 = g * per, j1 = min(nb, j0 + per);
     double W = 0.0, mu = 0.0, M2 = 0.0;
@@ -374,6 +379,144 @@ __global__ void __launch_bounds__(256) k_finalize_dims(Consts<T> k, Bufs<T> b, i
     }
 }
 
+__device__ __forceinline__ void restart_begin_body(DevStats* st, int mode) {
+    if (threadIdx.x != 0) return;
+    if (mode == YY_RESTART_FORCE) st->restart_flag = 1;
+    st->last_restarted = 0;
+}
+
+template <typename T>
+__device__ __forceinline__ void restart_commit_body(const Consts<T>& k, const Bufs<T>& b) {
+    if (b.stats->restart_flag == 0) return;
+    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) b.centre[d] = (d < k.r) ? b.mean[d] : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        b.stats->restarts += 1;
+        b.stats->restart_flag = 0;
+        b.stats->last_restarted = 1;
+    }
+}
+
+// Row of the estimate history: x_hat[r], v_hat[r], ESS, Lambda, Z, restart test result.
+template <typename T>
+__device__ __forceinline__ void record_body(const Consts<T>& k, const Bufs<T>& b, double* __restrict__ row) {
+    for (int d = threadIdx.x; d < k.r; d += blockDim.x) {
+        row[d] = b.mean[d];
+        row[k.r + d] = b.var[d];
+    }
+    if (threadIdx.x == 0) {
+        row[2 * k.r] = b.stats->ess;
+        row[2 * k.r + 1] = b.stats->lam;
+        row[2 * k.r + 2] = b.stats->lognorm;
+        row[2 * k.r + 3] = b.stats->restart_flag ? 1.0 : 0.0;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// single-filter wrappers
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_obs_prep(Consts<T> k, Bufs<T> b, const double* __restrict__ dy) { obs_prep_body<T>(k, b, dy); }
+template <typename T>
+__global__ void __launch_bounds__(256) k_loglik(Consts<T> k, Bufs<T> b) { loglik_body<T>(k, b, blockIdx.x, gridDim.x); }
+template <typename T>
+__global__ void __launch_bounds__(256) k_lse_partials(Consts<T> k, Bufs<T> b, int conditional) {
+    lse_partials_body<T>(k, b, conditional, blockIdx.x, gridDim.x);
+}
+__global__ void k_lse_merge(const double* __restrict__ part, int nb, DevStats* st, int conditional) {
+    lse_merge_body(part, nb, st, conditional);
+}
+template <typename T>
+__global__ void k_subtract(Consts<T> k, Bufs<T> b, int conditional) {
+    subtract_body<T>(k, b, conditional, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_moments(Consts<T> k, Bufs<T> b) { moments_body<T>(k, b, blockIdx.x, gridDim.x); }
+template <typename T>
+__global__ void __launch_bounds__(512) k_finalize_scalars(Consts<T> k, Bufs<T> b, int nb, int restart_interval,
+                                                          double ess_frac) {
+    finalize_scalars_body<T>(k, b, nb, restart_interval, ess_frac);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) k_finalize_dims(Consts<T> k, Bufs<T> b, int nb) {
+    finalize_dims_body<T>(k, b, nb, blockIdx.x);
+}
+template <typename T>
+__global__ void k_restart_begin(DevStats* st, int mode) { restart_begin_body(st, mode); }
+template <typename T>
+__global__ void k_restart_commit(Consts<T> k, Bufs<T> b) { restart_commit_body<T>(k, b); }
+template <typename T>
+__global__ void k_record(Consts<T> k, Bufs<T> b, double* __restrict__ row) { record_body<T>(k, b, row); }
+
+// ---------------------------------------------------------------------------------------
+// batched wrappers: trajectory = blockIdx.y
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void kb_obs_prep(const Traj<T>* __restrict__ tr, const double* __restrict__ dy_row) {
+    const Traj<T>& t = tr[blockIdx.y];
+    obs_prep_body<T>(t.k, t.b, dy_row + t.dy_off);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) kb_loglik(const Traj<T>* __restrict__ tr) {
+    const Traj<T>& t = tr[blockIdx.y];
+    loglik_body<T>(t.k, t.b, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void kb_lse_merge(const Traj<T>* __restrict__ tr, int nb, int conditional) {
+    const Traj<T>& t = tr[blockIdx.y];
+    lse_merge_body(t.b.part, nb, t.b.stats, conditional);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) kb_moments(const Traj<T>* __restrict__ tr) {
+    const Traj<T>& t = tr[blockIdx.y];
+    moments_body<T>(t.k, t.b, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void __launch_bounds__(512) kb_finalize_scalars(const Traj<T>* __restrict__ tr, int nb) {
+    const Traj<T>& t = tr[blockIdx.y];
+    finalize_scalars_body<T>(t.k, t.b, nb, t.restart_interval, t.ess_frac);
+}
+template <typename T>
+__global__ void __launch_bounds__(256) kb_finalize_dims(const Traj<T>* __restrict__ tr, int nb) {
+    const Traj<T>& t = tr[blockIdx.y];
+    finalize_dims_body<T>(t.k, t.b, nb, blockIdx.x);
+}
+template <typename T>
+__global__ void kb_record(const Traj<T>* __restrict__ tr, double* __restrict__ hist_row) {
+    const Traj<T>& t = tr[blockIdx.y];
+    record_body<T>(t.k, t.b, hist_row + t.hist_off);
+}
+template <typename T>
+__global__ void kb_reset(const Traj<T>* __restrict__ tr, int B) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B) return;
+    tr[i].b.stats->clamps = 0u;
+    tr[i].b.stats->candidates = 0ull;
+}
+template <typename T>
+__global__ void kb_restart_begin(const Traj<T>* __restrict__ tr) { restart_begin_body(tr[blockIdx.y].b.stats, YY_RESTART_AUTO); }
+template <typename T>
+__global__ void __launch_bounds__(256) kb_lse_partials(const Traj<T>* __restrict__ tr) {
+    const Traj<T>& t = tr[blockIdx.y];
+    lse_partials_body<T>(t.k, t.b, 1, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void kb_subtract(const Traj<T>* __restrict__ tr) {
+    const Traj<T>& t = tr[blockIdx.y];
+    subtract_body<T>(t.k, t.b, 1, blockIdx.x, gridDim.x);
+}
+template <typename T>
+__global__ void kb_restart_commit(const Traj<T>* __restrict__ tr) {
+    const Traj<T>& t = tr[blockIdx.y];
+    restart_commit_body<T>(t.k, t.b);
+}
+
+// ---------------------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------------------
+
 template <typename T>
 cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy,
                           int restart_interval, double ess_frac, cudaStream_t s, int* launches) {
@@ -400,33 +543,23 @@ cudaError_t launch_normalise_only(const Consts<T>& k, const Bufs<T>& b, cudaStre
 }
 
 template <typename T>
-__global__ void k_restart_begin(DevStats* st, int mode) {
-    if (mode == YY_RESTART_FORCE) st->restart_flag = 1;
-    st->last_restarted = 0;
-}
-
-template <typename T>
-__global__ void k_restart_commit(Consts<T> k, Bufs<T> b) {
-    if (b.stats->restart_flag == 0) return;
-    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) b.centre[d] = (d < k.r) ? b.mean[d] : 0.0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        b.stats->restarts += 1;
-        b.stats->restart_flag = 0;
-        b.stats->last_restarted = 1;
-    }
+cudaError_t launch_record(const Consts<T>& k, const Bufs<T>& b, double* hist_row, cudaStream_t s) {
+    k_record<T><<<1, 256, 0, s>>>(k, b, hist_row);
+    return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, bool first,
                              double prior_mean, double prior_var, int init_kind, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prep_restart_batch(const Traj<T>* d_traj, int B, long long n_pad_max, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind,
                            cudaStream_t s, int* launches) {
     if (mode == YY_RESTART_NEVER) return cudaSuccess;
     const int nb = kNumPartBlocks;
-    k_restart_begin<T><<<1, 1, 0, s>>>(b.stats, mode);
+    k_restart_begin<T><<<1, 32, 0, s>>>(b.stats, mode);
     cudaError_t e = launch_prep_mode<T>(k, b, 2 /*restart*/, false, 0.0, 1.0, init_kind, s);
     if (e != cudaSuccess) return e;
     k_lse_partials<T><<<nb, 256, 0, s>>>(k, b, 1);
@@ -437,35 +570,62 @@ cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int i
     return cudaGetLastError();
 }
 
-// Row of the estimate history: x_hat[r], v_hat[r], ESS, Lambda, Z, restart test result.
 template <typename T>
-__global__ void k_record(Consts<T> k, Bufs<T> b, double* __restrict__ row) {
-    for (int d = threadIdx.x; d < k.r; d += blockDim.x) {
-        row[d] = b.mean[d];
-        row[k.r + d] = b.var[d];
-    }
-    if (threadIdx.x == 0) {
-        row[2 * k.r] = b.stats->ess;
-        row[2 * k.r + 1] = b.stats->lam;
-        row[2 * k.r + 2] = b.stats->lognorm;
-        row[2 * k.r + 3] = b.stats->restart_flag ? 1.0 : 0.0;
-    }
-}
-
-template <typename T>
-cudaError_t launch_record(const Consts<T>& k, const Bufs<T>& b, double* hist_row, cudaStream_t s) {
-    k_record<T><<<1, 256, 0, s>>>(k, b, hist_row);
+cudaError_t launch_update_batch(const Traj<T>* d_traj, int B, int r_max, const double* dy_row,
+                                int nbu, cudaStream_t s, int* launches) {
+    const dim3 one(1, B), many(nbu, B);
+    kb_obs_prep<T><<<one, 256, 0, s>>>(d_traj, dy_row);
+    kb_loglik<T><<<many, 256, 0, s>>>(d_traj);
+    kb_lse_merge<T><<<one, 256, 0, s>>>(d_traj, nbu, 0);
+    kb_moments<T><<<many, 256, 0, s>>>(d_traj);
+    kb_finalize_scalars<T><<<one, 512, 0, s>>>(d_traj, nbu);
+    kb_finalize_dims<T><<<dim3((r_max + 31) / 32, B), 256, 0, s>>>(d_traj, nbu);
+    if (launches) *launches += 6;
     return cudaGetLastError();
 }
 
-#define YY_INST(T)                                                                             \
-    template cudaError_t launch_record<T>(const Consts<T>&, const Bufs<T>&, double*, cudaStream_t); \
-    template cudaError_t launch_update<T>(const Consts<T>&, const Bufs<T>&, const double*, int, \
-                                          double, cudaStream_t, int*);                         \
-    template cudaError_t launch_normalise_only<T>(const Consts<T>&, const Bufs<T>&,             \
-                                                  cudaStream_t, int*);                          \
-    template cudaError_t launch_restart<T>(const Consts<T>&, const Bufs<T>&, int, int,          \
-                                           cudaStream_t, int*);
+template <typename T>
+cudaError_t launch_restart_batch(const Traj<T>* d_traj, int B, int r_max, long long n_pad_max,
+                                 int nbu, cudaStream_t s, int* launches) {
+    (void)r_max;
+    const dim3 one(1, B), many(nbu, B);
+    kb_restart_begin<T><<<one, 32, 0, s>>>(d_traj);
+    cudaError_t e = launch_prep_restart_batch<T>(d_traj, B, n_pad_max, s);
+    if (e != cudaSuccess) return e;
+    kb_lse_partials<T><<<many, 256, 0, s>>>(d_traj);
+    kb_lse_merge<T><<<one, 256, 0, s>>>(d_traj, nbu, 1);
+    kb_subtract<T><<<many, 256, 0, s>>>(d_traj);
+    kb_restart_commit<T><<<one, 256, 0, s>>>(d_traj);
+    if (launches) *launches += 7;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_record_batch(const Traj<T>* d_traj, int B, double* hist_row, cudaStream_t s, int* launches) {
+    kb_record<T><<<dim3(1, B), 256, 0, s>>>(d_traj, hist_row);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_reset_batch(const Traj<T>* d_traj, int B, cudaStream_t s, int* launches) {
+    kb_reset<T><<<(B + 127) / 128, 128, 0, s>>>(d_traj, B);
+    if (launches) *launches += 1;
+    return cudaGetLastError();
+}
+
+#define YY_INST(T)                                                                                      \
+    template cudaError_t launch_record<T>(const Consts<T>&, const Bufs<T>&, double*, cudaStream_t);     \
+    template cudaError_t launch_update<T>(const Consts<T>&, const Bufs<T>&, const double*, int, double, \
+                                          cudaStream_t, int*);                                          \
+    template cudaError_t launch_normalise_only<T>(const Consts<T>&, const Bufs<T>&, cudaStream_t, int*); \
+    template cudaError_t launch_restart<T>(const Consts<T>&, const Bufs<T>&, int, int, cudaStream_t, int*); \
+    template cudaError_t launch_update_batch<T>(const Traj<T>*, int, int, const double*, int, cudaStream_t, \
+                                                int*);                                                  \
+    template cudaError_t launch_restart_batch<T>(const Traj<T>*, int, int, long long, int, cudaStream_t,  \
+                                                 int*);                                                 \
+    template cudaError_t launch_record_batch<T>(const Traj<T>*, int, double*, cudaStream_t, int*);      \
+    template cudaError_t launch_reset_batch<T>(const Traj<T>*, int, cudaStream_t, int*);
 YY_INST(float)
 YY_INST(double)
 #undef YY_INST
