@@ -375,6 +375,7 @@ def run_batch(args):
     t_tune = time.perf_counter()
     bn, grid = bt.autotune(cache, reps=2)
     t_tune = time.perf_counter() - t_tune
+    routing = bt.routing()
     with torch.cuda.stream(bt.stream):
         if W:
             bt.run_steps(dy_all[:W])
@@ -413,7 +414,9 @@ def run_batch(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
            "data": "synthetic (seeded Euler-Maruyama cubic sensor / linear-Gaussian, scrambled Sobol nodes)",
            "config": {"workload": "batched_256", "trajectories": 256, "r": "10..200", "n": "2048..32768 log-uniform",
-                      "n_scales": 2, "schedule": {"bn": bn, "grid": grid, "autotune_s": round(t_tune, 2)},
+                      "n_scales": 2, "schedule": {"bn": bn, "grid": grid, "autotune_s": round(t_tune, 2),
+                                                  "fp32_form_members": int(routing.sum()),
+                                                  "fp32_form_max_r": int(max([m.r for m, p in zip(members, routing) if p] or [0]))},
                       "time_loop": "one CUDA graph of K batched steps"},
            "gpu_launches": int(launches), "clocks": clk.summary(),
            "rmse_cubic_mean": float(np.mean(rm_c)), "rmse_linear_mean": float(np.mean(rm_l)),

@@ -225,14 +225,20 @@ YY_EXPORT yy_status yy_batch_graph_capture(yy_batch* bt, const double* d_dy_all,
 YY_EXPORT yy_status yy_batch_graph_launch(yy_batch* bt);
 
 /* Schedule of the batched BF16 prediction: source-tile width bn (128 or 256) and the
- * number of persistent CTAs (1..1024).  yy_batch_autotune times the candidates bn x
- * {1, 2, 4} x SM count on the batch itself (reps predictions each), keeps the fastest and,
- * if cache_path is not NULL, records it there keyed by the batch's shape (and reuses a
- * recorded choice instead of timing). */
+ * number of persistent CTAs (1..1024).  yy_batch_autotune first runs one prediction with
+ * every filter on the tensor-core screen and reads each filter's screen pass fraction
+ * (pairs evaluated exactly / n^2); it then times, on the batch itself (reps predictions
+ * each), every combination of a routing threshold in {1e-3, 1e-2, 5e-2, never} (filters
+ * whose fraction exceeds it use the FP32 form, which is faster when most pairs are within
+ * reach of the kernel, i.e. at low r), bn in {256, 128} and grid in {1, 2, 4} x SM count,
+ * and keeps the fastest.  If cache_path is not NULL the choice is recorded there keyed by
+ * the batch's shape and reused instead of timing.  yy_batch_get_routing reports the
+ * per-filter choice (0 = tensor-core screen, 1 = FP32 form; host int32 [B]). */
 YY_EXPORT yy_status yy_batch_set_schedule(yy_batch* bt, int32_t bn, int32_t grid);
 YY_EXPORT yy_status yy_batch_get_schedule(const yy_batch* bt, int32_t* h_bn, int32_t* h_grid);
 YY_EXPORT yy_status yy_batch_autotune(yy_batch* bt, const char* cache_path, int32_t reps, int32_t* h_bn,
                                       int32_t* h_grid);
+YY_EXPORT yy_status yy_batch_get_routing(const yy_batch* bt, int32_t* h_path);
 
 /* Kernel launches issued so far, and per replay of the captured graph. */
 YY_EXPORT int64_t yy_batch_launch_count(const yy_batch* bt);
@@ -283,6 +289,11 @@ YY_EXPORT yy_status yy_weighted_moments_static(const float* d_u, int64_t n, int3
 
 /* Kernel launches issued by this handle so far (for launch accounting). */
 YY_EXPORT int64_t yy_launch_count(const yy_filter* f);
+
+/* Work counters of the last yy_predict: non-positive combinations (as yy_get_clamps) and,
+ * for BF16 precision, the pairs that passed the screen and were evaluated exactly in
+ * float32 (self terms not included).  Synchronises. */
+YY_EXPORT yy_status yy_get_counters(yy_filter* f, int64_t* h_clamps, int64_t* h_exact_pairs);
 
 /* Human-readable name of a status code (static storage). */
 YY_EXPORT const char* yy_status_str(yy_status s);

@@ -37,7 +37,8 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_batch_workspace_bytes", "yy_batch_create", "yy_batch_destroy", "yy_batch_filter",
            "yy_batch_run_steps", "yy_batch_predict", "yy_batch_graph_capture", "yy_batch_graph_launch",
            "yy_batch_set_schedule", "yy_batch_get_schedule", "yy_batch_autotune",
-           "yy_batch_launch_count", "yy_batch_graph_kernel_count")
+           "yy_batch_launch_count", "yy_batch_graph_kernel_count", "yy_get_counters",
+           "yy_batch_get_routing")
 
 
 class YYError(RuntimeError):
@@ -92,6 +93,8 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_batch_autotune": (I32, [P, ctypes.c_char_p, I32, P, P]),
         "yy_batch_launch_count": (I64, [P]),
         "yy_batch_graph_kernel_count": (I64, [P]),
+        "yy_get_counters": (I32, [P, P, P]),
+        "yy_batch_get_routing": (I32, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -256,6 +259,12 @@ class Filter:
     def launches(self) -> int:
         return int(self.lib.yy_launch_count(self.h))
 
+    def counters(self):
+        """(clamps, pairs evaluated exactly) of the last prediction."""
+        c, p = ctypes.c_int64(), ctypes.c_int64()
+        _check("yy_get_counters", self.lib.yy_get_counters(self.h, ctypes.byref(c), ctypes.byref(p)))
+        return c.value, p.value
+
     def run_steps(self, dy_all_dev, hist_dev=None) -> None:
         """dy_all_dev: float64 [K][r] device tensor; hist_dev: float64 [K][2r + 4] or None."""
         K = dy_all_dev.shape[0]
@@ -372,6 +381,11 @@ class Batch:
         _check("yy_batch_autotune", self.lib.yy_batch_autotune(
             self.h, None if cache_path is None else cache_path.encode(), reps, ctypes.byref(bn), ctypes.byref(grid)))
         return bn.value, grid.value
+
+    def routing(self):
+        out = np.zeros(self.B, dtype=np.int32)
+        _check("yy_batch_get_routing", self.lib.yy_batch_get_routing(self.h, _ptr(out)))
+        return out
 
     def launches(self) -> int:
         return int(self.lib.yy_batch_launch_count(self.h))

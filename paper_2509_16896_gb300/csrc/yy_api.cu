@@ -484,6 +484,18 @@ yy_status yy_get_clamps(yy_filter* f, int64_t* h_clamps) {
 
 int64_t yy_launch_count(const yy_filter* f) { return f ? f->launches : 0; }
 
+yy_status yy_get_counters(yy_filter* f, int64_t* h_clamps, int64_t* h_exact_pairs) {
+    if (!f) return YY_ERR_ARG;
+    DevStats* st = f->fp64 ? f->bd.stats : f->bf.stats;
+    DevStats hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, st, sizeof(DevStats), cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    if (h_clamps) *h_clamps = hs.clamps;
+    if (h_exact_pairs) *h_exact_pairs = (int64_t)hs.candidates;
+    return YY_OK;
+}
+
 const char* yy_status_str(yy_status s) {
     switch (s) {
         case YY_OK: return "YY_OK";

@@ -1,8 +1,9 @@
 // Batches of independent filters with ragged n and r: one launch per pass covers every
 // trajectory, the prediction is one persistent tcgen05 launch over a longest-processing-
-// time-first work list, and the K-step loop can be captured as one CUDA graph.  A small
-// autotuner picks the source-tile width and the persistent grid by timing the batch's own
-// prediction.
+// time-first work list (plus one batched FP32-form launch for the filters routed there),
+// and the K-step loop can be captured as one CUDA graph.  The autotuner measures each
+// filter's screen pass fraction, then times routing thresholds x source-tile widths x
+// persistent grid sizes on the batch's own prediction and keeps the fastest.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -40,6 +41,9 @@ struct yy_batch {
     int max_items, max_grid;
     // schedule
     int bn, grid, n_items;
+    std::vector<int> path;          // per filter: 0 = tcgen05 screen, 1 = FP32 form
+    double dense_frac;              // screen pass fraction above which a filter is routed to FP32
+    int n_tc, n_simt;
     bool uploaded;
     long long launches;
     cudaGraph_t graph;
@@ -94,6 +98,7 @@ void lpt_schedule(const yy_batch* bt, int grid, int bn, std::vector<int2>& items
     std::vector<It> all;
     for (int b = 0; b < bt->B; ++b) {
         const yy_filter* f = bt->filters[b];
+        if (bt->path[b] != 0) continue;
         const long long tiles = f->n_pad / 128;
         const double src_tiles = (double)(f->n_pad / bn);
         const double cost = src_tiles * ((double)(f->r_pad / 64) + 1.0);
@@ -135,6 +140,7 @@ yy_status upload(yy_batch* bt) {
         tr[b].restart_interval = f->cfg.restart_interval;
         tr[b].ess_frac = f->cfg.ess_frac;
         tr[b].restart_init = f->cfg.restart_init;
+        tr[b].path = bt->path[b];
         if (bt->precision == YY_PREC_BF16) {
             if (!make_tc_map(&maps[kMapBytes * 2 * b], f->bf.ubf, f->n_pad, f->r_pad, 128) ||
                 !make_tc_map(&maps[kMapBytes * (2 * b + 1)], f->bf.ubf, f->n_pad, f->r_pad, bt->bn))
@@ -158,6 +164,9 @@ yy_status upload(yy_batch* bt) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(bt->stream);
     if (e != cudaSuccess) return YY_ERR_CUDA;
     bt->n_items = (int)items.size();
+    bt->n_tc = 0;
+    for (int b = 0; b < bt->B; ++b) bt->n_tc += (bt->path[b] == 0);
+    bt->n_simt = bt->B - bt->n_tc;
     bt->uploaded = true;
     return YY_OK;
 }
@@ -165,14 +174,12 @@ yy_status upload(yy_batch* bt) {
 yy_status batch_predict(yy_batch* bt) {
     int l = 0;
     cudaError_t e = launch_reset_batch<float>(bt->d_traj, bt->B, bt->stream, &l);
-    if (e == cudaSuccess) {
-        if (bt->precision == YY_PREC_BF16)
-            e = launch_ksum_tc_batch(bt->d_traj, bt->B, bt->N, bt->n_pad_max, bt->d_maps, bt->d_items,
-                                     bt->d_cta_start, bt->grid, bt->bn, bt->filters[0]->kf, bt->filters[0]->bf,
-                                     bt->map_any, bt->stream, &l);
-        else
-            e = launch_ksum_simt_batch<float>(bt->d_traj, bt->B, bt->N, bt->n_pad_max, bt->r_max, bt->stream, &l);
-    }
+    if (e == cudaSuccess && bt->n_tc > 0)
+        e = launch_ksum_tc_batch(bt->d_traj, bt->B, bt->N, bt->n_pad_max, bt->d_maps, bt->d_items,
+                                 bt->d_cta_start, bt->grid, bt->bn, bt->filters[0]->kf, bt->filters[0]->bf,
+                                 bt->map_any, bt->stream, &l);
+    if (e == cudaSuccess && bt->n_simt > 0)
+        e = launch_ksum_simt_batch<float>(bt->d_traj, bt->B, bt->N, bt->n_pad_max, bt->r_max, bt->stream, &l);
     bt->launches += l;
     return e == cudaSuccess ? YY_OK : YY_ERR_CUDA;
 }
@@ -231,6 +238,8 @@ yy_status yy_batch_create(const yy_config* cfgs, int32_t B, void* d_workspace, s
     bt->ws = (char*)d_workspace;
     bt->ws_bytes = bytes;
     bt->nbu = kBatchRedBlocks;
+    bt->path.assign(B, cfgs[0].precision == YY_PREC_BF16 ? 0 : 1);
+    bt->dense_frac = INFINITY;
     bt->bn = 256;
     bt->grid = sm_count();
     bt->max_grid = kMaxGrid;
@@ -364,16 +373,35 @@ yy_status yy_batch_autotune(yy_batch* bt, const char* cache_path, int32_t reps, 
         if (h_grid) *h_grid = bt->grid;
         return YY_OK;
     }
+    // 1. screen pass fraction of every filter, from one batched prediction on the screen path
+    std::fill(bt->path.begin(), bt->path.end(), 0);
+    bt->uploaded = false;
+    yy_status st = upload(bt);
+    if (st != YY_OK) return st;
+    if ((st = batch_predict(bt)) != YY_OK) return st;
+    std::vector<double> frac(bt->B);
+    for (int b = 0; b < bt->B; ++b) {
+        int64_t cl = 0, ex = 0;
+        if ((st = yy_get_counters(bt->filters[b], &cl, &ex)) != YY_OK) return st;
+        const double n = (double)bt->filters[b]->cfg.n;
+        frac[b] = (double)ex / (n * n);
+    }
+    auto route = [&](double thr) {
+        for (int b = 0; b < bt->B; ++b) bt->path[b] = (frac[b] > thr) ? 1 : 0;
+    };
+    // 2. cached choice, or time the candidates
     const uint64_t sig = batch_signature(bt);
     if (cache_path) {
         if (FILE* fh = fopen(cache_path, "r")) {
             unsigned long long s;
             int bn, grid;
+            double thr;
             bool hit = false;
-            while (fscanf(fh, "%llx %d %d", &s, &bn, &grid) == 3)
-                if (s == sig) { hit = true; bt->bn = bn; bt->grid = grid; }
+            while (fscanf(fh, "%llx %d %d %lf", &s, &bn, &grid, &thr) == 4)
+                if (s == sig) { hit = true; bt->bn = bn; bt->grid = grid; bt->dense_frac = thr; }
             fclose(fh);
             if (hit) {
+                route(bt->dense_frac);
                 bt->uploaded = false;
                 if (h_bn) *h_bn = bt->bn;
                 if (h_grid) *h_grid = bt->grid;
@@ -384,40 +412,51 @@ yy_status yy_batch_autotune(yy_batch* bt, const char* cache_path, int32_t reps, 
     const int sms = sm_count();
     const int cand_bn[2] = {256, 128};
     const int cand_mul[3] = {1, 2, 4};
+    const double cand_thr[4] = {1e-3, 1e-2, 5e-2, INFINITY};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return YY_ERR_CUDA;
     float best = INFINITY;
     int best_bn = bt->bn, best_grid = bt->grid;
-    for (int bn : cand_bn)
-        for (int mul : cand_mul) {
-            const int grid = std::min(kMaxGrid, sms * mul);
-            bt->bn = bn;
-            bt->grid = grid;
-            bt->uploaded = false;
-            yy_status st = upload(bt);
-            if (st != YY_OK) continue;
-            if ((st = batch_predict(bt)) != YY_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
-            cudaEventRecord(e0, bt->stream);
-            for (int r = 0; r < reps; ++r) batch_predict(bt);
-            cudaEventRecord(e1, bt->stream);
-            if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return YY_ERR_CUDA; }
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_bn = bn; best_grid = grid; }
-        }
+    double best_thr = INFINITY;
+    for (double thr : cand_thr)
+        for (int bn : cand_bn)
+            for (int mul : cand_mul) {
+                const int grid = std::min(kMaxGrid, sms * mul);
+                route(thr);
+                bt->bn = bn;
+                bt->grid = grid;
+                bt->uploaded = false;
+                if (upload(bt) != YY_OK) continue;
+                if ((st = batch_predict(bt)) != YY_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+                cudaEventRecord(e0, bt->stream);
+                for (int r = 0; r < reps; ++r) batch_predict(bt);
+                cudaEventRecord(e1, bt->stream);
+                if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return YY_ERR_CUDA; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; best_bn = bn; best_grid = grid; best_thr = thr; }
+            }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     bt->bn = best_bn;
     bt->grid = best_grid;
+    bt->dense_frac = best_thr;
+    route(best_thr);
     bt->uploaded = false;
     if (cache_path) {
         if (FILE* fh = fopen(cache_path, "a")) {
-            fprintf(fh, "%llx %d %d\n", (unsigned long long)sig, best_bn, best_grid);
+            fprintf(fh, "%llx %d %d %.17g\n", (unsigned long long)sig, best_bn, best_grid, best_thr);
             fclose(fh);
         }
     }
     if (h_bn) *h_bn = best_bn;
     if (h_grid) *h_grid = best_grid;
+    return YY_OK;
+}
+
+yy_status yy_batch_get_routing(const yy_batch* bt, int32_t* h_path) {
+    if (!bt || !h_path) return YY_ERR_ARG;
+    for (int b = 0; b < bt->B; ++b) h_path[b] = bt->path[b];
     return YY_OK;
 }
 

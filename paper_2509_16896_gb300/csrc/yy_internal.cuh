@@ -94,6 +94,7 @@ struct Traj {
     int restart_interval;
     double ess_frac;
     int restart_init;
+    int path;              // prediction kernel: 0 = tcgen05 screen, 1 = FP32 form
 };
 
 // Launch helpers (defined in the .cu files).

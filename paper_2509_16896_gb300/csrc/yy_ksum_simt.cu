@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int r
 template <typename T, int N>
 __global__ void __launch_bounds__(256) kb_ksum_simt(const Traj<T>* __restrict__ tr) {
     const Traj<T>& t = tr[blockIdx.y];
-    if ((long long)blockIdx.x * BM >= t.k.n_pad) return;
+    if (t.path == 0 || (long long)blockIdx.x * BM >= t.k.n_pad) return;
     const int rk = ((t.k.r + BK - 1) / BK) * BK;
     ksum_simt_body<T, N>(t.k, t.b, rk, blockIdx.x);
 }

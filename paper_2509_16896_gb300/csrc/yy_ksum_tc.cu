@@ -21,8 +21,13 @@
 //     and lmax the largest source log-weight of the tile.  With T = ln n + 20 the skipped
 //     terms add at most e^-20 relative mass;
 //  4. pairs that survive the screen are evaluated exactly in float32 from the float32
-//     node coordinates (difference form, warp-cooperative over the coordinates) and fed
-//     to the online log-sum-exp of their target row.
+//     node coordinates (difference form; for r > 64 warp-cooperative over the
+//     coordinates, one pair at a time; for r <= 64 each lane evaluates its own row's
+//     pairs) and fed to the online log-sum-exp of their target row.
+//
+// The screen pays off when few pairs survive (high r: at r >= 100 essentially only the
+// self terms).  At low r most pairs are within reach of the kernel and the plain FP32
+// form is faster; the batch autotuner routes such filters there.
 //
 // Work item = one tile of 128 targets of one filter over all of that filter's sources
 // (source tiles of BN = 256 or 128).  A single filter launches one CTA per item; a batch
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(128) k_tc_colprep(Consts<float> k, Bufs<float>
 
 __global__ void __launch_bounds__(128) kb_tc_colprep(const Traj<float>* __restrict__ tr) {
     const Traj<float>& t = tr[blockIdx.y];
-    if ((long long)blockIdx.x * 128 >= t.k.n_pad) return;
+    if (t.path != 0 || (long long)blockIdx.x * 128 >= t.k.n_pad) return;
     colprep_body(t.k, t.b, blockIdx.x);
 }
 
@@ -432,6 +437,42 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     }
                     const long long sb = (long long)t * BN + ch * 32;
                     if (i >= sb && i < sb + 32) cm &= ~(1u << (int)(i - sb));   // self term already counted
+                    if (k.r <= 64) {
+                        // short rows: every lane evaluates its own row's candidates (its own
+                        // target, the chunk's sources) over the coordinates
+                        const float* ut = b.u + (size_t)i * k.r_pad;
+                        const float* ft = b.f + (size_t)i * k.r_pad;
+                        while (cm) {
+                            const int c = __ffs(cm) - 1;
+                            cm &= cm - 1u;
+                            const long long src = sb + c;
+                            const float* us = b.u + (size_t)src * k.r_pad;
+                            float s1 = 0.f, s2 = 0.f;
+                            for (int d = 0; d < k.r; ++d) {
+                                const float dl = ut[d] - us[d];
+                                s1 = fmaf(dl, dl, s1);
+                                s2 = fmaf(dl, ft[d], s2);
+                            }
+                            const float ls = b.mask[src] ? -INFINITY : b.logw[src];
+                            if (ls != -INFINITY) {
+#pragma unroll
+                                for (int j = 0; j < N; ++j) {
+                                    const float sc = fmaf(-s1, k.inv2tau[j], s2) + (rowc[j] + ls);
+                                    if (sc > mx[j]) {
+                                        sm[j] = (mx[j] == -INFINITY) ? 1.f : sm[j] * expf(mx[j] - sc) + 1.f;
+                                        mx[j] = sc;
+                                    } else {
+                                        sm[j] += expf(sc - mx[j]);
+                                    }
+                                }
+                            }
+                            ++ncand;
+                        }
+                        theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
+                        continue;
+                    }
+                    // long rows: the warp evaluates one candidate at a time, coalesced over
+                    // the coordinates
                     while (true) {
                         const uint32_t who = __ballot_sync(0xffffffffu, cm != 0u);
                         if (who == 0u) break;

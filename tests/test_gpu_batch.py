@@ -107,5 +107,12 @@ def test_every_schedule_gives_the_same_prediction(yy_lib, tmp_path):
     bn, grid = bt.autotune(cache, reps=2)
     assert bn in (128, 256) and 1 <= grid <= 1024
     assert bt.schedule() == (bn, grid)
+    routing = bt.routing()
     bt2 = _batch("bf16")
     assert bt2.autotune(cache, reps=2) == (bn, grid)   # cached choice reused
+    assert np.array_equal(bt2.routing(), routing)
+    # the tuned batch (some members possibly on the FP32 form) gives the same answer
+    hist = torch.zeros((K, bt.H), dtype=torch.float64, device="cuda")
+    bt.run_steps(dy_all, hist)
+    h = hist.cpu().numpy()
+    assert np.max(np.abs(h - ref) / np.maximum(1.0, np.abs(ref))) <= 1e-5
