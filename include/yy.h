@@ -82,6 +82,13 @@ typedef enum { YY_PREC_FP64 = 0, YY_PREC_FP32 = 1, YY_PREC_BF16 = 2 } yy_precisi
  * GAUSS = log N(x; x_hat, diag(max(v_hat, (R/4)^2))), UNIFORM = equal weights. */
 typedef enum { YY_RESTART_INIT_GAUSS = 0, YY_RESTART_INIT_UNIFORM = 1 } yy_restart_init;
 
+/* Where a restart puts the new box.  PLAIN: centre x_hat, half-widths unchanged (Section
+ * 5).  LEARNED: centre x_hat + delta and half-widths R exp(lambda) from the restart-proposal
+ * network attached with yy_set_restart_mlp (a library addition, not in the paper); it falls
+ * back to PLAIN when no network is attached, when an output is not finite, or when a
+ * half-width leaves [R/8, 8R]. */
+typedef enum { YY_RESTART_PLAIN = 0, YY_RESTART_LEARNED = 1 } yy_restart_rule;
+
 /* yy_restart modes: AUTO applies the device-side test computed by the last yy_update
  * (ESS < ess_frac * n, or restart_interval >= 2 and step % restart_interval == 0);
  * FORCE restarts unconditionally; NEVER only reports the test. */
@@ -102,6 +109,7 @@ typedef struct {
     int32_t restart_init;      /* yy_restart_init */
     double prior_mean;         /* x_0 ~ N(prior_mean, prior_var I) */
     double prior_var;          /* > 0 */
+    int32_t restart_rule;      /* yy_restart_rule */
 } yy_config;
 
 /* Bytes of device workspace that yy_create needs for cfg (0 if cfg is invalid). */
@@ -187,6 +195,44 @@ YY_EXPORT yy_status yy_graph_launch(yy_filter* f);
 /* Number of kernel launches one replay of the captured graph performs (0 if none). */
 YY_EXPORT int64_t yy_graph_kernel_count(const yy_filter* f);
 
+/* ---- restart-proposal network (a library addition; the paper has no counterpart) -----
+ * A perceptron z = [x_hat; sqrt(v_hat); dy/sqrt(dt)] (3r) -> H -> H (ReLU) -> [delta; lambda]
+ * (2r), trained and run on the device with BF16 operands and FP32 accumulation.  Loss:
+ * mean over rows and coordinates of (t - delta)^2 / (2 s^2) + log s, s = (R/3) exp(lambda),
+ * where t = x_true - x_hat at restarts of a plain run.  Parameters are packed FP32:
+ * W1 [H][3r], b1 [H], W2 [H][H], b2 [H], W3 [2r][H], b3 [2r].  Memory: one caller-owned device
+ * workspace of yy_mlp_workspace_bytes bytes (256-byte aligned). */
+typedef struct yy_mlp yy_mlp;
+
+YY_EXPORT int64_t yy_mlp_param_count(int32_t r, int32_t hidden);
+YY_EXPORT size_t yy_mlp_workspace_bytes(int32_t r, int32_t hidden, int32_t max_batch);
+YY_EXPORT yy_status yy_mlp_create(int32_t r, int32_t hidden, int32_t max_batch, void* d_workspace, size_t bytes,
+                                  void* stream, yy_mlp** out);
+YY_EXPORT yy_status yy_mlp_destroy(yy_mlp* net);
+
+/* Copies parameters in (and resets the Adam moments) / out; host float [param_count]. */
+YY_EXPORT yy_status yy_mlp_set_params(yy_mlp* net, const float* h_params);
+YY_EXPORT yy_status yy_mlp_get_params(yy_mlp* net, float* h_params);
+
+/* Forward pass: d_x device float [B][3r] -> d_out device float [B][2r]. */
+YY_EXPORT yy_status yy_mlp_forward(yy_mlp* net, const float* d_x, int32_t B, float* d_out);
+
+/* Loss and parameter gradients of one batch (B <= max_batch): d_x [B][3r], d_t [B][r];
+ * R the base half-width.  h_loss (host float) and h_grads (host float [param_count]) may be
+ * NULL.  Synchronises. */
+YY_EXPORT yy_status yy_mlp_loss_grad(yy_mlp* net, const float* d_x, const float* d_t, int32_t B, double R,
+                                     float* h_loss, float* h_grads);
+
+/* Adam training (b1 0.9, b2 0.999, eps 1e-8) on M rows, epochs passes of shuffled
+ * mini-batches (seeded); h_last_loss receives the last mini-batch's loss.  Synchronises. */
+YY_EXPORT yy_status yy_mlp_train(yy_mlp* net, const float* d_x, const float* d_t, int64_t M, double R,
+                                 int32_t epochs, int32_t batch, float lr, uint64_t seed, float* h_last_loss);
+
+/* Attaches (or with NULL detaches) the network used by restarts of a filter whose
+ * cfg.restart_rule is YY_RESTART_LEARNED.  The network must have been created with the
+ * filter's r; it must stay alive while attached. */
+YY_EXPORT yy_status yy_set_restart_mlp(yy_filter* f, yy_mlp* net);
+
 /* ---- batches of independent filters ------------------------------------------------
  * B filters with their own r, n, model, box and restart settings (same precision, FP32 or
  * BF16, and same n_scales) advance together: every pass of a step is one launch for the
@@ -258,6 +304,10 @@ YY_EXPORT yy_status yy_get_log_weights(yy_filter* f, void* h_logw, double* h_off
  * step counter.  Re-evaluates the drift at the nodes.  Used for checkpoint/resume. */
 YY_EXPORT yy_status yy_set_state(yy_filter* f, const double* h_center, const void* h_logw,
                        double lognorm, int64_t step);
+
+/* Reads the current box: centre and half-widths (host double [r] each, either may be
+ * NULL).  Synchronises. */
+YY_EXPORT yy_status yy_get_box(yy_filter* f, double* h_center, double* h_halfwidth);
 
 /* Reads the box centre (host double [r]), Z and step counter. Synchronises. */
 YY_EXPORT yy_status yy_get_state(yy_filter* f, double* h_center, double* h_lognorm, int64_t* h_step);

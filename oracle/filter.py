@@ -17,8 +17,11 @@ Per step k (Section 2.2, "Procedure"; log-domain forms of Section 7):
      v_hat = sum w_hat (x - x_hat)^2; ESS = 1 / sum w_hat^2.
   5. restart  (Section 5): when ESS < rho n, or iota >= 2 and k mod iota == 0, the box is
      re-centred at x_hat, the reference nodes are translated (the same u), and the
-     weights are re-initialised from N(x_hat, diag(max(v_hat, v_min))), v_min = (R/4)^2,
-     or uniformly.  Z is left unchanged by a restart.
+     weights are re-initialised from N(c, diag(max(v_hat, v_min))), v_min = (R/4)^2,
+     c the new centre, or uniformly.  Z is left unchanged by a restart.  With the learned
+     rule (a library addition, see oracle/mlp.py) the centre is x_hat + delta and the
+     half-widths R exp(lambda); the reference nodes are re-mapped from their Sobol
+     integers to the new half-widths.
 
 Nodes are held as float32 box coordinates u (what both implementations store) and
 float64 centre c; positions are x = c + u in float64.
@@ -47,6 +50,8 @@ class Problem:
     prior_mean: float = 0.0
     prior_var: float = 1.0
     restart_init: str = "gauss"   # "gauss" | "uniform"
+    restart_rule: str = "plain"   # "plain" | "learned"
+    mlp_params: dict | None = None
 
     @property
     def taus(self) -> np.ndarray:
@@ -54,7 +59,7 @@ class Problem:
 
     @property
     def log_wq(self) -> float:
-        return float(np.sum(np.log(2.0 * self.R)) - np.log(self.n))
+        return log_wq(self.R, self.n)
 
     @property
     def coef(self) -> np.ndarray:
@@ -69,17 +74,22 @@ class Prepared:
     mask: np.ndarray   # [n] bool
 
 
+def log_wq(half: np.ndarray, n: int) -> float:
+    """Quadrature volume per node of the box with these half-widths (Sec. 4.1 Remark)."""
+    return float(np.sum(np.log(2.0 * half)) - np.log(n))
+
+
 def boundary_mask(u: np.ndarray, R: np.ndarray) -> np.ndarray:
     """Nodes within omega = 1e-12 R of a face of [-R, R]^r (Section 4.2, step 3)."""
     uu = np.abs(u.astype(np.float64))
     return np.any(uu >= R[None, :] - 1e-12 * R[None, :], axis=1)
 
 
-def prepare(p: Problem, u: np.ndarray, centre: np.ndarray) -> Prepared:
+def prepare(p: Problem, u: np.ndarray, centre: np.ndarray, half: np.ndarray | None = None) -> Prepared:
     x = centre[None, :].astype(np.float64) + u.astype(np.float64)
     return Prepared(x=x, f=mdl.drift(p.model, x, p.model_a),
                     divf=mdl.divergence(p.model, x, p.model_a),
-                    mask=boundary_mask(u, p.R))
+                    mask=boundary_mask(u, p.R if half is None else half))
 
 
 def log_sum_exp(a: np.ndarray) -> float:
@@ -101,9 +111,10 @@ def prior_logw(p: Problem, x: np.ndarray) -> np.ndarray:
 
 
 def kernel_lse(p: Problem, prep: Prepared, logw: np.ndarray, t0: int = 0, t1: int | None = None,
-               n_threads: int = 0) -> np.ndarray:
+               n_threads: int = 0, half: np.ndarray | None = None) -> np.ndarray:
     """L_j(i) for targets t0 <= i < t1 and every scale j: [(t1 - t0)][N]."""
     t1 = p.n if t1 is None else t1
+    lwq = p.log_wq if half is None else log_wq(half, p.n)
     L = _lib.lib()
     x = np.ascontiguousarray(prep.x, dtype=np.float64)
     f = np.ascontiguousarray(prep.f, dtype=np.float64)
@@ -114,7 +125,7 @@ def kernel_lse(p: Problem, prep: Prepared, logw: np.ndarray, t0: int = 0, t1: in
     out = np.empty((t1 - t0, p.n_scales), dtype=np.float64)
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     L.yyo_kernel_lse(p.n, p.r, ptr(x), ptr(f), ptr(dv), ptr(lw), ptr(mk), p.n_scales,
-                     ptr(tau), p.log_wq, t0, t1, ptr(out), n_threads)
+                     ptr(tau), lwq, t0, t1, ptr(out), n_threads)
     return out
 
 
@@ -151,9 +162,9 @@ def combine(p: Problem, Lj: np.ndarray, logw_t: np.ndarray, mask_t: np.ndarray) 
 
 
 def predict(p: Problem, prep: Prepared, logw: np.ndarray, t0: int = 0, t1: int | None = None,
-            n_threads: int = 0) -> tuple[np.ndarray, int]:
+            n_threads: int = 0, half: np.ndarray | None = None) -> tuple[np.ndarray, int]:
     t1 = p.n if t1 is None else t1
-    Lj = kernel_lse(p, prep, logw, t0, t1, n_threads)
+    Lj = kernel_lse(p, prep, logw, t0, t1, n_threads, half)
     return combine(p, Lj, logw[t0:t1], prep.mask[t0:t1])
 
 
@@ -178,12 +189,14 @@ def restart_due(p: Problem, ess: float, k: int) -> bool:
     return bool(by_ess or by_interval)
 
 
-def restart_logw(p: Problem, x: np.ndarray, mean: np.ndarray, var: np.ndarray) -> np.ndarray:
-    """Fresh normalised log-weights after a restart centred at the estimate."""
+def restart_logw(p: Problem, x: np.ndarray, centre: np.ndarray, var: np.ndarray,
+                 half: np.ndarray | None = None) -> np.ndarray:
+    """Fresh normalised log-weights after a restart: N(centre, diag(max(var, (R/4)^2)))."""
     if p.restart_init == "uniform":
         return np.full(p.n, -np.log(p.n))
-    v = np.maximum(var, (p.R / 4.0) ** 2)
-    d = x - mean[None, :]
+    R = p.R if half is None else half
+    v = np.maximum(var, (R / 4.0) ** 2)
+    d = x - centre[None, :]
     lw = -0.5 * np.sum(d * d / v[None, :], axis=1) - 0.5 * np.sum(np.log(2 * np.pi * v))
     return normalise(lw)[1]
 
@@ -195,6 +208,8 @@ class State:
     logw: np.ndarray       # [n] float64, normalised
     lognorm: float = 0.0   # Z
     k: int = 0
+    half: np.ndarray | None = None   # [r] current half-widths (None: the problem's R)
+    y: np.ndarray | None = None      # [n][r] Sobol integers of the nodes (learned rule)
 
 
 @dataclass
@@ -206,6 +221,7 @@ class StepRecord:
     lognorm: float
     restarted: bool
     clamps: int
+    learned: bool = False
     logw_pred: np.ndarray = field(repr=False, default=None)
     logw_hat: np.ndarray = field(repr=False, default=None)
 
@@ -220,8 +236,9 @@ def init_state(p: Problem, u: np.ndarray, centre: np.ndarray) -> State:
 
 def step(p: Problem, st: State, dy: np.ndarray, n_threads: int = 0,
          keep_logw: bool = False) -> tuple[StepRecord, State]:
-    prep = prepare(p, st.u, st.centre)
-    lw_pred, clamps = predict(p, prep, st.logw, n_threads=n_threads)
+    half = p.R if st.half is None else st.half
+    prep = prepare(p, st.u, st.centre, half)
+    lw_pred, clamps = predict(p, prep, st.logw, n_threads=n_threads, half=half)
     lw_upd = lw_pred + log_likelihood(p, prep.x, dy)
     lam, lw_hat = normalise(lw_upd)
     if np.isinf(lam):
@@ -232,14 +249,21 @@ def step(p: Problem, st: State, dy: np.ndarray, n_threads: int = 0,
     rec = StepRecord(mean=mean, var=var, ess=ess, lam=lam, lognorm=Z, restarted=False,
                      clamps=clamps, logw_pred=lw_pred if keep_logw else None,
                      logw_hat=lw_hat if keep_logw else None)
-    new = State(u=st.u, centre=st.centre, logw=lw_hat, lognorm=Z, k=k)
+    new = State(u=st.u, centre=st.centre, logw=lw_hat, lognorm=Z, k=k, half=st.half, y=st.y)
     if restart_due(p, ess, k):
         rec.restarted = True
-        centre = mean.copy()
-        prep2 = prepare(p, st.u, centre)
-        lw0 = restart_logw(p, prep2.x, mean, var)
+        centre, new_half, u = mean.copy(), half, st.u
+        if p.restart_rule == "learned":
+            from . import mlp, sobol
+            centre, new_half, ok = mlp.proposal(p.mlp_params, mean, var, dy, p.dt, p.R)
+            rec.learned = ok
+            if ok:
+                u = sobol.to_box(st.y, new_half)
+        prep2 = prepare(p, u, centre, new_half)
+        lw0 = restart_logw(p, prep2.x, centre, var, new_half)
         lw0[prep2.mask] = -np.inf
-        new = State(u=st.u, centre=centre, logw=lw0, lognorm=Z, k=k)
+        new = State(u=u, centre=centre, logw=lw0, lognorm=Z, k=k, half=np.array(new_half, dtype=np.float64),
+                    y=st.y)
     return rec, new
 
 

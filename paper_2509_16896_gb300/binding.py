@@ -24,6 +24,7 @@ STATUS_NAMES = {0: "YY_OK", 1: "YY_ERR_ARG", 2: "YY_ERR_CUDA", 3: "YY_ERR_WORKSP
 MODELS = {"cubic": 0, "linear": 1}
 PRECISIONS = {"f64": 0, "f32": 1, "bf16": 2}
 RESTART_INIT = {"gauss": 0, "uniform": 1}
+RESTART_RULE = {"plain": 0, "learned": 1}
 RESTART_AUTO, RESTART_FORCE, RESTART_NEVER = 0, 1, 2
 SOBOL_POLY_WORDS = 16
 SOBOL_SCRAMBLE_WORDS = 33
@@ -38,7 +39,9 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_batch_run_steps", "yy_batch_predict", "yy_batch_graph_capture", "yy_batch_graph_launch",
            "yy_batch_set_schedule", "yy_batch_get_schedule", "yy_batch_autotune",
            "yy_batch_launch_count", "yy_batch_graph_kernel_count", "yy_get_counters",
-           "yy_batch_get_routing")
+           "yy_batch_get_routing", "yy_get_box", "yy_set_restart_mlp", "yy_mlp_param_count",
+           "yy_mlp_workspace_bytes", "yy_mlp_create", "yy_mlp_destroy", "yy_mlp_set_params",
+           "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train")
 
 
 class YYError(RuntimeError):
@@ -53,7 +56,8 @@ class YYConfig(ctypes.Structure):
                 ("model", ctypes.c_int32), ("model_a", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("restart_interval", ctypes.c_int32),
                 ("ess_frac", ctypes.c_double), ("restart_init", ctypes.c_int32),
-                ("prior_mean", ctypes.c_double), ("prior_var", ctypes.c_double)]
+                ("prior_mean", ctypes.c_double), ("prior_var", ctypes.c_double),
+                ("restart_rule", ctypes.c_int32)]
 
 
 def _declare(L: ctypes.CDLL) -> None:
@@ -95,6 +99,17 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_batch_graph_kernel_count": (I64, [P]),
         "yy_get_counters": (I32, [P, P, P]),
         "yy_batch_get_routing": (I32, [P, P]),
+        "yy_get_box": (I32, [P, P, P]),
+        "yy_set_restart_mlp": (I32, [P, P]),
+        "yy_mlp_param_count": (I64, [I32, I32]),
+        "yy_mlp_workspace_bytes": (S, [I32, I32, I32]),
+        "yy_mlp_create": (I32, [I32, I32, I32, P, S, P, P]),
+        "yy_mlp_destroy": (I32, [P]),
+        "yy_mlp_set_params": (I32, [P, P]),
+        "yy_mlp_get_params": (I32, [P, P]),
+        "yy_mlp_forward": (I32, [P, P, I32, P]),
+        "yy_mlp_loss_grad": (I32, [P, P, P, I32, D, P, P]),
+        "yy_mlp_train": (I32, [P, P, P, I64, D, I32, I32, ctypes.c_float, ctypes.c_uint64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -134,19 +149,19 @@ def _check(fn: str, code: int) -> None:
 def make_config(model: str, r: int, n: int, dt: float, R: float, n_scales: int,
                 precision: str, restart_interval: int = 0, ess_frac: float = 0.0,
                 model_a: float = -0.5, restart_init: str = "gauss", prior_mean: float = 0.0,
-                prior_var: float = 1.0) -> YYConfig:
+                prior_var: float = 1.0, restart_rule: str = "plain") -> YYConfig:
     return YYConfig(r=r, m=r, n=n, dt=dt, R=R, n_scales=n_scales, model=MODELS[model],
                     model_a=model_a, precision=PRECISIONS[precision],
                     restart_interval=restart_interval, ess_frac=ess_frac,
                     restart_init=RESTART_INIT[restart_init], prior_mean=prior_mean,
-                    prior_var=prior_var)
+                    prior_var=prior_var, restart_rule=RESTART_RULE[restart_rule])
 
 
 def config_from_workload(w, precision: str | None = None, **over) -> YYConfig:
     kw = dict(model=w.model, r=w.r, n=w.n, dt=w.dt, R=w.R, n_scales=w.n_scales,
               precision=precision or w.precision, restart_interval=w.restart_interval,
               ess_frac=w.ess_frac, model_a=w.model_a, prior_mean=w.prior_mean,
-              prior_var=w.prior_var)
+              prior_var=w.prior_var, restart_rule=w.restart_rule)
     kw.update(over)
     return make_config(**kw)
 
@@ -244,6 +259,16 @@ class Filter:
         lw = np.ascontiguousarray(logw, dtype=np.float64 if self.fp64 else np.float32)
         _check("yy_set_state", self.lib.yy_set_state(self.h, _ptr(cen), _ptr(lw), lognorm, step))
 
+    def get_box(self):
+        cen = np.empty(self.r)
+        half = np.empty(self.r)
+        _check("yy_get_box", self.lib.yy_get_box(self.h, _ptr(cen), _ptr(half)))
+        return cen, half
+
+    def set_restart_mlp(self, net) -> None:
+        _check("yy_set_restart_mlp", self.lib.yy_set_restart_mlp(self.h, None if net is None else net.h))
+        self._mlp = net   # keep the network alive while attached
+
     def get_state(self):
         cen = np.empty(self.r)
         z = ctypes.c_double()
@@ -283,6 +308,87 @@ class Filter:
 
     def graph_kernels(self) -> int:
         return int(self.lib.yy_graph_kernel_count(self.h))
+
+
+class MLP:
+    """Restart-proposal network (include/yy.h, network section)."""
+
+    def __init__(self, r: int, hidden: int = 256, max_batch: int = 256, device: str = "cuda:0", stream=None):
+        import torch
+        self.torch = torch
+        self.lib = load()
+        self.r, self.hidden, self.max_batch = r, hidden, max_batch
+        self.device = torch.device(device)
+        self.n_params = int(self.lib.yy_mlp_param_count(r, hidden))
+        nbytes = int(self.lib.yy_mlp_workspace_bytes(r, hidden, max_batch))
+        if nbytes == 0:
+            raise YYError("yy_mlp_workspace_bytes", 1)
+        self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        ptr = (self.ws.data_ptr() + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check("yy_mlp_create", self.lib.yy_mlp_create(r, hidden, max_batch, ctypes.c_void_p(ptr), nbytes,
+                                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.yy_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, flat: np.ndarray) -> None:
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.n_params
+        _check("yy_mlp_set_params", self.lib.yy_mlp_set_params(self.h, _ptr(flat)))
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check("yy_mlp_get_params", self.lib.yy_mlp_get_params(self.h, _ptr(out)))
+        return out
+
+    def forward(self, x_dev):
+        B = x_dev.shape[0]
+        out = self.torch.empty((B, 2 * self.r), dtype=self.torch.float32, device=self.device)
+        _check("yy_mlp_forward", self.lib.yy_mlp_forward(self.h, ctypes.c_void_p(x_dev.data_ptr()), B,
+                                                         ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def loss_grad(self, x_dev, t_dev, R: float):
+        loss = ctypes.c_float()
+        g = np.empty(self.n_params, dtype=np.float32)
+        _check("yy_mlp_loss_grad", self.lib.yy_mlp_loss_grad(
+            self.h, ctypes.c_void_p(x_dev.data_ptr()), ctypes.c_void_p(t_dev.data_ptr()), x_dev.shape[0], R,
+            ctypes.byref(loss), _ptr(g)))
+        return loss.value, g
+
+    def train(self, x_dev, t_dev, R: float, epochs: int, batch: int, lr: float, seed: int = 0) -> float:
+        loss = ctypes.c_float()
+        _check("yy_mlp_train", self.lib.yy_mlp_train(
+            self.h, ctypes.c_void_p(x_dev.data_ptr()), ctypes.c_void_p(t_dev.data_ptr()), x_dev.shape[0], R,
+            epochs, batch, ctypes.c_float(lr), ctypes.c_uint64(seed), ctypes.byref(loss)))
+        return loss.value
+
+
+def pack_mlp_params(p: dict) -> np.ndarray:
+    """Packs {W1, b1, W2, b2, W3, b3} in the layout of yy_mlp_set_params."""
+    return np.concatenate([p[k].ravel() for k in ("W1", "b1", "W2", "b2", "W3", "b3")]).astype(np.float32)
+
+
+def unpack_mlp_params(flat: np.ndarray, r: int, hidden: int) -> dict:
+    shapes = [("W1", (hidden, 3 * r)), ("b1", (hidden,)), ("W2", (hidden, hidden)), ("b2", (hidden,)),
+              ("W3", (2 * r, hidden)), ("b3", (2 * r,))]
+    out, o = {}, 0
+    for k, shp in shapes:
+        n = int(np.prod(shp))
+        out[k] = np.asarray(flat[o:o + n], dtype=np.float64).reshape(shp)
+        o += n
+    return out
 
 
 class _BorrowedFilter(Filter):

@@ -24,6 +24,7 @@ bool cfg_valid(const yy_config* c) {
     if (c->precision < YY_PREC_FP64 || c->precision > YY_PREC_BF16) return false;
     if (c->restart_init != YY_RESTART_INIT_GAUSS && c->restart_init != YY_RESTART_INIT_UNIFORM) return false;
     if (!(c->ess_frac >= 0.0) || c->ess_frac > 1.0) return false;
+    if (c->restart_rule != YY_RESTART_PLAIN && c->restart_rule != YY_RESTART_LEARNED) return false;
     return true;
 }
 
@@ -65,6 +66,9 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.obs_g = cv.take<T>(r_pad * sizeof(T));
     b.obs_c = cv.take<T>(r_pad * sizeof(T));
     b.dimc = cv.take<T>(3 * (size_t)r_pad * sizeof(T));
+    b.next_centre = cv.take<double>(r_pad * sizeof(double));
+    b.next_half = cv.take<double>(r_pad * sizeof(double));
+    b.dy_last = cv.take<double>(r_pad * sizeof(double));
     b.part = cv.take<double>(part_bytes(r_pad));
     b.stats = cv.take<DevStats>(sizeof(DevStats));
     if (c->precision == YY_PREC_BF16) {
@@ -152,6 +156,8 @@ __global__ void k_set_stats(DevStats* st, double lognorm, long long step) {
     st->step = step;
 }
 
+__global__ void k_init_cref(DevStats* st, double c_ref) { st->c_ref = c_ref; }
+
 template <typename T>
 yy_status do_init_nodes(yy_filter* f, Bufs<T>& b, Consts<T>& k, const uint32_t* h_poly,
                         const uint32_t* h_scr, const double* h_center, const double* h_half) {
@@ -190,7 +196,8 @@ yy_status do_init_nodes(yy_filter* f, Bufs<T>& b, Consts<T>& k, const uint32_t* 
     int l = 0;
     if ((e = launch_normalise_only<T>(k, b, s, &l)) != cudaSuccess) return YY_ERR_CUDA;
     k_set_stats<<<1, 1, 0, s>>>(b.stats, 0.0, 0);
-    f->launches += 5 + l;
+    k_init_cref<<<1, 1, 0, s>>>(b.stats, f->c_ref);
+    f->launches += 6 + l;
     f->nodes_ready = true;
     f->predicted = false;
     return cuda_status(cudaGetLastError());
@@ -330,9 +337,10 @@ yy_status yy_restart(yy_filter* f, int32_t mode, int32_t* h_did_restart) {
     if (mode != YY_RESTART_AUTO && mode != YY_RESTART_FORCE && mode != YY_RESTART_NEVER) return YY_ERR_ARG;
     if (!f->nodes_ready || f->predicted) return YY_ERR_STATE;
     int l = 0;
+    yy_mlp* net = (f->cfg.restart_rule == YY_RESTART_LEARNED) ? f->mlp : nullptr;
     cudaError_t e = f->fp64
-        ? launch_restart<double>(f->kd, f->bd, mode, f->cfg.restart_init, f->stream, &l)
-        : launch_restart<float>(f->kf, f->bf, mode, f->cfg.restart_init, f->stream, &l);
+        ? launch_restart<double>(f->kd, f->bd, mode, f->cfg.restart_init, f->cfg.R, net, f->stream, &l)
+        : launch_restart<float>(f->kf, f->bf, mode, f->cfg.restart_init, f->cfg.R, net, f->stream, &l);
     f->launches += l;
     if (e != cudaSuccess) return YY_ERR_CUDA;
     if (h_did_restart) {
@@ -427,9 +435,12 @@ yy_status yy_get_log_weights(yy_filter* f, void* h_logw, double* h_offset) {
     const size_t es = f->fp64 ? sizeof(double) : sizeof(float);
     const void* src = f->predicted ? (f->fp64 ? (void*)f->bd.logw_pred : (void*)f->bf.logw_pred)
                                    : (f->fp64 ? (void*)f->bd.logw : (void*)f->bf.logw);
+    DevStats* st = f->fp64 ? f->bd.stats : f->bf.stats;
+    double cref = 0.0;
     cudaError_t e = cudaMemcpyAsync(h_logw, src, es * (size_t)f->cfg.n, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cref, &st->c_ref, sizeof(double), cudaMemcpyDeviceToHost, f->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
-    if (h_offset) *h_offset = f->predicted ? f->c_ref : 0.0;
+    if (h_offset) *h_offset = f->predicted ? cref : 0.0;
     return cuda_status(e);
 }
 
@@ -452,6 +463,26 @@ yy_status yy_set_state(yy_filter* f, const double* h_center, const void* h_logw,
                 : launch_prep<float>(f->kf, f->bf, false, false, 0.0, 1.0, f->stream);
     f->launches += 3;
     f->predicted = false;
+    return cuda_status(e);
+}
+
+yy_status yy_set_restart_mlp(yy_filter* f, yy_mlp* net) {
+    if (!f) return YY_ERR_ARG;
+    if (net && f->fp64) return YY_ERR_UNSUPPORTED;
+    f->mlp = net;
+    return YY_OK;
+}
+
+yy_status yy_get_box(yy_filter* f, double* h_center, double* h_halfwidth) {
+    if (!f) return YY_ERR_ARG;
+    if (!f->nodes_ready) return YY_ERR_STATE;
+    const double* cen = f->fp64 ? f->bd.centre : f->bf.centre;
+    const double* half = f->fp64 ? f->bd.halfwidth : f->bf.halfwidth;
+    cudaError_t e = cudaSuccess;
+    if (h_center) e = cudaMemcpyAsync(h_center, cen, sizeof(double) * f->cfg.r, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess && h_halfwidth)
+        e = cudaMemcpyAsync(h_halfwidth, half, sizeof(double) * f->cfg.r, cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
     return cuda_status(e);
 }
 

@@ -19,7 +19,7 @@ template <> __device__ __forceinline__ double cmb_log<double>(double x) { return
 
 template <typename T, int N>
 __device__ __forceinline__ T combine_scales(const Consts<T>& k, const T (&mx)[N], const T (&sm)[N],
-                                            T divf, T logw_i, unsigned int* clamps) {
+                                            T divf, T logw_i, double c_ref, unsigned int* clamps) {
     T term[N + 1], sg[N + 1];
     T M = T(-INFINITY);
 #pragma unroll
@@ -33,7 +33,7 @@ __device__ __forceinline__ T combine_scales(const Consts<T>& k, const T (&mx)[N]
     sg[N] = k.sign_c[N];
     term[N] = (sg[N] == T(0) || logw_i == T(-INFINITY))
                   ? T(-INFINITY)
-                  : k.logabs_c[N] + (T)((double)logw_i - k.c_ref);
+                  : k.logabs_c[N] + (T)((double)logw_i - c_ref);
     M = fmax(M, term[N]);
     if (M == T(-INFINITY)) return T(-INFINITY);
     T S = T(0);

@@ -24,4 +24,5 @@ struct yy_filter {
     cudaGraph_t graph;
     cudaGraphExec_t gexec;
     long long graph_kernels;
+    struct yy_mlp* mlp;   // restart-proposal network for YY_RESTART_LEARNED (not owned)
 };

@@ -8,6 +8,8 @@
 
 #include "yy.h"
 
+struct yy_mlp;
+
 namespace yy {
 
 constexpr int kMaxScales = YY_MAX_SCALES;
@@ -36,6 +38,8 @@ struct DevStats {
     unsigned int clamps; // non-positive combinations in the last predict
     unsigned long long candidates;  // exact pair evaluations in the last BF16 predict
     int last_restarted;  // 1 if the last yy_restart call re-centred the box
+    int scale_changed;   // 1 while a restart re-maps the nodes to new half-widths
+    double c_ref;        // offset of the predicted log-weights (moves with the box volume)
 };
 
 // Constants of one filter handed to kernels by value.
@@ -76,6 +80,9 @@ struct Bufs {
     T* obs_g;             // [r_pad] dy - dt h(c)
     T* obs_c;             // [r_pad] centre in T
     T* dimc;              // [3][r_pad] per-dimension constants of the preparation pass
+    double* next_centre;  // [r_pad] box of the restart in progress
+    double* next_half;    // [r_pad]
+    double* dy_last;      // [r_pad] observation increment of the last update
     double* part;         // reduction partials
     DevStats* stats;
     // BF16 path scratch
@@ -123,14 +130,20 @@ cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy
                           int restart_interval, double ess_frac, cudaStream_t s, int* launches);
 
 template <typename T>
-cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind,
-                           cudaStream_t s, int* launches);
+cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind, double base_R,
+                           struct ::yy_mlp* net, cudaStream_t s, int* launches);
 
 template <typename T>
 cudaError_t launch_normalise_only(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s,
                                   int* launches);
 
 size_t part_bytes(int r_pad);
+
+cudaError_t launch_sobol_points_restart(const uint32_t* dirs, int r, int r_pad, long long n, float* u,
+                                        const double* next_half, const DevStats* st, cudaStream_t s);
+cudaError_t mlp_propose(struct ::yy_mlp* net, int r, const double* mean, const double* var, const double* dy,
+                        double dt, const int* flag, cudaStream_t s, int* launches);
+const float* mlp_output(const struct ::yy_mlp* net);
 
 // Batched launches: one launch covers every trajectory (grid.y = trajectory).
 template <typename T>

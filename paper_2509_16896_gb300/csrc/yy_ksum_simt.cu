@@ -147,7 +147,7 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
         const long long i = i0 + ty * TM + a;
         if (i >= k.n) continue;
         if (b.mask[i]) { b.logw_pred[i] = T(-INFINITY); continue; }
-        b.logw_pred[i] = combine_scales<T, N>(k, mx[a], sm[a], b.divf[i], b.logw[i], &b.stats->clamps);
+        b.logw_pred[i] = combine_scales<T, N>(k, mx[a], sm[a], b.divf[i], b.logw[i], b.stats->c_ref, &b.stats->clamps);
     }
 }
 

@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 if (lane == 0) mbar_arrive(&tempty[acc]);
             }
             if (ok && in_range)
-                b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li, &b.stats->clamps)
+                b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li, b.stats->c_ref, &b.stats->clamps)
                                       : -INFINITY;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);

@@ -38,7 +38,8 @@ __device__ __forceinline__ T warp_sum(T v) {
 template <typename T>
 __device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind) {
     if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
-    const double* cen = (mode == kPrepRestart) ? b.mean : b.centre;
+    const double* cen = (mode == kPrepRestart) ? b.next_centre : b.centre;
+    const double* half = (mode == kPrepRestart) ? b.next_half : b.halfwidth;
     for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
         T hi = T(0), lo = T(0), iv = T(0);
         if (d < k.r) {
@@ -46,7 +47,7 @@ __device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>
             hi = (T)c;
             lo = (T)(c - (double)hi);
             if (mode == kPrepRestart && init_kind == YY_RESTART_INIT_GAUSS) {
-                const double R4 = 0.25 * b.halfwidth[d];
+                const double R4 = 0.25 * half[d];
                 iv = (T)(0.5 / fmax(b.var[d], R4 * R4));
             }
         }
@@ -60,6 +61,9 @@ template <typename T>
 __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, int mode, int first,
                                           double prior_mean, double prior_var, int bid, int nblk) {
     if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
+    // a restart that re-mapped the nodes to new half-widths also redoes the node-only
+    // quantities (|u|^2, mask against the new faces, bf16 copy)
+    if (mode == kPrepRestart && b.stats->scale_changed) first = 1;
     __shared__ T s_hi[YY_MAX_DIM], s_lo[YY_MAX_DIM], s_iv[YY_MAX_DIM];
     for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
         s_hi[d] = b.dimc[d];
@@ -70,7 +74,8 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
     const int lane = threadIdx.x & 31;
     const long long warp = (bid * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)nblk * blockDim.x) >> 5;
-    const double* cen = (mode == kPrepRestart) ? b.mean : b.centre;
+    const double* cen = (mode == kPrepRestart) ? b.next_centre : b.centre;
+    const double* halfw = (mode == kPrepRestart) ? b.next_half : b.halfwidth;
     for (long long i = warp; i < k.n_pad; i += nwarps) {
         const float* ui = b.u + (size_t)i * k.r_pad;
         T* fi = b.f + (size_t)i * k.r_pad;
@@ -120,7 +125,7 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
                         if (mode == kPrepRestart) lw -= (T)uf * (T)uf * s_iv[d];
                         if (first) {
                             nu += (T)uf * (T)uf;
-                            const double R = b.halfwidth[d];
+                            const double R = halfw[d];
                             if (fabs((double)uf) >= R - 1e-12 * R) on_face = 1;
                         }
                         if (mode == kPrepInit) {

@@ -70,6 +70,39 @@ __global__ void k_sobol_points(const uint32_t* __restrict__ dirs, int r, int r_p
     }
 }
 
+// Re-mapping of the reference nodes to new half-widths during a restart (no-op unless the
+// restart flag and the scale-changed flag are set).
+__global__ void k_sobol_points_restart(const uint32_t* __restrict__ dirs, int r, int r_pad, long long n,
+                                       float* __restrict__ u, const double* __restrict__ half,
+                                       const DevStats* __restrict__ st) {
+    if (st->restart_flag == 0 || st->scale_changed == 0) return;
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= r) return;
+    const uint32_t* V = dirs + (size_t)d * 33;
+    const double R = half[d];
+    for (long long i = blockIdx.y * (long long)blockDim.y + threadIdx.y; i < n; i += (long long)gridDim.y * blockDim.y) {
+        const unsigned long long idx = (unsigned long long)i;
+        const uint32_t g = (uint32_t)(idx ^ (idx >> 1));
+        uint32_t y = V[32];
+#pragma unroll 8
+        for (int b = 0; b < 32; ++b)
+            if ((g >> b) & 1u) y ^= V[b];
+        double t = __dadd_rn((double)y, 0.5);
+        t = __dmul_rn(t, 0x1p-31);
+        t = __dsub_rn(t, 1.0);
+        u[(size_t)i * r_pad + d] = __double2float_rn(__dmul_rn(R, t));
+    }
+}
+
+cudaError_t launch_sobol_points_restart(const uint32_t* dirs, int r, int r_pad, long long n, float* u,
+                                        const double* next_half, const DevStats* st, cudaStream_t s) {
+    dim3 block(64, 4);
+    long long gy = (n + 3) / 4;
+    if (gy > 65535) gy = 65535;
+    k_sobol_points_restart<<<dim3((r + 63) / 64, (unsigned)gy), block, 0, s>>>(dirs, r, r_pad, n, u, next_half, st);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_sobol_dirs(const uint32_t* params, uint32_t* dirs, int r, cudaStream_t s) {
     k_sobol_dirs<<<(r + 63) / 64, 64, 0, s>>>(params, dirs, r);

@@ -68,6 +68,7 @@ __device__ __forceinline__ void obs_prep_body(const Consts<T>& k, const Bufs<T>&
             const double c = b.centre[d];
             const double hc = (k.model == YY_MODEL_CUBIC) ? c * c * c : c;
             const double y = dy[d];
+            b.dy_last[d] = y;
             b.obs_g[d] = (T)(y - (double)k.dt * hc);
             b.obs_c[d] = (T)c;
             acc += hc * y - 0.5 * (double)k.dt * hc * hc;
@@ -321,7 +322,7 @@ __device__ __forceinline__ void finalize_scalars_body(const Consts<T>& k, const 
         st->wsq = Q;
         const double ess = (Q > 0.0) ? W * W / Q : 0.0;
         st->ess = ess;
-        const double lam = k.c_ref + st->lam_c + st->lam_rel;
+        const double lam = st->c_ref + st->lam_c + st->lam_rel;
         st->lam = lam;
         st->lognorm += lam;
         if (!isfinite(lam)) st->status |= kStatusNonFinite;
@@ -385,10 +386,67 @@ __device__ __forceinline__ void restart_begin_body(DevStats* st, int mode) {
     st->last_restarted = 0;
 }
 
+// Box of the restart in progress.  Plain rule: centre x_hat, half-widths unchanged.
+// Learned rule (out = network output [delta; lambda], or NULL): centre x_hat + delta,
+// half-widths base_R exp(lambda), accepted only if every value is finite and every
+// half-width lies in [base_R / 8, 8 base_R]; the offset c_ref follows the box volume.
+template <typename T>
+__device__ __forceinline__ void restart_box_body(const Consts<T>& k, const Bufs<T>& b, const float* out,
+                                                 double base_R) {
+    __shared__ int s_ok;
+    if (b.stats->restart_flag == 0) return;
+    if (threadIdx.x == 0) s_ok = (out != nullptr) ? 1 : 0;
+    __syncthreads();
+    if (out) {
+        for (int d = threadIdx.x; d < k.r; d += blockDim.x) {
+            const double delta = (double)out[d], lam = (double)out[k.r + d];
+            const double h = base_R * exp(lam);
+            if (!isfinite(delta) || !isfinite(h) || h < base_R / 8.0 || h > 8.0 * base_R) atomicAnd(&s_ok, 0);
+        }
+        __syncthreads();
+    }
+    const bool learned = s_ok != 0;
+    __shared__ double red[32];
+    double dl = 0.0;
+    int changed = 0;
+    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
+        double c = 0.0, h = b.halfwidth[d];
+        if (d < k.r) {
+            c = b.mean[d];
+            if (learned) {
+                c += (double)out[d];
+                h = base_R * exp((double)out[k.r + d]);
+                dl += log(h / b.halfwidth[d]);
+                changed |= (h != b.halfwidth[d]);
+            }
+        }
+        b.next_centre[d] = c;
+        b.next_half[d] = h;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) dl += __shfl_xor_sync(0xffffffffu, dl, o);
+    changed = __any_sync(0xffffffffu, changed);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dl;
+    __shared__ int s_changed;
+    if (threadIdx.x == 0) s_changed = 0;
+    __syncthreads();
+    if (changed && (threadIdx.x & 31) == 0) atomicOr(&s_changed, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+        b.stats->c_ref += tot;
+        b.stats->scale_changed = s_changed;
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void restart_commit_body(const Consts<T>& k, const Bufs<T>& b) {
     if (b.stats->restart_flag == 0) return;
-    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) b.centre[d] = (d < k.r) ? b.mean[d] : 0.0;
+    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
+        b.centre[d] = b.next_centre[d];
+        b.halfwidth[d] = b.next_half[d];
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         b.stats->restarts += 1;
@@ -446,6 +504,10 @@ template <typename T>
 __global__ void k_restart_begin(DevStats* st, int mode) { restart_begin_body(st, mode); }
 template <typename T>
 __global__ void k_restart_commit(Consts<T> k, Bufs<T> b) { restart_commit_body<T>(k, b); }
+template <typename T>
+__global__ void k_restart_box(Consts<T> k, Bufs<T> b, const float* out, double base_R) {
+    restart_box_body<T>(k, b, out, base_R);
+}
 template <typename T>
 __global__ void k_record(Consts<T> k, Bufs<T> b, double* __restrict__ row) { record_body<T>(k, b, row); }
 
@@ -508,6 +570,11 @@ __global__ void kb_subtract(const Traj<T>* __restrict__ tr) {
     subtract_body<T>(t.k, t.b, 1, blockIdx.x, gridDim.x);
 }
 template <typename T>
+__global__ void kb_restart_box(const Traj<T>* __restrict__ tr) {
+    const Traj<T>& t = tr[blockIdx.y];
+    restart_box_body<T>(t.k, t.b, nullptr, 0.0);
+}
+template <typename T>
 __global__ void kb_restart_commit(const Traj<T>* __restrict__ tr) {
     const Traj<T>& t = tr[blockIdx.y];
     restart_commit_body<T>(t.k, t.b);
@@ -554,19 +621,33 @@ cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, boo
 template <typename T>
 cudaError_t launch_prep_restart_batch(const Traj<T>* d_traj, int B, long long n_pad_max, cudaStream_t s);
 
+// Restart sequence (every kernel is a no-op unless the restart flag is set): begin, the
+// learned proposal (network forward pass, if a network is attached), the box, re-mapping of
+// the nodes when the half-widths change, preparation at the new box, weights, commit.
 template <typename T>
-cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind,
-                           cudaStream_t s, int* launches) {
+cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind, double base_R,
+                           struct ::yy_mlp* net, cudaStream_t s, int* launches) {
     if (mode == YY_RESTART_NEVER) return cudaSuccess;
     const int nb = kNumPartBlocks;
+    int l = 0;
     k_restart_begin<T><<<1, 32, 0, s>>>(b.stats, mode);
-    cudaError_t e = launch_prep_mode<T>(k, b, 2 /*restart*/, false, 0.0, 1.0, init_kind, s);
+    const float* out = nullptr;
+    if (net) {
+        cudaError_t e = mlp_propose(net, k.r, b.mean, b.var, b.dy_last, (double)k.dt, &b.stats->restart_flag, s, &l);
+        if (e != cudaSuccess) return e;
+        out = mlp_output(net);
+    }
+    k_restart_box<T><<<1, 256, 0, s>>>(k, b, out, base_R);
+    cudaError_t e = cudaSuccess;
+    if (net) e = launch_sobol_points_restart(b.dirs, k.r, k.r_pad, k.n, b.u, b.next_half, b.stats, s);
+    if (e != cudaSuccess) return e;
+    e = launch_prep_mode<T>(k, b, 2 /*restart*/, false, 0.0, 1.0, init_kind, s);
     if (e != cudaSuccess) return e;
     k_lse_partials<T><<<nb, 256, 0, s>>>(k, b, 1);
     k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 1);
     k_subtract<T><<<nb, 256, 0, s>>>(k, b, 1);
     k_restart_commit<T><<<1, 256, 0, s>>>(k, b);
-    if (launches) *launches += 7;
+    if (launches) *launches += 8 + l + (net ? 1 : 0);
     return cudaGetLastError();
 }
 
@@ -590,13 +671,14 @@ cudaError_t launch_restart_batch(const Traj<T>* d_traj, int B, int r_max, long l
     (void)r_max;
     const dim3 one(1, B), many(nbu, B);
     kb_restart_begin<T><<<one, 32, 0, s>>>(d_traj);
+    kb_restart_box<T><<<one, 256, 0, s>>>(d_traj);
     cudaError_t e = launch_prep_restart_batch<T>(d_traj, B, n_pad_max, s);
     if (e != cudaSuccess) return e;
     kb_lse_partials<T><<<many, 256, 0, s>>>(d_traj);
     kb_lse_merge<T><<<one, 256, 0, s>>>(d_traj, nbu, 1);
     kb_subtract<T><<<many, 256, 0, s>>>(d_traj);
     kb_restart_commit<T><<<one, 256, 0, s>>>(d_traj);
-    if (launches) *launches += 7;
+    if (launches) *launches += 8;
     return cudaGetLastError();
 }
 
@@ -619,7 +701,8 @@ cudaError_t launch_reset_batch(const Traj<T>* d_traj, int B, cudaStream_t s, int
     template cudaError_t launch_update<T>(const Consts<T>&, const Bufs<T>&, const double*, int, double, \
                                           cudaStream_t, int*);                                          \
     template cudaError_t launch_normalise_only<T>(const Consts<T>&, const Bufs<T>&, cudaStream_t, int*); \
-    template cudaError_t launch_restart<T>(const Consts<T>&, const Bufs<T>&, int, int, cudaStream_t, int*); \
+    template cudaError_t launch_restart<T>(const Consts<T>&, const Bufs<T>&, int, int, double, struct ::yy_mlp*, \
+                                           cudaStream_t, int*);                                          \
     template cudaError_t launch_update_batch<T>(const Traj<T>*, int, int, const double*, int, cudaStream_t, \
                                                 int*);                                                  \
     template cudaError_t launch_restart_batch<T>(const Traj<T>*, int, int, long long, int, cudaStream_t,  \
