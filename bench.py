@@ -426,6 +426,42 @@ def run_batch(args):
     print(json.dumps(out), flush=True)
 
 
+def run_learned(args):
+    """Learned restart workload (r = 50, n = 8192, 500 steps, frequent ESS restarts): trains
+    the proposal network on plain-run restarts of 64 training trajectories (seeds 100..163)
+    and runs the held-out trajectory (seed 5) with both rules."""
+    import torch
+    from paper_2509_16896_gb300 import learned_restart as LR
+    rank, ws_, local, dist = _dist()
+    device = f"cuda:{local}"
+    torch.cuda.set_device(device)
+    w = WORKLOADS["cubic_r50_n8192"]
+    if args.steps:
+        w = w.with_(steps=max(args.steps, 10))
+    t0 = time.perf_counter()
+    X, T, plain_train = LR.collect_restarts(w, seeds=list(range(100, 164)), device=device)
+    t_collect = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    net, loss = LR.train_proposal(w.r, X, T, w.R, hidden=256, epochs=args.mlp_epochs, batch=256, lr=1e-3,
+                                  seed=7, device=device)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    LR.run_filter(w, 5, "plain", device=device)          # warm-up
+    rm_p, sps_p, rs_p = LR.run_filter(w, 5, "plain", device=device)
+    rm_l, sps_l, rs_l = LR.run_filter(w, 5, "learned", net=net, device=device)
+    out = {"metric": "RMSE and filter steps/s, learned vs plain restart", "value": round(sps_l, 3),
+           "unit": "filter steps/s", "n_gpus": 1, "steps": w.steps, "warmup": 1, "ms_per_step": round(1e3 / sps_l, 4),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
+           "data": "synthetic (seeded Euler-Maruyama cubic sensor, scrambled Sobol nodes)",
+           "config": {"workload": w.name, "r": w.r, "n": w.n, "steps": w.steps, "train_seeds": "100..163",
+                      "eval_seed": 5, "mlp": f"{3 * w.r}-256-256-{2 * w.r} BF16", "epochs": args.mlp_epochs},
+           "plain": {"rmse": rm_p, "steps_per_s": round(sps_p, 3), "restarts": rs_p},
+           "learned": {"rmse": rm_l, "steps_per_s": round(sps_l, 3), "restarts": rs_l, "train_loss": loss},
+           "training": {"rows": int(X.shape[0]), "collect_s": round(t_collect, 2), "train_s": round(t_train, 2),
+                        "plain_rmse_train_mean": float(np.mean(plain_train))}}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -436,6 +472,7 @@ def main():
     ap.add_argument("--impl", default="yy", choices=["yy", "reference"])
     ap.add_argument("--fp32-steps", type=int, default=10, help="steps of the plain FP32 comparator")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--mlp-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "yy":
@@ -444,6 +481,8 @@ def main():
         run_reference(args)
     elif args.workload == "batched_256":
         run_batch(args)
+    elif args.workload == "cubic_r50_n8192":
+        run_learned(args)
     else:
         run_yy(args)
 
