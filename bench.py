@@ -435,9 +435,7 @@ def run_learned(args):
     rank, ws_, local, dist = _dist()
     device = f"cuda:{local}"
     torch.cuda.set_device(device)
-    w = WORKLOADS["cubic_r50_n8192"]
-    if args.steps:
-        w = w.with_(steps=max(args.steps, 10))
+    w = WORKLOADS["cubic_r50_n8192"]   # 500 steps, as the workload defines
     t0 = time.perf_counter()
     X, T, plain_train = LR.collect_restarts(w, seeds=list(range(100, 164)), device=device)
     t_collect = time.perf_counter() - t0
