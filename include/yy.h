@@ -85,8 +85,8 @@ typedef enum { YY_RESTART_INIT_GAUSS = 0, YY_RESTART_INIT_UNIFORM = 1 } yy_resta
 /* Where a restart puts the new box.  PLAIN: centre x_hat, half-widths unchanged (Section
  * 5).  LEARNED: centre x_hat + delta and half-widths R exp(lambda) from the restart-proposal
  * network attached with yy_set_restart_mlp (a library addition, not in the paper); it falls
- * back to PLAIN when no network is attached, when an output is not finite, or when a
- * half-width leaves [R/8, 8R]. */
+ * back to PLAIN when no network is attached, when an output is not finite, when a
+ * half-width leaves [R/8, 8R], or when the box would not contain x_hat. */
 typedef enum { YY_RESTART_PLAIN = 0, YY_RESTART_LEARNED = 1 } yy_restart_rule;
 
 /* yy_restart modes: AUTO applies the device-side test computed by the last yy_update
@@ -196,7 +196,8 @@ YY_EXPORT yy_status yy_graph_launch(yy_filter* f);
 YY_EXPORT int64_t yy_graph_kernel_count(const yy_filter* f);
 
 /* ---- restart-proposal network (a library addition; the paper has no counterpart) -----
- * A perceptron z = [x_hat; sqrt(v_hat); dy/sqrt(dt)] (3r) -> H -> H (ReLU) -> [delta; lambda]
+ * A perceptron z = [x_hat; sqrt(v_hat); dy/sqrt(dt)] (3r, normalised, see
+ * yy_mlp_set_input_norm) -> H -> H (ReLU) -> [delta; lambda]
  * (2r), trained and run on the device with BF16 operands and FP32 accumulation.  Loss:
  * mean over rows and coordinates of (t - delta)^2 / (2 s^2) + log s, s = (R/3) exp(lambda),
  * where t = x_true - x_hat at restarts of a plain run.  Parameters are packed FP32:
@@ -213,6 +214,10 @@ YY_EXPORT yy_status yy_mlp_destroy(yy_mlp* net);
 /* Copies parameters in (and resets the Adam moments) / out; host float [param_count]. */
 YY_EXPORT yy_status yy_mlp_set_params(yy_mlp* net, const float* h_params);
 YY_EXPORT yy_status yy_mlp_get_params(yy_mlp* net, float* h_params);
+
+/* Input normalisation zn = clamp((z - mean) / std, -4, 4) applied before the first layer
+ * (host float [3r] each, std > 0); identity (mean 0, std 1) after yy_mlp_create. */
+YY_EXPORT yy_status yy_mlp_set_input_norm(yy_mlp* net, const float* h_mean, const float* h_std);
 
 /* Forward pass: d_x device float [B][3r] -> d_out device float [B][2r]. */
 YY_EXPORT yy_status yy_mlp_forward(yy_mlp* net, const float* d_x, int32_t B, float* d_out);

@@ -1,10 +1,12 @@
 """FP64 reference of the restart-proposal network (a library addition; the paper's
 restart, Section 5, re-centres the box at the estimate with a fixed half-width).
 
-Network: features z = [x_hat; sqrt(v_hat); dy / sqrt(dt)] in R^{3r} ->
-    h1 = relu(W1 z + b1),  h2 = relu(W2 h1 + b2),  o = W3 h2 + b3,  o = [delta; lambda] in R^{2r}.
-Proposed box: centre x_hat + delta, half-widths R exp(lambda) (falls back to the plain rule
-when not finite or outside [R/8, 8R]).
+Network: features z = [x_hat; sqrt(v_hat); dy / sqrt(dt)] in R^{3r}, normalised per
+feature and clamped, zn = clip((z - mu) / s, -4, 4) (mu, s from the training set), ->
+    h1 = relu(W1 zn + b1),  h2 = relu(W2 h1 + b2),  o = W3 h2 + b3,  o = [delta; lambda] in R^{2r}.
+Proposed box: centre x_hat + delta, half-widths R exp(lambda); it falls back to the plain
+rule when a value is not finite, a half-width leaves [R/8, 8R], or the box would not
+contain the current estimate (|delta_d| > R exp(lambda_d)).
 
 Training target: the true state's offset t = x_true - x_hat at each restart of a plain run.
 Loss (Gaussian negative log-likelihood with sigma = (R/3) exp(lambda), so that the box
@@ -29,10 +31,22 @@ def init_params(r: int, hidden: int, seed: int) -> dict:
         p[f"W{i}"] = rng.uniform(-lim, lim, size=(o, n_in))
         p[f"b{i}"] = np.zeros(o)
     p["W3"] *= 0.01   # start near the plain rule: delta ~ 0, lambda ~ 0
+    p["mu"] = np.zeros(3 * r)
+    p["s"] = np.ones(3 * r)
     return p
 
 
-def forward(p: dict, z: np.ndarray) -> tuple[np.ndarray, dict]:
+TRAINED = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def normalise(p: dict, z: np.ndarray) -> np.ndarray:
+    mu = p.get("mu", np.zeros(z.shape[-1]))
+    s = p.get("s", np.ones(z.shape[-1]))
+    return np.clip((z - mu) / s, -4.0, 4.0)
+
+
+def forward(p: dict, z_raw: np.ndarray) -> tuple[np.ndarray, dict]:
+    z = normalise(p, z_raw)
     a1 = z @ p["W1"].T + p["b1"]
     h1 = np.maximum(a1, 0.0)
     a2 = h1 @ p["W2"].T + p["b2"]
@@ -73,7 +87,7 @@ def backward(p: dict, cache: dict, g_o: np.ndarray) -> dict:
 
 def adam_step(p: dict, g: dict, m: dict, v: dict, t: int, lr: float, b1: float = 0.9, b2: float = 0.999,
               eps: float = 1e-8) -> None:
-    for k in p:
+    for k in g:
         m[k] = b1 * m[k] + (1 - b1) * g[k]
         v[k] = b2 * v[k] + (1 - b2) * g[k] * g[k]
         mh = m[k] / (1 - b1 ** t)
@@ -92,7 +106,7 @@ def proposal(p: dict, mean: np.ndarray, var: np.ndarray, dy: np.ndarray, dt: flo
     delta, lam = o[0, :r], o[0, r:]
     half = R * np.exp(lam)
     ok = bool(np.all(np.isfinite(delta)) and np.all(np.isfinite(half))
-              and np.all(half >= R / 8) and np.all(half <= 8 * R))
+              and np.all(half >= R / 8) and np.all(half <= 8 * R) and np.all(np.abs(delta) <= half))
     if not ok:
         return mean.copy(), R.copy(), False
     return mean + delta, half, True

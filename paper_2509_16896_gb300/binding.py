@@ -41,7 +41,8 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_batch_launch_count", "yy_batch_graph_kernel_count", "yy_get_counters",
            "yy_batch_get_routing", "yy_get_box", "yy_set_restart_mlp", "yy_mlp_param_count",
            "yy_mlp_workspace_bytes", "yy_mlp_create", "yy_mlp_destroy", "yy_mlp_set_params",
-           "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train")
+           "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train",
+           "yy_mlp_set_input_norm")
 
 
 class YYError(RuntimeError):
@@ -110,6 +111,7 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_mlp_forward": (I32, [P, P, I32, P]),
         "yy_mlp_loss_grad": (I32, [P, P, P, I32, D, P, P]),
         "yy_mlp_train": (I32, [P, P, P, I64, D, I32, I32, ctypes.c_float, ctypes.c_uint64, P]),
+        "yy_mlp_set_input_norm": (I32, [P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -346,6 +348,11 @@ class MLP:
         flat = np.ascontiguousarray(flat, dtype=np.float32)
         assert flat.size == self.n_params
         _check("yy_mlp_set_params", self.lib.yy_mlp_set_params(self.h, _ptr(flat)))
+
+    def set_input_norm(self, mean: np.ndarray, std: np.ndarray) -> None:
+        mean = np.ascontiguousarray(mean, dtype=np.float32)
+        std = np.ascontiguousarray(std, dtype=np.float32)
+        _check("yy_mlp_set_input_norm", self.lib.yy_mlp_set_input_norm(self.h, _ptr(mean), _ptr(std)))
 
     def get_params(self) -> np.ndarray:
         out = np.empty(self.n_params, dtype=np.float32)

@@ -2,7 +2,8 @@
 // library's own kernels (a library addition; the paper's restart, Section 5, uses a fixed
 // box at the estimate).
 //
-//   z = [x_hat; sqrt(v_hat); dy / sqrt(dt)] (3r)  ->  relu(W1 z + b1) (H)  ->  relu(W2 . + b2) (H)
+//   z = [x_hat; sqrt(v_hat); dy / sqrt(dt)] (3r), zn = clamp((z - mu) / s, -4, 4) (per-feature
+//   statistics of the training set)  ->  relu(W1 zn + b1) (H)  ->  relu(W2 . + b2) (H)
 //     ->  o = W3 . + b3 = [delta; lambda] (2r)
 //   proposed box: centre x_hat + delta, half-widths R exp(lambda)
 //   loss: mean over rows and coordinates of (t - delta)^2 / (2 sigma^2) + log sigma,
@@ -34,6 +35,9 @@ struct yy_mlp {
     float* m;
     float* v;
     float* x;           // [max_batch][3r] gathered inputs
+    float* xn;          // [max_batch][3r] normalised inputs
+    float* mu;          // [3r] input normalisation: mean
+    float* istd;        // [3r] input normalisation: 1 / standard deviation
     float* t;           // [max_batch][r]  gathered targets
     float* a1; float* h1; float* a2; float* h2; float* o;   // activations
     float* g_o; float* g_h; float* g_a;                     // backward scratch [max_batch][max(H, 2r)]
@@ -97,6 +101,19 @@ void gemm(cudaStream_t s, int M, int N, int K, const float* A, long long sam, lo
                                       accumulate ? 1 : 0);
 }
 
+__global__ void k_normalise(int B, int w, const float* __restrict__ x, const float* __restrict__ mu,
+                            const float* __restrict__ istd, float* __restrict__ xn) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= B * w) return;
+    const int c = i % w;
+    xn[i] = fminf(fmaxf((x[i] - mu[c]) * istd[c], -4.f), 4.f);
+}
+
+__global__ void k_fill(int n, float* __restrict__ p, float v) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) p[i] = v;
+}
+
 __global__ void k_relu_back(int n, const float* __restrict__ g_h, const float* __restrict__ a, float* __restrict__ g_a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) g_a[i] = a[i] > 0.f ? g_h[i] : 0.f;
@@ -154,7 +171,7 @@ __global__ void k_gather(int B, int w, const int* __restrict__ idx, const float*
 size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t params, grads, m, v, x, t, a1, h1, a2, h2, o, g_o, g_h, g_a, loss, idx, total;
+    size_t params, grads, m, v, x, xn, mu, istd, t, a1, h1, a2, h2, o, g_o, g_h, g_a, loss, idx, total;
     long long n_params;
 };
 
@@ -169,6 +186,9 @@ Layout layout(int r, int H, int mb) {
     L.m = take(sizeof(float) * np);
     L.v = take(sizeof(float) * np);
     L.x = take(sizeof(float) * (size_t)mb * 3 * r);
+    L.xn = take(sizeof(float) * (size_t)mb * 3 * r);
+    L.mu = take(sizeof(float) * 3 * (size_t)r);
+    L.istd = take(sizeof(float) * 3 * (size_t)r);
     L.t = take(sizeof(float) * (size_t)mb * r);
     L.a1 = take(sizeof(float) * (size_t)mb * H);
     L.h1 = take(sizeof(float) * (size_t)mb * H);
@@ -188,7 +208,8 @@ Layout layout(int r, int H, int mb) {
 void forward(yy_mlp* n, const float* x, int B) {
     const int r = n->r, H = n->H;
     const float* P = n->params;
-    gemm(n->stream, B, H, 3 * r, x, 3 * r, 1, P + n->off_W1, 1, 3 * r, n->h1, H, P + n->off_b1, n->a1, true, false);
+    k_normalise<<<(B * 3 * r + 255) / 256, 256, 0, n->stream>>>(B, 3 * r, x, n->mu, n->istd, n->xn);
+    gemm(n->stream, B, H, 3 * r, n->xn, 3 * r, 1, P + n->off_W1, 1, 3 * r, n->h1, H, P + n->off_b1, n->a1, true, false);
     gemm(n->stream, B, H, H, n->h1, H, 1, P + n->off_W2, 1, H, n->h2, H, P + n->off_b2, n->a2, true, false);
     gemm(n->stream, B, 2 * r, H, n->h2, H, 1, P + n->off_W3, 1, H, n->o, 2 * r, P + n->off_b3, nullptr, false, false);
 }
@@ -213,7 +234,7 @@ void forward_backward(yy_mlp* n, int B, float R) {
     gemm(s, B, H, H, n->g_a, H, 1, P + n->off_W2, H, 1, n->g_h, H, nullptr, nullptr, false, false);
     k_relu_back<<<(B * H + 255) / 256, 256, 0, s>>>(B * H, n->g_h, n->a1, n->g_a);
     // layer 1
-    gemm(s, H, 3 * r, B, n->g_a, 1, H, n->x, 3 * r, 1, G + n->off_W1, 3 * r, nullptr, nullptr, false, false);
+    gemm(s, H, 3 * r, B, n->g_a, 1, H, n->xn, 3 * r, 1, G + n->off_W1, 3 * r, nullptr, nullptr, false, false);
     k_colsum<<<(H + 127) / 128, 128, 0, s>>>(B, H, n->g_a, G + n->off_b1);
 }
 
@@ -242,7 +263,7 @@ cudaError_t mlp_propose(struct ::yy_mlp* net, int r, const double* mean, const d
     k_mlp_features<<<1, 256, 0, s>>>(r, mean, var, dy, dt, flag, net->x);
     forward(net, net->x, 1);
     net->stream = old;
-    if (launches) *launches += 4;
+    if (launches) *launches += 5;
     return cudaGetLastError();
 }
 
@@ -278,6 +299,7 @@ yy_status yy_mlp_create(int32_t r, int32_t hidden, int32_t max_batch, void* d_ws
     n->params = (float*)(b + L.params); n->grads = (float*)(b + L.grads);
     n->m = (float*)(b + L.m); n->v = (float*)(b + L.v);
     n->x = (float*)(b + L.x); n->t = (float*)(b + L.t);
+    n->xn = (float*)(b + L.xn); n->mu = (float*)(b + L.mu); n->istd = (float*)(b + L.istd);
     n->a1 = (float*)(b + L.a1); n->h1 = (float*)(b + L.h1); n->a2 = (float*)(b + L.a2); n->h2 = (float*)(b + L.h2);
     n->o = (float*)(b + L.o); n->g_o = (float*)(b + L.g_o); n->g_h = (float*)(b + L.g_h); n->g_a = (float*)(b + L.g_a);
     n->loss = (float*)(b + L.loss); n->idx = (int*)(b + L.idx);
@@ -289,6 +311,7 @@ yy_status yy_mlp_create(int32_t r, int32_t hidden, int32_t max_batch, void* d_ws
     n->off_W3 = n->off_b2 + hidden;
     n->off_b3 = n->off_W3 + (size_t)2 * r * hidden;
     if (cudaMemsetAsync(d_ws, 0, need, n->stream) != cudaSuccess) { delete n; return YY_ERR_CUDA; }
+    k_fill<<<(3 * r + 255) / 256, 256, 0, n->stream>>>(3 * r, n->istd, 1.0f);   // identity normalisation
     *out = n;
     return YY_OK;
 }
@@ -305,6 +328,19 @@ yy_status yy_mlp_set_params(yy_mlp* n, const float* h_params) {
     if (e == cudaSuccess) e = cudaMemsetAsync(n->v, 0, sizeof(float) * n->n_params, n->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     n->step = 0;
+    return e == cudaSuccess ? YY_OK : YY_ERR_CUDA;
+}
+
+yy_status yy_mlp_set_input_norm(yy_mlp* n, const float* h_mean, const float* h_std) {
+    if (!n || !h_mean || !h_std) return YY_ERR_ARG;
+    std::vector<float> istd(3 * (size_t)n->r);
+    for (int i = 0; i < 3 * n->r; ++i) {
+        if (!(h_std[i] > 0.f) || !isfinite(h_mean[i])) return YY_ERR_ARG;
+        istd[i] = 1.f / h_std[i];
+    }
+    cudaError_t e = cudaMemcpyAsync(n->mu, h_mean, sizeof(float) * 3 * n->r, cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(n->istd, istd.data(), sizeof(float) * 3 * n->r, cudaMemcpyHostToDevice, n->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
     return e == cudaSuccess ? YY_OK : YY_ERR_CUDA;
 }
 

@@ -388,8 +388,9 @@ __device__ __forceinline__ void restart_begin_body(DevStats* st, int mode) {
 
 // Box of the restart in progress.  Plain rule: centre x_hat, half-widths unchanged.
 // Learned rule (out = network output [delta; lambda], or NULL): centre x_hat + delta,
-// half-widths base_R exp(lambda), accepted only if every value is finite and every
-// half-width lies in [base_R / 8, 8 base_R]; the offset c_ref follows the box volume.
+// half-widths base_R exp(lambda), accepted only if every value is finite, every
+// half-width lies in [base_R / 8, 8 base_R] and the box contains x_hat (|delta_d| <= half-
+// width); the offset c_ref follows the box volume.
 template <typename T>
 __device__ __forceinline__ void restart_box_body(const Consts<T>& k, const Bufs<T>& b, const float* out,
                                                  double base_R) {
@@ -401,7 +402,8 @@ __device__ __forceinline__ void restart_box_body(const Consts<T>& k, const Bufs<
         for (int d = threadIdx.x; d < k.r; d += blockDim.x) {
             const double delta = (double)out[d], lam = (double)out[k.r + d];
             const double h = base_R * exp(lam);
-            if (!isfinite(delta) || !isfinite(h) || h < base_R / 8.0 || h > 8.0 * base_R) atomicAnd(&s_ok, 0);
+            if (!isfinite(delta) || !isfinite(h) || h < base_R / 8.0 || h > 8.0 * base_R || fabs(delta) > h)
+                atomicAnd(&s_ok, 0);
         }
         __syncthreads();
     }

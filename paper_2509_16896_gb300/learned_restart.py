@@ -58,6 +58,8 @@ def train_proposal(r: int, X: np.ndarray, T: np.ndarray, R: float, hidden: int =
     net = binding.MLP(r, hidden, max_batch=batch, device=device)
     if init_params is not None:
         net.set_params(init_params)
+    # per-feature statistics of the training set, applied (and clamped) before layer 1
+    net.set_input_norm(X.mean(axis=0), np.maximum(X.std(axis=0), 1e-3))
     xd = torch.tensor(X, device=device)
     td = torch.tensor(T, device=device)
     loss = net.train(xd, td, R, epochs, batch, lr, seed)

@@ -15,8 +15,10 @@ def _rand_params(r, H, seed):
     from oracle import mlp
     p = mlp.init_params(r, H, seed)
     rng = np.random.default_rng(seed)
-    for k in p:
+    for k in mlp.TRAINED:
         p[k] = p[k] + 0.1 * rng.normal(size=p[k].shape)
+    p["mu"] = 0.2 * rng.normal(size=3 * r)
+    p["s"] = 1.0 + 0.3 * rng.random(3 * r)
     return p
 
 
@@ -38,6 +40,7 @@ def test_forward_and_gradients_match_oracle(yy_lib):
     T = (0.2 * rng.normal(size=(B, r))).astype(np.float32)
     net = binding.MLP(r, H, max_batch=B)
     net.set_params(binding.pack_mlp_params(p))
+    net.set_input_norm(p["mu"], p["s"])
     xd, td = torch.tensor(X, device="cuda"), torch.tensor(T, device="cuda")
     o_gpu = net.forward(xd).cpu().numpy().astype(np.float64)
     o_ref, cache = mlp.forward(p, X.astype(np.float64))
@@ -47,7 +50,7 @@ def test_forward_and_gradients_match_oracle(yy_lib):
     g_ref = mlp.backward(p, cache, g_o)
     assert loss == pytest.approx(L_ref, rel=1e-2)
     g_gpu = binding.unpack_mlp_params(g, r, H)
-    for k in g_ref:
+    for k in mlp.TRAINED:
         err = np.linalg.norm(g_gpu[k] - g_ref[k]) / np.linalg.norm(g_ref[k])
         assert err <= 2e-2, (k, err)
 

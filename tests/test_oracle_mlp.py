@@ -9,8 +9,10 @@ from synth import simulate, sobol_poly_params, sobol_scramble_params
 def _setup(r=3, hidden=8, B=5, seed=0):
     p = mlp.init_params(r, hidden, seed)
     rng = np.random.default_rng(seed)
-    for k in p:   # non-trivial values everywhere (the init has zero biases and tiny W3)
+    for k in mlp.TRAINED:   # non-trivial values everywhere (the init has zero biases and tiny W3)
         p[k] = p[k] + 0.3 * rng.normal(size=p[k].shape)
+    p["mu"] = 0.1 * rng.normal(size=3 * r)
+    p["s"] = 1.0 + 0.2 * rng.random(3 * r)
     z = rng.normal(size=(B, 3 * r))
     t = 0.2 * rng.normal(size=(B, r))
     return p, z, t
@@ -24,7 +26,7 @@ def test_backward_matches_central_differences():
     g = mlp.backward(p, cache, g_o)
     rng = np.random.default_rng(1)
     h = 1e-6
-    for k in p:
+    for k in mlp.TRAINED:
         for _ in range(6):
             idx = tuple(rng.integers(0, s) for s in p[k].shape)
             q = {kk: vv.copy() for kk, vv in p.items()}
@@ -86,3 +88,21 @@ def test_zero_output_network_reproduces_plain_restarts():
         recs = F.run(p, st, tr.dy)
         out.append(np.array([q.mean for q in recs]))
     assert np.array_equal(out[0], out[1])
+
+
+def test_normalisation_clamps_out_of_range_features():
+    p = mlp.init_params(2, 4, 0)
+    p["mu"] = np.array([1.0, 0, 0, 0, 0, 0])
+    p["s"] = np.full(6, 0.5)
+    zn = mlp.normalise(p, np.array([[1.5, 10.0, -10.0, 0.0, 0.5, 2.1]]))
+    assert np.allclose(zn, [[1.0, 4.0, -4.0, 0.0, 1.0, 4.0]])
+
+
+def test_box_must_contain_the_estimate():
+    r = 2
+    p = mlp.init_params(r, 4, 0)
+    p["W3"][:] = 0.0
+    p["b3"][:r] = [0.5, 0.0]      # shift beyond the half-width R = 0.3
+    R = np.full(r, 0.3)
+    c, h, ok = mlp.proposal(p, np.zeros(r), np.full(r, 0.01), np.zeros(r), 0.01, R)
+    assert not ok
