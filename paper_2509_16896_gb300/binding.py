@@ -185,6 +185,9 @@ class Filter:
         base = self.ws.data_ptr()
         self.ws_ptr = (base + 255) & ~255
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        # the workspace is used on self.stream: the caching allocator must not hand it out
+        # again before that stream's work has finished
+        self.ws.record_stream(self.stream)
         h = ctypes.c_void_p()
         _check("yy_create", self.lib.yy_create(ctypes.byref(cfg), ctypes.c_void_p(self.ws_ptr),
                                                self.ws_bytes, ctypes.c_void_p(self.stream.cuda_stream),
@@ -195,6 +198,7 @@ class Filter:
 
     def close(self) -> None:
         if getattr(self, "h", None):
+            self.stream.synchronize()   # no kernel of this handle may outlive its workspace
             self.lib.yy_destroy(self.h)
             self.h = None
 
@@ -218,8 +222,10 @@ class Filter:
 
     def sobol_bits(self, first: int, count: int):
         out = self.torch.empty((count, self.r), dtype=self.torch.int32, device=self.device)
+        _order_after_torch(self.stream, self.device)
         _check("yy_sobol_bits", self.lib.yy_sobol_bits(self.h, ctypes.c_void_p(out.data_ptr()),
                                                        first, count))
+        self.stream.synchronize()
         return out
 
     def predict(self) -> None:
@@ -228,6 +234,7 @@ class Filter:
     def update(self, dy_dev) -> None:
         """dy_dev: torch float64 tensor [r] on the device."""
         assert dy_dev.dtype == self.torch.float64 and dy_dev.is_cuda and dy_dev.numel() == self.r
+        _order_after_torch(self.stream, self.device)
         _check("yy_update", self.lib.yy_update(self.h, ctypes.c_void_p(dy_dev.data_ptr())))
 
     def estimate(self):
@@ -295,9 +302,11 @@ class Filter:
     def run_steps(self, dy_all_dev, hist_dev=None) -> None:
         """dy_all_dev: float64 [K][r] device tensor; hist_dev: float64 [K][2r + 4] or None."""
         K = dy_all_dev.shape[0]
+        _order_after_torch(self.stream, self.device)
         _check("yy_run_steps", self.lib.yy_run_steps(
             self.h, ctypes.c_void_p(dy_all_dev.data_ptr()), K,
             None if hist_dev is None else ctypes.c_void_p(hist_dev.data_ptr())))
+        _order_torch_after(self.stream, self.device)
 
     def graph_capture(self, dy_all_dev, hist_dev=None) -> None:
         K = dy_all_dev.shape[0]
@@ -306,7 +315,9 @@ class Filter:
             None if hist_dev is None else ctypes.c_void_p(hist_dev.data_ptr())))
 
     def graph_launch(self) -> None:
+        _order_after_torch(self.stream, self.device)
         _check("yy_graph_launch", self.lib.yy_graph_launch(self.h))
+        _order_torch_after(self.stream, self.device)
 
     def graph_kernels(self) -> int:
         return int(self.lib.yy_graph_kernel_count(self.h))
@@ -328,6 +339,7 @@ class MLP:
         self.ws = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
         ptr = (self.ws.data_ptr() + 255) & ~255
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ws.record_stream(self.stream)
         h = ctypes.c_void_p()
         _check("yy_mlp_create", self.lib.yy_mlp_create(r, hidden, max_batch, ctypes.c_void_p(ptr), nbytes,
                                                        ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
@@ -335,6 +347,7 @@ class MLP:
 
     def close(self):
         if getattr(self, "h", None):
+            self.stream.synchronize()
             self.lib.yy_mlp_destroy(self.h)
             self.h = None
 
@@ -362,13 +375,16 @@ class MLP:
     def forward(self, x_dev):
         B = x_dev.shape[0]
         out = self.torch.empty((B, 2 * self.r), dtype=self.torch.float32, device=self.device)
+        _order_after_torch(self.stream, self.device)
         _check("yy_mlp_forward", self.lib.yy_mlp_forward(self.h, ctypes.c_void_p(x_dev.data_ptr()), B,
                                                          ctypes.c_void_p(out.data_ptr())))
+        _order_torch_after(self.stream, self.device)
         return out
 
     def loss_grad(self, x_dev, t_dev, R: float):
         loss = ctypes.c_float()
         g = np.empty(self.n_params, dtype=np.float32)
+        _order_after_torch(self.stream, self.device)
         _check("yy_mlp_loss_grad", self.lib.yy_mlp_loss_grad(
             self.h, ctypes.c_void_p(x_dev.data_ptr()), ctypes.c_void_p(t_dev.data_ptr()), x_dev.shape[0], R,
             ctypes.byref(loss), _ptr(g)))
@@ -376,10 +392,30 @@ class MLP:
 
     def train(self, x_dev, t_dev, R: float, epochs: int, batch: int, lr: float, seed: int = 0) -> float:
         loss = ctypes.c_float()
+        _order_after_torch(self.stream, self.device)
         _check("yy_mlp_train", self.lib.yy_mlp_train(
             self.h, ctypes.c_void_p(x_dev.data_ptr()), ctypes.c_void_p(t_dev.data_ptr()), x_dev.shape[0], R,
             epochs, batch, ctypes.c_float(lr), ctypes.c_uint64(seed), ctypes.byref(loss)))
         return loss.value
+
+
+def _order_after_torch(stream, device) -> None:
+    """Makes `stream` wait for the work already queued on torch's current and default
+    streams (buffers filled there, e.g. torch.zeros, must be ready before the library
+    reads or writes them on its own stream)."""
+    import torch
+    for other in (torch.cuda.current_stream(device), torch.cuda.default_stream(device)):
+        if other.cuda_stream != stream.cuda_stream:
+            stream.wait_stream(other)
+
+
+def _order_torch_after(stream, device) -> None:
+    """Makes torch's current and default streams wait for the library's stream, so that
+    device outputs (histories, network outputs) are ready for torch work queued next."""
+    import torch
+    for other in (torch.cuda.current_stream(device), torch.cuda.default_stream(device)):
+        if other.cuda_stream != stream.cuda_stream:
+            other.wait_stream(stream)
 
 
 def pack_mlp_params(p: dict) -> np.ndarray:
@@ -435,6 +471,7 @@ class Batch:
         self.ws = torch.empty(int(nbytes) + 256, dtype=torch.uint8, device=self.device)
         ptr = (self.ws.data_ptr() + 255) & ~255
         self.stream = stream if stream is not None else torch.cuda.Stream(self.device)
+        self.ws.record_stream(self.stream)
         h = ctypes.c_void_p()
         _check("yy_batch_create", self.lib.yy_batch_create(arr, self.B, ctypes.c_void_p(ptr), int(nbytes),
                                                            ctypes.c_void_p(self.stream.cuda_stream),
@@ -454,6 +491,7 @@ class Batch:
 
     def close(self) -> None:
         if getattr(self, "h", None):
+            self.stream.synchronize()   # no kernel of the batch may outlive its workspace
             self.lib.yy_batch_destroy(self.h)
             self.h = None
 
@@ -465,9 +503,11 @@ class Batch:
 
     def run_steps(self, dy_all_dev, hist_dev=None) -> None:
         K = dy_all_dev.shape[0]
+        _order_after_torch(self.stream, self.device)
         _check("yy_batch_run_steps", self.lib.yy_batch_run_steps(
             self.h, ctypes.c_void_p(dy_all_dev.data_ptr()), K,
             None if hist_dev is None else ctypes.c_void_p(hist_dev.data_ptr())))
+        _order_torch_after(self.stream, self.device)
 
     def predict(self) -> None:
         _check("yy_batch_predict", self.lib.yy_batch_predict(self.h))
@@ -479,7 +519,9 @@ class Batch:
             None if hist_dev is None else ctypes.c_void_p(hist_dev.data_ptr())))
 
     def graph_launch(self) -> None:
+        _order_after_torch(self.stream, self.device)
         _check("yy_batch_graph_launch", self.lib.yy_batch_graph_launch(self.h))
+        _order_torch_after(self.stream, self.device)
 
     def set_schedule(self, bn: int, grid: int) -> None:
         _check("yy_batch_set_schedule", self.lib.yy_batch_set_schedule(self.h, bn, grid))

@@ -72,6 +72,7 @@ def test_batch_graph_replays_run_steps(yy_lib):
     a = _batch("bf16")
     ha = torch.zeros((2 * K, a.H), dtype=torch.float64, device="cuda")
     a.run_steps(dy_all, ha)
+    torch.cuda.synchronize()
     g = _batch("bf16")
     buf = torch.empty((K, g.M), dtype=torch.float64, device="cuda")
     hg = torch.zeros((K, g.H), dtype=torch.float64, device="cuda")
@@ -97,6 +98,7 @@ def test_every_schedule_gives_the_same_prediction(yy_lib, tmp_path):
         bt.set_schedule(bn, grid)
         hist = torch.zeros((K, bt.H), dtype=torch.float64, device="cuda")
         bt.run_steps(dy_all, hist)
+        torch.cuda.synchronize()
         h = hist.cpu().numpy()
         if ref is None:
             ref = h
@@ -114,5 +116,6 @@ def test_every_schedule_gives_the_same_prediction(yy_lib, tmp_path):
     # the tuned batch (some members possibly on the FP32 form) gives the same answer
     hist = torch.zeros((K, bt.H), dtype=torch.float64, device="cuda")
     bt.run_steps(dy_all, hist)
+    torch.cuda.synchronize()
     h = hist.cpu().numpy()
     assert np.max(np.abs(h - ref) / np.maximum(1.0, np.abs(ref))) <= 1e-5
