@@ -52,9 +52,16 @@ def collect_restarts(workload, seeds, precision: str = "bf16", device: str = "cu
 
 def train_proposal(r: int, X: np.ndarray, T: np.ndarray, R: float, hidden: int = 256, epochs: int = 20,
                    batch: int = 256, lr: float = 1e-3, seed: int = 0, init_params: np.ndarray | None = None,
-                   device: str = "cuda:0"):
-    """Trains a fresh network on (X, T); returns (network, last mini-batch loss)."""
+                   clip: float | None = None, device: str = "cuda:0"):
+    """Trains a fresh network on (X, T); returns (network, last mini-batch loss).
+
+    clip (default R): the targets are clipped to [-clip, clip] first.  A box can only be
+    moved within its own scale (the proposal must contain the estimate), and offsets far
+    beyond it -- frequent when the plain filter has lost track -- otherwise dominate the
+    loss and make training diverge."""
     import torch
+    clip = R if clip is None else clip
+    T = np.clip(T, -clip, clip) if clip > 0 else T
     net = binding.MLP(r, hidden, max_batch=batch, device=device)
     if init_params is not None:
         net.set_params(init_params)
