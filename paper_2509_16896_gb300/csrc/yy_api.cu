@@ -4,7 +4,9 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "yy_handle.cuh"
 
@@ -13,6 +15,41 @@ using namespace yy;
 namespace {
 
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
+
+constexpr int kMaxTcGrid = 1024;
+
+// Work list of the single-filter BF16 prediction: one persistent CTA per SM, every target
+// tile split into S source ranges (S minimising the makespan), items dealt round-robin
+// (all items cost the same).  Copied into the workspace; synchronous (set-up only).
+yy_status build_tc_schedule(yy_filter* f) {
+    int dev = 0, sms = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long tiles = f->n_pad / 128;
+    const int nst = (int)(f->n_pad / 256);
+    const int grid = (int)std::min<long long>(std::min(sms, kMaxTcGrid), tiles * 8);
+    const int S = tc_choose_splits(tiles, nst, grid);
+    std::vector<std::vector<int4>> per(grid);
+    long long j = 0;
+    for (long long t = 0; t < tiles; ++t)
+        for (int q = 0; q < S; ++q, ++j) per[j % grid].push_back(make_int4(0, (int)t, q, S));
+    std::vector<int4> items;
+    std::vector<int> start(grid + 1);
+    for (int c = 0; c < grid; ++c) {
+        start[c] = (int)items.size();
+        items.insert(items.end(), per[c].begin(), per[c].end());
+    }
+    start[grid] = (int)items.size();
+    cudaError_t e = cudaMemcpyAsync(f->bf.tc_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice,
+                                    f->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(f->bf.tc_cta_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice,
+                            f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    f->bf.tc_grid = grid;
+    f->bf.tc_splits = S;
+    return YY_OK;
+}
 
 bool cfg_valid(const yy_config* c) {
     if (!c) return false;
@@ -75,6 +112,9 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
         b.tc_q = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_tile_lmax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
         b.tc_tile_numax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
+        b.tc_part = cv.take<float>((size_t)n_pad * 8 * kMaxScales * 2 * sizeof(float));
+        b.tc_items = cv.take<int4>((size_t)(n_pad / 128) * 8 * sizeof(int4));
+        b.tc_cta_start = cv.take<int>((size_t)(kMaxTcGrid + 1) * sizeof(int));
     }
     if (out) *out = b;
     return cv.off + 256;
@@ -198,6 +238,10 @@ yy_status do_init_nodes(yy_filter* f, Bufs<T>& b, Consts<T>& k, const uint32_t* 
     k_set_stats<<<1, 1, 0, s>>>(b.stats, 0.0, 0);
     k_init_cref<<<1, 1, 0, s>>>(b.stats, f->c_ref);
     f->launches += 6 + l;
+    if (f->cfg.precision == YY_PREC_BF16) {
+        const yy_status st = build_tc_schedule(f);
+        if (st != YY_OK) return st;
+    }
     f->nodes_ready = true;
     f->predicted = false;
     return cuda_status(cudaGetLastError());

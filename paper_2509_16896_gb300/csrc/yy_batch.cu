@@ -36,7 +36,7 @@ struct yy_batch {
     // device descriptors (inside the workspace)
     Traj<float>* d_traj;
     void* d_maps;                   // CUtensorMap[2B]
-    int2* d_items;
+    int4* d_items;
     int* d_cta_start;
     int max_items, max_grid;
     // schedule
@@ -73,14 +73,14 @@ bool batch_cfg_ok(const yy_config* cfgs, int B) {
 long long total_items(const yy_config* cfgs, int B) {
     long long t = 0;
     for (int b = 0; b < B; ++b) t += (cfgs[b].n + 255) / 256 * 2;   // 128-row target tiles
-    return t;
+    return t * 8;                                                    // up to 8 source splits
 }
 
 size_t header_bytes(const yy_config* cfgs, int B) {
     size_t s = 0;
     s += al256(sizeof(Traj<float>) * (size_t)B);
     s += al256(kMapBytes * 2 * (size_t)B);
-    s += al256(sizeof(int2) * (size_t)total_items(cfgs, B));
+    s += al256(sizeof(int4) * (size_t)total_items(cfgs, B));
     s += al256(sizeof(int) * (kMaxGrid + 1));
     return s;
 }
@@ -92,27 +92,42 @@ int sm_count() {
 }
 
 // Longest-processing-time-first: items sorted by cost, each given to the least-loaded CTA;
-// returns the concatenated per-CTA lists and their offsets.
-void lpt_schedule(const yy_batch* bt, int grid, int bn, std::vector<int2>& items, std::vector<int>& start) {
-    struct It { double cost; int b, t; };
+// returns the concatenated per-CTA lists and their offsets.  A member whose target tile
+// would cost more than a quarter of the average CTA load has its sources split (up to 8
+// ranges), so that no single item dominates a CTA; splits[b] receives the split count.
+void lpt_schedule(const yy_batch* bt, int grid, int bn, std::vector<int4>& items, std::vector<int>& start,
+                  std::vector<int>& splits) {
+    struct It { double cost; int b, t, q, S; };
     std::vector<It> all;
+    double total = 0.0;
+    for (int b = 0; b < bt->B; ++b) {
+        const yy_filter* f = bt->filters[b];
+        if (bt->path[b] != 0) continue;
+        total += (double)(f->n_pad / 128) * (double)(f->n_pad / bn) * ((double)(f->r_pad / 64) + 1.0);
+    }
+    const double avg = total / std::max(grid, 1);
+    splits.assign(bt->B, 1);
     for (int b = 0; b < bt->B; ++b) {
         const yy_filter* f = bt->filters[b];
         if (bt->path[b] != 0) continue;
         const long long tiles = f->n_pad / 128;
-        const double src_tiles = (double)(f->n_pad / bn);
-        const double cost = src_tiles * ((double)(f->r_pad / 64) + 1.0);
-        for (long long t = 0; t < tiles; ++t) all.push_back({cost, b, (int)t});
+        const int nst = (int)(f->n_pad / bn);
+        const double tile_cost = (double)nst * ((double)(f->r_pad / 64) + 1.0);
+        int S = (int)std::ceil(tile_cost / std::max(avg / 4.0, 1e-9));
+        S = std::max(1, std::min({S, 8, nst}));
+        splits[b] = S;
+        for (long long t = 0; t < tiles; ++t)
+            for (int q = 0; q < S; ++q) all.push_back({tile_cost / S, b, (int)t, q, S});
     }
     std::stable_sort(all.begin(), all.end(), [](const It& a, const It& c) { return a.cost > c.cost; });
     using Load = std::pair<double, int>;
     std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
     for (int c = 0; c < grid; ++c) heap.push({0.0, c});
-    std::vector<std::vector<int2>> per(grid);
+    std::vector<std::vector<int4>> per(grid);
     for (const It& it : all) {
         Load l = heap.top();
         heap.pop();
-        per[l.second].push_back(make_int2(it.b, it.t));
+        per[l.second].push_back(make_int4(it.b, it.t, it.q, it.S));
         heap.push({l.first + it.cost, l.second});
     }
     items.clear();
@@ -131,6 +146,10 @@ yy_status upload(yy_batch* bt) {
         if (!bt->filters[b]->nodes_ready) return YY_ERR_STATE;
     std::vector<Traj<float>> tr(bt->B);
     std::vector<unsigned char> maps(kMapBytes * 2 * (size_t)bt->B, 0);
+    std::vector<int4> items;
+    std::vector<int> start, splits;
+    lpt_schedule(bt, bt->grid, bt->bn, items, start, splits);
+    if ((long long)items.size() > (long long)bt->max_items) return YY_ERR_ARG;
     for (int b = 0; b < bt->B; ++b) {
         yy_filter* f = bt->filters[b];
         tr[b].k = f->kf;
@@ -141,6 +160,7 @@ yy_status upload(yy_batch* bt) {
         tr[b].ess_frac = f->cfg.ess_frac;
         tr[b].restart_init = f->cfg.restart_init;
         tr[b].path = bt->path[b];
+        tr[b].b.tc_splits = splits[b];
         if (bt->precision == YY_PREC_BF16) {
             if (!make_tc_map(&maps[kMapBytes * 2 * b], f->bf.ubf, f->n_pad, f->r_pad, 128) ||
                 !make_tc_map(&maps[kMapBytes * (2 * b + 1)], f->bf.ubf, f->n_pad, f->r_pad, bt->bn))
@@ -148,16 +168,12 @@ yy_status upload(yy_batch* bt) {
             if (b == 0) memcpy(bt->map_any, &maps[0], kMapBytes);
         }
     }
-    std::vector<int2> items;
-    std::vector<int> start;
-    lpt_schedule(bt, bt->grid, bt->bn, items, start);
-    if ((int)items.size() > bt->max_items) return YY_ERR_ARG;
     cudaError_t e = cudaMemcpyAsync(bt->d_traj, tr.data(), sizeof(Traj<float>) * tr.size(), cudaMemcpyHostToDevice,
                                     bt->stream);
     if (e == cudaSuccess && bt->precision == YY_PREC_BF16)
         e = cudaMemcpyAsync(bt->d_maps, maps.data(), maps.size(), cudaMemcpyHostToDevice, bt->stream);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(bt->d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, bt->stream);
+        e = cudaMemcpyAsync(bt->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice, bt->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(bt->d_cta_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice,
                             bt->stream);
@@ -249,8 +265,8 @@ yy_status yy_batch_create(const yy_config* cfgs, int32_t B, void* d_workspace, s
     p += al256(sizeof(Traj<float>) * (size_t)B);
     bt->d_maps = p;
     p += al256(kMapBytes * 2 * (size_t)B);
-    bt->d_items = reinterpret_cast<int2*>(p);
-    p += al256(sizeof(int2) * (size_t)bt->max_items);
+    bt->d_items = reinterpret_cast<int4*>(p);
+    p += al256(sizeof(int4) * (size_t)bt->max_items);
     bt->d_cta_start = reinterpret_cast<int*>(p);
     p += al256(sizeof(int) * (kMaxGrid + 1));
     long long M = 0, H = 0;

@@ -89,6 +89,11 @@ struct Bufs {
     float* tc_q;          // [n_pad] |u_s|^2 of live sources, 3e38 for dead ones
     float* tc_tile_lmax;  // [n_pad / 128] max live log-weight per chunk of 128 sources
     float* tc_tile_numax; // [n_pad / 128] max |u_s|^2 per chunk of 128 sources
+    float* tc_part;       // [n_pad][8][4][2] partial (max, sum) of split work items
+    int4* tc_items;       // single-filter work list (target tile, split, nsplit)
+    int* tc_cta_start;    // [tc_grid + 1]
+    int tc_grid;          // persistent CTAs of the single-filter prediction
+    int tc_splits;        // source splits per target tile
 };
 
 // Device-side descriptor of one trajectory of a batch (kernels index it by blockIdx.y).
@@ -121,6 +126,8 @@ cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStr
                            int* launches);
 size_t tc_scratch_bytes(long long n_pad);
 cudaError_t prepare_ksum_tc();
+int tc_choose_splits(long long tiles, int nst, int grid);
+int tc_max_split();
 
 template <typename T>
 cudaError_t launch_record(const Consts<T>& k, const Bufs<T>& b, double* hist_row, cudaStream_t s);
@@ -158,7 +165,7 @@ template <typename T>
 cudaError_t launch_reset_batch(const Traj<T>* d_traj, int B, cudaStream_t s, int* launches);
 bool make_tc_map(void* map /* CUtensorMap */, const void* base, long long rows, int cols, int box_rows);
 cudaError_t launch_ksum_tc_batch(const Traj<float>* d_traj, int B, int N, long long n_pad_max,
-                                 const void* d_maps /* CUtensorMap[2B] */, const int2* d_items,
+                                 const void* d_maps /* CUtensorMap[2B] */, const int4* d_items,
                                  const int* d_cta_start, int grid, int bn, const Consts<float>& k_any,
                                  const Bufs<float>& b_any, const void* map_any, cudaStream_t s, int* launches);
 

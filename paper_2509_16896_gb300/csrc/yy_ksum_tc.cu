@@ -29,11 +29,14 @@
 // self terms).  At low r most pairs are within reach of the kernel and the plain FP32
 // form is faster; the batch autotuner routes such filters there.
 //
-// Work item = one tile of 128 targets of one filter over all of that filter's sources
-// (source tiles of BN = 256 or 128).  A single filter launches one CTA per item; a batch
-// of ragged filters launches a persistent grid in which every CTA walks its own list of
-// (filter, target tile) items, prepared on the host by a longest-processing-time-first
-// assignment, with the TMA descriptors of every filter in global memory.  Warp roles:
+// Work item = one tile of 128 targets of one filter over one of nsplit contiguous ranges
+// of that filter's source tiles (BN = 256 or 128 sources per tile).  Every launch is a
+// persistent grid in which each CTA walks its own list of items, prepared on the host by
+// a longest-processing-time-first assignment; splitting the sources of a target tile
+// fills the last wave (a filter with 512 target tiles on 152 SMs would otherwise leave
+// 16 % of the SMs idle).  An item over part of the sources stores its rows' online
+// (max, sum) states and a merge kernel combines them.  For a batch the TMA descriptors of
+// every filter live in global memory.  Warp roles:
 // warp 0 issues TMA loads, warp 1 allocates TMEM and issues tcgen05.mma (one thread),
 // warps 2-5 read the accumulators with tcgen05.ld (each warp its TMEM lane quarter, one
 // target row per thread) and screen.  Every wait is bounded (%globaltimer); on expiry the
@@ -41,6 +44,8 @@
 // bounded wait, frees TMEM and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+
+#include <algorithm>
 
 #include "yy_combine.cuh"
 
@@ -244,16 +249,24 @@ __global__ void __launch_bounds__(128) kb_tc_colprep(const Traj<float>* __restri
     colprep_body(t.k, t.b, blockIdx.x);
 }
 
-// Work list of a launch.  items == nullptr: one item per CTA, target tile blockIdx.x of
-// the filter passed by value.  Otherwise CTA c processes items[cta_start[c] ..
-// cta_start[c + 1]), each (filter index, target tile), with descriptors tr[filter] and
-// TMA maps maps[2 filter] (A, 128-row box) and maps[2 filter + 1] (B, BN-row box).
+// Work list of a launch: CTA c processes items[cta_start[c] .. cta_start[c + 1]), each
+// (filter, target tile, split, nsplit): target rows 128 tile .. +127 against source tiles
+// [nst split / nsplit, nst (split + 1) / nsplit).  tr == nullptr: single filter, passed by
+// value with its TMA maps; otherwise descriptors tr[filter] and TMA maps maps[2 filter]
+// (A, 128-row box) and maps[2 filter + 1] (B, BN-row box).
 struct TcWork {
     const Traj<float>* tr;
     const CUtensorMap* maps;
-    const int2* items;
+    const int4* items;
     const int* cta_start;
 };
+
+constexpr int kMaxSplit = 8;
+
+// Partial online log-sum-exp states of split items: [row][split][scale] (max, sum).
+__device__ __forceinline__ float* part_slot(const Bufs<float>& b, long long i, int split, int j) {
+    return b.tc_part + (((size_t)i * kMaxSplit + split) * kMaxScales + j) * 2;
+}
 
 template <int N, int BN>
 __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
@@ -276,12 +289,12 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const bool batched = (w.items != nullptr);
-    const int it_begin = batched ? w.cta_start[blockIdx.x] : 0;
-    const int it_end = batched ? w.cta_start[blockIdx.x + 1] : 1;
-    // status word for timeouts: the first filter of this CTA (or the single filter)
-    unsigned int* status = batched ? (it_end > it_begin ? &w.tr[w.items[it_begin].x].b.stats->status : nullptr)
-                                   : &b0.stats->status;
+    const bool batched = (w.tr != nullptr);
+    const int it_begin = w.cta_start[blockIdx.x];
+    const int it_end = w.cta_start[blockIdx.x + 1];
+    // status word for timeouts: the first filter of this CTA (none if the CTA has no work)
+    unsigned int* status = (it_end <= it_begin) ? nullptr
+                           : batched ? &w.tr[w.items[it_begin].x].b.stats->status : &b0.stats->status;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -299,18 +312,22 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // per-item view: descriptors, maps, first target row, K stages, source tiles
+    // per-item view: descriptors, maps, first target row, source tile range, split
     auto item_kb = [&](int idx, const Consts<float>*& kp, const Bufs<float>*& bp, const CUtensorMap*& ma,
-                       const CUtensorMap*& mb, long long& i0) {
+                       const CUtensorMap*& mb, long long& i0, int& t0, int& t1, int& split, int& nsplit) {
+        const int4 it = w.items[idx];
         if (!batched) {
             kp = &k0; bp = &b0; ma = &tmA; mb = &tmB;
-            i0 = (long long)blockIdx.x * BM;
         } else {
-            const int2 it = w.items[idx];
             kp = &w.tr[it.x].k; bp = &w.tr[it.x].b;
             ma = &w.maps[2 * it.x]; mb = &w.maps[2 * it.x + 1];
-            i0 = (long long)it.y * BM;
         }
+        i0 = (long long)it.y * BM;
+        split = it.z;
+        nsplit = it.w;
+        const int nst = (int)(kp->n_pad / BN);
+        t0 = (int)(((long long)nst * split) / nsplit);
+        t1 = (int)(((long long)nst * (split + 1)) / nsplit);
     };
 
     if (warp == 0) {
@@ -323,10 +340,10 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             for (int idx = it_begin; idx < it_end && ok; ++idx) {
                 const Consts<float>* kp; const Bufs<float>* bp; const CUtensorMap* ma; const CUtensorMap* mb;
                 long long i0;
-                item_kb(idx, kp, bp, ma, mb, i0);
+                int t0, t1, split, nsplit;
+                item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit);
                 const int nk = kp->r_pad / BK;
-                const int nst = (int)(kp->n_pad / BN);
-                for (int t = 0; t < nst && ok; ++t) {
+                for (int t = t0; t < t1 && ok; ++t) {
                     for (int kb = 0; kb < nk; ++kb, ++it) {
                         const int s = (int)(it % STAGES);
                         const uint32_t ph = (it / STAGES) & 1u;
@@ -351,10 +368,10 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             for (int idx = it_begin; idx < it_end && ok; ++idx) {
                 const Consts<float>* kp; const Bufs<float>* bp; const CUtensorMap* ma; const CUtensorMap* mb;
                 long long i0;
-                item_kb(idx, kp, bp, ma, mb, i0);
+                int t0, t1, split, nsplit;
+                item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit);
                 const int nk = kp->r_pad / BK;
-                const int nst = (int)(kp->n_pad / BN);
-                for (int t = 0; t < nst && ok; ++t, ++tcount) {
+                for (int t = t0; t < t1 && ok; ++t, ++tcount) {
                     const int acc = (int)(tcount & 1u);
                     const uint32_t aph = (tcount >> 1) & 1u;
                     if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) { ok = false; break; }
@@ -389,10 +406,10 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         for (int idx = it_begin; idx < it_end && ok; ++idx) {
             const Consts<float>* kp; const Bufs<float>* bp; const CUtensorMap* ma; const CUtensorMap* mb;
             long long i0;
-            item_kb(idx, kp, bp, ma, mb, i0);
+            int t0, t1, split, nsplit;
+            item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit);
             const Consts<float>& k = *kp;
             const Bufs<float>& b = *bp;
-            const int nst = (int)(k.n_pad / BN);
             const float T = logf((float)k.n) + 20.0f;
             const long long i = i0 + q * 32 + lane;
             const bool in_range = i < k.n;
@@ -401,15 +418,18 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             if (in_range) { nu_i = b.nu[i]; nf_i = b.nf[i]; li = b.logw[i]; }
             const float Fi = sqrtf(nf_i);
             float rowc[N], mx[N], sm[N];
+            // the exact self term (u_i - u_i = 0) is the screening reference of every split
+            // and is counted by the split whose source range holds i
+            const bool self_here = (i / BN) >= t0 && (i / BN) < t1;
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 rowc[j] = -0.5f * k.tau[j] * nf_i;
                 const bool self = live && li != -INFINITY;
-                mx[j] = self ? rowc[j] + li : -INFINITY;   // exact self term (u_i - u_i = 0)
-                sm[j] = self ? 1.f : 0.f;
+                mx[j] = self ? rowc[j] + li : -INFINITY;
+                sm[j] = (self && self_here) ? 1.f : 0.f;
             }
             unsigned long long ncand = 0;
-            for (int t = 0; t < nst; ++t, ++tcount) {
+            for (int t = t0; t < t1; ++t, ++tcount) {
                 const int acc = (int)(tcount & 1u);
                 const uint32_t aph = (tcount >> 1) & 1u;
                 __syncwarp();
@@ -518,9 +538,20 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[acc]);
             }
-            if (ok && in_range)
-                b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li, b.stats->c_ref, &b.stats->clamps)
-                                      : -INFINITY;
+            if (ok && in_range) {
+                if (nsplit == 1) {
+                    b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li, b.stats->c_ref,
+                                                                     &b.stats->clamps)
+                                          : -INFINITY;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) {
+                        float* ps = part_slot(b, i, split, j);
+                        ps[0] = (sm[j] > 0.f) ? mx[j] : -INFINITY;
+                        ps[1] = sm[j];
+                    }
+                }
+            }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
             if (lane == 0 && ncand) atomicAdd(&b.stats->candidates, ncand);
@@ -535,9 +566,60 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     }
 }
 
-size_t tc_scratch_bytes(long long n_pad) {
-    return (size_t)n_pad * sizeof(float) + 2 * (size_t)(n_pad / 128) * sizeof(float) + 1024;
+// Combines the split states of every row and applies the multi-scale combination.
+template <int N>
+__device__ __forceinline__ void tc_merge_body(const Consts<float>& k, const Bufs<float>& b, int nsplit, int bid, int nblk) {
+    if (nsplit <= 1) return;
+    for (long long i = bid * (long long)blockDim.x + threadIdx.x; i < k.n; i += (long long)nblk * blockDim.x) {
+        if (b.mask[i]) { b.logw_pred[i] = -INFINITY; continue; }
+        float mx[N], sm[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            float m = -INFINITY, s = 0.f;
+            for (int q = 0; q < nsplit; ++q) {
+                const float* ps = part_slot(b, i, q, j);
+                const float m2 = ps[0], s2 = ps[1];
+                if (m2 == -INFINITY) continue;
+                if (m == -INFINITY) { m = m2; s = s2; }
+                else if (m2 > m) { s = s * expf(m - m2) + s2; m = m2; }
+                else s += s2 * expf(m2 - m);
+            }
+            mx[j] = m;
+            sm[j] = s;
+        }
+        b.logw_pred[i] = combine_scales<float, N>(k, mx, sm, b.divf[i], b.logw[i], b.stats->c_ref, &b.stats->clamps);
+    }
 }
+
+template <int N>
+__global__ void k_tc_merge(Consts<float> k, Bufs<float> b, int nsplit) { tc_merge_body<N>(k, b, nsplit, blockIdx.x, gridDim.x); }
+
+template <int N>
+__global__ void kb_tc_merge(const Traj<float>* __restrict__ tr) {
+    const Traj<float>& t = tr[blockIdx.y];
+    if (t.path != 0) return;
+    tc_merge_body<N>(t.k, t.b, t.b.tc_splits, blockIdx.x, gridDim.x);
+}
+
+size_t tc_scratch_bytes(long long n_pad) {
+    return (size_t)n_pad * sizeof(float) + 2 * (size_t)(n_pad / 128) * sizeof(float) +
+           (size_t)n_pad * kMaxSplit * kMaxScales * 2 * sizeof(float) + 2048;
+}
+
+// Split count of a single filter's prediction: minimises the makespan
+// ceil(tiles * S / grid) * (source tiles / S + overhead) over S = 1..8.
+int tc_choose_splits(long long tiles, int nst, int grid) {
+    int best = 1;
+    double best_t = INFINITY;
+    for (int S = 1; S <= kMaxSplit && S <= nst; ++S) {
+        const double waves = (double)((tiles * S + grid - 1) / grid);
+        const double t = waves * ((double)nst / S + 2.0);
+        if (t < best_t - 1e-9) { best_t = t; best = S; }
+    }
+    return best;
+}
+
+int tc_max_split() { return kMaxSplit; }
 
 namespace {
 
@@ -571,6 +653,7 @@ cudaError_t set_attr_all() {
 template <int BN>
 cudaError_t launch_bn(int N, unsigned grid, const CUtensorMap& a, const CUtensorMap& bm, const Consts<float>& k,
                       const Bufs<float>& b, const TcWork& w, cudaStream_t s) {
+    if (grid == 0) return cudaSuccess;
     const int sm = tc::Cfg<BN>::SMEM_BYTES;
     switch (N) {
         case 1: k_ksum_tc<1, BN><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
@@ -606,8 +689,10 @@ cudaError_t prepare_ksum_tc() {
     return e;
 }
 
+// Single filter: the work list (items, cta_start) was built by the handle
+// (yy_api.cu::build_tc_schedule) in the filter's workspace; nsplit source splits.
 cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s, int* launches) {
-    if (!b.ubf || k.n_pad % 256 != 0 || k.r_pad % tc::BK != 0) return cudaErrorInvalidValue;
+    if (!b.ubf || !b.tc_items || k.n_pad % 256 != 0 || k.r_pad % tc::BK != 0) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
     if (!make_tc_map(&ma, b.ubf, k.n_pad, k.r_pad, tc::BM) || !make_tc_map(&mb, b.ubf, k.n_pad, k.r_pad, 256))
         return cudaErrorNotSupported;
@@ -615,16 +700,28 @@ cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStr
     if (e != cudaSuccess) return e;
     k_tc_colprep<<<(unsigned)(k.n_pad / 128), 128, 0, s>>>(k, b);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const TcWork w{nullptr, nullptr, nullptr, nullptr};
-    e = launch_bn<256>(k.N, (unsigned)(k.n_pad / tc::BM), ma, mb, k, b, w, s);
-    if (launches) *launches += 2;
-    return e;
+    const TcWork w{nullptr, nullptr, b.tc_items, b.tc_cta_start};
+    e = launch_bn<256>(k.N, (unsigned)b.tc_grid, ma, mb, k, b, w, s);
+    if (e != cudaSuccess) return e;
+    int l = 2;
+    if (b.tc_splits > 1) {
+        const unsigned g = (unsigned)std::min<long long>((k.n + 255) / 256, 1024);
+        switch (k.N) {
+            case 1: k_tc_merge<1><<<g, 256, 0, s>>>(k, b, b.tc_splits); break;
+            case 2: k_tc_merge<2><<<g, 256, 0, s>>>(k, b, b.tc_splits); break;
+            case 3: k_tc_merge<3><<<g, 256, 0, s>>>(k, b, b.tc_splits); break;
+            case 4: k_tc_merge<4><<<g, 256, 0, s>>>(k, b, b.tc_splits); break;
+        }
+        l += 1;
+    }
+    if (launches) *launches += l;
+    return cudaGetLastError();
 }
 
 // Batched prediction: column preparation for every filter, then one persistent launch
 // over the precomputed item lists.  bn selects the source-tile width (256 or 128).
 cudaError_t launch_ksum_tc_batch(const Traj<float>* d_traj, int B, int N, long long n_pad_max,
-                                 const void* d_maps, const int2* d_items, const int* d_cta_start,
+                                 const void* d_maps, const int4* d_items, const int* d_cta_start,
                                  int grid, int bn, const Consts<float>& k_any, const Bufs<float>& b_any,
                                  const void* map_any_v, cudaStream_t s, int* launches) {
     kb_tc_colprep<<<dim3((unsigned)(n_pad_max / 128), B), 128, 0, s>>>(d_traj);
@@ -634,8 +731,16 @@ cudaError_t launch_ksum_tc_batch(const Traj<float>* d_traj, int B, int N, long l
     const TcWork w{d_traj, static_cast<const CUtensorMap*>(d_maps), d_items, d_cta_start};
     e = (bn == 128) ? launch_bn<128>(N, (unsigned)grid, map_any, map_any, k_any, b_any, w, s)
                     : launch_bn<256>(N, (unsigned)grid, map_any, map_any, k_any, b_any, w, s);
-    if (launches) *launches += 2;
-    return e;
+    if (e != cudaSuccess) return e;
+    const dim3 mg((unsigned)std::min<long long>((n_pad_max + 255) / 256, 256), B);
+    switch (N) {
+        case 1: kb_tc_merge<1><<<mg, 256, 0, s>>>(d_traj); break;
+        case 2: kb_tc_merge<2><<<mg, 256, 0, s>>>(d_traj); break;
+        case 3: kb_tc_merge<3><<<mg, 256, 0, s>>>(d_traj); break;
+        case 4: kb_tc_merge<4><<<mg, 256, 0, s>>>(d_traj); break;
+    }
+    if (launches) *launches += 3;
+    return cudaGetLastError();
 }
 
 }  // namespace yy
