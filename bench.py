@@ -35,6 +35,10 @@ from synth import WORKLOADS, simulate, sobol_poly_params, sobol_scramble_params 
 from synth.configs import batched_workloads  # noqa: E402
 
 DEFAULT_WORKLOAD = "cubic_r1000_n65536"
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the prediction
+# kernel, from one ncu capture of the workload (profiles/k_ksum_tc_cubic_r1000_n65536.md).
+# An entry is removed whenever the kernel changes after its capture.
+NCU_TRAFFIC = {("cubic_r1000_n65536", "bf16"): 2222.489e6 + 13.444e6}
 METRIC = "filter steps/s & kernel pair-evals/s at r=1000: mixed vs FP32, same RMSE"
 
 
@@ -255,7 +259,8 @@ def run_yy(args):
                 "h2d_bytes_per_step": 8 * w.r, "d2h_bytes_per_step": 8 * (2 * w.r + 2) + 56},
         "gpu_launches": int(launches),
         "roofline": {"bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "frac": round(achieved / peak, 4),
+                     "traffic": NCU_TRAFFIC.get((w.name, prec)),
                      "kernel": "prediction (kernel sum)", "kernel_ms": round(pred_ms, 4),
                      "peak_source": peak_note},
     }
