@@ -38,7 +38,7 @@ DEFAULT_WORKLOAD = "cubic_r1000_n65536"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the prediction
 # kernel, from one ncu capture of the workload (profiles/k_ksum_tc_cubic_r1000_n65536.md).
 # An entry is removed whenever the kernel changes after its capture.
-NCU_TRAFFIC = {("cubic_r1000_n65536", "bf16"): 2222.489e6 + 13.444e6}
+NCU_TRAFFIC: dict = {}
 METRIC = "filter steps/s & kernel pair-evals/s at r=1000: mixed vs FP32, same RMSE"
 
 
@@ -117,19 +117,22 @@ def _dist():
     return rank, ws, local, dist
 
 
-def _make_filter(w, precision, seed, device, stream=None):
+def _make_filter(w, precision, seed, device, stream=None, screen_prefix=0):
     from paper_2509_16896_gb300 import binding
-    cfg = binding.config_from_workload(w, precision=precision)
+    cfg = binding.config_from_workload(w, precision=precision, screen_prefix=screen_prefix)
     flt = binding.Filter(cfg, device=device, stream=stream)
     flt.init_nodes(sobol_poly_params(w.r, seed), sobol_scramble_params(w.r, seed), np.zeros(w.r))
     return flt
 
 
-def _algorithmic_flops(w, precision):
-    """Per prediction launch: BF16 path -> the Gram screen U U^T (2 n^2 r flops);
+def _algorithmic_flops(w, precision, screen=None):
+    """Per prediction launch: BF16 path -> the Gram products of the screen, 2 n^2 (64 k)
+    flops for the first pass over the first 64 k coordinates plus 2 n^2 r for the fraction
+    of tiles screened again over all coordinates (screen = (k, tiles, rescreened));
     FP32/FP64 path -> difference form, 3 flops per coordinate per pair."""
     if precision == "bf16":
-        return 2.0 * w.n * w.n * w.r, "tensor"
+        k, tiles, resc = screen
+        return 2.0 * w.n * w.n * (min(64 * k, w.r) + w.r * resc / max(tiles, 1)), "tensor"
     return 3.0 * w.n * w.n * w.r, "alu"
 
 
@@ -149,7 +152,7 @@ def run_yy(args):
     W, K = args.warmup, args.steps
     tr = simulate(w.model, w.r, W + K, w.dt, seed=seed)
     stream = torch.cuda.Stream(device)
-    flt = _make_filter(w, prec, seed, device, stream)
+    flt = _make_filter(w, prec, seed, device, stream, screen_prefix=args.screen_prefix)
     dys = torch.tensor(tr.dy, dtype=torch.float64, device=device)
     hist = torch.zeros((K, 2 * w.r + 4), dtype=torch.float64, device=device)
     with torch.cuda.stream(stream):
@@ -184,7 +187,6 @@ def run_yy(args):
     restarts = int(h[:, 2 * w.r + 3].sum())
     mean, var, ess, z = flt.estimate()
     # ---- dominant kernel: prediction launches timed alone on the filter's stream ----
-    flops, bound = _algorithmic_flops(w, prec)
     n_pred = max(3, min(20, K))
     pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -194,6 +196,12 @@ def run_yy(args):
     pe1.record(stream)
     torch.cuda.synchronize()
     pred_ms = pe0.elapsed_time(pe1) / n_pred
+    screen = None
+    if prec == "bf16":
+        last, nxt, tiles, resc = flt.screen()
+        screen = {"first_pass_chunks": last, "chunks": (w.r + 63) // 64, "tiles": tiles,
+                  "rescreened": resc, "exact_pairs": flt.counters()[1]}
+    flops, bound = _algorithmic_flops(w, prec, None if screen is None else (last, tiles, resc))
     with torch.cuda.stream(stream):
         flt.update(dys[0])   # leave the handle in a consistent state
     # ---- end to end through the C ABI with host buffers ---------------------------
@@ -258,6 +266,7 @@ def run_yy(args):
         "e2e": {"value": round(e2e_val, 4), "unit": "filter steps/s",
                 "h2d_bytes_per_step": 8 * w.r, "d2h_bytes_per_step": 8 * (2 * w.r + 2) + 56},
         "gpu_launches": int(launches),
+        "screen": screen,
         "roofline": {"bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4),
                      "traffic": NCU_TRAFFIC.get((w.name, prec)),
@@ -479,6 +488,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mlp-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--screen-prefix", type=int, default=0,
+                    help="BF16 screen: first-pass coordinate chunks of 64 (0 = chosen on the device)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "yy":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)

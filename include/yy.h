@@ -110,6 +110,12 @@ typedef struct {
     double prior_mean;         /* x_0 ~ N(prior_mean, prior_var I) */
     double prior_var;          /* > 0 */
     int32_t restart_rule;      /* yy_restart_rule */
+    int32_t screen_prefix;     /* YY_PREC_BF16 only: coordinates of the first screening pass
+                                * of the prediction, in units of 64 (see yy_predict); 0 =
+                                * chosen on the device from the previous predictions
+                                * (default), k >= 1 = fixed (values >= ceil(r/64) give one
+                                * full-coordinate pass), < 0 invalid. Results do not depend
+                                * on it beyond float32 rounding. */
 } yy_config;
 
 /* Bytes of device workspace that yy_create needs for cfg (0 if cfg is invalid). */
@@ -150,7 +156,13 @@ YY_EXPORT yy_status yy_sobol_bits(yy_filter* f, uint32_t* d_bits, int64_t first,
  *   L_j(i) = log sum_{s unmasked} K_{dt/s_j}(x_i, x_s) w_q e^{ell(s)},
  * K the first-order kernel of eq. kernel, w_q = prod_d 2 R_d / n, c the solution of the
  * generalised Vandermonde system.  Boundary nodes get -inf.  A non-positive combination
- * gives -inf and is counted.  Asynchronous. */
+ * gives -inf and is counted.  Asynchronous.
+ * YY_PREC_BF16: pairs are screened on the tensor cores by a lower bound of |u_i - u_s|
+ * (a BF16 Gram product with a rigorous error bound) and only pairs that can carry more
+ * than e^-20 of a row's sum are evaluated exactly in float32.  The first screening pass
+ * uses the first 64 k coordinates (k = cfg.screen_prefix, or chosen on the device);
+ * |u_i - u_s| restricted to them is still a lower bound.  Tiles in which that pass leaves
+ * many candidates are screened again with all coordinates. */
 YY_EXPORT yy_status yy_predict(yy_filter* f);
 
 /* Correction and estimate (Section 2.2 Online stage and step 4; Section 7):
@@ -349,6 +361,15 @@ YY_EXPORT int64_t yy_launch_count(const yy_filter* f);
  * for BF16 precision, the pairs that passed the screen and were evaluated exactly in
  * float32 (self terms not included).  Synchronises. */
 YY_EXPORT yy_status yy_get_counters(yy_filter* f, int64_t* h_clamps, int64_t* h_exact_pairs);
+
+/* Screen of the last BF16 yy_predict (no counterpart in the paper; work accounting of the
+ * screening passes described at yy_predict): *h_last_prefix = coordinate chunks of 64 of
+ * its first pass (0 before the first prediction), *h_next_prefix = those the next
+ * prediction will use, *h_tiles = 128-target x source-tile blocks screened (256 sources per
+ * tile for a single filter), *h_rescreened = blocks screened again over all coordinates.
+ * Any pointer may be NULL.  YY_ERR_UNSUPPORTED for other precisions.  Synchronises. */
+YY_EXPORT yy_status yy_get_screen(yy_filter* f, int32_t* h_last_prefix, int32_t* h_next_prefix,
+                                  int64_t* h_tiles, int64_t* h_rescreened);
 
 /* Human-readable name of a status code (static storage). */
 YY_EXPORT const char* yy_status_str(yy_status s);

@@ -42,7 +42,7 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_batch_get_routing", "yy_get_box", "yy_set_restart_mlp", "yy_mlp_param_count",
            "yy_mlp_workspace_bytes", "yy_mlp_create", "yy_mlp_destroy", "yy_mlp_set_params",
            "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train",
-           "yy_mlp_set_input_norm")
+           "yy_mlp_set_input_norm", "yy_get_screen")
 
 
 class YYError(RuntimeError):
@@ -58,7 +58,7 @@ class YYConfig(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("restart_interval", ctypes.c_int32),
                 ("ess_frac", ctypes.c_double), ("restart_init", ctypes.c_int32),
                 ("prior_mean", ctypes.c_double), ("prior_var", ctypes.c_double),
-                ("restart_rule", ctypes.c_int32)]
+                ("restart_rule", ctypes.c_int32), ("screen_prefix", ctypes.c_int32)]
 
 
 def _declare(L: ctypes.CDLL) -> None:
@@ -77,6 +77,7 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_get_log_weights": (I32, [P, P, P]),
         "yy_set_state": (I32, [P, P, P, D, I64]),
         "yy_get_state": (I32, [P, P, P, P]),
+        "yy_get_screen": (I32, [P, P, P, P, P]),
         "yy_get_clamps": (I32, [P, P]),
         "yy_launch_count": (I64, [P]),
         "yy_status_str": (ctypes.c_char_p, [I32]),
@@ -151,12 +152,13 @@ def _check(fn: str, code: int) -> None:
 def make_config(model: str, r: int, n: int, dt: float, R: float, n_scales: int,
                 precision: str, restart_interval: int = 0, ess_frac: float = 0.0,
                 model_a: float = -0.5, restart_init: str = "gauss", prior_mean: float = 0.0,
-                prior_var: float = 1.0, restart_rule: str = "plain") -> YYConfig:
+                prior_var: float = 1.0, restart_rule: str = "plain", screen_prefix: int = 0) -> YYConfig:
     return YYConfig(r=r, m=r, n=n, dt=dt, R=R, n_scales=n_scales, model=MODELS[model],
                     model_a=model_a, precision=PRECISIONS[precision],
                     restart_interval=restart_interval, ess_frac=ess_frac,
                     restart_init=RESTART_INIT[restart_init], prior_mean=prior_mean,
-                    prior_var=prior_var, restart_rule=RESTART_RULE[restart_rule])
+                    prior_var=prior_var, restart_rule=RESTART_RULE[restart_rule],
+                    screen_prefix=screen_prefix)
 
 
 def config_from_workload(w, precision: str | None = None, **over) -> YYConfig:
@@ -292,6 +294,14 @@ class Filter:
 
     def launches(self) -> int:
         return int(self.lib.yy_launch_count(self.h))
+
+    def screen(self):
+        """(first-pass chunks of the last prediction, of the next one, tiles, tiles
+        rescreened) of the last BF16 prediction."""
+        last, nxt, t, e = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        _check("yy_get_screen", self.lib.yy_get_screen(self.h, ctypes.byref(last), ctypes.byref(nxt),
+                                                       ctypes.byref(t), ctypes.byref(e)))
+        return last.value, nxt.value, t.value, e.value
 
     def counters(self):
         """(clamps, pairs evaluated exactly) of the last prediction."""

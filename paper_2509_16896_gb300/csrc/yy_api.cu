@@ -62,6 +62,7 @@ bool cfg_valid(const yy_config* c) {
     if (c->restart_init != YY_RESTART_INIT_GAUSS && c->restart_init != YY_RESTART_INIT_UNIFORM) return false;
     if (!(c->ess_frac >= 0.0) || c->ess_frac > 1.0) return false;
     if (c->restart_rule != YY_RESTART_PLAIN && c->restart_rule != YY_RESTART_LEARNED) return false;
+    if (c->screen_prefix < 0) return false;
     return true;
 }
 
@@ -109,9 +110,12 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.part = cv.take<double>(part_bytes(r_pad));
     b.stats = cv.take<DevStats>(sizeof(DevStats));
     if (c->precision == YY_PREC_BF16) {
+        b.nu_chunk = cv.take<float>((size_t)n_pad * (r_pad / kColAlign) * sizeof(float));
         b.tc_q = cv.take<float>((size_t)n_pad * sizeof(float));
+        b.tc_q1 = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_tile_lmax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
         b.tc_tile_numax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
+        b.tc_tile_numax1 = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
         b.tc_part = cv.take<float>((size_t)n_pad * 8 * kMaxScales * 2 * sizeof(float));
         b.tc_items = cv.take<int4>((size_t)(n_pad / 128) * 8 * sizeof(int4));
         b.tc_cta_start = cv.take<int>((size_t)(kMaxTcGrid + 1) * sizeof(int));
@@ -164,6 +168,7 @@ void fill_consts(yy_filter* f, Consts<T>* k, const double* halfwidth) {
     k->N = c.n_scales;
     k->model = c.model;
     k->model_a = (T)c.model_a;
+    k->tc_prefix = c.screen_prefix > 0 ? c.screen_prefix : 0;
     k->dt = (T)c.dt;
     double log_vol = 0.0;
     for (int d = 0; d < c.r; ++d) log_vol += log(2.0 * (halfwidth ? halfwidth[d] : c.R));
@@ -196,7 +201,10 @@ __global__ void k_set_stats(DevStats* st, double lognorm, long long step) {
     st->step = step;
 }
 
-__global__ void k_init_cref(DevStats* st, double c_ref) { st->c_ref = c_ref; }
+__global__ void k_init_cref(DevStats* st, double c_ref) {
+    st->c_ref = c_ref;
+    st->tc_t0 = ~0ull;   // no prediction launch running
+}
 
 template <typename T>
 yy_status do_init_nodes(yy_filter* f, Bufs<T>& b, Consts<T>& k, const uint32_t* h_poly,
@@ -568,6 +576,24 @@ yy_status yy_get_counters(yy_filter* f, int64_t* h_clamps, int64_t* h_exact_pair
     if (e != cudaSuccess) return YY_ERR_CUDA;
     if (h_clamps) *h_clamps = hs.clamps;
     if (h_exact_pairs) *h_exact_pairs = (int64_t)hs.candidates;
+    return YY_OK;
+}
+
+yy_status yy_get_screen(yy_filter* f, int32_t* h_last_prefix, int32_t* h_next_prefix, int64_t* h_tiles,
+                        int64_t* h_rescreened) {
+    if (!f) return YY_ERR_ARG;
+    if (f->cfg.precision != YY_PREC_BF16) return YY_ERR_UNSUPPORTED;
+    DevStats hs;
+    cudaError_t e = cudaMemcpyAsync(&hs, f->bf.stats, sizeof(DevStats), cudaMemcpyDeviceToHost, f->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    const int nk = f->r_pad / kColAlign;
+    int v = f->cfg.screen_prefix > 0 ? f->cfg.screen_prefix : hs.tc_nk1;
+    if (v <= 0) v = (nk + 3) / 4;
+    if (h_last_prefix) *h_last_prefix = hs.tc_last_nk1;
+    if (h_next_prefix) *h_next_prefix = std::max(1, std::min(v, nk));
+    if (h_tiles) *h_tiles = (int64_t)hs.tc_last_blk;
+    if (h_rescreened) *h_rescreened = (int64_t)hs.tc_last_esc;
     return YY_OK;
 }
 

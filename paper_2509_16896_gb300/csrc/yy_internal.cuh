@@ -40,6 +40,18 @@ struct DevStats {
     int last_restarted;  // 1 if the last yy_restart call re-centred the box
     int scale_changed;   // 1 while a restart re-maps the nodes to new half-widths
     double c_ref;        // offset of the predicted log-weights (moves with the box volume)
+    // BF16 screen: coordinate chunks (of 64) of the first screening pass and its controller
+    int tc_nk1;          // 0 = not chosen yet
+    int tc_streak;       // consecutive clean predictions (batch members)
+    int tc_from;         // first-pass length of the prediction before the last one
+    float tc_time[YY_MAX_DIM / 64 + 1];   // last launch time (ns) per first-pass length, 0 = none
+    int tc_age[YY_MAX_DIM / 64 + 1];      // predictions since that time was taken (< 0: known slow)
+    unsigned long long tc_t0;    // earliest CTA start of the running launch (%globaltimer)
+    unsigned long long tc_blk;   // tiles screened by the last prediction
+    unsigned long long tc_esc;   // of which rescreened with all coordinates
+    unsigned long long tc_last_blk, tc_last_esc;   // the same, kept for the host
+    int tc_last_nk1;             // first-pass chunks the last prediction used
+    unsigned int tc_done;        // CTAs of the running prediction launch that finished
 };
 
 // Constants of one filter handed to kernels by value.
@@ -54,6 +66,7 @@ struct Consts {
     T tau[kMaxScales];
     T inv2tau[kMaxScales];   // 1 / (2 tau_j)
     T cj_off[kMaxScales];    // C_j - C_ref, C_j = -(r/2) log(2 pi tau_j) + log w_q
+    int tc_prefix;           // fixed first-pass chunks of the BF16 screen (0 = adaptive)
     T logabs_c[kMaxScales + 1];
     T sign_c[kMaxScales + 1];  // 0 for a zero coefficient
     double c_ref;
@@ -86,9 +99,12 @@ struct Bufs {
     double* part;         // reduction partials
     DevStats* stats;
     // BF16 path scratch
+    float* nu_chunk;      // [n_pad][r_pad / 64] |u_i|^2 per chunk of 64 coordinates (BF16 only)
     float* tc_q;          // [n_pad] |u_s|^2 of live sources, 3e38 for dead ones
+    float* tc_q1;         // [n_pad] the same over the first-pass coordinates
     float* tc_tile_lmax;  // [n_pad / 128] max live log-weight per chunk of 128 sources
     float* tc_tile_numax; // [n_pad / 128] max |u_s|^2 per chunk of 128 sources
+    float* tc_tile_numax1;// [n_pad / 128] the same over the first-pass coordinates
     float* tc_part;       // [n_pad][8][4][2] partial (max, sum) of split work items
     int4* tc_items;       // single-filter work list (target tile, split, nsplit)
     int* tc_cta_start;    // [tc_grid + 1]

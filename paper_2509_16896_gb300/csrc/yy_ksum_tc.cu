@@ -55,13 +55,15 @@ namespace tc {
 constexpr int BM = 128;      // targets per item (UMMA M)
 constexpr int BK = 64;       // coordinates per stage: 64 bf16 = one 128-byte swizzle row
 constexpr int UK = 16;       // K of one tcgen05.mma kind::f16
-constexpr int NUM_THREADS = 192;
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each on half of a tile's columns
+constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
 constexpr float kEpsGram = 0.015625f;   // 2^-6
 constexpr float kDeadQ = 3.0e38f;
 constexpr float kThetaMax = 1.0e30f;
+constexpr int kEscWords = 32;    // per epilogue warp and parity: marks of up to 1024 source tiles
+constexpr int kEscThresh = 16;   // candidates of one warp in one tile above which it is rescreened
 
 // Shape-dependent constants.  BN = 256: 4 stages, 512 TMEM columns, one CTA per SM.
 // BN = 128: 3 stages (96 KB), 256 TMEM columns, so two CTAs fit on one SM.
@@ -71,7 +73,11 @@ struct Cfg {
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators of BN fp32 columns
-    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + EPI_WARPS * BN * 4 + 256;
+    static constexpr int HALF = BN / 2;   // columns of one epilogue warp
+    // ring | q values and candidate masks per epilogue warp | marking bitmaps | row states
+    // exchanged between the two warps of a lane quarter | barriers
+    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 2 * EPI_WARPS * HALF * 4 +
+                                      EPI_WARPS * 2 * kEscWords * 4 + 128 * kMaxScales * 2 * 4 + 256;
     // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1),
     // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -193,6 +199,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "r"(taddr)
         : "memory");
 }
+__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]),
+          "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]),
+          "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]),
+          "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]),
+          "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
+        : "r"(taddr)
+        : "memory");
+}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Screening threshold on |u_s|^2 - 2 G for one target row (see the file comment).
@@ -213,31 +238,56 @@ __device__ __forceinline__ float screen_theta(const Consts<float>& k, bool live,
 
 }  // namespace
 
-// Per source chunk of 128: |u_s|^2 of live sources (kDeadQ for masked, padded or -inf
-// ones), the largest live log-weight and the largest live |u_s|^2.
+// First-pass coordinate chunks (of 64) of one filter's screen: fixed by the configuration,
+// else the controller's last choice (tc_adapt), else a quarter of the coordinates.
+__device__ __forceinline__ int prefix_chunks(const Consts<float>& k, const DevStats* st) {
+    const int nk = k.r_pad / tc::BK;
+    int v = k.tc_prefix > 0 ? k.tc_prefix : st->tc_nk1;
+    if (v <= 0) v = (nk + 3) / 4;
+    return v < 1 ? 1 : (v > nk ? nk : v);
+}
+
+// Per source chunk of 128: |u_s|^2 of live sources over all coordinates (tc_q) and over the
+// first-pass coordinates (tc_q1), kDeadQ for masked, padded or -inf ones; the largest live
+// log-weight; the largest live value of each kind of |u_s|^2.
 __device__ __forceinline__ void colprep_body(const Consts<float>& k, const Bufs<float>& b, int chunk) {
-    __shared__ float red_l[4], red_n[4];
+    __shared__ float red_l[4], red_n[4], red_n1[4];
     const long long s = (long long)chunk * 128 + threadIdx.x;
-    float lw = -INFINITY, nu = 0.f;
+    const int nkc = k.r_pad / tc::BK;
+    const int nk1 = prefix_chunks(k, b.stats);
+    float lw = -INFINITY, nu = 0.f, nu1 = 0.f;
     bool live = false;
     if (s < k.n) {
         lw = b.logw[s];
         nu = b.nu[s];
+        const float* nc = b.nu_chunk + (size_t)s * nkc;
+        for (int c = 0; c < nk1; ++c) nu1 += nc[c];
         live = !b.mask[s] && lw != -INFINITY;
     }
     b.tc_q[s] = live ? nu : tc::kDeadQ;
-    float lm = live ? lw : -INFINITY, nm = live ? nu : 0.f;
+    b.tc_q1[s] = live ? nu1 : tc::kDeadQ;
+    float lm = live ? lw : -INFINITY, nm = live ? nu : 0.f, nm1 = live ? nu1 : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         lm = fmaxf(lm, __shfl_xor_sync(0xffffffffu, lm, o));
         nm = fmaxf(nm, __shfl_xor_sync(0xffffffffu, nm, o));
+        nm1 = fmaxf(nm1, __shfl_xor_sync(0xffffffffu, nm1, o));
     }
-    if ((threadIdx.x & 31) == 0) { red_l[threadIdx.x >> 5] = lm; red_n[threadIdx.x >> 5] = nm; }
+    if ((threadIdx.x & 31) == 0) {
+        red_l[threadIdx.x >> 5] = lm;
+        red_n[threadIdx.x >> 5] = nm;
+        red_n1[threadIdx.x >> 5] = nm1;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int w = 1; w < 4; ++w) { lm = fmaxf(lm, red_l[w]); nm = fmaxf(nm, red_n[w]); }
+        for (int w = 1; w < 4; ++w) {
+            lm = fmaxf(lm, red_l[w]);
+            nm = fmaxf(nm, red_n[w]);
+            nm1 = fmaxf(nm1, red_n1[w]);
+        }
         b.tc_tile_lmax[chunk] = lm;
         b.tc_tile_numax[chunk] = nm;
+        b.tc_tile_numax1[chunk] = nm1;
     }
 }
 
@@ -249,16 +299,87 @@ __global__ void __launch_bounds__(128) kb_tc_colprep(const Traj<float>* __restri
     colprep_body(t.k, t.b, blockIdx.x);
 }
 
+// Controller of the first-pass length, run once per prediction launch and filter (by the
+// last CTA to finish).  The work beyond the first pass, in chunks per tile, is
+//     extra = (rescreened tiles x all chunks + exact pair evaluations x r / 4096) / tiles
+// (an exact pair costs about r / 4096 of the tensor time of one chunk of one tile); a
+// prediction is clean when it had neither.
+//  - extra > 1: the first pass was much too short -- lengthen it at once (by 2 if extra > 4)
+//    and hold the short length off for 1024 predictions.
+//  - single filter (launch time dt_ns known): the latest launch time per length is kept
+//    for 64 predictions; move to a neighbouring length measured faster, else probe a
+//    neighbour without a recent time -- one chunk longer after a prediction that was not
+//    clean, one shorter after four clean ones in a row at this length (candidates grow
+//    steeply as the first pass shortens, and the weights of the first steps spread out
+//    fast, so a length is only shortened from a settled clean one).  A length that came
+//    out more than twice as slow as the one before it is held off for 1024 predictions.
+//  - batch member (dt_ns < 0, the launch is shared): one chunk shorter after two clean
+//    predictions in a row, unless the shorter length is held off.
+__device__ void tc_adapt(const Consts<float>& k, DevStats* st, double dt_ns) {
+    const unsigned long long blk = atomicExch(&st->tc_blk, 0ull);
+    const unsigned long long esc = atomicExch(&st->tc_esc, 0ull);
+    const unsigned long long cand = atomicAdd(&st->candidates, 0ull);
+    const int nk1 = prefix_chunks(k, st);
+    st->tc_last_blk = blk;
+    st->tc_last_esc = esc;
+    st->tc_last_nk1 = nk1;
+    if (k.tc_prefix > 0 || blk == 0) return;
+    const int nk = k.r_pad / tc::BK;
+    constexpr int kFresh = 64, kHold = 1024;
+    for (int x = 1; x <= nk; ++x)
+        if (st->tc_age[x] < (1 << 30)) ++st->tc_age[x];
+    const int from = st->tc_from;
+    st->tc_from = nk1;
+    const double extra = ((double)esc * nk + (double)cand * k.r / 4096.0) / (double)blk;
+    const bool clean = esc == 0 && cand == 0;
+    if (dt_ns >= 0.0) st->tc_time[nk1] = (float)dt_ns;
+    if (extra > 1.0 && nk1 < nk) {
+        st->tc_age[nk1] = -kHold;
+        st->tc_streak = 0;
+        st->tc_nk1 = min(nk, nk1 + (extra > 4.0 ? 2 : 1));
+        return;
+    }
+    if (dt_ns < 0.0) {   // batch member
+        int next = nk1;
+        if (!clean) {
+            st->tc_streak = 0;
+        } else if (++st->tc_streak >= 2) {
+            st->tc_streak = 0;
+            if (nk1 > 1 && st->tc_age[nk1 - 1] >= 0) next = nk1 - 1;
+        }
+        st->tc_nk1 = next;
+        return;
+    }
+    st->tc_age[nk1] = 0;
+    st->tc_streak = (from == nk1 && clean) ? st->tc_streak + 1 : (clean ? 1 : 0);
+    if (from >= 1 && from <= nk && from != nk1 && st->tc_time[from] > 0.f && dt_ns > 2.0 * st->tc_time[from]) {
+        st->tc_age[nk1] = -kHold;   // keeps its (slow) time
+        st->tc_nk1 = from;
+        return;
+    }
+    auto known = [&](int x) { return st->tc_time[x] > 0.f && st->tc_age[x] < kFresh; };
+    auto held = [&](int x) { return st->tc_age[x] < 0; };
+    int best = nk1;
+    if (nk1 < nk && known(nk1 + 1) && st->tc_time[nk1 + 1] < st->tc_time[best]) best = nk1 + 1;
+    if (nk1 > 1 && known(nk1 - 1) && st->tc_time[nk1 - 1] < st->tc_time[best]) best = nk1 - 1;
+    if (best == nk1) {
+        if (!clean && nk1 < nk && !known(nk1 + 1) && !held(nk1 + 1)) best = nk1 + 1;
+        else if (st->tc_streak >= 4 && nk1 > 1 && !known(nk1 - 1) && !held(nk1 - 1)) best = nk1 - 1;
+    }
+    st->tc_nk1 = best;
+}
+
 // Work list of a launch: CTA c processes items[cta_start[c] .. cta_start[c + 1]), each
 // (filter, target tile, split, nsplit): target rows 128 tile .. +127 against source tiles
 // [nst split / nsplit, nst (split + 1) / nsplit).  tr == nullptr: single filter, passed by
-// value with its TMA maps; otherwise descriptors tr[filter] and TMA maps maps[2 filter]
-// (A, 128-row box) and maps[2 filter + 1] (B, BN-row box).
+// value with its TMA maps; otherwise descriptors tr[filter] (nb filters) and TMA maps
+// maps[2 filter] (A, 128-row box) and maps[2 filter + 1] (B, BN-row box).
 struct TcWork {
     const Traj<float>* tr;
     const CUtensorMap* maps;
     const int4* items;
     const int* cta_start;
+    int nb;
 };
 
 constexpr int kMaxSplit = 8;
@@ -268,6 +389,13 @@ __device__ __forceinline__ float* part_slot(const Bufs<float>& b, long long i, i
     return b.tc_part + (((size_t)i * kMaxSplit + split) * kMaxScales + j) * 2;
 }
 
+// Two-pass screen of one item.  Pass 1 runs the Gram product over the first nk1 of nk
+// coordinate chunks only: restricted to them, |u_i - u_s| is still a lower bound of the full
+// distance, so the same test (with the restricted norms) rejects pairs rigorously.  An
+// epilogue warp whose 32 rows keep more than kEscThresh candidates in a tile marks the tile
+// for pass 2 instead of evaluating them; after pass 1 of the item the three roles meet at
+// an mbarrier, and pass 2 recomputes the marked tiles over all coordinates and screens them
+// again (only the marking warps use the result).  With nk1 = nk there is one pass.
 template <int N, int BN>
 __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     k_ksum_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -276,16 +404,24 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     using C = Cfg<BN>;
     constexpr int STAGES = C::STAGES;
     constexpr int STAGE_BYTES = C::STAGE_BYTES;
+    constexpr int NCH = BN / 32;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    float* qs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
-    uint64_t* bars = reinterpret_cast<uint64_t*>(qs + EPI_WARPS * BN);
+    constexpr int HALF = C::HALF;
+    float* qs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);   // [EPI_WARPS][HALF]
+    uint32_t* cms = reinterpret_cast<uint32_t*>(qs + EPI_WARPS * HALF);  // [EPI_WARPS][HALF / 32][32]
+    uint32_t* escm = cms + EPI_WARPS * HALF;                             // [EPI_WARPS][2][kEscWords]
+    float* xch = reinterpret_cast<float*>(escm + EPI_WARPS * 2 * kEscWords);   // [128 rows][kMaxScales][2]
+    uint64_t* bars = reinterpret_cast<uint64_t*>(xch + 128 * kMaxScales * 2);
     uint64_t* full = bars;
     uint64_t* empty = bars + STAGES;
     uint64_t* tfull = bars + 2 * STAGES;
     uint64_t* tempty = tfull + 2;
     uint64_t* drain = tempty + 2;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* escb = drain + 1;
+    uint64_t* xfull = escb + 1;    // [4]: the second warp of lane quarter q stored its row states
+    uint64_t* xfree = xfull + 4;   // [4]: the first warp of lane quarter q has read them
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xfree + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -296,10 +432,14 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     unsigned int* status = (it_end <= it_begin) ? nullptr
                            : batched ? &w.tr[w.items[it_begin].x].b.stats->status : &b0.stats->status;
 
+    DevStats* const ctr = batched ? w.tr[0].b.stats : b0.stats;   // launch-wide counters
     if (threadIdx.x == 0) {
+        atomicMin(&ctr->tc_t0, globaltimer());
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], EPI_WARPS); }
         mbar_init(drain, 1);
+        mbar_init(escb, EPI_WARPS);
+        for (int a = 0; a < 4; ++a) { mbar_init(&xfull[a], 1); mbar_init(&xfree[a], 1); }
         *abort_flag = 0;
         mbar_fence_init();
     }
@@ -312,9 +452,12 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    // per-item view: descriptors, maps, first target row, source tile range, split
+    // per-item view: descriptors, maps, first target row, source tile range, split, chunks
+    // of all coordinates (nk) and of the first pass (nk1; nk when the range does not fit
+    // the marking bitmaps)
     auto item_kb = [&](int idx, const Consts<float>*& kp, const Bufs<float>*& bp, const CUtensorMap*& ma,
-                       const CUtensorMap*& mb, long long& i0, int& t0, int& t1, int& split, int& nsplit) {
+                       const CUtensorMap*& mb, long long& i0, int& t0, int& t1, int& split, int& nsplit, int& nk,
+                       int& nk1) {
         const int4 it = w.items[idx];
         if (!batched) {
             kp = &k0; bp = &b0; ma = &tmA; mb = &tmB;
@@ -328,6 +471,18 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         const int nst = (int)(kp->n_pad / BN);
         t0 = (int)(((long long)nst * split) / nsplit);
         t1 = (int)(((long long)nst * (split + 1)) / nsplit);
+        nk = kp->r_pad / BK;
+        nk1 = (t1 - t0 <= kEscWords * 32) ? prefix_chunks(*kp, bp->stats) : nk;
+    };
+    // tile j of the item marked by epilogue warp e / by any epilogue warp (bitmap parity par)
+    auto esc_bit = [&](int e, uint32_t par, int j) -> bool {
+        return (escm[(e * 2 + par) * kEscWords + (j >> 5)] >> (j & 31)) & 1u;
+    };
+    auto esc_any = [&](uint32_t par, int j) -> bool {
+        bool m = false;
+#pragma unroll
+        for (int e = 0; e < EPI_WARPS; ++e) m |= esc_bit(e, par, j);
+        return m;
     };
 
     if (warp == 0) {
@@ -335,25 +490,32 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             // ---- TMA producer -------------------------------------------------------
             int last_phase[STAGES];
             for (int s = 0; s < STAGES; ++s) last_phase[s] = -1;
-            uint32_t it = 0;
+            uint32_t it = 0, npre = 0;
             bool ok = true;
+            auto load_tile = [&](const CUtensorMap* ma, const CUtensorMap* mb, long long i0, int t, int nkb) -> bool {
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = (int)(it % STAGES);
+                    const uint32_t ph = (it / STAGES) & 1u;
+                    if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, status)) return false;
+                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
+                    uint8_t* dA = smem + s * STAGE_BYTES;
+                    tma_load_2d(ma, &full[s], dA, kb * BK, (int)i0);
+                    tma_load_2d(mb, &full[s], dA + A_BYTES, kb * BK, t * BN);
+                    last_phase[s] = (int)ph;
+                }
+                return true;
+            };
             for (int idx = it_begin; idx < it_end && ok; ++idx) {
                 const Consts<float>* kp; const Bufs<float>* bp; const CUtensorMap* ma; const CUtensorMap* mb;
                 long long i0;
-                int t0, t1, split, nsplit;
-                item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit);
-                const int nk = kp->r_pad / BK;
-                for (int t = t0; t < t1 && ok; ++t) {
-                    for (int kb = 0; kb < nk; ++kb, ++it) {
-                        const int s = (int)(it % STAGES);
-                        const uint32_t ph = (it / STAGES) & 1u;
-                        if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, status)) { ok = false; break; }
-                        mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
-                        uint8_t* dA = smem + s * STAGE_BYTES;
-                        tma_load_2d(ma, &full[s], dA, kb * BK, (int)i0);
-                        tma_load_2d(mb, &full[s], dA + A_BYTES, kb * BK, t * BN);
-                        last_phase[s] = (int)ph;
-                    }
+                int t0, t1, split, nsplit, nk, nk1;
+                item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit, nk, nk1);
+                for (int t = t0; t < t1 && ok; ++t) ok = load_tile(ma, mb, i0, t, nk1);
+                if (ok && nk1 < nk) {
+                    const uint32_t par = npre++ & 1u;
+                    if (!wait_bounded(escb, par, abort_flag, status)) { ok = false; break; }
+                    for (int t = t0; t < t1 && ok; ++t)
+                        if (esc_any(par, t - t0)) ok = load_tile(ma, mb, i0, t, nk);
                 }
             }
             if (!ok)   // let our own copies land before shared memory is released
@@ -363,34 +525,47 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     } else if (warp == 1) {
         if (lane == 0 && status) {
             // ---- MMA issuer -----------------------------------------------------------
-            uint32_t it = 0, tcount = 0;
+            uint32_t it = 0, tcount = 0, npre = 0;
             bool ok = true;
+            auto mma_tile = [&](int nkb) -> bool {
+                const int acc = (int)(tcount & 1u);
+                const uint32_t aph = (tcount >> 1) & 1u;
+                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) return false;
+                tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < nkb; ++kb, ++it) {
+                    const int s = (int)(it % STAGES);
+                    const uint32_t ph = (it / STAGES) & 1u;
+                    if (!wait_bounded(&full[s], ph, abort_flag, status)) return false;
+                    tc_fence_after();
+                    const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t b0a = a0 + A_BYTES;
+#pragma unroll
+                    for (int kk = 0; kk < BK / UK; ++kk)
+                        mma_bf16(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0a + kk * UK * 2), C::IDESC,
+                                 (kb | kk) != 0 ? 1u : 0u);
+                    mma_commit(&empty[s]);
+                }
+                mma_commit(&tfull[acc]);
+                ++tcount;
+                return true;
+            };
             for (int idx = it_begin; idx < it_end && ok; ++idx) {
                 const Consts<float>* kp; const Bufs<float>* bp; const CUtensorMap* ma; const CUtensorMap* mb;
                 long long i0;
-                int t0, t1, split, nsplit;
-                item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit);
-                const int nk = kp->r_pad / BK;
-                for (int t = t0; t < t1 && ok; ++t, ++tcount) {
-                    const int acc = (int)(tcount & 1u);
-                    const uint32_t aph = (tcount >> 1) & 1u;
-                    if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
-                    for (int kb = 0; kb < nk; ++kb, ++it) {
-                        const int s = (int)(it % STAGES);
-                        const uint32_t ph = (it / STAGES) & 1u;
-                        if (!wait_bounded(&full[s], ph, abort_flag, status)) { ok = false; break; }
-                        tc_fence_after();
-                        const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
-                        const uint32_t b0a = a0 + A_BYTES;
-#pragma unroll
-                        for (int kk = 0; kk < BK / UK; ++kk)
-                            mma_bf16(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0a + kk * UK * 2), C::IDESC,
-                                     (kb | kk) != 0 ? 1u : 0u);
-                        mma_commit(&empty[s]);
-                    }
-                    if (ok) mma_commit(&tfull[acc]);
+                int t0, t1, split, nsplit, nk, nk1;
+                item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit, nk, nk1);
+                for (int t = t0; t < t1 && ok; ++t) ok = mma_tile(nk1);
+                unsigned long long nesc = 0;
+                if (ok && nk1 < nk) {
+                    const uint32_t par = npre++ & 1u;
+                    if (!wait_bounded(escb, par, abort_flag, status)) { ok = false; break; }
+                    for (int t = t0; t < t1 && ok; ++t)
+                        if (esc_any(par, t - t0)) { ok = mma_tile(nk); ++nesc; }
+                }
+                if (ok) {
+                    atomicAdd(&bp->stats->tc_blk, (unsigned long long)(t1 - t0));
+                    if (nesc) atomicAdd(&bp->stats->tc_esc, nesc);
                 }
             }
             // all MMAs issued by this thread have completed once drain fires
@@ -399,28 +574,45 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         }
     } else if (status) {
         // ---- epilogue: screening + exact evaluation --------------------------------------
-        const int q = warp & 3;
-        float* qw = qs + (warp - 2) * BN;
-        uint32_t tcount = 0;
+        // warp pair (q, h): TMEM lane quarter q (its 32 target rows), columns h HALF ..
+        // h HALF + HALF - 1 of every tile; each warp keeps its own online log-sum-exp of its
+        // rows over its columns, and the pair merges them at the end of an item
+        const int ew = warp - 2;       // epilogue warp index 0..7
+        const int q = warp & 3;        // TMEM lane quarter (fixed by the warp's rank in its warpgroup)
+        const int h = ew >> 2;         // column half
+        float* qw = qs + ew * HALF;
+        uint32_t* cmw = cms + ew * HALF;   // candidate masks of one tile, [HALF / 32][32 lanes]
+        float* xrow = xch + (size_t)(q * 32 + lane) * kMaxScales * 2;
+        uint32_t tcount = 0, npre = 0, nitem = 0;
         bool ok = true;
-        for (int idx = it_begin; idx < it_end && ok; ++idx) {
+        for (int idx = it_begin; idx < it_end && ok; ++idx, ++nitem) {
             const Consts<float>* kp; const Bufs<float>* bp; const CUtensorMap* ma; const CUtensorMap* mb;
             long long i0;
-            int t0, t1, split, nsplit;
-            item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit);
+            int t0, t1, split, nsplit, nk, nk1;
+            item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit, nk, nk1);
             const Consts<float>& k = *kp;
             const Bufs<float>& b = *bp;
+            const bool pre = nk1 < nk;
             const float T = logf((float)k.n) + 20.0f;
             const long long i = i0 + q * 32 + lane;
             const bool in_range = i < k.n;
             const bool live = in_range && !b.mask[i];
-            float nu_i = 0.f, nf_i = 0.f, li = -INFINITY;
-            if (in_range) { nu_i = b.nu[i]; nf_i = b.nf[i]; li = b.logw[i]; }
+            float nu_i = 0.f, nu1_i = 0.f, nf_i = 0.f, li = -INFINITY;
+            if (in_range) {
+                nu_i = b.nu[i];
+                nf_i = b.nf[i];
+                li = b.logw[i];
+                if (pre) {   // same summation order as colprep's tc_q1
+                    const float* nc = b.nu_chunk + (size_t)i * nk;
+                    for (int c = 0; c < nk1; ++c) nu1_i += nc[c];
+                }
+            }
             const float Fi = sqrtf(nf_i);
             float rowc[N], mx[N], sm[N];
             // the exact self term (u_i - u_i = 0) is the screening reference of every split
-            // and is counted by the split whose source range holds i
-            const bool self_here = (i / BN) >= t0 && (i / BN) < t1;
+            // and of both halves; it is counted once, by the first half of the split whose
+            // source range holds i
+            const bool self_here = h == 0 && (i / BN) >= t0 && (i / BN) < t1;
 #pragma unroll
             for (int j = 0; j < N; ++j) {
                 rowc[j] = -0.5f * k.tau[j] * nf_i;
@@ -429,39 +621,111 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 sm[j] = (self && self_here) ? 1.f : 0.f;
             }
             unsigned long long ncand = 0;
-            for (int t = t0; t < t1; ++t, ++tcount) {
+            const uint32_t par = npre & 1u;
+            uint32_t* myesc = escm + (ew * 2 + par) * kEscWords;
+            if (pre) {
+                ++npre;
+                for (int wd = lane; wd < kEscWords; wd += 32) myesc[wd] = 0u;
+                __syncwarp();
+            }
+            // one exact score of this lane's row against source src
+            auto add_score = [&](float s1, float s2, long long src) {
+                const float ls = b.mask[src] ? -INFINITY : b.logw[src];
+                if (ls == -INFINITY) return;
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    const float sc = fmaf(-s1, k.inv2tau[j], s2) + (rowc[j] + ls);
+                    if (sc > mx[j]) {
+                        sm[j] = (mx[j] == -INFINITY) ? 1.f : sm[j] * expf(mx[j] - sc) + 1.f;
+                        mx[j] = sc;
+                    } else {
+                        sm[j] += expf(sc - mx[j]);
+                    }
+                }
+            };
+            // long rows: the warp evaluates the candidates of its 32 rows one at a time,
+            // coalesced over the coordinates
+            auto eval_warp = [&](uint32_t cm, long long sb) {
+                while (true) {
+                    const uint32_t who = __ballot_sync(0xffffffffu, cm != 0u);
+                    if (who == 0u) break;
+                    const int leader = __ffs(who) - 1;
+                    const int c = __shfl_sync(0xffffffffu, __ffs(cm) - 1, leader);
+                    const long long src = sb + c;
+                    const long long tgt = i0 + q * 32 + leader;
+                    const float* ut = b.u + (size_t)tgt * k.r_pad;
+                    const float* us = b.u + (size_t)src * k.r_pad;
+                    const float* ft = b.f + (size_t)tgt * k.r_pad;
+                    float s1 = 0.f, s2 = 0.f;
+                    for (int d = lane; d < k.r; d += 32) {
+                        const float dl = ut[d] - us[d];
+                        s1 = fmaf(dl, dl, s1);
+                        s2 = fmaf(dl, ft[d], s2);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                    }
+                    if (lane == leader) {
+                        add_score(s1, s2, src);
+                        cm &= cm - 1u;
+                        ++ncand;
+                    }
+                }
+            };
+            auto release = [&](int acc) {
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[acc]);
+            };
+            // one tile: mode 0 = single full pass, 1 = first pass, 2 = second pass of a tile
+            // this warp marked, 3 = second pass of a tile only other warps marked
+            auto tile = [&](int t, int mode) -> bool {
                 const int acc = (int)(tcount & 1u);
                 const uint32_t aph = (tcount >> 1) & 1u;
-                __syncwarp();
-                for (int c = lane; c < BN; c += 32) qw[c] = b.tc_q[(size_t)t * BN + c];
-                __syncwarp();
-                float lmax = b.tc_tile_lmax[t * (BN / 128)], numax = b.tc_tile_numax[t * (BN / 128)];
-                if (BN == 256) {
-                    lmax = fmaxf(lmax, b.tc_tile_lmax[2 * t + 1]);
-                    numax = fmaxf(numax, b.tc_tile_numax[2 * t + 1]);
-                }
-                float theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
-                if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
-                for (int ch = 0; ch < BN / 32; ++ch) {
-                    uint32_t v[32];
+                ++tcount;
+                float theta = -INFINITY, lmax = -INFINITY, numax = 0.f;
+                const float nu_s = (mode == 1) ? nu1_i : nu_i;
+                const long long c0 = (long long)t * BN + h * HALF;   // first source of this warp
+                if (mode != 3) {
+                    const float* qsrc = (mode == 1) ? b.tc_q1 : b.tc_q;
+                    const float* nmx = (mode == 1) ? b.tc_tile_numax1 : b.tc_tile_numax;
                     __syncwarp();
-                    tmem_ld32(tbase + (uint32_t)(ch * 32), v);
-                    tmem_ld_wait();
-                    uint32_t cm = 0;
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) {
-                        const float dd = fmaf(-2.f, __uint_as_float(v[c]), qw[ch * 32 + c]);
-                        cm |= (dd <= theta ? 1u : 0u) << c;
+                    const float4* src4 = reinterpret_cast<const float4*>(qsrc + c0);
+                    float4* dst4 = reinterpret_cast<float4*>(qw);
+                    for (int c = lane; c < HALF / 4; c += 32) dst4[c] = src4[c];
+                    __syncwarp();
+                    lmax = b.tc_tile_lmax[t * (BN / 128)];
+                    numax = nmx[t * (BN / 128)];
+                    if (BN == 256) {
+                        lmax = fmaxf(lmax, b.tc_tile_lmax[2 * t + 1]);
+                        numax = fmaxf(numax, nmx[2 * t + 1]);
                     }
-                    const long long sb = (long long)t * BN + ch * 32;
-                    if (i >= sb && i < sb + 32) cm &= ~(1u << (int)(i - sb));   // self term already counted
-                    if (k.r <= 64) {
-                        // short rows: every lane evaluates its own row's candidates (its own
-                        // target, the chunk's sources) over the coordinates
-                        const float* ut = b.u + (size_t)i * k.r_pad;
-                        const float* ft = b.f + (size_t)i * k.r_pad;
+                    theta = screen_theta<N>(k, live, nu_s, Fi, mx, lmax, numax, T);
+                }
+                if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) return false;
+                tc_fence_after();
+                if (mode == 3) { release(acc); return true; }
+                const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + h * HALF);
+                if (k.r <= 64) {
+                    // short rows (one pass): every lane evaluates its own row's candidates
+                    // chunk by chunk, tightening the screen as the running maxima grow
+                    const float* ut = b.u + (size_t)i * k.r_pad;
+                    const float* ft = b.f + (size_t)i * k.r_pad;
+                    for (int ch = 0; ch < HALF / 32; ++ch) {
+                        uint32_t v[32];
+                        __syncwarp();
+                        tmem_ld32(tbase + (uint32_t)(ch * 32), v);
+                        tmem_ld_wait();
+                        uint32_t cm = 0;
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            const float dd = fmaf(-2.f, __uint_as_float(v[c]), qw[ch * 32 + c]);
+                            cm |= (dd <= theta ? 1u : 0u) << c;
+                        }
+                        const long long sb = c0 + ch * 32;
+                        if (i >= sb && i < sb + 32) cm &= ~(1u << (int)(i - sb));   // self term already counted
                         while (cm) {
                             const int c = __ffs(cm) - 1;
                             cm &= cm - 1u;
@@ -473,82 +737,105 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                                 s1 = fmaf(dl, dl, s1);
                                 s2 = fmaf(dl, ft[d], s2);
                             }
-                            const float ls = b.mask[src] ? -INFINITY : b.logw[src];
-                            if (ls != -INFINITY) {
-#pragma unroll
-                                for (int j = 0; j < N; ++j) {
-                                    const float sc = fmaf(-s1, k.inv2tau[j], s2) + (rowc[j] + ls);
-                                    if (sc > mx[j]) {
-                                        sm[j] = (mx[j] == -INFINITY) ? 1.f : sm[j] * expf(mx[j] - sc) + 1.f;
-                                        mx[j] = sc;
-                                    } else {
-                                        sm[j] += expf(sc - mx[j]);
-                                    }
-                                }
-                            }
+                            add_score(s1, s2, src);
                             ++ncand;
                         }
-                        theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
-                        continue;
+                        theta = screen_theta<N>(k, live, nu_s, Fi, mx, lmax, numax, T);
                     }
-                    // long rows: the warp evaluates one candidate at a time, coalesced over
-                    // the coordinates
-                    while (true) {
-                        const uint32_t who = __ballot_sync(0xffffffffu, cm != 0u);
-                        if (who == 0u) break;
-                        const int leader = __ffs(who) - 1;
-                        const int c = __shfl_sync(0xffffffffu, __ffs(cm) - 1, leader);
-                        const long long src = sb + c;
-                        const long long tgt = i0 + q * 32 + leader;
-                        const float* ut = b.u + (size_t)tgt * k.r_pad;
-                        const float* us = b.u + (size_t)src * k.r_pad;
-                        const float* ft = b.f + (size_t)tgt * k.r_pad;
-                        float s1 = 0.f, s2 = 0.f;
-                        for (int d = lane; d < k.r; d += 32) {
-                            const float dl = ut[d] - us[d];
-                            s1 = fmaf(dl, dl, s1);
-                            s2 = fmaf(dl, ft[d], s2);
-                        }
-#pragma unroll
-                        for (int o = 16; o > 0; o >>= 1) {
-                            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-                        }
-                        if (lane == leader) {
-                            const float ls = b.mask[src] ? -INFINITY : b.logw[src];
-                            if (ls != -INFINITY) {
-#pragma unroll
-                                for (int j = 0; j < N; ++j) {
-                                    const float sc = fmaf(-s1, k.inv2tau[j], s2) + (rowc[j] + ls);
-                                    if (sc > mx[j]) {
-                                        sm[j] = (mx[j] == -INFINITY) ? 1.f : sm[j] * expf(mx[j] - sc) + 1.f;
-                                        mx[j] = sc;
-                                    } else {
-                                        sm[j] += expf(sc - mx[j]);
-                                    }
-                                }
-                            }
-                            cm &= cm - 1u;
-                            ++ncand;
-                            theta = screen_theta<N>(k, live, nu_i, Fi, mx, lmax, numax, T);
-                        }
-                    }
+                    release(acc);
+                    return true;
                 }
-                tc_fence_before();
+                // long rows: 64 columns per TMEM load; the smallest q_s - 2 G of a lane's 64
+                // columns decides whether its candidate masks are needed at all
+                int cnt = 0;
+                for (int part = 0; part < HALF / 64; ++part) {
+                    uint32_t v[64];
+                    __syncwarp();
+                    tmem_ld64(tbase + (uint32_t)(part * 64), v);
+                    tmem_ld_wait();
+                    const float4* q4 = reinterpret_cast<const float4*>(qw + part * 64);
+                    float mn = INFINITY;
+#pragma unroll
+                    for (int c4 = 0; c4 < 16; ++c4) {
+                        const float4 qq = q4[c4];
+                        mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 0]), qq.x));
+                        mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 1]), qq.y));
+                        mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 2]), qq.z));
+                        mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 3]), qq.w));
+                    }
+                    uint32_t m0 = 0, m1 = 0;
+                    if (mn <= theta) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) {
+                            m0 |= (fmaf(-2.f, __uint_as_float(v[c]), qw[part * 64 + c]) <= theta ? 1u : 0u) << c;
+                            m1 |= (fmaf(-2.f, __uint_as_float(v[32 + c]), qw[part * 64 + 32 + c]) <= theta ? 1u : 0u)
+                                  << c;
+                        }
+                        const long long sb = c0 + part * 64;   // self term already counted
+                        if (i >= sb && i < sb + 32) m0 &= ~(1u << (int)(i - sb));
+                        if (i >= sb + 32 && i < sb + 64) m1 &= ~(1u << (int)(i - sb - 32));
+                        cnt += __popc(m0) + __popc(m1);
+                    }
+                    cmw[(2 * part) * 32 + lane] = m0;
+                    cmw[(2 * part + 1) * 32 + lane] = m1;
+                }
+                release(acc);
+                const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
+                if (tot == 0) return true;
+                if (mode == 1 && tot > kEscThresh) {
+                    if (lane == 0) myesc[(t - t0) >> 5] |= 1u << ((t - t0) & 31);
+                    return true;
+                }
+                for (int ch = 0; ch < HALF / 32; ++ch) eval_warp(cmw[ch * 32 + lane], c0 + ch * 32);
+                return true;
+            };
+            for (int t = t0; t < t1 && ok; ++t) ok = tile(t, pre ? 1 : 0);
+            if (ok && pre) {
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[acc]);
+                if (lane == 0) mbar_arrive(escb);
+                if (!wait_bounded(escb, par, abort_flag, status)) ok = false;
+                for (int t = t0; t < t1 && ok; ++t)
+                    if (esc_any(par, t - t0)) ok = tile(t, esc_bit(ew, par, t - t0) ? 2 : 3);
             }
-            if (ok && in_range) {
-                if (nsplit == 1) {
-                    b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li, b.stats->c_ref,
-                                                                     &b.stats->clamps)
-                                          : -INFINITY;
-                } else {
+            // merge the pair's row states: the second half hands its (max, sum) over through
+            // shared memory (bounded hand-shakes, so an aborted partner cannot block)
+            const uint32_t xph = nitem & 1u;
+            if (ok && h == 1) {
+                if (nitem > 0 && !wait_bounded(&xfree[q], xph ^ 1u, abort_flag, status)) ok = false;
+                if (ok) {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) { xrow[2 * j] = mx[j]; xrow[2 * j + 1] = sm[j]; }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&xfull[q]);
+                }
+            }
+            if (ok && h == 0) {
+                if (!wait_bounded(&xfull[q], xph, abort_flag, status)) ok = false;
+                if (ok) {
 #pragma unroll
                     for (int j = 0; j < N; ++j) {
-                        float* ps = part_slot(b, i, split, j);
-                        ps[0] = (sm[j] > 0.f) ? mx[j] : -INFINITY;
-                        ps[1] = sm[j];
+                        const float m2 = xrow[2 * j], s2 = xrow[2 * j + 1];
+                        if (s2 > 0.f) {
+                            if (sm[j] == 0.f) { mx[j] = m2; sm[j] = s2; }
+                            else if (m2 > mx[j]) { sm[j] = sm[j] * expf(mx[j] - m2) + s2; mx[j] = m2; }
+                            else sm[j] += s2 * expf(m2 - mx[j]);
+                        }
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&xfree[q]);
+                    if (in_range) {
+                        if (nsplit == 1) {
+                            b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li,
+                                                                             b.stats->c_ref, &b.stats->clamps)
+                                                  : -INFINITY;
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < N; ++j) {
+                                float* ps = part_slot(b, i, split, j);
+                                ps[0] = (sm[j] > 0.f) ? mx[j] : -INFINITY;
+                                ps[1] = sm[j];
+                            }
+                        }
                     }
                 }
             }
@@ -563,6 +850,23 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     if (warp == 1) {
         __syncwarp();
         tmem_dealloc(tmem, C::TMEM_COLS);
+    }
+    // the last CTA to finish runs the first-pass controller of every filter of the launch
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int prev = atomicAdd(&ctr->tc_done, 1u);
+        if (prev == gridDim.x - 1) {
+            __threadfence();
+            const unsigned long long t_start = atomicExch(&ctr->tc_t0, ~0ull);
+            const unsigned long long t_end = globaltimer();
+            if (!batched) {
+                tc_adapt(k0, b0.stats, t_end > t_start ? (double)(t_end - t_start) : -1.0);
+            } else {
+                for (int f = 0; f < w.nb; ++f)
+                    if (w.tr[f].path == 0) tc_adapt(w.tr[f].k, w.tr[f].b.stats, -1.0);
+            }
+            atomicExch(&ctr->tc_done, 0u);
+        }
     }
 }
 
@@ -700,7 +1004,7 @@ cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStr
     if (e != cudaSuccess) return e;
     k_tc_colprep<<<(unsigned)(k.n_pad / 128), 128, 0, s>>>(k, b);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const TcWork w{nullptr, nullptr, b.tc_items, b.tc_cta_start};
+    const TcWork w{nullptr, nullptr, b.tc_items, b.tc_cta_start, 1};
     e = launch_bn<256>(k.N, (unsigned)b.tc_grid, ma, mb, k, b, w, s);
     if (e != cudaSuccess) return e;
     int l = 2;
@@ -728,7 +1032,7 @@ cudaError_t launch_ksum_tc_batch(const Traj<float>* d_traj, int B, int N, long l
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const CUtensorMap& map_any = *static_cast<const CUtensorMap*>(map_any_v);
-    const TcWork w{d_traj, static_cast<const CUtensorMap*>(d_maps), d_items, d_cta_start};
+    const TcWork w{d_traj, static_cast<const CUtensorMap*>(d_maps), d_items, d_cta_start, B};
     e = (bn == 128) ? launch_bn<128>(N, (unsigned)grid, map_any, map_any, k_any, b_any, w, s)
                     : launch_bn<256>(N, (unsigned)grid, map_any, map_any, k_any, b_any, w, s);
     if (e != cudaSuccess) return e;

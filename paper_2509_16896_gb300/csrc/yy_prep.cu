@@ -87,6 +87,8 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
                 b.logw[i] = T(-INFINITY);
                 if (first) { b.nu[i] = T(0); b.mask[i] = 1; }
             }
+            if (first && b.nu_chunk)
+                for (int c = lane; c < k.r_pad / 64; c += 32) b.nu_chunk[(size_t)i * (k.r_pad / 64) + c] = 0.f;
             continue;
         }
         T div = T(0), nf = T(0), nu = T(0), lw = T(0);
@@ -104,7 +106,8 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const int dq = 2 * (v0 + 32 * q);
-                if (dq >= k.r_pad) continue;
+                if (dq >= k.r_pad) continue;   // uniform over the warp (r_pad is a multiple of 64)
+                float cq = 0.f;                // |u|^2 of this lane's two coordinates
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
                     const int d = dq + e;
@@ -125,6 +128,7 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
                         if (mode == kPrepRestart) lw -= (T)uf * (T)uf * s_iv[d];
                         if (first) {
                             nu += (T)uf * (T)uf;
+                            cq = fmaf(uf, uf, cq);
                             const double R = halfw[d];
                             if (fabs((double)uf) >= R - 1e-12 * R) on_face = 1;
                         }
@@ -135,6 +139,11 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
                     }
                     if (first && b.ubf) b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(d < k.r ? uf : 0.0f);
                     fi[d] = fv;
+                }
+                if (first && b.nu_chunk) {
+                    // the warp's 64 coordinates 2 (v0 - lane + 32 q) .. +63 form one chunk
+                    cq = warp_sum(cq);
+                    if (lane == 0) b.nu_chunk[(size_t)i * (k.r_pad / 64) + (dq >> 6)] = cq;
                 }
             }
         }

@@ -42,7 +42,7 @@ def test_workspace_bytes_and_invalid_configs(lib):
     good = _cfg()
     assert lib.yy_workspace_bytes(ctypes.byref(good)) > 0
     bad = [_cfg(r=0), _cfg(n=1), _cfg(dt=0.0), _cfg(R=-1.0), _cfg(n_scales=0), _cfg(n_scales=5),
-           _cfg(r=1025), _cfg(ess_frac=1.5)]
+           _cfg(r=1025), _cfg(ess_frac=1.5), _cfg(screen_prefix=-1)]
     for c in bad:
         assert lib.yy_workspace_bytes(ctypes.byref(c)) == 0
         h = ctypes.c_void_p()
