@@ -88,6 +88,7 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     const size_t nr = (size_t)n_pad * r_pad;
     b.u = cv.take<float>(nr * sizeof(float));
     b.f = cv.take<T>(nr * sizeof(T));
+    b.store_f = (c->precision == YY_PREC_BF16) ? 0 : 1;
     b.ubf = (c->precision == YY_PREC_BF16) ? cv.take<__nv_bfloat16>(nr * sizeof(__nv_bfloat16)) : nullptr;
     b.divf = cv.take<T>(n_pad * sizeof(T));
     b.nu = cv.take<T>(n_pad * sizeof(T));
@@ -201,10 +202,7 @@ __global__ void k_set_stats(DevStats* st, double lognorm, long long step) {
     st->step = step;
 }
 
-__global__ void k_init_cref(DevStats* st, double c_ref) {
-    st->c_ref = c_ref;
-    st->tc_t0 = ~0ull;   // no prediction launch running
-}
+__global__ void k_init_cref(DevStats* st, double c_ref) { st->c_ref = c_ref; }
 
 template <typename T>
 yy_status do_init_nodes(yy_filter* f, Bufs<T>& b, Consts<T>& k, const uint32_t* h_poly,

@@ -281,6 +281,7 @@ yy_status yy_batch_create(const yy_config* cfgs, int32_t B, void* d_workspace, s
             delete bt;
             return st;
         }
+        f->bf.store_f = 1;   // a member may be routed to the FP32 form, which reads f
         bt->filters.push_back(f);
         p += al256(wb);
         bt->dy_off.push_back(M);

@@ -42,11 +42,9 @@ struct DevStats {
     double c_ref;        // offset of the predicted log-weights (moves with the box volume)
     // BF16 screen: coordinate chunks (of 64) of the first screening pass and its controller
     int tc_nk1;          // 0 = not chosen yet
-    int tc_streak;       // consecutive clean predictions (batch members)
+    int tc_streak;       // consecutive acceptable predictions at the current length
     int tc_from;         // first-pass length of the prediction before the last one
-    float tc_time[YY_MAX_DIM / 64 + 1];   // last launch time (ns) per first-pass length, 0 = none
-    int tc_age[YY_MAX_DIM / 64 + 1];      // predictions since that time was taken (< 0: known slow)
-    unsigned long long tc_t0;    // earliest CTA start of the running launch (%globaltimer)
+    int tc_hold[YY_MAX_DIM / 64 + 1];     // predictions a length is still held off
     unsigned long long tc_blk;   // tiles screened by the last prediction
     unsigned long long tc_esc;   // of which rescreened with all coordinates
     unsigned long long tc_last_blk, tc_last_esc;   // the same, kept for the host
@@ -82,6 +80,8 @@ struct Bufs {
     T* nu;                // [n_pad] |u_i|^2
     T* nf;                // [n_pad] |f_i|^2
     uint8_t* mask;        // [n_pad] Dirichlet boundary
+    int store_f;          // f is written by the preparation pass (the BF16 screen of a single
+                          // filter recomputes f of its few exact pairs instead)
     T* logw;              // [n_pad] current (normalised or unnormalised) log-weights
     T* logw_pred;         // [n_pad] predicted log-weights minus c_ref
     double* centre;       // [r_pad]

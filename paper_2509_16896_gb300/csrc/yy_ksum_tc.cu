@@ -63,7 +63,8 @@ constexpr float kEpsGram = 0.015625f;   // 2^-6
 constexpr float kDeadQ = 3.0e38f;
 constexpr float kThetaMax = 1.0e30f;
 constexpr int kEscWords = 32;    // per epilogue warp and parity: marks of up to 1024 source tiles
-constexpr int kEscThresh = 16;   // candidates of one warp in one tile above which it is rescreened
+constexpr int kEscThresh = 8;    // candidates of one warp in one tile above which it is rescreened
+constexpr int kExactBudget = 64; // exact pairs one warp evaluates per item in the first pass
 
 // Shape-dependent constants.  BN = 256: 4 stages, 512 TMEM columns, one CTA per SM.
 // BN = 128: 3 stages (96 KB), 256 TMEM columns, so two CTAs fit on one SM.
@@ -247,6 +248,18 @@ __device__ __forceinline__ int prefix_chunks(const Consts<float>& k, const DevSt
     return v < 1 ? 1 : (v > nk ? nk : v);
 }
 
+// Drift component d at x = c + u with the preparation pass's arithmetic (the centre split
+// into head and tail, dimc), so that it equals the value that pass would store in f.
+__device__ __forceinline__ float drift_at(const Consts<float>& k, const Bufs<float>& b, float u, int d) {
+    const float x = b.dimc[d] + (u + b.dimc[k.r_pad + d]);
+    if (k.model == YY_MODEL_CUBIC) {
+        float sn, cs;
+        sincosf(x, &sn, &cs);
+        return cs;
+    }
+    return k.model_a * x;
+}
+
 // Per source chunk of 128: |u_s|^2 of live sources over all coordinates (tc_q) and over the
 // first-pass coordinates (tc_q1), kDeadQ for masked, padded or -inf ones; the largest live
 // log-weight; the largest live value of each kind of |u_s|^2.
@@ -302,20 +315,13 @@ __global__ void __launch_bounds__(128) kb_tc_colprep(const Traj<float>* __restri
 // Controller of the first-pass length, run once per prediction launch and filter (by the
 // last CTA to finish).  The work beyond the first pass, in chunks per tile, is
 //     extra = (rescreened tiles x all chunks + exact pair evaluations x r / 4096) / tiles
-// (an exact pair costs about r / 4096 of the tensor time of one chunk of one tile); a
-// prediction is clean when it had neither.
-//  - extra > 1: the first pass was much too short -- lengthen it at once (by 2 if extra > 4)
-//    and hold the short length off for 1024 predictions.
-//  - single filter (launch time dt_ns known): the latest launch time per length is kept
-//    for 64 predictions; move to a neighbouring length measured faster, else probe a
-//    neighbour without a recent time -- one chunk longer after a prediction that was not
-//    clean, one shorter after four clean ones in a row at this length (candidates grow
-//    steeply as the first pass shortens, and the weights of the first steps spread out
-//    fast, so a length is only shortened from a settled clean one).  A length that came
-//    out more than twice as slow as the one before it is held off for 1024 predictions.
-//  - batch member (dt_ns < 0, the launch is shared): one chunk shorter after two clean
-//    predictions in a row, unless the shorter length is held off.
-__device__ void tc_adapt(const Consts<float>& k, DevStats* st, double dt_ns) {
+// (an exact pair costs about r / 4096 of the tensor time of one chunk of one tile).  A
+// length is acceptable when extra <= 1/50.  After an unacceptable prediction the length
+// grows at once (by 2 when extra > 4) and the one just used is held off for 1024
+// predictions; after four acceptable predictions in a row at one length, one chunk shorter
+// is tried unless it is held off.  Candidates grow steeply as the first pass shortens, so
+// the shortest acceptable length is found from above and probed again only rarely.
+__device__ void tc_adapt(const Consts<float>& k, DevStats* st) {
     const unsigned long long blk = atomicExch(&st->tc_blk, 0ull);
     const unsigned long long esc = atomicExch(&st->tc_esc, 0ull);
     const unsigned long long cand = atomicAdd(&st->candidates, 0ull);
@@ -325,48 +331,27 @@ __device__ void tc_adapt(const Consts<float>& k, DevStats* st, double dt_ns) {
     st->tc_last_nk1 = nk1;
     if (k.tc_prefix > 0 || blk == 0) return;
     const int nk = k.r_pad / tc::BK;
-    constexpr int kFresh = 64, kHold = 1024;
+    constexpr int kHold = 1024, kSettle = 4;
     for (int x = 1; x <= nk; ++x)
-        if (st->tc_age[x] < (1 << 30)) ++st->tc_age[x];
+        if (st->tc_hold[x] > 0) --st->tc_hold[x];
     const int from = st->tc_from;
     st->tc_from = nk1;
     const double extra = ((double)esc * nk + (double)cand * k.r / 4096.0) / (double)blk;
-    const bool clean = esc == 0 && cand == 0;
-    if (dt_ns >= 0.0) st->tc_time[nk1] = (float)dt_ns;
-    if (extra > 1.0 && nk1 < nk) {
-        st->tc_age[nk1] = -kHold;
+    int next = nk1;
+    if (extra > 0.02) {
         st->tc_streak = 0;
-        st->tc_nk1 = min(nk, nk1 + (extra > 4.0 ? 2 : 1));
-        return;
-    }
-    if (dt_ns < 0.0) {   // batch member
-        int next = nk1;
-        if (!clean) {
-            st->tc_streak = 0;
-        } else if (++st->tc_streak >= 2) {
-            st->tc_streak = 0;
-            if (nk1 > 1 && st->tc_age[nk1 - 1] >= 0) next = nk1 - 1;
+        if (nk1 < nk) {
+            st->tc_hold[nk1] = kHold;
+            next = min(nk, nk1 + (extra > 4.0 ? 2 : 1));
         }
-        st->tc_nk1 = next;
-        return;
+    } else {
+        st->tc_streak = (from == nk1) ? st->tc_streak + 1 : 1;
+        if (st->tc_streak >= kSettle && nk1 > 1 && st->tc_hold[nk1 - 1] == 0) {
+            next = nk1 - 1;
+            st->tc_streak = 0;
+        }
     }
-    st->tc_age[nk1] = 0;
-    st->tc_streak = (from == nk1 && clean) ? st->tc_streak + 1 : (clean ? 1 : 0);
-    if (from >= 1 && from <= nk && from != nk1 && st->tc_time[from] > 0.f && dt_ns > 2.0 * st->tc_time[from]) {
-        st->tc_age[nk1] = -kHold;   // keeps its (slow) time
-        st->tc_nk1 = from;
-        return;
-    }
-    auto known = [&](int x) { return st->tc_time[x] > 0.f && st->tc_age[x] < kFresh; };
-    auto held = [&](int x) { return st->tc_age[x] < 0; };
-    int best = nk1;
-    if (nk1 < nk && known(nk1 + 1) && st->tc_time[nk1 + 1] < st->tc_time[best]) best = nk1 + 1;
-    if (nk1 > 1 && known(nk1 - 1) && st->tc_time[nk1 - 1] < st->tc_time[best]) best = nk1 - 1;
-    if (best == nk1) {
-        if (!clean && nk1 < nk && !known(nk1 + 1) && !held(nk1 + 1)) best = nk1 + 1;
-        else if (st->tc_streak >= 4 && nk1 > 1 && !known(nk1 - 1) && !held(nk1 - 1)) best = nk1 - 1;
-    }
-    st->tc_nk1 = best;
+    st->tc_nk1 = next;
 }
 
 // Work list of a launch: CTA c processes items[cta_start[c] .. cta_start[c + 1]), each
@@ -432,9 +417,8 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     unsigned int* status = (it_end <= it_begin) ? nullptr
                            : batched ? &w.tr[w.items[it_begin].x].b.stats->status : &b0.stats->status;
 
-    DevStats* const ctr = batched ? w.tr[0].b.stats : b0.stats;   // launch-wide counters
+    DevStats* const ctr = batched ? w.tr[0].b.stats : b0.stats;   // launch-wide counter
     if (threadIdx.x == 0) {
-        atomicMin(&ctr->tc_t0, globaltimer());
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
         for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], EPI_WARPS); }
         mbar_init(drain, 1);
@@ -621,6 +605,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 sm[j] = (self && self_here) ? 1.f : 0.f;
             }
             unsigned long long ncand = 0;
+            int exact1 = 0;   // first-pass exact evaluations of this warp in this item
             const uint32_t par = npre & 1u;
             uint32_t* myesc = escm + (ew * 2 + par) * kEscWords;
             if (pre) {
@@ -655,12 +640,11 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     const long long tgt = i0 + q * 32 + leader;
                     const float* ut = b.u + (size_t)tgt * k.r_pad;
                     const float* us = b.u + (size_t)src * k.r_pad;
-                    const float* ft = b.f + (size_t)tgt * k.r_pad;
                     float s1 = 0.f, s2 = 0.f;
                     for (int d = lane; d < k.r; d += 32) {
                         const float dl = ut[d] - us[d];
                         s1 = fmaf(dl, dl, s1);
-                        s2 = fmaf(dl, ft[d], s2);
+                        s2 = fmaf(dl, drift_at(k, b, ut[d], d), s2);
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -712,7 +696,6 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     // short rows (one pass): every lane evaluates its own row's candidates
                     // chunk by chunk, tightening the screen as the running maxima grow
                     const float* ut = b.u + (size_t)i * k.r_pad;
-                    const float* ft = b.f + (size_t)i * k.r_pad;
                     for (int ch = 0; ch < HALF / 32; ++ch) {
                         uint32_t v[32];
                         __syncwarp();
@@ -735,7 +718,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                             for (int d = 0; d < k.r; ++d) {
                                 const float dl = ut[d] - us[d];
                                 s1 = fmaf(dl, dl, s1);
-                                s2 = fmaf(dl, ft[d], s2);
+                                s2 = fmaf(dl, drift_at(k, b, ut[d], d), s2);
                             }
                             add_score(s1, s2, src);
                             ++ncand;
@@ -782,10 +765,11 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 release(acc);
                 const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
                 if (tot == 0) return true;
-                if (mode == 1 && tot > kEscThresh) {
+                if (mode == 1 && (tot > kEscThresh || exact1 + tot > kExactBudget)) {
                     if (lane == 0) myesc[(t - t0) >> 5] |= 1u << ((t - t0) & 31);
                     return true;
                 }
+                if (mode == 1) exact1 += tot;
                 for (int ch = 0; ch < HALF / 32; ++ch) eval_warp(cmw[ch * 32 + lane], c0 + ch * 32);
                 return true;
             };
@@ -857,13 +841,11 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         const unsigned int prev = atomicAdd(&ctr->tc_done, 1u);
         if (prev == gridDim.x - 1) {
             __threadfence();
-            const unsigned long long t_start = atomicExch(&ctr->tc_t0, ~0ull);
-            const unsigned long long t_end = globaltimer();
             if (!batched) {
-                tc_adapt(k0, b0.stats, t_end > t_start ? (double)(t_end - t_start) : -1.0);
+                tc_adapt(k0, b0.stats);
             } else {
                 for (int f = 0; f < w.nb; ++f)
-                    if (w.tr[f].path == 0) tc_adapt(w.tr[f].k, w.tr[f].b.stats, -1.0);
+                    if (w.tr[f].path == 0) tc_adapt(w.tr[f].k, w.tr[f].b.stats);
             }
             atomicExch(&ctr->tc_done, 0u);
         }

@@ -80,7 +80,8 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
         const float* ui = b.u + (size_t)i * k.r_pad;
         T* fi = b.f + (size_t)i * k.r_pad;
         if (i >= k.n) {  // padding rows: inert
-            for (int d = lane; d < k.r_pad; d += 32) fi[d] = T(0);
+            if (b.store_f)
+                for (int d = lane; d < k.r_pad; d += 32) fi[d] = T(0);
             if (lane == 0) {
                 b.divf[i] = T(0);
                 b.nf[i] = T(0);
@@ -138,7 +139,7 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
                         }
                     }
                     if (first && b.ubf) b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(d < k.r ? uf : 0.0f);
-                    fi[d] = fv;
+                    if (b.store_f) fi[d] = fv;
                 }
                 if (first && b.nu_chunk) {
                     // the warp's 64 coordinates 2 (v0 - lane + 32 q) .. +63 form one chunk
