@@ -104,7 +104,7 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.params = cv.take<uint32_t>((size_t)c->r * (YY_SOBOL_POLY_WORDS + YY_SOBOL_SCRAMBLE_WORDS) * sizeof(uint32_t));
     b.obs_g = cv.take<T>(r_pad * sizeof(T));
     b.obs_c = cv.take<T>(r_pad * sizeof(T));
-    b.dimc = cv.take<T>(3 * (size_t)r_pad * sizeof(T));
+    b.dimc = cv.take<T>(5 * (size_t)r_pad * sizeof(T));
     b.next_centre = cv.take<double>(r_pad * sizeof(double));
     b.next_half = cv.take<double>(r_pad * sizeof(double));
     b.dy_last = cv.take<double>(r_pad * sizeof(double));

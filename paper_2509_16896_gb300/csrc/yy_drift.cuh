@@ -1,0 +1,47 @@
+// Drift of the cubic sensor model (Section 9.1), f_d(x) = cos x_d, and sin x_d (for the
+// divergence), in float32 at x_d = c_d + u from per-dimension constants of the box:
+//     cos(c + u) = cos c cos u - sin c sin u,    sin(c + u) = sin c cos u + cos c sin u,
+// with cos c, sin c taken once per dimension in float64 and cos u, sin u from their Taylor
+// polynomials through u^8 and u^9 (Horner in u^2).  For |u| <= kPolyMaxU = 0.6 the
+// truncation error is below 2e-9, under float32 rounding.  A dimension whose box half-width
+// exceeds kPolyMaxU carries cc = NaN and is evaluated by sincosf of x = hi + (u + lo) (the
+// centre split into a float head and tail).  The preparation pass and the exact pair
+// evaluation of the BF16 screen both call this, so the drift they use is the same value.
+#pragma once
+
+namespace yy {
+
+constexpr double kPolyMaxU = 0.6;
+
+// out of line: keeps the unrolled loops that call cubic_drift small
+static __device__ __noinline__ void cubic_drift_wide(float x, float* f, float* s) { sincosf(x, s, f); }
+
+// Narrow boxes only (cc finite): the polynomial form without the fallback branch.
+__device__ __forceinline__ void cubic_drift_narrow(float u, float cc, float sc, float* f, float* s) {
+    const float u2 = u * u;
+    const float cu =
+        fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f), 1.0f);
+    const float su =
+        u * fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, 1.0f / 362880.0f, -1.0f / 5040.0f), 1.0f / 120.0f), -1.0f / 6.0f),
+                 1.0f);
+    *f = fmaf(cc, cu, -sc * su);
+    *s = fmaf(sc, cu, cc * su);
+}
+
+__device__ __forceinline__ void cubic_drift(float u, float hi, float lo, float cc, float sc, float* f, float* s) {
+    if (cc == cc) {
+        const float u2 = u * u;
+        const float cu =
+            fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, 1.0f / 40320.0f, -1.0f / 720.0f), 1.0f / 24.0f), -0.5f), 1.0f);
+        const float su =
+            u * fmaf(u2, fmaf(u2, fmaf(u2, fmaf(u2, 1.0f / 362880.0f, -1.0f / 5040.0f), 1.0f / 120.0f),
+                          -1.0f / 6.0f),
+                     1.0f);
+        *f = fmaf(cc, cu, -sc * su);
+        *s = fmaf(sc, cu, cc * su);
+    } else {
+        cubic_drift_wide(hi + (u + lo), f, s);
+    }
+}
+
+}  // namespace yy

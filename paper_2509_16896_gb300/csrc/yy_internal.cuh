@@ -92,7 +92,8 @@ struct Bufs {
     double* var;          // [r_pad] v_hat
     T* obs_g;             // [r_pad] dy - dt h(c)
     T* obs_c;             // [r_pad] centre in T
-    T* dimc;              // [3][r_pad] per-dimension constants of the preparation pass
+    T* dimc;              // [5][r_pad] per-dimension constants of the preparation pass:
+                          // centre head, tail, Gaussian restart 1 / (2 var), cos c, sin c
     double* next_centre;  // [r_pad] box of the restart in progress
     double* next_half;    // [r_pad]
     double* dy_last;      // [r_pad] observation increment of the last update

@@ -48,6 +48,7 @@
 #include <algorithm>
 
 #include "yy_combine.cuh"
+#include "yy_drift.cuh"
 
 namespace yy {
 
@@ -248,16 +249,16 @@ __device__ __forceinline__ int prefix_chunks(const Consts<float>& k, const DevSt
     return v < 1 ? 1 : (v > nk ? nk : v);
 }
 
-// Drift component d at x = c + u with the preparation pass's arithmetic (the centre split
-// into head and tail, dimc), so that it equals the value that pass would store in f.
+// Drift component d at x = c + u with the preparation pass's arithmetic (per-dimension
+// constants dimc), so that it equals the value that pass would store in f.
 __device__ __forceinline__ float drift_at(const Consts<float>& k, const Bufs<float>& b, float u, int d) {
-    const float x = b.dimc[d] + (u + b.dimc[k.r_pad + d]);
+    const int rp = k.r_pad;
     if (k.model == YY_MODEL_CUBIC) {
-        float sn, cs;
-        sincosf(x, &sn, &cs);
-        return cs;
+        float fv, sn;
+        cubic_drift(u, b.dimc[d], b.dimc[rp + d], b.dimc[3 * rp + d], b.dimc[4 * rp + d], &fv, &sn);
+        return fv;
     }
-    return k.model_a * x;
+    return k.model_a * (b.dimc[d] + (u + b.dimc[rp + d]));
 }
 
 // Per source chunk of 128: |u_s|^2 of live sources over all coordinates (tc_q) and over the

@@ -9,21 +9,19 @@
 //             (Section 5; the density is this library's reading of "re-initialise")
 // Constants that cancel in the normalisation that follows are dropped.
 //
-// One warp per node row; lanes stride over coordinates.  x = c + u is formed as
-// c_hi + (u + c_lo) with the float64 centre split into a head and a tail in the working
-// precision T (k_prep_dims), and the model is evaluated in T.
+// One warp per node row; lane l holds float2 l + 32 q of the row for q = 0 .. r_pad / 64 - 1
+// (coordinates 64 q + 2 l, +1: chunk q of 64 coordinates), the whole row loaded before any
+// arithmetic.  x = c + u is formed as c_hi + (u + c_lo) with the float64 centre split into a
+// head and a tail in the working precision T (k_prep_dims).  In float32 the cubic drift
+// comes from the angle-addition form of yy_drift.cuh; in float64 from sincos.
 #include "yy_internal.cuh"
+#include "yy_drift.cuh"
+
+#include <type_traits>
 
 namespace yy {
 
 enum PrepMode { kPrepOnly = 0, kPrepInit = 1, kPrepRestart = 2 };
-
-template <typename T>
-__device__ __forceinline__ void sincos_t(T x, T* s, T* c);
-template <>
-__device__ __forceinline__ void sincos_t<float>(float x, float* s, float* c) { sincosf(x, s, c); }
-template <>
-__device__ __forceinline__ void sincos_t<double>(double x, double* s, double* c) { sincos(x, s, c); }
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -32,16 +30,20 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+constexpr int kRowQ = YY_MAX_DIM / 64;   // float2 per lane of the longest row
+
 // Per-dimension constants of one preparation pass: the centre split into a T-precision
-// head and tail (x = c_hi + (u + c_lo) loses only the final rounding), and for a Gaussian
-// restart 1 / (2 max(v_hat_d, (R_d / 4)^2)).
+// head and tail (x = c_hi + (u + c_lo) loses only the final rounding), for a Gaussian
+// restart 1 / (2 max(v_hat_d, (R_d / 4)^2)), and cos c_d, sin c_d (NaN cosine where the
+// half-width is too wide for the polynomials of yy_drift.cuh).
 template <typename T>
 __device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind) {
     if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
     const double* cen = (mode == kPrepRestart) ? b.next_centre : b.centre;
     const double* half = (mode == kPrepRestart) ? b.next_half : b.halfwidth;
-    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
-        T hi = T(0), lo = T(0), iv = T(0);
+    const int rp = k.r_pad;
+    for (int d = threadIdx.x; d < rp; d += blockDim.x) {
+        T hi = T(0), lo = T(0), iv = T(0), cc = T(1), sc = T(0);
         if (d < k.r) {
             const double c = cen[d];
             hi = (T)c;
@@ -50,38 +52,37 @@ __device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>
                 const double R4 = 0.25 * half[d];
                 iv = (T)(0.5 / fmax(b.var[d], R4 * R4));
             }
+            cc = (half[d] <= kPolyMaxU) ? (T)cos(c) : (T)NAN;
+            sc = (T)sin(c);
         }
         b.dimc[d] = hi;
-        b.dimc[k.r_pad + d] = lo;
-        b.dimc[2 * k.r_pad + d] = iv;
+        b.dimc[rp + d] = lo;
+        b.dimc[2 * rp + d] = iv;
+        b.dimc[3 * rp + d] = cc;
+        b.dimc[4 * rp + d] = sc;
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, int mode, int first,
-                                          double prior_mean, double prior_var, int bid, int nblk) {
-    if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
-    // a restart that re-mapped the nodes to new half-widths also redoes the node-only
-    // quantities (|u|^2, mask against the new faces, bf16 copy)
-    if (mode == kPrepRestart && b.stats->scale_changed) first = 1;
-    __shared__ T s_hi[YY_MAX_DIM], s_lo[YY_MAX_DIM], s_iv[YY_MAX_DIM];
-    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
-        s_hi[d] = b.dimc[d];
-        s_lo[d] = b.dimc[k.r_pad + d];
-        s_iv[d] = b.dimc[2 * k.r_pad + d];
-    }
-    __syncthreads();
+// The pass proper, compiled per mode and per "first" (node-only quantities too), so that
+// the restart pass carries none of the other modes' float64 arithmetic.
+template <typename T, int mode, bool first, bool narrow>
+__device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, double prior_mean,
+                                          double prior_var, int bid, int nblk, const T* s_hi, const T* s_lo,
+                                          const T* s_iv, const T* s_cc, const T* s_sc) {
+    const int rp = k.r_pad;
     const int lane = threadIdx.x & 31;
     const long long warp = (bid * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)nblk * blockDim.x) >> 5;
     const double* cen = (mode == kPrepRestart) ? b.next_centre : b.centre;
     const double* halfw = (mode == kPrepRestart) ? b.next_half : b.halfwidth;
+    const int nq = rp >> 6;   // float2 per lane
+    const bool cubic = k.model == YY_MODEL_CUBIC;
     for (long long i = warp; i < k.n_pad; i += nwarps) {
-        const float* ui = b.u + (size_t)i * k.r_pad;
-        T* fi = b.f + (size_t)i * k.r_pad;
+        const float* ui = b.u + (size_t)i * rp;
+        T* fi = b.f + (size_t)i * rp;
         if (i >= k.n) {  // padding rows: inert
             if (b.store_f)
-                for (int d = lane; d < k.r_pad; d += 32) fi[d] = T(0);
+                for (int d = lane; d < rp; d += 32) fi[d] = T(0);
             if (lane == 0) {
                 b.divf[i] = T(0);
                 b.nf[i] = T(0);
@@ -89,63 +90,60 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
                 if (first) { b.nu[i] = T(0); b.mask[i] = 1; }
             }
             if (first && b.nu_chunk)
-                for (int c = lane; c < k.r_pad / 64; c += 32) b.nu_chunk[(size_t)i * (k.r_pad / 64) + c] = 0.f;
+                for (int c = lane; c < nq; c += 32) b.nu_chunk[(size_t)i * nq + c] = 0.f;
             continue;
         }
+        // the whole row first: up to kRowQ loads in flight per lane
+        const float2* ui2 = reinterpret_cast<const float2*>(ui);
+        float2 uu[kRowQ];
+#pragma unroll
+        for (int q = 0; q < kRowQ; ++q) uu[q] = (q < nq) ? ui2[lane + 32 * q] : make_float2(0.f, 0.f);
         T div = T(0), nf = T(0), nu = T(0), lw = T(0);
         int on_face = 0;
-        // two coordinates per lane per load, four loads in flight (r_pad is a multiple of 64)
-        const int nv = k.r_pad >> 1;
-        const float2* ui2 = reinterpret_cast<const float2*>(ui);
-        for (int v0 = lane; v0 < nv; v0 += 128) {
-            float2 uu[4];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int v = v0 + 32 * q;
-                uu[q] = (v < nv) ? ui2[v] : make_float2(0.f, 0.f);
-            }
+        for (int q = 0; q < kRowQ; ++q) {
+            if (q >= nq) break;   // uniform over the warp
+            const int dq = 64 * q + 2 * lane;
+            float cq = 0.f;       // |u|^2 of this lane's two coordinates
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int dq = 2 * (v0 + 32 * q);
-                if (dq >= k.r_pad) continue;   // uniform over the warp (r_pad is a multiple of 64)
-                float cq = 0.f;                // |u|^2 of this lane's two coordinates
-#pragma unroll
-                for (int e = 0; e < 2; ++e) {
-                    const int d = dq + e;
-                    const float uf = e ? uu[q].y : uu[q].x;
-                    T fv = T(0);
-                    if (d < k.r) {
-                        const T x = s_hi[d] + ((T)uf + s_lo[d]);
-                        if (k.model == YY_MODEL_CUBIC) {
-                            T sn, cs;
-                            sincos_t<T>(x, &sn, &cs);
-                            fv = cs;
-                            div -= sn;
+            for (int e = 0; e < 2; ++e) {
+                const int d = dq + e;
+                const float uf = e ? uu[q].y : uu[q].x;
+                T fv = T(0);
+                if (d < k.r) {
+                    if (cubic) {
+                        T sn;
+                        if constexpr (std::is_same<T, float>::value && narrow) {
+                            cubic_drift_narrow(uf, s_cc[d], s_sc[d], &fv, &sn);
+                        } else if constexpr (std::is_same<T, float>::value) {
+                            cubic_drift(uf, s_hi[d], s_lo[d], s_cc[d], s_sc[d], &fv, &sn);
                         } else {
-                            fv = k.model_a * x;
-                            div += k.model_a;
+                            sincos(s_hi[d] + ((T)uf + s_lo[d]), &sn, &fv);
                         }
-                        nf += fv * fv;
-                        if (mode == kPrepRestart) lw -= (T)uf * (T)uf * s_iv[d];
-                        if (first) {
-                            nu += (T)uf * (T)uf;
-                            cq = fmaf(uf, uf, cq);
-                            const double R = halfw[d];
-                            if (fabs((double)uf) >= R - 1e-12 * R) on_face = 1;
-                        }
-                        if (mode == kPrepInit) {
-                            const double z = cen[d] + (double)uf - prior_mean;
-                            lw -= (T)(0.5 * z * z / prior_var);
-                        }
+                        div -= sn;
+                    } else {
+                        fv = k.model_a * (s_hi[d] + ((T)uf + s_lo[d]));
+                        div += k.model_a;
                     }
-                    if (first && b.ubf) b.ubf[(size_t)i * k.r_pad + d] = __float2bfloat16_rn(d < k.r ? uf : 0.0f);
-                    if (b.store_f) fi[d] = fv;
+                    nf += fv * fv;
+                    if constexpr (mode == kPrepRestart) lw -= (T)uf * (T)uf * s_iv[d];
+                    if constexpr (first) {
+                        nu += (T)uf * (T)uf;
+                        cq = fmaf(uf, uf, cq);
+                        const double R = halfw[d];
+                        if (fabs((double)uf) >= R - 1e-12 * R) on_face = 1;
+                    }
+                    if constexpr (mode == kPrepInit) {
+                        const double z = cen[d] + (double)uf - prior_mean;
+                        lw -= (T)(0.5 * z * z / prior_var);
+                    }
                 }
-                if (first && b.nu_chunk) {
-                    // the warp's 64 coordinates 2 (v0 - lane + 32 q) .. +63 form one chunk
-                    cq = warp_sum(cq);
-                    if (lane == 0) b.nu_chunk[(size_t)i * (k.r_pad / 64) + (dq >> 6)] = cq;
-                }
+                if (first && b.ubf) b.ubf[(size_t)i * rp + d] = __float2bfloat16_rn(d < k.r ? uf : 0.0f);
+                if (b.store_f) fi[d] = fv;
+            }
+            if (first && b.nu_chunk) {
+                cq = warp_sum(cq);
+                if (lane == 0) b.nu_chunk[(size_t)i * nq + q] = cq;
             }
         }
         div = warp_sum(div);
@@ -165,6 +163,42 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
             if (mode != kPrepOnly) b.logw[i] = b.mask[i] ? T(-INFINITY) : lw;
         }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, int mode, int first,
+                                          double prior_mean, double prior_var, int bid, int nblk) {
+    if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
+    // a restart that re-mapped the nodes to new half-widths also redoes the node-only
+    // quantities (|u|^2, mask against the new faces, bf16 copy)
+    if (mode == kPrepRestart && b.stats->scale_changed) first = 1;
+    __shared__ T s_hi[YY_MAX_DIM], s_lo[YY_MAX_DIM], s_iv[YY_MAX_DIM], s_cc[YY_MAX_DIM], s_sc[YY_MAX_DIM];
+    const int rp = k.r_pad;
+    for (int d = threadIdx.x; d < rp; d += blockDim.x) {
+        s_hi[d] = b.dimc[d];
+        s_lo[d] = b.dimc[rp + d];
+        s_iv[d] = b.dimc[2 * rp + d];
+        s_cc[d] = b.dimc[3 * rp + d];
+        s_sc[d] = b.dimc[4 * rp + d];
+    }
+    // every dimension inside the polynomials' range: no per-element fallback test
+    int my_narrow = 1;
+    for (int d = threadIdx.x; d < k.r; d += blockDim.x) my_narrow &= (s_cc[d] == s_cc[d]) ? 1 : 0;
+    const int narrow = __syncthreads_and(my_narrow);
+#define YY_PREP_ROWS(M, F, W) \
+    prep_rows<T, M, F, W>(k, b, prior_mean, prior_var, bid, nblk, s_hi, s_lo, s_iv, s_cc, s_sc)
+    if (mode == kPrepRestart) {
+        if (first) YY_PREP_ROWS(kPrepRestart, true, false);
+        else if (narrow) YY_PREP_ROWS(kPrepRestart, false, true);
+        else YY_PREP_ROWS(kPrepRestart, false, false);
+    } else if (mode == kPrepInit) {
+        if (first) YY_PREP_ROWS(kPrepInit, true, false); else YY_PREP_ROWS(kPrepInit, false, false);
+    } else {
+        if (first) YY_PREP_ROWS(kPrepOnly, true, false);
+        else if (narrow) YY_PREP_ROWS(kPrepOnly, false, true);
+        else YY_PREP_ROWS(kPrepOnly, false, false);
+    }
+#undef YY_PREP_ROWS
 }
 
 template <typename T>

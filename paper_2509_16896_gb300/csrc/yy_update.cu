@@ -50,7 +50,7 @@ __device__ __forceinline__ void lse_merge(double& m, double& s, double m2, doubl
 }
 
 // Moment partials: 4 + 2 r_pad doubles per block (the log-sum-exp partials reuse the
-// first 2 kNumPartBlocks doubles earlier in the step).
+// first 2 x (blocks of their pass, at most 4 kNumPartBlocks) doubles earlier in the step).
 size_t part_bytes(int r_pad) {
     return (size_t)kNumPartBlocks * (size_t)(4 + 2 * r_pad) * sizeof(double);
 }
@@ -88,9 +88,12 @@ __device__ __forceinline__ void obs_prep_body(const Consts<T>& k, const Bufs<T>&
 }
 
 // ell'(i) = ell_pred(i) + sum_d dh_d (g_d - dt/2 dh_d); per-block (max, sum) partials.
-// One warp per row, two coordinates per lane per load (float2), four loads in flight;
-// the per-step vectors g and c sit in shared memory.  Coordinates r..r_pad-1 are zero in
-// u and in g, so they add nothing.
+// One warp per row; lane l holds float2 l + 32 q of the row (the whole row is loaded
+// before any arithmetic, so that up to r_pad / 64 loads per lane are in flight); the
+// per-step vectors g and c sit in shared memory.  Coordinates r..r_pad-1 are zero in u and
+// in g, so they add nothing.
+constexpr int kRowQ = YY_MAX_DIM / 64;
+
 template <typename T>
 __device__ __forceinline__ void loglik_body(const Consts<T>& k, const Bufs<T>& b, int bid, int nblk) {
     __shared__ double sm[8], ss[8];
@@ -102,32 +105,26 @@ __device__ __forceinline__ void loglik_body(const Consts<T>& k, const Bufs<T>& b
     const long long nwarps = ((long long)nblk * blockDim.x) >> 5;
     const T half_dt = T(0.5) * k.dt;
     const bool cubic = k.model == YY_MODEL_CUBIC;
+    const int nq = k.r_pad >> 6;
     double m = -INFINITY, s = 0.0;
     for (long long i = warp; i < k.n; i += nwarps) {
         const T p = b.logw_pred[i];
         const float2* ui = reinterpret_cast<const float2*>(b.u + (size_t)i * k.r_pad);
-        T acc[4] = {T(0), T(0), T(0), T(0)};
-        const int nv = k.r_pad >> 1;   // float2 per row (r_pad is a multiple of 64)
-        for (int v0 = lane; v0 < nv; v0 += 128) {
-            float2 uu[4];
+        float2 uu[kRowQ];
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int v = v0 + 32 * q;
-                uu[q] = (v < nv) ? ui[v] : make_float2(0.f, 0.f);
-            }
+        for (int q = 0; q < kRowQ; ++q) uu[q] = (q < nq) ? ui[lane + 32 * q] : make_float2(0.f, 0.f);
+        T acc[2] = {T(0), T(0)};
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int d = 2 * (v0 + 32 * q);
-                if (d < k.r_pad) {
-                    const T u0 = (T)uu[q].x, u1 = (T)uu[q].y;
-                    const T c0 = s_c[d], c1 = s_c[d + 1];
-                    const T h0 = cubic ? u0 * (T(3) * c0 * c0 + T(3) * c0 * u0 + u0 * u0) : u0;
-                    const T h1 = cubic ? u1 * (T(3) * c1 * c1 + T(3) * c1 * u1 + u1 * u1) : u1;
-                    acc[q] += h0 * (s_g[d] - half_dt * h0) + h1 * (s_g[d + 1] - half_dt * h1);
-                }
-            }
+        for (int q = 0; q < kRowQ; ++q) {
+            if (q >= nq) break;   // uniform over the warp
+            const int d = 64 * q + 2 * lane;
+            const T u0 = (T)uu[q].x, u1 = (T)uu[q].y;
+            const T c0 = s_c[d], c1 = s_c[d + 1];
+            const T h0 = cubic ? u0 * (T(3) * c0 * c0 + T(3) * c0 * u0 + u0 * u0) : u0;
+            const T h1 = cubic ? u1 * (T(3) * c1 * c1 + T(3) * c1 * u1 + u1 * u1) : u1;
+            acc[q & 1] += h0 * (s_g[d] - half_dt * h0) + h1 * (s_g[d + 1] - half_dt * h1);
         }
-        T tot = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        T tot = acc[0] + acc[1];
         tot = warp_sum_u(tot);
         const T lw = (p == T(-INFINITY)) ? T(-INFINITY) : p + tot;
         if (lane == 0) {
@@ -590,9 +587,12 @@ template <typename T>
 cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy,
                           int restart_interval, double ess_frac, cudaStream_t s, int* launches) {
     const int nb = kNumPartBlocks;
+    // the likelihood pass runs 4 blocks per SM (its partials are 2 doubles per block,
+    // well inside the moment partials' space)
+    const int nbl = 4 * kNumPartBlocks;
     k_obs_prep<T><<<1, 256, 0, s>>>(k, b, dy);
-    k_loglik<T><<<nb, 256, 0, s>>>(k, b);
-    k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 0);
+    k_loglik<T><<<nbl, 256, 0, s>>>(k, b);
+    k_lse_merge<<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0);
     k_moments<T><<<nb, 256, 0, s>>>(k, b);
     k_finalize_scalars<T><<<1, 512, 0, s>>>(k, b, nb, restart_interval, ess_frac);
     k_finalize_dims<T><<<(k.r + 31) / 32, 256, 0, s>>>(k, b, nb);
