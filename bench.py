@@ -126,13 +126,15 @@ def _make_filter(w, precision, seed, device, stream=None, screen_prefix=0):
 
 
 def _algorithmic_flops(w, precision, screen=None):
-    """Per prediction launch: BF16 path -> the Gram products of the screen, 2 n^2 (64 k)
-    flops for the first pass over the first 64 k coordinates plus 2 n^2 r for the fraction
-    of tiles screened again over all coordinates (screen = (k, tiles, rescreened));
+    """Per prediction launch: BF16 path -> the Gram products the screen runs, i.e. per
+    screened block of 128 targets x 256 sources 2 x 128 x 256 x (64 k) flops for the first
+    pass over the first 64 k coordinates, plus 2 x 128 x 256 x r for every block screened
+    again over all coordinates (screen = (k, blocks, rescreened); with the symmetric screen
+    the blocks cover the upper block triangle, about half of the n^2 pairs);
     FP32/FP64 path -> difference form, 3 flops per coordinate per pair."""
     if precision == "bf16":
         k, tiles, resc = screen
-        return 2.0 * w.n * w.n * (min(64 * k, w.r) + w.r * resc / max(tiles, 1)), "tensor"
+        return 2.0 * 128 * 256 * (tiles * min(64 * k, w.r) + resc * w.r), "tensor"
     return 3.0 * w.n * w.n * w.r, "alu"
 
 

@@ -18,20 +18,43 @@ long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
 constexpr int kMaxTcGrid = 1024;
 
-// Work list of the single-filter BF16 prediction: one persistent CTA per SM, every target
-// tile split into S source ranges (S minimising the makespan), items dealt round-robin
-// (all items cost the same).  Copied into the workspace; synchronous (set-up only).
+// Work list of the single-filter BF16 prediction: one persistent CTA per SM.  Symmetric
+// screen (the usual case): target tile a (128 rows) covers the source tiles from the one
+// holding row 128 a on (L_a = nst - a / 2 tiles of 256), split into tc_sym_splits(L_a)
+// ranges; items are assigned longest first to the least loaded CTA.  Otherwise every
+// target tile is split into S ranges (S minimising the makespan) dealt round-robin.
+// Copied into the workspace; synchronous (set-up only).
 yy_status build_tc_schedule(yy_filter* f) {
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long tiles = f->n_pad / 128;
     const int nst = (int)(f->n_pad / 256);
     const int grid = (int)std::min<long long>(std::min(sms, kMaxTcGrid), tiles * 8);
-    const int S = tc_choose_splits(tiles, nst, grid);
     std::vector<std::vector<int4>> per(grid);
-    long long j = 0;
-    for (long long t = 0; t < tiles; ++t)
-        for (int q = 0; q < S; ++q, ++j) per[j % grid].push_back(make_int4(0, (int)t, q, S));
+    int S = 1;
+    if (f->kf.tc_sym) {
+        struct It { double cost; int t, q, S; };
+        std::vector<It> all;
+        for (long long t = 0; t < tiles; ++t) {
+            const int L = nst - (int)(t / 2);
+            const int St = tc_sym_splits(L);
+            for (int q = 0; q < St; ++q)
+                all.push_back({(double)((L * (q + 1)) / St - (L * q) / St) + 1.0, (int)t, q, St});
+            S = std::max(S, St);
+        }
+        std::stable_sort(all.begin(), all.end(), [](const It& x, const It& y) { return x.cost > y.cost; });
+        std::vector<double> load(grid, 0.0);
+        for (const It& it : all) {
+            const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            per[c].push_back(make_int4(0, it.t, it.q, it.S));
+            load[c] += it.cost;
+        }
+    } else {
+        S = tc_choose_splits(tiles, nst, grid);
+        long long j = 0;
+        for (long long t = 0; t < tiles; ++t)
+            for (int q = 0; q < S; ++q, ++j) per[j % grid].push_back(make_int4(0, (int)t, q, S));
+    }
     std::vector<int4> items;
     std::vector<int> start(grid + 1);
     for (int c = 0; c < grid; ++c) {
@@ -114,6 +137,10 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
         b.nu_chunk = cv.take<float>((size_t)n_pad * (r_pad / kColAlign) * sizeof(float));
         b.tc_q = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_q1 = cv.take<float>((size_t)n_pad * sizeof(float));
+        b.tc_q1t = cv.take<float>((size_t)n_pad * sizeof(float));
+        b.tc_qt = cv.take<float>((size_t)n_pad * sizeof(float));
+        b.tc_qt1 = cv.take<float>((size_t)n_pad * sizeof(float));
+        b.tc_xlse = cv.take<unsigned long long>((size_t)n_pad * kMaxScales * sizeof(unsigned long long));
         b.tc_tile_lmax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
         b.tc_tile_numax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
         b.tc_tile_numax1 = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
@@ -170,6 +197,8 @@ void fill_consts(yy_filter* f, Consts<T>* k, const double* halfwidth) {
     k->model = c.model;
     k->model_a = (T)c.model_a;
     k->tc_prefix = c.screen_prefix > 0 ? c.screen_prefix : 0;
+    // symmetric blocks need the long-row epilogue (r > 64)
+    k->tc_sym = (c.precision == YY_PREC_BF16 && c.r > 64) ? 1 : 0;
     k->dt = (T)c.dt;
     double log_vol = 0.0;
     for (int d = 0; d < c.r; ++d) log_vol += log(2.0 * (halfwidth ? halfwidth[d] : c.R));

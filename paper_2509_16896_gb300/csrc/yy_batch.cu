@@ -160,6 +160,7 @@ yy_status upload(yy_batch* bt) {
         tr[b].ess_frac = f->cfg.ess_frac;
         tr[b].restart_init = f->cfg.restart_init;
         tr[b].path = bt->path[b];
+        tr[b].k.tc_sym = 0;   // batch work lists cover every block
         tr[b].b.tc_splits = splits[b];
         if (bt->precision == YY_PREC_BF16) {
             if (!make_tc_map(&maps[kMapBytes * 2 * b], f->bf.ubf, f->n_pad, f->r_pad, 128) ||

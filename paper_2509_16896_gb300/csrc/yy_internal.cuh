@@ -65,6 +65,7 @@ struct Consts {
     T inv2tau[kMaxScales];   // 1 / (2 tau_j)
     T cj_off[kMaxScales];    // C_j - C_ref, C_j = -(r/2) log(2 pi tau_j) + log w_q
     int tc_prefix;           // fixed first-pass chunks of the BF16 screen (0 = adaptive)
+    int tc_sym;              // BF16 screen over the upper block triangle, both directions per block
     T logabs_c[kMaxScales + 1];
     T sign_c[kMaxScales + 1];  // 0 for a zero coefficient
     double c_ref;
@@ -103,6 +104,12 @@ struct Bufs {
     float* nu_chunk;      // [n_pad][r_pad / 64] |u_i|^2 per chunk of 64 coordinates (BF16 only)
     float* tc_q;          // [n_pad] |u_s|^2 of live sources, 3e38 for dead ones
     float* tc_q1;         // [n_pad] the same over the first-pass coordinates
+    float* tc_q1t;        // [n_pad] first-pass |u_s|^2 of every node (as a target)
+    float* tc_qt;         // [n_pad] column-direction screen value of every node as a target:
+                          // |u_c|^2 - (rho_c^2 + err_c) (+inf: no target, -inf: no bound)
+    float* tc_qt1;        // [n_pad] the same over the first-pass coordinates
+    unsigned long long* tc_xlse;   // [n_pad][kMaxScales] (max, sum) float pairs of the terms a
+                                   // node receives as the column of a symmetric block
     float* tc_tile_lmax;  // [n_pad / 128] max live log-weight per chunk of 128 sources
     float* tc_tile_numax; // [n_pad / 128] max |u_s|^2 per chunk of 128 sources
     float* tc_tile_numax1;// [n_pad / 128] the same over the first-pass coordinates
@@ -125,6 +132,13 @@ struct Traj {
     int restart_init;
     int path;              // prediction kernel: 0 = tcgen05 screen, 1 = FP32 form
 };
+
+// Source splits of target tile a of the symmetric screen: its L source tiles in ranges of
+// about 64 (at most 8), so that the work list balances.
+__host__ __device__ __forceinline__ int tc_sym_splits(int L) {
+    const int s = (L + 63) / 64;
+    return s < 1 ? 1 : (s > 8 ? 8 : s);
+}
 
 // Launch helpers (defined in the .cu files).
 template <typename T>

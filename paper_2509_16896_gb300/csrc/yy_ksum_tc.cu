@@ -76,9 +76,10 @@ struct Cfg {
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators of BN fp32 columns
     static constexpr int HALF = BN / 2;   // columns of one epilogue warp
-    // ring | q values and candidate masks per epilogue warp | marking bitmaps | row states
+    // ring | row- and column-direction q values and candidate masks per epilogue warp |
+    // marking bitmaps | row states
     // exchanged between the two warps of a lane quarter | barriers
-    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 2 * EPI_WARPS * HALF * 4 +
+    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 4 * EPI_WARPS * HALF * 4 +
                                       EPI_WARPS * 2 * kEscWords * 4 + 128 * kMaxScales * 2 * 4 + 256;
     // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1),
     // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -280,6 +281,9 @@ __device__ __forceinline__ void colprep_body(const Consts<float>& k, const Bufs<
     }
     b.tc_q[s] = live ? nu : tc::kDeadQ;
     b.tc_q1[s] = live ? nu1 : tc::kDeadQ;
+    b.tc_q1t[s] = nu1;
+#pragma unroll
+    for (int j = 0; j < kMaxScales; ++j) b.tc_xlse[(size_t)s * kMaxScales + j] = 0ull;   // empty (sum 0)
     float lm = live ? lw : -INFINITY, nm = live ? nu : 0.f, nm1 = live ? nu1 : 0.f;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -355,6 +359,82 @@ __device__ void tc_adapt(const Consts<float>& k, DevStats* st) {
     st->tc_nk1 = next;
 }
 
+// Column direction of the symmetric screen, per node c as a target: every source s with
+// |u_c - u_s| <= rho_c can carry more than e^-T of c's row, where, as in the row direction,
+//     rho_c = max_j [tau_j |f_c| + sqrt(2 tau_j max(0, lmax - M_j(c) + T))],
+// but with the reference M_j(c) = the exact self term of c (a lower bound of the row
+// maximum) and lmax the largest live log-weight of all sources.  The screen compares
+// |u_i|^2 + |u_c|^2 - 2 G with rho_c^2 + err_c (err_c as in the row direction, with the
+// largest live |u_s|^2); stored is |u_c|^2 - (rho_c^2 + err_c), over all coordinates (tc_qt)
+// and over the first-pass coordinates (tc_qt1).  Masked or padded nodes are no targets
+// (+inf); a live node without a finite log-weight has no reference (-inf: every pair).
+__device__ __forceinline__ void colprep2_body(const Consts<float>& k, const Bufs<float>& b, int chunk) {
+    __shared__ float red[3][4];
+    const int nch = (int)(k.n_pad / 128);
+    float lg = -INFINITY, ng = 0.f, ng1 = 0.f;
+    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+        lg = fmaxf(lg, b.tc_tile_lmax[c]);
+        ng = fmaxf(ng, b.tc_tile_numax[c]);
+        ng1 = fmaxf(ng1, b.tc_tile_numax1[c]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lg = fmaxf(lg, __shfl_xor_sync(0xffffffffu, lg, o));
+        ng = fmaxf(ng, __shfl_xor_sync(0xffffffffu, ng, o));
+        ng1 = fmaxf(ng1, __shfl_xor_sync(0xffffffffu, ng1, o));
+    }
+    if ((threadIdx.x & 31) == 0) { red[0][threadIdx.x >> 5] = lg; red[1][threadIdx.x >> 5] = ng; red[2][threadIdx.x >> 5] = ng1; }
+    __syncthreads();
+    for (int w = 0; w < 4; ++w) { lg = fmaxf(lg, red[0][w]); ng = fmaxf(ng, red[1][w]); ng1 = fmaxf(ng1, red[2][w]); }
+    const long long c = (long long)chunk * 128 + threadIdx.x;
+    float qt = INFINITY, qt1 = INFINITY;
+    if (c < k.n && !b.mask[c] && lg != -INFINITY) {
+        const float lc = b.logw[c];
+        if (lc == -INFINITY) {
+            qt = qt1 = -INFINITY;
+        } else {
+            const float T = logf((float)k.n) + 20.0f;
+            const float nfc = b.nf[c], Fc = sqrtf(nfc);
+            float rho = 0.f;
+#pragma unroll 4
+            for (int j = 0; j < k.N; ++j) {
+                const float gap = fmaxf(lg - (-0.5f * k.tau[j] * nfc + lc) + T, 0.f);
+                rho = fmaxf(rho, k.tau[j] * Fc + sqrtf(2.f * k.tau[j] * gap));
+            }
+            const float q = b.nu[c], q1 = b.tc_q1t[c];
+            const float e = 2.f * tc::kEpsGram * sqrtf(q * ng) + 1e-6f * (q + ng + rho * rho);
+            const float e1 = 2.f * tc::kEpsGram * sqrtf(q1 * ng1) + 1e-6f * (q1 + ng1 + rho * rho);
+            qt = q - fminf(rho * rho + e, tc::kThetaMax);
+            qt1 = q1 - fminf(rho * rho + e1, tc::kThetaMax);
+        }
+    }
+    b.tc_qt[c] = qt;
+    b.tc_qt1[c] = qt1;
+}
+
+__global__ void __launch_bounds__(128) k_tc_colprep2(Consts<float> k, Bufs<float> b) { colprep2_body(k, b, blockIdx.x); }
+
+// Adds e^score to a log-sum-exp accumulator kept as one 64-bit word (low half: running
+// maximum, high half: sum of e^(term - maximum); sum 0 = empty) by compare-and-swap.  Every
+// failed exchange means another thread's update went through, so the loop ends; it is
+// capped all the same, with the status word recording a give-up.
+__device__ __forceinline__ void lse_atomic_add(unsigned long long* w, float score, unsigned int* status) {
+    unsigned long long old = *reinterpret_cast<volatile unsigned long long*>(w);
+    for (int tries = 0; tries < (1 << 20); ++tries) {
+        const float m = __uint_as_float((uint32_t)old), sm = __uint_as_float((uint32_t)(old >> 32));
+        float m2, s2;
+        if (sm == 0.f) { m2 = score; s2 = 1.f; }
+        else if (score > m) { m2 = score; s2 = fmaf(sm, expf(m - score), 1.f); }
+        else { m2 = m; s2 = sm + expf(score - m); }
+        const unsigned long long nw = (unsigned long long)__float_as_uint(m2) |
+                                      ((unsigned long long)__float_as_uint(s2) << 32);
+        const unsigned long long seen = atomicCAS(w, old, nw);
+        if (seen == old) return;
+        old = seen;
+    }
+    atomicOr(status, kStatusTimeout);
+}
+
 // Work list of a launch: CTA c processes items[cta_start[c] .. cta_start[c + 1]), each
 // (filter, target tile, split, nsplit): target rows 128 tile .. +127 against source tiles
 // [nst split / nsplit, nst (split + 1) / nsplit).  tr == nullptr: single filter, passed by
@@ -383,6 +463,8 @@ __device__ __forceinline__ float* part_slot(const Bufs<float>& b, long long i, i
 // an mbarrier, and pass 2 recomputes the marked tiles over all coordinates and screens them
 // again (only the marking warps use the result).  With nk1 = nk there is one pass.
 template <int N, int BN>
+// One CTA per SM; with 10 warps two of the four SM sub-partitions hold three warps each, so
+// the register budget is 168 per thread.
 __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     k_ksum_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ Consts<float> k0, const __grid_constant__ Bufs<float> b0, TcWork w) {
@@ -390,13 +472,14 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     using C = Cfg<BN>;
     constexpr int STAGES = C::STAGES;
     constexpr int STAGE_BYTES = C::STAGE_BYTES;
-    constexpr int NCH = BN / 32;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int HALF = C::HALF;
     float* qs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);   // [EPI_WARPS][HALF]
-    uint32_t* cms = reinterpret_cast<uint32_t*>(qs + EPI_WARPS * HALF);  // [EPI_WARPS][HALF / 32][32]
-    uint32_t* escm = cms + EPI_WARPS * HALF;                             // [EPI_WARPS][2][kEscWords]
+    float* qts = qs + EPI_WARPS * HALF;                                  // [EPI_WARPS][HALF]
+    uint32_t* cms = reinterpret_cast<uint32_t*>(qts + EPI_WARPS * HALF); // [EPI_WARPS][HALF / 32][32]
+    uint32_t* tcms = cms + EPI_WARPS * HALF;                             // [EPI_WARPS][HALF / 32][32]
+    uint32_t* escm = tcms + EPI_WARPS * HALF;                            // [EPI_WARPS][2][kEscWords]
     float* xch = reinterpret_cast<float*>(escm + EPI_WARPS * 2 * kEscWords);   // [128 rows][kMaxScales][2]
     uint64_t* bars = reinterpret_cast<uint64_t*>(xch + 128 * kMaxScales * 2);
     uint64_t* full = bars;
@@ -453,9 +536,12 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         i0 = (long long)it.y * BM;
         split = it.z;
         nsplit = it.w;
+        // symmetric screen: only source tiles from the one holding the tile's first row on
         const int nst = (int)(kp->n_pad / BN);
-        t0 = (int)(((long long)nst * split) / nsplit);
-        t1 = (int)(((long long)nst * (split + 1)) / nsplit);
+        const int bmin = kp->tc_sym ? (int)(i0 / BN) : 0;
+        const int L = nst - bmin;
+        t0 = bmin + (int)(((long long)L * split) / nsplit);
+        t1 = bmin + (int)(((long long)L * (split + 1)) / nsplit);
         nk = kp->r_pad / BK;
         nk1 = (t1 - t0 <= kEscWords * 32) ? prefix_chunks(*kp, bp->stats) : nk;
     };
@@ -566,7 +652,9 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         const int q = warp & 3;        // TMEM lane quarter (fixed by the warp's rank in its warpgroup)
         const int h = ew >> 2;         // column half
         float* qw = qs + ew * HALF;
+        float* qtw = qts + ew * HALF;      // column direction: q_c - (rho_c^2 + err_c)
         uint32_t* cmw = cms + ew * HALF;   // candidate masks of one tile, [HALF / 32][32 lanes]
+        uint32_t* tcmw = tcms + ew * HALF; // column-direction candidate masks
         float* xrow = xch + (size_t)(q * 32 + lane) * kMaxScales * 2;
         uint32_t tcount = 0, npre = 0, nitem = 0;
         bool ok = true;
@@ -664,38 +752,97 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&tempty[acc]);
             };
+            // column direction of a symmetric block: target c (a column) from source i (a
+            // row of this item); exact score with the drift at the target, added to the
+            // target's accumulator word
+            const bool src_live = live && li != -INFINITY;
+            auto eval_warp_t = [&](uint32_t cm, long long sb) {
+                while (true) {
+                    const uint32_t who = __ballot_sync(0xffffffffu, cm != 0u);
+                    if (who == 0u) break;
+                    const int leader = __ffs(who) - 1;
+                    const int c = __shfl_sync(0xffffffffu, __ffs(cm) - 1, leader);
+                    const long long tgt = sb + c;
+                    const long long src = i0 + q * 32 + leader;
+                    const float* ut = b.u + (size_t)tgt * k.r_pad;
+                    const float* us = b.u + (size_t)src * k.r_pad;
+                    float s1 = 0.f, s2 = 0.f;
+                    for (int d = lane; d < k.r; d += 32) {
+                        const float dl = ut[d] - us[d];
+                        s1 = fmaf(dl, dl, s1);
+                        s2 = fmaf(dl, drift_at(k, b, ut[d], d), s2);
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                    }
+                    if (lane == leader) {
+                        const float nft = b.nf[tgt];
+#pragma unroll
+                        for (int j = 0; j < N; ++j) {
+                            const float sc = fmaf(-s1, k.inv2tau[j], s2) + (-0.5f * k.tau[j] * nft + li);
+                            lse_atomic_add(&b.tc_xlse[(size_t)tgt * kMaxScales + j], sc, status);
+                        }
+                        cm &= cm - 1u;
+                        ++ncand;
+                    }
+                }
+            };
+            const long long a_chunk = i0 / 128;   // the item's target tile as a chunk of 128
             // one tile: mode 0 = single full pass, 1 = first pass, 2 = second pass of a tile
-            // this warp marked, 3 = second pass of a tile only other warps marked
+            // this warp marked, 3 = second pass of a tile only other warps marked.  In a
+            // symmetric screen this warp's 128-column chunk c is skipped when c < a_chunk
+            // (its pairs belong to the block with the roles swapped), screened for this
+            // item's rows only when c = a_chunk, and screened in both directions when
+            // c > a_chunk.
             auto tile = [&](int t, int mode) -> bool {
                 const int acc = (int)(tcount & 1u);
                 const uint32_t aph = (tcount >> 1) & 1u;
                 ++tcount;
-                float theta = -INFINITY, lmax = -INFINITY, numax = 0.f;
-                const float nu_s = (mode == 1) ? nu1_i : nu_i;
                 const long long c0 = (long long)t * BN + h * HALF;   // first source of this warp
-                if (mode != 3) {
-                    const float* qsrc = (mode == 1) ? b.tc_q1 : b.tc_q;
-                    const float* nmx = (mode == 1) ? b.tc_tile_numax1 : b.tc_tile_numax;
-                    __syncwarp();
+                const long long cchunk = c0 / 128;
+                const int hm = !k.tc_sym ? 1 : (cchunk < a_chunk ? 0 : (cchunk == a_chunk ? 1 : 2));
+                if (mode == 3 || hm == 0) {
+                    if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) return false;
+                    tc_fence_after();
+                    release(acc);
+                    return true;
+                }
+                const bool first_pass = (mode == 1);
+                const float nu_s = first_pass ? nu1_i : nu_i;
+                const float* qsrc = first_pass ? b.tc_q1 : b.tc_q;
+                const float* nmx = first_pass ? b.tc_tile_numax1 : b.tc_tile_numax;
+                __syncwarp();
+                {
                     const float4* src4 = reinterpret_cast<const float4*>(qsrc + c0);
                     float4* dst4 = reinterpret_cast<float4*>(qw);
                     for (int c = lane; c < HALF / 4; c += 32) dst4[c] = src4[c];
-                    __syncwarp();
-                    lmax = b.tc_tile_lmax[t * (BN / 128)];
-                    numax = nmx[t * (BN / 128)];
-                    if (BN == 256) {
-                        lmax = fmaxf(lmax, b.tc_tile_lmax[2 * t + 1]);
-                        numax = fmaxf(numax, nmx[2 * t + 1]);
-                    }
-                    theta = screen_theta<N>(k, live, nu_s, Fi, mx, lmax, numax, T);
                 }
+                float lmax = b.tc_tile_lmax[t * (BN / 128)];
+                float numax = nmx[t * (BN / 128)];
+                if (BN == 256) {
+                    lmax = fmaxf(lmax, b.tc_tile_lmax[2 * t + 1]);
+                    numax = fmaxf(numax, nmx[2 * t + 1]);
+                }
+                float theta = screen_theta<N>(k, live, nu_s, Fi, mx, lmax, numax, T);
+                // column direction: per column c the precomputed q_c - (rho_c^2 + err_c) of c
+                // as a target; the row side adds nu_i (+inf for dead rows)
+                float nu_src = INFINITY;
+                if (hm == 2) {
+                    nu_src = src_live ? nu_s : INFINITY;
+                    const float4* t4 = reinterpret_cast<const float4*>((first_pass ? b.tc_qt1 : b.tc_qt) + c0);
+                    float4* d4 = reinterpret_cast<float4*>(qtw);
+                    for (int c = lane; c < HALF / 4; c += 32) d4[c] = t4[c];
+                }
+                __syncwarp();
                 if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) return false;
                 tc_fence_after();
-                if (mode == 3) { release(acc); return true; }
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + h * HALF);
                 if (k.r <= 64) {
-                    // short rows (one pass): every lane evaluates its own row's candidates
-                    // chunk by chunk, tightening the screen as the running maxima grow
+                    // short rows (one pass, no symmetric blocks): every lane evaluates its own
+                    // row's candidates chunk by chunk, tightening the screen as the running
+                    // maxima grow
                     const float* ut = b.u + (size_t)i * k.r_pad;
                     for (int ch = 0; ch < HALF / 32; ++ch) {
                         uint32_t v[32];
@@ -730,7 +877,8 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     return true;
                 }
                 // long rows: 64 columns per TMEM load; the smallest q_s - 2 G of a lane's 64
-                // columns decides whether its candidate masks are needed at all
+                // columns (and, for symmetric blocks, the smallest column-direction value)
+                // decides whether candidate masks are needed at all
                 int cnt = 0;
                 for (int part = 0; part < HALF / 64; ++part) {
                     uint32_t v[64];
@@ -747,7 +895,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                         mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 2]), qq.z));
                         mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 3]), qq.w));
                     }
-                    uint32_t m0 = 0, m1 = 0;
+                    uint32_t m0 = 0, m1 = 0, t0m = 0, t1m = 0;
                     if (mn <= theta) {
 #pragma unroll
                         for (int c = 0; c < 32; ++c) {
@@ -760,18 +908,46 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                         if (i >= sb + 32 && i < sb + 64) m1 &= ~(1u << (int)(i - sb - 32));
                         cnt += __popc(m0) + __popc(m1);
                     }
+                    if (hm == 2) {
+                        const float4* t4 = reinterpret_cast<const float4*>(qtw + part * 64);
+                        float mt = INFINITY;
+#pragma unroll
+                        for (int c4 = 0; c4 < 16; ++c4) {
+                            const float4 qq = t4[c4];
+                            mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 0]), qq.x));
+                            mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 1]), qq.y));
+                            mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 2]), qq.z));
+                            mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 3]), qq.w));
+                        }
+                        if (mt + nu_src <= 0.f) {
+#pragma unroll
+                            for (int c = 0; c < 32; ++c) {
+                                t0m |= (fmaf(-2.f, __uint_as_float(v[c]), qtw[part * 64 + c]) + nu_src <= 0.f ? 1u : 0u)
+                                       << c;
+                                t1m |= (fmaf(-2.f, __uint_as_float(v[32 + c]), qtw[part * 64 + 32 + c]) + nu_src <= 0.f
+                                            ? 1u
+                                            : 0u)
+                                       << c;
+                            }
+                            cnt += __popc(t0m) + __popc(t1m);
+                        }
+                    }
                     cmw[(2 * part) * 32 + lane] = m0;
                     cmw[(2 * part + 1) * 32 + lane] = m1;
+                    tcmw[(2 * part) * 32 + lane] = t0m;
+                    tcmw[(2 * part + 1) * 32 + lane] = t1m;
                 }
                 release(acc);
                 const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
                 if (tot == 0) return true;
-                if (mode == 1 && (tot > kEscThresh || exact1 + tot > kExactBudget)) {
+                if (first_pass && (tot > kEscThresh || exact1 + tot > kExactBudget)) {
                     if (lane == 0) myesc[(t - t0) >> 5] |= 1u << ((t - t0) & 31);
                     return true;
                 }
-                if (mode == 1) exact1 += tot;
+                if (first_pass) exact1 += tot;
                 for (int ch = 0; ch < HALF / 32; ++ch) eval_warp(cmw[ch * 32 + lane], c0 + ch * 32);
+                if (hm == 2)
+                    for (int ch = 0; ch < HALF / 32; ++ch) eval_warp_t(tcmw[ch * 32 + lane], c0 + ch * 32);
                 return true;
             };
             for (int t = t0; t < t1 && ok; ++t) ok = tile(t, pre ? 1 : 0);
@@ -809,7 +985,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&xfree[q]);
                     if (in_range) {
-                        if (nsplit == 1) {
+                        if (nsplit == 1 && !k.tc_sym) {
                             b.logw_pred[i] = live ? combine_scales<float, N>(k, mx, sm, b.divf[i], li,
                                                                              b.stats->c_ref, &b.stats->clamps)
                                                   : -INFINITY;
@@ -853,23 +1029,32 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     }
 }
 
-// Combines the split states of every row and applies the multi-scale combination.
+// Combines the split states of every row (and, for the symmetric screen, the terms the row
+// received as a column) and applies the multi-scale combination.
 template <int N>
 __device__ __forceinline__ void tc_merge_body(const Consts<float>& k, const Bufs<float>& b, int nsplit, int bid, int nblk) {
-    if (nsplit <= 1) return;
+    if (nsplit <= 1 && !k.tc_sym) return;
+    const int nst = (int)(k.n_pad / 256);
     for (long long i = bid * (long long)blockDim.x + threadIdx.x; i < k.n; i += (long long)nblk * blockDim.x) {
         if (b.mask[i]) { b.logw_pred[i] = -INFINITY; continue; }
+        const int ns = k.tc_sym ? tc_sym_splits(nst - (int)(i / 256)) : nsplit;
         float mx[N], sm[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
             float m = -INFINITY, s = 0.f;
-            for (int q = 0; q < nsplit; ++q) {
-                const float* ps = part_slot(b, i, q, j);
-                const float m2 = ps[0], s2 = ps[1];
-                if (m2 == -INFINITY) continue;
+            auto add = [&](float m2, float s2) {
+                if (m2 == -INFINITY || !(s2 > 0.f)) return;
                 if (m == -INFINITY) { m = m2; s = s2; }
                 else if (m2 > m) { s = s * expf(m - m2) + s2; m = m2; }
                 else s += s2 * expf(m2 - m);
+            };
+            for (int q = 0; q < ns; ++q) {
+                const float* ps = part_slot(b, i, q, j);
+                add(ps[0], ps[1]);
+            }
+            if (k.tc_sym) {
+                const unsigned long long w = b.tc_xlse[(size_t)i * kMaxScales + j];
+                add(__uint_as_float((uint32_t)w), __uint_as_float((uint32_t)(w >> 32)));
             }
             mx[j] = m;
             sm[j] = s;
@@ -930,6 +1115,10 @@ template <int BN>
 cudaError_t set_attr_all() {
     cudaError_t e = cudaSuccess;
     const int sm = tc::Cfg<BN>::SMEM_BYTES;
+    // the block must be launchable at its size (registers per thread x threads)
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, k_ksum_tc<3, BN>)) != cudaSuccess) return e;
+    if (fa.maxThreadsPerBlock < tc::NUM_THREADS) return cudaErrorLaunchOutOfResources;
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<1, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<2, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<3, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
@@ -987,11 +1176,15 @@ cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStr
     if (e != cudaSuccess) return e;
     k_tc_colprep<<<(unsigned)(k.n_pad / 128), 128, 0, s>>>(k, b);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (k.tc_sym) {
+        k_tc_colprep2<<<(unsigned)(k.n_pad / 128), 128, 0, s>>>(k, b);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     const TcWork w{nullptr, nullptr, b.tc_items, b.tc_cta_start, 1};
     e = launch_bn<256>(k.N, (unsigned)b.tc_grid, ma, mb, k, b, w, s);
     if (e != cudaSuccess) return e;
-    int l = 2;
-    if (b.tc_splits > 1) {
+    int l = k.tc_sym ? 3 : 2;
+    if (b.tc_splits > 1 || k.tc_sym) {
         const unsigned g = (unsigned)std::min<long long>((k.n + 255) / 256, 1024);
         switch (k.N) {
             case 1: k_tc_merge<1><<<g, 256, 0, s>>>(k, b, b.tc_splits); break;

@@ -51,7 +51,10 @@ def test_every_first_pass_length_matches_fp32_path(yy_lib, r, n, N):
         b, b_off = flt.get_log_weights()
         assert rel_err(b.astype(np.float64) + b_off, a) <= 2e-6, (prefix, spread)
         last, nxt, tiles, resc = flt.screen()
-        assert tiles == (n_pad // 128) * (n_pad // 256)
+        # the screen covers the upper block triangle: target tile a (128 rows) against the
+        # source tiles (256) from the one holding its first row on
+        nst = n_pad // 256
+        assert tiles == sum(nst - a // 2 for a in range(n_pad // 128))
         assert 0 <= resc <= tiles
         assert 1 <= last <= nk and 1 <= nxt <= nk
         if prefix == nk:
