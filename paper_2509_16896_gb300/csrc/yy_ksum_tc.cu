@@ -76,10 +76,10 @@ struct Cfg {
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators of BN fp32 columns
     static constexpr int HALF = BN / 2;   // columns of one epilogue warp
-    // ring | row- and column-direction q values and candidate masks per epilogue warp |
-    // marking bitmaps | row states
-    // exchanged between the two warps of a lane quarter | barriers
-    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 4 * EPI_WARPS * HALF * 4 +
+    // ring | row- and column-direction q values per accumulator | candidate masks per
+    // epilogue warp | marking bitmaps | row states exchanged between the two warps of a lane
+    // quarter | barriers
+    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 4 * BN * 4 + 2 * EPI_WARPS * HALF * 4 +
                                       EPI_WARPS * 2 * kEscWords * 4 + 128 * kMaxScales * 2 * 4 + 256;
     // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1),
     // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -137,6 +137,16 @@ __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, vol
             return false;
         }
     }
+}
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16)
+// completing on an mbarrier.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    uint64_t g;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(reinterpret_cast<uint64_t>(src)));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(g), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
 }
 // Bounded wait used while draining after an abort (ignores the abort flag).
 __device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity) {
@@ -475,9 +485,11 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
     constexpr int HALF = C::HALF;
-    float* qs = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);   // [EPI_WARPS][HALF]
-    float* qts = qs + EPI_WARPS * HALF;                                  // [EPI_WARPS][HALF]
-    uint32_t* cms = reinterpret_cast<uint32_t*>(qts + EPI_WARPS * HALF); // [EPI_WARPS][HALF / 32][32]
+    // q_s of the tile's sources and, for symmetric blocks, the column-direction values,
+    // staged by the producer per accumulator: [2][BN] each
+    float* qbuf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
+    float* qtbuf = qbuf + 2 * BN;
+    uint32_t* cms = reinterpret_cast<uint32_t*>(qtbuf + 2 * BN);         // [EPI_WARPS][HALF / 32][32]
     uint32_t* tcms = cms + EPI_WARPS * HALF;                             // [EPI_WARPS][HALF / 32][32]
     uint32_t* escm = tcms + EPI_WARPS * HALF;                            // [EPI_WARPS][2][kEscWords]
     float* xch = reinterpret_cast<float*>(escm + EPI_WARPS * 2 * kEscWords);   // [128 rows][kMaxScales][2]
@@ -490,7 +502,8 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     uint64_t* escb = drain + 1;
     uint64_t* xfull = escb + 1;    // [4]: the second warp of lane quarter q stored its row states
     uint64_t* xfree = xfull + 4;   // [4]: the first warp of lane quarter q has read them
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(xfree + 4);
+    uint64_t* qfull = xfree + 4;   // [2]: the q values of the tile in accumulator a landed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(qfull + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -508,6 +521,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         mbar_init(drain, 1);
         mbar_init(escb, EPI_WARPS);
         for (int a = 0; a < 4; ++a) { mbar_init(&xfull[a], 1); mbar_init(&xfree[a], 1); }
+        for (int a = 0; a < 2; ++a) mbar_init(&qfull[a], 1);
         *abort_flag = 0;
         mbar_fence_init();
     }
@@ -561,9 +575,23 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             // ---- TMA producer -------------------------------------------------------
             int last_phase[STAGES];
             for (int s = 0; s < STAGES; ++s) last_phase[s] = -1;
-            uint32_t it = 0, npre = 0;
+            int last_qphase[2] = {-1, -1};
+            uint32_t it = 0, npre = 0, tp = 0;
             bool ok = true;
-            auto load_tile = [&](const CUtensorMap* ma, const CUtensorMap* mb, long long i0, int t, int nkb) -> bool {
+            // one tile: its q values into the accumulator's buffer (once the epilogue has
+            // released that accumulator), then its coordinate chunks into the ring
+            auto load_tile = [&](const Consts<float>* kp, const Bufs<float>* bp, const CUtensorMap* ma,
+                                 const CUtensorMap* mb, long long i0, int t, int nkb, bool prefix) -> bool {
+                const int acc = (int)(tp & 1u);
+                const uint32_t aph = (tp >> 1) & 1u;
+                ++tp;
+                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) return false;
+                const uint32_t qb = (uint32_t)(BN * sizeof(float));
+                mbar_arrive_expect_tx(&qfull[acc], kp->tc_sym ? 2 * qb : qb);
+                bulk_load(qbuf + acc * BN, (prefix ? bp->tc_q1 : bp->tc_q) + (size_t)t * BN, qb, &qfull[acc]);
+                if (kp->tc_sym)
+                    bulk_load(qtbuf + acc * BN, (prefix ? bp->tc_qt1 : bp->tc_qt) + (size_t)t * BN, qb, &qfull[acc]);
+                last_qphase[acc] = (int)aph;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = (int)(it % STAGES);
                     const uint32_t ph = (it / STAGES) & 1u;
@@ -581,17 +609,21 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 long long i0;
                 int t0, t1, split, nsplit, nk, nk1;
                 item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit, nk, nk1);
-                for (int t = t0; t < t1 && ok; ++t) ok = load_tile(ma, mb, i0, t, nk1);
-                if (ok && nk1 < nk) {
+                const bool pre = nk1 < nk;
+                for (int t = t0; t < t1 && ok; ++t) ok = load_tile(kp, bp, ma, mb, i0, t, nk1, pre);
+                if (ok && pre) {
                     const uint32_t par = npre++ & 1u;
                     if (!wait_bounded(escb, par, abort_flag, status)) { ok = false; break; }
                     for (int t = t0; t < t1 && ok; ++t)
-                        if (esc_any(par, t - t0)) ok = load_tile(ma, mb, i0, t, nk);
+                        if (esc_any(par, t - t0)) ok = load_tile(kp, bp, ma, mb, i0, t, nk, false);
                 }
             }
-            if (!ok)   // let our own copies land before shared memory is released
+            if (!ok) {   // let our own copies land before shared memory is released
                 for (int s = 0; s < STAGES; ++s)
                     if (last_phase[s] >= 0) wait_drain(&full[s], (uint32_t)last_phase[s]);
+                for (int a = 0; a < 2; ++a)
+                    if (last_qphase[a] >= 0) wait_drain(&qfull[a], (uint32_t)last_qphase[a]);
+            }
         }
     } else if (warp == 1) {
         if (lane == 0 && status) {
@@ -651,8 +683,6 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         const int ew = warp - 2;       // epilogue warp index 0..7
         const int q = warp & 3;        // TMEM lane quarter (fixed by the warp's rank in its warpgroup)
         const int h = ew >> 2;         // column half
-        float* qw = qs + ew * HALF;
-        float* qtw = qts + ew * HALF;      // column direction: q_c - (rho_c^2 + err_c)
         uint32_t* cmw = cms + ew * HALF;   // candidate masks of one tile, [HALF / 32][32 lanes]
         uint32_t* tcmw = tcms + ew * HALF; // column-direction candidate masks
         float* xrow = xch + (size_t)(q * 32 + lane) * kMaxScales * 2;
@@ -811,14 +841,10 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 }
                 const bool first_pass = (mode == 1);
                 const float nu_s = first_pass ? nu1_i : nu_i;
-                const float* qsrc = first_pass ? b.tc_q1 : b.tc_q;
                 const float* nmx = first_pass ? b.tc_tile_numax1 : b.tc_tile_numax;
-                __syncwarp();
-                {
-                    const float4* src4 = reinterpret_cast<const float4*>(qsrc + c0);
-                    float4* dst4 = reinterpret_cast<float4*>(qw);
-                    for (int c = lane; c < HALF / 4; c += 32) dst4[c] = src4[c];
-                }
+                // this warp's columns of the staged q values (producer, per accumulator)
+                const float* qw = qbuf + acc * BN + h * HALF;
+                const float* qtw = qtbuf + acc * BN + h * HALF;   // q_c - (rho_c^2 + err_c)
                 float lmax = b.tc_tile_lmax[t * (BN / 128)];
                 float numax = nmx[t * (BN / 128)];
                 if (BN == 256) {
@@ -828,14 +854,8 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 float theta = screen_theta<N>(k, live, nu_s, Fi, mx, lmax, numax, T);
                 // column direction: per column c the precomputed q_c - (rho_c^2 + err_c) of c
                 // as a target; the row side adds nu_i (+inf for dead rows)
-                float nu_src = INFINITY;
-                if (hm == 2) {
-                    nu_src = src_live ? nu_s : INFINITY;
-                    const float4* t4 = reinterpret_cast<const float4*>((first_pass ? b.tc_qt1 : b.tc_qt) + c0);
-                    float4* d4 = reinterpret_cast<float4*>(qtw);
-                    for (int c = lane; c < HALF / 4; c += 32) d4[c] = t4[c];
-                }
-                __syncwarp();
+                const float nu_src = (hm == 2 && src_live) ? nu_s : INFINITY;
+                if (!wait_bounded(&qfull[acc], aph, abort_flag, status)) return false;
                 if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) return false;
                 tc_fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + h * HALF);
