@@ -896,43 +896,39 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     release(acc);
                     return true;
                 }
-                // long rows: 64 columns per TMEM load; the smallest q_s - 2 G of a lane's 64
+                // long rows: 32 columns per TMEM load; the smallest q_s - 2 G of a lane's 32
                 // columns (and, for symmetric blocks, the smallest column-direction value)
                 // decides whether candidate masks are needed at all
                 int cnt = 0;
-                for (int part = 0; part < HALF / 64; ++part) {
-                    uint32_t v[64];
+                for (int ch = 0; ch < HALF / 32; ++ch) {
+                    uint32_t v[32];
                     __syncwarp();
-                    tmem_ld64(tbase + (uint32_t)(part * 64), v);
+                    tmem_ld32(tbase + (uint32_t)(ch * 32), v);
                     tmem_ld_wait();
-                    const float4* q4 = reinterpret_cast<const float4*>(qw + part * 64);
+                    const float4* q4 = reinterpret_cast<const float4*>(qw + ch * 32);
                     float mn = INFINITY;
 #pragma unroll
-                    for (int c4 = 0; c4 < 16; ++c4) {
+                    for (int c4 = 0; c4 < 8; ++c4) {
                         const float4 qq = q4[c4];
                         mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 0]), qq.x));
                         mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 1]), qq.y));
                         mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 2]), qq.z));
                         mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 3]), qq.w));
                     }
-                    uint32_t m0 = 0, m1 = 0, t0m = 0, t1m = 0;
+                    uint32_t m0 = 0, t0m = 0;
                     if (mn <= theta) {
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            m0 |= (fmaf(-2.f, __uint_as_float(v[c]), qw[part * 64 + c]) <= theta ? 1u : 0u) << c;
-                            m1 |= (fmaf(-2.f, __uint_as_float(v[32 + c]), qw[part * 64 + 32 + c]) <= theta ? 1u : 0u)
-                                  << c;
-                        }
-                        const long long sb = c0 + part * 64;   // self term already counted
+                        for (int c = 0; c < 32; ++c)
+                            m0 |= (fmaf(-2.f, __uint_as_float(v[c]), qw[ch * 32 + c]) <= theta ? 1u : 0u) << c;
+                        const long long sb = c0 + ch * 32;   // self term already counted
                         if (i >= sb && i < sb + 32) m0 &= ~(1u << (int)(i - sb));
-                        if (i >= sb + 32 && i < sb + 64) m1 &= ~(1u << (int)(i - sb - 32));
-                        cnt += __popc(m0) + __popc(m1);
+                        cnt += __popc(m0);
                     }
                     if (hm == 2) {
-                        const float4* t4 = reinterpret_cast<const float4*>(qtw + part * 64);
+                        const float4* t4 = reinterpret_cast<const float4*>(qtw + ch * 32);
                         float mt = INFINITY;
 #pragma unroll
-                        for (int c4 = 0; c4 < 16; ++c4) {
+                        for (int c4 = 0; c4 < 8; ++c4) {
                             const float4 qq = t4[c4];
                             mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 0]), qq.x));
                             mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 1]), qq.y));
@@ -941,21 +937,13 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                         }
                         if (mt + nu_src <= 0.f) {
 #pragma unroll
-                            for (int c = 0; c < 32; ++c) {
-                                t0m |= (fmaf(-2.f, __uint_as_float(v[c]), qtw[part * 64 + c]) + nu_src <= 0.f ? 1u : 0u)
-                                       << c;
-                                t1m |= (fmaf(-2.f, __uint_as_float(v[32 + c]), qtw[part * 64 + 32 + c]) + nu_src <= 0.f
-                                            ? 1u
-                                            : 0u)
-                                       << c;
-                            }
-                            cnt += __popc(t0m) + __popc(t1m);
+                            for (int c = 0; c < 32; ++c)
+                                t0m |= (fmaf(-2.f, __uint_as_float(v[c]), qtw[ch * 32 + c]) + nu_src <= 0.f ? 1u : 0u) << c;
+                            cnt += __popc(t0m);
                         }
                     }
-                    cmw[(2 * part) * 32 + lane] = m0;
-                    cmw[(2 * part + 1) * 32 + lane] = m1;
-                    tcmw[(2 * part) * 32 + lane] = t0m;
-                    tcmw[(2 * part + 1) * 32 + lane] = t1m;
+                    cmw[ch * 32 + lane] = m0;
+                    tcmw[ch * 32 + lane] = t0m;
                 }
                 release(acc);
                 const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
