@@ -108,6 +108,8 @@ struct Bufs {
     float* tc_qt;         // [n_pad] column-direction screen value of every node as a target:
                           // |u_c|^2 - (rho_c^2 + err_c) (+inf: no target, -inf: no bound)
     float* tc_qt1;        // [n_pad] the same over the first-pass coordinates
+    float* tc_tile_rmax;  // [n_pad / 128] largest rho_c^2 + err_c of a chunk's targets (+inf: unbounded)
+    float* tc_tile_rmax1; // [n_pad / 128] the same over the first-pass coordinates
     unsigned long long* tc_xlse;   // [n_pad][kMaxScales] (max, sum) float pairs of the terms a
                                    // node receives as the column of a symmetric block
     float* tc_tile_lmax;  // [n_pad / 128] max live log-weight per chunk of 128 sources

@@ -420,6 +420,23 @@ __device__ __forceinline__ void colprep2_body(const Consts<float>& k, const Bufs
     }
     b.tc_qt[c] = qt;
     b.tc_qt1[c] = qt1;
+    // the chunk's largest bound rho_c^2 + err_c (targets only; -inf value: unbounded)
+    __shared__ float rr[2][4];
+    float r0 = (qt == INFINITY) ? 0.f : (qt == -INFINITY ? INFINITY : b.nu[c] - qt);
+    float r1 = (qt1 == INFINITY) ? 0.f : (qt1 == -INFINITY ? INFINITY : b.tc_q1t[c] - qt1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        r0 = fmaxf(r0, __shfl_xor_sync(0xffffffffu, r0, o));
+        r1 = fmaxf(r1, __shfl_xor_sync(0xffffffffu, r1, o));
+    }
+    if ((threadIdx.x & 31) == 0) { rr[0][threadIdx.x >> 5] = r0; rr[1][threadIdx.x >> 5] = r1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 4; ++w) { r0 = fmaxf(r0, rr[0][w]); r1 = fmaxf(r1, rr[1][w]); }
+        // widened by float rounding of q_c - (q_c - R_c), so the combined test stays conservative
+        b.tc_tile_rmax[chunk] = r0 + 1e-6f * (fabsf(r0) + 1.f);
+        b.tc_tile_rmax1[chunk] = r1 + 1e-6f * (fabsf(r1) + 1.f);
+    }
 }
 
 __global__ void __launch_bounds__(128) k_tc_colprep2(Consts<float> k, Bufs<float> b) { colprep2_body(k, b, blockIdx.x); }
@@ -855,6 +872,13 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 // column direction: per column c the precomputed q_c - (rho_c^2 + err_c) of c
                 // as a target; the row side adds nu_i (+inf for dead rows)
                 const float nu_src = (hm == 2 && src_live) ? nu_s : INFINITY;
+                // one test per lane and 32 columns covers both directions: a pair can be a
+                // candidate only if q_s - 2 G <= max(theta_i, Rmax - nu_i), Rmax the largest
+                // column bound of this warp's chunk
+                const float theta_any =
+                    (hm == 2 && src_live)
+                        ? fmaxf(theta, (first_pass ? b.tc_tile_rmax1 : b.tc_tile_rmax)[cchunk] - nu_src)
+                        : theta;
                 if (!wait_bounded(&qfull[acc], aph, abort_flag, status)) return false;
                 if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) return false;
                 tc_fence_after();
@@ -897,8 +921,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     return true;
                 }
                 // long rows: 32 columns per TMEM load; the smallest q_s - 2 G of a lane's 32
-                // columns (and, for symmetric blocks, the smallest column-direction value)
-                // decides whether candidate masks are needed at all
+                // columns against theta_any decides whether candidate masks are needed at all
                 int cnt = 0;
                 for (int ch = 0; ch < HALF / 32; ++ch) {
                     uint32_t v[32];
@@ -916,31 +939,16 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                         mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 3]), qq.w));
                     }
                     uint32_t m0 = 0, t0m = 0;
-                    if (mn <= theta) {
+                    if (mn <= theta_any) {
 #pragma unroll
-                        for (int c = 0; c < 32; ++c)
-                            m0 |= (fmaf(-2.f, __uint_as_float(v[c]), qw[ch * 32 + c]) <= theta ? 1u : 0u) << c;
+                        for (int c = 0; c < 32; ++c) {
+                            const float g2 = -2.f * __uint_as_float(v[c]);
+                            m0 |= (g2 + qw[ch * 32 + c] <= theta ? 1u : 0u) << c;
+                            if (hm == 2) t0m |= ((g2 + qtw[ch * 32 + c]) + nu_src <= 0.f ? 1u : 0u) << c;
+                        }
                         const long long sb = c0 + ch * 32;   // self term already counted
                         if (i >= sb && i < sb + 32) m0 &= ~(1u << (int)(i - sb));
-                        cnt += __popc(m0);
-                    }
-                    if (hm == 2) {
-                        const float4* t4 = reinterpret_cast<const float4*>(qtw + ch * 32);
-                        float mt = INFINITY;
-#pragma unroll
-                        for (int c4 = 0; c4 < 8; ++c4) {
-                            const float4 qq = t4[c4];
-                            mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 0]), qq.x));
-                            mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 1]), qq.y));
-                            mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 2]), qq.z));
-                            mt = fminf(mt, fmaf(-2.f, __uint_as_float(v[4 * c4 + 3]), qq.w));
-                        }
-                        if (mt + nu_src <= 0.f) {
-#pragma unroll
-                            for (int c = 0; c < 32; ++c)
-                                t0m |= (fmaf(-2.f, __uint_as_float(v[c]), qtw[ch * 32 + c]) + nu_src <= 0.f ? 1u : 0u) << c;
-                            cnt += __popc(t0m);
-                        }
+                        cnt += __popc(m0) + __popc(t0m);
                     }
                     cmw[ch * 32 + lane] = m0;
                     tcmw[ch * 32 + lane] = t0m;
