@@ -31,6 +31,8 @@ CASES = {
     "tc_lowr_bf16": ("cubic", 2, 1024, 4.0, 2, "bf16", 1),
     "tc_linear_bf16": ("linear", 8, 777, 1.0, 1, "bf16", 3),
     "tc_N4_bf16": ("cubic", 33, 1500, 0.5, 4, "bf16", 10),
+    # the largest dimension the library takes (YY_MAX_DIM), symmetric screen, ragged n
+    "tc_rmax_bf16": ("cubic", 1024, 1000, 0.3, 2, "bf16", 11),
 }
 TOL = {"f64": 1e-10, "f32": 1e-5, "bf16": 1e-5}
 
