@@ -371,33 +371,34 @@ def run_reference(args):
 def run_batch(args):
     """256 ragged trajectories (r in 10..200, n log-uniform in 2048..32768, half cubic, half
     linear-Gaussian) advanced as one batch; value = trajectory-steps per second."""
-    import tempfile
-
     import torch
     from paper_2509_16896_gb300 import binding
     rank, ws_, local, dist = _dist()
     device = f"cuda:{local}"
     torch.cuda.set_device(device)
     W, K = args.warmup, args.steps
-    members = batched_workloads(256, seed=4 + 1000 * rank, steps=W + K)
+    # untimed steps before the timed ones: at least 8, so that the autotuner routes on
+    # posteriors that have spread out rather than on the prior
+    S = max(W, 8)
+    members = batched_workloads(256, seed=4 + 1000 * rank, steps=S + K)
     prec = args.precision or "bf16"
     cfgs = [binding.config_from_workload(m, precision=prec) for m in members]
     bt = binding.Batch(cfgs, device=device)
     trs = []
     for b, m in enumerate(members):
         bt.filters[b].init_nodes(sobol_poly_params(m.r, m.seed), sobol_scramble_params(m.r, m.seed), np.zeros(m.r))
-        trs.append(simulate(m.model, m.r, W + K, m.dt, seed=m.seed, model_a=m.model_a))
+        trs.append(simulate(m.model, m.r, S + K, m.dt, seed=m.seed, model_a=m.model_a))
     dy_all = torch.tensor(np.concatenate([t.dy for t in trs], axis=1), dtype=torch.float64, device=device)
     hist = torch.zeros((K, bt.H), dtype=torch.float64, device=device)
-    cache = os.path.join(tempfile.gettempdir(), "yy_batch_autotune.txt")
+    with torch.cuda.stream(bt.stream):
+        bt.run_steps(dy_all[:S])
+    torch.cuda.synchronize()
     t_tune = time.perf_counter()
-    bn, grid = bt.autotune(cache, reps=2)
+    bn, grid = bt.autotune(None, reps=2)
     t_tune = time.perf_counter() - t_tune
     routing = bt.routing()
     with torch.cuda.stream(bt.stream):
-        if W:
-            bt.run_steps(dy_all[:W])
-        bt.graph_capture(dy_all[W:W + K], hist)
+        bt.graph_capture(dy_all[S:S + K], hist)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = bt.launches()
@@ -421,14 +422,14 @@ def run_batch(args):
     rm_c, rm_l = [], []
     for b, (m, t) in enumerate(zip(members, trs)):
         est = h[:, bt.hist_off[b]:bt.hist_off[b] + m.r]
-        rm = _rmse(est, t.x[W:W + K])
+        rm = _rmse(est, t.x[S:S + K])
         (rm_c if m.model == "cubic" else rm_l).append(rm)
     flops = float(sum(2.0 * m.n * m.n * m.r for m in members))
     peaks, src = _peaks()
     peak = peaks.get("bf16_tflops", 1900.0)
     achieved = flops / (pred_ms / 1e3) / 1e12
     out = {"metric": "trajectory-steps/s, 256 ragged filters in one batch", "value": round(256 * K / (ms / 1e3), 2),
-           "unit": "trajectory-steps/s", "n_gpus": 1, "steps": K, "warmup": W, "ms_per_step": round(ms / K, 4),
+           "unit": "trajectory-steps/s", "n_gpus": 1, "steps": K, "warmup": S, "ms_per_step": round(ms / K, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
            "data": "synthetic (seeded Euler-Maruyama cubic sensor / linear-Gaussian, scrambled Sobol nodes)",
            "config": {"workload": "batched_256", "trajectories": 256, "r": "10..200", "n": "2048..32768 log-uniform",

@@ -114,7 +114,8 @@ typedef struct {
                                 * of the prediction, in units of 64 (see yy_predict); 0 =
                                 * chosen on the device from the previous predictions
                                 * (default), k >= 1 = fixed (values >= ceil(r/64) give one
-                                * full-coordinate pass), < 0 invalid. Results do not depend
+                                * full-coordinate pass), < 0 invalid. Members of a batch
+                                * default to one full-coordinate pass. Results do not depend
                                 * on it beyond float32 rounding. */
 } yy_config;
 

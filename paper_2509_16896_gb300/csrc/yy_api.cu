@@ -132,6 +132,7 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.next_half = cv.take<double>(r_pad * sizeof(double));
     b.dy_last = cv.take<double>(r_pad * sizeof(double));
     b.part = cv.take<double>(part_bytes(r_pad));
+    b.part_list = cv.take<int>((size_t)kNumPartBlocks * sizeof(int));
     b.stats = cv.take<DevStats>(sizeof(DevStats));
     if (c->precision == YY_PREC_BF16) {
         b.nu_chunk = cv.take<float>((size_t)n_pad * (r_pad / kColAlign) * sizeof(float));

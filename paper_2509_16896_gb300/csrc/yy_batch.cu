@@ -161,6 +161,9 @@ yy_status upload(yy_batch* bt) {
         tr[b].restart_init = f->cfg.restart_init;
         tr[b].path = bt->path[b];
         tr[b].k.tc_sym = 0;   // batch work lists cover every block
+        // one full-coordinate pass unless configured: a member's probe of a short first pass
+        // would hold up the whole batch's launch
+        if (f->cfg.screen_prefix <= 0) tr[b].k.tc_prefix = f->r_pad / 64;
         tr[b].b.tc_splits = splits[b];
         if (bt->precision == YY_PREC_BF16) {
             if (!make_tc_map(&maps[kMapBytes * 2 * b], f->bf.ubf, f->n_pad, f->r_pad, 128) ||

@@ -40,6 +40,7 @@ struct DevStats {
     int last_restarted;  // 1 if the last yy_restart call re-centred the box
     int scale_changed;   // 1 while a restart re-maps the nodes to new half-widths
     double c_ref;        // offset of the predicted log-weights (moves with the box volume)
+    int part_count;      // entries of part_list
     // BF16 screen: coordinate chunks (of 64) of the first screening pass and its controller
     int tc_nk1;          // 0 = not chosen yet
     int tc_streak;       // consecutive acceptable predictions at the current length
@@ -99,6 +100,7 @@ struct Bufs {
     double* next_half;    // [r_pad]
     double* dy_last;      // [r_pad] observation increment of the last update
     double* part;         // reduction partials
+    int* part_list;       // [kNumPartBlocks] moment partials with weight, in block order
     DevStats* stats;
     // BF16 path scratch
     float* nu_chunk;      // [n_pad][r_pad / 64] |u_i|^2 per chunk of 64 coordinates (BF16 only)
@@ -149,6 +151,7 @@ cudaError_t launch_sobol_points(const uint32_t* dirs, int r, int r_pad, long lon
                                 long long count, float* u, uint32_t* bits, const double* halfwidth,
                                 cudaStream_t s);
 
+int prep_grid(long long n_pad);
 template <typename T>
 cudaError_t launch_prep(const Consts<T>& k, const Bufs<T>& b, bool init_weights, bool first,
                         double prior_mean, double prior_var, cudaStream_t s);

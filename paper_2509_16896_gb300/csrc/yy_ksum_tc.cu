@@ -260,10 +260,12 @@ __device__ __forceinline__ int prefix_chunks(const Consts<float>& k, const DevSt
     return v < 1 ? 1 : (v > nk ? nk : v);
 }
 
-// Drift component d at x = c + u with the preparation pass's arithmetic (per-dimension
-// constants dimc), so that it equals the value that pass would store in f.
-__device__ __forceinline__ float drift_at(const Consts<float>& k, const Bufs<float>& b, float u, int d) {
+// Drift component d of node row `row` at x = c + u: the stored f where the preparation pass
+// writes it, else recomputed with that pass's arithmetic (per-dimension constants dimc),
+// which gives the value it would have stored.
+__device__ __forceinline__ float drift_at(const Consts<float>& k, const Bufs<float>& b, long long row, float u, int d) {
     const int rp = k.r_pad;
+    if (b.store_f) return b.f[(size_t)row * rp + d];
     if (k.model == YY_MODEL_CUBIC) {
         float fv, sn;
         cubic_drift(u, b.dimc[d], b.dimc[rp + d], b.dimc[3 * rp + d], b.dimc[4 * rp + d], &fv, &sn);
@@ -780,7 +782,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     for (int d = lane; d < k.r; d += 32) {
                         const float dl = ut[d] - us[d];
                         s1 = fmaf(dl, dl, s1);
-                        s2 = fmaf(dl, drift_at(k, b, ut[d], d), s2);
+                        s2 = fmaf(dl, drift_at(k, b, tgt, ut[d], d), s2);
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -817,7 +819,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     for (int d = lane; d < k.r; d += 32) {
                         const float dl = ut[d] - us[d];
                         s1 = fmaf(dl, dl, s1);
-                        s2 = fmaf(dl, drift_at(k, b, ut[d], d), s2);
+                        s2 = fmaf(dl, drift_at(k, b, tgt, ut[d], d), s2);
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
@@ -910,7 +912,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                             for (int d = 0; d < k.r; ++d) {
                                 const float dl = ut[d] - us[d];
                                 s1 = fmaf(dl, dl, s1);
-                                s2 = fmaf(dl, drift_at(k, b, ut[d], d), s2);
+                                s2 = fmaf(dl, drift_at(k, b, i, ut[d], d), s2);
                             }
                             add_score(s1, s2, src);
                             ++ncand;

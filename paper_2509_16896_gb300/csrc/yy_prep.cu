@@ -68,7 +68,8 @@ __device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>
 template <typename T, int mode, bool first, bool narrow>
 __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, double prior_mean,
                                           double prior_var, int bid, int nblk, const T* s_hi, const T* s_lo,
-                                          const T* s_iv, const T* s_cc, const T* s_sc) {
+                                          const T* s_iv, const T* s_cc, const T* s_sc, double& lse_m,
+                                          double& lse_s) {
     const int rp = k.r_pad;
     const int lane = threadIdx.x & 31;
     const long long warp = (bid * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -160,14 +161,25 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
                 b.nu[i] = nu;
                 b.mask[i] = (uint8_t)on_face;
             }
-            if (mode != kPrepOnly) b.logw[i] = b.mask[i] ? T(-INFINITY) : lw;
+            if (mode != kPrepOnly) {
+                const T out = b.mask[i] ? T(-INFINITY) : lw;
+                b.logw[i] = out;
+                // running (max, sum) of the written log-weights (lane 0 of every warp)
+                const double l = (double)out;
+                if (l != -INFINITY) {
+                    if (l > lse_m) { lse_s = lse_s * (double)expf((float)(lse_m - l)) + 1.0; lse_m = l; }
+                    else lse_s += (double)expf((float)(l - lse_m));
+                }
+            }
         }
     }
 }
 
+// lse_out: also write the block's (max, sum) log-sum-exp partial of the new log-weights to
+// b.part[2 bid], b.part[2 bid + 1] (restart and init passes).
 template <typename T>
 __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, int mode, int first,
-                                          double prior_mean, double prior_var, int bid, int nblk) {
+                                          double prior_mean, double prior_var, int bid, int nblk, bool lse_out) {
     if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
     // a restart that re-mapped the nodes to new half-widths also redoes the node-only
     // quantities (|u|^2, mask against the new faces, bf16 copy)
@@ -185,8 +197,9 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
     int my_narrow = 1;
     for (int d = threadIdx.x; d < k.r; d += blockDim.x) my_narrow &= (s_cc[d] == s_cc[d]) ? 1 : 0;
     const int narrow = __syncthreads_and(my_narrow);
+    double lse_m = -INFINITY, lse_s = 0.0;
 #define YY_PREP_ROWS(M, F, W) \
-    prep_rows<T, M, F, W>(k, b, prior_mean, prior_var, bid, nblk, s_hi, s_lo, s_iv, s_cc, s_sc)
+    prep_rows<T, M, F, W>(k, b, prior_mean, prior_var, bid, nblk, s_hi, s_lo, s_iv, s_cc, s_sc, lse_m, lse_s)
     if (mode == kPrepRestart) {
         if (first) YY_PREP_ROWS(kPrepRestart, true, false);
         else if (narrow) YY_PREP_ROWS(kPrepRestart, false, true);
@@ -199,6 +212,24 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
         else YY_PREP_ROWS(kPrepOnly, false, false);
     }
 #undef YY_PREP_ROWS
+    if (lse_out && mode != kPrepOnly) {
+        __shared__ double sm_m[8], sm_s[8];
+        const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+        if (lane == 0) { sm_m[wib] = lse_m; sm_s[wib] = lse_s; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double M = -INFINITY, S = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                const double m2 = sm_m[w], s2 = sm_s[w];
+                if (m2 == -INFINITY) continue;
+                if (M == -INFINITY) { M = m2; S = s2; }
+                else if (m2 > M) { S = S * exp(M - m2) + s2; M = m2; }
+                else S += s2 * exp(m2 - M);
+            }
+            b.part[2 * bid] = M;
+            b.part[2 * bid + 1] = S;
+        }
+    }
 }
 
 template <typename T>
@@ -206,7 +237,7 @@ __global__ void k_prep_dims(Consts<T> k, Bufs<T> b, int mode, int init_kind) { p
 template <typename T>
 __global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, int first, double prior_mean,
                                               double prior_var) {
-    prep_body<T>(k, b, mode, first, prior_mean, prior_var, blockIdx.x, gridDim.x);
+    prep_body<T>(k, b, mode, first, prior_mean, prior_var, blockIdx.x, gridDim.x, true);
 }
 // batched restart preparation: trajectory = blockIdx.y
 template <typename T>
@@ -217,7 +248,7 @@ __global__ void kb_prep_dims(const Traj<T>* __restrict__ tr) {
 template <typename T>
 __global__ void __launch_bounds__(256) kb_prep(const Traj<T>* __restrict__ tr) {
     const Traj<T>& t = tr[blockIdx.y];
-    prep_body<T>(t.k, t.b, kPrepRestart, 0, 0.0, 1.0, blockIdx.x, gridDim.x);
+    prep_body<T>(t.k, t.b, kPrepRestart, 0, 0.0, 1.0, blockIdx.x, gridDim.x, false);
 }
 
 template <typename T>
@@ -231,14 +262,19 @@ cudaError_t launch_prep_restart_batch(const Traj<T>* d_traj, int B, long long n_
 template cudaError_t launch_prep_restart_batch<float>(const Traj<float>*, int, long long, cudaStream_t);
 template cudaError_t launch_prep_restart_batch<double>(const Traj<double>*, int, long long, cudaStream_t);
 
+// Blocks of the single-filter preparation pass (one warp per row, at most 8 per SM); also
+// the number of log-sum-exp partials it writes.
+int prep_grid(long long n_pad) {
+    long long blocks = (n_pad * 32 + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    return (int)blocks;
+}
+
 template <typename T>
 cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, bool first,
                              double prior_mean, double prior_var, int init_kind, cudaStream_t s) {
     k_prep_dims<T><<<1, 256, 0, s>>>(k, b, mode, init_kind);
-    long long warps = k.n_pad;
-    long long blocks = (warps * 32 + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_prep<T><<<(unsigned)blocks, 256, 0, s>>>(k, b, mode, first ? 1 : 0, prior_mean, prior_var);
+    k_prep<T><<<(unsigned)prep_grid(k.n_pad), 256, 0, s>>>(k, b, mode, first ? 1 : 0, prior_mean, prior_var);
     return cudaGetLastError();
 }
 

@@ -227,12 +227,20 @@ __device__ __forceinline__ void subtract_body(const Consts<T>& k, const Bufs<T>&
 
 constexpr int kMomDims = YY_MAX_DIM / 256;   // coordinates per thread in the moments pass
 
-// Normalises ell' and accumulates per-block weighted moments of u.
+// Normalises ell' and accumulates per-block weighted moments of u.  The block's rows are
+// taken 256 at a time (one per thread): ell_hat = ell' - Lambda_rel and w = e^ell_hat, the
+// round's weight sum and sum of squares (float64), and the rows with w > 0 compacted in
+// row order (ballot prefix sums, so the result does not depend on scheduling).  Only those
+// rows are read: per coordinate the round's weighted mean, then its centred second moment,
+// merged into the block's running values with Chan's rule (float64).  With posteriors
+// concentrated on few nodes most rounds read no coordinates at all.
 template <typename T>
 __device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& b, int bid, int nblk) {
-    __shared__ T w_s[32];
-    __shared__ double wc_s[2];
-    const int tid = threadIdx.x;
+    __shared__ int s_rows[256];
+    __shared__ T s_w[256];
+    __shared__ int s_wcnt[8];
+    __shared__ double s_red[2][8];
+    const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
     const long long rows_per = (k.n + nblk - 1) / nblk;
     const long long i0 = bid * rows_per;
     const long long i1 = min(k.n, i0 + rows_per);
@@ -241,34 +249,45 @@ __device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& 
     double mu[kMomDims], M2[kMomDims];
 #pragma unroll
     for (int q = 0; q < kMomDims; ++q) { mu[q] = 0.0; M2[q] = 0.0; }
-    for (long long c0 = i0; c0 < i1; c0 += 32) {
-        const int cn = (int)min((long long)32, i1 - c0);
-        if (tid < 32) {
-            T w = T(0);
-            if (tid < cn) {
-                const T lh = b.logw[c0 + tid] - lam;
-                b.logw[c0 + tid] = lh;
-                w = exp_t<T>(lh);
-            }
-            w_s[tid] = w;
-            const double wsum = warp_sum_u((double)w);
-            const double wsq = warp_sum_u((double)w * (double)w);
-            if (tid == 0) { wc_s[0] = wsum; wc_s[1] = wsq; }
+    for (long long c0 = i0; c0 < i1; c0 += 256) {
+        const long long i = c0 + tid;
+        T w = T(0);
+        if (i < i1) {
+            const T lh = b.logw[i] - lam;
+            b.logw[i] = lh;
+            w = exp_t<T>(lh);
+        }
+        // round sums and the compacted list of rows with weight
+        const double wsum = warp_sum_u((double)w), wsq = warp_sum_u((double)w * (double)w);
+        const uint32_t bal = __ballot_sync(0xffffffffu, w > T(0));
+        if (lane == 0) { s_red[0][wib] = wsum; s_red[1][wib] = wsq; s_wcnt[wib] = __popc(bal); }
+        __syncthreads();
+        int off = 0, cnt = 0;
+        double Wc = 0.0, Qc = 0.0;
+        for (int g = 0; g < 8; ++g) {
+            if (g < wib) off += s_wcnt[g];
+            cnt += s_wcnt[g];
+            Wc += s_red[0][g];
+            Qc += s_red[1][g];
+        }
+        if (w > T(0)) {
+            const int slot = off + __popc(bal & ((1u << lane) - 1u));
+            s_rows[slot] = (int)(i - c0);
+            s_w[slot] = w;
         }
         __syncthreads();
-        const double Wc = wc_s[0];
-        if (Wc > 0.0) {
+        if (cnt > 0 && Wc > 0.0) {
 #pragma unroll
             for (int q = 0; q < kMomDims; ++q) {
                 const int d = tid + 256 * q;
                 if (d < k.r) {
                     T S = T(0);
-                    for (int l = 0; l < cn; ++l) S += w_s[l] * (T)b.u[(size_t)(c0 + l) * k.r_pad + d];
+                    for (int l = 0; l < cnt; ++l) S += s_w[l] * (T)b.u[(size_t)(c0 + s_rows[l]) * k.r_pad + d];
                     const T muc = S / (T)Wc;
                     T m2 = T(0);
-                    for (int l = 0; l < cn; ++l) {
-                        const T dv = (T)b.u[(size_t)(c0 + l) * k.r_pad + d] - muc;
-                        m2 += w_s[l] * dv * dv;
+                    for (int l = 0; l < cnt; ++l) {
+                        const T dv = (T)b.u[(size_t)(c0 + s_rows[l]) * k.r_pad + d] - muc;
+                        m2 += s_w[l] * dv * dv;
                     }
                     const double delta = (double)muc - mu[q];
                     const double Wn = W + Wc;
@@ -277,8 +296,8 @@ __device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& 
                 }
             }
             W += Wc;
-            Q += wc_s[1];
         }
+        Q += Qc;
         __syncthreads();
     }
     double* p = b.part + (size_t)bid * (4 + 2 * k.r_pad);
@@ -297,13 +316,29 @@ template <typename T>
 __device__ __forceinline__ void finalize_scalars_body(const Consts<T>& k, const Bufs<T>& b, int nb,
                                                       int restart_interval, double ess_frac) {
     __shared__ double red_w[32], red_q[32];
+    __shared__ int s_cnt[32];
     DevStats* st = b.stats;
     const int t = threadIdx.x;
     double w = 0.0, q = 0.0;
-    for (int j = t; j < nb; j += blockDim.x) {
-        const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
-        if (p[0] > 0.0) w += p[0];
+    // partials with weight, listed in block order for the per-coordinate merge (nb <= blockDim.x)
+    bool has = false;
+    if (t < nb) {
+        const double* p = b.part + (size_t)t * (4 + 2 * k.r_pad);
+        has = p[0] > 0.0;
+        if (has) w += p[0];
         q += p[1];
+    }
+    const uint32_t bal = __ballot_sync(0xffffffffu, has);
+    if ((t & 31) == 0) s_cnt[t >> 5] = __popc(bal);
+    __syncthreads();
+    {
+        int off = 0, tot = 0;
+        for (int g = 0; g < (int)(blockDim.x >> 5); ++g) {
+            if (g < (t >> 5)) off += s_cnt[g];
+            tot += s_cnt[g];
+        }
+        if (has) b.part_list[off + __popc(bal & ((1u << (t & 31)) - 1u))] = t;
+        if (t == 0) st->part_count = tot;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -336,14 +371,16 @@ __device__ __forceinline__ void finalize_scalars_body(const Consts<T>& k, const 
 template <typename T>
 __device__ __forceinline__ void finalize_dims_body(const Consts<T>& k, const Bufs<T>& b, int nb, int bid) {
     __shared__ double g_w[8][32], g_mu[8][32], g_m2[8][32];
+    (void)nb;
     const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
     const int d = bid * 32 + lane;
-    const int per = (nb + 7) / 8;
-    const int j0 = g * per, j1 = min(nb, j0 + per);
+    const int np = b.stats->part_count;   // partials with weight (finalize_scalars' list)
+    const int per = (np + 7) / 8;
+    const int j0 = g * per, j1 = min(np, j0 + per);
     double W = 0.0, mu = 0.0, M2 = 0.0;
     if (d < k.r) {
-        for (int j = j0; j < j1; ++j) {
-            const double* p = b.part + (size_t)j * (4 + 2 * k.r_pad);
+        for (int jj = j0; jj < j1; ++jj) {
+            const double* p = b.part + (size_t)b.part_list[jj] * (4 + 2 * k.r_pad);
             const double wc = p[0];
             if (!(wc > 0.0)) continue;
             const double Wn = W + wc;
@@ -645,11 +682,11 @@ cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int i
     if (e != cudaSuccess) return e;
     e = launch_prep_mode<T>(k, b, 2 /*restart*/, false, 0.0, 1.0, init_kind, s);
     if (e != cudaSuccess) return e;
-    k_lse_partials<T><<<nb, 256, 0, s>>>(k, b, 1);
-    k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 1);
+    // the preparation pass wrote the log-sum-exp partials of the new weights
+    k_lse_merge<<<1, 256, 0, s>>>(b.part, prep_grid(k.n_pad), b.stats, 1);
     k_subtract<T><<<nb, 256, 0, s>>>(k, b, 1);
     k_restart_commit<T><<<1, 256, 0, s>>>(k, b);
-    if (launches) *launches += 8 + l + (net ? 1 : 0);
+    if (launches) *launches += 7 + l + (net ? 1 : 0);
     return cudaGetLastError();
 }
 
