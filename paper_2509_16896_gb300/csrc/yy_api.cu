@@ -619,7 +619,7 @@ yy_status yy_get_screen(yy_filter* f, int32_t* h_last_prefix, int32_t* h_next_pr
     if (e != cudaSuccess) return YY_ERR_CUDA;
     const int nk = f->r_pad / kColAlign;
     int v = f->cfg.screen_prefix > 0 ? f->cfg.screen_prefix : hs.tc_nk1;
-    if (v <= 0) v = (nk + 3) / 4;
+    if (v <= 0) v = (nk + 1) / 2;
     if (h_last_prefix) *h_last_prefix = hs.tc_last_nk1;
     if (h_next_prefix) *h_next_prefix = std::max(1, std::min(v, nk));
     if (h_tiles) *h_tiles = (int64_t)hs.tc_last_blk;

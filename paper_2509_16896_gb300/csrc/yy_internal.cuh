@@ -43,7 +43,7 @@ struct DevStats {
     int part_count;      // entries of part_list
     // BF16 screen: coordinate chunks (of 64) of the first screening pass and its controller
     int tc_nk1;          // 0 = not chosen yet
-    int tc_streak;       // consecutive acceptable predictions at the current length
+    int tc_streak;       // consecutive clean predictions at the current length
     int tc_from;         // first-pass length of the prediction before the last one
     int tc_hold[YY_MAX_DIM / 64 + 1];     // predictions a length is still held off
     unsigned long long tc_blk;   // tiles screened by the last prediction

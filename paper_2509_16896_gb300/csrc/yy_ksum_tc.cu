@@ -252,11 +252,12 @@ __device__ __forceinline__ float screen_theta(const Consts<float>& k, bool live,
 }  // namespace
 
 // First-pass coordinate chunks (of 64) of one filter's screen: fixed by the configuration,
-// else the controller's last choice (tc_adapt), else a quarter of the coordinates.
+// else the controller's last choice (tc_adapt), else half of the coordinates (the
+// controller finds the shortest clean length from above).
 __device__ __forceinline__ int prefix_chunks(const Consts<float>& k, const DevStats* st) {
     const int nk = k.r_pad / tc::BK;
     int v = k.tc_prefix > 0 ? k.tc_prefix : st->tc_nk1;
-    if (v <= 0) v = (nk + 3) / 4;
+    if (v <= 0) v = (nk + 1) / 2;
     return v < 1 ? 1 : (v > nk ? nk : v);
 }
 
@@ -333,11 +334,12 @@ __global__ void __launch_bounds__(128) kb_tc_colprep(const Traj<float>* __restri
 // last CTA to finish).  The work beyond the first pass, in chunks per tile, is
 //     extra = (rescreened tiles x all chunks + exact pair evaluations x r / 4096) / tiles
 // (an exact pair costs about r / 4096 of the tensor time of one chunk of one tile).  A
-// length is acceptable when extra <= 1/50.  After an unacceptable prediction the length
-// grows at once (by 2 when extra > 4) and the one just used is held off for 1024
-// predictions; after four acceptable predictions in a row at one length, one chunk shorter
-// is tried unless it is held off.  Candidates grow steeply as the first pass shortens, so
-// the shortest acceptable length is found from above and probed again only rarely.
+// length is acceptable when extra <= 1/50 and clean when extra = 0.  After an unacceptable
+// prediction the length grows at once (by 2 when extra > 4) and the one just used is held
+// off for 1024 predictions; after four clean predictions in a row at one length, one chunk
+// shorter is tried unless it is held off (an acceptable but not clean length is kept, not
+// shortened: candidates grow steeply as the first pass shortens, and a shorter pass saves
+// little once the screening epilogue, not the Gram product, sets the pace).
 __device__ void tc_adapt(const Consts<float>& k, DevStats* st) {
     const unsigned long long blk = atomicExch(&st->tc_blk, 0ull);
     const unsigned long long esc = atomicExch(&st->tc_esc, 0ull);
@@ -362,7 +364,8 @@ __device__ void tc_adapt(const Consts<float>& k, DevStats* st) {
             next = min(nk, nk1 + (extra > 4.0 ? 2 : 1));
         }
     } else {
-        st->tc_streak = (from == nk1) ? st->tc_streak + 1 : 1;
+        const bool clean = esc == 0 && cand == 0;
+        st->tc_streak = clean ? ((from == nk1) ? st->tc_streak + 1 : 1) : 0;
         if (st->tc_streak >= kSettle && nk1 > 1 && st->tc_hold[nk1 - 1] == 0) {
             next = nk1 - 1;
             st->tc_streak = 0;
