@@ -38,7 +38,7 @@ DEFAULT_WORKLOAD = "cubic_r1000_n65536"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the prediction
 # kernel, from one ncu capture of the workload (profiles/k_ksum_tc_cubic_r1000_n65536.md).
 # An entry is removed whenever the kernel changes after its capture.
-NCU_TRAFFIC: dict = {}
+NCU_TRAFFIC = {("cubic_r1000_n65536", "bf16"): 56.677120e6 + 2.271232e6}
 METRIC = "filter steps/s & kernel pair-evals/s at r=1000: mixed vs FP32, same RMSE"
 
 
