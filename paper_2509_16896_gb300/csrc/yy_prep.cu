@@ -43,7 +43,7 @@ __device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>
     const double* half = (mode == kPrepRestart) ? b.next_half : b.halfwidth;
     const int rp = k.r_pad;
     for (int d = threadIdx.x; d < rp; d += blockDim.x) {
-        T hi = T(0), lo = T(0), iv = T(0), cc = T(1), sc = T(0);
+        T hi = T(0), lo = T(0), iv = T(0), cc = T(0), sc = T(0);   // padded: u = 0 gives f = 0
         if (d < k.r) {
             const double c = cen[d];
             hi = (T)c;
@@ -101,8 +101,35 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
         for (int q = 0; q < kRowQ; ++q) uu[q] = (q < nq) ? ui2[lane + 32 * q] : make_float2(0.f, 0.f);
         T div = T(0), nf = T(0), nu = T(0), lw = T(0);
         int on_face = 0;
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value && narrow && !first) {
+            // the common restart and re-preparation case: cubic drift by the polynomials,
+            // padded coordinates inert by construction (u = 0, cos c = sin c = 0, no Gaussian
+            // term), so no per-element tests; per-dimension constants as float2 pairs
+            if (cubic) {
+#pragma unroll
+                for (int q = 0; q < kRowQ; ++q) {
+                    if (q >= nq) break;   // uniform over the warp
+                    const int d = 64 * q + 2 * lane;
+                    const float2 cc = *reinterpret_cast<const float2*>(s_cc + d);
+                    const float2 sc = *reinterpret_cast<const float2*>(s_sc + d);
+                    float f0, f1, sn0, sn1;
+                    cubic_drift_narrow(uu[q].x, cc.x, sc.x, &f0, &sn0);
+                    cubic_drift_narrow(uu[q].y, cc.y, sc.y, &f1, &sn1);
+                    div -= sn0 + sn1;
+                    nf = fmaf(f0, f0, fmaf(f1, f1, nf));
+                    if constexpr (mode == kPrepRestart) {
+                        const float2 iv = *reinterpret_cast<const float2*>(s_iv + d);
+                        lw = fmaf(-uu[q].x * uu[q].x, iv.x, fmaf(-uu[q].y * uu[q].y, iv.y, lw));
+                    }
+                    if (b.store_f) *reinterpret_cast<float2*>(fi + d) = make_float2(f0, f1);
+                }
+                done = true;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < kRowQ; ++q) {
+            if (done) break;
             if (q >= nq) break;   // uniform over the warp
             const int dq = 64 * q + 2 * lane;
             float cq = 0.f;       // |u|^2 of this lane's two coordinates
@@ -235,7 +262,7 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
 template <typename T>
 __global__ void k_prep_dims(Consts<T> k, Bufs<T> b, int mode, int init_kind) { prep_dims_body<T>(k, b, mode, init_kind); }
 template <typename T>
-__global__ void __launch_bounds__(256) k_prep(Consts<T> k, Bufs<T> b, int mode, int first, double prior_mean,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_prep(Consts<T> k, Bufs<T> b, int mode, int first, double prior_mean,
                                               double prior_var) {
     prep_body<T>(k, b, mode, first, prior_mean, prior_var, blockIdx.x, gridDim.x, true);
 }

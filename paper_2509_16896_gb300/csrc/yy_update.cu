@@ -366,48 +366,49 @@ __device__ __forceinline__ void finalize_scalars_body(const Consts<T>& k, const 
 }
 
 // Per coordinate: mean and variance merged from the block partials with Chan's rule;
-// x_hat = c + mean.  32 coordinates per block; the 8 warps take 8 contiguous groups of
-// partials and their group results are merged at the end.
+// x_hat = c + mean.  8 coordinates per block and 32 groups of partials (group g takes the
+// listed partials g, g + 32, ...); the 32 group results are merged pairwise in a tree.
+__device__ __forceinline__ void chan_merge(double& W, double& mu, double& M2, double W2, double mu2, double M22) {
+    if (!(W2 > 0.0)) return;
+    if (!(W > 0.0)) { W = W2; mu = mu2; M2 = M22; return; }
+    const double Wn = W + W2;
+    const double delta = mu2 - mu;
+    mu = fma(delta, W2 / Wn, mu);
+    M2 += M22 + delta * delta * (W * W2 / Wn);
+    W = Wn;
+}
+
 template <typename T>
 __device__ __forceinline__ void finalize_dims_body(const Consts<T>& k, const Bufs<T>& b, int nb, int bid) {
-    __shared__ double g_w[8][32], g_mu[8][32], g_m2[8][32];
+    __shared__ double g_w[32][8], g_mu[32][8], g_m2[32][8];
     (void)nb;
-    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-    const int d = bid * 32 + lane;
+    const int c8 = threadIdx.x & 7, g = threadIdx.x >> 3;
+    const int d = bid * 8 + c8;
     const int np = b.stats->part_count;   // partials with weight (finalize_scalars' list)
-    const int per = (np + 7) / 8;
-    const int j0 = g * per, j1 = min(np, j0 + per);
     double W = 0.0, mu = 0.0, M2 = 0.0;
-    if (d < k.r) {
-        for (int jj = j0; jj < j1; ++jj) {
+    if (d < k.r)
+        for (int jj = g; jj < np; jj += 32) {
             const double* p = b.part + (size_t)b.part_list[jj] * (4 + 2 * k.r_pad);
-            const double wc = p[0];
-            if (!(wc > 0.0)) continue;
-            const double Wn = W + wc;
-            const double a = wc / Wn, bcoef = W * wc / Wn;
-            const double delta = p[4 + d] - mu;
-            mu = fma(delta, a, mu);
-            M2 += p[4 + k.r_pad + d] + delta * delta * bcoef;
-            W = Wn;
+            chan_merge(W, mu, M2, p[0], p[4 + d], p[4 + k.r_pad + d]);
         }
-    }
-    g_w[g][lane] = W;
-    g_mu[g][lane] = mu;
-    g_m2[g][lane] = M2;
+    g_w[g][c8] = W;
+    g_mu[g][c8] = mu;
+    g_m2[g][c8] = M2;
     __syncthreads();
-    if (g == 0 && d < k.r) {
-        double Wt = 0.0, mt = 0.0, Mt = 0.0;
-        for (int q = 0; q < 8; ++q) {
-            const double wc = g_w[q][lane];
-            if (!(wc > 0.0)) continue;
-            const double Wn = Wt + wc;
-            const double delta = g_mu[q][lane] - mt;
-            mt += delta * (wc / Wn);
-            Mt += g_m2[q][lane] + delta * delta * (Wt * wc / Wn);
-            Wt = Wn;
+    for (int s = 16; s > 0; s >>= 1) {
+        if (g < s) {
+            double Wa = g_w[g][c8], ma = g_mu[g][c8], Ma = g_m2[g][c8];
+            chan_merge(Wa, ma, Ma, g_w[g + s][c8], g_mu[g + s][c8], g_m2[g + s][c8]);
+            g_w[g][c8] = Wa;
+            g_mu[g][c8] = ma;
+            g_m2[g][c8] = Ma;
         }
-        const double mean = b.centre[d] + mt;
-        const double var = (Wt > 0.0) ? Mt / Wt : 0.0;
+        __syncthreads();
+    }
+    if (g == 0 && d < k.r) {
+        const double Wt = g_w[0][c8];
+        const double mean = b.centre[d] + g_mu[0][c8];
+        const double var = (Wt > 0.0) ? g_m2[0][c8] / Wt : 0.0;
         b.mean[d] = mean;
         b.var[d] = var;
         if (!isfinite(mean) || !isfinite(var)) atomicOr(&b.stats->status, kStatusNonFinite);
@@ -632,7 +633,7 @@ cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy
     k_lse_merge<<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0);
     k_moments<T><<<nb, 256, 0, s>>>(k, b);
     k_finalize_scalars<T><<<1, 512, 0, s>>>(k, b, nb, restart_interval, ess_frac);
-    k_finalize_dims<T><<<(k.r + 31) / 32, 256, 0, s>>>(k, b, nb);
+    k_finalize_dims<T><<<(k.r + 7) / 8, 256, 0, s>>>(k, b, nb);
     if (launches) *launches += 6;
     return cudaGetLastError();
 }
@@ -699,7 +700,7 @@ cudaError_t launch_update_batch(const Traj<T>* d_traj, int B, int r_max, const d
     kb_lse_merge<T><<<one, 256, 0, s>>>(d_traj, nbu, 0);
     kb_moments<T><<<many, 256, 0, s>>>(d_traj);
     kb_finalize_scalars<T><<<one, 512, 0, s>>>(d_traj, nbu);
-    kb_finalize_dims<T><<<dim3((r_max + 31) / 32, B), 256, 0, s>>>(d_traj, nbu);
+    kb_finalize_dims<T><<<dim3((r_max + 7) / 8, B), 256, 0, s>>>(d_traj, nbu);
     if (launches) *launches += 6;
     return cudaGetLastError();
 }
