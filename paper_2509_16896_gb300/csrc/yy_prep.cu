@@ -37,12 +37,13 @@ constexpr int kRowQ = YY_MAX_DIM / 64;   // float2 per lane of the longest row
 // restart 1 / (2 max(v_hat_d, (R_d / 4)^2)), and cos c_d, sin c_d (NaN cosine where the
 // half-width is too wide for the polynomials of yy_drift.cuh).
 template <typename T>
-__device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind) {
+__device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind,
+                                               int bid, int nblk) {
     if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
     const double* cen = (mode == kPrepRestart) ? b.next_centre : b.centre;
     const double* half = (mode == kPrepRestart) ? b.next_half : b.halfwidth;
     const int rp = k.r_pad;
-    for (int d = threadIdx.x; d < rp; d += blockDim.x) {
+    for (int d = bid * blockDim.x + threadIdx.x; d < rp; d += nblk * blockDim.x) {
         T hi = T(0), lo = T(0), iv = T(0), cc = T(0), sc = T(0);   // padded: u = 0 gives f = 0
         if (d < k.r) {
             const double c = cen[d];
@@ -260,7 +261,9 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
 }
 
 template <typename T>
-__global__ void k_prep_dims(Consts<T> k, Bufs<T> b, int mode, int init_kind) { prep_dims_body<T>(k, b, mode, init_kind); }
+__global__ void k_prep_dims(Consts<T> k, Bufs<T> b, int mode, int init_kind) {
+    prep_dims_body<T>(k, b, mode, init_kind, blockIdx.x, gridDim.x);
+}
 template <typename T>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_prep(Consts<T> k, Bufs<T> b, int mode, int first, double prior_mean,
                                               double prior_var) {
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 3 : 1) k_prep(Consts<T> 
 template <typename T>
 __global__ void kb_prep_dims(const Traj<T>* __restrict__ tr) {
     const Traj<T>& t = tr[blockIdx.y];
-    prep_dims_body<T>(t.k, t.b, kPrepRestart, t.restart_init);
+    prep_dims_body<T>(t.k, t.b, kPrepRestart, t.restart_init, 0, 1);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) kb_prep(const Traj<T>* __restrict__ tr) {
@@ -300,7 +303,8 @@ int prep_grid(long long n_pad) {
 template <typename T>
 cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, bool first,
                              double prior_mean, double prior_var, int init_kind, cudaStream_t s) {
-    k_prep_dims<T><<<1, 256, 0, s>>>(k, b, mode, init_kind);
+    // float64 cosine and sine per dimension: one 32-thread block per 32 dimensions
+    k_prep_dims<T><<<(unsigned)((k.r_pad + 31) / 32), 32, 0, s>>>(k, b, mode, init_kind);
     k_prep<T><<<(unsigned)prep_grid(k.n_pad), 256, 0, s>>>(k, b, mode, first ? 1 : 0, prior_mean, prior_var);
     return cudaGetLastError();
 }
