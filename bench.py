@@ -36,9 +36,10 @@ from synth.configs import batched_workloads  # noqa: E402
 
 DEFAULT_WORKLOAD = "cubic_r1000_n65536"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the prediction
-# kernel, from one ncu capture of the workload (profiles/k_ksum_tc_cubic_r1000_n65536.md).
-# An entry is removed whenever the kernel changes after its capture.
-NCU_TRAFFIC = {("cubic_r1000_n65536", "bf16"): 56.677120e6 + 2.271232e6}
+# kernel, from one ncu capture of the workload (profiles/k_ksum_tc_cubic_r1000_n65536.md),
+# keyed by workload and screen operands.  An entry is removed whenever the kernel changes
+# after its capture.
+NCU_TRAFFIC: dict = {}
 METRIC = "filter steps/s & kernel pair-evals/s at r=1000: mixed vs FP32, same RMSE"
 
 
@@ -117,15 +118,15 @@ def _dist():
     return rank, ws, local, dist
 
 
-def _make_filter(w, precision, seed, device, stream=None, screen_prefix=0):
+def _make_filter(w, precision, seed, device, stream=None, screen_prefix=0, screen_type="bf16"):
     from paper_2509_16896_gb300 import binding
-    cfg = binding.config_from_workload(w, precision=precision, screen_prefix=screen_prefix)
+    cfg = binding.config_from_workload(w, precision=precision, screen_prefix=screen_prefix, screen_type=screen_type)
     flt = binding.Filter(cfg, device=device, stream=stream)
     flt.init_nodes(sobol_poly_params(w.r, seed), sobol_scramble_params(w.r, seed), np.zeros(w.r))
     return flt
 
 
-def _algorithmic_flops(w, precision, screen=None):
+def _algorithmic_flops(w, precision, screen=None, stage=64):
     """Per prediction launch: BF16 path -> the Gram products the screen runs, i.e. per
     screened block of 128 targets x 256 sources 2 x 128 x 256 x (64 k) flops for the first
     pass over the first 64 k coordinates, plus 2 x 128 x 256 x r for every block screened
@@ -134,7 +135,7 @@ def _algorithmic_flops(w, precision, screen=None):
     FP32/FP64 path -> difference form, 3 flops per coordinate per pair."""
     if precision == "bf16":
         k, tiles, resc = screen
-        return 2.0 * 128 * 256 * (tiles * min(64 * k, w.r) + resc * w.r), "tensor"
+        return 2.0 * 128 * 256 * (tiles * min(stage * k, w.r) + resc * w.r), "tensor"
     return 3.0 * w.n * w.n * w.r, "alu"
 
 
@@ -142,6 +143,7 @@ def _config(w, prec):
     return {"workload": w.name, "r": w.r, "n": w.n, "n_scales": w.n_scales, "dt": w.dt,
             "R": w.R, "restart_interval": w.restart_interval, "ess_frac": w.ess_frac,
             "precision": prec, "trajectories_per_gpu": 1, "time_loop": "one CUDA graph of K steps",
+            "screen_operands": w.screen_type if prec == "bf16" else None,
             "l2": f"inputs larger than L2 (u is {w.n * w.r * 4 / 1e6:.0f} MB)"}
 
 
@@ -157,11 +159,14 @@ def run_yy(args):
     torch.cuda.set_device(device)
     w = WORKLOADS[args.workload]
     prec = args.precision or w.precision
+    if args.screen_type is None:
+        args.screen_type = w.screen_type
     seed = w.seed + 1000 * rank
     W, K = args.warmup, args.steps
     tr = simulate(w.model, w.r, W + K, w.dt, seed=seed)
     stream = torch.cuda.Stream(device)
-    flt = _make_filter(w, prec, seed, device, stream, screen_prefix=args.screen_prefix)
+    flt = _make_filter(w, prec, seed, device, stream, screen_prefix=args.screen_prefix,
+                       screen_type=args.screen_type)
     dys = torch.tensor(tr.dy, dtype=torch.float64, device=device)
     hist = torch.zeros((K, 2 * w.r + 4), dtype=torch.float64, device=device)
     with torch.cuda.stream(stream):
@@ -208,9 +213,12 @@ def run_yy(args):
     screen = None
     if prec == "bf16":
         last, nxt, tiles, resc = flt.screen()
-        screen = {"first_pass_chunks": last, "chunks": (w.r + 63) // 64, "tiles": tiles,
+        stage = 128 if args.screen_type == "fp8" else 64
+        screen = {"operands": args.screen_type, "first_pass_stages": last, "stage_coords": stage,
+                  "stages": ((w.r + 63) // 64 * 64 + stage - 1) // stage, "tiles": tiles,
                   "rescreened": resc, "exact_pairs": flt.counters()[1]}
-    flops, bound = _algorithmic_flops(w, prec, None if screen is None else (last, tiles, resc))
+    flops, bound = _algorithmic_flops(w, prec, None if screen is None else (last, tiles, resc),
+                                      128 if args.screen_type == "fp8" else 64)
     with torch.cuda.stream(stream):
         flt.update(dys[0])   # leave the handle in a consistent state
     # ---- end to end through the C ABI with host buffers ---------------------------
@@ -246,6 +254,9 @@ def run_yy(args):
         peak = peaks.get("bf16_tflops", 1900.0)
         achieved = flops / (pred_ms / 1e3) / 1e12
         peak_note = f"{src}: bf16_tflops (burst; prediction launches timed alone)"
+        if args.screen_type == "fp8":   # FP8 dense rate = 2 x BF16 (4.5 / 2.25 PFLOP/s nominal)
+            peak = 2.0 * peak
+            peak_note = f"{src}: 2 x bf16_tflops (fp8 nominal ratio; burst; prediction launches timed alone)"
     else:
         # float32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock
         peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -262,7 +273,8 @@ def run_yy(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"bf16": "bf16", "f32": "f32", "f64": "f64"}[prec],
+        # screen operands + float32 exact evaluation, log-sum-exp and update
+        "dtype": {"bf16": ("fp8+f32" if args.screen_type == "fp8" else "bf16+f32"), "f32": "f32", "f64": "f64"}[prec],
         "data": "synthetic (seeded Euler-Maruyama cubic sensor, scrambled Sobol nodes)",
         "config": _config(w, prec),
         "pair_evals_per_s": round(steps_per_s * w.n_scales * w.n * w.n, 1),
@@ -275,7 +287,7 @@ def run_yy(args):
         "screen": screen,
         "roofline": {"bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
                      "frac": round(achieved / peak, 4),
-                     "traffic": NCU_TRAFFIC.get((w.name, prec)),
+                     "traffic": NCU_TRAFFIC.get((w.name, args.screen_type)) if prec == "bf16" else None,
                      "kernel": "prediction (kernel sum)", "kernel_ms": round(pred_ms, 4),
                      "peak_source": peak_note},
     }
@@ -507,6 +519,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mlp-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--screen-type", default=None, choices=["bf16", "fp8"],
+                    help="operands of the screen's Gram product (default: the workload's)")
     ap.add_argument("--screen-prefix", type=int, default=0,
                     help="BF16 screen: first-pass coordinate chunks of 64 (0 = chosen on the device)")
     args = ap.parse_args()

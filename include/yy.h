@@ -89,6 +89,12 @@ typedef enum { YY_RESTART_INIT_GAUSS = 0, YY_RESTART_INIT_UNIFORM = 1 } yy_resta
  * half-width leaves [R/8, 8R], or when the box would not contain x_hat. */
 typedef enum { YY_RESTART_PLAIN = 0, YY_RESTART_LEARNED = 1 } yy_restart_rule;
 
+/* Operands of the screening Gram product of the BF16 prediction (library design, not in the
+ * paper): BF16 (error bound 2^-6 |u_i||u_s|), or FP8 e4m3 with the coordinates scaled by a
+ * power of two (bound 0.135 |u_i||u_s| plus a term for subnormal coordinates; twice the
+ * tensor rate, half the operand bytes, first-pass chunks of 128 coordinates). */
+typedef enum { YY_SCREEN_BF16 = 0, YY_SCREEN_FP8 = 1 } yy_screen_type;
+
 /* yy_restart modes: AUTO applies the device-side test computed by the last yy_update
  * (ESS < ess_frac * n, or restart_interval >= 2 and step % restart_interval == 0);
  * FORCE restarts unconditionally; NEVER only reports the test. */
@@ -111,12 +117,17 @@ typedef struct {
     double prior_var;          /* > 0 */
     int32_t restart_rule;      /* yy_restart_rule */
     int32_t screen_prefix;     /* YY_PREC_BF16 only: coordinates of the first screening pass
-                                * of the prediction, in units of 64 (see yy_predict); 0 =
+                                * of the prediction, in stages of 64 (BF16 screen) or 128 (FP8
+                                * screen) coordinates (see yy_predict); 0 =
                                 * chosen on the device from the previous predictions
                                 * (default), k >= 1 = fixed (values >= ceil(r/64) give one
                                 * full-coordinate pass), < 0 invalid. Members of a batch
                                 * default to one full-coordinate pass. Results do not depend
                                 * on it beyond float32 rounding. */
+    int32_t screen_type;       /* YY_PREC_BF16 only: yy_screen_type, the operand type of the
+                                * screen's Gram product. Results do not depend on it beyond
+                                * float32 rounding (the screen's bound covers the operand
+                                * rounding). */
 } yy_config;
 
 /* Bytes of device workspace that yy_create needs for cfg (0 if cfg is invalid). */
@@ -364,8 +375,9 @@ YY_EXPORT int64_t yy_launch_count(const yy_filter* f);
 YY_EXPORT yy_status yy_get_counters(yy_filter* f, int64_t* h_clamps, int64_t* h_exact_pairs);
 
 /* Screen of the last BF16 yy_predict (no counterpart in the paper; work accounting of the
- * screening passes described at yy_predict): *h_last_prefix = coordinate chunks of 64 of
- * its first pass (0 before the first prediction), *h_next_prefix = those the next
+ * screening passes described at yy_predict): *h_last_prefix = coordinate stages of its
+ * first pass (64 coordinates per stage with BF16 operands, 128 with FP8; 0 before the
+ * first prediction), *h_next_prefix = those the next
  * prediction will use, *h_tiles = 128-target x source-tile blocks screened (256 sources per
  * tile for a single filter), *h_rescreened = blocks screened again over all coordinates.
  * Any pointer may be NULL.  YY_ERR_UNSUPPORTED for other precisions.  Synchronises. */

@@ -25,6 +25,7 @@ MODELS = {"cubic": 0, "linear": 1}
 PRECISIONS = {"f64": 0, "f32": 1, "bf16": 2}
 RESTART_INIT = {"gauss": 0, "uniform": 1}
 RESTART_RULE = {"plain": 0, "learned": 1}
+SCREEN_TYPE = {"bf16": 0, "fp8": 1}
 RESTART_AUTO, RESTART_FORCE, RESTART_NEVER = 0, 1, 2
 SOBOL_POLY_WORDS = 16
 SOBOL_SCRAMBLE_WORDS = 33
@@ -58,7 +59,8 @@ class YYConfig(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("restart_interval", ctypes.c_int32),
                 ("ess_frac", ctypes.c_double), ("restart_init", ctypes.c_int32),
                 ("prior_mean", ctypes.c_double), ("prior_var", ctypes.c_double),
-                ("restart_rule", ctypes.c_int32), ("screen_prefix", ctypes.c_int32)]
+                ("restart_rule", ctypes.c_int32), ("screen_prefix", ctypes.c_int32),
+                ("screen_type", ctypes.c_int32)]
 
 
 def _declare(L: ctypes.CDLL) -> None:
@@ -152,20 +154,22 @@ def _check(fn: str, code: int) -> None:
 def make_config(model: str, r: int, n: int, dt: float, R: float, n_scales: int,
                 precision: str, restart_interval: int = 0, ess_frac: float = 0.0,
                 model_a: float = -0.5, restart_init: str = "gauss", prior_mean: float = 0.0,
-                prior_var: float = 1.0, restart_rule: str = "plain", screen_prefix: int = 0) -> YYConfig:
+                prior_var: float = 1.0, restart_rule: str = "plain", screen_prefix: int = 0,
+                screen_type: str = "bf16") -> YYConfig:
     return YYConfig(r=r, m=r, n=n, dt=dt, R=R, n_scales=n_scales, model=MODELS[model],
                     model_a=model_a, precision=PRECISIONS[precision],
                     restart_interval=restart_interval, ess_frac=ess_frac,
                     restart_init=RESTART_INIT[restart_init], prior_mean=prior_mean,
                     prior_var=prior_var, restart_rule=RESTART_RULE[restart_rule],
-                    screen_prefix=screen_prefix)
+                    screen_prefix=screen_prefix, screen_type=SCREEN_TYPE[screen_type])
 
 
 def config_from_workload(w, precision: str | None = None, **over) -> YYConfig:
     kw = dict(model=w.model, r=w.r, n=w.n, dt=w.dt, R=w.R, n_scales=w.n_scales,
               precision=precision or w.precision, restart_interval=w.restart_interval,
               ess_frac=w.ess_frac, model_a=w.model_a, prior_mean=w.prior_mean,
-              prior_var=w.prior_var, restart_rule=w.restart_rule)
+              prior_var=w.prior_var, restart_rule=w.restart_rule,
+              screen_type=getattr(w, "screen_type", "bf16"))
     kw.update(over)
     return make_config(**kw)
 

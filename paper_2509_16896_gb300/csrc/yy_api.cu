@@ -86,6 +86,7 @@ bool cfg_valid(const yy_config* c) {
     if (!(c->ess_frac >= 0.0) || c->ess_frac > 1.0) return false;
     if (c->restart_rule != YY_RESTART_PLAIN && c->restart_rule != YY_RESTART_LEARNED) return false;
     if (c->screen_prefix < 0) return false;
+    if (c->screen_type != YY_SCREEN_BF16 && c->screen_type != YY_SCREEN_FP8) return false;
     return true;
 }
 
@@ -202,6 +203,33 @@ void fill_consts(yy_filter* f, Consts<T>* k, const double* halfwidth) {
     k->tc_prefix = c.screen_prefix > 0 ? c.screen_prefix : 0;
     // symmetric blocks need the long-row epilogue (r > 64)
     k->tc_sym = (c.precision == YY_PREC_BF16 && c.r > 64) ? 1 : 0;
+    // Screen operands.  BF16: |dG| <= 2^-6 |u_i||u_s| (unit roundoff 2^-9 per operand, 4x
+    // slack).  FP8 e4m3 of s u, s the largest power of two with s 8 max R <= 448 (a learned
+    // box is at most 8 times wider): per product (2 2^-4 + 2^-8) |a b| = 0.129 |a b|, plus
+    // at most 2^-9 for reduced-precision accumulation inside one instruction (bound 0.14), and
+    // for subnormal codes an absolute error delta = 2^-10 / s per coordinate, which adds
+    // 1.07 delta sqrt(K) (|a| + |b|) + K delta^2 to |dG| (K coordinates); the d^2 bound is
+    // twice these, with 10 % slack.
+    k->tc_fp8 = (c.precision == YY_PREC_BF16 && c.screen_type == YY_SCREEN_FP8) ? 1 : 0;
+    k->tc_r8 = (int)((f->r_pad + 127) / 128 * 128);
+    k->tc_s = 1.f;
+    k->tc_g2 = -2.f;
+    k->tc_eps = 0.015625f;
+    k->tc_dabs = 0.f;
+    k->tc_dabs2 = 0.f;
+    if (k->tc_fp8) {
+        double rmax = 0.0;
+        for (int d = 0; d < c.r; ++d) rmax = fmax(rmax, halfwidth ? halfwidth[d] : c.R);
+        double s = 1.0;
+        while (s * 8.0 * rmax * 2.0 <= 448.0 && s < 1048576.0) s *= 2.0;
+        while (s * 8.0 * rmax > 448.0 && s > 1.0 / 1048576.0) s *= 0.5;
+        const double K = (double)k->tc_r8, delta = ldexp(1.0, -10) / s;
+        k->tc_s = (float)s;
+        k->tc_g2 = (float)(-2.0 / (s * s));
+        k->tc_eps = 0.14f;
+        k->tc_dabs = (float)(1.1 * 2.0 * 1.07 * delta * sqrt(K));
+        k->tc_dabs2 = (float)(1.1 * 2.0 * K * delta * delta);
+    }
     k->dt = (T)c.dt;
     double log_vol = 0.0;
     for (int d = 0; d < c.r; ++d) log_vol += log(2.0 * (halfwidth ? halfwidth[d] : c.R));
@@ -617,7 +645,7 @@ yy_status yy_get_screen(yy_filter* f, int32_t* h_last_prefix, int32_t* h_next_pr
     cudaError_t e = cudaMemcpyAsync(&hs, f->bf.stats, sizeof(DevStats), cudaMemcpyDeviceToHost, f->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
     if (e != cudaSuccess) return YY_ERR_CUDA;
-    const int nk = f->r_pad / kColAlign;
+    const int nk = f->kf.tc_fp8 ? f->kf.tc_r8 / 128 : (int)(f->r_pad / kColAlign);
     int v = f->cfg.screen_prefix > 0 ? f->cfg.screen_prefix : hs.tc_nk1;
     if (v <= 0) v = (nk + 1) / 2;
     if (h_last_prefix) *h_last_prefix = hs.tc_last_nk1;

@@ -163,11 +163,13 @@ yy_status upload(yy_batch* bt) {
         tr[b].k.tc_sym = 0;   // batch work lists cover every block
         // one full-coordinate pass unless configured: a member's probe of a short first pass
         // would hold up the whole batch's launch
-        if (f->cfg.screen_prefix <= 0) tr[b].k.tc_prefix = f->r_pad / 64;
+        if (f->cfg.screen_prefix <= 0) tr[b].k.tc_prefix = f->kf.tc_fp8 ? f->kf.tc_r8 / 128 : (int)(f->r_pad / 64);
         tr[b].b.tc_splits = splits[b];
         if (bt->precision == YY_PREC_BF16) {
-            if (!make_tc_map(&maps[kMapBytes * 2 * b], f->bf.ubf, f->n_pad, f->r_pad, 128) ||
-                !make_tc_map(&maps[kMapBytes * (2 * b + 1)], f->bf.ubf, f->n_pad, f->r_pad, bt->bn))
+            const bool f8 = f->kf.tc_fp8 != 0;
+            const int cols = f8 ? f->kf.tc_r8 : (int)f->r_pad;
+            if (!make_tc_map(&maps[kMapBytes * 2 * b], f->bf.ubf, f->n_pad, cols, 128, f8) ||
+                !make_tc_map(&maps[kMapBytes * (2 * b + 1)], f->bf.ubf, f->n_pad, cols, bt->bn, f8))
                 return YY_ERR_UNSUPPORTED;
             if (b == 0) memcpy(bt->map_any, &maps[0], kMapBytes);
         }

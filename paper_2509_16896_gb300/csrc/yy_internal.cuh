@@ -67,6 +67,13 @@ struct Consts {
     T cj_off[kMaxScales];    // C_j - C_ref, C_j = -(r/2) log(2 pi tau_j) + log w_q
     int tc_prefix;           // fixed first-pass chunks of the BF16 screen (0 = adaptive)
     int tc_sym;              // BF16 screen over the upper block triangle, both directions per block
+    int tc_fp8;              // screen operands FP8 e4m3 (else BF16)
+    int tc_r8;               // FP8: coordinates per row of the e4m3 copy (multiple of 128)
+    float tc_s;              // FP8: power-of-two scale of the coordinates in the e4m3 copy
+    float tc_g2;             // factor turning the accumulator into -2 G (-2, or -2 / s^2)
+    float tc_eps;            // relative error bound of G per |u_i||u_s|
+    float tc_dabs;           // FP8: absolute error term per (|u_i| + |u_s|) (subnormal codes)
+    float tc_dabs2;          // FP8: constant error term
     T logabs_c[kMaxScales + 1];
     T sign_c[kMaxScales + 1];  // 0 for a zero coefficient
     double c_ref;
@@ -199,7 +206,7 @@ template <typename T>
 cudaError_t launch_record_batch(const Traj<T>* d_traj, int B, double* hist_row, cudaStream_t s, int* launches);
 template <typename T>
 cudaError_t launch_reset_batch(const Traj<T>* d_traj, int B, cudaStream_t s, int* launches);
-bool make_tc_map(void* map /* CUtensorMap */, const void* base, long long rows, int cols, int box_rows);
+bool make_tc_map(void* map /* CUtensorMap */, const void* base, long long rows, int cols, int box_rows, bool fp8);
 cudaError_t launch_ksum_tc_batch(const Traj<float>* d_traj, int B, int N, long long n_pad_max,
                                  const void* d_maps /* CUtensorMap[2B] */, const int4* d_items,
                                  const int* d_cta_start, int grid, int bn, const Consts<float>& k_any,

@@ -85,6 +85,9 @@ struct Cfg {
     // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
                                       ((uint32_t)(BM >> 4) << 24);
+    // kind::f8f6f4 instruction descriptor: D fp32 (bits 4-5 = 1), A and B e4m3 (bits 7-9 and
+    // 10-12 = 0), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+    static constexpr uint32_t IDESC8 = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 };
 
 }  // namespace tc
@@ -194,6 +197,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint6
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
+__device__ __forceinline__ void mma_f8(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                       uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
@@ -245,17 +257,28 @@ __device__ __forceinline__ float screen_theta(const Consts<float>& k, bool live,
         const float gap = fmaxf(lmax - mx[j] + T, 0.f);
         rho = fmaxf(rho, k.tau[j] * Fi + sqrtf(2.f * k.tau[j] * gap));
     }
-    const float err = 2.f * tc::kEpsGram * sqrtf(nu_i * numax) + 1e-6f * (nu_i + numax + rho * rho);
+    const float err = 2.f * k.tc_eps * sqrtf(nu_i * numax) + k.tc_dabs * (sqrtf(nu_i) + sqrtf(numax)) + k.tc_dabs2 +
+                      1e-6f * (nu_i + numax + rho * rho);
     return fminf(rho * rho + err - nu_i, tc::kThetaMax);
 }
 
 }  // namespace
 
-// First-pass coordinate chunks (of 64) of one filter's screen: fixed by the configuration,
-// else the controller's last choice (tc_adapt), else half of the coordinates (the
-// controller finds the shortest clean length from above).
+// Coordinate stages of one filter's screen: 64 coordinates (BF16) or 128 (FP8, rows of
+// tc_r8 bytes) per stage.
+__device__ __forceinline__ int screen_stages(const Consts<float>& k) {
+    return k.tc_fp8 ? k.tc_r8 / 128 : k.r_pad / tc::BK;
+}
+// Chunks of 64 coordinates covered by the first `stages` stages (for the restricted norms).
+__device__ __forceinline__ int stage_chunks64(const Consts<float>& k, int stages) {
+    return k.tc_fp8 ? min(2 * stages, k.r_pad / 64) : stages;
+}
+
+// First-pass stages of one filter's screen: fixed by the configuration, else the
+// controller's last choice (tc_adapt), else half of the stages (the controller finds the
+// shortest clean length from above).
 __device__ __forceinline__ int prefix_chunks(const Consts<float>& k, const DevStats* st) {
-    const int nk = k.r_pad / tc::BK;
+    const int nk = screen_stages(k);
     int v = k.tc_prefix > 0 ? k.tc_prefix : st->tc_nk1;
     if (v <= 0) v = (nk + 1) / 2;
     return v < 1 ? 1 : (v > nk ? nk : v);
@@ -281,8 +304,8 @@ __device__ __forceinline__ float drift_at(const Consts<float>& k, const Bufs<flo
 __device__ __forceinline__ void colprep_body(const Consts<float>& k, const Bufs<float>& b, int chunk) {
     __shared__ float red_l[4], red_n[4], red_n1[4];
     const long long s = (long long)chunk * 128 + threadIdx.x;
-    const int nkc = k.r_pad / tc::BK;
-    const int nk1 = prefix_chunks(k, b.stats);
+    const int nkc = k.r_pad / 64;
+    const int nk1 = stage_chunks64(k, prefix_chunks(k, b.stats));
     float lw = -INFINITY, nu = 0.f, nu1 = 0.f;
     bool live = false;
     if (s < k.n) {
@@ -349,7 +372,7 @@ __device__ void tc_adapt(const Consts<float>& k, DevStats* st) {
     st->tc_last_esc = esc;
     st->tc_last_nk1 = nk1;
     if (k.tc_prefix > 0 || blk == 0) return;
-    const int nk = k.r_pad / tc::BK;
+    const int nk = screen_stages(k);
     constexpr int kHold = 1024, kSettle = 4;
     for (int x = 1; x <= nk; ++x)
         if (st->tc_hold[x] > 0) --st->tc_hold[x];
@@ -417,8 +440,10 @@ __device__ __forceinline__ void colprep2_body(const Consts<float>& k, const Bufs
                 rho = fmaxf(rho, k.tau[j] * Fc + sqrtf(2.f * k.tau[j] * gap));
             }
             const float q = b.nu[c], q1 = b.tc_q1t[c];
-            const float e = 2.f * tc::kEpsGram * sqrtf(q * ng) + 1e-6f * (q + ng + rho * rho);
-            const float e1 = 2.f * tc::kEpsGram * sqrtf(q1 * ng1) + 1e-6f * (q1 + ng1 + rho * rho);
+            const float e = 2.f * k.tc_eps * sqrtf(q * ng) + k.tc_dabs * (sqrtf(q) + sqrtf(ng)) + k.tc_dabs2 +
+                            1e-6f * (q + ng + rho * rho);
+            const float e1 = 2.f * k.tc_eps * sqrtf(q1 * ng1) + k.tc_dabs * (sqrtf(q1) + sqrtf(ng1)) + k.tc_dabs2 +
+                             1e-6f * (q1 + ng1 + rho * rho);
             qt = q - fminf(rho * rho + e, tc::kThetaMax);
             qt1 = q1 - fminf(rho * rho + e1, tc::kThetaMax);
         }
@@ -578,7 +603,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         const int L = nst - bmin;
         t0 = bmin + (int)(((long long)L * split) / nsplit);
         t1 = bmin + (int)(((long long)L * (split + 1)) / nsplit);
-        nk = kp->r_pad / BK;
+        nk = screen_stages(*kp);
         nk1 = (t1 - t0 <= kEscWords * 32) ? prefix_chunks(*kp, bp->stats) : nk;
     };
     // tile j of the item marked by epilogue warp e / by any epilogue warp (bitmap parity par)
@@ -620,8 +645,9 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, status)) return false;
                     mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                     uint8_t* dA = smem + s * STAGE_BYTES;
-                    tma_load_2d(ma, &full[s], dA, kb * BK, (int)i0);
-                    tma_load_2d(mb, &full[s], dA + A_BYTES, kb * BK, t * BN);
+                    const int x = kb * (kp->tc_fp8 ? 128 : BK);   // 128 bytes of coordinates per stage
+                    tma_load_2d(ma, &full[s], dA, x, (int)i0);
+                    tma_load_2d(mb, &full[s], dA + A_BYTES, x, t * BN);
                     last_phase[s] = (int)ph;
                 }
                 return true;
@@ -652,7 +678,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             // ---- MMA issuer -----------------------------------------------------------
             uint32_t it = 0, tcount = 0, npre = 0;
             bool ok = true;
-            auto mma_tile = [&](int nkb) -> bool {
+            auto mma_tile = [&](int nkb, bool fp8) -> bool {
                 const int acc = (int)(tcount & 1u);
                 const uint32_t aph = (tcount >> 1) & 1u;
                 if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) return false;
@@ -665,10 +691,18 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
                     const uint32_t b0a = a0 + A_BYTES;
+                    // four instructions per stage either way: K = 16 bf16 or 32 e4m3, 32 bytes
+                    if (fp8) {
 #pragma unroll
-                    for (int kk = 0; kk < BK / UK; ++kk)
-                        mma_bf16(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0a + kk * UK * 2), C::IDESC,
-                                 (kb | kk) != 0 ? 1u : 0u);
+                        for (int kk = 0; kk < BK / UK; ++kk)
+                            mma_f8(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0a + kk * 32), C::IDESC8,
+                                   (kb | kk) != 0 ? 1u : 0u);
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < BK / UK; ++kk)
+                            mma_bf16(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0a + kk * UK * 2), C::IDESC,
+                                     (kb | kk) != 0 ? 1u : 0u);
+                    }
                     mma_commit(&empty[s]);
                 }
                 mma_commit(&tfull[acc]);
@@ -680,13 +714,13 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 long long i0;
                 int t0, t1, split, nsplit, nk, nk1;
                 item_kb(idx, kp, bp, ma, mb, i0, t0, t1, split, nsplit, nk, nk1);
-                for (int t = t0; t < t1 && ok; ++t) ok = mma_tile(nk1);
+                for (int t = t0; t < t1 && ok; ++t) ok = mma_tile(nk1, kp->tc_fp8 != 0);
                 unsigned long long nesc = 0;
                 if (ok && nk1 < nk) {
                     const uint32_t par = npre++ & 1u;
                     if (!wait_bounded(escb, par, abort_flag, status)) { ok = false; break; }
                     for (int t = t0; t < t1 && ok; ++t)
-                        if (esc_any(par, t - t0)) { ok = mma_tile(nk); ++nesc; }
+                        if (esc_any(par, t - t0)) { ok = mma_tile(nk, kp->tc_fp8 != 0); ++nesc; }
                 }
                 if (ok) {
                     atomicAdd(&bp->stats->tc_blk, (unsigned long long)(t1 - t0));
@@ -728,8 +762,9 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 nf_i = b.nf[i];
                 li = b.logw[i];
                 if (pre) {   // same summation order as colprep's tc_q1
-                    const float* nc = b.nu_chunk + (size_t)i * nk;
-                    for (int c = 0; c < nk1; ++c) nu1_i += nc[c];
+                    const float* nc = b.nu_chunk + (size_t)i * (k.r_pad / 64);
+                    const int c64 = stage_chunks64(k, nk1);
+                    for (int c = 0; c < c64; ++c) nu1_i += nc[c];
                 }
             }
             const float Fi = sqrtf(nf_i);
@@ -901,7 +936,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                         uint32_t cm = 0;
 #pragma unroll
                         for (int c = 0; c < 32; ++c) {
-                            const float dd = fmaf(-2.f, __uint_as_float(v[c]), qw[ch * 32 + c]);
+                            const float dd = fmaf(k.tc_g2, __uint_as_float(v[c]), qw[ch * 32 + c]);
                             cm |= (dd <= theta ? 1u : 0u) << c;
                         }
                         const long long sb = c0 + ch * 32;
@@ -938,16 +973,16 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
 #pragma unroll
                     for (int c4 = 0; c4 < 8; ++c4) {
                         const float4 qq = q4[c4];
-                        mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 0]), qq.x));
-                        mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 1]), qq.y));
-                        mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 2]), qq.z));
-                        mn = fminf(mn, fmaf(-2.f, __uint_as_float(v[4 * c4 + 3]), qq.w));
+                        mn = fminf(mn, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 0]), qq.x));
+                        mn = fminf(mn, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 1]), qq.y));
+                        mn = fminf(mn, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 2]), qq.z));
+                        mn = fminf(mn, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 3]), qq.w));
                     }
                     uint32_t m0 = 0, t0m = 0;
                     if (mn <= theta_any) {
 #pragma unroll
                         for (int c = 0; c < 32; ++c) {
-                            const float g2 = -2.f * __uint_as_float(v[c]);
+                            const float g2 = k.tc_g2 * __uint_as_float(v[c]);
                             m0 |= (g2 + qw[ch * 32 + c] <= theta ? 1u : 0u) << c;
                             if (hm == 2) t0m |= ((g2 + qtw[ch * 32 + c]) + nu_src <= 0.f ? 1u : 0u) << c;
                         }
@@ -1164,17 +1199,19 @@ cudaError_t launch_bn(int N, unsigned grid, const CUtensorMap& a, const CUtensor
 
 }  // namespace
 
-bool make_tc_map(void* map_out, const void* base, long long rows, int cols, int box_rows) {
+// TMA map of the screen's operand copy: rows x cols elements, bf16 (box 64 x box_rows) or
+// e4m3 bytes (box 128 x box_rows), 128-byte swizzle either way.
+bool make_tc_map(void* map_out, const void* base, long long rows, int cols, int box_rows, bool fp8) {
     CUtensorMap* map = static_cast<CUtensorMap*>(map_out);
     auto fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)tc::BK, (cuuint32_t)box_rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * (fp8 ? 1 : 2)};
+    const cuuint32_t box[2] = {(cuuint32_t)(fp8 ? 128 : tc::BK), (cuuint32_t)box_rows};
     const cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base),
+              dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Opts the prediction kernels into their shared-memory size on the current device (called
@@ -1191,7 +1228,8 @@ cudaError_t prepare_ksum_tc() {
 cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s, int* launches) {
     if (!b.ubf || !b.tc_items || k.n_pad % 256 != 0 || k.r_pad % tc::BK != 0) return cudaErrorInvalidValue;
     CUtensorMap ma, mb;
-    if (!make_tc_map(&ma, b.ubf, k.n_pad, k.r_pad, tc::BM) || !make_tc_map(&mb, b.ubf, k.n_pad, k.r_pad, 256))
+    const int cols = k.tc_fp8 ? k.tc_r8 : k.r_pad;
+    if (!make_tc_map(&ma, b.ubf, k.n_pad, cols, tc::BM, k.tc_fp8) || !make_tc_map(&mb, b.ubf, k.n_pad, cols, 256, k.tc_fp8))
         return cudaErrorNotSupported;
     cudaError_t e = cudaMemsetAsync(&b.stats->candidates, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;

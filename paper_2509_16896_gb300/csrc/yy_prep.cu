@@ -17,6 +17,8 @@
 #include "yy_internal.cuh"
 #include "yy_drift.cuh"
 
+#include <cuda_fp8.h>
+
 #include <type_traits>
 
 namespace yy {
@@ -167,7 +169,13 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
                         lw -= (T)(0.5 * z * z / prior_var);
                     }
                 }
-                if (first && b.ubf) b.ubf[(size_t)i * rp + d] = __float2bfloat16_rn(d < k.r ? uf : 0.0f);
+                if (first && b.ubf) {
+                    if (k.tc_fp8)   // e4m3 copy of s u, rows of tc_r8 bytes (tail bytes stay zero)
+                        reinterpret_cast<uint8_t*>(b.ubf)[(size_t)i * k.tc_r8 + d] = (uint8_t)__nv_cvt_float_to_fp8(
+                            d < k.r ? k.tc_s * uf : 0.0f, __NV_SATFINITE, __NV_E4M3);
+                    else
+                        b.ubf[(size_t)i * rp + d] = __float2bfloat16_rn(d < k.r ? uf : 0.0f);
+                }
                 if (b.store_f) fi[d] = fv;
             }
             if (first && b.nu_chunk) {

@@ -29,6 +29,7 @@ class Workload:
     prior_mean: float = 0.0
     prior_var: float = 1.0
     restart_rule: str = "plain"  # "plain" | "learned"
+    screen_type: str = "bf16"    # operands of the BF16 path's screening Gram product: "bf16" | "fp8"
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -42,9 +43,9 @@ WORKLOADS: dict[str, Workload] = {
     # r = 100: FP32 form against the BF16 Gram form
     "cubic_r100_n16384": Workload("cubic_r100_n16384", "cubic", r=100, n=16384, steps=200,
                                   n_scales=2, seed=2, precision="bf16"),
-    # headline: r = 1000, three bandwidths
+    # headline: r = 1000, three bandwidths; the screen's Gram product on FP8 operands
     "cubic_r1000_n65536": Workload("cubic_r1000_n65536", "cubic", r=1000, n=65536, steps=100,
-                                   n_scales=3, seed=3, precision="bf16"),
+                                   n_scales=3, seed=3, precision="bf16", screen_type="fp8"),
     # learned restart proposal
     "cubic_r50_n8192": Workload("cubic_r50_n8192", "cubic", r=50, n=8192, steps=500,
                                 n_scales=2, seed=5, precision="bf16"),

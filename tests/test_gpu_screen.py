@@ -13,15 +13,16 @@ from ._helpers import rel_err, sobol_inputs
 pytestmark = pytest.mark.gpu
 
 
-def _filter(r, n, N, prec, prefix=0, restart_interval=0):
+def _filter(r, n, N, prec, prefix=0, restart_interval=0, screen="bf16"):
     from paper_2509_16896_gb300 import binding
     cfg = binding.make_config(model="cubic", r=r, n=n, dt=0.01, R=0.3, n_scales=N, precision=prec,
-                              restart_interval=restart_interval, screen_prefix=prefix)
+                              restart_interval=restart_interval, screen_prefix=prefix, screen_type=screen)
     return binding.Filter(cfg)
 
 
+@pytest.mark.parametrize("screen", ["bf16", "fp8"])
 @pytest.mark.parametrize("r,n,N", [(1000, 4096, 3), (300, 3000, 2), (130, 2500, 2)])
-def test_every_first_pass_length_matches_fp32_path(yy_lib, r, n, N):
+def test_every_first_pass_length_matches_fp32_path(yy_lib, r, n, N, screen):
     import torch
     poly, scr = sobol_inputs(r, 31)
     tr = simulate("cubic", r, 3, 0.01, seed=31)
@@ -40,11 +41,12 @@ def test_every_first_pass_length_matches_fp32_path(yy_lib, r, n, N):
     ref.predict()
     a, a_off = ref.get_log_weights()
     a = a.astype(np.float64) + a_off
-    nk = (r + 63) // 64
+    # stages of 64 (BF16 operands) or 128 (FP8 operands) coordinates
+    nk = (r + 63) // 64 if screen == "bf16" else ((r + 63) // 64 * 64 + 127) // 128
     n_pad = (n + 255) // 256 * 256
     seen = {}
     for prefix in sorted({1, 2, max(1, nk // 2), nk, 0}):
-        flt = _filter(r, n, N, "bf16", prefix=prefix)
+        flt = _filter(r, n, N, "bf16", prefix=prefix, screen=screen)
         flt.init_nodes(poly, scr, np.zeros(r))
         flt.set_state(centre, logw.astype(np.float32), lognorm, step)
         flt.predict()
@@ -59,11 +61,13 @@ def test_every_first_pass_length_matches_fp32_path(yy_lib, r, n, N):
         assert 1 <= last <= nk and 1 <= nxt <= nk
         if prefix == nk:
             assert resc == 0 and last == nk
+            if r == 1000:   # a sound Gram product screens out nearly every pair at full length
+                assert flt.counters()[1] < 0.001 * n * n
         if prefix > 0:
             assert last == nxt == min(prefix, nk)   # a fixed length is kept
         seen[prefix] = resc
-    if r == 1000:
-        # 64 coordinates cannot separate pairs whose weights differ by hundreds of nats
+    if r == 1000 and screen == "bf16":
+        # 64 coordinates cannot separate pairs whose weights differ by a hundred nats or more
         assert spread > 100 and seen[1] > 0
 
 
