@@ -144,6 +144,7 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
         b.tc_qt1 = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_tile_rmax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
         b.tc_tile_rmax1 = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
+        b.tc_cinfo = cv.take<float>((size_t)(n_pad / 128) * 8 * sizeof(float));
         b.tc_xlse = cv.take<unsigned long long>((size_t)n_pad * kMaxScales * sizeof(unsigned long long));
         b.tc_tile_lmax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));
         b.tc_tile_numax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));

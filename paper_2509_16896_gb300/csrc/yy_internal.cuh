@@ -118,6 +118,7 @@ struct Bufs {
                           // |u_c|^2 - (rho_c^2 + err_c) (+inf: no target, -inf: no bound)
     float* tc_qt1;        // [n_pad] the same over the first-pass coordinates
     float* tc_tile_rmax;  // [n_pad / 128] largest rho_c^2 + err_c of a chunk's targets (+inf: unbounded)
+    float* tc_cinfo;      // [n_pad / 128][8] per chunk: lmax, numax, numax1, rmax, rmax1 (staged per tile)
     float* tc_tile_rmax1; // [n_pad / 128] the same over the first-pass coordinates
     unsigned long long* tc_xlse;   // [n_pad][kMaxScales] (max, sum) float pairs of the terms a
                                    // node receives as the column of a symmetric block

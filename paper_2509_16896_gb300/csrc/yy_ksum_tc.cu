@@ -79,7 +79,7 @@ struct Cfg {
     // ring | row- and column-direction q values per accumulator | candidate masks per
     // epilogue warp | marking bitmaps | row states exchanged between the two warps of a lane
     // quarter | barriers
-    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 4 * BN * 4 + 2 * EPI_WARPS * HALF * 4 +
+    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 4 * BN * 4 + 2 * 16 * 4 + 2 * EPI_WARPS * HALF * 4 +
                                       EPI_WARPS * 2 * kEscWords * 4 + 128 * kMaxScales * 2 * 4 + 256;
     // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1),
     // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
@@ -245,20 +245,29 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// Screening threshold on |u_s|^2 - 2 G for one target row (see the file comment).
+// An upper bound of sqrt(x) for x >= 0: x times the reciprocal square root (hardware
+// approximation, relative error far below 1e-6), widened by 1e-6.  The screen only needs
+// its radii not to be underestimated.
+__device__ __forceinline__ float sqrt_up(float x) {
+    return x > 0.f ? x * rsqrtf(x) * 1.000001f : 0.f;
+}
+
+// Screening threshold on |u_s|^2 - 2 G for one target row (see the file comment).  rnu_i
+// and rnumax are the square roots of nu_i and numax (per row and per tile, precomputed).
 template <int N>
-__device__ __forceinline__ float screen_theta(const Consts<float>& k, bool live, float nu_i, float Fi,
-                                              const float (&mx)[N], float lmax, float numax, float T) {
+__device__ __forceinline__ float screen_theta(const Consts<float>& k, bool live, float nu_i, float rnu_i, float Fi,
+                                              const float (&mx)[N], float lmax, float numax, float rnumax,
+                                              float T) {
     if (!live || lmax == -INFINITY) return -INFINITY;
     float rho = 0.f;
 #pragma unroll
     for (int j = 0; j < N; ++j) {
         if (mx[j] == -INFINITY) return tc::kThetaMax;
         const float gap = fmaxf(lmax - mx[j] + T, 0.f);
-        rho = fmaxf(rho, k.tau[j] * Fi + sqrtf(2.f * k.tau[j] * gap));
+        rho = fmaxf(rho, k.tau[j] * Fi + sqrt_up(2.f * k.tau[j] * gap));
     }
-    const float err = 2.f * k.tc_eps * sqrtf(nu_i * numax) + k.tc_dabs * (sqrtf(nu_i) + sqrtf(numax)) + k.tc_dabs2 +
-                      1e-6f * (nu_i + numax + rho * rho);
+    const float err = 2.f * k.tc_eps * rnu_i * rnumax + k.tc_dabs * (rnu_i + rnumax) + k.tc_dabs2 +
+                      2e-6f * (nu_i + numax + rho * rho);
     return fminf(rho * rho + err - nu_i, tc::kThetaMax);
 }
 
@@ -342,6 +351,13 @@ __device__ __forceinline__ void colprep_body(const Consts<float>& k, const Bufs<
         b.tc_tile_lmax[chunk] = lm;
         b.tc_tile_numax[chunk] = nm;
         b.tc_tile_numax1[chunk] = nm1;
+        float* ci = b.tc_cinfo + (size_t)chunk * 8;   // staged per tile by the prediction's producer
+        ci[0] = lm;
+        ci[1] = nm;
+        ci[2] = nm1;
+        ci[5] = sqrt_up(nm);    // square roots of the norm maxima, for the screen's error term
+        ci[6] = sqrt_up(nm1);
+        ci[7] = 0.f;
     }
 }
 
@@ -466,6 +482,8 @@ __device__ __forceinline__ void colprep2_body(const Consts<float>& k, const Bufs
         // widened by float rounding of q_c - (q_c - R_c), so the combined test stays conservative
         b.tc_tile_rmax[chunk] = r0 + 1e-6f * (fabsf(r0) + 1.f);
         b.tc_tile_rmax1[chunk] = r1 + 1e-6f * (fabsf(r1) + 1.f);
+        b.tc_cinfo[(size_t)chunk * 8 + 3] = b.tc_tile_rmax[chunk];
+        b.tc_cinfo[(size_t)chunk * 8 + 4] = b.tc_tile_rmax1[chunk];
     }
 }
 
@@ -536,7 +554,8 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     // staged by the producer per accumulator: [2][BN] each
     float* qbuf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
     float* qtbuf = qbuf + 2 * BN;
-    uint32_t* cms = reinterpret_cast<uint32_t*>(qtbuf + 2 * BN);         // [EPI_WARPS][HALF / 32][32]
+    float* qinfo = qtbuf + 2 * BN;                                       // [2][16]: the tile's chunk maxima
+    uint32_t* cms = reinterpret_cast<uint32_t*>(qinfo + 2 * 16);         // [EPI_WARPS][HALF / 32][32]
     uint32_t* tcms = cms + EPI_WARPS * HALF;                             // [EPI_WARPS][HALF / 32][32]
     uint32_t* escm = tcms + EPI_WARPS * HALF;                            // [EPI_WARPS][2][kEscWords]
     float* xch = reinterpret_cast<float*>(escm + EPI_WARPS * 2 * kEscWords);   // [128 rows][kMaxScales][2]
@@ -634,8 +653,10 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 ++tp;
                 if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) return false;
                 const uint32_t qb = (uint32_t)(BN * sizeof(float));
-                mbar_arrive_expect_tx(&qfull[acc], kp->tc_sym ? 2 * qb : qb);
+                const uint32_t ib = (uint32_t)((BN / 128) * 8 * sizeof(float));
+                mbar_arrive_expect_tx(&qfull[acc], (kp->tc_sym ? 2 * qb : qb) + ib);
                 bulk_load(qbuf + acc * BN, (prefix ? bp->tc_q1 : bp->tc_q) + (size_t)t * BN, qb, &qfull[acc]);
+                bulk_load(qinfo + acc * 16, bp->tc_cinfo + (size_t)t * (BN / 128) * 8, ib, &qfull[acc]);
                 if (kp->tc_sym)
                     bulk_load(qtbuf + acc * BN, (prefix ? bp->tc_qt1 : bp->tc_qt) + (size_t)t * BN, qb, &qfull[acc]);
                 last_qphase[acc] = (int)aph;
@@ -768,6 +789,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 }
             }
             const float Fi = sqrtf(nf_i);
+            const float rnu_i = sqrt_up(nu_i), rnu1_i = sqrt_up(nu1_i);
             float rowc[N], mx[N], sm[N];
             // the exact self term (u_i - u_i = 0) is the screening reference of every split
             // and of both halves; it is counted once, by the first half of the split whose
@@ -898,28 +920,29 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 }
                 const bool first_pass = (mode == 1);
                 const float nu_s = first_pass ? nu1_i : nu_i;
-                const float* nmx = first_pass ? b.tc_tile_numax1 : b.tc_tile_numax;
-                // this warp's columns of the staged q values (producer, per accumulator)
+                // this warp's columns of the staged q values and the tile's chunk maxima
+                // (producer, per accumulator)
                 const float* qw = qbuf + acc * BN + h * HALF;
                 const float* qtw = qtbuf + acc * BN + h * HALF;   // q_c - (rho_c^2 + err_c)
-                float lmax = b.tc_tile_lmax[t * (BN / 128)];
-                float numax = nmx[t * (BN / 128)];
+                const float* ci = qinfo + acc * 16;
+                if (!wait_bounded(&qfull[acc], aph, abort_flag, status)) return false;
+                float lmax = ci[0];
+                float numax = first_pass ? ci[2] : ci[1];
+                float rnumax = first_pass ? ci[6] : ci[5];
                 if (BN == 256) {
-                    lmax = fmaxf(lmax, b.tc_tile_lmax[2 * t + 1]);
-                    numax = fmaxf(numax, nmx[2 * t + 1]);
+                    lmax = fmaxf(lmax, ci[8]);
+                    numax = fmaxf(numax, first_pass ? ci[10] : ci[9]);
+                    rnumax = fmaxf(rnumax, first_pass ? ci[14] : ci[13]);
                 }
-                float theta = screen_theta<N>(k, live, nu_s, Fi, mx, lmax, numax, T);
-                // column direction: per column c the precomputed q_c - (rho_c^2 + err_c) of c
-                // as a target; the row side adds nu_i (+inf for dead rows)
+                const float rnu_s = first_pass ? rnu1_i : rnu_i;
+                float theta = screen_theta<N>(k, live, nu_s, rnu_s, Fi, mx, lmax, numax, rnumax, T);
                 const float nu_src = (hm == 2 && src_live) ? nu_s : INFINITY;
                 // one test per lane and 32 columns covers both directions: a pair can be a
                 // candidate only if q_s - 2 G <= max(theta_i, Rmax - nu_i), Rmax the largest
                 // column bound of this warp's chunk
                 const float theta_any =
-                    (hm == 2 && src_live)
-                        ? fmaxf(theta, (first_pass ? b.tc_tile_rmax1 : b.tc_tile_rmax)[cchunk] - nu_src)
-                        : theta;
-                if (!wait_bounded(&qfull[acc], aph, abort_flag, status)) return false;
+                    (hm == 2 && src_live) ? fmaxf(theta, ci[(BN == 256 ? h : 0) * 8 + (first_pass ? 4 : 3)] - nu_src)
+                                          : theta;
                 if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) return false;
                 tc_fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + h * HALF);
@@ -955,7 +978,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                             add_score(s1, s2, src);
                             ++ncand;
                         }
-                        theta = screen_theta<N>(k, live, nu_s, Fi, mx, lmax, numax, T);
+                        theta = screen_theta<N>(k, live, nu_s, rnu_s, Fi, mx, lmax, numax, rnumax, T);
                     }
                     release(acc);
                     return true;
@@ -969,15 +992,17 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     tmem_ld32(tbase + (uint32_t)(ch * 32), v);
                     tmem_ld_wait();
                     const float4* q4 = reinterpret_cast<const float4*>(qw + ch * 32);
-                    float mn = INFINITY;
+                    // four independent minimum chains (no 32-long dependency)
+                    float m0c = INFINITY, m1c = INFINITY, m2c = INFINITY, m3c = INFINITY;
 #pragma unroll
                     for (int c4 = 0; c4 < 8; ++c4) {
                         const float4 qq = q4[c4];
-                        mn = fminf(mn, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 0]), qq.x));
-                        mn = fminf(mn, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 1]), qq.y));
-                        mn = fminf(mn, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 2]), qq.z));
-                        mn = fminf(mn, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 3]), qq.w));
+                        m0c = fminf(m0c, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 0]), qq.x));
+                        m1c = fminf(m1c, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 1]), qq.y));
+                        m2c = fminf(m2c, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 2]), qq.z));
+                        m3c = fminf(m3c, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 3]), qq.w));
                     }
+                    const float mn = fminf(fminf(m0c, m1c), fminf(m2c, m3c));
                     uint32_t m0 = 0, t0m = 0;
                     if (mn <= theta_any) {
 #pragma unroll
