@@ -1,6 +1,7 @@
-"""Parity at the headline size in the configuration the bench times: the cubic sensor with
-r = 1000, n = 65536 scrambled Sobol nodes, N = 3 bandwidths, BF16 screen with the device-
-chosen first pass, steps replayed as one CUDA graph.  The oracle cannot predict all 65536
+"""Parity at full workload sizes in the configuration the bench times: the cubic sensor with
+r = 1000, n = 65536 scrambled Sobol nodes, N = 3 bandwidths (FP8 screen operands), and with
+r = 100, n = 16384, N = 2 (BF16 screen operands), the device-chosen first pass, steps
+replayed as one CUDA graph.  The oracle cannot predict all 65536
 rows, so it predicts sampled blocks of target rows (each against all sources) from the
 exact state the GPU holds after the graph, and the GPU prediction from that state must
 agree there within the float32 tolerance; the whole-vector properties (no NaN, -inf
@@ -20,11 +21,12 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-5
 
 
-def test_headline_size_sampled_rows_match_oracle(yy_lib):
+@pytest.mark.parametrize("name", ["cubic_r1000_n65536", "cubic_r100_n16384"])
+def test_full_size_sampled_rows_match_oracle(yy_lib, name):
     import torch
     from oracle import filter as F
     from paper_2509_16896_gb300 import binding
-    w = WORKLOADS["cubic_r1000_n65536"]
+    w = WORKLOADS[name]
     W, K = 3, 4
     cfg = binding.config_from_workload(w, precision="bf16")
     stream = torch.cuda.Stream()
