@@ -34,6 +34,13 @@ __device__ __forceinline__ T warp_sum(T v) {
 
 constexpr int kRowQ = YY_MAX_DIM / 64;   // float2 per lane of the longest row
 
+template <typename T>
+__device__ __forceinline__ T exp_w(T x);
+template <>
+__device__ __forceinline__ float exp_w<float>(float x) { return expf(x); }
+template <>
+__device__ __forceinline__ double exp_w<double>(double x) { return exp(x); }
+
 // Per-dimension constants of one preparation pass: the centre split into a T-precision
 // head and tail (x = c_hi + (u + c_lo) loses only the final rounding), for a Gaussian
 // restart 1 / (2 max(v_hat_d, (R_d / 4)^2)), and cos c_d, sin c_d (NaN cosine where the
@@ -71,8 +78,8 @@ __device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>
 template <typename T, int mode, bool first, bool narrow>
 __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, double prior_mean,
                                           double prior_var, int bid, int nblk, const T* s_hi, const T* s_lo,
-                                          const T* s_iv, const T* s_cc, const T* s_sc, double& lse_m,
-                                          double& lse_s) {
+                                          const T* s_iv, const T* s_cc, const T* s_sc, T& lse_m,
+                                          T& lse_s) {
     const int rp = k.r_pad;
     const int lane = threadIdx.x & 31;
     const long long warp = (bid * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -200,11 +207,15 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
             if (mode != kPrepOnly) {
                 const T out = b.mask[i] ? T(-INFINITY) : lw;
                 b.logw[i] = out;
-                // running (max, sum) of the written log-weights (lane 0 of every warp)
-                const double l = (double)out;
-                if (l != -INFINITY) {
-                    if (l > lse_m) { lse_s = lse_s * (double)expf((float)(lse_m - l)) + 1.0; lse_m = l; }
-                    else lse_s += (double)expf((float)(l - lse_m));
+                // running (max, sum) of the written log-weights (lane 0 of every warp), in the
+                // working precision: float64 issue time per row is large on this part
+                if (out != T(-INFINITY)) {
+                    if (out > lse_m) {
+                        lse_s = (lse_m == T(-INFINITY)) ? T(1) : lse_s * exp_w<T>(lse_m - out) + T(1);
+                        lse_m = out;
+                    } else {
+                        lse_s += exp_w<T>(out - lse_m);
+                    }
                 }
             }
         }
@@ -233,7 +244,7 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
     int my_narrow = 1;
     for (int d = threadIdx.x; d < k.r; d += blockDim.x) my_narrow &= (s_cc[d] == s_cc[d]) ? 1 : 0;
     const int narrow = __syncthreads_and(my_narrow);
-    double lse_m = -INFINITY, lse_s = 0.0;
+    T lse_m = T(-INFINITY), lse_s = T(0);
 #define YY_PREP_ROWS(M, F, W) \
     prep_rows<T, M, F, W>(k, b, prior_mean, prior_var, bid, nblk, s_hi, s_lo, s_iv, s_cc, s_sc, lse_m, lse_s)
     if (mode == kPrepRestart) {
@@ -251,7 +262,7 @@ __device__ __forceinline__ void prep_body(const Consts<T>& k, const Bufs<T>& b, 
     if (lse_out && mode != kPrepOnly) {
         __shared__ double sm_m[8], sm_s[8];
         const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-        if (lane == 0) { sm_m[wib] = lse_m; sm_s[wib] = lse_s; }
+        if (lane == 0) { sm_m[wib] = (double)lse_m; sm_s[wib] = (double)lse_s; }
         __syncthreads();
         if (threadIdx.x == 0) {
             double M = -INFINITY, S = 0.0;

@@ -106,7 +106,7 @@ __device__ __forceinline__ void loglik_body(const Consts<T>& k, const Bufs<T>& b
     const T half_dt = T(0.5) * k.dt;
     const bool cubic = k.model == YY_MODEL_CUBIC;
     const int nq = k.r_pad >> 6;
-    double m = -INFINITY, s = 0.0;
+    T m = T(-INFINITY), s = T(0);   // working precision (see below)
     for (long long i = warp; i < k.n; i += nwarps) {
         const T p = b.logw_pred[i];
         const float2* ui = reinterpret_cast<const float2*>(b.u + (size_t)i * k.r_pad);
@@ -129,15 +129,19 @@ __device__ __forceinline__ void loglik_body(const Consts<T>& k, const Bufs<T>& b
         const T lw = (p == T(-INFINITY)) ? T(-INFINITY) : p + tot;
         if (lane == 0) {
             b.logw[i] = lw;
-            // running (max, sum) of this warp's rows; float exponentials, float64 sums
-            const double l = (double)lw;
-            if (l != -INFINITY) {
-                if (l > m) { s = s * (double)expf((float)(m - l)) + 1.0; m = l; }
-                else s += (double)expf((float)(l - m));
+            // running (max, sum) of this warp's rows in the working precision (float64 issue
+            // time per row is large on this part); blocks merge in float64
+            if (lw != T(-INFINITY)) {
+                if (lw > m) {
+                    s = (m == T(-INFINITY)) ? T(1) : s * exp_t<T>(m - lw) + T(1);
+                    m = lw;
+                } else {
+                    s += exp_t<T>(lw - m);
+                }
             }
         }
     }
-    if (lane == 0) { sm[wib] = m; ss[wib] = s; }
+    if (lane == 0) { sm[wib] = (double)m; ss[wib] = (double)s; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double M = -INFINITY, S = 0.0;
