@@ -303,10 +303,10 @@ YY_EXPORT yy_status yy_batch_graph_launch(yy_batch* bt);
  * number of persistent CTAs (1..1024).  yy_batch_autotune first runs one prediction with
  * every filter on the tensor-core screen and reads each filter's screen pass fraction
  * (pairs evaluated exactly / n^2); it then times, on the batch itself (reps predictions
- * each), every combination of a routing threshold in {1e-3, 1e-2, 5e-2, never} (filters
- * whose fraction exceeds it use the FP32 form, which is faster when most pairs are within
- * reach of the kernel, i.e. at low r), bn in {256, 128} and grid in {1, 2, 4} x SM count,
- * and keeps the fastest.  If cache_path is not NULL the choice is recorded there keyed by
+ * each), the routing thresholds {3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1, never} (filters whose
+ * fraction exceeds it use the FP32 form, which is faster when most pairs are within reach
+ * of the kernel, i.e. at low r) with bn = 256 and grid = 2 x SM count, then bn in
+ * {256, 128} x grid in {1, 2, 4} x SM count with the best routing, and keeps the fastest.  If cache_path is not NULL the choice is recorded there keyed by
  * the batch's shape and reused instead of timing.  yy_batch_get_routing reports the
  * per-filter choice (0 = tensor-core screen, 1 = FP32 form; host int32 [B]). */
 YY_EXPORT yy_status yy_batch_set_schedule(yy_batch* bt, int32_t bn, int32_t grid);

@@ -2,8 +2,9 @@
 // trajectory, the prediction is one persistent tcgen05 launch over a longest-processing-
 // time-first work list (plus one batched FP32-form launch for the filters routed there),
 // and the K-step loop can be captured as one CUDA graph.  The autotuner measures each
-// filter's screen pass fraction, then times routing thresholds x source-tile widths x
-// persistent grid sizes on the batch's own prediction and keeps the fastest.
+// filter's screen pass fraction, then times routing thresholds (with a middle schedule) and
+// then source-tile widths x persistent grid sizes (with the best routing) on the batch's own
+// prediction and keeps the fastest.
 #include <math.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -435,30 +436,44 @@ yy_status yy_batch_autotune(yy_batch* bt, const char* cache_path, int32_t reps, 
     const int sms = sm_count();
     const int cand_bn[2] = {256, 128};
     const int cand_mul[3] = {1, 2, 4};
-    const double cand_thr[4] = {1e-3, 1e-2, 5e-2, INFINITY};
+    // routing thresholds in steps of about 3x; timed first with a middle schedule, then the
+    // schedules with the best routing (13 timings instead of the 42 of the full product)
+    const double cand_thr[7] = {3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1, INFINITY};
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return YY_ERR_CUDA;
     float best = INFINITY;
-    int best_bn = bt->bn, best_grid = bt->grid;
+    int best_bn = 256, best_grid = std::min(kMaxGrid, 2 * sms);
     double best_thr = INFINITY;
-    for (double thr : cand_thr)
-        for (int bn : cand_bn)
-            for (int mul : cand_mul) {
-                const int grid = std::min(kMaxGrid, sms * mul);
-                route(thr);
-                bt->bn = bn;
-                bt->grid = grid;
-                bt->uploaded = false;
-                if (upload(bt) != YY_OK) continue;
-                if ((st = batch_predict(bt)) != YY_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
-                cudaEventRecord(e0, bt->stream);
-                for (int r = 0; r < reps; ++r) batch_predict(bt);
-                cudaEventRecord(e1, bt->stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return YY_ERR_CUDA; }
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; best_bn = bn; best_grid = grid; best_thr = thr; }
-            }
+    auto time_one = [&](double thr, int bn, int grid, float* out_ms) -> yy_status {
+        route(thr);
+        bt->bn = bn;
+        bt->grid = grid;
+        bt->uploaded = false;
+        *out_ms = INFINITY;
+        if (upload(bt) != YY_OK) return YY_OK;   // schedule does not fit: skip it
+        yy_status s2 = batch_predict(bt);
+        if (s2 != YY_OK) return s2;
+        cudaEventRecord(e0, bt->stream);
+        for (int r = 0; r < reps; ++r) batch_predict(bt);
+        cudaEventRecord(e1, bt->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return YY_ERR_CUDA;
+        cudaEventElapsedTime(out_ms, e0, e1);
+        return YY_OK;
+    };
+    for (double thr : cand_thr) {
+        float ms;
+        if ((st = time_one(thr, best_bn, best_grid, &ms)) != YY_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+        if (ms < best) { best = ms; best_thr = thr; }
+    }
+    const int mid_bn = best_bn, mid_grid = best_grid;
+    for (int bn : cand_bn)
+        for (int mul : cand_mul) {
+            const int grid = std::min(kMaxGrid, sms * mul);
+            if (bn == mid_bn && grid == mid_grid) continue;
+            float ms;
+            if ((st = time_one(best_thr, bn, grid, &ms)) != YY_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return st; }
+            if (ms < best) { best = ms; best_bn = bn; best_grid = grid; }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     bt->bn = best_bn;
