@@ -108,14 +108,38 @@ class ClockSampler:
 
 
 def _dist():
+    """(rank, world size, local rank, torch.distributed or None) from the torchrun
+    environment; NCCL when CUDA is present, else gloo (host-side tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return 0, 1, 0, None
+    import torch
     import torch.distributed as dist
     rank = int(os.environ["RANK"])
     local = int(os.environ.get("LOCAL_RANK", rank))
-    dist.init_process_group("nccl")
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return rank, ws, local, dist
+
+
+def shard_seed(base: int, rank: int) -> int:
+    """Seed of rank `rank`'s trajectory: every rank filters its own independent trajectory
+    (weak scaling; the path has no exchange step, so no collective in the data path)."""
+    return base + 1000 * rank
+
+
+def max_over_ranks(x: float, dist, device=None, dtype=None) -> float:
+    """The largest value of x over all ranks (timed regions end when the slowest rank does)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([x], device=device if device is not None else "cpu", dtype=dtype or torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ws: int, t_max_s: float) -> float:
+    """Units processed by all ranks per second of the slowest rank's time."""
+    return units_per_rank * ws / t_max_s
 
 
 def _make_filter(w, precision, seed, device, stream=None, screen_prefix=0, screen_type="bf16"):
@@ -161,7 +185,7 @@ def run_yy(args):
     prec = args.precision or w.precision
     if args.screen_type is None:
         args.screen_type = w.screen_type
-    seed = w.seed + 1000 * rank
+    seed = shard_seed(w.seed, rank)
     W, K = args.warmup, args.steps
     tr = simulate(w.model, w.r, W + K, w.dt, seed=seed)
     stream = torch.cuda.Stream(device)
@@ -190,11 +214,7 @@ def run_yy(args):
         dist.barrier()
     launches = flt.launches() - l0
     ms = e0.elapsed_time(e1)
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=device)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
+    t_max = max_over_ranks(ms, dist, device)
     h = hist.cpu().numpy()
     est = h[:, :w.r]
     rmse = _rmse(est, tr.x[W:W + K])
@@ -236,18 +256,14 @@ def run_yy(args):
         flt.restart(mode=0)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    e2e_val = n_e2e / e2e_s
-    if dist is not None:
-        t = torch.tensor([e2e_s], device=device, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = n_e2e * ws / float(t.item())
+    e2e_val = whole_job_rate(n_e2e, ws, max_over_ranks(e2e_s, dist, device))
     if rank != 0:
         if dist is not None:
             dist.barrier()
             dist.destroy_process_group()
         return
     peaks, src = _peaks()
-    steps_per_s = K * ws / (t_max / 1e3)
+    steps_per_s = whole_job_rate(K, ws, t_max / 1e3)
     if bound == "tensor":
         # the prediction launches are timed back to back on their own (about 0.1 s), so the
         # burst figure is the matching denominator
@@ -295,7 +311,7 @@ def run_yy(args):
         S = min(args.fp32_steps, K)
         out["fp32_comparator"] = _time_precision(w, "f32", S, W, tr, device)
         out["fp32_comparator"]["rmse_mixed_same_steps"] = _rmse(est[:S], tr.x[W:W + S])
-    if args.cpu_baseline:
+    if args.cpu_baseline and ws == 1:   # the oracle's baseline runs at N = 1 only
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
     print(json.dumps(out), flush=True)
     if dist is not None:
@@ -408,7 +424,7 @@ def run_batch(args):
     # untimed steps before the timed ones: at least 8, so that the autotuner routes on
     # posteriors that have spread out rather than on the prior
     S = max(W, 8)
-    members = batched_workloads(256, seed=4 + 1000 * rank, steps=S + K)
+    members = batched_workloads(256, seed=shard_seed(4, rank), steps=S + K)
     prec = args.precision or "bf16"
     cfgs = [binding.config_from_workload(m, precision=prec) for m in members]
     bt = binding.Batch(cfgs, device=device)
@@ -430,12 +446,15 @@ def run_batch(args):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = bt.launches()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         e0.record(bt.stream)
         bt.graph_launch()
         e1.record(bt.stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, device)
     launches = bt.launches() - l0
     # prediction alone
     torch.cuda.synchronize()
@@ -452,12 +471,15 @@ def run_batch(args):
         est = h[:, bt.hist_off[b]:bt.hist_off[b] + m.r]
         rm = _rmse(est, t.x[S:S + K])
         (rm_c if m.model == "cubic" else rm_l).append(rm)
+    if rank != 0:
+        return
     flops = float(sum(2.0 * m.n * m.n * m.r for m in members))
     peaks, src = _peaks()
     peak = peaks.get("bf16_tflops", 1900.0)
     achieved = flops / (pred_ms / 1e3) / 1e12
-    out = {"metric": "trajectory-steps/s, 256 ragged filters in one batch", "value": round(256 * K / (ms / 1e3), 2),
-           "unit": "trajectory-steps/s", "n_gpus": 1, "steps": K, "warmup": S, "ms_per_step": round(ms / K, 4),
+    out = {"metric": "trajectory-steps/s, 256 ragged filters in one batch",
+           "value": round(whole_job_rate(256 * K, ws_, ms / 1e3), 2),
+           "unit": "trajectory-steps/s", "n_gpus": ws_, "steps": K, "warmup": S, "ms_per_step": round(ms / K, 4),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
            "data": "synthetic (seeded Euler-Maruyama cubic sensor / linear-Gaussian, scrambled Sobol nodes)",
            "config": {"workload": "batched_256", "trajectories": 256, "r": "10..200", "n": "2048..32768 log-uniform",
@@ -480,6 +502,8 @@ def run_learned(args):
     import torch
     from paper_2509_16896_gb300 import learned_restart as LR
     rank, ws_, local, dist = _dist()
+    if rank != 0:
+        return   # a quality comparison on one GPU: the other ranks do no work
     device = f"cuda:{local}"
     torch.cuda.set_device(device)
     w = WORKLOADS["cubic_r50_n8192"]   # 500 steps, as the workload defines
