@@ -37,9 +37,11 @@
 // 16 % of the SMs idle).  An item over part of the sources stores its rows' online
 // (max, sum) states and a merge kernel combines them.  For a batch the TMA descriptors of
 // every filter live in global memory.  Warp roles:
-// warp 0 issues TMA loads, warp 1 allocates TMEM and issues tcgen05.mma (one thread),
-// warps 2-5 read the accumulators with tcgen05.ld (each warp its TMEM lane quarter, one
-// target row per thread) and screen.  Every wait is bounded (%globaltimer); on expiry the
+// warp 0 issues TMA loads (a tile's coordinate chunks as soon as ring slots free up, its
+// q values once the epilogue has released the tile's accumulator), warp 1 allocates TMEM
+// and issues tcgen05.mma (one thread), warps 2-9 read the accumulators with tcgen05.ld
+// (two warps per TMEM lane quarter, each on half of a tile's columns, one target row per
+// thread) and screen.  Every wait is bounded (%globaltimer); on expiry the
 // kernel records YY_ERR_TIMEOUT in the status word, drains its own copies and MMAs with a
 // bounded wait, frees TMEM and returns.
 #include <cuda.h>
@@ -60,7 +62,6 @@ constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each on half of a ti
 constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int A_BYTES = BM * BK * 2;
 constexpr unsigned long long kTimeoutNs = 4000000000ull;
-constexpr float kEpsGram = 0.015625f;   // 2^-6
 constexpr float kDeadQ = 3.0e38f;
 constexpr float kThetaMax = 1.0e30f;
 constexpr int kEscWords = 32;    // per epilogue warp and parity: marks of up to 1024 source tiles
@@ -224,27 +225,7 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "r"(taddr)
         : "memory");
 }
-__device__ __forceinline__ void tmem_ld64(uint32_t taddr, uint32_t (&v)[64]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-          "=r"(v[29]), "=r"(v[30]), "=r"(v[31]), "=r"(v[32]), "=r"(v[33]), "=r"(v[34]), "=r"(v[35]),
-          "=r"(v[36]), "=r"(v[37]), "=r"(v[38]), "=r"(v[39]), "=r"(v[40]), "=r"(v[41]), "=r"(v[42]),
-          "=r"(v[43]), "=r"(v[44]), "=r"(v[45]), "=r"(v[46]), "=r"(v[47]), "=r"(v[48]), "=r"(v[49]),
-          "=r"(v[50]), "=r"(v[51]), "=r"(v[52]), "=r"(v[53]), "=r"(v[54]), "=r"(v[55]), "=r"(v[56]),
-          "=r"(v[57]), "=r"(v[58]), "=r"(v[59]), "=r"(v[60]), "=r"(v[61]), "=r"(v[62]), "=r"(v[63])
-        : "r"(taddr)
-        : "memory");
-}
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
 // An upper bound of sqrt(x) for x >= 0: x times the reciprocal square root (hardware
 // approximation, relative error far below 1e-6), widened by 1e-6.  The screen only needs
 // its radii not to be underestimated.
@@ -305,6 +286,41 @@ __device__ __forceinline__ float drift_at(const Consts<float>& k, const Bufs<flo
         return fv;
     }
     return k.model_a * (b.dimc[d] + (u + b.dimc[rp + d]));
+}
+
+// Exact pair sums of target row tgt and source row src, warp-cooperative over the
+// coordinates: s1 = |u_t - u_s|^2 and s2 = (u_t - u_s) . f(x_t), each lane over the
+// coordinates lane, lane + 32, ... in increasing order (then summed across the warp by the
+// caller).  Four coordinates per lane are loaded before any is used, so that a pair costs
+// r / 128 memory round trips rather than r / 32.
+__device__ __forceinline__ void pair_sums_warp(const Consts<float>& k, const Bufs<float>& b, long long tgt,
+                                               long long src, int lane, float& s1, float& s2) {
+    const float* ut = b.u + (size_t)tgt * k.r_pad;
+    const float* us = b.u + (size_t)src * k.r_pad;
+    const float* ft = b.f + (size_t)tgt * k.r_pad;
+    const bool sf = b.store_f != 0;
+    s1 = 0.f;
+    s2 = 0.f;
+    for (int d0 = 0; d0 < k.r; d0 += 128) {
+        float a[4], c[4], g[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int d = d0 + 32 * m + lane;
+            const bool in = d < k.r;
+            a[m] = in ? ut[d] : 0.f;
+            c[m] = in ? us[d] : 0.f;
+            g[m] = (in && sf) ? ft[d] : 0.f;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const int d = d0 + 32 * m + lane;
+            if (d < k.r) {
+                const float dl = a[m] - c[m];
+                s1 = fmaf(dl, dl, s1);
+                s2 = fmaf(dl, sf ? g[m] : drift_at(k, b, tgt, a[m], d), s2);
+            }
+        }
+    }
 }
 
 // Per source chunk of 128: |u_s|^2 of live sources over all coordinates (tc_q) and over the
@@ -376,9 +392,12 @@ __global__ void __launch_bounds__(128) kb_tc_colprep(const Traj<float>* __restri
 // length is acceptable when extra <= 1/50 and clean when extra = 0.  After an unacceptable
 // prediction the length grows at once (by 2 when extra > 4) and the one just used is held
 // off for 1024 predictions; after four clean predictions in a row at one length, one chunk
-// shorter is tried unless it is held off (an acceptable but not clean length is kept, not
-// shortened: candidates grow steeply as the first pass shortens, and a shorter pass saves
-// little once the screening epilogue, not the Gram product, sets the pace).
+// shorter is tried unless it is held off.  A shorter length that is acceptable but not
+// clean is given up at once for the clean one it came from (and held off): every exact
+// pair stalls its epilogue warp for the memory latency of a whole row, so a few hundred
+// of them cost more than the chunk they save (measured at r = 1000, n = 65536, FP8: 3 of 8
+// stages with 395 exact pairs 1.09 ms, 4 stages and none 0.89 ms).  An acceptable length
+// that is not clean and was not reached by shortening is kept.
 __device__ void tc_adapt(const Consts<float>& k, DevStats* st) {
     const unsigned long long blk = atomicExch(&st->tc_blk, 0ull);
     const unsigned long long esc = atomicExch(&st->tc_esc, 0ull);
@@ -404,10 +423,17 @@ __device__ void tc_adapt(const Consts<float>& k, DevStats* st) {
         }
     } else {
         const bool clean = esc == 0 && cand == 0;
-        st->tc_streak = clean ? ((from == nk1) ? st->tc_streak + 1 : 1) : 0;
-        if (st->tc_streak >= kSettle && nk1 > 1 && st->tc_hold[nk1 - 1] == 0) {
-            next = nk1 - 1;
+        if (!clean && from > nk1) {
+            // a shortening step that is not clean: return to the clean length it came from
+            st->tc_hold[nk1] = kHold;
+            next = from;
             st->tc_streak = 0;
+        } else {
+            st->tc_streak = clean ? ((from == nk1) ? st->tc_streak + 1 : 1) : 0;
+            if (st->tc_streak >= kSettle && nk1 > 1 && st->tc_hold[nk1 - 1] == 0) {
+                next = nk1 - 1;
+                st->tc_streak = 0;
+            }
         }
     }
     st->tc_nk1 = next;
@@ -644,22 +670,14 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             int last_qphase[2] = {-1, -1};
             uint32_t it = 0, npre = 0, tp = 0;
             bool ok = true;
-            // one tile: its q values into the accumulator's buffer (once the epilogue has
-            // released that accumulator), then its coordinate chunks into the ring
+            // one tile: its coordinate chunks into the ring (gated by the ring's slots only,
+            // so they stream in while the epilogue still holds the accumulator), then its q
+            // values into the accumulator's buffer once the epilogue has released it
             auto load_tile = [&](const Consts<float>* kp, const Bufs<float>* bp, const CUtensorMap* ma,
                                  const CUtensorMap* mb, long long i0, int t, int nkb, bool prefix) -> bool {
                 const int acc = (int)(tp & 1u);
                 const uint32_t aph = (tp >> 1) & 1u;
                 ++tp;
-                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) return false;
-                const uint32_t qb = (uint32_t)(BN * sizeof(float));
-                const uint32_t ib = (uint32_t)((BN / 128) * 8 * sizeof(float));
-                mbar_arrive_expect_tx(&qfull[acc], (kp->tc_sym ? 2 * qb : qb) + ib);
-                bulk_load(qbuf + acc * BN, (prefix ? bp->tc_q1 : bp->tc_q) + (size_t)t * BN, qb, &qfull[acc]);
-                bulk_load(qinfo + acc * 16, bp->tc_cinfo + (size_t)t * (BN / 128) * 8, ib, &qfull[acc]);
-                if (kp->tc_sym)
-                    bulk_load(qtbuf + acc * BN, (prefix ? bp->tc_qt1 : bp->tc_qt) + (size_t)t * BN, qb, &qfull[acc]);
-                last_qphase[acc] = (int)aph;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = (int)(it % STAGES);
                     const uint32_t ph = (it / STAGES) & 1u;
@@ -671,6 +689,15 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     tma_load_2d(mb, &full[s], dA + A_BYTES, x, t * BN);
                     last_phase[s] = (int)ph;
                 }
+                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) return false;
+                const uint32_t qb = (uint32_t)(BN * sizeof(float));
+                const uint32_t ib = (uint32_t)((BN / 128) * 8 * sizeof(float));
+                mbar_arrive_expect_tx(&qfull[acc], (kp->tc_sym ? 2 * qb : qb) + ib);
+                bulk_load(qbuf + acc * BN, (prefix ? bp->tc_q1 : bp->tc_q) + (size_t)t * BN, qb, &qfull[acc]);
+                bulk_load(qinfo + acc * 16, bp->tc_cinfo + (size_t)t * (BN / 128) * 8, ib, &qfull[acc]);
+                if (kp->tc_sym)
+                    bulk_load(qtbuf + acc * BN, (prefix ? bp->tc_qt1 : bp->tc_qt) + (size_t)t * BN, qb, &qfull[acc]);
+                last_qphase[acc] = (int)aph;
                 return true;
             };
             for (int idx = it_begin; idx < it_end && ok; ++idx) {
@@ -836,14 +863,8 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     const int c = __shfl_sync(0xffffffffu, __ffs(cm) - 1, leader);
                     const long long src = sb + c;
                     const long long tgt = i0 + q * 32 + leader;
-                    const float* ut = b.u + (size_t)tgt * k.r_pad;
-                    const float* us = b.u + (size_t)src * k.r_pad;
-                    float s1 = 0.f, s2 = 0.f;
-                    for (int d = lane; d < k.r; d += 32) {
-                        const float dl = ut[d] - us[d];
-                        s1 = fmaf(dl, dl, s1);
-                        s2 = fmaf(dl, drift_at(k, b, tgt, ut[d], d), s2);
-                    }
+                    float s1, s2;
+                    pair_sums_warp(k, b, tgt, src, lane, s1, s2);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -873,14 +894,8 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     const int c = __shfl_sync(0xffffffffu, __ffs(cm) - 1, leader);
                     const long long tgt = sb + c;
                     const long long src = i0 + q * 32 + leader;
-                    const float* ut = b.u + (size_t)tgt * k.r_pad;
-                    const float* us = b.u + (size_t)src * k.r_pad;
-                    float s1 = 0.f, s2 = 0.f;
-                    for (int d = lane; d < k.r; d += 32) {
-                        const float dl = ut[d] - us[d];
-                        s1 = fmaf(dl, dl, s1);
-                        s2 = fmaf(dl, drift_at(k, b, tgt, ut[d], d), s2);
-                    }
+                    float s1, s2;
+                    pair_sums_warp(k, b, tgt, src, lane, s1, s2);
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
