@@ -226,6 +226,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "memory");
 }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+// a * b + c on two float lanes at once (one packed FMA, each lane rounded as fmaf)
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    uint64_t av, bv, cv, dv;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(av) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(bv) : "f"(b.x), "f"(b.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(cv) : "f"(c.x), "f"(c.y));
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(dv) : "l"(av), "l"(bv), "l"(cv));
+    float2 d;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(dv));
+    return d;
+}
+// the smallest of three floats (exact)
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
 // An upper bound of sqrt(x) for x >= 0: x times the reciprocal square root (hardware
 // approximation, relative error far below 1e-6), widened by 1e-6.  The screen only needs
 // its radii not to be underestimated.
@@ -1007,17 +1024,21 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     tmem_ld32(tbase + (uint32_t)(ch * 32), v);
                     tmem_ld_wait();
                     const float4* q4 = reinterpret_cast<const float4*>(qw + ch * 32);
-                    // four independent minimum chains (no 32-long dependency)
-                    float m0c = INFINITY, m1c = INFINITY, m2c = INFINITY, m3c = INFINITY;
+                    // q_s - 2 G two columns per packed FMA, folded into two independent
+                    // minimum chains by three-input minima
+                    const float2 g2v = make_float2(k.tc_g2, k.tc_g2);
+                    float m0c = INFINITY, m1c = INFINITY;
 #pragma unroll
                     for (int c4 = 0; c4 < 8; ++c4) {
                         const float4 qq = q4[c4];
-                        m0c = fminf(m0c, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 0]), qq.x));
-                        m1c = fminf(m1c, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 1]), qq.y));
-                        m2c = fminf(m2c, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 2]), qq.z));
-                        m3c = fminf(m3c, fmaf(k.tc_g2, __uint_as_float(v[4 * c4 + 3]), qq.w));
+                        const float2 d01 = ffma2(g2v, make_float2(__uint_as_float(v[4 * c4 + 0]), __uint_as_float(v[4 * c4 + 1])),
+                                                 make_float2(qq.x, qq.y));
+                        const float2 d23 = ffma2(g2v, make_float2(__uint_as_float(v[4 * c4 + 2]), __uint_as_float(v[4 * c4 + 3])),
+                                                 make_float2(qq.z, qq.w));
+                        m0c = fmin3(m0c, d01.x, d01.y);
+                        m1c = fmin3(m1c, d23.x, d23.y);
                     }
-                    const float mn = fminf(fminf(m0c, m1c), fminf(m2c, m3c));
+                    const float mn = fminf(m0c, m1c);
                     uint32_t m0 = 0, t0m = 0;
                     if (mn <= theta_any) {
 #pragma unroll
