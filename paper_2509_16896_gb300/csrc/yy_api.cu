@@ -140,6 +140,8 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
         b.tc_q = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_q1 = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_q1t = cv.take<float>((size_t)n_pad * sizeof(float));
+        b.tc_qmin = cv.take<float>((size_t)(n_pad / 32) * sizeof(float));
+        b.tc_qmin1 = cv.take<float>((size_t)(n_pad / 32) * sizeof(float));
         b.tc_qt = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_qt1 = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_tile_rmax = cv.take<float>((size_t)(n_pad / 128) * sizeof(float));

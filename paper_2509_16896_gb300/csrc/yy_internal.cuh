@@ -114,6 +114,8 @@ struct Bufs {
     float* tc_q;          // [n_pad] |u_s|^2 of live sources, 3e38 for dead ones
     float* tc_q1;         // [n_pad] the same over the first-pass coordinates
     float* tc_q1t;        // [n_pad] first-pass |u_s|^2 of every node (as a target)
+    float* tc_qmin;       // [n_pad / 32] smallest tc_q of each group of 32 sources
+    float* tc_qmin1;      // [n_pad / 32] smallest tc_q1 of each group of 32 sources
     float* tc_qt;         // [n_pad] column-direction screen value of every node as a target:
                           // |u_c|^2 - (rho_c^2 + err_c) (+inf: no target, -inf: no bound)
     float* tc_qt1;        // [n_pad] the same over the first-pass coordinates

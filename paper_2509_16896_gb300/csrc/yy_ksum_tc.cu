@@ -81,7 +81,7 @@ struct Cfg {
     // epilogue warp | marking bitmaps | row states exchanged between the two warps of a lane
     // quarter | barriers
     static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 4 * BN * 4 + 2 * 16 * 4 + 2 * EPI_WARPS * HALF * 4 +
-                                      EPI_WARPS * 2 * kEscWords * 4 + 128 * kMaxScales * 2 * 4 + 256;
+                                      EPI_WARPS * 2 * kEscWords * 4 + 128 * kMaxScales * 2 * 4 + 2 * (BN / 32) * 4 + 256;
     // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1),
     // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
@@ -237,6 +237,12 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(dv));
     return d;
 }
+// the largest of three floats (exact)
+__device__ __forceinline__ float fmax3(float a, float b, float c) {
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
 // the smallest of three floats (exact)
 __device__ __forceinline__ float fmin3(float a, float b, float c) {
     float d;
@@ -360,6 +366,18 @@ __device__ __forceinline__ void colprep_body(const Consts<float>& k, const Bufs<
     b.tc_q[s] = live ? nu : tc::kDeadQ;
     b.tc_q1[s] = live ? nu1 : tc::kDeadQ;
     b.tc_q1t[s] = nu1;
+    {   // the smallest of each group of 32 (one warp), for the screen's first test
+        float qa = live ? nu : tc::kDeadQ, qb = live ? nu1 : tc::kDeadQ;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            qa = fminf(qa, __shfl_xor_sync(0xffffffffu, qa, o));
+            qb = fminf(qb, __shfl_xor_sync(0xffffffffu, qb, o));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            b.tc_qmin[s >> 5] = qa;
+            b.tc_qmin1[s >> 5] = qb;
+        }
+    }
 #pragma unroll
     for (int j = 0; j < kMaxScales; ++j) b.tc_xlse[(size_t)s * kMaxScales + j] = 0ull;   // empty (sum 0)
     float lm = live ? lw : -INFINITY, nm = live ? nu : 0.f, nm1 = live ? nu1 : 0.f;
@@ -598,7 +616,8 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     float* qbuf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
     float* qtbuf = qbuf + 2 * BN;
     float* qinfo = qtbuf + 2 * BN;                                       // [2][16]: the tile's chunk maxima
-    uint32_t* cms = reinterpret_cast<uint32_t*>(qinfo + 2 * 16);         // [EPI_WARPS][HALF / 32][32]
+    float* qmbuf = qinfo + 2 * 16;                                       // [2][BN / 32]: smallest q_s per 32
+    uint32_t* cms = reinterpret_cast<uint32_t*>(qmbuf + 2 * (BN / 32));  // [EPI_WARPS][HALF / 32][32]
     uint32_t* tcms = cms + EPI_WARPS * HALF;                             // [EPI_WARPS][HALF / 32][32]
     uint32_t* escm = tcms + EPI_WARPS * HALF;                            // [EPI_WARPS][2][kEscWords]
     float* xch = reinterpret_cast<float*>(escm + EPI_WARPS * 2 * kEscWords);   // [128 rows][kMaxScales][2]
@@ -709,9 +728,12 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) return false;
                 const uint32_t qb = (uint32_t)(BN * sizeof(float));
                 const uint32_t ib = (uint32_t)((BN / 128) * 8 * sizeof(float));
-                mbar_arrive_expect_tx(&qfull[acc], (kp->tc_sym ? 2 * qb : qb) + ib);
+                const uint32_t qmb = (uint32_t)((BN / 32) * sizeof(float));
+                mbar_arrive_expect_tx(&qfull[acc], (kp->tc_sym ? 2 * qb : qb) + ib + qmb);
                 bulk_load(qbuf + acc * BN, (prefix ? bp->tc_q1 : bp->tc_q) + (size_t)t * BN, qb, &qfull[acc]);
                 bulk_load(qinfo + acc * 16, bp->tc_cinfo + (size_t)t * (BN / 128) * 8, ib, &qfull[acc]);
+                bulk_load(qmbuf + acc * (BN / 32), (prefix ? bp->tc_qmin1 : bp->tc_qmin) + (size_t)t * (BN / 32), qmb,
+                          &qfull[acc]);
                 if (kp->tc_sym)
                     bulk_load(qtbuf + acc * BN, (prefix ? bp->tc_qt1 : bp->tc_qt) + (size_t)t * BN, qb, &qfull[acc]);
                 last_qphase[acc] = (int)aph;
@@ -1015,14 +1037,32 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     release(acc);
                     return true;
                 }
-                // long rows: 32 columns per TMEM load; the smallest q_s - 2 G of a lane's 32
-                // columns against theta_any decides whether candidate masks are needed at all
+                // long rows: 32 columns per TMEM load.  First test: with q_min the smallest
+                // q_s of the 32 columns and a_max the largest accumulator, q_min + g2 a_max
+                // (g2 < 0) is below every column's q_s - 2 G up to rounding, which the margin
+                // covers; only a lane that passes it (some lane of the warp) computes the
+                // smallest q_s - 2 G, and only when that passes theta_any the candidate masks
                 int cnt = 0;
+                const float* qmw = qmbuf + acc * (BN / 32) + h * (HALF / 32);
                 for (int ch = 0; ch < HALF / 32; ++ch) {
                     uint32_t v[32];
                     __syncwarp();
                     tmem_ld32(tbase + (uint32_t)(ch * 32), v);
                     tmem_ld_wait();
+                    float am0 = __uint_as_float(v[0]), am1 = __uint_as_float(v[1]);
+#pragma unroll
+                    for (int c = 2; c < 32; c += 4) {
+                        am0 = fmax3(am0, __uint_as_float(v[c]), __uint_as_float(v[c + 1]));
+                        if (c + 3 < 32) am1 = fmax3(am1, __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
+                    }
+                    const float qm = qmw[ch];
+                    const float g2a = k.tc_g2 * fmaxf(am0, am1);
+                    const float l0 = qm + g2a;
+                    if (!(l0 <= theta_any + 1e-6f * (fabsf(theta_any) + fabsf(qm) + fabsf(g2a)))) {
+                        cmw[ch * 32 + lane] = 0u;
+                        tcmw[ch * 32 + lane] = 0u;
+                        continue;
+                    }
                     const float4* q4 = reinterpret_cast<const float4*>(qw + ch * 32);
                     // q_s - 2 G two columns per packed FMA, folded into two independent
                     // minimum chains by three-input minima
