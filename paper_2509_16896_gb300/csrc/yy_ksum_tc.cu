@@ -878,9 +878,30 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 __syncwarp();
             }
             // one exact score of this lane's row against source src
+            // the largest log-weight and source norms over the item's source range (both
+            // halves of every tile), for an upper bound of every tile's threshold
+            float it_lmax = -INFINITY, it_numax = 0.f, it_numax1 = 0.f;
+            {
+                const int ca = (int)(((long long)t0 * BN) / 128), cb = (int)(((long long)t1 * BN) / 128);
+                for (int c = ca + lane; c < cb; c += 32) {
+                    it_lmax = fmaxf(it_lmax, b.tc_tile_lmax[c]);
+                    it_numax = fmaxf(it_numax, b.tc_tile_numax[c]);
+                    it_numax1 = fmaxf(it_numax1, b.tc_tile_numax1[c]);
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    it_lmax = fmaxf(it_lmax, __shfl_xor_sync(0xffffffffu, it_lmax, o));
+                    it_numax = fmaxf(it_numax, __shfl_xor_sync(0xffffffffu, it_numax, o));
+                    it_numax1 = fmaxf(it_numax1, __shfl_xor_sync(0xffffffffu, it_numax1, o));
+                }
+            }
+            const float it_rnumax = sqrt_up(it_numax), it_rnumax1 = sqrt_up(it_numax1);
+            float th_hi0 = 0.f, th_hi1 = 0.f;   // the bound over all / first-pass coordinates
+            int th_ok = 0;                      // bit fp: th_hi<fp> is current
             auto add_score = [&](float s1, float s2, long long src) {
                 const float ls = b.mask[src] ? -INFINITY : b.logw[src];
                 if (ls == -INFINITY) return;
+                th_ok = 0;   // the row maxima may grow
 #pragma unroll
                 for (int j = 0; j < N; ++j) {
                     const float sc = fmaf(-s1, k.inv2tau[j], s2) + (rowc[j] + ls);
@@ -980,23 +1001,24 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 const float* qtw = qtbuf + acc * BN + h * HALF;   // q_c - (rho_c^2 + err_c)
                 const float* ci = qinfo + acc * 16;
                 if (!wait_bounded(&qfull[acc], aph, abort_flag, status)) return false;
-                float lmax = ci[0];
-                float numax = first_pass ? ci[2] : ci[1];
-                float rnumax = first_pass ? ci[6] : ci[5];
-                if (BN == 256) {
-                    lmax = fmaxf(lmax, ci[8]);
-                    numax = fmaxf(numax, first_pass ? ci[10] : ci[9]);
-                    rnumax = fmaxf(rnumax, first_pass ? ci[14] : ci[13]);
-                }
                 const float rnu_s = first_pass ? rnu1_i : rnu_i;
-                float theta = screen_theta<N>(k, live, nu_s, rnu_s, Fi, mx, lmax, numax, rnumax, T);
+                // the tile's threshold, from its chunk maxima
+                auto tile_theta = [&]() -> float {
+                    float lmax = ci[0];
+                    float numax = first_pass ? ci[2] : ci[1];
+                    float rnumax = first_pass ? ci[6] : ci[5];
+                    if (BN == 256) {
+                        lmax = fmaxf(lmax, ci[8]);
+                        numax = fmaxf(numax, first_pass ? ci[10] : ci[9]);
+                        rnumax = fmaxf(rnumax, first_pass ? ci[14] : ci[13]);
+                    }
+                    return screen_theta<N>(k, live, nu_s, rnu_s, Fi, mx, lmax, numax, rnumax, T);
+                };
                 const float nu_src = (hm == 2 && src_live) ? nu_s : INFINITY;
                 // one test per lane and 32 columns covers both directions: a pair can be a
                 // candidate only if q_s - 2 G <= max(theta_i, Rmax - nu_i), Rmax the largest
                 // column bound of this warp's chunk
-                const float theta_any =
-                    (hm == 2 && src_live) ? fmaxf(theta, ci[(BN == 256 ? h : 0) * 8 + (first_pass ? 4 : 3)] - nu_src)
-                                          : theta;
+                const float rmax_c = ci[(BN == 256 ? h : 0) * 8 + (first_pass ? 4 : 3)];
                 if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) return false;
                 tc_fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + h * HALF);
@@ -1005,6 +1027,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     // row's candidates chunk by chunk, tightening the screen as the running
                     // maxima grow
                     const float* ut = b.u + (size_t)i * k.r_pad;
+                    float theta = tile_theta();
                     for (int ch = 0; ch < HALF / 32; ++ch) {
                         uint32_t v[32];
                         __syncwarp();
@@ -1032,7 +1055,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                             add_score(s1, s2, src);
                             ++ncand;
                         }
-                        theta = screen_theta<N>(k, live, nu_s, rnu_s, Fi, mx, lmax, numax, rnumax, T);
+                        theta = tile_theta();
                     }
                     release(acc);
                     return true;
@@ -1044,6 +1067,21 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 // smallest q_s - 2 G, and only when that passes theta_any the candidate masks
                 int cnt = 0;
                 const float* qmw = qmbuf + acc * (BN / 32) + h * (HALF / 32);
+                // the threshold from the item's maxima bounds every tile's from above
+                // (screen_theta grows with lmax, numax and rnumax; the margin covers
+                // rounding); the tile's own is computed only for a lane that passes with it
+                const int fp = first_pass ? 1 : 0;
+                if (!(th_ok & (1 << fp))) {
+                    const float th = screen_theta<N>(k, live, nu_s, rnu_s, Fi, mx, it_lmax, fp ? it_numax1 : it_numax,
+                                                     fp ? it_rnumax1 : it_rnumax, T);
+                    const float thm = (th == -INFINITY) ? th : th + 1e-6f * (fabsf(th) + nu_s + 1.f);
+                    if (fp) th_hi1 = thm; else th_hi0 = thm;
+                    th_ok |= 1 << fp;
+                }
+                const float th_hi = fp ? th_hi1 : th_hi0;
+                const float tany_hi = (hm == 2 && src_live) ? fmaxf(th_hi, rmax_c - nu_src) : th_hi;
+                float theta = 0.f, theta_any = 0.f;
+                bool have_theta = false;
                 for (int ch = 0; ch < HALF / 32; ++ch) {
                     uint32_t v[32];
                     __syncwarp();
@@ -1058,7 +1096,17 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     const float qm = qmw[ch];
                     const float g2a = k.tc_g2 * fmaxf(am0, am1);
                     const float l0 = qm + g2a;
-                    if (!(l0 <= theta_any + 1e-6f * (fabsf(theta_any) + fabsf(qm) + fabsf(g2a)))) {
+                    const float l0m = 1e-6f * (fabsf(qm) + fabsf(g2a));
+                    bool pass = l0 <= tany_hi + (l0m + 1e-6f * fabsf(tany_hi));
+                    if (pass) {
+                        if (!have_theta) {
+                            theta = tile_theta();
+                            theta_any = (hm == 2 && src_live) ? fmaxf(theta, rmax_c - nu_src) : theta;
+                            have_theta = true;
+                        }
+                        pass = l0 <= theta_any + (l0m + 1e-6f * fabsf(theta_any));
+                    }
+                    if (!pass) {
                         cmw[ch * 32 + lane] = 0u;
                         tcmw[ch * 32 + lane] = 0u;
                         continue;
