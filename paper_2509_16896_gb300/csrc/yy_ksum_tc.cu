@@ -1082,6 +1082,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 const float tany_hi = (hm == 2 && src_live) ? fmaxf(th_hi, rmax_c - nu_src) : th_hi;
                 float theta = 0.f, theta_any = 0.f;
                 bool have_theta = false;
+                uint32_t nzm = 0;
                 for (int ch = 0; ch < HALF / 32; ++ch) {
                     uint32_t v[32];
                     __syncwarp();
@@ -1106,11 +1107,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                         }
                         pass = l0 <= theta_any + (l0m + 1e-6f * fabsf(theta_any));
                     }
-                    if (!pass) {
-                        cmw[ch * 32 + lane] = 0u;
-                        tcmw[ch * 32 + lane] = 0u;
-                        continue;
-                    }
+                    if (!pass) continue;
                     const float4* q4 = reinterpret_cast<const float4*>(qw + ch * 32);
                     // q_s - 2 G two columns per packed FMA, folded into two independent
                     // minimum chains by three-input minima
@@ -1139,8 +1136,11 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                         if (i >= sb && i < sb + 32) m0 &= ~(1u << (int)(i - sb));
                         cnt += __popc(m0) + __popc(t0m);
                     }
-                    cmw[ch * 32 + lane] = m0;
-                    tcmw[ch * 32 + lane] = t0m;
+                    if (m0 | t0m) {   // masks are stored only where nonzero (bit ch of nzm)
+                        cmw[ch * 32 + lane] = m0;
+                        tcmw[ch * 32 + lane] = t0m;
+                        nzm |= 1u << ch;
+                    }
                 }
                 release(acc);
                 const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
@@ -1150,9 +1150,11 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     return true;
                 }
                 if (first_pass) exact1 += tot;
-                for (int ch = 0; ch < HALF / 32; ++ch) eval_warp(cmw[ch * 32 + lane], c0 + ch * 32);
+                for (int ch = 0; ch < HALF / 32; ++ch)
+                    eval_warp(((nzm >> ch) & 1u) ? cmw[ch * 32 + lane] : 0u, c0 + ch * 32);
                 if (hm == 2)
-                    for (int ch = 0; ch < HALF / 32; ++ch) eval_warp_t(tcmw[ch * 32 + lane], c0 + ch * 32);
+                    for (int ch = 0; ch < HALF / 32; ++ch)
+                        eval_warp_t(((nzm >> ch) & 1u) ? tcmw[ch * 32 + lane] : 0u, c0 + ch * 32);
                 return true;
             };
             for (int t = t0; t < t1 && ok; ++t) ok = tile(t, pre ? 1 : 0);
