@@ -898,6 +898,11 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             const float it_rnumax = sqrt_up(it_numax), it_rnumax1 = sqrt_up(it_numax1);
             float th_hi0 = 0.f, th_hi1 = 0.f;   // the bound over all / first-pass coordinates
             int th_ok = 0;                      // bit fp: th_hi<fp> is current
+            // the first test is kept while it settles most chunks of 32 columns (warp-uniform
+            // counts): where the screen's margin is thin (low r) it would mostly be work
+            // on top of the exact test
+            bool use_l0 = true;
+            int l0_chunks = 0, l0_pass = 0;
             auto add_score = [&](float s1, float s2, long long src) {
                 const float ls = b.mask[src] ? -INFINITY : b.logw[src];
                 if (ls == -INFINITY) return;
@@ -1071,7 +1076,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 // (screen_theta grows with lmax, numax and rnumax; the margin covers
                 // rounding); the tile's own is computed only for a lane that passes with it
                 const int fp = first_pass ? 1 : 0;
-                if (!(th_ok & (1 << fp))) {
+                if (use_l0 && !(th_ok & (1 << fp))) {
                     const float th = screen_theta<N>(k, live, nu_s, rnu_s, Fi, mx, it_lmax, fp ? it_numax1 : it_numax,
                                                      fp ? it_rnumax1 : it_rnumax, T);
                     const float thm = (th == -INFINITY) ? th : th + 1e-6f * (fabsf(th) + nu_s + 1.f);
@@ -1082,32 +1087,41 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 const float tany_hi = (hm == 2 && src_live) ? fmaxf(th_hi, rmax_c - nu_src) : th_hi;
                 float theta = 0.f, theta_any = 0.f;
                 bool have_theta = false;
+                if (!use_l0) {
+                    theta = tile_theta();
+                    theta_any = (hm == 2 && src_live) ? fmaxf(theta, rmax_c - nu_src) : theta;
+                    have_theta = true;
+                }
                 uint32_t nzm = 0;
                 for (int ch = 0; ch < HALF / 32; ++ch) {
                     uint32_t v[32];
                     __syncwarp();
                     tmem_ld32(tbase + (uint32_t)(ch * 32), v);
                     tmem_ld_wait();
-                    float am0 = __uint_as_float(v[0]), am1 = __uint_as_float(v[1]);
+                    if (use_l0) {
+                        float am0 = __uint_as_float(v[0]), am1 = __uint_as_float(v[1]);
 #pragma unroll
-                    for (int c = 2; c < 32; c += 4) {
-                        am0 = fmax3(am0, __uint_as_float(v[c]), __uint_as_float(v[c + 1]));
-                        if (c + 3 < 32) am1 = fmax3(am1, __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
-                    }
-                    const float qm = qmw[ch];
-                    const float g2a = k.tc_g2 * fmaxf(am0, am1);
-                    const float l0 = qm + g2a;
-                    const float l0m = 1e-6f * (fabsf(qm) + fabsf(g2a));
-                    bool pass = l0 <= tany_hi + (l0m + 1e-6f * fabsf(tany_hi));
-                    if (pass) {
-                        if (!have_theta) {
-                            theta = tile_theta();
-                            theta_any = (hm == 2 && src_live) ? fmaxf(theta, rmax_c - nu_src) : theta;
-                            have_theta = true;
+                        for (int c = 2; c < 32; c += 4) {
+                            am0 = fmax3(am0, __uint_as_float(v[c]), __uint_as_float(v[c + 1]));
+                            if (c + 3 < 32) am1 = fmax3(am1, __uint_as_float(v[c + 2]), __uint_as_float(v[c + 3]));
                         }
-                        pass = l0 <= theta_any + (l0m + 1e-6f * fabsf(theta_any));
+                        const float qm = qmw[ch];
+                        const float g2a = k.tc_g2 * fmaxf(am0, am1);
+                        const float l0 = qm + g2a;
+                        const float l0m = 1e-6f * (fabsf(qm) + fabsf(g2a));
+                        bool pass = l0 <= tany_hi + (l0m + 1e-6f * fabsf(tany_hi));
+                        ++l0_chunks;
+                        l0_pass += __any_sync(0xffffffffu, pass) ? 1 : 0;
+                        if (pass) {
+                            if (!have_theta) {
+                                theta = tile_theta();
+                                theta_any = (hm == 2 && src_live) ? fmaxf(theta, rmax_c - nu_src) : theta;
+                                have_theta = true;
+                            }
+                            pass = l0 <= theta_any + (l0m + 1e-6f * fabsf(theta_any));
+                        }
+                        if (!pass) continue;
                     }
-                    if (!pass) continue;
                     const float4* q4 = reinterpret_cast<const float4*>(qw + ch * 32);
                     // q_s - 2 G two columns per packed FMA, folded into two independent
                     // minimum chains by three-input minima
@@ -1143,6 +1157,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     }
                 }
                 release(acc);
+                if (use_l0 && l0_chunks >= 16 && 2 * l0_pass > l0_chunks) use_l0 = false;
                 const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
                 if (tot == 0) return true;
                 if (first_pass && (tot > kEscThresh || exact1 + tot > kExactBudget)) {

@@ -313,9 +313,11 @@ template cudaError_t launch_prep_restart_batch<double>(const Traj<double>*, int,
 
 // Blocks of the single-filter preparation pass (one warp per row, at most 8 per SM); also
 // the number of log-sum-exp partials it writes.
+// One resident wave of the float pass (3 blocks of 256 per SM at its register budget), so
+// that no SM runs a partial last wave.
 int prep_grid(long long n_pad) {
     long long blocks = (n_pad * 32 + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > 152 * 3) blocks = 152 * 3;
     return (int)blocks;
 }
 

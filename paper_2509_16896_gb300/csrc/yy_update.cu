@@ -518,7 +518,7 @@ __device__ __forceinline__ void record_body(const Consts<T>& k, const Bufs<T>& b
 template <typename T>
 __global__ void k_obs_prep(Consts<T> k, Bufs<T> b, const double* __restrict__ dy) { obs_prep_body<T>(k, b, dy); }
 template <typename T>
-__global__ void __launch_bounds__(256) k_loglik(Consts<T> k, Bufs<T> b) { loglik_body<T>(k, b, blockIdx.x, gridDim.x); }
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_loglik(Consts<T> k, Bufs<T> b) { loglik_body<T>(k, b, blockIdx.x, gridDim.x); }
 template <typename T>
 __global__ void __launch_bounds__(256) k_lse_partials(Consts<T> k, Bufs<T> b, int conditional) {
     lse_partials_body<T>(k, b, conditional, blockIdx.x, gridDim.x);
@@ -629,9 +629,10 @@ template <typename T>
 cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy,
                           int restart_interval, double ess_frac, cudaStream_t s, int* launches) {
     const int nb = kNumPartBlocks;
-    // the likelihood pass runs 4 blocks per SM (its partials are 2 doubles per block,
-    // well inside the moment partials' space)
-    const int nbl = 4 * kNumPartBlocks;
+    // the likelihood pass runs one wave of blocks: 4 per SM in float (64 registers a
+    // thread), 2 in double (its partials are 2 doubles per block, well inside the moment
+    // partials' space)
+    const int nbl = (sizeof(T) == 4 ? 2 : 1) * kNumPartBlocks;
     k_obs_prep<T><<<1, 256, 0, s>>>(k, b, dy);
     k_loglik<T><<<nbl, 256, 0, s>>>(k, b);
     k_lse_merge<<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0);
