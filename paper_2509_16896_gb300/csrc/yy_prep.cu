@@ -109,6 +109,8 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
         float2 uu[kRowQ];
 #pragma unroll
         for (int q = 0; q < kRowQ; ++q) uu[q] = (q < nq) ? ui2[lane + 32 * q] : make_float2(0.f, 0.f);
+        // the stored boundary mask, loaded with the row rather than after its reductions
+        const uint8_t mk = first ? (uint8_t)0 : b.mask[i];
         T div = T(0), nf = T(0), nu = T(0), lw = T(0);
         int on_face = 0;
         bool done = false;
@@ -205,7 +207,8 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
                 b.mask[i] = (uint8_t)on_face;
             }
             if (mode != kPrepOnly) {
-                const T out = b.mask[i] ? T(-INFINITY) : lw;
+                const bool masked = first ? (on_face != 0) : (mk != 0);
+                const T out = masked ? T(-INFINITY) : lw;
                 b.logw[i] = out;
                 // running (max, sum) of the written log-weights (lane 0 of every warp), in the
                 // working precision: float64 issue time per row is large on this part
