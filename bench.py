@@ -53,30 +53,48 @@ def _peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms.  Sampling is live before
+    the region starts (the first sample has arrived); the summary keeps the samples read
+    between mark_start() and one interval after mark_end() (all of them without marks)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_S = 0.1
 
     def __init__(self, gpu_index: int):
         self.idx = gpu_index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
+        self.t0 = self.t1 = None
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", str(int(self.INTERVAL_S * 1000))], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            deadline = time.monotonic() + 3.0
+            while not self.lines and self.proc.poll() is None and time.monotonic() < deadline:
+                time.sleep(0.01)
         except (OSError, ValueError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
+        if self.proc is not None:   # let the sample covering the region's last interval arrive
+            deadline = self.t1 + 2.5 * self.INTERVAL_S
+            while time.monotonic() < deadline and not any(t > self.t1 for t, _ in self.lines):
+                time.sleep(0.01)
 
     def __exit__(self, *a):
         if self.proc is not None:
@@ -86,10 +104,19 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
+    def _selected(self):
+        if self.t0 is None or self.t1 is None:
+            return [ln for _, ln in self.lines]
+        inside = [ln for t, ln in self.lines if self.t0 <= t <= self.t1 + self.INTERVAL_S]
+        if inside:
+            return inside
+        after = [ln for t, ln in self.lines if t >= self.t0]
+        return after[:1]
+
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in self._selected():
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -206,10 +233,12 @@ def run_yy(args):
     torch.cuda.synchronize()
     l0 = flt.launches()
     with ClockSampler(local) as clk:
+        clk.mark_start()
         e0.record(stream)
         flt.graph_launch()
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     if dist is not None:
         dist.barrier()
     launches = flt.launches() - l0
@@ -450,10 +479,12 @@ def run_batch(args):
         dist.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        clk.mark_start()
         e0.record(bt.stream)
         bt.graph_launch()
         e1.record(bt.stream)
         torch.cuda.synchronize()
+        clk.mark_end()
     ms = max_over_ranks(e0.elapsed_time(e1), dist, device)
     launches = bt.launches() - l0
     # prediction alone
