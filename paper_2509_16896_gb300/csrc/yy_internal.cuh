@@ -21,7 +21,6 @@ constexpr int kNumPartBlocks = 304;  // blocks of the reduction passes (2 per SM
 constexpr uint32_t kStatusNonFinite = 1u << 0;
 constexpr uint32_t kStatusDegenerate = 1u << 1;
 constexpr uint32_t kStatusTimeout = 1u << 2;
-constexpr uint32_t kStatusCandOverflow = 1u << 3;
 
 // Device-side per-filter scalars.
 struct DevStats {
@@ -41,7 +40,7 @@ struct DevStats {
     int scale_changed;   // 1 while a restart re-maps the nodes to new half-widths
     double c_ref;        // offset of the predicted log-weights (moves with the box volume)
     int part_count;      // entries of part_list
-    // BF16 screen: coordinate chunks (of 64) of the first screening pass and its controller
+    // tensor-core screen: stages (64 BF16 or 128 e4m3 coordinates) of the first pass and its controller
     int tc_nk1;          // 0 = not chosen yet
     int tc_streak;       // consecutive clean predictions at the current length
     int tc_from;         // first-pass length of the prediction before the last one
@@ -65,8 +64,8 @@ struct Consts {
     T tau[kMaxScales];
     T inv2tau[kMaxScales];   // 1 / (2 tau_j)
     T cj_off[kMaxScales];    // C_j - C_ref, C_j = -(r/2) log(2 pi tau_j) + log w_q
-    int tc_prefix;           // fixed first-pass chunks of the BF16 screen (0 = adaptive)
-    int tc_sym;              // BF16 screen over the upper block triangle, both directions per block
+    int tc_prefix;           // fixed first-pass stages of the tensor-core screen (0 = adaptive)
+    int tc_sym;              // screen over the upper block triangle, both directions per block
     int tc_fp8;              // screen operands FP8 e4m3 (else BF16)
     int tc_r8;               // FP8: coordinates per row of the e4m3 copy (multiple of 128)
     float tc_s;              // FP8: power-of-two scale of the coordinates in the e4m3 copy
@@ -109,7 +108,7 @@ struct Bufs {
     double* part;         // reduction partials
     int* part_list;       // [kNumPartBlocks] moment partials with weight, in block order
     DevStats* stats;
-    // BF16 path scratch
+    // tensor-core screen scratch (BF16 precision only)
     float* nu_chunk;      // [n_pad][r_pad / 64] |u_i|^2 per chunk of 64 coordinates (BF16 only)
     float* tc_q;          // [n_pad] |u_s|^2 of live sources, 3e38 for dead ones
     float* tc_q1;         // [n_pad] the same over the first-pass coordinates

@@ -1,5 +1,5 @@
-// Prediction step on the 5th-generation tensor cores (sm_103a): BF16 Gram screening on
-// tcgen05 + exact float32 evaluation of the surviving pairs.
+// Prediction step on the 5th-generation tensor cores (sm_103a): Gram screening on tcgen05
+// (BF16 or e4m3 operands) + exact float32 evaluation of the surviving pairs.
 //
 // The kernel sum of the prediction (Section 4, eq. general_kernel; Section 7) is, per
 // target i and scale j, a log-sum-exp over sources s of
@@ -8,12 +8,16 @@
 // nats, so it is computed as a flash-attention-style tile loop that never materialises the
 // n x n matrix and only spends exponentials where they matter:
 //
-//  1. G = U_t U_s^T on tcgen05 (BF16 operands staged by TMA in 128-byte-swizzled shared
-//     memory, FP32 accumulators in TMEM, double-buffered so the MMA of source tile t+1
-//     overlaps the screening of tile t);
+//  1. G = U_t U_s^T on tcgen05 (BF16 operands, or e4m3 copies of s u, staged by TMA in
+//     128-byte-swizzled shared memory, FP32 accumulators in TMEM, double-buffered so the
+//     MMA of source tile t+1 overlaps the screening of tile t), first over a prefix of the
+//     coordinates (a lower bound of the distance), the tiles that keep candidates again
+//     over all of them;
 //  2. |u_i - u_s|^2 ~= |u_i|^2 + |u_s|^2 - 2 G with a rigorous error bound
-//     (|dG| <= 2^-6 |u_i||u_s| for BF16 operands with FP32 accumulation, plus float32
-//     rounding);
+//     (|dG| <= 2^-6 |u_i||u_s| for BF16 operands with FP32 accumulation; for e4m3
+//     0.14 |u_i||u_s| + 1.07 delta sqrt(K) (|u_i| + |u_s|) + K delta^2, delta = 2^-10 / s;
+//     plus float32 rounding), tested per 32 columns first through the largest accumulator
+//     and the smallest |u_s|^2, then per column;
 //  3. by the triangle inequality |u_i - tau f_i - u_s| >= |u_i - u_s| - tau |f_i|, a pair
 //     whose distance exceeds rho_i = max_j [tau_j |f_i| + sqrt(2 tau_j max(0, lmax - M_j(i)
 //     + T))] has score_j < M_j(i) - T for every scale, where M_j(i) is the running maximum
