@@ -281,22 +281,42 @@ __device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& 
         }
         __syncthreads();
         if (cnt > 0 && Wc > 0.0) {
+            // every coordinate slot of this thread in one sweep over the rows (its loads in
+            // flight together); per slot the sums run over the rows in the same order
+            T S[kMomDims], muc[kMomDims], m2[kMomDims];
+#pragma unroll
+            for (int q = 0; q < kMomDims; ++q) { S[q] = T(0); m2[q] = T(0); }
+            for (int l = 0; l < cnt; ++l) {
+                const float* ur = b.u + (size_t)(c0 + s_rows[l]) * k.r_pad;
+                const T wl = s_w[l];
+#pragma unroll
+                for (int q = 0; q < kMomDims; ++q) {
+                    const int d = tid + 256 * q;
+                    if (d < k.r) S[q] += wl * (T)ur[d];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kMomDims; ++q) muc[q] = S[q] / (T)Wc;
+            for (int l = 0; l < cnt; ++l) {
+                const float* ur = b.u + (size_t)(c0 + s_rows[l]) * k.r_pad;
+                const T wl = s_w[l];
+#pragma unroll
+                for (int q = 0; q < kMomDims; ++q) {
+                    const int d = tid + 256 * q;
+                    if (d < k.r) {
+                        const T dv = (T)ur[d] - muc[q];
+                        m2[q] += wl * dv * dv;
+                    }
+                }
+            }
 #pragma unroll
             for (int q = 0; q < kMomDims; ++q) {
                 const int d = tid + 256 * q;
                 if (d < k.r) {
-                    T S = T(0);
-                    for (int l = 0; l < cnt; ++l) S += s_w[l] * (T)b.u[(size_t)(c0 + s_rows[l]) * k.r_pad + d];
-                    const T muc = S / (T)Wc;
-                    T m2 = T(0);
-                    for (int l = 0; l < cnt; ++l) {
-                        const T dv = (T)b.u[(size_t)(c0 + s_rows[l]) * k.r_pad + d] - muc;
-                        m2 += s_w[l] * dv * dv;
-                    }
-                    const double delta = (double)muc - mu[q];
+                    const double delta = (double)muc[q] - mu[q];
                     const double Wn = W + Wc;
                     mu[q] += delta * (Wc / Wn);
-                    M2[q] += (double)m2 + delta * delta * (W * Wc / Wn);
+                    M2[q] += (double)m2[q] + delta * delta * (W * Wc / Wn);
                 }
             }
             W += Wc;
