@@ -314,6 +314,10 @@ YY_EXPORT yy_status yy_batch_get_schedule(const yy_batch* bt, int32_t* h_bn, int
 YY_EXPORT yy_status yy_batch_autotune(yy_batch* bt, const char* cache_path, int32_t reps, int32_t* h_bn,
                                       int32_t* h_grid);
 YY_EXPORT yy_status yy_batch_get_routing(const yy_batch* bt, int32_t* h_path);
+/* Fixes the per-filter prediction path (host int32 [B]: 0 = tensor-core screen, allowed only
+ * for BF16 precision; 1 = FP32 form), replacing the autotuner's routing.  Results agree
+ * within float32 rounding either way. */
+YY_EXPORT yy_status yy_batch_set_routing(yy_batch* bt, const int32_t* h_path);
 
 /* Kernel launches issued so far, and per replay of the captured graph. */
 YY_EXPORT int64_t yy_batch_launch_count(const yy_batch* bt);
@@ -357,14 +361,26 @@ YY_EXPORT yy_status yy_get_clamps(yy_filter* f, int64_t* h_clamps);
  *   d_logw  device float [n], log-weights with any common offset (-inf allowed)
  *   d_out   device double [2r + 3]: mean[r], var[r], ESS, LSE(logw), sum of weights
  *   stream  cudaStream_t or NULL
+ * If every log-weight is -inf the output reads LSE = -inf with weight sum, ESS, mean and
+ * variance 0 (the call is asynchronous, so this is reported in the output, not as a code).
  * Limits: 1 <= r <= YY_NOALLOC_MAX_DIM and n >= 1; anything else returns YY_ERR_ARG
- * before any launch.  Scratch lives in a fixed device array of about 2 MB inside the
+ * before any launch.  YY_ERR_CUDA reports a failure of this call's own launches only.  Scratch lives in a fixed device array of about 2 MB inside the
  * library, held by every GPU that loads it until the process exits.  The first call on a
  * device looks up that array's device address; make it before any stream capture.  All
  * calls share the array: calls that overlap on the GPU race and must be serialised by
  * the caller.  Asynchronous; no device memory is allocated or freed. */
 YY_EXPORT yy_status yy_weighted_moments_static(const float* d_u, int64_t n, int32_t r, int64_t ld,
                                                const float* d_logw, double* d_out, void* stream);
+
+/* Limit of every bounded device-side wait in this handle's prediction kernel (the
+ * tensor-core screen's pipeline waits), in seconds, 0 < seconds <= 3600; default 4 s.  When
+ * a wait runs out the kernel stops, records YY_ERR_TIMEOUT in the sticky status word (read
+ * by yy_estimate), lets its own copies and tensor-core work finish and returns; the
+ * predicted weights of that call are not valid and the handle should be recreated.  Takes
+ * effect for launches issued (or graphs captured) after the call.  A library service with
+ * no counterpart in the paper: it lets a caller bound how long a stalled launch can hold
+ * the GPU, and lets a test make a wait expire. */
+YY_EXPORT yy_status yy_set_wait_limit(yy_filter* f, double seconds);
 
 /* Kernel launches issued by this handle so far (for launch accounting). */
 YY_EXPORT int64_t yy_launch_count(const yy_filter* f);

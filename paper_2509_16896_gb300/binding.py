@@ -43,7 +43,8 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_batch_get_routing", "yy_get_box", "yy_set_restart_mlp", "yy_mlp_param_count",
            "yy_mlp_workspace_bytes", "yy_mlp_create", "yy_mlp_destroy", "yy_mlp_set_params",
            "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train",
-           "yy_mlp_set_input_norm", "yy_get_screen")
+           "yy_mlp_set_input_norm", "yy_get_screen", "yy_batch_set_routing",
+           "yy_set_wait_limit")
 
 
 class YYError(RuntimeError):
@@ -103,6 +104,8 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_batch_graph_kernel_count": (I64, [P]),
         "yy_get_counters": (I32, [P, P, P]),
         "yy_batch_get_routing": (I32, [P, P]),
+        "yy_batch_set_routing": (I32, [P, P]),
+        "yy_set_wait_limit": (I32, [P, D]),
         "yy_get_box": (I32, [P, P, P]),
         "yy_set_restart_mlp": (I32, [P, P]),
         "yy_mlp_param_count": (I64, [I32, I32]),
@@ -298,6 +301,9 @@ class Filter:
 
     def launches(self) -> int:
         return int(self.lib.yy_launch_count(self.h))
+
+    def set_wait_limit(self, seconds: float) -> None:
+        _check("yy_set_wait_limit", self.lib.yy_set_wait_limit(self.h, float(seconds)))
 
     def screen(self):
         """(first-pass chunks of the last prediction, of the next one, tiles, tiles
@@ -556,6 +562,12 @@ class Batch:
         _check("yy_batch_get_routing", self.lib.yy_batch_get_routing(self.h, _ptr(out)))
         return out
 
+    def set_routing(self, path) -> None:
+        """Per-filter prediction path: 0 = tensor-core screen, 1 = FP32 form."""
+        arr = np.ascontiguousarray(path, dtype=np.int32)
+        assert arr.shape == (self.B,)
+        _check("yy_batch_set_routing", self.lib.yy_batch_set_routing(self.h, _ptr(arr)))
+
     def launches(self) -> int:
         return int(self.lib.yy_batch_launch_count(self.h))
 
@@ -566,15 +578,18 @@ class Batch:
 def weighted_moments_static(u_dev, logw_dev, out_dev, stream=None) -> None:
     """Calls yy_weighted_moments_static, which allocates no device memory: u_dev is a
     float32 [n][ld] device tensor (row stride ld >= r = u_dev.shape[1] when 2-D), logw_dev
-    float32 [n], out_dev float64 [2r + 3] (mean, var, ESS, LSE, weight sum)."""
+    float32 [n], out_dev float64 [2r + 3] (mean, var, ESS, LSE, weight sum).  All three
+    tensors must be on one device; the call runs with that device current."""
     import torch
     L = load()
     n, r = u_dev.shape
     ld = u_dev.stride(0)
     assert u_dev.dtype == torch.float32 and u_dev.stride(1) == 1
-    assert logw_dev.dtype == torch.float32 and logw_dev.numel() == n
-    assert out_dev.dtype == torch.float64 and out_dev.numel() >= 2 * r + 3
-    s = stream if stream is not None else torch.cuda.current_stream(u_dev.device)
-    _check("yy_weighted_moments_static", L.yy_weighted_moments_static(
-        ctypes.c_void_p(u_dev.data_ptr()), n, r, ld, ctypes.c_void_p(logw_dev.data_ptr()),
-        ctypes.c_void_p(out_dev.data_ptr()), ctypes.c_void_p(s.cuda_stream)))
+    assert logw_dev.dtype == torch.float32 and logw_dev.numel() == n and logw_dev.is_contiguous()
+    assert out_dev.dtype == torch.float64 and out_dev.numel() >= 2 * r + 3 and out_dev.is_contiguous()
+    assert u_dev.is_cuda and logw_dev.device == u_dev.device and out_dev.device == u_dev.device
+    with torch.cuda.device(u_dev.device):
+        s = stream if stream is not None else torch.cuda.current_stream(u_dev.device)
+        _check("yy_weighted_moments_static", L.yy_weighted_moments_static(
+            ctypes.c_void_p(u_dev.data_ptr()), n, r, ld, ctypes.c_void_p(logw_dev.data_ptr()),
+            ctypes.c_void_p(out_dev.data_ptr()), ctypes.c_void_p(s.cuda_stream)))

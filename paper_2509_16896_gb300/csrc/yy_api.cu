@@ -17,6 +17,7 @@ namespace {
 long long round_up(long long v, long long a) { return (v + a - 1) / a * a; }
 
 constexpr int kMaxTcGrid = 1024;
+constexpr unsigned long long kDefaultWaitNs = 4000000000ull;   // 4 s
 
 // Work list of the single-filter BF16 prediction: one persistent CTA per SM.  Symmetric
 // screen (the usual case): target tile a (128 rows) covers the source tiles from the one
@@ -256,6 +257,7 @@ void fill_consts(yy_filter* f, Consts<T>* k, const double* halfwidth) {
     }
     k->c_ref = cref;
     f->c_ref = cref;
+    k->wait_ns = f->wait_ns;
 }
 
 yy_status cuda_status(cudaError_t e) { return e == cudaSuccess ? YY_OK : YY_ERR_CUDA; }
@@ -342,6 +344,8 @@ yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t bytes, void*
     f->ws = (char*)d_workspace;
     f->ws_bytes = bytes;
     f->fp64 = (cfg->precision == YY_PREC_FP64);
+    f->wait_ns = kDefaultWaitNs;
+    f->kf.wait_ns = f->kd.wait_ns = kDefaultWaitNs;
     multiscale_coefficients(cfg->n_scales, f->coef);
     if (f->fp64) carve<double>(cfg, f->ws, &f->bd);
     else carve<float>(cfg, f->ws, &f->bf);
@@ -627,6 +631,16 @@ yy_status yy_get_clamps(yy_filter* f, int64_t* h_clamps) {
 }
 
 int64_t yy_launch_count(const yy_filter* f) { return f ? f->launches : 0; }
+
+yy_status yy_set_wait_limit(yy_filter* f, double seconds) {
+    if (!f || !(seconds > 0.0) || seconds > 3600.0) return YY_ERR_ARG;
+    unsigned long long ns = (unsigned long long)(seconds * 1e9);
+    if (ns < 1) ns = 1;
+    f->wait_ns = ns;
+    f->kf.wait_ns = ns;
+    f->kd.wait_ns = ns;
+    return YY_OK;
+}
 
 yy_status yy_get_counters(yy_filter* f, int64_t* h_clamps, int64_t* h_exact_pairs) {
     if (!f) return YY_ERR_ARG;

@@ -341,7 +341,11 @@ yy_status yy_batch_predict(yy_batch* bt) {
         const yy_status st = upload(bt);
         if (st != YY_OK) return st;
     }
-    return batch_predict(bt);
+    const yy_status st = batch_predict(bt);
+    // the borrowed handles now hold a prediction (yy_get_log_weights reads it)
+    if (st == YY_OK)
+        for (yy_filter* f : bt->filters) f->predicted = true;
+    return st;
 }
 
 yy_status yy_batch_run_steps(yy_batch* bt, const double* d_dy_all, int64_t K, double* d_hist) {
@@ -350,7 +354,19 @@ yy_status yy_batch_run_steps(yy_batch* bt, const double* d_dy_all, int64_t K, do
         const yy_status st = upload(bt);
         if (st != YY_OK) return st;
     }
+    for (yy_filter* f : bt->filters) f->predicted = false;
     return batch_steps(bt, d_dy_all, K, d_hist);
+}
+
+yy_status yy_batch_set_routing(yy_batch* bt, const int32_t* h_path) {
+    if (!bt || !h_path) return YY_ERR_ARG;
+    for (int b = 0; b < bt->B; ++b) {
+        if (h_path[b] != 0 && h_path[b] != 1) return YY_ERR_ARG;
+        if (h_path[b] == 0 && bt->precision != YY_PREC_BF16) return YY_ERR_ARG;
+    }
+    for (int b = 0; b < bt->B; ++b) bt->path[b] = h_path[b];
+    bt->uploaded = false;
+    return YY_OK;
 }
 
 yy_status yy_batch_graph_capture(yy_batch* bt, const double* d_dy_all, int64_t K, double* d_hist) {

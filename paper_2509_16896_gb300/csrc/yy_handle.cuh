@@ -25,4 +25,5 @@ struct yy_filter {
     cudaGraphExec_t gexec;
     long long graph_kernels;
     struct yy_mlp* mlp;   // restart-proposal network for YY_RESTART_LEARNED (not owned)
+    unsigned long long wait_ns;   // limit of bounded device waits (default 4 s)
 };

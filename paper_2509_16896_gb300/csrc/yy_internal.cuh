@@ -76,6 +76,7 @@ struct Consts {
     T logabs_c[kMaxScales + 1];
     T sign_c[kMaxScales + 1];  // 0 for a zero coefficient
     double c_ref;
+    unsigned long long wait_ns;  // limit of the prediction kernel's bounded waits (yy_set_wait_limit)
 };
 
 // Pointers into the caller's workspace.

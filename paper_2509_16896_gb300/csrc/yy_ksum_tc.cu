@@ -65,7 +65,7 @@ constexpr int UK = 16;       // K of one tcgen05.mma kind::f16
 constexpr int EPI_WARPS = 8;  // two per TMEM lane quarter, each on half of a tile's columns
 constexpr int NUM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr int A_BYTES = BM * BK * 2;
-constexpr unsigned long long kTimeoutNs = 4000000000ull;
+constexpr unsigned long long kTimeoutNs = 4000000000ull;   // default wait limit; drain limit
 constexpr float kDeadQ = 3.0e38f;
 constexpr float kThetaMax = 1.0e30f;
 constexpr int kEscWords = 32;    // per epilogue warp and parity: marks of up to 1024 source tiles
@@ -133,13 +133,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 // Bounded wait: false when the limit expired (status recorded) or another role aborted.
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
-                                             unsigned int* status) {
+                                             unsigned int* status, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (true) {
         if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (globaltimer() - t0 > tc::kTimeoutNs) {
+        if (globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
             atomicOr(status, kStatusTimeout);
             return false;
@@ -586,6 +586,7 @@ struct TcWork {
     const int4* items;
     const int* cta_start;
     int nb;
+    unsigned long long wait_ns;   // limit of every bounded wait (the drain after an abort keeps 4 s)
 };
 
 constexpr int kMaxSplit = 8;
@@ -721,7 +722,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = (int)(it % STAGES);
                     const uint32_t ph = (it / STAGES) & 1u;
-                    if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, status)) return false;
+                    if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, status, w.wait_ns)) return false;
                     mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                     uint8_t* dA = smem + s * STAGE_BYTES;
                     const int x = kb * (kp->tc_fp8 ? 128 : BK);   // 128 bytes of coordinates per stage
@@ -729,7 +730,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     tma_load_2d(mb, &full[s], dA + A_BYTES, x, t * BN);
                     last_phase[s] = (int)ph;
                 }
-                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) return false;
+                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status, w.wait_ns)) return false;
                 const uint32_t qb = (uint32_t)(BN * sizeof(float));
                 const uint32_t ib = (uint32_t)((BN / 128) * 8 * sizeof(float));
                 const uint32_t qmb = (uint32_t)((BN / 32) * sizeof(float));
@@ -752,7 +753,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 for (int t = t0; t < t1 && ok; ++t) ok = load_tile(kp, bp, ma, mb, i0, t, nk1, pre);
                 if (ok && pre) {
                     const uint32_t par = npre++ & 1u;
-                    if (!wait_bounded(escb, par, abort_flag, status)) { ok = false; break; }
+                    if (!wait_bounded(escb, par, abort_flag, status, w.wait_ns)) { ok = false; break; }
                     for (int t = t0; t < t1 && ok; ++t)
                         if (esc_any(par, t - t0)) ok = load_tile(kp, bp, ma, mb, i0, t, nk, false);
                 }
@@ -772,13 +773,13 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             auto mma_tile = [&](int nkb, bool fp8) -> bool {
                 const int acc = (int)(tcount & 1u);
                 const uint32_t aph = (tcount >> 1) & 1u;
-                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status)) return false;
+                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status, w.wait_ns)) return false;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = (int)(it % STAGES);
                     const uint32_t ph = (it / STAGES) & 1u;
-                    if (!wait_bounded(&full[s], ph, abort_flag, status)) return false;
+                    if (!wait_bounded(&full[s], ph, abort_flag, status, w.wait_ns)) return false;
                     tc_fence_after();
                     const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
                     const uint32_t b0a = a0 + A_BYTES;
@@ -809,7 +810,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 unsigned long long nesc = 0;
                 if (ok && nk1 < nk) {
                     const uint32_t par = npre++ & 1u;
-                    if (!wait_bounded(escb, par, abort_flag, status)) { ok = false; break; }
+                    if (!wait_bounded(escb, par, abort_flag, status, w.wait_ns)) { ok = false; break; }
                     for (int t = t0; t < t1 && ok; ++t)
                         if (esc_any(par, t - t0)) { ok = mma_tile(nk, kp->tc_fp8 != 0); ++nesc; }
                 }
@@ -997,7 +998,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 const long long cchunk = c0 / 128;
                 const int hm = !k.tc_sym ? 1 : (cchunk < a_chunk ? 0 : (cchunk == a_chunk ? 1 : 2));
                 if (mode == 3 || hm == 0) {
-                    if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) return false;
+                    if (!wait_bounded(&tfull[acc], aph, abort_flag, status, w.wait_ns)) return false;
                     tc_fence_after();
                     release(acc);
                     return true;
@@ -1009,7 +1010,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 const float* qw = qbuf + acc * BN + h * HALF;
                 const float* qtw = qtbuf + acc * BN + h * HALF;   // q_c - (rho_c^2 + err_c)
                 const float* ci = qinfo + acc * 16;
-                if (!wait_bounded(&qfull[acc], aph, abort_flag, status)) return false;
+                if (!wait_bounded(&qfull[acc], aph, abort_flag, status, w.wait_ns)) return false;
                 const float rnu_s = first_pass ? rnu1_i : rnu_i;
                 // the tile's threshold, from its chunk maxima
                 auto tile_theta = [&]() -> float {
@@ -1028,7 +1029,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 // candidate only if q_s - 2 G <= max(theta_i, Rmax - nu_i), Rmax the largest
                 // column bound of this warp's chunk
                 const float rmax_c = ci[(BN == 256 ? h : 0) * 8 + (first_pass ? 4 : 3)];
-                if (!wait_bounded(&tfull[acc], aph, abort_flag, status)) return false;
+                if (!wait_bounded(&tfull[acc], aph, abort_flag, status, w.wait_ns)) return false;
                 tc_fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + h * HALF);
                 if (k.r <= 64) {
@@ -1180,7 +1181,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             if (ok && pre) {
                 __syncwarp();
                 if (lane == 0) mbar_arrive(escb);
-                if (!wait_bounded(escb, par, abort_flag, status)) ok = false;
+                if (!wait_bounded(escb, par, abort_flag, status, w.wait_ns)) ok = false;
                 for (int t = t0; t < t1 && ok; ++t)
                     if (esc_any(par, t - t0)) ok = tile(t, esc_bit(ew, par, t - t0) ? 2 : 3);
             }
@@ -1188,7 +1189,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             // shared memory (bounded hand-shakes, so an aborted partner cannot block)
             const uint32_t xph = nitem & 1u;
             if (ok && h == 1) {
-                if (nitem > 0 && !wait_bounded(&xfree[q], xph ^ 1u, abort_flag, status)) ok = false;
+                if (nitem > 0 && !wait_bounded(&xfree[q], xph ^ 1u, abort_flag, status, w.wait_ns)) ok = false;
                 if (ok) {
 #pragma unroll
                     for (int j = 0; j < N; ++j) { xrow[2 * j] = mx[j]; xrow[2 * j + 1] = sm[j]; }
@@ -1197,7 +1198,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 }
             }
             if (ok && h == 0) {
-                if (!wait_bounded(&xfull[q], xph, abort_flag, status)) ok = false;
+                if (!wait_bounded(&xfull[q], xph, abort_flag, status, w.wait_ns)) ok = false;
                 if (ok) {
 #pragma unroll
                     for (int j = 0; j < N; ++j) {
@@ -1409,7 +1410,7 @@ cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStr
         k_tc_colprep2<<<(unsigned)(k.n_pad / 128), 128, 0, s>>>(k, b);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    const TcWork w{nullptr, nullptr, b.tc_items, b.tc_cta_start, 1};
+    const TcWork w{nullptr, nullptr, b.tc_items, b.tc_cta_start, 1, k.wait_ns};
     e = launch_bn<256>(k.N, (unsigned)b.tc_grid, ma, mb, k, b, w, s);
     if (e != cudaSuccess) return e;
     int l = k.tc_sym ? 3 : 2;
@@ -1437,7 +1438,7 @@ cudaError_t launch_ksum_tc_batch(const Traj<float>* d_traj, int B, int N, long l
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const CUtensorMap& map_any = *static_cast<const CUtensorMap*>(map_any_v);
-    const TcWork w{d_traj, static_cast<const CUtensorMap*>(d_maps), d_items, d_cta_start, B};
+    const TcWork w{d_traj, static_cast<const CUtensorMap*>(d_maps), d_items, d_cta_start, B, k_any.wait_ns};
     e = (bn == 128) ? launch_bn<128>(N, (unsigned)grid, map_any, map_any, k_any, b_any, w, s)
                     : launch_bn<256>(N, (unsigned)grid, map_any, map_any, k_any, b_any, w, s);
     if (e != cudaSuccess) return e;

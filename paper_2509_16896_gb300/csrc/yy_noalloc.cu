@@ -180,6 +180,15 @@ cudaError_t scratch_for_current_device(double** out) {
     return cudaSuccess;
 }
 
+// Launches one kernel through cudaLaunchKernel, whose return value is the error of that
+// launch alone (cudaGetLastError would also report, and clear, an error left on the thread
+// by unrelated earlier work).
+template <typename... Args>
+cudaError_t launch_own(void (*kern)(Args...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+    void* argv[] = {static_cast<void*>(&args)...};
+    return cudaLaunchKernel(reinterpret_cast<const void*>(kern), dim3(grid), dim3(block), argv, 0, s);
+}
+
 }  // namespace noalloc
 }  // namespace yy
 
@@ -190,9 +199,11 @@ extern "C" yy_status yy_weighted_moments_static(const float* d_u, int64_t n, int
     double* scr = nullptr;
     if (scratch_for_current_device(&scr) != cudaSuccess) return YY_ERR_CUDA;
     cudaStream_t s = (cudaStream_t)stream;
-    k_na_lse<<<kBlocks, 256, 0, s>>>(d_logw, n, scr);
-    k_na_lse_merge<<<1, 32, 0, s>>>(scr);
-    k_na_moments<<<kBlocks, 256, 0, s>>>(d_u, n, r, ld, d_logw, scr);
-    k_na_finalize<<<1, 256, 0, s>>>(r, scr, d_out);
-    return cudaGetLastError() == cudaSuccess ? YY_OK : YY_ERR_CUDA;
+    const long long nn = n, lld = ld;
+    const int rr = r;
+    cudaError_t e = launch_own(k_na_lse, kBlocks, 256, s, d_logw, nn, scr);
+    if (e == cudaSuccess) e = launch_own(k_na_lse_merge, 1, 32, s, scr);
+    if (e == cudaSuccess) e = launch_own(k_na_moments, kBlocks, 256, s, d_u, nn, rr, lld, d_logw, scr);
+    if (e == cudaSuccess) e = launch_own(k_na_finalize, 1, 256, s, rr, static_cast<const double*>(scr), d_out);
+    return e == cudaSuccess ? YY_OK : YY_ERR_CUDA;
 }
