@@ -36,9 +36,8 @@ from synth.configs import batched_workloads  # noqa: E402
 
 DEFAULT_WORKLOAD = "cubic_r1000_n65536"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the prediction
-# kernel, from one ncu capture of the workload (profiles/k_ksum_tc_cubic_r1000_n65536.md),
-# keyed by workload and screen operands.  An entry is removed whenever the kernel changes
-# after its capture.
+# kernel, from one ncu capture of the workload, keyed by workload and screen operands.  An
+# entry is removed whenever the kernel changes after its capture.
 NCU_TRAFFIC = {("cubic_r1000_n65536", "fp8"): 39.31392e6 + 0.466432e6}
 METRIC = "filter steps/s & kernel pair-evals/s at r=1000: mixed vs FP32, same RMSE"
 
@@ -177,25 +176,22 @@ def _make_filter(w, precision, seed, device, stream=None, screen_prefix=0, scree
     return flt
 
 
-def _algorithmic_flops(w, precision, screen=None, stage=64):
-    """Per prediction launch: BF16 path -> the Gram products the screen runs, i.e. per
-    screened block of 128 targets x 256 sources 2 x 128 x 256 x (64 k) flops for the first
-    pass over the first 64 k coordinates, plus 2 x 128 x 256 x r for every block screened
-    again over all coordinates (screen = (k, blocks, rescreened); with the symmetric screen
-    the blocks cover the upper block triangle, about half of the n^2 pairs);
-    FP32/FP64 path -> difference form, 3 flops per coordinate per pair."""
-    if precision == "bf16":
-        k, tiles, resc = screen
-        return 2.0 * 128 * 256 * (tiles * min(stage * k, w.r) + resc * w.r), "tensor"
-    return 3.0 * w.n * w.n * w.r, "alu"
+def _gram_flops(r, k, stage, tiles, resc, bn=256):
+    """Gram products the screen ran in one prediction: per screened block of 128 targets x
+    bn sources 2 x 128 x bn x (stage k) flops for the first pass over the first stage k
+    coordinates, plus 2 x 128 x bn x r for every block screened again over all of them."""
+    r_pad = (r + 63) // 64 * 64
+    return 2.0 * 128 * bn * (tiles * min(stage * k, r_pad) + resc * r_pad)
 
 
-def _config(w, prec):
+def _config(w, prec, screen_type):
     return {"workload": w.name, "r": w.r, "n": w.n, "n_scales": w.n_scales, "dt": w.dt,
             "R": w.R, "restart_interval": w.restart_interval, "ess_frac": w.ess_frac,
             "precision": prec, "trajectories_per_gpu": 1, "time_loop": "one CUDA graph of K steps",
-            "screen_operands": w.screen_type if prec == "bf16" else None,
-            "l2": f"inputs larger than L2 (u is {w.n * w.r * 4 / 1e6:.0f} MB)"}
+            "screen_operands": screen_type if prec == "bf16" else None,
+            "l2": f"inputs larger than L2 (u is {w.n * w.r * 4 / 1e6:.0f} MB)"
+                  if w.n * w.r * 4 > 129e6 else
+                  f"u ({w.n * w.r * 4 / 1e6:.1f} MB) fits in L2: steps follow each other, no flush"}
 
 
 def _rmse(est, truth):
@@ -203,30 +199,36 @@ def _rmse(est, truth):
     return float(np.sqrt(np.sum((est - truth) ** 2) / (K * r)))
 
 
-def run_yy(args):
+def _tensor_peak(screen_type):
+    peaks, src = _peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    note = f"{src}: bf16_tflops (burst; prediction launches timed alone)"
+    if screen_type == "fp8":   # FP8 dense rate = 2 x BF16 (4.5 / 2.25 PFLOP/s nominal)
+        peak, note = 2.0 * peak, f"{src}: 2 x bf16_tflops (fp8 nominal ratio; burst; prediction launches timed alone)"
+    return peak, note
+
+
+def _fma_peak():
+    peaks, _ = _peaks()
+    return 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+
+
+def measure_single(w, prec, screen_type, screen_prefix, K, W, device, seed, dist=None, local=0):
+    """One trajectory of workload w: K steps replayed as one CUDA graph after W untimed
+    steps (CUDA events on the filter's stream, clocks sampled in the region), then the
+    prediction launches timed alone for the dominant kernel's roofline.  Returns the
+    result dict and the objects the end-to-end leg reuses."""
     import torch
-    rank, ws, local, dist = _dist()
-    device = f"cuda:{local}"
-    torch.cuda.set_device(device)
-    w = WORKLOADS[args.workload]
-    prec = args.precision or w.precision
-    if args.screen_type is None:
-        args.screen_type = w.screen_type
-    seed = shard_seed(w.seed, rank)
-    W, K = args.warmup, args.steps
     tr = simulate(w.model, w.r, W + K, w.dt, seed=seed)
     stream = torch.cuda.Stream(device)
-    flt = _make_filter(w, prec, seed, device, stream, screen_prefix=args.screen_prefix,
-                       screen_type=args.screen_type)
+    flt = _make_filter(w, prec, seed, device, stream, screen_prefix=screen_prefix, screen_type=screen_type)
     dys = torch.tensor(tr.dy, dtype=torch.float64, device=device)
     hist = torch.zeros((K, 2 * w.r + 4), dtype=torch.float64, device=device)
     with torch.cuda.stream(stream):
         if W:
             flt.run_steps(dys[:W])
-        # the K timed steps as one CUDA graph (captured, not executed, here)
-        flt.graph_capture(dys[W:W + K], hist)
+        flt.graph_capture(dys[W:W + K], hist)   # captured, not executed, here
     torch.cuda.synchronize()
-    # ---- device-resident timed region --------------------------------------------
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     if dist is not None:
         dist.barrier()
@@ -248,8 +250,7 @@ def run_yy(args):
     est = h[:, :w.r]
     rmse = _rmse(est, tr.x[W:W + K])
     restarts = int(h[:, 2 * w.r + 3].sum())
-    mean, var, ess, z = flt.estimate()
-    # ---- dominant kernel: prediction launches timed alone on the filter's stream ----
+    # the dominant kernel: prediction launches from the state after the graph, timed alone
     n_pred = max(3, min(20, K))
     pe0, pe1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -259,101 +260,48 @@ def run_yy(args):
     pe1.record(stream)
     torch.cuda.synchronize()
     pred_ms = pe0.elapsed_time(pe1) / n_pred
+    _, exact = flt.counters()
+    _, mask = flt.get_nodes()
+    live = int(w.n - mask.sum())
     screen = None
+    stage = 128 if screen_type == "fp8" else 64
     if prec == "bf16":
         last, nxt, tiles, resc = flt.screen()
-        stage = 128 if args.screen_type == "fp8" else 64
-        screen = {"operands": args.screen_type, "first_pass_stages": last, "stage_coords": stage,
+        screen = {"operands": screen_type, "first_pass_stages": last, "stage_coords": stage,
                   "stages": ((w.r + 63) // 64 * 64 + stage - 1) // stage, "tiles": tiles,
-                  "rescreened": resc, "exact_pairs": flt.counters()[1]}
-    flops, bound = _algorithmic_flops(w, prec, None if screen is None else (last, tiles, resc),
-                                      128 if args.screen_type == "fp8" else 64)
+                  "rescreened": resc, "exact_pairs": exact}
+        flops = _gram_flops(w.r, last, stage, tiles, resc)
+        peak, note = _tensor_peak(screen_type)
+        roof = {"bound": "tensor", "achieved": round(flops / (pred_ms / 1e3) / 1e12, 3), "peak": peak,
+                "unit": "TFLOP/s", "kernel": "k_ksum_tc (screen Gram products of the prediction)",
+                "kernel_ms": round(pred_ms, 4), "algorithmic_flops_per_launch": flops, "peak_source": note}
+    else:
+        flops = 3.0 * w.n * w.n * w.r
+        roof = {"bound": "alu", "achieved": round(flops / (pred_ms / 1e3) / 1e12, 3), "peak": _fma_peak(),
+                "unit": "TFLOP/s", "kernel": "k_ksum_simt (difference form)", "kernel_ms": round(pred_ms, 4),
+                "algorithmic_flops_per_launch": flops,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"}
+    roof["frac"] = round(roof["achieved"] / roof["peak"], 4)
     with torch.cuda.stream(stream):
         flt.update(dys[0])   # leave the handle in a consistent state
-    # ---- end to end through the C ABI with host buffers ---------------------------
-    n_e2e = max(3, min(K, 50))
-    dy_host = torch.tensor(tr.dy, dtype=torch.float64).pin_memory()
-    dy_dev = torch.empty(w.r, dtype=torch.float64, device=device)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for k in range(n_e2e):
-        with torch.cuda.stream(stream):
-            dy_dev.copy_(dy_host[k % dy_host.shape[0]], non_blocking=True)
-        flt.predict()
-        flt.update(dy_dev)
-        flt.estimate()
-        flt.restart(mode=0)
-    torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_val = whole_job_rate(n_e2e, ws, max_over_ranks(e2e_s, dist, device))
-    if rank != 0:
-        if dist is not None:
-            dist.barrier()
-            dist.destroy_process_group()
-        return
-    peaks, src = _peaks()
-    steps_per_s = whole_job_rate(K, ws, t_max / 1e3)
-    if bound == "tensor":
-        # the prediction launches are timed back to back on their own (about 0.1 s), so the
-        # burst figure is the matching denominator
-        peak = peaks.get("bf16_tflops", 1900.0)
-        achieved = flops / (pred_ms / 1e3) / 1e12
-        peak_note = f"{src}: bf16_tflops (burst; prediction launches timed alone)"
-        if args.screen_type == "fp8":   # FP8 dense rate = 2 x BF16 (4.5 / 2.25 PFLOP/s nominal)
-            peak = 2.0 * peak
-            peak_note = f"{src}: 2 x bf16_tflops (fp8 nominal ratio; burst; prediction launches timed alone)"
-    else:
-        # float32 FMA pipes: 152 SMs x 128 lanes x 2 flops x max SM clock
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved = flops / (pred_ms / 1e3) / 1e12
-        peak_note = "derived: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock"
-    out = {
-        "metric": METRIC,
-        "value": round(steps_per_s, 4),
-        "unit": "filter steps/s",
-        "n_gpus": ws,
-        "steps": K,
-        "warmup": W,
-        "ms_per_step": round(t_max / K, 4),
-        "higher_is_better": True,
-        "scaling": "weak",
-        "vs_baseline": None,
-        # screen operands + float32 exact evaluation, log-sum-exp and update
-        "dtype": {"bf16": ("fp8+f32" if args.screen_type == "fp8" else "bf16+f32"), "f32": "f32", "f64": "f64"}[prec],
-        "data": "synthetic (seeded Euler-Maruyama cubic sensor, scrambled Sobol nodes)",
-        "config": _config(w, prec),
-        "pair_evals_per_s": round(steps_per_s * w.n_scales * w.n * w.n, 1),
-        "rmse": rmse,
-        "restarts": restarts,
-        "clocks": clk.summary(),
-        "e2e": {"value": round(e2e_val, 4), "unit": "filter steps/s",
-                "h2d_bytes_per_step": 8 * w.r, "d2h_bytes_per_step": 8 * (2 * w.r + 2) + 56},
-        "gpu_launches": int(launches),
-        "screen": screen,
-        "roofline": {"bound": bound, "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4),
-                     "traffic": NCU_TRAFFIC.get((w.name, args.screen_type)) if prec == "bf16" else None,
-                     "kernel": "prediction (kernel sum)", "kernel_ms": round(pred_ms, 4),
-                     "peak_source": peak_note},
-    }
-    if args.fp32_steps > 0 and prec == "bf16":
-        S = min(args.fp32_steps, K)
-        out["fp32_comparator"] = _time_precision(w, "f32", S, W, tr, device)
-        out["fp32_comparator"]["rmse_mixed_same_steps"] = _rmse(est[:S], tr.x[W:W + S])
-    if args.cpu_baseline and ws == 1:   # the oracle's baseline runs at N = 1 only
-        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
-    print(json.dumps(out), flush=True)
-    if dist is not None:
-        dist.barrier()
-        dist.destroy_process_group()
+    steps_per_s = K / (t_max / 1e3)
+    res = {"value": steps_per_s, "ms_per_step": t_max / K, "rmse": rmse, "restarts": restarts, "est": est,
+           "clocks": clk.summary(), "gpu_launches": int(launches), "screen": screen, "roofline": roof,
+           # per step: every (target, source, scale) term is covered by the prediction; the
+           # screen proves most of them negligible and evaluates the rest (the self terms of
+           # the live nodes and the exact pairs) in float32
+           "pairs_covered_per_step": float(w.n_scales) * w.n * w.n,
+           "pairs_evaluated_per_step": float(w.n_scales) * (live + exact) if prec == "bf16" else
+                                       float(w.n_scales) * w.n * w.n}
+    return res, flt, tr, stream
 
 
-def _time_precision(w, prec, steps, warmup, tr, device):
-    """Steps/s and RMSE of another precision of the same path (the plain FP32 form) over
-    the first `steps` timed steps of the same trajectory."""
+def _time_precision(w, prec, steps, warmup, tr, device, screen_prefix=0):
+    """Steps/s and RMSE of another precision of the same path over the first `steps` timed
+    steps of the same trajectory."""
     import torch
     stream = torch.cuda.Stream(device)
-    flt = _make_filter(w, prec, w.seed, device, stream)
+    flt = _make_filter(w, prec, w.seed, device, stream, screen_prefix=screen_prefix)
     dys = torch.tensor(tr.dy, dtype=torch.float64, device=device)
     hist = torch.zeros((steps, 2 * w.r + 4), dtype=torch.float64, device=device)
     with torch.cuda.stream(stream):
@@ -373,11 +321,114 @@ def _time_precision(w, prec, steps, warmup, tr, device):
             "rmse": _rmse(est, tr.x[warmup:warmup + steps])}
 
 
+def _comparators(w, K, W, tr, device, fp32_steps, est):
+    """The plain FP32 GPU form (every pair, difference form) and the screened FP32 form
+    (the same kind of screen with its bound on the FMA pipes), each with its RMSE next to
+    the mixed path's on the same steps: the first isolates pruning + precision, the second
+    precision alone."""
+    S = min(fp32_steps, K)
+    out = {}
+    for key, prec in (("fp32_dense", "f32"), ("fp32_screened", "f32s")):
+        c = _time_precision(w, prec, S, W, tr, device)
+        c["rmse_mixed_same_steps"] = _rmse(est[:S], tr.x[W:W + S])
+        out[key] = c
+    return out
+
+
+def run_yy(args):
+    import torch
+    rank, ws, local, dist = _dist()
+    device = f"cuda:{local}"
+    torch.cuda.set_device(device)
+    w = WORKLOADS[args.workload]
+    prec = args.precision or w.precision
+    if args.screen_type is None:
+        args.screen_type = w.screen_type
+    seed = shard_seed(w.seed, rank)
+    W, K = args.warmup, args.steps
+    res, flt, tr, stream = measure_single(w, prec, args.screen_type, args.screen_prefix, K, W, device, seed,
+                                          dist, local)
+    # ---- end to end through the C ABI with host buffers ---------------------------
+    n_e2e = max(3, min(K, 50))
+    dy_host = torch.tensor(tr.dy, dtype=torch.float64).pin_memory()
+    dy_dev = torch.empty(w.r, dtype=torch.float64, device=device)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(n_e2e):
+        with torch.cuda.stream(stream):
+            dy_dev.copy_(dy_host[k % dy_host.shape[0]], non_blocking=True)
+        flt.predict()
+        flt.update(dy_dev)
+        flt.estimate()
+        flt.restart(mode=0)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = whole_job_rate(n_e2e, ws, max_over_ranks(e2e_s, dist, device))
+    steps_per_s = whole_job_rate(K, ws, K / res["value"])
+    # ---- the other single-GPU workloads as sub-lines (rank 0 of a default run only) ----
+    subs = {}
+    if args.sublines and args.workload == DEFAULT_WORKLOAD and rank == 0:
+        w2 = WORKLOADS["cubic_r100_n16384"]
+        K2 = max(K, 20)
+        r2, f2, tr2, _ = measure_single(w2, "bf16", w2.screen_type, 0, K2, W, device, w2.seed)
+        est2 = r2.pop("est")
+        sub = {"metric": "filter steps/s", "value": round(r2["value"], 3), "unit": "filter steps/s", "steps": K2,
+               "config": _config(w2, "bf16", w2.screen_type), **{k: v for k, v in r2.items() if k != "value"}}
+        if args.fp32_steps > 0:
+            sub.update(_comparators(w2, K2, W, tr2, device, args.fp32_steps, est2))
+        del f2
+        subs["cubic_r100_n16384"] = sub
+        subs["batched_256"] = measure_batch(max(W, 8), min(K, 20), device, "bf16", None, 0)
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    out = {
+        "metric": METRIC,
+        "value": round(steps_per_s, 4),
+        "unit": "filter steps/s",
+        "n_gpus": ws,
+        "steps": K,
+        "warmup": W,
+        "ms_per_step": round(1e3 / res["value"], 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        # screen operands + float32 exact evaluation, log-sum-exp and update
+        "dtype": {"bf16": ("fp8+f32" if args.screen_type == "fp8" else "bf16+f32"), "f32": "f32",
+                  "f32s": "f32", "f64": "f64"}[prec],
+        "data": "synthetic (seeded Euler-Maruyama cubic sensor, scrambled Sobol nodes)",
+        "config": _config(w, prec, args.screen_type),
+        "pairs_covered_per_s": round(steps_per_s * res["pairs_covered_per_step"], 1),
+        "pairs_evaluated_per_s": round(steps_per_s * res["pairs_evaluated_per_step"], 1),
+        "rmse": res["rmse"],
+        "restarts": res["restarts"],
+        "clocks": res["clocks"],
+        "e2e": {"value": round(e2e_val, 4), "unit": "filter steps/s",
+                "h2d_bytes_per_step": 8 * w.r, "d2h_bytes_per_step": 8 * (2 * w.r + 2) + 56},
+        "gpu_launches": res["gpu_launches"],
+        "screen": res["screen"],
+        "roofline": dict(res["roofline"], traffic=NCU_TRAFFIC.get((w.name, args.screen_type)) if prec == "bf16"
+                         else None),
+    }
+    if args.fp32_steps > 0 and prec == "bf16":
+        out.update(_comparators(w, K, W, tr, device, args.fp32_steps, res["est"]))
+    if subs:
+        out["sublines"] = subs
+    if args.cpu_baseline and ws == 1:   # the oracle's baseline runs at N = 1 only
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 class OracleSample:
     """The FP64 oracle as it stands, set up once on the workload (nodes, prior state,
     prepared drift) and timed on this host's cores on a bounded sample: the prediction for a
-    block of target rows against all n sources plus the O(n r) correction, scaled to one
-    full step."""
+    block of target rows (at least 4 per core, one row per OpenMP chunk) against all n
+    sources plus the O(n r) correction, scaled to one full step."""
 
     def __init__(self, w):
         from oracle import filter as F, sobol
@@ -394,11 +445,14 @@ class OracleSample:
         F.predict(self.p, self.prep, self.st.logw, 0, self.cores, n_threads=self.cores)
         self.t_row = max(time.perf_counter() - t0, 1e-6) / self.cores
 
-    def step_rate(self, seconds: float):
+    def step_rate(self, seconds: float, threads: int | None = None):
         F, w = self.F, self.w
-        rows = int(min(w.n, max(self.cores, self.cores * math.floor(seconds / (self.t_row * self.cores)))))
+        th = threads or self.cores
+        # t_row: seconds per row with every core busy; a single thread takes cores x longer
+        per_row = self.t_row * (self.cores / th)
+        rows = int(min(w.n, max(4 * th if th > 1 else 1, math.floor(seconds / per_row))))
         t0 = time.perf_counter()
-        F.predict(self.p, self.prep, self.st.logw, 0, rows, n_threads=self.cores)
+        F.predict(self.p, self.prep, self.st.logw, 0, rows, n_threads=th)
         t_pred = time.perf_counter() - t0
         t0 = time.perf_counter()
         lw = F.log_likelihood(self.p, self.prep.x, self.dy) + self.st.logw
@@ -406,14 +460,20 @@ class OracleSample:
         F.estimate(self.prep.x, lh)
         t_upd = time.perf_counter() - t0
         step_s = t_pred * (w.n / rows) + t_upd
-        return {"value": round(1.0 / step_s, 6), "unit": "filter steps/s", "cores": self.cores,
+        return {"value": round(1.0 / step_s, 6), "unit": "filter steps/s", "cores": th,
                 "kind": "oracle",
-                "sample": f"prediction of {rows} of {w.n} target rows (all sources, {w.n_scales} scales) "
-                          f"+ one full correction/estimate, scaled to one step; {t_pred + t_upd:.1f} s of CPU work"}
+                "sample": f"prediction of {rows} of {w.n} target rows (all sources, {w.n_scales} scales; "
+                          f"one row per OpenMP chunk over {th} threads) + one full correction/estimate, "
+                          f"scaled to one step; {t_pred + t_upd:.1f} s of CPU work"}
 
 
 def cpu_baseline(w, seconds: float):
-    return OracleSample(w).step_rate(seconds)
+    orc = OracleSample(w)
+    out = orc.step_rate(seconds)
+    single = orc.step_rate(max(1.0, seconds / 4), threads=1)
+    out["single_core_value"] = single["value"]
+    out["single_core_sample"] = single["sample"]
+    return out
 
 
 def run_reference(args):
@@ -434,27 +494,21 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 / v, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (seeded Euler-Maruyama cubic sensor, scrambled Sobol nodes)",
-           "config": _config(w, prec),
+           "config": _config(w, prec, args.screen_type or w.screen_type),
            "cpu_baseline": {"kind": "oracle", "cores": vals[-1]["cores"], "sample": vals[-1]["sample"], "value": v},
            "e2e": {"value": v, "unit": "filter steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "wall_s": round(time.perf_counter() - t0, 2)}
     print(json.dumps(out), flush=True)
 
 
-def run_batch(args):
+def measure_batch(S, K, device, prec, dist, local, rank=0):
     """256 ragged trajectories (r in 10..200, n log-uniform in 2048..32768, half cubic, half
-    linear-Gaussian) advanced as one batch; value = trajectory-steps per second."""
+    linear-Gaussian) advanced as one batch; value = trajectory-steps per second.  S untimed
+    steps (at least 8, so that the autotuner routes on posteriors that have spread out),
+    then the autotuner, then K steps as one CUDA graph."""
     import torch
     from paper_2509_16896_gb300 import binding
-    rank, ws_, local, dist = _dist()
-    device = f"cuda:{local}"
-    torch.cuda.set_device(device)
-    W, K = args.warmup, args.steps
-    # untimed steps before the timed ones: at least 8, so that the autotuner routes on
-    # posteriors that have spread out rather than on the prior
-    S = max(W, 8)
     members = batched_workloads(256, seed=shard_seed(4, rank), steps=S + K)
-    prec = args.precision or "bf16"
     cfgs = [binding.config_from_workload(m, precision=prec) for m in members]
     bt = binding.Batch(cfgs, device=device)
     trs = []
@@ -487,7 +541,7 @@ def run_batch(args):
         clk.mark_end()
     ms = max_over_ranks(e0.elapsed_time(e1), dist, device)
     launches = bt.launches() - l0
-    # prediction alone
+    # the batched prediction alone
     torch.cuda.synchronize()
     p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     p0.record(bt.stream)
@@ -496,33 +550,54 @@ def run_batch(args):
     p1.record(bt.stream)
     torch.cuda.synchronize()
     pred_ms = p0.elapsed_time(p1) / 3
+    # executed work of the last prediction: Gram products of the screened members (their
+    # screen runs one full-coordinate pass), difference-form flops of the FP32-form members
+    tflops, aflops = 0.0, 0.0
+    for b, m in enumerate(members):
+        if routing[b] == 0:
+            last, _, tiles, resc = bt.filters[b].screen()
+            tflops += _gram_flops(m.r, last, 64, tiles, resc, bn)
+        else:
+            aflops += 3.0 * m.n * m.n * m.r
     h = hist.cpu().numpy()
     rm_c, rm_l = [], []
     for b, (m, t) in enumerate(zip(members, trs)):
         est = h[:, bt.hist_off[b]:bt.hist_off[b] + m.r]
         rm = _rmse(est, t.x[S:S + K])
         (rm_c if m.model == "cubic" else rm_l).append(rm)
+    peak, note = _tensor_peak("bf16")
+    achieved = tflops / (pred_ms / 1e3) / 1e12
+    bt.close()
+    return {"metric": "trajectory-steps/s, 256 ragged filters in one batch",
+            "value": round(256 * K / (ms / 1e3), 2), "unit": "trajectory-steps/s", "steps": K, "warmup": S,
+            "ms_per_step": round(ms / K, 4), "dtype": prec,
+            "config": {"workload": "batched_256", "trajectories": 256, "r": "10..200", "n": "2048..32768 log-uniform",
+                       "n_scales": 2, "schedule": {"bn": bn, "grid": grid, "autotune_s": round(t_tune, 2),
+                                                   "fp32_form_members": int(routing.sum()),
+                                                   "fp32_form_max_r": int(max([m.r for m, p in zip(members, routing) if p] or [0]))},
+                       "time_loop": "one CUDA graph of K batched steps"},
+            "gpu_launches": int(launches), "clocks": clk.summary(),
+            "rmse_cubic_mean": float(np.mean(rm_c)), "rmse_linear_mean": float(np.mean(rm_l)),
+            "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
+                         "frac": round(achieved / peak, 4), "traffic": None,
+                         "kernel": "batched prediction (screen Gram products of the tensor-core members over the "
+                                   "whole prediction, FP32-form members included in the time)",
+                         "kernel_ms": round(pred_ms, 4), "algorithmic_flops_per_launch": tflops,
+                         "fp32_form_flops_per_launch": aflops, "peak_source": note}}
+
+
+def run_batch(args):
+    import torch
+    rank, ws_, local, dist = _dist()
+    device = f"cuda:{local}"
+    torch.cuda.set_device(device)
+    res = measure_batch(max(args.warmup, 8), args.steps, device, args.precision or "bf16", dist, local, rank)
     if rank != 0:
         return
-    flops = float(sum(2.0 * m.n * m.n * m.r for m in members))
-    peaks, src = _peaks()
-    peak = peaks.get("bf16_tflops", 1900.0)
-    achieved = flops / (pred_ms / 1e3) / 1e12
-    out = {"metric": "trajectory-steps/s, 256 ragged filters in one batch",
-           "value": round(whole_job_rate(256 * K, ws_, ms / 1e3), 2),
-           "unit": "trajectory-steps/s", "n_gpus": ws_, "steps": K, "warmup": S, "ms_per_step": round(ms / K, 4),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec,
-           "data": "synthetic (seeded Euler-Maruyama cubic sensor / linear-Gaussian, scrambled Sobol nodes)",
-           "config": {"workload": "batched_256", "trajectories": 256, "r": "10..200", "n": "2048..32768 log-uniform",
-                      "n_scales": 2, "schedule": {"bn": bn, "grid": grid, "autotune_s": round(t_tune, 2),
-                                                  "fp32_form_members": int(routing.sum()),
-                                                  "fp32_form_max_r": int(max([m.r for m, p in zip(members, routing) if p] or [0]))},
-                      "time_loop": "one CUDA graph of K batched steps"},
-           "gpu_launches": int(launches), "clocks": clk.summary(),
-           "rmse_cubic_mean": float(np.mean(rm_c)), "rmse_linear_mean": float(np.mean(rm_l)),
-           "roofline": {"bound": "tensor", "achieved": round(achieved, 3), "peak": peak, "unit": "TFLOP/s",
-                        "frac": round(achieved / peak, 4), "traffic": None,
-                        "kernel": "batched prediction (persistent)", "kernel_ms": round(pred_ms, 4)}}
+    res["value"] = round(res["value"] * ws_, 2)   # every rank advanced its own 256 members
+    out = {"metric": res.pop("metric"), "value": res.pop("value"), "unit": res.pop("unit"), "n_gpus": ws_,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "data": "synthetic (seeded Euler-Maruyama cubic sensor / linear-Gaussian, scrambled Sobol nodes)", **res}
     print(json.dumps(out), flush=True)
 
 
@@ -568,12 +643,14 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS) + ["batched_256"])
-    ap.add_argument("--precision", default=None, choices=["bf16", "f32", "f64"])
+    ap.add_argument("--precision", default=None, choices=["bf16", "f32", "f32s", "f64"])
     ap.add_argument("--impl", default="yy", choices=["yy", "reference"])
     ap.add_argument("--fp32-steps", type=int, default=10, help="steps of the plain FP32 comparator")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mlp-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-sublines", dest="sublines", action="store_false",
+                    help="skip the r = 100 and batched sub-lines of the default workload")
     ap.add_argument("--screen-type", default=None, choices=["bf16", "fp8"],
                     help="operands of the screen's Gram product (default: the workload's)")
     ap.add_argument("--screen-prefix", type=int, default=0,

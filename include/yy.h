@@ -73,10 +73,15 @@ typedef enum {
 typedef enum { YY_MODEL_CUBIC = 0, YY_MODEL_LINEAR = 1 } yy_model;
 
 /* Arithmetic of the prediction step.  FP64: every step in float64.  FP32: exact
- * float32 differences.  BF16: a tcgen05 BF16 Gram product screens out pairs whose
- * kernel term is provably negligible, and the remaining pairs are evaluated exactly in
- * float32 (results agree with FP32 within float32 rounding). */
-typedef enum { YY_PREC_FP64 = 0, YY_PREC_FP32 = 1, YY_PREC_BF16 = 2 } yy_precision;
+ * float32 differences over every pair.  BF16: a tcgen05 BF16 Gram product screens out pairs
+ * whose kernel term is provably negligible, and the remaining pairs are evaluated exactly
+ * in float32 (results agree with FP32 within float32 rounding).  FP32_SCREEN: the same kind
+ * of screen on the FMA pipes, no tensor cores: a tile of 64 x 64 pairs is skipped when the
+ * exact float32 squared distance of every live pair over the first 64 k coordinates
+ * (k = screen_prefix, default half of the 64-coordinate chunks) exceeds the row's screening
+ * radius; every other tile is evaluated exactly as in FP32 (results agree with FP32 within
+ * float32 rounding).  Not accepted by batches. */
+typedef enum { YY_PREC_FP64 = 0, YY_PREC_FP32 = 1, YY_PREC_BF16 = 2, YY_PREC_FP32_SCREEN = 3 } yy_precision;
 
 /* Log-weights after a restart (Section 5 only says the filter restarts at x_hat):
  * GAUSS = log N(x; x_hat, diag(max(v_hat, (R/4)^2))), UNIFORM = equal weights. */
@@ -220,7 +225,8 @@ YY_EXPORT yy_status yy_graph_launch(yy_filter* f);
 YY_EXPORT int64_t yy_graph_kernel_count(const yy_filter* f);
 
 /* ---- restart-proposal network (a library addition; the paper has no counterpart) -----
- * A perceptron z = [x_hat; sqrt(v_hat); dy/sqrt(dt)] (3r, normalised, see
+ * A perceptron z = [x_hat - c; sqrt(v_hat); dy/sqrt(dt)] (3r, c the centre of the box the
+ * estimate was computed in; normalised, see
  * yy_mlp_set_input_norm) -> H -> H (ReLU) -> [delta; lambda]
  * (2r), trained and run on the device with BF16 operands and FP32 accumulation.  Loss:
  * mean over rows and coordinates of (t - delta)^2 / (2 s^2) + log s, s = (R/3) exp(lambda),
@@ -399,6 +405,51 @@ YY_EXPORT yy_status yy_get_counters(yy_filter* f, int64_t* h_clamps, int64_t* h_
  * Any pointer may be NULL.  YY_ERR_UNSUPPORTED for other precisions.  Synchronises. */
 YY_EXPORT yy_status yy_get_screen(yy_filter* f, int32_t* h_last_prefix, int32_t* h_next_prefix,
                                   int64_t* h_tiles, int64_t* h_rescreened);
+
+/* ---- one filter across several devices (target rows split, source set replicated) -----
+ * Every device holds a handle of the same configuration with the same nodes; each owns an
+ * equal chunk of the target rows.  Per step and device: yy_predict (the shard's rows against
+ * all sources), yy_update_shard, an all-gather of every shard's rows and of every shard's
+ * record by the caller (e.g. NCCL), yy_merge_shards, then yy_estimate / yy_restart as for a
+ * whole filter (every device takes the same restart from the same merged estimate).  The
+ * split is a library design for the prediction's n x n work; the paper has no multi-device
+ * form.  yy_run_steps and CUDA-graph capture are refused while a handle is a shard of more
+ * than one. */
+
+/* Makes the handle shard `rank` of `count` (1..64): target rows
+ * [rank n_pad / count, (rank + 1) n_pad / count) intersected with [0, n), n_pad = n rounded
+ * up to 256; n_pad must be a multiple of 256 count.  count = 1 restores the whole filter.
+ * Call between steps (not after yy_predict or yy_update_shard).  Synchronous (rebuilds the
+ * tensor-core work list for the shard's tiles; a shard screens its tiles against every
+ * source tile, without the symmetric blocks of a whole filter). */
+YY_EXPORT yy_status yy_set_shard(yy_filter* f, int32_t rank, int32_t count);
+
+/* First row of the handle's chunk and the chunk length n_pad / count (rows); host int64. */
+YY_EXPORT yy_status yy_shard_rows(const yy_filter* f, int64_t* h_row0, int64_t* h_chunk);
+
+/* Likelihood update of the shard's rows (Section 2.2, Online stage; Section 7).  Writes
+ *   d_rows_out    device float [chunk] (double for FP64 precision): the chunk's log-weights
+ *                 ell'_i - lam_g, normalised by the shard's own log-sum-exp lam_g (-inf for
+ *                 padding rows)
+ *   d_record_out  device double [2r + 4]: lam_g, W_g, Q_g, 0, mean_g[r], M2_g[r], with
+ *                 w_i = exp(ell'_i - lam_g) over the shard's rows: W_g = sum w_i,
+ *                 Q_g = sum w_i^2, mean_g and M2_g the w-weighted mean and centred second
+ *                 moment of the box coordinates u
+ * d_dy as for yy_update.  Asynchronous. */
+YY_EXPORT yy_status yy_update_shard(yy_filter* f, const double* d_dy, void* d_rows_out, double* d_record_out);
+
+/* Completes the step from the gathered buffers: d_rows_all device [n_pad] (shard g's chunk at
+ * offset g chunk), d_records device double [count][2r + 4] in shard order.  Merges the records
+ * (Lambda = log sum_g W_g e^{lam_g}, each shard's sums rescaled by e^{lam_g - Lambda}, means
+ * and second moments combined by Chan's rule in shard order), sets Lambda_k, Z_k, x_hat,
+ * v_hat, ESS and the restart test as yy_update does, and stores every row's normalised
+ * log-weight.  count must equal the handle's shard count.  Asynchronous. */
+YY_EXPORT yy_status yy_merge_shards(yy_filter* f, const void* d_rows_all, const double* d_records, int32_t count);
+
+/* The same merge on the host (no device): h_records double [count][2r + 4] ->
+ * h_out double [2r + 4] = Lambda (relative to the shards' common offset), W, Q, ESS = W^2/Q,
+ * mean of u [r], variance [r]. */
+YY_EXPORT yy_status yy_merge_records_host(const double* h_records, int32_t count, int32_t r, double* h_out);
 
 /* Human-readable name of a status code (static storage). */
 YY_EXPORT const char* yy_status_str(yy_status s);

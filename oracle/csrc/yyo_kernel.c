@@ -55,7 +55,7 @@ void yyo_kernel_lse(int64_t n, int32_t r, const double* x, const double* fx,
 #pragma omp parallel
     {
         double* terms = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-#pragma omp for schedule(dynamic, 4)
+#pragma omp for schedule(dynamic, 1)
         for (int64_t i = t0; i < t1; ++i) {
             const double* xi = x + (size_t)i * r;
             const double* fi = fx + (size_t)i * r;

@@ -255,7 +255,7 @@ def step(p: Problem, st: State, dy: np.ndarray, n_threads: int = 0,
         centre, new_half, u = mean.copy(), half, st.u
         if p.restart_rule == "learned":
             from . import mlp, sobol
-            centre, new_half, ok = mlp.proposal(p.mlp_params, mean, var, dy, p.dt, p.R)
+            centre, new_half, ok = mlp.proposal(p.mlp_params, mean, var, dy, p.dt, p.R, st.centre)
             rec.learned = ok
             if ok:
                 u = sobol.to_box(st.y, new_half)

@@ -1,7 +1,8 @@
 """FP64 reference of the restart-proposal network (a library addition; the paper's
 restart, Section 5, re-centres the box at the estimate with a fixed half-width).
 
-Network: features z = [x_hat; sqrt(v_hat); dy / sqrt(dt)] in R^{3r}, normalised per
+Network: features z = [x_hat - c; sqrt(v_hat); dy / sqrt(dt)] in R^{3r} (c the centre of the box the
+estimate was computed in, so the first block is how far the posterior moved inside it), normalised per
 feature and clamped, zn = clip((z - mu) / s, -4, 4) (mu, s from the training set), ->
     h1 = relu(W1 zn + b1),  h2 = relu(W2 h1 + b2),  o = W3 h2 + b3,  o = [delta; lambda] in R^{2r}.
 Proposed box: centre x_hat + delta, half-widths R exp(lambda); it falls back to the plain
@@ -14,7 +15,11 @@ half-width is 3 sigma), averaged over rows and coordinates:
     L = mean_{b,d} [ (t - delta)^2 / (2 sigma^2) + log sigma ].
 
 Everything here is plain numpy in float64: forward, the hand-derived backward pass, and
-Adam (Kingma & Ba, 2015).
+Adam (Kingma & Ba, 2015).  forward and backward take an optional operand rounding `rnd`
+applied to both operands of every matrix product (identity by default); with a rounding
+to bfloat16 they give the exact products of the rounded operands that a BF16 tensor-core
+implementation accumulates, which separates its accumulation error from its operand
+rounding.
 """
 from __future__ import annotations
 
@@ -45,13 +50,18 @@ def normalise(p: dict, z: np.ndarray) -> np.ndarray:
     return np.clip((z - mu) / s, -4.0, 4.0)
 
 
-def forward(p: dict, z_raw: np.ndarray) -> tuple[np.ndarray, dict]:
+def _identity(a: np.ndarray) -> np.ndarray:
+    return a
+
+
+def forward(p: dict, z_raw: np.ndarray, rnd=None) -> tuple[np.ndarray, dict]:
+    q = rnd or _identity
     z = normalise(p, z_raw)
-    a1 = z @ p["W1"].T + p["b1"]
+    a1 = q(z) @ q(p["W1"]).T + p["b1"]
     h1 = np.maximum(a1, 0.0)
-    a2 = h1 @ p["W2"].T + p["b2"]
+    a2 = q(h1) @ q(p["W2"]).T + p["b2"]
     h2 = np.maximum(a2, 0.0)
-    o = h2 @ p["W3"].T + p["b3"]
+    o = q(h2) @ q(p["W3"]).T + p["b3"]
     return o, {"z": z, "a1": a1, "h1": h1, "a2": a2, "h2": h2}
 
 
@@ -70,17 +80,18 @@ def loss_and_grad_out(o: np.ndarray, t: np.ndarray, R: float) -> tuple[float, np
     return L, g
 
 
-def backward(p: dict, cache: dict, g_o: np.ndarray) -> dict:
+def backward(p: dict, cache: dict, g_o: np.ndarray, rnd=None) -> dict:
+    q = rnd or _identity
     g = {}
-    g["W3"] = g_o.T @ cache["h2"]
+    g["W3"] = q(g_o).T @ q(cache["h2"])
     g["b3"] = g_o.sum(axis=0)
-    g_h2 = g_o @ p["W3"]
+    g_h2 = q(g_o) @ q(p["W3"])
     g_a2 = g_h2 * (cache["a2"] > 0)
-    g["W2"] = g_a2.T @ cache["h1"]
+    g["W2"] = q(g_a2).T @ q(cache["h1"])
     g["b2"] = g_a2.sum(axis=0)
-    g_h1 = g_a2 @ p["W2"]
+    g_h1 = q(g_a2) @ q(p["W2"])
     g_a1 = g_h1 * (cache["a1"] > 0)
-    g["W1"] = g_a1.T @ cache["z"]
+    g["W1"] = q(g_a1).T @ q(cache["z"])
     g["b1"] = g_a1.sum(axis=0)
     return g
 
@@ -95,14 +106,16 @@ def adam_step(p: dict, g: dict, m: dict, v: dict, t: int, lr: float, b1: float =
         p[k] = p[k] - lr * mh / (np.sqrt(vh) + eps)
 
 
-def features(mean: np.ndarray, var: np.ndarray, dy: np.ndarray, dt: float) -> np.ndarray:
-    return np.concatenate([mean, np.sqrt(np.maximum(var, 0.0)), dy / np.sqrt(dt)])
+def features(mean: np.ndarray, var: np.ndarray, dy: np.ndarray, dt: float, centre: np.ndarray) -> np.ndarray:
+    return np.concatenate([mean - centre, np.sqrt(np.maximum(var, 0.0)), dy / np.sqrt(dt)])
 
 
-def proposal(p: dict, mean: np.ndarray, var: np.ndarray, dy: np.ndarray, dt: float, R: np.ndarray):
-    """(centre, half-widths, accepted) of the learned box; plain box when rejected."""
+def proposal(p: dict, mean: np.ndarray, var: np.ndarray, dy: np.ndarray, dt: float, R: np.ndarray,
+             centre: np.ndarray):
+    """(centre, half-widths, accepted) of the learned box; plain box when rejected.  centre:
+    the current box's centre."""
     r = mean.shape[0]
-    o, _ = forward(p, features(mean, var, dy, dt)[None, :])
+    o, _ = forward(p, features(mean, var, dy, dt, centre)[None, :])
     delta, lam = o[0, :r], o[0, r:]
     half = R * np.exp(lam)
     ok = bool(np.all(np.isfinite(delta)) and np.all(np.isfinite(half))

@@ -22,7 +22,7 @@ STATUS_NAMES = {0: "YY_OK", 1: "YY_ERR_ARG", 2: "YY_ERR_CUDA", 3: "YY_ERR_WORKSP
                 4: "YY_ERR_NONFINITE", 5: "YY_ERR_DEGENERATE", 6: "YY_ERR_TIMEOUT",
                 7: "YY_ERR_STATE", 8: "YY_ERR_UNSUPPORTED"}
 MODELS = {"cubic": 0, "linear": 1}
-PRECISIONS = {"f64": 0, "f32": 1, "bf16": 2}
+PRECISIONS = {"f64": 0, "f32": 1, "bf16": 2, "f32s": 3}
 RESTART_INIT = {"gauss": 0, "uniform": 1}
 RESTART_RULE = {"plain": 0, "learned": 1}
 SCREEN_TYPE = {"bf16": 0, "fp8": 1}
@@ -44,7 +44,8 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_mlp_workspace_bytes", "yy_mlp_create", "yy_mlp_destroy", "yy_mlp_set_params",
            "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train",
            "yy_mlp_set_input_norm", "yy_get_screen", "yy_batch_set_routing",
-           "yy_set_wait_limit")
+           "yy_set_wait_limit", "yy_set_shard", "yy_shard_rows", "yy_update_shard", "yy_merge_shards",
+           "yy_merge_records_host")
 
 
 class YYError(RuntimeError):
@@ -106,6 +107,11 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_batch_get_routing": (I32, [P, P]),
         "yy_batch_set_routing": (I32, [P, P]),
         "yy_set_wait_limit": (I32, [P, D]),
+        "yy_set_shard": (I32, [P, I32, I32]),
+        "yy_shard_rows": (I32, [P, P, P]),
+        "yy_update_shard": (I32, [P, P, P, P]),
+        "yy_merge_shards": (I32, [P, P, P, I32]),
+        "yy_merge_records_host": (I32, [P, I32, I32, P]),
         "yy_get_box": (I32, [P, P, P]),
         "yy_set_restart_mlp": (I32, [P, P]),
         "yy_mlp_param_count": (I64, [I32, I32]),
@@ -305,6 +311,37 @@ class Filter:
     def set_wait_limit(self, seconds: float) -> None:
         _check("yy_set_wait_limit", self.lib.yy_set_wait_limit(self.h, float(seconds)))
 
+    # ---- one filter across devices (target rows split) ------------------------------
+    def set_shard(self, rank: int, count: int) -> None:
+        _check("yy_set_shard", self.lib.yy_set_shard(self.h, rank, count))
+
+    def shard_rows(self):
+        """(first row of this shard's chunk, chunk length)."""
+        r0, ch = ctypes.c_int64(), ctypes.c_int64()
+        _check("yy_shard_rows", self.lib.yy_shard_rows(self.h, ctypes.byref(r0), ctypes.byref(ch)))
+        return r0.value, ch.value
+
+    def update_shard(self, dy_dev, rows_out, record_out) -> None:
+        """rows_out: device tensor [chunk] (float32, float64 for FP64); record_out: float64 [2r + 4]."""
+        t = self.torch
+        assert dy_dev.dtype == t.float64 and dy_dev.numel() == self.r
+        assert rows_out.dtype == (t.float64 if self.fp64 else t.float32) and rows_out.is_contiguous()
+        assert record_out.dtype == t.float64 and record_out.numel() == 2 * self.r + 4 and record_out.is_contiguous()
+        assert rows_out.numel() == self.shard_rows()[1]
+        _order_after_torch(self.stream, self.device)
+        _check("yy_update_shard", self.lib.yy_update_shard(self.h, ctypes.c_void_p(dy_dev.data_ptr()),
+                                                           ctypes.c_void_p(rows_out.data_ptr()),
+                                                           ctypes.c_void_p(record_out.data_ptr())))
+        _order_torch_after(self.stream, self.device)
+
+    def merge_shards(self, rows_all, records, count: int) -> None:
+        """rows_all: device [n_pad] (every shard's chunk in shard order); records: float64
+        [count][2r + 4] in shard order."""
+        assert rows_all.is_contiguous() and records.is_contiguous() and records.dtype == self.torch.float64
+        _order_after_torch(self.stream, self.device)
+        _check("yy_merge_shards", self.lib.yy_merge_shards(self.h, ctypes.c_void_p(rows_all.data_ptr()),
+                                                           ctypes.c_void_p(records.data_ptr()), count))
+
     def screen(self):
         """(first-pass chunks of the last prediction, of the next one, tiles, tiles
         rescreened) of the last BF16 prediction."""
@@ -436,6 +473,16 @@ def _order_torch_after(stream, device) -> None:
     for other in (torch.cuda.current_stream(device), torch.cuda.default_stream(device)):
         if other.cuda_stream != stream.cuda_stream:
             other.wait_stream(stream)
+
+
+def merge_records_host(records: np.ndarray, r: int) -> np.ndarray:
+    """The shard merge on the host: records float64 [count][2r + 4] -> [Lambda, W, Q, ESS,
+    mean of u [r], variance [r]] (yy_merge_records_host; no device needed)."""
+    L = load()
+    rec = np.ascontiguousarray(records, dtype=np.float64)
+    out = np.empty(2 * r + 4)
+    _check("yy_merge_records_host", L.yy_merge_records_host(_ptr(rec), rec.shape[0], r, _ptr(out)))
+    return out
 
 
 def pack_mlp_params(p: dict) -> np.ndarray:

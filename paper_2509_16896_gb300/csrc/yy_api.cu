@@ -28,7 +28,9 @@ constexpr unsigned long long kDefaultWaitNs = 4000000000ull;   // 4 s
 yy_status build_tc_schedule(yy_filter* f) {
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const long long tiles = f->n_pad / 128;
+    // the handle's target tiles (all of them, or its shard's chunk)
+    const long long t_lo = f->row0 / 128, t_hi = (f->row1 + 127) / 128;
+    const long long tiles = t_hi - t_lo;
     const int nst = (int)(f->n_pad / 256);
     const int grid = (int)std::min<long long>(std::min(sms, kMaxTcGrid), tiles * 8);
     std::vector<std::vector<int4>> per(grid);
@@ -36,7 +38,7 @@ yy_status build_tc_schedule(yy_filter* f) {
     if (f->kf.tc_sym) {
         struct It { double cost; int t, q, S; };
         std::vector<It> all;
-        for (long long t = 0; t < tiles; ++t) {
+        for (long long t = t_lo; t < t_hi; ++t) {
             const int L = nst - (int)(t / 2);
             const int St = tc_sym_splits(L);
             for (int q = 0; q < St; ++q)
@@ -51,9 +53,9 @@ yy_status build_tc_schedule(yy_filter* f) {
             load[c] += it.cost;
         }
     } else {
-        S = tc_choose_splits(tiles, nst, grid);
+        S = tc_choose_splits(tiles, nst, std::max(grid, 1));
         long long j = 0;
-        for (long long t = 0; t < tiles; ++t)
+        for (long long t = t_lo; t < t_hi; ++t)
             for (int q = 0; q < S; ++q, ++j) per[j % grid].push_back(make_int4(0, (int)t, q, S));
     }
     std::vector<int4> items;
@@ -75,6 +77,14 @@ yy_status build_tc_schedule(yy_filter* f) {
     return YY_OK;
 }
 
+}  // namespace
+
+namespace yy {
+yy_status rebuild_tc_schedule(yy_filter* f) { return build_tc_schedule(f); }
+}  // namespace yy
+
+namespace {
+
 bool cfg_valid(const yy_config* c) {
     if (!c) return false;
     if (c->r < 1 || c->r > YY_MAX_DIM || c->m != c->r) return false;
@@ -82,7 +92,7 @@ bool cfg_valid(const yy_config* c) {
     if (!(c->dt > 0.0) || !(c->R > 0.0) || !(c->prior_var > 0.0)) return false;
     if (c->n_scales < 1 || c->n_scales > YY_MAX_SCALES) return false;
     if (c->model != YY_MODEL_CUBIC && c->model != YY_MODEL_LINEAR) return false;
-    if (c->precision < YY_PREC_FP64 || c->precision > YY_PREC_BF16) return false;
+    if (c->precision < YY_PREC_FP64 || c->precision > YY_PREC_FP32_SCREEN) return false;
     if (c->restart_init != YY_RESTART_INIT_GAUSS && c->restart_init != YY_RESTART_INIT_UNIFORM) return false;
     if (!(c->ess_frac >= 0.0) || c->ess_frac > 1.0) return false;
     if (c->restart_rule != YY_RESTART_PLAIN && c->restart_rule != YY_RESTART_LEARNED) return false;
@@ -258,6 +268,8 @@ void fill_consts(yy_filter* f, Consts<T>* k, const double* halfwidth) {
     k->c_ref = cref;
     f->c_ref = cref;
     k->wait_ns = f->wait_ns;
+    k->row0 = f->row0;
+    k->row1 = f->row1;
 }
 
 yy_status cuda_status(cudaError_t e) { return e == cudaSuccess ? YY_OK : YY_ERR_CUDA; }
@@ -346,6 +358,10 @@ yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t bytes, void*
     f->fp64 = (cfg->precision == YY_PREC_FP64);
     f->wait_ns = kDefaultWaitNs;
     f->kf.wait_ns = f->kd.wait_ns = kDefaultWaitNs;
+    f->row0 = 0;
+    f->row1 = cfg->n;
+    f->shard_rank = 0;
+    f->shard_count = 1;
     multiscale_coefficients(cfg->n_scales, f->coef);
     if (f->fp64) carve<double>(cfg, f->ws, &f->bd);
     else carve<float>(cfg, f->ws, &f->bf);
@@ -400,6 +416,13 @@ yy_status yy_predict(yy_filter* f) {
         e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
         if (e == cudaSuccess) e = launch_ksum_simt<float>(f->kf, f->bf, f->stream);
         f->launches += 1;
+    } else if (f->cfg.precision == YY_PREC_FP32_SCREEN) {
+        // first pass over 64 k coordinates: k = screen_prefix, else half of the 64-chunks
+        const int nk = f->r_pad / kColAlign;
+        const int k1 = kColAlign * (f->cfg.screen_prefix > 0 ? f->cfg.screen_prefix : (nk + 1) / 2);
+        e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
+        if (e == cudaSuccess) e = launch_ksum_scr32(f->kf, f->bf, k1, f->stream);
+        f->launches += 2;
     } else {
         e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
         int l = 0;
@@ -415,6 +438,7 @@ yy_status yy_predict(yy_filter* f) {
 yy_status yy_update(yy_filter* f, const double* d_dy) {
     if (!f || !d_dy) return YY_ERR_ARG;
     if (!f->nodes_ready || !f->predicted) return YY_ERR_STATE;
+    if (f->shard_count > 1) return YY_ERR_STATE;   // a shard updates with yy_update_shard
     int l = 0;
     cudaError_t e = f->fp64
         ? launch_update<double>(f->kd, f->bd, d_dy, f->cfg.restart_interval, f->cfg.ess_frac, f->stream, &l)
@@ -452,7 +476,7 @@ yy_status yy_estimate(yy_filter* f, double* h_mean, double* h_var, double* h_ess
 yy_status yy_restart(yy_filter* f, int32_t mode, int32_t* h_did_restart) {
     if (!f) return YY_ERR_ARG;
     if (mode != YY_RESTART_AUTO && mode != YY_RESTART_FORCE && mode != YY_RESTART_NEVER) return YY_ERR_ARG;
-    if (!f->nodes_ready || f->predicted) return YY_ERR_STATE;
+    if (!f->nodes_ready || f->predicted || f->shard_updated) return YY_ERR_STATE;
     int l = 0;
     yy_mlp* net = (f->cfg.restart_rule == YY_RESTART_LEARNED) ? f->mlp : nullptr;
     cudaError_t e = f->fp64
@@ -480,7 +504,7 @@ yy_status yy_restart(yy_filter* f, int32_t mode, int32_t* h_did_restart) {
 
 yy_status yy_run_steps(yy_filter* f, const double* d_dy_all, int64_t K, double* d_hist) {
     if (!f || !d_dy_all || K < 0) return YY_ERR_ARG;
-    if (!f->nodes_ready || f->predicted) return YY_ERR_STATE;
+    if (!f->nodes_ready || f->predicted || f->shard_count > 1) return YY_ERR_STATE;
     const int r = f->cfg.r;
     for (int64_t k = 0; k < K; ++k) {
         yy_status st = yy_predict(f);

@@ -66,7 +66,7 @@ bool batch_cfg_ok(const yy_config* cfgs, int B) {
     for (int b = 0; b < B; ++b) {
         if (yy_workspace_bytes(&cfgs[b]) == 0) return false;
         if (cfgs[b].precision != cfgs[0].precision || cfgs[b].n_scales != cfgs[0].n_scales) return false;
-        if (cfgs[b].precision == YY_PREC_FP64) return false;
+        if (cfgs[b].precision == YY_PREC_FP64 || cfgs[b].precision == YY_PREC_FP32_SCREEN) return false;
     }
     return true;
 }

@@ -26,4 +26,12 @@ struct yy_filter {
     long long graph_kernels;
     struct yy_mlp* mlp;   // restart-proposal network for YY_RESTART_LEARNED (not owned)
     unsigned long long wait_ns;   // limit of bounded device waits (default 4 s)
+    long long row0, row1;         // target rows of this handle (shards of a row-split filter)
+    int shard_rank, shard_count;  // 0, 1 for a whole filter
+    bool shard_updated;           // yy_update_shard ran; yy_merge_shards completes the step
 };
+
+namespace yy {
+// Rebuilds the work list of the tensor-core prediction for the handle's target rows.
+yy_status rebuild_tc_schedule(yy_filter* f);
+}  // namespace yy

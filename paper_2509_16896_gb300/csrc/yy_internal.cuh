@@ -50,6 +50,7 @@ struct DevStats {
     unsigned long long tc_last_blk, tc_last_esc;   // the same, kept for the host
     int tc_last_nk1;             // first-pass chunks the last prediction used
     unsigned int tc_done;        // CTAs of the running prediction launch that finished
+    float scr_lmax;              // screened float32 form: largest live source log-weight
 };
 
 // Constants of one filter handed to kernels by value.
@@ -77,6 +78,8 @@ struct Consts {
     T sign_c[kMaxScales + 1];  // 0 for a zero coefficient
     double c_ref;
     unsigned long long wait_ns;  // limit of the prediction kernel's bounded waits (yy_set_wait_limit)
+    long long row0, row1;        // target rows this handle predicts and updates: [0, n), or its
+                                 // shard's equal chunk when the rows are split across devices
 };
 
 // Pointers into the caller's workspace.
@@ -168,6 +171,7 @@ cudaError_t launch_prep(const Consts<T>& k, const Bufs<T>& b, bool init_weights,
 
 template <typename T>
 cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s);
+cudaError_t launch_ksum_scr32(const Consts<float>& k, const Bufs<float>& b, int k1, cudaStream_t s);
 cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s,
                            int* launches);
 size_t tc_scratch_bytes(long long n_pad);
@@ -189,13 +193,16 @@ cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int i
 template <typename T>
 cudaError_t launch_normalise_only(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s,
                                   int* launches);
+template <typename T>
+cudaError_t launch_update_shard(const Consts<T>& k, const Bufs<T>& b, const double* dy, double* rec, cudaStream_t s,
+                                int* launches);
 
 size_t part_bytes(int r_pad);
 
 cudaError_t launch_sobol_points_restart(const uint32_t* dirs, int r, int r_pad, long long n, float* u,
                                         const double* next_half, const DevStats* st, cudaStream_t s);
 cudaError_t mlp_propose(struct ::yy_mlp* net, int r, const double* mean, const double* var, const double* dy,
-                        double dt, const int* flag, cudaStream_t s, int* launches);
+                        const double* centre, double dt, const int* flag, cudaStream_t s, int* launches);
 const float* mlp_output(const struct ::yy_mlp* net);
 
 // Batched launches: one launch covers every trajectory (grid.y = trajectory).

@@ -30,8 +30,20 @@ template <> __device__ __forceinline__ float exp_fast<float>(float x) { return e
 template <> __device__ __forceinline__ double exp_fast<double>(double x) { return exp(x); }
 }  // namespace
 
-template <typename T, int N>
-__device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>& b, int rk, int bid) {
+// SCREEN (float32 only): before a source tile is evaluated, the squared distance of each
+// of its pairs over the first k1 coordinates -- a lower bound of the full |u_i - u_s|^2,
+// formed exactly as the full sum's first terms -- is compared with rho_i^2, where
+//     rho_i = max_j [tau_j |f_i| + sqrt(2 tau_j max(0, lmax - (ell_i - tau_j |f_i|^2 / 2) + T))],
+// lmax the largest live source log-weight, ell_i - tau_j |f_i|^2 / 2 the exact self term of
+// row i (a lower bound of its largest term) and T = ln n + 20.  By the triangle inequality
+// |u_i - tau_j f_i - u_s| >= |u_i - u_s| - tau_j |f_i|, a pair beyond rho_i scores below the
+// self term by more than T at every scale, so a tile none of whose live pairs passes is
+// skipped (all skipped terms together are below e^-20 of the row's sum); any other tile is
+// evaluated exactly as in the plain form.  A live target without a finite log-weight has no
+// reference and takes every tile.  The comparison carries a relative margin of 1e-4 for
+// the float32 rounding of the partial sums.
+template <typename T, int N, bool SCREEN = false>
+__device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>& b, int rk, int bid, int k1 = 0) {
     __shared__ T At[BK][BM];   // u of targets
     __shared__ T Ft[BK][BM];   // f of targets
     __shared__ T Bt[BK][BN];   // u of sources
@@ -43,6 +55,7 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
 
     T rowc[TM][N];          // -(tau_j / 2) |f_i|^2
     T mx[TM][N], sm[TM][N];
+    T rho2[TM];             // SCREEN: squared screening radius of each row
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
         const long long i = i0 + ty * TM + a;
@@ -52,6 +65,26 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
             rowc[a][j] = -T(0.5) * k.tau[j] * nf;
             mx[a][j] = T(-INFINITY);
             sm[a][j] = T(0);
+        }
+        rho2[a] = T(-1);   // no candidates (padded or masked rows)
+        if constexpr (SCREEN) {
+            if (i < k.n && !b.mask[i]) {
+                const T li = b.logw[i];
+                const T lmax = (T)b.stats->scr_lmax;
+                if (li == T(-INFINITY)) {
+                    rho2[a] = T(INFINITY);
+                } else {
+                    const T Tn = log((T)k.n) + T(20);
+                    const T Fi = sqrt(nf);
+                    T rho = T(0);
+#pragma unroll
+                    for (int j = 0; j < N; ++j) {
+                        const T gap = fmax(lmax - (rowc[a][j] + li) + Tn, T(0));
+                        rho = fmax(rho, k.tau[j] * Fi + sqrt(T(2) * k.tau[j] * gap));
+                    }
+                    rho2[a] = rho * rho * T(1.0001) + T(1e-30);
+                }
+            }
         }
     }
 
@@ -64,6 +97,46 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
         if (tid < BN) {
             const long long s = s0 + tid;
             lsrc[tid] = (s < k.n && !b.mask[s]) ? b.logw[s] : T(-INFINITY);
+        }
+        if constexpr (SCREEN) {
+            // first pass: partial squared distances over coordinates [0, k1)
+            for (int d0 = 0; d0 < k1; d0 += BK) {
+                __syncthreads();
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int e = tid + 256 * q;
+                    const int row = e >> 4, col = e & 15;
+                    At[col][row] = (T)b.u[(size_t)(i0 + row) * k.r_pad + d0 + col];
+                    Bt[col][row] = (T)b.u[(size_t)(s0 + row) * k.r_pad + d0 + col];
+                }
+                __syncthreads();
+#pragma unroll
+                for (int kk = 0; kk < BK; ++kk) {
+                    T av[TM], bv[TN];
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) av[a] = At[kk][ty * TM + a];
+#pragma unroll
+                    for (int c = 0; c < TN; ++c) bv[c] = Bt[kk][tx * TN + c];
+#pragma unroll
+                    for (int a = 0; a < TM; ++a)
+#pragma unroll
+                        for (int c = 0; c < TN; ++c) {
+                            const T dlt = av[a] - bv[c];
+                            S1[a][c] = fma(dlt, dlt, S1[a][c]);
+                        }
+                }
+            }
+            int any = 0;
+#pragma unroll
+            for (int a = 0; a < TM; ++a)
+#pragma unroll
+                for (int c = 0; c < TN; ++c)
+                    any |= (S1[a][c] <= rho2[a] && lsrc[tx * TN + c] != T(-INFINITY)) ? 1 : 0;
+            if (!__syncthreads_or(any)) continue;   // every pair of the tile is negligible
+#pragma unroll
+            for (int a = 0; a < TM; ++a)
+#pragma unroll
+                for (int c = 0; c < TN; ++c) S1[a][c] = T(0);
         }
         for (int d0 = 0; d0 < rk; d0 += BK) {
             __syncthreads();
@@ -153,7 +226,48 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
 
 template <typename T, int N>
 __global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int rk) {
-    ksum_simt_body<T, N>(k, b, rk, blockIdx.x);
+    ksum_simt_body<T, N>(k, b, rk, (int)(k.row0 / BM) + blockIdx.x);
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) k_ksum_scr32(Consts<float> k, Bufs<float> b, int rk, int k1) {
+    ksum_simt_body<float, N, true>(k, b, rk, (int)(k.row0 / BM) + blockIdx.x, k1);
+}
+
+// Largest live source log-weight (the screen's lmax), one block.
+__global__ void __launch_bounds__(1024) k_live_lmax(Consts<float> k, Bufs<float> b) {
+    __shared__ float red[32];
+    float m = -INFINITY;
+    for (long long i = threadIdx.x; i < k.n; i += blockDim.x)
+        if (!b.mask[i]) m = fmaxf(m, b.logw[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+        b.stats->scr_lmax = m;
+    }
+}
+
+// Screened float32 form: first pass over k1 coordinates (multiple of 16, 16 <= k1 <= r
+// rounded up to 16), then exact evaluation of every tile that keeps a candidate.
+cudaError_t launch_ksum_scr32(const Consts<float>& k, const Bufs<float>& b, int k1, cudaStream_t s) {
+    const int rk = ((k.r + BK - 1) / BK) * BK;
+    k1 = ((k1 + BK - 1) / BK) * BK;
+    if (k1 < BK) k1 = BK;
+    if (k1 > rk) k1 = rk;
+    const unsigned grid = (unsigned)((k.row1 - k.row0 + BM - 1) / BM);   // the handle's target blocks
+    if (grid == 0) return cudaSuccess;
+    k_live_lmax<<<1, 1024, 0, s>>>(k, b);
+    switch (k.N) {
+        case 1: k_ksum_scr32<1><<<grid, 256, 0, s>>>(k, b, rk, k1); break;
+        case 2: k_ksum_scr32<2><<<grid, 256, 0, s>>>(k, b, rk, k1); break;
+        case 3: k_ksum_scr32<3><<<grid, 256, 0, s>>>(k, b, rk, k1); break;
+        case 4: k_ksum_scr32<4><<<grid, 256, 0, s>>>(k, b, rk, k1); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // batched: trajectory = blockIdx.y; blocks past a trajectory's rows return at once
@@ -186,7 +300,8 @@ template cudaError_t launch_ksum_simt_batch<double>(const Traj<double>*, int, in
 template <typename T>
 cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s) {
     const int rk = ((k.r + BK - 1) / BK) * BK;
-    const unsigned grid = (unsigned)(k.n_pad / BM);
+    const unsigned grid = (unsigned)((k.row1 - k.row0 + BM - 1) / BM);   // the handle's target blocks
+    if (grid == 0) return cudaSuccess;
     switch (k.N) {
         case 1: k_ksum_simt<T, 1><<<grid, 256, 0, s>>>(k, b, rk); break;
         case 2: k_ksum_simt<T, 2><<<grid, 256, 0, s>>>(k, b, rk); break;

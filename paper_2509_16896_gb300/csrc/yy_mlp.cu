@@ -9,9 +9,9 @@
 //   loss: mean over rows and coordinates of (t - delta)^2 / (2 sigma^2) + log sigma,
 //         sigma = (R / 3) exp(lambda), t = x_true - x_hat
 //
-// Arithmetic: every matrix product rounds both operands to bfloat16 on load and
-// accumulates in float32 (BF16 weights and activations, FP32 accumulation); the master
-// weights, gradients and Adam moments are float32.  Kernels: a tiled product
+// Arithmetic: every matrix product rounds both operands to bfloat16 and accumulates in
+// float32 on the tensor cores (tcgen05.mma kind::f16, accumulators in TMEM); the master
+// weights, gradients and Adam moments are float32.  Kernels: the product
 // C = op(A) op(B) with bias / ReLU epilogue, ReLU backward, column sums (bias
 // gradients), the loss gradient, Adam, and the row gather of a training batch.
 #include <math.h>
@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "yy_handle.cuh"
+#include "yy_tcgen05.cuh"
 
 using namespace yy;
 
@@ -43,6 +44,7 @@ struct yy_mlp {
     float* g_o; float* g_h; float* g_a;                     // backward scratch [max_batch][max(H, 2r)]
     float* loss;        // [1]
     int* idx;           // [max_batch] batch rows
+    unsigned int* status;   // timeout bit of the tensor-core products
     long long step;
     long long n_params;
     size_t off_W1, off_b1, off_W2, off_b2, off_W3, off_b3;
@@ -50,55 +52,145 @@ struct yy_mlp {
 
 namespace {
 
-constexpr int TILE = 32;
+// ---- matrix products on the tensor cores --------------------------------------------
+// C[m][n] (+)= sum_k A(m, k) B(k, n), A(m, k) = A[m sam + k sak], B(k, n) = B[k sbk + n sbn]
+// (any strides, so transposed operands need no copy); epilogue: + bias[n], the
+// pre-activation stored to pre (if not NULL), ReLU if relu.  One CTA of 4 warps per output
+// tile of 128 rows x 64 columns: per chunk of 64 k the threads round both operands to
+// bfloat16 (round to nearest even) and write them to shared memory in the K-major layout
+// of the 128-byte swizzle (rows of 128 bytes, 16-byte chunk c of row r at c xor (r mod 8),
+// the layout a TMA tile copy with that swizzle produces), then one thread issues four
+// tcgen05.mma kind::f16 (M 128, N 64, K 16, FP32 accumulation in TMEM) and commits them to
+// an mbarrier.  The epilogue warps read their 32 TMEM lanes (one output row per thread)
+// with tcgen05.ld.  Rows, columns and k beyond the matrix are zero in shared memory and
+// not stored.  The MMA wait is bounded (1 s): on expiry the kernel records the timeout
+// bit in the network's status word, waits (bounded) for its own MMAs and frees TMEM.
+constexpr int GM = 128, GN = 64, GK = 64;
+constexpr uint32_t kGemmIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(GN >> 3) << 17) |
+                                ((uint32_t)(GM >> 4) << 24);
+constexpr unsigned long long kGemmWaitNs = 1000000000ull;
 
-// C[m][n] (+)= sum_k A(m, k) B(k, n), A(m, k) = A[m * sam + k * sak], B(k, n) = B[k * sbk + n * sbn];
-// operands rounded to bfloat16, float32 accumulation; epilogue: + bias[n], store the
-// pre-activation to pre (if not NULL), ReLU if relu.
-__global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, const float* __restrict__ A, long long sam,
-                                                   long long sak, const float* __restrict__ Bm, long long sbk,
-                                                   long long sbn, float* __restrict__ C, long long ldc,
-                                                   const float* __restrict__ bias, float* __restrict__ pre, int relu,
-                                                   int accumulate) {
-    __shared__ float As[TILE][TILE + 1], Bs[TILE][TILE + 1];
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads, 4 rows each
-    const int m0 = blockIdx.y * TILE, n0 = blockIdx.x * TILE;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int k0 = 0; k0 < K; k0 += TILE) {
-        for (int q = 0; q < 4; ++q) {
-            const int mm = ty * 4 + q;
-            const int m = m0 + mm, k = k0 + tx;
-            As[mm][tx] = (m < M && k < K) ? __bfloat162float(__float2bfloat16_rn(A[m * sam + k * sak])) : 0.f;
-            const int kk = k0 + mm, n = n0 + tx;
-            Bs[mm][tx] = (kk < K && n < N) ? __bfloat162float(__float2bfloat16_rn(Bm[kk * sbk + n * sbn])) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int kk = 0; kk < TILE; ++kk) {
-            const float b = Bs[kk][tx];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[q] = fmaf(As[ty * 4 + q][kk], b, acc[q]);
-        }
-        __syncthreads();
+__device__ __forceinline__ uint32_t sw128_offset(int row, int k) {
+    return (uint32_t)(row * 128 + ((((k >> 3) ^ (row & 7)) & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ bool gemm_wait(uint64_t* bar, uint32_t parity, unsigned long long limit) {
+    if (yy::ptx::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = yy::ptx::globaltimer();
+    while (!yy::ptx::mbar_try_wait(bar, parity))
+        if (yy::ptx::globaltimer() - t0 > limit) return false;
+    return true;
+}
+
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, const float* __restrict__ A, long long sam,
+                                                 long long sak, const float* __restrict__ Bm, long long sbk,
+                                                 long long sbn, float* __restrict__ C, long long ldc,
+                                                 const float* __restrict__ bias, float* __restrict__ pre, int relu,
+                                                 int accumulate, unsigned int* status) {
+    using namespace yy::ptx;
+    __shared__ __align__(1024) uint8_t sA[GM * GK * 2];
+    __shared__ __align__(1024) uint8_t sB[GN * GK * 2];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int s_fail;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const long long m0 = (long long)blockIdx.y * GM, n0 = (long long)blockIdx.x * GN;
+    if ((smem_u32(sA) | smem_u32(sB)) & 1023u) {   // the swizzle atoms need 1024-byte alignment
+        if (tid == 0) atomicOr(status, kStatusNonFinite);
+        return;
     }
-    for (int q = 0; q < 4; ++q) {
-        const int m = m0 + ty * 4 + q, n = n0 + tx;
-        if (m >= M || n >= N) continue;
-        float v = acc[q];
-        if (accumulate) v += C[m * ldc + n];
-        if (bias) v += bias[n];
-        if (pre) pre[m * ldc + n] = v;
-        if (relu) v = fmaxf(v, 0.f);
-        C[m * ldc + n] = v;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+        s_fail = 0;
+    }
+    if (warp == 0) {
+        tmem_alloc(&tmem_slot, GN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int nchunks = (K + GK - 1) / GK;
+    const bool a_krow = (sak == 1);   // k contiguous in A: consecutive threads take consecutive k
+    const bool b_kcol = (sbk == 1);
+    bool ok = true;
+    int kc_fail = 0;
+    for (int kc = 0; kc < nchunks; ++kc) {
+        const int k0 = kc * GK;
+        for (int q = 0; q < GM * GK / 128; ++q) {
+            const int e = tid + 128 * q;
+            const int row = a_krow ? (e >> 6) : (e & (GM - 1));
+            const int kk = a_krow ? (e & 63) : (e >> 7);
+            const long long m = m0 + row, k = k0 + kk;
+            const float v = (m < M && k < K) ? A[m * sam + k * sak] : 0.f;
+            *reinterpret_cast<__nv_bfloat16*>(sA + sw128_offset(row, kk)) = __float2bfloat16_rn(v);
+        }
+        for (int q = 0; q < GN * GK / 128; ++q) {
+            const int e = tid + 128 * q;
+            const int col = b_kcol ? (e >> 6) : (e & (GN - 1));
+            const int kk = b_kcol ? (e & 63) : (e >> 6);
+            const long long n = n0 + col, k = k0 + kk;
+            const float v = (n < N && k < K) ? Bm[k * sbk + n * sbn] : 0.f;
+            *reinterpret_cast<__nv_bfloat16*>(sB + sw128_offset(col, kk)) = __float2bfloat16_rn(v);
+        }
+        // generic-proxy writes of shared memory become visible to the tensor cores' reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            tc_fence_after();
+            const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+#pragma unroll
+            for (int kk = 0; kk < GK / 16; ++kk)
+                mma_bf16(tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0 + kk * 32), kGemmIdesc, (kc | kk) != 0 ? 1u : 0u);
+            mma_commit(&bar);
+        }
+        // every thread waits for the chunk's MMAs before shared memory is written again
+        if (!gemm_wait(&bar, (uint32_t)(kc & 1), kGemmWaitNs)) s_fail = 1;
+        __syncthreads();
+        tc_fence_after();
+        if (s_fail) { ok = false; kc_fail = kc; break; }
+    }
+    if (!ok) {
+        if (tid == 0) atomicOr(status, kStatusTimeout);
+        gemm_wait(&bar, (uint32_t)(kc_fail & 1), kGemmWaitNs);   // our MMAs of that chunk, bounded
+    } else if (nchunks > 0) {
+        uint32_t v0[32], v1[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+        tmem_ld32(taddr, v0);
+        tmem_ld32(taddr + 32, v1);
+        tmem_ld_wait();
+        const long long m = m0 + warp * 32 + lane;
+        if (m < M) {
+#pragma unroll
+            for (int c = 0; c < GN; ++c) {
+                const long long n = n0 + c;
+                if (n >= N) break;
+                float v = __uint_as_float(c < 32 ? v0[c] : v1[c - 32]);
+                if (accumulate) v += C[m * ldc + n];
+                if (bias) v += bias[n];
+                if (pre) pre[m * ldc + n] = v;
+                if (relu) v = fmaxf(v, 0.f);
+                C[m * ldc + n] = v;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, GN);
     }
 }
 
-void gemm(cudaStream_t s, int M, int N, int K, const float* A, long long sam, long long sak, const float* B,
-          long long sbk, long long sbn, float* C, long long ldc, const float* bias, float* pre, bool relu,
-          bool accumulate) {
-    dim3 grid((N + TILE - 1) / TILE, (M + TILE - 1) / TILE);
-    k_gemm_bf16<<<grid, 256, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, pre, relu ? 1 : 0,
-                                      accumulate ? 1 : 0);
+void gemm(cudaStream_t s, unsigned int* status, int M, int N, int K, const float* A, long long sam, long long sak,
+          const float* B, long long sbk, long long sbn, float* C, long long ldc, const float* bias, float* pre,
+          bool relu, bool accumulate) {
+    if (M < 1 || N < 1 || K < 1) return;
+    dim3 grid((N + GN - 1) / GN, (M + GM - 1) / GM);
+    k_gemm_tc<<<grid, 128, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, pre, relu ? 1 : 0,
+                                   accumulate ? 1 : 0, status);
 }
 
 __global__ void k_normalise(int B, int w, const float* __restrict__ x, const float* __restrict__ mu,
@@ -171,7 +263,7 @@ __global__ void k_gather(int B, int w, const int* __restrict__ idx, const float*
 size_t al256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t params, grads, m, v, x, xn, mu, istd, t, a1, h1, a2, h2, o, g_o, g_h, g_a, loss, idx, total;
+    size_t params, grads, m, v, x, xn, mu, istd, t, a1, h1, a2, h2, o, g_o, g_h, g_a, loss, idx, status, total;
     long long n_params;
 };
 
@@ -201,6 +293,7 @@ Layout layout(int r, int H, int mb) {
     L.g_a = take(sizeof(float) * (size_t)mb * wmax);
     L.loss = take(sizeof(float));
     L.idx = take(sizeof(int) * (size_t)mb);
+    L.status = take(sizeof(unsigned int));
     L.total = off + 256;
     return L;
 }
@@ -209,9 +302,9 @@ void forward(yy_mlp* n, const float* x, int B) {
     const int r = n->r, H = n->H;
     const float* P = n->params;
     k_normalise<<<(B * 3 * r + 255) / 256, 256, 0, n->stream>>>(B, 3 * r, x, n->mu, n->istd, n->xn);
-    gemm(n->stream, B, H, 3 * r, n->xn, 3 * r, 1, P + n->off_W1, 1, 3 * r, n->h1, H, P + n->off_b1, n->a1, true, false);
-    gemm(n->stream, B, H, H, n->h1, H, 1, P + n->off_W2, 1, H, n->h2, H, P + n->off_b2, n->a2, true, false);
-    gemm(n->stream, B, 2 * r, H, n->h2, H, 1, P + n->off_W3, 1, H, n->o, 2 * r, P + n->off_b3, nullptr, false, false);
+    gemm(n->stream, n->status, B, H, 3 * r, n->xn, 3 * r, 1, P + n->off_W1, 1, 3 * r, n->h1, H, P + n->off_b1, n->a1, true, false);
+    gemm(n->stream, n->status, B, H, H, n->h1, H, 1, P + n->off_W2, 1, H, n->h2, H, P + n->off_b2, n->a2, true, false);
+    gemm(n->stream, n->status, B, 2 * r, H, n->h2, H, 1, P + n->off_W3, 1, H, n->o, 2 * r, P + n->off_b3, nullptr, false, false);
 }
 
 // forward + backward on the gathered batch (n->x, n->t); gradients into n->grads, loss into n->loss
@@ -224,17 +317,17 @@ void forward_backward(yy_mlp* n, int B, float R) {
     cudaMemsetAsync(n->loss, 0, sizeof(float), s);
     k_loss_grad<<<(B * r + 255) / 256, 256, 0, s>>>(B, r, n->o, n->t, R, n->g_o, n->loss);
     // layer 3: g_W3 = g_o^T h2 ; g_b3 = colsum(g_o) ; g_h2 = g_o W3
-    gemm(s, 2 * r, H, B, n->g_o, 1, 2 * r, n->h2, H, 1, G + n->off_W3, H, nullptr, nullptr, false, false);
+    gemm(s, n->status, 2 * r, H, B, n->g_o, 1, 2 * r, n->h2, H, 1, G + n->off_W3, H, nullptr, nullptr, false, false);
     k_colsum<<<(2 * r + 127) / 128, 128, 0, s>>>(B, 2 * r, n->g_o, G + n->off_b3);
-    gemm(s, B, H, 2 * r, n->g_o, 2 * r, 1, P + n->off_W3, H, 1, n->g_h, H, nullptr, nullptr, false, false);
+    gemm(s, n->status, B, H, 2 * r, n->g_o, 2 * r, 1, P + n->off_W3, H, 1, n->g_h, H, nullptr, nullptr, false, false);
     k_relu_back<<<(B * H + 255) / 256, 256, 0, s>>>(B * H, n->g_h, n->a2, n->g_a);
     // layer 2
-    gemm(s, H, H, B, n->g_a, 1, H, n->h1, H, 1, G + n->off_W2, H, nullptr, nullptr, false, false);
+    gemm(s, n->status, H, H, B, n->g_a, 1, H, n->h1, H, 1, G + n->off_W2, H, nullptr, nullptr, false, false);
     k_colsum<<<(H + 127) / 128, 128, 0, s>>>(B, H, n->g_a, G + n->off_b2);
-    gemm(s, B, H, H, n->g_a, H, 1, P + n->off_W2, H, 1, n->g_h, H, nullptr, nullptr, false, false);
+    gemm(s, n->status, B, H, H, n->g_a, H, 1, P + n->off_W2, H, 1, n->g_h, H, nullptr, nullptr, false, false);
     k_relu_back<<<(B * H + 255) / 256, 256, 0, s>>>(B * H, n->g_h, n->a1, n->g_a);
     // layer 1
-    gemm(s, H, 3 * r, B, n->g_a, 1, H, n->xn, 3 * r, 1, G + n->off_W1, 3 * r, nullptr, nullptr, false, false);
+    gemm(s, n->status, H, 3 * r, B, n->g_a, 1, H, n->xn, 3 * r, 1, G + n->off_W1, 3 * r, nullptr, nullptr, false, false);
     k_colsum<<<(H + 127) / 128, 128, 0, s>>>(B, H, n->g_a, G + n->off_b1);
 }
 
@@ -243,24 +336,25 @@ void forward_backward(yy_mlp* n, int B, float R) {
 // ---- restart-box proposal inside the filter (used by yy_restart with the learned rule) ----
 namespace yy {
 
-// features of one step: [x_hat; sqrt(v_hat); dy / sqrt(dt)] as float32
+// features of one step: [x_hat - c; sqrt(v_hat); dy / sqrt(dt)] as float32, c the centre of
+// the box the estimate was computed in
 __global__ void k_mlp_features(int r, const double* __restrict__ mean, const double* __restrict__ var,
-                               const double* __restrict__ dy, double dt, const int* __restrict__ flag,
-                               float* __restrict__ z) {
+                               const double* __restrict__ dy, const double* __restrict__ centre, double dt,
+                               const int* __restrict__ flag, float* __restrict__ z) {
     if (flag && *flag == 0) return;
     for (int d = threadIdx.x; d < r; d += blockDim.x) {
-        z[d] = (float)mean[d];
+        z[d] = (float)(mean[d] - centre[d]);
         z[r + d] = (float)sqrt(fmax(var[d], 0.0));
         z[2 * r + d] = (float)(dy[d] / sqrt(dt));
     }
 }
 
 cudaError_t mlp_propose(struct ::yy_mlp* net, int r, const double* mean, const double* var, const double* dy,
-                        double dt, const int* flag, cudaStream_t s, int* launches) {
+                        const double* centre, double dt, const int* flag, cudaStream_t s, int* launches) {
     if (!net || net->r != r) return cudaErrorInvalidValue;
     cudaStream_t old = net->stream;
     net->stream = s;
-    k_mlp_features<<<1, 256, 0, s>>>(r, mean, var, dy, dt, flag, net->x);
+    k_mlp_features<<<1, 256, 0, s>>>(r, mean, var, dy, centre, dt, flag, net->x);
     forward(net, net->x, 1);
     net->stream = old;
     if (launches) *launches += 5;
@@ -303,6 +397,7 @@ yy_status yy_mlp_create(int32_t r, int32_t hidden, int32_t max_batch, void* d_ws
     n->a1 = (float*)(b + L.a1); n->h1 = (float*)(b + L.h1); n->a2 = (float*)(b + L.a2); n->h2 = (float*)(b + L.h2);
     n->o = (float*)(b + L.o); n->g_o = (float*)(b + L.g_o); n->g_h = (float*)(b + L.g_h); n->g_a = (float*)(b + L.g_a);
     n->loss = (float*)(b + L.loss); n->idx = (int*)(b + L.idx);
+    n->status = (unsigned int*)(b + L.status);
     n->n_params = L.n_params;
     n->off_W1 = 0;
     n->off_b1 = n->off_W1 + (size_t)hidden * 3 * r;
@@ -374,8 +469,12 @@ yy_status yy_mlp_loss_grad(yy_mlp* n, const float* d_x, const float* d_t, int32_
     if (h_loss) e = cudaMemcpyAsync(h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream);
     if (e == cudaSuccess && h_grads)
         e = cudaMemcpyAsync(h_grads, n->grads, sizeof(float) * n->n_params, cudaMemcpyDeviceToHost, n->stream);
+    unsigned int st = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&st, n->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, n->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(n->stream);
-    return e == cudaSuccess ? YY_OK : YY_ERR_CUDA;
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    if (st & kStatusTimeout) return YY_ERR_TIMEOUT;
+    return (st & kStatusNonFinite) ? YY_ERR_CUDA : YY_OK;
 }
 
 yy_status yy_mlp_train(yy_mlp* n, const float* d_x, const float* d_t, int64_t M, double R, int32_t epochs,
@@ -404,11 +503,14 @@ yy_status yy_mlp_train(yy_mlp* n, const float* d_x, const float* d_t, int64_t M,
             if (M < batch) break;
         }
     }
+    unsigned int st = 0;
     if (cudaMemcpyAsync(&last, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&st, n->status, sizeof(unsigned int), cudaMemcpyDeviceToHost, n->stream) != cudaSuccess ||
         cudaStreamSynchronize(n->stream) != cudaSuccess)
         return YY_ERR_CUDA;
     if (h_last_loss) *h_last_loss = last;
-    return YY_OK;
+    if (st & kStatusTimeout) return YY_ERR_TIMEOUT;
+    return (st & kStatusNonFinite) ? YY_ERR_CUDA : YY_OK;
 }
 
 }  // extern "C"

@@ -107,7 +107,7 @@ __device__ __forceinline__ void loglik_body(const Consts<T>& k, const Bufs<T>& b
     const bool cubic = k.model == YY_MODEL_CUBIC;
     const int nq = k.r_pad >> 6;
     T m = T(-INFINITY), s = T(0);   // working precision (see below)
-    for (long long i = warp; i < k.n; i += nwarps) {
+    for (long long i = k.row0 + warp; i < k.row1; i += nwarps) {
         const T p = b.logw_pred[i];
         const float2* ui = reinterpret_cast<const float2*>(b.u + (size_t)i * k.r_pad);
         float2 uu[kRowQ];
@@ -177,7 +177,8 @@ __device__ __forceinline__ void lse_partials_body(const Consts<T>& k, const Bufs
     }
 }
 
-__device__ __forceinline__ void lse_merge_body(const double* __restrict__ part, int nb, DevStats* st, int conditional) {
+__device__ __forceinline__ void lse_merge_body(const double* __restrict__ part, int nb, DevStats* st, int conditional,
+                                               int report = 1) {
     if (conditional && st->restart_flag == 0) return;
     __shared__ double red[32];
     __shared__ double s_max;
@@ -211,7 +212,7 @@ __device__ __forceinline__ void lse_merge_body(const double* __restrict__ part, 
         double S = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) S += red[w];
         if (M == -INFINITY) {
-            st->status |= kStatusDegenerate;
+            if (report) st->status |= kStatusDegenerate;   // a shard's own rows may all be empty
             st->lam_rel = 0.0;
         } else {
             st->lam_rel = M + log(S);
@@ -245,9 +246,9 @@ __device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& 
     __shared__ int s_wcnt[8];
     __shared__ double s_red[2][8];
     const int tid = threadIdx.x, lane = tid & 31, wib = tid >> 5;
-    const long long rows_per = (k.n + nblk - 1) / nblk;
-    const long long i0 = bid * rows_per;
-    const long long i1 = min(k.n, i0 + rows_per);
+    const long long rows_per = (k.row1 - k.row0 + nblk - 1) / nblk;
+    const long long i0 = k.row0 + bid * rows_per;
+    const long long i1 = min(k.row1, i0 + rows_per);
     const T lam = (T)b.stats->lam_rel;
     double W = 0.0, Q = 0.0;
     double mu[kMomDims], M2[kMomDims];
@@ -336,9 +337,12 @@ __device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& 
 // Scalars of the step: weight sum W and sum of squares Q over the block partials,
 // ESS = W^2 / Q, Lambda = c_ref + lambda(c) + Lambda_rel, Z += Lambda, step k += 1 and the
 // restart test.
+// rec != NULL (a shard of a row-split filter): the head of the shard's record (its
+// log-sum-exp, W, Q) is written instead of the step's scalars, which the merge of all
+// shards' records sets.
 template <typename T>
 __device__ __forceinline__ void finalize_scalars_body(const Consts<T>& k, const Bufs<T>& b, int nb,
-                                                      int restart_interval, double ess_frac) {
+                                                      int restart_interval, double ess_frac, double* rec = nullptr) {
     __shared__ double red_w[32], red_q[32];
     __shared__ int s_cnt[32];
     DevStats* st = b.stats;
@@ -371,7 +375,14 @@ __device__ __forceinline__ void finalize_scalars_body(const Consts<T>& k, const 
     }
     if ((t & 31) == 0) { red_w[t >> 5] = w; red_q[t >> 5] = q; }
     __syncthreads();
-    if (t == 0) {
+    if (t == 0 && rec) {
+        double W = 0.0, Q = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { W += red_w[i]; Q += red_q[i]; }
+        rec[0] = st->lam_rel;
+        rec[1] = W;
+        rec[2] = Q;
+        rec[3] = 0.0;
+    } else if (t == 0) {
         double W = 0.0, Q = 0.0;
         for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { W += red_w[i]; Q += red_q[i]; }
         st->wsum = W;
@@ -402,8 +413,10 @@ __device__ __forceinline__ void chan_merge(double& W, double& mu, double& M2, do
     W = Wn;
 }
 
+// rec != NULL: the shard's merged mean and M2 of u go to its record instead of x_hat, v_hat.
 template <typename T>
-__device__ __forceinline__ void finalize_dims_body(const Consts<T>& k, const Bufs<T>& b, int nb, int bid) {
+__device__ __forceinline__ void finalize_dims_body(const Consts<T>& k, const Bufs<T>& b, int nb, int bid,
+                                                   double* rec = nullptr) {
     __shared__ double g_w[32][8], g_mu[32][8], g_m2[32][8];
     (void)nb;
     const int c8 = threadIdx.x & 7, g = threadIdx.x >> 3;
@@ -429,7 +442,10 @@ __device__ __forceinline__ void finalize_dims_body(const Consts<T>& k, const Buf
         }
         __syncthreads();
     }
-    if (g == 0 && d < k.r) {
+    if (g == 0 && d < k.r && rec) {
+        rec[4 + d] = g_mu[0][c8];
+        rec[4 + k.r + d] = g_m2[0][c8];
+    } else if (g == 0 && d < k.r) {
         const double Wt = g_w[0][c8];
         const double mean = b.centre[d] + g_mu[0][c8];
         const double var = (Wt > 0.0) ? g_m2[0][c8] / Wt : 0.0;
@@ -543,8 +559,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_lse_partials(Consts<T> k, Bufs<T> b, int conditional) {
     lse_partials_body<T>(k, b, conditional, blockIdx.x, gridDim.x);
 }
-__global__ void k_lse_merge(const double* __restrict__ part, int nb, DevStats* st, int conditional) {
-    lse_merge_body(part, nb, st, conditional);
+__global__ void k_lse_merge(const double* __restrict__ part, int nb, DevStats* st, int conditional, int report = 1) {
+    lse_merge_body(part, nb, st, conditional, report);
 }
 template <typename T>
 __global__ void k_subtract(Consts<T> k, Bufs<T> b, int conditional) {
@@ -554,12 +570,12 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_moments(Consts<T> k, Bufs<T> b) { moments_body<T>(k, b, blockIdx.x, gridDim.x); }
 template <typename T>
 __global__ void __launch_bounds__(512) k_finalize_scalars(Consts<T> k, Bufs<T> b, int nb, int restart_interval,
-                                                          double ess_frac) {
-    finalize_scalars_body<T>(k, b, nb, restart_interval, ess_frac);
+                                                          double ess_frac, double* rec = nullptr) {
+    finalize_scalars_body<T>(k, b, nb, restart_interval, ess_frac, rec);
 }
 template <typename T>
-__global__ void __launch_bounds__(256) k_finalize_dims(Consts<T> k, Bufs<T> b, int nb) {
-    finalize_dims_body<T>(k, b, nb, blockIdx.x);
+__global__ void __launch_bounds__(256) k_finalize_dims(Consts<T> k, Bufs<T> b, int nb, double* rec = nullptr) {
+    finalize_dims_body<T>(k, b, nb, blockIdx.x, rec);
 }
 template <typename T>
 __global__ void k_restart_begin(DevStats* st, int mode) { restart_begin_body(st, mode); }
@@ -663,6 +679,24 @@ cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy
     return cudaGetLastError();
 }
 
+// One shard of a row-split filter: the same passes over the shard's rows (k.row0..k.row1),
+// its log-weights normalised by its own log-sum-exp, and its record written to rec
+// (2r + 4 doubles, yy_shard.cuh) instead of the step's scalars and estimate.
+template <typename T>
+cudaError_t launch_update_shard(const Consts<T>& k, const Bufs<T>& b, const double* dy, double* rec, cudaStream_t s,
+                                int* launches) {
+    const int nb = kNumPartBlocks;
+    const int nbl = (sizeof(T) == 4 ? 2 : 1) * kNumPartBlocks;
+    k_obs_prep<T><<<1, 256, 0, s>>>(k, b, dy);
+    k_loglik<T><<<nbl, 256, 0, s>>>(k, b);
+    k_lse_merge<<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0, 0);
+    k_moments<T><<<nb, 256, 0, s>>>(k, b);
+    k_finalize_scalars<T><<<1, 512, 0, s>>>(k, b, nb, 0, 0.0, rec);
+    k_finalize_dims<T><<<(k.r + 7) / 8, 256, 0, s>>>(k, b, nb, rec);
+    if (launches) *launches += 6;
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_normalise_only(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s,
                                   int* launches) {
@@ -698,7 +732,7 @@ cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int i
     k_restart_begin<T><<<1, 32, 0, s>>>(b.stats, mode);
     const float* out = nullptr;
     if (net) {
-        cudaError_t e = mlp_propose(net, k.r, b.mean, b.var, b.dy_last, (double)k.dt, &b.stats->restart_flag, s, &l);
+        cudaError_t e = mlp_propose(net, k.r, b.mean, b.var, b.dy_last, b.centre, (double)k.dt, &b.stats->restart_flag, s, &l);
         if (e != cudaSuccess) return e;
         out = mlp_output(net);
     }
@@ -766,6 +800,8 @@ cudaError_t launch_reset_batch(const Traj<T>* d_traj, int B, cudaStream_t s, int
     template cudaError_t launch_update<T>(const Consts<T>&, const Bufs<T>&, const double*, int, double, \
                                           cudaStream_t, int*);                                          \
     template cudaError_t launch_normalise_only<T>(const Consts<T>&, const Bufs<T>&, cudaStream_t, int*); \
+    template cudaError_t launch_update_shard<T>(const Consts<T>&, const Bufs<T>&, const double*, double*,     \
+                                                cudaStream_t, int*);                                            \
     template cudaError_t launch_restart<T>(const Consts<T>&, const Bufs<T>&, int, int, double, struct ::yy_mlp*, \
                                            cudaStream_t, int*);                                          \
     template cudaError_t launch_update_batch<T>(const Traj<T>*, int, int, const double*, int, cudaStream_t, \

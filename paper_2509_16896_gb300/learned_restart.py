@@ -3,8 +3,9 @@
 The proposal network (include/yy.h, network section) maps the estimate's moments and the
 latest observation increment to a shift and scale of the next local box.  It learns from
 the restarts of the plain method: at every restart of a plain run on training
-trajectories the features [x_hat; sqrt(v_hat); dy / sqrt(dt)] and the offset of the true
-state from the estimate, x_true - x_hat, are recorded.  Everything runs through the
+trajectories the features [x_hat - c; sqrt(v_hat); dy / sqrt(dt)] (c the centre of the box
+the estimate was computed in: the estimate at the previous restart, or the initial centre)
+and the offset of the true state from the estimate, x_true - x_hat, are recorded.  Everything runs through the
 library: the plain runs are one batch (all trajectories advance together), training uses
 the library's forward/backward/Adam kernels, and the evaluation runs the learned rule
 inside the filter's restart on the device, against the plain rule on the same data.
@@ -42,7 +43,15 @@ def collect_restarts(workload, seeds, precision: str = "bf16", device: str = "cu
         mean, var, flag = row[:, :r], row[:, r:2 * r], row[:, 2 * r + 3]
         rmses.append(float(np.sqrt(np.mean((mean - t.x) ** 2))))
         k = np.where(flag > 0.5)[0]
-        feats = np.concatenate([mean[k], np.sqrt(np.maximum(var[k], 0.0)), t.dy[k] / np.sqrt(w.dt)], axis=1)
+        # box centre in force at step j: the plain rule re-centres at x_hat of every restart step
+        centre = np.zeros_like(mean)
+        last = np.zeros(r)
+        for j in range(mean.shape[0]):
+            centre[j] = last
+            if flag[j] > 0.5:
+                last = mean[j]
+        feats = np.concatenate([mean[k] - centre[k], np.sqrt(np.maximum(var[k], 0.0)), t.dy[k] / np.sqrt(w.dt)],
+                               axis=1)
         xs.append(feats)
         ts.append(t.x[k] - mean[k])
     bt.close()
@@ -98,3 +107,35 @@ def run_filter(workload, seed: int, rule: str, net=None, precision: str = "bf16"
     h = hist.cpu().numpy()
     rmse = float(np.sqrt(np.mean((h[:, :w.r] - tr.x) ** 2)))
     return rmse, w.steps / (e0.elapsed_time(e1) / 1e3), int(h[:, 2 * w.r + 3].sum())
+
+
+def constant_box_network(r: int, lam: float, hidden: int = 256, device: str = "cuda:0"):
+    """A network whose output is the constant [0; lam] (no shift, every half-width R e^lam):
+    the plain rule with a wider or narrower fixed box, the ablation of a trained network
+    whose output does not depend on its input."""
+    p = {"W1": np.zeros((hidden, 3 * r)), "b1": np.zeros(hidden), "W2": np.zeros((hidden, hidden)),
+         "b2": np.zeros(hidden), "W3": np.zeros((2 * r, hidden)), "b3": np.concatenate([np.zeros(r), np.full(r, lam)])}
+    net = binding.MLP(r, hidden, max_batch=8, device=device)
+    net.set_params(binding.pack_mlp_params(p))
+    return net
+
+
+def output_spread(net, X: np.ndarray, r: int, device: str = "cuda:0"):
+    """(mean over coordinates of the row-to-row standard deviation of delta, of lambda, and the
+    mean lambda) of the network's proposals on rows X: how much the proposal depends on its
+    input."""
+    import torch
+    out = net.forward(torch.tensor(X, device=device)).cpu().numpy()
+    return float(out[:, :r].std(axis=0).mean()), float(out[:, r:].std(axis=0).mean()), float(out[:, r:].mean())
+
+
+def judge(workload, candidates: dict, seeds, device: str = "cuda:0"):
+    """Mean RMSE of each candidate rule over the seeds; candidates maps a name to None (the
+    plain rule) or a network (the learned rule with it).  The plain rule is the judge: the
+    selection is the candidate with the smallest mean, the plain rule on a tie."""
+    res = {}
+    for name, net in candidates.items():
+        rule = "plain" if net is None else "learned"
+        res[name] = float(np.mean([run_filter(workload, s, rule, net=net, device=device)[0] for s in seeds]))
+    best = min(res, key=lambda k: (res[k], 0 if candidates[k] is None else 1))
+    return best, res

@@ -4,10 +4,14 @@ screen and FP32 form), whole runs with interval restarts, and the linear-Gaussia
 against the exact discrete Kalman filter.
 
 Bars: 1e-5 relative for the step-local outputs (the float32 bar of the single-filter
-parity tests); 1e-4 absolute on posterior means over whole runs; for the Kalman
+parity tests); over whole runs every step's posterior mean within 1e-3 x state scale (the
+RMS of the true trajectory) of the oracle's, and the RMSE likewise; for the Kalman
 comparison, the batch's RMS deviation from the Kalman mean within 1e-3 sqrt(P_inf) of the
 oracle's own deviation (the method's quadrature error is the oracle's; the batch must
-reproduce it), and below 0.01 sqrt(P_inf) for the global-box members."""
+reproduce it); in absolute terms below 0.005 sqrt(P_inf) at n = 4096, the size the oracle
+itself is pinned at (measured 4.2e-4), and reported at node counts that are not powers of
+two, whose scrambled Sobol sets are not complete nets and integrate less evenly (measured
+9.5e-3 at n = 3001 and 1.9e-2 at n = 5000, the oracle's values to four digits)."""
 import math
 
 import numpy as np
@@ -120,6 +124,16 @@ def _whole_runs(members, N, K, restart_interval, paths):
     return out
 
 
+def _assert_whole_run(tr, gpu, ref, b):
+    scale = float(np.sqrt(np.mean(tr.x ** 2)))
+    err = float(np.max(np.abs(gpu - ref)))
+    rm_g = float(np.sqrt(np.mean((gpu - tr.x) ** 2)))
+    rm_o = float(np.sqrt(np.mean((ref - tr.x) ** 2)))
+    print(f"member {b}: max |x_hat - oracle| {err:.2e}, RMSE gpu {rm_g:.6f} oracle {rm_o:.6f} (scale {scale:.3f})")
+    assert err <= 1e-3 * scale, b
+    assert abs(rm_g - rm_o) <= 1e-3 * scale, b
+
+
 def test_batch_linear_members_follow_the_kalman_filter(yy_lib):
     """Global box (R = 6), first-order kernel, no restart: the linear-Gaussian members track
     the exact discrete Kalman filter as the oracle does (reading A4: the Kalman pin uses
@@ -130,7 +144,7 @@ def test_batch_linear_members_follow_the_kalman_filter(yy_lib):
                ("cubic", 2, 1024, 4.0, 84)]
     res = _whole_runs(members, 1, K, 0, paths=[0, 1, 0, 1])
     for b, (tr, gpu, ref, fg, fr) in enumerate(res):
-        assert np.max(np.abs(gpu - ref)) <= 1e-4, b
+        _assert_whole_run(tr, gpu, ref, b)
         if members[b][0] != "linear":
             continue
         km, _ = kalman.kalman_filter(tr.dy, -0.5, 0.01)
@@ -138,7 +152,8 @@ def test_batch_linear_members_follow_the_kalman_filter(yy_lib):
         dev_ref = float(np.sqrt(np.mean((ref - km) ** 2)))
         print(f"member {b}: RMS |x_hat - KF| gpu {dev_gpu:.3e} oracle {dev_ref:.3e} (sqrt P_inf {math.sqrt(P_INF):.3f})")
         assert abs(dev_gpu - dev_ref) <= 1e-3 * math.sqrt(P_INF), b
-        assert dev_gpu <= 0.01 * math.sqrt(P_INF), b
+        if members[b][2] == 4096:
+            assert dev_gpu <= 0.005 * math.sqrt(P_INF), b
 
 
 def test_batch_local_box_members_match_oracle_runs(yy_lib):
@@ -153,7 +168,7 @@ def test_batch_local_box_members_match_oracle_runs(yy_lib):
     res = _whole_runs(members, 2, K, 2, paths=[1, 0, 0, 1])
     for b, (tr, gpu, ref, fg, fr) in enumerate(res):
         assert np.array_equal(fg, fr), b
-        assert np.max(np.abs(gpu - ref)) <= 1e-4, b
+        _assert_whole_run(tr, gpu, ref, b)
         if members[b][0] == "linear":
             km, _ = kalman.kalman_filter(tr.dy, -0.5, 0.01)
             dev_gpu = float(np.sqrt(np.mean((gpu - km) ** 2)))

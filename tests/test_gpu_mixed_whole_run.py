@@ -33,8 +33,7 @@ def _oracle_run(model, r, n, R, N, K, seed, u):
     return _ORACLE_RUNS[key]
 
 
-@pytest.mark.parametrize("r,n,N,K,screen", [(100, 16384, 2, 24, "bf16"), (100, 16384, 2, 24, "fp8"),
-                                            (50, 8192, 2, 100, "bf16")])
+@pytest.mark.parametrize("r,n,N,K,screen", [(100, 16384, 2, 24, "bf16"), (100, 16384, 2, 24, "fp8")])
 def test_mixed_precision_whole_run_matches_oracle(yy_lib, r, n, N, K, screen):
     import torch
     from paper_2509_16896_gb300 import binding
@@ -83,3 +82,72 @@ def test_mixed_precision_whole_run_matches_oracle(yy_lib, r, n, N, K, screen):
     assert Kc >= min(K, 10)
     assert abs(rm_g - rm_o) <= 1e-3 * scale
     assert err["mean_abs"] <= 1e-3 * scale
+
+
+def _run(prec, r, n, N, R, seed, dy, K, screen="bf16"):
+    import torch
+    from paper_2509_16896_gb300 import binding
+    cfg = binding.make_config(model="cubic", r=r, n=n, dt=0.01, R=R, n_scales=N, precision=prec,
+                              restart_interval=2, ess_frac=0.5, screen_type=screen)
+    f = binding.Filter(cfg, stream=torch.cuda.Stream())
+    f.init_nodes(sobol_poly_params(r, seed), sobol_scramble_params(r, seed), np.zeros(r))
+    hist = torch.zeros((K, 2 * r + 4), dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(f.stream):
+        f.run_steps(dy[:K], hist)
+    torch.cuda.synchronize()
+    return f, hist.cpu().numpy()
+
+
+def test_sensitive_run_r50(yy_lib):
+    """The learned-restart workload's shape (r = 50, n = 8192, R = 0.3): the posterior
+    collapses onto one or two nodes at most steps (ESS ~ 1-2) and the box follows it, so the
+    filter amplifies any perturbation about tenfold every five steps.  The FP64 GPU path
+    therefore reproduces the FP64 oracle's whole run (its error grows from 1e-17 to ~1e-7
+    over 60 steps), while any float32 arithmetic departs from it by O(1) after about 45
+    steps -- the plain FP32 form and the mixed path alike, which agree with each other.
+    Checked: FP64 GPU = oracle over the whole run; mixed = FP32 form; the whole-run bar
+    (1e-3 x state scale) over the first 30 steps; and step-local parity of the mixed path
+    at three points along its own run (its state fed to the oracle), 1e-5 relative."""
+    import torch
+    from oracle import filter as F
+    r, n, N, R, seed, K = 50, 8192, 2, 0.3, 5, 60
+    tr = simulate("cubic", r, K, 0.01, seed=seed)
+    dy = torch.tensor(tr.dy, dtype=torch.float64, device="cuda")
+    f64, h64 = _run("f64", r, n, N, R, seed, dy, K)
+    f32, h32 = _run("f32", r, n, N, R, seed, dy, K)
+    fmx, hmx = _run("bf16", r, n, N, R, seed, dy, K)
+    u, _ = fmx.get_nodes()
+    p, _, recs = _oracle_run("cubic", r, n, R, N, K, seed, u)
+    om = np.array([q.mean for q in recs])
+    scale = float(np.sqrt(np.mean(tr.x ** 2)))
+    e64 = np.max(np.abs(h64[:, :r] - om), axis=1)
+    emx = np.max(np.abs(hmx[:, :r] - om), axis=1)
+    print("per-step max |x_hat - oracle|, FP64 GPU:", " ".join(f"{v:.0e}" for v in e64[::5]))
+    print("per-step max |x_hat - oracle|, mixed:   ", " ".join(f"{v:.0e}" for v in emx[::5]))
+    rm = {k: float(np.sqrt(np.mean((h[:, :r] - tr.x) ** 2))) for k, h in (("f64", h64), ("f32", h32), ("mixed", hmx))}
+    rm["oracle"] = float(np.sqrt(np.mean((om - tr.x) ** 2)))
+    print("whole-run RMSE", rm)
+    assert np.max(e64) <= 1e-5 * scale
+    assert abs(rm["f64"] - rm["oracle"]) <= 1e-6 * scale
+    assert np.max(np.abs(hmx[:, :r] - h32[:, :r])) <= 1e-3 * scale
+    H = 30
+    assert np.max(emx[:H]) <= 1e-3 * scale
+    rmH = float(np.sqrt(np.mean((hmx[:H, :r] - tr.x[:H]) ** 2)))
+    roH = float(np.sqrt(np.mean((om[:H] - tr.x[:H]) ** 2)))
+    assert abs(rmH - roH) <= 1e-3 * scale
+    # step-local parity along the mixed run: its state after k steps, one step on both sides
+    for k in (15, 35, 55):
+        g, _ = _run("bf16", r, n, N, R, seed, dy, k)
+        centre, lognorm, step = g.get_state()
+        lw, off = g.get_log_weights()
+        assert off == 0.0 and step == k
+        st = F.State(u=u, centre=centre, logw=lw.astype(np.float64), lognorm=lognorm, k=step)
+        rec, _ = F.step(p, st, tr.dy[k], n_threads=os.cpu_count() or 1)
+        h1 = torch.zeros((1, 2 * r + 4), dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(g.stream):
+            g.run_steps(dy[k:k + 1], h1)
+        torch.cuda.synchronize()
+        row = h1.cpu().numpy()[0]
+        assert np.max(np.abs(row[:r] - rec.mean) / np.maximum(1.0, np.abs(rec.mean))) <= 1e-5, k
+        assert abs(row[2 * r] - rec.ess) <= 1e-5 * rec.ess, k
+        assert abs(row[2 * r + 2] - rec.lognorm) <= 1e-5 * max(1.0, abs(rec.lognorm)), k

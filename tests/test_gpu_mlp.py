@@ -46,18 +46,26 @@ def test_forward_and_gradients_match_oracle(yy_lib):
     o_ref, cache = mlp.forward(p, X.astype(np.float64))
     assert np.linalg.norm(o_gpu - o_ref) <= 1e-2 * np.linalg.norm(o_ref)
     loss, g = net.loss_grad(xd, td, R)
+    g_gpu = binding.unpack_mlp_params(g, r, H)
+    # The kernels round both operands of every product to bfloat16 and accumulate in float32
+    # on the tensor cores.  The oracle fed the same rounding (its rnd hook) computes the exact
+    # products of the rounded operands, so what remains is float32 accumulation and the rare
+    # operand that rounds the other way because its float32 value differs in the last bit:
+    # the bar of 1e-2 relative (norm-wise) holds with room to spare.
+    o_rb, cache_rb = mlp.forward(p, X.astype(np.float64), rnd=_bf16)
+    L_rb, g_o_rb = mlp.loss_and_grad_out(o_rb, T.astype(np.float64), R)
+    g_rb = mlp.backward(p, cache_rb, g_o_rb, rnd=_bf16)
+    assert np.linalg.norm(o_gpu - o_rb) <= 1e-3 * np.linalg.norm(o_rb)
+    assert loss == pytest.approx(L_rb, rel=1e-3)
+    errs = {}
+    for k in mlp.TRAINED:
+        errs[k] = float(np.linalg.norm(g_gpu[k] - g_rb[k]) / np.linalg.norm(g_rb[k]))
+        assert errs[k] <= 1e-2, (k, errs[k])
+    # against the unrounded FP64 gradients: the BF16 operand rounding itself (reported)
     L_ref, g_o = mlp.loss_and_grad_out(o_ref, T.astype(np.float64), R)
     g_ref = mlp.backward(p, cache, g_o)
-    assert loss == pytest.approx(L_ref, rel=1e-2)
-    g_gpu = binding.unpack_mlp_params(g, r, H)
-    # Every product rounds both operands to bfloat16 (unit roundoff u = 2^-8), so a gradient
-    # that passes through d products (3 forward + 1..3 backward) is within 2 u d of the
-    # exact one, norm-wise, to first order: W3 d = 4, W2 d = 5, W1 d = 6.
-    u = 2.0 ** -8
-    depth = {"W3": 4, "b3": 3, "W2": 5, "b2": 4, "W1": 6, "b1": 5}
-    for k in mlp.TRAINED:
-        err = np.linalg.norm(g_gpu[k] - g_ref[k]) / np.linalg.norm(g_ref[k])
-        assert err <= 2 * u * depth[k], (k, err)
+    exact = {k: float(np.linalg.norm(g_gpu[k] - g_ref[k]) / np.linalg.norm(g_ref[k])) for k in mlp.TRAINED}
+    print("gradient error vs oracle with BF16 operands", errs, "vs FP64 oracle", exact)
 
 
 def test_training_reduces_the_loss(yy_lib):
@@ -109,7 +117,7 @@ def test_learned_restart_matches_oracle(yy_lib, lam0, accepted):
     cen, half = flt.get_box()
     prob = oracle_problem("cubic", r, n, 0.01, R, 2)
     prob.restart_rule, prob.mlp_params = "learned", p
-    c_ref, h_ref, ok = mlp.proposal(p, mean, var, tr.dy[0], 0.01, prob.R)
+    c_ref, h_ref, ok = mlp.proposal(p, mean, var, tr.dy[0], 0.01, prob.R, np.zeros(r))
     assert ok == accepted
     assert np.allclose(cen, c_ref, rtol=0, atol=1e-12) and np.allclose(half, h_ref, rtol=1e-12, atol=0)
     y, _ = sobol.nodes(poly, scr, n, R)
@@ -130,18 +138,28 @@ def test_learned_restart_matches_oracle(yy_lib, lam0, accepted):
 
 
 def test_trained_proposal_against_plain_rule(yy_lib):
-    """Trains the network on restarts of plain runs (16 training trajectories) and runs
-    both rules on held-out trajectories.  Reports the RMSE of each; the learned rule must
-    run and stay finite, and its gain (or loss) is printed."""
+    """Trains the network on restarts of plain runs (16 training trajectories), then judges
+    three rules on 3 validation seeds with the plain rule as the judge (the plain rule, the
+    constant box that training settles on -- the network's mean lambda with no shift -- and
+    the network) and compares the selected rule with the plain rule on 3 held-out test
+    seeds.  Asserted: the selection does not lose more than 3 % RMSE to the plain rule on
+    the test seeds (validation and test seeds differ), and a rule judged worse than the plain
+    rule on validation is never selected.  Reported: every RMSE and how much the network's
+    proposal varies with its input (on this workload it does not: the restart features carry
+    no usable information about the filter's error, and training settles on a constant)."""
     from paper_2509_16896_gb300 import learned_restart as LR
     from synth import WORKLOADS
     w = WORKLOADS["cubic_r50_n8192"].with_(n=4096, steps=150)
     X, T, _ = LR.collect_restarts(w, seeds=list(range(100, 116)))
     assert X.shape[0] > 500 and np.all(np.isfinite(X)) and np.all(np.isfinite(T))
-    net, loss = LR.train_proposal(w.r, X, T, w.R, hidden=256, epochs=10, batch=256, lr=1e-3, seed=1)
+    net, loss = LR.train_proposal(w.r, X, T, w.R, hidden=256, epochs=30, batch=256, lr=1e-3, seed=1)
     assert np.isfinite(loss)
-    res = {}
-    for rule in ("plain", "learned"):
-        res[rule] = [LR.run_filter(w, s, rule, net=net)[0] for s in (5, 6)]
-    print("RMSE plain", res["plain"], "learned", res["learned"])
-    assert np.all(np.isfinite(res["learned"]))
+    sd_delta, sd_lam, lam_mean = LR.output_spread(net, X, w.r)
+    const = LR.constant_box_network(w.r, lam_mean)
+    cands = {"plain": None, "constant_box": const, "network": net}
+    best, val = LR.judge(w, cands, seeds=(5, 6, 7))
+    _, test = LR.judge(w, cands, seeds=(8, 9, 10))
+    print(f"proposal spread over inputs: delta {sd_delta:.2e}, lambda {sd_lam:.2e} (mean lambda {lam_mean:.3f}); "
+          f"validation RMSE {val}; test RMSE {test}; selected {best}")
+    assert val[best] <= val["plain"]
+    assert test[best] <= 1.03 * test["plain"]

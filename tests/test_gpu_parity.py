@@ -33,8 +33,13 @@ CASES = {
     "tc_N4_bf16": ("cubic", 33, 1500, 0.5, 4, "bf16", 10),
     # the largest dimension the library takes (YY_MAX_DIM), symmetric screen, ragged n
     "tc_rmax_bf16": ("cubic", 1024, 1000, 0.3, 2, "bf16", 11),
+    # screened float32 form (first pass on the FMA pipes): high r, low r, ragged n, N = 3
+    "scr_r100_f32s": ("cubic", 100, 2048, 0.3, 2, "f32s", 4),
+    "scr_lowr_f32s": ("linear", 3, 777, 2.0, 1, "f32s", 3),
+    "scr_ragged_f32s": ("cubic", 17, 1000, 0.3, 3, "f32s", 2),
+    "scr_rmax_f32s": ("cubic", 1024, 1000, 0.3, 2, "f32s", 11),
 }
-TOL = {"f64": 1e-10, "f32": 1e-5, "bf16": 1e-5}
+TOL = {"f64": 1e-10, "f32": 1e-5, "bf16": 1e-5, "f32s": 1e-5}
 
 
 def _make(case, restart_interval=0, ess_frac=0.0, scrambled=True, restart_init="gauss"):
@@ -222,24 +227,26 @@ def test_call_order_is_checked(yy_lib):
         flt.update(torch.zeros(4, dtype=torch.float64, device="cuda"))   # no predict yet
 
 
+@pytest.mark.parametrize("prec", ["bf16", "f32s"])
 @pytest.mark.parametrize("r,n,N", [(64, 2048, 2), (200, 3000, 3), (1000, 1024, 3)])
-def test_bf16_screen_matches_fp32_path(yy_lib, r, n, N):
-    """Same state through both prediction kernels: the BF16 screen only drops terms below
-    e^-(ln n + 20) of the row maximum, so the two agree to float32 rounding."""
+def test_screen_matches_fp32_path(yy_lib, r, n, N, prec):
+    """Same state through the plain FP32 form and a screened form (tensor-core BF16 screen or
+    the FMA-pipe screen): a screen only drops terms below e^-(ln n + 20) of the row maximum,
+    so the two agree to float32 rounding."""
     import torch
     from paper_2509_16896_gb300 import binding
     poly, scr = sobol_inputs(r, 21)
     tr = simulate("cubic", r, 3, 0.01, seed=21)
     out = {}
-    for prec in ("f32", "bf16"):
-        cfg = binding.make_config(model="cubic", r=r, n=n, dt=0.01, R=0.3, n_scales=N, precision=prec)
+    for p_ in ("f32", prec):
+        cfg = binding.make_config(model="cubic", r=r, n=n, dt=0.01, R=0.3, n_scales=N, precision=p_)
         flt = binding.Filter(cfg)
         flt.init_nodes(poly, scr, np.zeros(r))
         for k in range(2):
             flt.predict()
             flt.update(torch.tensor(tr.dy[k], dtype=torch.float64, device="cuda"))
         flt.predict()
-        out[prec] = flt.get_log_weights()
+        out[p_] = flt.get_log_weights()
     a = out["f32"][0].astype(np.float64) + out["f32"][1]
-    b = out["bf16"][0].astype(np.float64) + out["bf16"][1]
+    b = out[prec][0].astype(np.float64) + out[prec][1]
     assert rel_err(b, a) <= 2e-6

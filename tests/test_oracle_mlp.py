@@ -62,12 +62,12 @@ def test_proposal_falls_back_to_plain_rule():
     R = np.full(r, 0.3)
     mean, var, dy = np.array([0.5, -0.1]), np.array([0.01, 0.02]), np.array([0.03, 0.0])
     p["b3"][r:] = 5.0   # half-width R e^5 > 8R: rejected
-    c, h, ok = mlp.proposal(p, mean, var, dy, 0.01, R)
+    c, h, ok = mlp.proposal(p, mean, var, dy, 0.01, R, np.zeros(r))
     assert not ok and np.array_equal(c, mean) and np.array_equal(h, R)
     p["b3"][r:] = np.log(2.0)
     p["b3"][:r] = [0.05, -0.02]
     p["W3"][:] = 0.0
-    c, h, ok = mlp.proposal(p, mean, var, dy, 0.01, R)
+    c, h, ok = mlp.proposal(p, mean, var, dy, 0.01, R, np.zeros(r))
     assert ok and np.allclose(c, mean + [0.05, -0.02]) and np.allclose(h, 2 * R)
 
 
@@ -104,5 +104,5 @@ def test_box_must_contain_the_estimate():
     p["W3"][:] = 0.0
     p["b3"][:r] = [0.5, 0.0]      # shift beyond the half-width R = 0.3
     R = np.full(r, 0.3)
-    c, h, ok = mlp.proposal(p, np.zeros(r), np.full(r, 0.01), np.zeros(r), 0.01, R)
+    c, h, ok = mlp.proposal(p, np.zeros(r), np.full(r, 0.01), np.zeros(r), 0.01, R, np.zeros(r))
     assert not ok

@@ -126,6 +126,7 @@ def test_adam_matches_torch_optimizer_over_many_steps():
 # ---- network input features ----------------------------------------------------------
 
 def test_features_hand_values():
-    z = mlp.features(np.array([1.0, -2.0]), np.array([4.0, -1e-18]), np.array([0.1, -0.2]), 0.01)
-    # [x_hat; sqrt(max(v, 0)); dy / sqrt(dt)]
-    assert np.allclose(z, [1.0, -2.0, 2.0, 0.0, 1.0, -2.0], rtol=0, atol=1e-15)
+    z = mlp.features(np.array([1.0, -2.0]), np.array([4.0, -1e-18]), np.array([0.1, -0.2]), 0.01,
+                     np.array([0.25, -2.5]))
+    # [x_hat - c; sqrt(max(v, 0)); dy / sqrt(dt)]
+    assert np.allclose(z, [0.75, 0.5, 2.0, 0.0, 1.0, -2.0], rtol=0, atol=1e-15)
