@@ -29,7 +29,10 @@
  *     every weight zero, a wait that timed out) set a sticky status word that
  *     yy_estimate returns.
  *   - Models.  m = r; h is componentwise.  YY_MODEL_CUBIC: f(x) = cos x, h(x) = x^3.
- *     YY_MODEL_LINEAR: f(x) = a x, h(x) = x.
+ *     YY_MODEL_LINEAR: f(x) = a x, h(x) = x.  YY_MODEL_PAPER_E1 (the paper's large-scale
+ *     scalability test, Section 9 "Large-Scale Scalability Test"): f(x) = sin(x) (A x) +
+ *     sin(2x) (A1 x) elementwise with A, A1 upper bidiagonal (diagonal -0.5 / -0.3,
+ *     superdiagonal 0.1 / 0.3), h(x) = (x - 100)^3.
  *   - Layout.  Node coordinates are float32 box coordinates u (x = c + u), rows of
  *     r values, row-major; host arrays passed in or out are dense [n][r].
  */
@@ -70,7 +73,11 @@ typedef enum {
     YY_ERR_UNSUPPORTED = 8   /* configuration not supported by this build */
 } yy_status;
 
-typedef enum { YY_MODEL_CUBIC = 0, YY_MODEL_LINEAR = 1 } yy_model;
+typedef enum { YY_MODEL_CUBIC = 0, YY_MODEL_LINEAR = 1, YY_MODEL_PAPER_E1 = 2 } yy_model;
+
+/* Node sets (Appendix A): scrambled Sobol (yy_init_nodes), or Halton / Faure
+ * (yy_init_nodes_lds), the paper's choices for low dimension. */
+typedef enum { YY_NODES_SOBOL = 0, YY_NODES_HALTON = 1, YY_NODES_FAURE = 2 } yy_nodes;
 
 /* Arithmetic of the prediction step.  FP64: every step in float64.  FP32: exact
  * float32 differences over every pair.  BF16: a tcgen05 BF16 Gram product screens out pairs
@@ -99,6 +106,17 @@ typedef enum { YY_RESTART_PLAIN = 0, YY_RESTART_LEARNED = 1 } yy_restart_rule;
  * power of two (bound 0.135 |u_i||u_s| plus a term for subnormal coordinates; twice the
  * tensor rate, half the operand bytes, first-pass chunks of 128 coordinates). */
 typedef enum { YY_SCREEN_BF16 = 0, YY_SCREEN_FP8 = 1 } yy_screen_type;
+
+/* Noise coefficients (Section "General Nonlinear Filtering with Noise Coefficients"):
+ * dX = f dt + U(X) dV, dY = h dt + V(X) dW.  UNIT: U = V = I.  DIAG: diagonal and
+ * state-dependent, U_d(x) = noise_u (1 + noise_u_kappa sin^2 x_d), zero for the first
+ * noise_u_zero coordinates (then a = U U^T is singular and its pseudo-inverse is used),
+ * V_d(x) = noise_v (1 + noise_v_kappa sin^2 x_d).  The kernel takes the metric a(x)^+ of the
+ * target and -1/2 log det_+ a(x) (the table's kernel row, as printed: its prefactor keeps
+ * (2 pi dt)^(-r/2)); the update weighs h and dy by b(x)^-1.  DIAG runs in FP64 and FP32
+ * precision with the cubic or linear model; other combinations return YY_ERR_UNSUPPORTED
+ * from yy_create. */
+typedef enum { YY_NOISE_UNIT = 0, YY_NOISE_DIAG = 1 } yy_noise;
 
 /* yy_restart modes: AUTO applies the device-side test computed by the last yy_update
  * (ESS < ess_frac * n, or restart_interval >= 2 and step % restart_interval == 0);
@@ -133,6 +151,10 @@ typedef struct {
                                 * screen's Gram product. Results do not depend on it beyond
                                 * float32 rounding (the screen's bound covers the operand
                                 * rounding). */
+    int32_t noise;             /* yy_noise (0 = unit noise) */
+    int32_t noise_u_zero;      /* DIAG: leading coordinates without state noise, 0..r */
+    double noise_u, noise_u_kappa;   /* DIAG: U_d(x) = noise_u (1 + noise_u_kappa sin^2 x_d); > 0, >= 0 */
+    double noise_v, noise_v_kappa;   /* DIAG: V_d(x) = noise_v (1 + noise_v_kappa sin^2 x_d); > 0, >= 0 */
 } yy_config;
 
 /* Bytes of device workspace that yy_create needs for cfg (0 if cfg is invalid). */
@@ -163,6 +185,18 @@ YY_EXPORT yy_status yy_destroy(yy_filter* f);
  * the scrambled 32-bit integer of point i (indices 0..n-1, Gray-code order). */
 YY_EXPORT yy_status yy_init_nodes(yy_filter* f, const uint32_t* h_poly, const uint32_t* h_scramble,
                         const double* h_center, const double* h_halfwidth);
+
+/* Node generation with Halton or Faure points (Appendix A, "Halton Sequence", "Faure
+ * Sequence"), otherwise as yy_init_nodes (prior weights, Dirichlet mask).  kind:
+ * YY_NODES_HALTON (coordinate d: radical inverse in the d-th prime) or YY_NODES_FAURE (one
+ * base, the smallest prime >= r; generator matrices the powers of the Pascal matrix mod
+ * that base).  Point i of the node set is sequence index i + 1 (index 0 is the corner of
+ * the box).  Coordinates u = R_d (2 phi - 1) in float64, rounded to float32, phi the point's
+ * coordinate in [0, 1) evaluated exactly (digit integer over p^M, p^M <= 2^53, one rounding).
+ * h_center, h_halfwidth as for yy_init_nodes.  A filter with these nodes does not take the
+ * learned restart (its re-mapping of nodes is defined for Sobol points): yy_set_restart_mlp
+ * then returns YY_ERR_UNSUPPORTED. */
+YY_EXPORT yy_status yy_init_nodes_lds(yy_filter* f, int32_t kind, const double* h_center, const double* h_halfwidth);
 
 /* Writes the scrambled Sobol integers of points first..first+count-1 to d_bits
  * (device uint32 [count][r], caller-owned).  Same generator as yy_init_nodes. */

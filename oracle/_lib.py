@@ -36,6 +36,7 @@ def lib() -> ctypes.CDLL:
                 ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                 ctypes.c_int32, ctypes.c_void_p, ctypes.c_double,
-                ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32]
+                ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int32,
+                ctypes.c_void_p, ctypes.c_void_p]
             _lib = L
     return _lib

@@ -15,7 +15,12 @@
  *                       - (y - x) . f(x) - (tau/2) (2 div f(x) + |f(x)|^2),
  *
  * where x (first argument) is the evaluation point and y the integration variable
- * (Remark after eq. L_Delta_t), and w_q = prod_d (2 R_d) / n is the quadrature
+ * (Remark after eq. L_Delta_t); with state-dependent noise coefficients (Section "General
+ * Nonlinear Filtering with Noise Coefficients", kernel row of its table) the squared norms
+ * and the inner product take the metric a(x)^-1 (its pseudo-inverse when a(x) is singular)
+ * of the evaluation point and log K gains -1/2 log det a(x) (det over the positive
+ * eigenvalues); here a(x) is diagonal, passed as minv[i][d] = 1/a_d(x_i) (0 where
+ * a_d(x_i) = 0) and hld[i] = 1/2 sum log a_d(x_i) over the positive a_d.  And w_q = prod_d (2 R_d) / n is the quadrature
  * volume per node that turns the integral into a sum over the nodes (the "Delta y"
  * factor of that Remark).  The sum is a log-sum-exp (Section 7, Prediction Step),
  * taken by the two-pass definition max + log sum exp(a - max).  Differences x - y are
@@ -40,11 +45,13 @@
  * t0, t1      : targets t0 <= i < t1 are evaluated
  * out         : [(t1 - t0)][n_tau] results L_tau(i); -inf when no source contributes
  * n_threads   : OpenMP threads (<= 0: library default)
+ * minv, hld   : [n][r] and [n] metric of diagonal noise coefficients, or NULL (unit noise)
  */
 void yyo_kernel_lse(int64_t n, int32_t r, const double* x, const double* fx,
                     const double* divf, const double* logw, const uint8_t* mask,
                     int32_t n_tau, const double* tau, double log_wq,
-                    int64_t t0, int64_t t1, double* out, int32_t n_threads)
+                    int64_t t0, int64_t t1, double* out, int32_t n_threads,
+                    const double* minv, const double* hld)
 {
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -59,11 +66,12 @@ void yyo_kernel_lse(int64_t n, int32_t r, const double* x, const double* fx,
         for (int64_t i = t0; i < t1; ++i) {
             const double* xi = x + (size_t)i * r;
             const double* fi = fx + (size_t)i * r;
+            const double* mi = minv ? minv + (size_t)i * r : NULL;
             double ff = 0.0;
-            for (int32_t d = 0; d < r; ++d) ff += fi[d] * fi[d];
+            for (int32_t d = 0; d < r; ++d) ff += (mi ? mi[d] : 1.0) * fi[d] * fi[d];
             for (int32_t q = 0; q < n_tau; ++q) {
                 const double t = tau[q];
-                const double log_c = -0.5 * r * (log_2pi + log(t));
+                const double log_c = -0.5 * r * (log_2pi + log(t)) - (hld ? hld[i] : 0.0);
                 const double tail = 0.5 * t * (2.0 * divf[i] + ff);
                 double mx = -INFINITY;
                 for (int64_t s = 0; s < n; ++s) {
@@ -72,8 +80,9 @@ void yyo_kernel_lse(int64_t n, int32_t r, const double* x, const double* fx,
                     double d2 = 0.0, drift = 0.0;
                     for (int32_t d = 0; d < r; ++d) {
                         const double diff = xi[d] - xs[d];
-                        d2 += diff * diff;
-                        drift += (xs[d] - xi[d]) * fi[d];
+                        const double m = mi ? mi[d] : 1.0;
+                        d2 += m * diff * diff;
+                        drift += (xs[d] - xi[d]) * m * fi[d];
                     }
                     const double logk = log_c - d2 / (2.0 * t) - drift - tail;
                     terms[s] = logk + logw[s];

@@ -52,6 +52,7 @@ class Problem:
     restart_init: str = "gauss"   # "gauss" | "uniform"
     restart_rule: str = "plain"   # "plain" | "learned"
     mlp_params: dict | None = None
+    noise: dict | None = None     # diagonal noise coefficients (model.state_noise); None: unit
 
     @property
     def taus(self) -> np.ndarray:
@@ -72,6 +73,8 @@ class Prepared:
     f: np.ndarray      # [n][r]
     divf: np.ndarray   # [n]
     mask: np.ndarray   # [n] bool
+    minv: np.ndarray | None = None   # [n][r] a(x)^+ (diagonal) with noise coefficients
+    hld: np.ndarray | None = None    # [n] 1/2 log det_+ a(x)
 
 
 def log_wq(half: np.ndarray, n: int) -> float:
@@ -87,9 +90,10 @@ def boundary_mask(u: np.ndarray, R: np.ndarray) -> np.ndarray:
 
 def prepare(p: Problem, u: np.ndarray, centre: np.ndarray, half: np.ndarray | None = None) -> Prepared:
     x = centre[None, :].astype(np.float64) + u.astype(np.float64)
+    minv, hld = mdl.kernel_metric(p.noise, x) if p.noise is not None else (None, None)
     return Prepared(x=x, f=mdl.drift(p.model, x, p.model_a),
                     divf=mdl.divergence(p.model, x, p.model_a),
-                    mask=boundary_mask(u, p.R if half is None else half))
+                    mask=boundary_mask(u, p.R if half is None else half), minv=minv, hld=hld)
 
 
 def log_sum_exp(a: np.ndarray) -> float:
@@ -124,8 +128,11 @@ def kernel_lse(p: Problem, prep: Prepared, logw: np.ndarray, t0: int = 0, t1: in
     tau = np.ascontiguousarray(p.taus, dtype=np.float64)
     out = np.empty((t1 - t0, p.n_scales), dtype=np.float64)
     ptr = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    mi = None if prep.minv is None else np.ascontiguousarray(prep.minv, dtype=np.float64)
+    hl = None if prep.hld is None else np.ascontiguousarray(prep.hld, dtype=np.float64)
     L.yyo_kernel_lse(p.n, p.r, ptr(x), ptr(f), ptr(dv), ptr(lw), ptr(mk), p.n_scales,
-                     ptr(tau), lwq, t0, t1, ptr(out), n_threads)
+                     ptr(tau), lwq, t0, t1, ptr(out), n_threads,
+                     None if mi is None else ptr(mi), None if hl is None else ptr(hl))
     return out
 
 
@@ -169,9 +176,14 @@ def predict(p: Problem, prep: Prepared, logw: np.ndarray, t0: int = 0, t1: int |
 
 
 def log_likelihood(p: Problem, x: np.ndarray, dy: np.ndarray) -> np.ndarray:
-    """h(x_i).dy - dt/2 |h(x_i)|^2, the Ito-corrected log update factor."""
+    """h(x_i).dy - dt/2 |h(x_i)|^2, the Ito-corrected log update factor; with noise
+    coefficients h^T b^-1 dy - dt/2 h^T b^-1 h, b = V V^T (table of the section on noise
+    coefficients, online update row)."""
     h = mdl.sensor(p.model, x)
-    return h @ dy - 0.5 * p.dt * np.sum(h * h, axis=1)
+    if p.noise is None:
+        return h @ dy - 0.5 * p.dt * np.sum(h * h, axis=1)
+    ib = 1.0 / mdl.obs_noise(p.noise, x) ** 2
+    return np.sum(ib * (h * dy[None, :] - 0.5 * p.dt * h * h), axis=1)
 
 
 def estimate(x: np.ndarray, logw_hat: np.ndarray) -> tuple[np.ndarray, np.ndarray, float]:

@@ -21,11 +21,12 @@ YY_OK = 0
 STATUS_NAMES = {0: "YY_OK", 1: "YY_ERR_ARG", 2: "YY_ERR_CUDA", 3: "YY_ERR_WORKSPACE",
                 4: "YY_ERR_NONFINITE", 5: "YY_ERR_DEGENERATE", 6: "YY_ERR_TIMEOUT",
                 7: "YY_ERR_STATE", 8: "YY_ERR_UNSUPPORTED"}
-MODELS = {"cubic": 0, "linear": 1}
+MODELS = {"cubic": 0, "linear": 1, "paper_e1": 2}
 PRECISIONS = {"f64": 0, "f32": 1, "bf16": 2, "f32s": 3}
 RESTART_INIT = {"gauss": 0, "uniform": 1}
 RESTART_RULE = {"plain": 0, "learned": 1}
 SCREEN_TYPE = {"bf16": 0, "fp8": 1}
+NODES = {"sobol": 0, "halton": 1, "faure": 2}
 RESTART_AUTO, RESTART_FORCE, RESTART_NEVER = 0, 1, 2
 SOBOL_POLY_WORDS = 16
 SOBOL_SCRAMBLE_WORDS = 33
@@ -45,7 +46,7 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train",
            "yy_mlp_set_input_norm", "yy_get_screen", "yy_batch_set_routing",
            "yy_set_wait_limit", "yy_set_shard", "yy_shard_rows", "yy_update_shard", "yy_merge_shards",
-           "yy_merge_records_host")
+           "yy_merge_records_host", "yy_init_nodes_lds")
 
 
 class YYError(RuntimeError):
@@ -62,7 +63,9 @@ class YYConfig(ctypes.Structure):
                 ("ess_frac", ctypes.c_double), ("restart_init", ctypes.c_int32),
                 ("prior_mean", ctypes.c_double), ("prior_var", ctypes.c_double),
                 ("restart_rule", ctypes.c_int32), ("screen_prefix", ctypes.c_int32),
-                ("screen_type", ctypes.c_int32)]
+                ("screen_type", ctypes.c_int32), ("noise", ctypes.c_int32), ("noise_u_zero", ctypes.c_int32),
+                ("noise_u", ctypes.c_double), ("noise_u_kappa", ctypes.c_double),
+                ("noise_v", ctypes.c_double), ("noise_v_kappa", ctypes.c_double)]
 
 
 def _declare(L: ctypes.CDLL) -> None:
@@ -112,6 +115,7 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_update_shard": (I32, [P, P, P, P]),
         "yy_merge_shards": (I32, [P, P, P, I32]),
         "yy_merge_records_host": (I32, [P, I32, I32, P]),
+        "yy_init_nodes_lds": (I32, [P, I32, P, P]),
         "yy_get_box": (I32, [P, P, P]),
         "yy_set_restart_mlp": (I32, [P, P]),
         "yy_mlp_param_count": (I64, [I32, I32]),
@@ -164,13 +168,19 @@ def make_config(model: str, r: int, n: int, dt: float, R: float, n_scales: int,
                 precision: str, restart_interval: int = 0, ess_frac: float = 0.0,
                 model_a: float = -0.5, restart_init: str = "gauss", prior_mean: float = 0.0,
                 prior_var: float = 1.0, restart_rule: str = "plain", screen_prefix: int = 0,
-                screen_type: str = "bf16") -> YYConfig:
+                screen_type: str = "bf16", noise: dict | None = None) -> YYConfig:
+    """noise: None (unit noise) or diagonal noise coefficients {u, u_kappa, u_zero, v, v_kappa}
+    (include/yy.h, yy_noise)."""
+    nz = noise or {}
     return YYConfig(r=r, m=r, n=n, dt=dt, R=R, n_scales=n_scales, model=MODELS[model],
                     model_a=model_a, precision=PRECISIONS[precision],
                     restart_interval=restart_interval, ess_frac=ess_frac,
                     restart_init=RESTART_INIT[restart_init], prior_mean=prior_mean,
                     prior_var=prior_var, restart_rule=RESTART_RULE[restart_rule],
-                    screen_prefix=screen_prefix, screen_type=SCREEN_TYPE[screen_type])
+                    screen_prefix=screen_prefix, screen_type=SCREEN_TYPE[screen_type],
+                    noise=1 if noise else 0, noise_u_zero=int(nz.get("u_zero", 0)),
+                    noise_u=float(nz.get("u", 1.0)), noise_u_kappa=float(nz.get("u_kappa", 0.0)),
+                    noise_v=float(nz.get("v", 1.0)), noise_v_kappa=float(nz.get("v_kappa", 0.0)))
 
 
 def config_from_workload(w, precision: str | None = None, **over) -> YYConfig:
@@ -234,6 +244,14 @@ class Filter:
         _check("yy_init_nodes", self.lib.yy_init_nodes(
             self.h, _ptr(poly), None if scr is None else _ptr(scr), _ptr(cen),
             None if hw is None else _ptr(hw)))
+
+    def init_nodes_lds(self, kind: str, center: np.ndarray, halfwidth: np.ndarray | None = None) -> None:
+        """Halton ("halton") or Faure ("faure") nodes instead of Sobol nodes."""
+        cen = np.ascontiguousarray(center, dtype=np.float64)
+        hw = None if halfwidth is None else np.ascontiguousarray(halfwidth, dtype=np.float64)
+        assert cen.shape == (self.r,)
+        _check("yy_init_nodes_lds", self.lib.yy_init_nodes_lds(self.h, NODES[kind], _ptr(cen),
+                                                               None if hw is None else _ptr(hw)))
 
     def sobol_bits(self, first: int, count: int):
         out = self.torch.empty((count, self.r), dtype=self.torch.int32, device=self.device)

@@ -91,13 +91,28 @@ bool cfg_valid(const yy_config* c) {
     if (c->n < 2 || c->n > (1LL << 31)) return false;
     if (!(c->dt > 0.0) || !(c->R > 0.0) || !(c->prior_var > 0.0)) return false;
     if (c->n_scales < 1 || c->n_scales > YY_MAX_SCALES) return false;
-    if (c->model != YY_MODEL_CUBIC && c->model != YY_MODEL_LINEAR) return false;
+    if (c->model != YY_MODEL_CUBIC && c->model != YY_MODEL_LINEAR && c->model != YY_MODEL_PAPER_E1) return false;
     if (c->precision < YY_PREC_FP64 || c->precision > YY_PREC_FP32_SCREEN) return false;
     if (c->restart_init != YY_RESTART_INIT_GAUSS && c->restart_init != YY_RESTART_INIT_UNIFORM) return false;
     if (!(c->ess_frac >= 0.0) || c->ess_frac > 1.0) return false;
     if (c->restart_rule != YY_RESTART_PLAIN && c->restart_rule != YY_RESTART_LEARNED) return false;
     if (c->screen_prefix < 0) return false;
     if (c->screen_type != YY_SCREEN_BF16 && c->screen_type != YY_SCREEN_FP8) return false;
+    if (c->noise != YY_NOISE_UNIT && c->noise != YY_NOISE_DIAG) return false;
+    if (c->noise == YY_NOISE_DIAG) {
+        if (!(c->noise_u > 0.0) || !(c->noise_v > 0.0) || !(c->noise_u_kappa >= 0.0) || !(c->noise_v_kappa >= 0.0))
+            return false;
+        if (c->noise_u_zero < 0 || c->noise_u_zero > c->r) return false;
+    }
+    return true;
+}
+
+// Configurations the library does not run: noise coefficients outside the plain FP32 / FP64
+// forms (the screens bound Euclidean distances) or with the large-scale model (its centred
+// update does not separate from state-dependent b(x)).
+bool cfg_supported(const yy_config* c) {
+    if (c->noise == YY_NOISE_DIAG)
+        return (c->precision == YY_PREC_FP32 || c->precision == YY_PREC_FP64) && c->model != YY_MODEL_PAPER_E1;
     return true;
 }
 
@@ -123,7 +138,9 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     const size_t nr = (size_t)n_pad * r_pad;
     b.u = cv.take<float>(nr * sizeof(float));
     b.f = cv.take<T>(nr * sizeof(T));
-    b.store_f = (c->precision == YY_PREC_BF16) ? 0 : 1;
+    // the screen's exact pairs recompute the drift from one coordinate unless f is stored; the
+    // large-scale model's drift couples neighbouring coordinates, so it is always stored
+    b.store_f = (c->precision == YY_PREC_BF16 && c->model != YY_MODEL_PAPER_E1) ? 0 : 1;
     b.ubf = (c->precision == YY_PREC_BF16) ? cv.take<__nv_bfloat16>(nr * sizeof(__nv_bfloat16)) : nullptr;
     b.divf = cv.take<T>(n_pad * sizeof(T));
     b.nu = cv.take<T>(n_pad * sizeof(T));
@@ -139,6 +156,12 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.params = cv.take<uint32_t>((size_t)c->r * (YY_SOBOL_POLY_WORDS + YY_SOBOL_SCRAMBLE_WORDS) * sizeof(uint32_t));
     b.obs_g = cv.take<T>(r_pad * sizeof(T));
     b.obs_c = cv.take<T>(r_pad * sizeof(T));
+    b.obs_l = cv.take<T>(r_pad * sizeof(T));
+    b.obs_ibc = cv.take<T>(r_pad * sizeof(T));
+    if (c->noise == YY_NOISE_DIAG) {
+        b.minv = cv.take<T>(nr * sizeof(T));
+        b.hld = cv.take<T>(n_pad * sizeof(T));
+    }
     b.dimc = cv.take<T>(5 * (size_t)r_pad * sizeof(T));
     b.next_centre = cv.take<double>(r_pad * sizeof(double));
     b.next_half = cv.take<double>(r_pad * sizeof(double));
@@ -270,6 +293,12 @@ void fill_consts(yy_filter* f, Consts<T>* k, const double* halfwidth) {
     k->wait_ns = f->wait_ns;
     k->row0 = f->row0;
     k->row1 = f->row1;
+    k->noise = c.noise;
+    k->noise_u_zero = c.noise_u_zero;
+    k->nz_u = (T)c.noise_u;
+    k->nz_uk = (T)c.noise_u_kappa;
+    k->nz_v = (T)c.noise_v;
+    k->nz_vk = (T)c.noise_v_kappa;
 }
 
 yy_status cuda_status(cudaError_t e) { return e == cudaSuccess ? YY_OK : YY_ERR_CUDA; }
@@ -281,24 +310,54 @@ __global__ void k_set_stats(DevStats* st, double lognorm, long long step) {
 
 __global__ void k_init_cref(DevStats* st, double c_ref) { st->c_ref = c_ref; }
 
+// The first `count` primes (trial division by the primes found so far).
+std::vector<uint32_t> first_primes_host(int count) {
+    std::vector<uint32_t> ps;
+    for (uint32_t c = 2; (int)ps.size() < count; ++c) {
+        bool prime = true;
+        for (uint32_t q : ps) {
+            if (q * q > c) break;
+            if (c % q == 0) { prime = false; break; }
+        }
+        if (prime) ps.push_back(c);
+    }
+    return ps;
+}
+
+uint32_t smallest_prime_at_least_host(uint32_t m) {
+    for (uint32_t c = m < 2 ? 2 : m;; ++c) {
+        bool prime = true;
+        for (uint32_t q = 2; q * q <= c; ++q)
+            if (c % q == 0) { prime = false; break; }
+        if (prime) return c;
+    }
+}
+
+// node_kind: YY_NODES_SOBOL (h_poly, h_scr: the Sobol parameters) or Halton / Faure.
 template <typename T>
 yy_status do_init_nodes(yy_filter* f, Bufs<T>& b, Consts<T>& k, const uint32_t* h_poly,
-                        const uint32_t* h_scr, const double* h_center, const double* h_half) {
+                        const uint32_t* h_scr, const double* h_center, const double* h_half,
+                        int node_kind = YY_NODES_SOBOL) {
     const yy_config& c = f->cfg;
     const int W = YY_SOBOL_POLY_WORDS + YY_SOBOL_SCRAMBLE_WORDS;
-    uint32_t* staging = (uint32_t*)malloc(sizeof(uint32_t) * (size_t)c.r * W);
+    uint32_t* staging = (uint32_t*)calloc((size_t)c.r * W, sizeof(uint32_t));
     double* cen = (double*)calloc(f->r_pad, sizeof(double));
     double* half = (double*)calloc(f->r_pad, sizeof(double));
     if (!staging || !cen || !half) { free(staging); free(cen); free(half); return YY_ERR_ARG; }
+    const std::vector<uint32_t> primes = node_kind == YY_NODES_HALTON ? first_primes_host(c.r) : std::vector<uint32_t>();
     for (int d = 0; d < c.r; ++d) {
-        memcpy(staging + (size_t)d * W, h_poly + (size_t)d * YY_SOBOL_POLY_WORDS,
-               sizeof(uint32_t) * YY_SOBOL_POLY_WORDS);
-        uint32_t* L = staging + (size_t)d * W + YY_SOBOL_POLY_WORDS;
-        if (h_scr) {
-            memcpy(L, h_scr + (size_t)d * YY_SOBOL_SCRAMBLE_WORDS, sizeof(uint32_t) * YY_SOBOL_SCRAMBLE_WORDS);
-        } else {
-            for (int q = 1; q <= 32; ++q) L[q - 1] = 1u << (32 - q);
-            L[32] = 0u;
+        if (node_kind == YY_NODES_SOBOL) {
+            memcpy(staging + (size_t)d * W, h_poly + (size_t)d * YY_SOBOL_POLY_WORDS,
+                   sizeof(uint32_t) * YY_SOBOL_POLY_WORDS);
+            uint32_t* L = staging + (size_t)d * W + YY_SOBOL_POLY_WORDS;
+            if (h_scr) {
+                memcpy(L, h_scr + (size_t)d * YY_SOBOL_SCRAMBLE_WORDS, sizeof(uint32_t) * YY_SOBOL_SCRAMBLE_WORDS);
+            } else {
+                for (int q = 1; q <= 32; ++q) L[q - 1] = 1u << (32 - q);
+                L[32] = 0u;
+            }
+        } else if (node_kind == YY_NODES_HALTON) {
+            staging[d] = primes[d];   // the staging area holds the bases
         }
         cen[d] = h_center[d];
         half[d] = h_half ? h_half[d] : c.R;
@@ -312,9 +371,16 @@ yy_status do_init_nodes(yy_filter* f, Bufs<T>& b, Consts<T>& k, const uint32_t* 
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     free(staging); free(cen); free(half);
     if (e != cudaSuccess) return YY_ERR_CUDA;
-    if ((e = launch_sobol_dirs<T>(b.params, b.dirs, c.r, s)) != cudaSuccess) return YY_ERR_CUDA;
-    if ((e = launch_sobol_points(b.dirs, c.r, f->r_pad, 0, c.n, b.u, nullptr, b.halfwidth, s)) != cudaSuccess)
-        return YY_ERR_CUDA;
+    if (node_kind == YY_NODES_SOBOL) {
+        if ((e = launch_sobol_dirs<T>(b.params, b.dirs, c.r, s)) != cudaSuccess) return YY_ERR_CUDA;
+        if ((e = launch_sobol_points(b.dirs, c.r, f->r_pad, 0, c.n, b.u, nullptr, b.halfwidth, s)) != cudaSuccess)
+            return YY_ERR_CUDA;
+    } else {
+        const uint32_t pf = smallest_prime_at_least_host((uint32_t)c.r);
+        if ((e = launch_lds_points(node_kind, b.params, pf, c.r, f->r_pad, c.n, b.u, b.halfwidth, s)) != cudaSuccess)
+            return YY_ERR_CUDA;
+    }
+    f->node_kind = node_kind;
     if ((e = launch_prep<T>(k, b, true, true, c.prior_mean, c.prior_var, s)) != cudaSuccess) return YY_ERR_CUDA;
     int l = 0;
     if ((e = launch_normalise_only<T>(k, b, s, &l)) != cudaSuccess) return YY_ERR_CUDA;
@@ -345,6 +411,7 @@ yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t bytes, void*
     if (!out) return YY_ERR_ARG;
     *out = nullptr;
     if (!cfg_valid(cfg)) return YY_ERR_ARG;
+    if (!cfg_supported(cfg)) return YY_ERR_UNSUPPORTED;
     const size_t need = yy_workspace_bytes(cfg);
     if (!d_workspace || ((uintptr_t)d_workspace & 255u) || bytes < need) return YY_ERR_WORKSPACE;
     yy_filter* f = new (std::nothrow) yy_filter();
@@ -395,9 +462,21 @@ yy_status yy_init_nodes(yy_filter* f, const uint32_t* h_poly, const uint32_t* h_
     return do_init_nodes<float>(f, f->bf, f->kf, h_poly, h_scramble, h_center, h_halfwidth);
 }
 
+yy_status yy_init_nodes_lds(yy_filter* f, int32_t kind, const double* h_center, const double* h_halfwidth) {
+    if (!f || !h_center || (kind != YY_NODES_HALTON && kind != YY_NODES_FAURE)) return YY_ERR_ARG;
+    if (f->mlp && f->cfg.restart_rule == YY_RESTART_LEARNED) return YY_ERR_UNSUPPORTED;
+    for (int d = 0; d < f->cfg.r; ++d) {
+        if (h_halfwidth && !(h_halfwidth[d] > 0.0)) return YY_ERR_ARG;
+        if (!isfinite(h_center[d])) return YY_ERR_ARG;
+    }
+    if (f->fp64) return do_init_nodes<double>(f, f->bd, f->kd, nullptr, nullptr, h_center, h_halfwidth, kind);
+    return do_init_nodes<float>(f, f->bf, f->kf, nullptr, nullptr, h_center, h_halfwidth, kind);
+}
+
 yy_status yy_sobol_bits(yy_filter* f, uint32_t* d_bits, int64_t first, int64_t count) {
     if (!f || !d_bits || first < 0 || count < 0) return YY_ERR_ARG;
     if (!f->nodes_ready) return YY_ERR_STATE;
+    if (f->node_kind != YY_NODES_SOBOL) return YY_ERR_UNSUPPORTED;
     const uint32_t* dirs = f->fp64 ? f->bd.dirs : f->bf.dirs;
     f->launches += 1;
     return cuda_status(launch_sobol_points(dirs, f->cfg.r, f->r_pad, first, count, nullptr, d_bits,
@@ -610,6 +689,7 @@ yy_status yy_set_state(yy_filter* f, const double* h_center, const void* h_logw,
 yy_status yy_set_restart_mlp(yy_filter* f, yy_mlp* net) {
     if (!f) return YY_ERR_ARG;
     if (net && f->fp64) return YY_ERR_UNSUPPORTED;
+    if (net && f->nodes_ready && f->node_kind != YY_NODES_SOBOL) return YY_ERR_UNSUPPORTED;
     f->mlp = net;
     return YY_OK;
 }

@@ -67,6 +67,7 @@ bool batch_cfg_ok(const yy_config* cfgs, int B) {
         if (yy_workspace_bytes(&cfgs[b]) == 0) return false;
         if (cfgs[b].precision != cfgs[0].precision || cfgs[b].n_scales != cfgs[0].n_scales) return false;
         if (cfgs[b].precision == YY_PREC_FP64 || cfgs[b].precision == YY_PREC_FP32_SCREEN) return false;
+        if (cfgs[b].noise != YY_NOISE_UNIT) return false;
     }
     return true;
 }

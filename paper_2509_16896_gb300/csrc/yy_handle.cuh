@@ -29,6 +29,7 @@ struct yy_filter {
     long long row0, row1;         // target rows of this handle (shards of a row-split filter)
     int shard_rank, shard_count;  // 0, 1 for a whole filter
     bool shard_updated;           // yy_update_shard ran; yy_merge_shards completes the step
+    int node_kind;                // yy_nodes of the last node generation
 };
 
 namespace yy {

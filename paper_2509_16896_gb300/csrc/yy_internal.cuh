@@ -80,6 +80,9 @@ struct Consts {
     unsigned long long wait_ns;  // limit of the prediction kernel's bounded waits (yy_set_wait_limit)
     long long row0, row1;        // target rows this handle predicts and updates: [0, n), or its
                                  // shard's equal chunk when the rows are split across devices
+    int noise;                   // yy_noise
+    int noise_u_zero;            // DIAG: coordinates without state noise
+    T nz_u, nz_uk, nz_v, nz_vk;  // DIAG: U_d = nz_u (1 + nz_uk sin^2 x_d), V_d = nz_v (1 + nz_vk sin^2 x_d)
 };
 
 // Pointers into the caller's workspace.
@@ -104,6 +107,10 @@ struct Bufs {
     double* var;          // [r_pad] v_hat
     T* obs_g;             // [r_pad] dy - dt h(c)
     T* obs_c;             // [r_pad] centre in T
+    T* obs_l;             // [r_pad] noise coefficients: h(c) dy - dt/2 h(c)^2 per coordinate
+    T* obs_ibc;           // [r_pad] noise coefficients: 1 / b_d(c)
+    T* minv;              // [n_pad][r_pad] noise coefficients: a(x)^+ (diagonal) at every node
+    T* hld;               // [n_pad] noise coefficients: 1/2 log det_+ a(x)
     T* dimc;              // [5][r_pad] per-dimension constants of the preparation pass:
                           // centre head, tail, Gaussian restart 1 / (2 var), cos c, sin c
     double* next_centre;  // [r_pad] box of the restart in progress
@@ -163,6 +170,8 @@ cudaError_t launch_sobol_dirs(const uint32_t* params, uint32_t* dirs, int r, cud
 cudaError_t launch_sobol_points(const uint32_t* dirs, int r, int r_pad, long long first,
                                 long long count, float* u, uint32_t* bits, const double* halfwidth,
                                 cudaStream_t s);
+cudaError_t launch_lds_points(int kind, const uint32_t* primes, uint32_t p_faure, int r, int r_pad, long long n,
+                              float* u, const double* halfwidth, cudaStream_t s);
 
 int prep_grid(long long n_pad);
 template <typename T>

@@ -42,11 +42,15 @@ template <> __device__ __forceinline__ double exp_fast<double>(double x) { retur
 // evaluated exactly as in the plain form.  A live target without a finite log-weight has no
 // reference and takes every tile.  The comparison carries a relative margin of 1e-4 for
 // the float32 rounding of the partial sums.
-template <typename T, int N, bool SCREEN = false>
+// NOISE (diagonal noise coefficients): the squared distance and the drift's inner product
+// take the target's metric a(x_i)^+, S1 = sum_d m_d D_d^2, S2 = sum_d m_d D_d f_d, with
+// |f_i|^2 in the same metric (nf) and -1/2 log det_+ a(x_i) added in the combination.
+template <typename T, int N, bool SCREEN = false, bool NOISE = false>
 __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>& b, int rk, int bid, int k1 = 0) {
     __shared__ T At[BK][BM];   // u of targets
     __shared__ T Ft[BK][BM];   // f of targets
     __shared__ T Bt[BK][BN];   // u of sources
+    __shared__ T Mt[NOISE ? BK : 1][NOISE ? BM : 1];   // metric of targets
     __shared__ T lsrc[BN];
 
     const int tid = threadIdx.x;
@@ -150,13 +154,18 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
                 At[col][row] = (T)b.u[ti];
                 Ft[col][row] = b.f[ti];
                 Bt[col][row] = (T)b.u[si];
+                if constexpr (NOISE) Mt[col][row] = b.minv[ti];
             }
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < BK; ++kk) {
-                T av[TM], fv[TM], bv[TN];
+                T av[TM], fv[TM], bv[TN], mv[TM];
 #pragma unroll
                 for (int a = 0; a < TM; ++a) { av[a] = At[kk][ty * TM + a]; fv[a] = Ft[kk][ty * TM + a]; }
+                if constexpr (NOISE) {
+#pragma unroll
+                    for (int a = 0; a < TM; ++a) { mv[a] = Mt[kk][ty * TM + a]; fv[a] *= mv[a]; }
+                }
 #pragma unroll
                 for (int c = 0; c < TN; ++c) bv[c] = Bt[kk][tx * TN + c];
 #pragma unroll
@@ -164,7 +173,8 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
 #pragma unroll
                     for (int c = 0; c < TN; ++c) {
                         const T dlt = av[a] - bv[c];
-                        S1[a][c] = fma(dlt, dlt, S1[a][c]);
+                        if constexpr (NOISE) S1[a][c] = fma(mv[a] * dlt, dlt, S1[a][c]);
+                        else S1[a][c] = fma(dlt, dlt, S1[a][c]);
                         S2[a][c] = fma(dlt, fv[a], S2[a][c]);
                     }
             }
@@ -220,13 +230,15 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
         const long long i = i0 + ty * TM + a;
         if (i >= k.n) continue;
         if (b.mask[i]) { b.logw_pred[i] = T(-INFINITY); continue; }
-        b.logw_pred[i] = combine_scales<T, N>(k, mx[a], sm[a], b.divf[i], b.logw[i], b.stats->c_ref, &b.stats->clamps);
+        const T hld = NOISE ? b.hld[i] : T(0);
+        b.logw_pred[i] = combine_scales<T, N>(k, mx[a], sm[a], b.divf[i], b.logw[i], b.stats->c_ref, &b.stats->clamps,
+                                              hld);
     }
 }
 
-template <typename T, int N>
+template <typename T, int N, bool NOISE = false>
 __global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int rk) {
-    ksum_simt_body<T, N>(k, b, rk, (int)(k.row0 / BM) + blockIdx.x);
+    ksum_simt_body<T, N, false, NOISE>(k, b, rk, (int)(k.row0 / BM) + blockIdx.x);
 }
 
 template <int N>
@@ -302,6 +314,16 @@ cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t 
     const int rk = ((k.r + BK - 1) / BK) * BK;
     const unsigned grid = (unsigned)((k.row1 - k.row0 + BM - 1) / BM);   // the handle's target blocks
     if (grid == 0) return cudaSuccess;
+    if (k.noise == YY_NOISE_DIAG) {
+        switch (k.N) {
+            case 1: k_ksum_simt<T, 1, true><<<grid, 256, 0, s>>>(k, b, rk); break;
+            case 2: k_ksum_simt<T, 2, true><<<grid, 256, 0, s>>>(k, b, rk); break;
+            case 3: k_ksum_simt<T, 3, true><<<grid, 256, 0, s>>>(k, b, rk); break;
+            case 4: k_ksum_simt<T, 4, true><<<grid, 256, 0, s>>>(k, b, rk); break;
+            default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (k.N) {
         case 1: k_ksum_simt<T, 1><<<grid, 256, 0, s>>>(k, b, rk); break;
         case 2: k_ksum_simt<T, 2><<<grid, 256, 0, s>>>(k, b, rk); break;

@@ -2,7 +2,9 @@
 // copy of u, and the initial or restart log-weights.
 //
 //   f(x)      cubic: cos x (componentwise); linear: a x              (Section 9.1 / 9.3)
-//   div f(x)  cubic: -sum_d sin x_d;       linear: a r
+//             large-scale test: sin(x) (A x) + sin(2x) (A1 x), A and A1 upper bidiagonal
+//   div f(x)  cubic: -sum_d sin x_d;       linear: a r;
+//             large-scale test: sum_d cos(x_d)(A x)_d - 0.5 sin x_d + 2 cos(2 x_d)(A1 x)_d - 0.3 sin 2x_d
 //   mask      |u_d| >= R_d - 1e-12 R_d for some d (Section 4.2, step 3), tested in float64
 //   prior     log sigma_0(x) = -|x - mu0|^2 / (2 s0^2) + const (Section 4.2, step 4)
 //   restart   log N(x; x_hat, diag(max(v_hat, (R/4)^2))) + const, or uniform
@@ -33,6 +35,33 @@ __device__ __forceinline__ T warp_sum(T v) {
 }
 
 constexpr int kRowQ = YY_MAX_DIM / 64;   // float2 per lane of the longest row
+
+// Drift component d of the large-scale test's model at x_d with neighbour x_{d+1} (nb = 0
+// for the last coordinate: the bidiagonal matrices have no entry there), and the
+// coordinate's term of div f.
+__device__ __forceinline__ void e1_drift(float x, float nb, float* f, float* dv) {
+    const float ax = fmaf(-0.5f, x, 0.1f * nb), a1x = fmaf(-0.3f, x, 0.3f * nb);
+    float s1, c1, s2, c2;
+    sincosf(x, &s1, &c1);
+    sincosf(2.0f * x, &s2, &c2);
+    *f = fmaf(s1, ax, s2 * a1x);
+    *dv = c1 * ax - 0.5f * s1 + 2.0f * c2 * a1x - 0.3f * s2;
+}
+__device__ __forceinline__ void e1_drift(double x, double nb, double* f, double* dv) {
+    const double ax = fma(-0.5, x, 0.1 * nb), a1x = fma(-0.3, x, 0.3 * nb);
+    double s1, c1, s2, c2;
+    sincos(x, &s1, &c1);
+    sincos(2.0 * x, &s2, &c2);
+    *f = fma(s1, ax, s2 * a1x);
+    *dv = c1 * ax - 0.5 * s1 + 2.0 * c2 * a1x - 0.3 * s2;
+}
+
+template <typename T> __device__ __forceinline__ T sin_w(T x);
+template <> __device__ __forceinline__ float sin_w<float>(float x) { return sinf(x); }
+template <> __device__ __forceinline__ double sin_w<double>(double x) { return sin(x); }
+template <typename T> __device__ __forceinline__ T log_w(T x);
+template <> __device__ __forceinline__ float log_w<float>(float x) { return logf(x); }
+template <> __device__ __forceinline__ double log_w<double>(double x) { return log(x); }
 
 template <typename T>
 __device__ __forceinline__ T exp_w(T x);
@@ -88,6 +117,7 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
     const double* halfw = (mode == kPrepRestart) ? b.next_half : b.halfwidth;
     const int nq = rp >> 6;   // float2 per lane
     const bool cubic = k.model == YY_MODEL_CUBIC;
+    const bool e1 = k.model == YY_MODEL_PAPER_E1;
     for (long long i = warp; i < k.n_pad; i += nwarps) {
         const float* ui = b.u + (size_t)i * rp;
         T* fi = b.f + (size_t)i * rp;
@@ -98,8 +128,11 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
                 b.divf[i] = T(0);
                 b.nf[i] = T(0);
                 b.logw[i] = T(-INFINITY);
+                if (b.hld) b.hld[i] = T(0);
                 if (first) { b.nu[i] = T(0); b.mask[i] = 1; }
             }
+            if (b.minv)
+                for (int d = lane; d < rp; d += 32) b.minv[(size_t)i * rp + d] = T(0);
             if (first && b.nu_chunk)
                 for (int c = lane; c < nq; c += 32) b.nu_chunk[(size_t)i * nq + c] = 0.f;
             continue;
@@ -112,13 +145,14 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
         // the stored boundary mask, loaded with the row rather than after its reductions
         const uint8_t mk = first ? (uint8_t)0 : b.mask[i];
         T div = T(0), nf = T(0), nu = T(0), lw = T(0);
+        T hl = T(0);   // noise coefficients: 1/2 log det_+ a(x) = sum of log U_d over U_d > 0
         int on_face = 0;
         bool done = false;
         if constexpr (std::is_same<T, float>::value && narrow && !first) {
             // the common restart and re-preparation case: cubic drift by the polynomials,
             // padded coordinates inert by construction (u = 0, cos c = sin c = 0, no Gaussian
             // term), so no per-element tests; per-dimension constants as float2 pairs
-            if (cubic) {
+            if (cubic && k.noise == YY_NOISE_UNIT) {
 #pragma unroll
                 for (int q = 0; q < kRowQ; ++q) {
                     if (q >= nq) break;   // uniform over the warp
@@ -145,13 +179,28 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
             if (q >= nq) break;   // uniform over the warp
             const int dq = 64 * q + 2 * lane;
             float cq = 0.f;       // |u|^2 of this lane's two coordinates
+            // large-scale model: u of coordinate dq + 2 (the next lane's first, or for the last
+            // lane the first lane's of the next chunk; zero padding beyond the row)
+            float u_next = 0.f;
+            if (e1) {
+                const float from_lane = __shfl_down_sync(0xffffffffu, uu[q].x, 1);
+                const float from_next = __shfl_sync(0xffffffffu, (q + 1 < kRowQ) ? uu[q + 1 < kRowQ ? q + 1 : q].x : 0.f, 0);
+                u_next = (lane < 31) ? from_lane : ((q + 1 < nq) ? from_next : 0.f);
+            }
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int d = dq + e;
                 const float uf = e ? uu[q].y : uu[q].x;
                 T fv = T(0);
                 if (d < k.r) {
-                    if (cubic) {
+                    if (e1) {
+                        const float un = e ? u_next : uu[q].y;   // u of coordinate d + 1
+                        const T x = s_hi[d] + ((T)uf + s_lo[d]);
+                        const T xn = (d + 1 < k.r) ? s_hi[d + 1] + ((T)un + s_lo[d + 1]) : T(0);
+                        T dv;
+                        e1_drift(x, xn, &fv, &dv);
+                        div += dv;
+                    } else if (cubic) {
                         T sn;
                         if constexpr (std::is_same<T, float>::value && narrow) {
                             cubic_drift_narrow(uf, s_cc[d], s_sc[d], &fv, &sn);
@@ -165,7 +214,18 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
                         fv = k.model_a * (s_hi[d] + ((T)uf + s_lo[d]));
                         div += k.model_a;
                     }
-                    nf += fv * fv;
+                    // noise coefficients: |f|^2 in the metric a(x)^+ of this node, stored per
+                    // coordinate for the kernel sum
+                    T mval = T(1);
+                    if (k.noise == YY_NOISE_DIAG) {
+                        const T x = s_hi[d] + ((T)uf + s_lo[d]);
+                        const T sx = sin_w<T>(x);
+                        const T U = (d < k.noise_u_zero) ? T(0) : k.nz_u * (T(1) + k.nz_uk * sx * sx);
+                        mval = (U > T(0)) ? T(1) / (U * U) : T(0);
+                        if (U > T(0)) hl += log_w<T>(U);
+                        b.minv[(size_t)i * rp + d] = mval;
+                    }
+                    nf += mval * fv * fv;
                     if constexpr (mode == kPrepRestart) lw -= (T)uf * (T)uf * s_iv[d];
                     if constexpr (first) {
                         nu += (T)uf * (T)uf;
@@ -186,6 +246,7 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
                         b.ubf[(size_t)i * rp + d] = __float2bfloat16_rn(d < k.r ? uf : 0.0f);
                 }
                 if (b.store_f) fi[d] = fv;
+                if (d >= k.r && b.minv) b.minv[(size_t)i * rp + d] = T(0);
             }
             if (first && b.nu_chunk) {
                 cq = warp_sum(cq);
@@ -195,6 +256,10 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
         div = warp_sum(div);
         nf = warp_sum(nf);
         lw = warp_sum(lw);
+        if (b.hld) {
+            hl = warp_sum(hl);
+            if (lane == 0) b.hld[i] = hl;
+        }
         if (first) {
             nu = warp_sum(nu);
             on_face = __any_sync(0xffffffffu, on_face);

@@ -94,6 +94,75 @@ __global__ void k_sobol_points_restart(const uint32_t* __restrict__ dirs, int r,
     }
 }
 
+// Halton and Faure nodes (Appendix A, "Halton Sequence" and "Faure Sequence"): thread per
+// (point, dimension), index k = first + i.  The fraction's base-p digits y_0, y_1, ... (most
+// significant first) form the integer R = sum_i y_i p^(M-1-i) with M the largest digit count
+// such that p^M <= 2^53, so R and p^M are exact in float64 and R / p^M is the correctly
+// rounded fraction whatever M is.
+//   Halton: p = the d-th prime, y_i = digit i of k (least significant first): the radical
+//           inverse.
+//   Faure:  p = the smallest prime >= r, y = C k mod p with C = P^(d-1), P_ij = binom(j, i);
+//           the power of the Pascal matrix has the closed form
+//           (P^c)_ij = binom(j, i) c^(j-i), used here (c = d - 1 mod p).
+// Box map as for Sobol nodes: u = R_d (2 phi - 1), float64 with explicit rounding, then float32.
+__device__ __forceinline__ int lds_digits(unsigned long long p, unsigned long long* pM) {
+    int M = 0;
+    unsigned long long v = 1;
+    while (v <= (1ull << 53) / p) { v *= p; ++M; }
+    *pM = v;
+    return M;
+}
+
+__global__ void k_lds_points(int kind, const uint32_t* __restrict__ primes, uint32_t p_faure, int r, int r_pad,
+                             long long first, long long count, float* __restrict__ u,
+                             const double* __restrict__ halfwidth) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= r) return;
+    const unsigned long long p = (kind == YY_NODES_HALTON) ? primes[d] : p_faure;
+    unsigned long long pM;
+    const int M = lds_digits(p, &pM);
+    const double R = halfwidth[d];
+    const unsigned long long c = (unsigned long long)d % p;   // Faure: power of the Pascal matrix
+    unsigned long long cp[64];                                  // c^t mod p
+    if (kind == YY_NODES_FAURE) {
+        cp[0] = 1 % p;
+        for (int t = 1; t < M; ++t) cp[t] = (cp[t - 1] * c) % p;
+    }
+    for (long long i = blockIdx.y * (long long)blockDim.y + threadIdx.y; i < count; i += (long long)gridDim.y * blockDim.y) {
+        unsigned long long kk = (unsigned long long)(first + i);
+        unsigned long long dig[64];
+        for (int t = 0; t < M; ++t) { dig[t] = kk % p; kk /= p; }
+        unsigned long long Rn = 0;
+        for (int a = 0; a < M; ++a) {
+            unsigned long long y;
+            if (kind == YY_NODES_HALTON) {
+                y = dig[a];
+            } else {
+                // y_a = sum_{j >= a} binom(j, a) c^(j-a) k_j mod p
+                unsigned long long acc = 0, binom = 1;   // binom(j, a), starting at j = a
+                for (int j = a; j < M; ++j) {
+                    if (j > a) binom = binom * (unsigned long long)j / (unsigned long long)(j - a);
+                    acc += ((binom % p) * cp[j - a] % p) * dig[j];
+                }
+                y = acc % p;
+            }
+            Rn = Rn * p + y;
+        }
+        const double phi = __ddiv_rn((double)Rn, (double)pM);
+        const double t = __dsub_rn(__dmul_rn(2.0, phi), 1.0);
+        u[(size_t)i * r_pad + d] = __double2float_rn(__dmul_rn(R, t));
+    }
+}
+
+cudaError_t launch_lds_points(int kind, const uint32_t* primes, uint32_t p_faure, int r, int r_pad, long long n,
+                              float* u, const double* halfwidth, cudaStream_t s) {
+    dim3 block(64, 4);
+    long long gy = (n + 3) / 4;
+    if (gy > 65535) gy = 65535;
+    k_lds_points<<<dim3((r + 63) / 64, (unsigned)gy), block, 0, s>>>(kind, primes, p_faure, r, r_pad, 1, n, u, halfwidth);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sobol_points_restart(const uint32_t* dirs, int r, int r_pad, long long n, float* u,
                                         const double* next_half, const DevStats* st, cudaStream_t s) {
     dim3 block(64, 4);

@@ -5,7 +5,8 @@
 //     lambda(c) + sum_d dh_d (g_d - dt/2 dh_d),   dh_d = h(c_d + u_d) - h(c_d),
 //     g_d = dy_d - dt h(c_d),
 // which is an exact rewrite: lambda(c) (float64, once per step) absorbs the large common
-// part, and the per-node sum has no cancellation (cubic: dh = u (3c^2 + 3cu + u^2)).
+// part, and the per-node sum has no cancellation (cubic: dh = u (3c^2 + 3cu + u^2); the
+// large-scale model's (x - 100)^3 is the same expansion about c - 100).
 // The log-weights kept in T are therefore relative to c_ref + lambda(c); the absolute
 // normaliser Lambda_k = c_ref + lambda(c) + LSE(relative) is accumulated in float64.
 //
@@ -33,6 +34,10 @@ __device__ __forceinline__ T warp_sum_u(T v) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
+
+template <typename T> __device__ __forceinline__ T sin_u(T x);
+template <> __device__ __forceinline__ float sin_u<float>(float x) { return sinf(x); }
+template <> __device__ __forceinline__ double sin_u<double>(double x) { return sin(x); }
 
 template <typename T>
 __device__ __forceinline__ T exp_t(T x);
@@ -66,15 +71,30 @@ __device__ __forceinline__ void obs_prep_body(const Consts<T>& k, const Bufs<T>&
     for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
         if (d < k.r) {
             const double c = b.centre[d];
-            const double hc = (k.model == YY_MODEL_CUBIC) ? c * c * c : c;
+            // h(c) and the centre of the cubic expansion: x^3 about c, (x - 100)^3 about c - 100
+            const double cc = (k.model == YY_MODEL_PAPER_E1) ? c - 100.0 : c;
+            const double hc = (k.model == YY_MODEL_LINEAR) ? c : cc * cc * cc;
             const double y = dy[d];
             b.dy_last[d] = y;
             b.obs_g[d] = (T)(y - (double)k.dt * hc);
-            b.obs_c[d] = (T)c;
-            acc += hc * y - 0.5 * (double)k.dt * hc * hc;
+            b.obs_c[d] = (T)cc;
+            const double lcd = hc * y - 0.5 * (double)k.dt * hc * hc;
+            if (k.noise == YY_NOISE_DIAG) {
+                // weighted by 1 / b_d(c); the nodes' own 1 / b_d(x) enters in the likelihood pass
+                const double sc = sin(c);
+                const double V = (double)k.nz_v * (1.0 + (double)k.nz_vk * sc * sc);
+                const double ibc = 1.0 / (V * V);
+                b.obs_l[d] = (T)lcd;
+                b.obs_ibc[d] = (T)ibc;
+                acc += lcd * ibc;
+            } else {
+                acc += lcd;
+            }
         } else {
             b.obs_g[d] = T(0);
             b.obs_c[d] = T(0);
+            b.obs_l[d] = T(0);
+            b.obs_ibc[d] = T(0);
         }
     }
     acc = warp_sum_u(acc);
@@ -94,17 +114,25 @@ __device__ __forceinline__ void obs_prep_body(const Consts<T>& k, const Bufs<T>&
 // in g, so they add nothing.
 constexpr int kRowQ = YY_MAX_DIM / 64;
 
-template <typename T>
+// NOISE (diagonal noise coefficients): per coordinate the update is
+//     (h_d dy_d - dt/2 h_d^2) / b_d(x) = (l_d + dh_d (g_d - dt/2 dh_d)) / b_d(x),
+// l_d = h(c_d) dy_d - dt/2 h(c_d)^2, stored relative to l_d / b_d(c) (whose sum is lambda(c)).
+template <typename T, bool NOISE = false>
 __device__ __forceinline__ void loglik_body(const Consts<T>& k, const Bufs<T>& b, int bid, int nblk) {
     __shared__ double sm[8], ss[8];
     __shared__ T s_g[YY_MAX_DIM], s_c[YY_MAX_DIM];
-    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) { s_g[d] = b.obs_g[d]; s_c[d] = b.obs_c[d]; }
+    __shared__ T s_l[NOISE ? YY_MAX_DIM : 1], s_ibc[NOISE ? YY_MAX_DIM : 1];
+    for (int d = threadIdx.x; d < k.r_pad; d += blockDim.x) {
+        s_g[d] = b.obs_g[d];
+        s_c[d] = b.obs_c[d];
+        if constexpr (NOISE) { s_l[d] = b.obs_l[d]; s_ibc[d] = b.obs_ibc[d]; }
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const long long warp = (bid * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nwarps = ((long long)nblk * blockDim.x) >> 5;
     const T half_dt = T(0.5) * k.dt;
-    const bool cubic = k.model == YY_MODEL_CUBIC;
+    const bool cubic = k.model != YY_MODEL_LINEAR;   // cubic in u about obs_c
     const int nq = k.r_pad >> 6;
     T m = T(-INFINITY), s = T(0);   // working precision (see below)
     for (long long i = k.row0 + warp; i < k.row1; i += nwarps) {
@@ -122,7 +150,16 @@ __device__ __forceinline__ void loglik_body(const Consts<T>& k, const Bufs<T>& b
             const T c0 = s_c[d], c1 = s_c[d + 1];
             const T h0 = cubic ? u0 * (T(3) * c0 * c0 + T(3) * c0 * u0 + u0 * u0) : u0;
             const T h1 = cubic ? u1 * (T(3) * c1 * c1 + T(3) * c1 * u1 + u1 * u1) : u1;
-            acc[q & 1] += h0 * (s_g[d] - half_dt * h0) + h1 * (s_g[d + 1] - half_dt * h1);
+            if constexpr (NOISE) {
+                // 1 / b_d at the node x = c + u (padded coordinates: u = l = 0, no term)
+                const T sx0 = sin_u<T>(c0 + u0), sx1 = sin_u<T>(c1 + u1);
+                const T v0 = k.nz_v * (T(1) + k.nz_vk * sx0 * sx0), v1 = k.nz_v * (T(1) + k.nz_vk * sx1 * sx1);
+                const T ib0 = T(1) / (v0 * v0), ib1 = T(1) / (v1 * v1);
+                acc[q & 1] += (s_l[d] + h0 * (s_g[d] - half_dt * h0)) * ib0 - s_l[d] * s_ibc[d] +
+                              (s_l[d + 1] + h1 * (s_g[d + 1] - half_dt * h1)) * ib1 - s_l[d + 1] * s_ibc[d + 1];
+            } else {
+                acc[q & 1] += h0 * (s_g[d] - half_dt * h0) + h1 * (s_g[d + 1] - half_dt * h1);
+            }
         }
         T tot = acc[0] + acc[1];
         tot = warp_sum_u(tot);
@@ -553,8 +590,10 @@ __device__ __forceinline__ void record_body(const Consts<T>& k, const Bufs<T>& b
 
 template <typename T>
 __global__ void k_obs_prep(Consts<T> k, Bufs<T> b, const double* __restrict__ dy) { obs_prep_body<T>(k, b, dy); }
-template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_loglik(Consts<T> k, Bufs<T> b) { loglik_body<T>(k, b, blockIdx.x, gridDim.x); }
+template <typename T, bool NOISE = false>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) k_loglik(Consts<T> k, Bufs<T> b) {
+    loglik_body<T, NOISE>(k, b, blockIdx.x, gridDim.x);
+}
 template <typename T>
 __global__ void __launch_bounds__(256) k_lse_partials(Consts<T> k, Bufs<T> b, int conditional) {
     lse_partials_body<T>(k, b, conditional, blockIdx.x, gridDim.x);
@@ -670,7 +709,8 @@ cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy
     // partials' space)
     const int nbl = (sizeof(T) == 4 ? 2 : 1) * kNumPartBlocks;
     k_obs_prep<T><<<1, 256, 0, s>>>(k, b, dy);
-    k_loglik<T><<<nbl, 256, 0, s>>>(k, b);
+    if (k.noise == YY_NOISE_DIAG) k_loglik<T, true><<<nbl, 256, 0, s>>>(k, b);
+    else k_loglik<T><<<nbl, 256, 0, s>>>(k, b);
     k_lse_merge<<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0);
     k_moments<T><<<nb, 256, 0, s>>>(k, b);
     k_finalize_scalars<T><<<1, 512, 0, s>>>(k, b, nb, restart_interval, ess_frac);
@@ -688,7 +728,8 @@ cudaError_t launch_update_shard(const Consts<T>& k, const Bufs<T>& b, const doub
     const int nb = kNumPartBlocks;
     const int nbl = (sizeof(T) == 4 ? 2 : 1) * kNumPartBlocks;
     k_obs_prep<T><<<1, 256, 0, s>>>(k, b, dy);
-    k_loglik<T><<<nbl, 256, 0, s>>>(k, b);
+    if (k.noise == YY_NOISE_DIAG) k_loglik<T, true><<<nbl, 256, 0, s>>>(k, b);
+    else k_loglik<T><<<nbl, 256, 0, s>>>(k, b);
     k_lse_merge<<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0, 0);
     k_moments<T><<<nb, 256, 0, s>>>(k, b);
     k_finalize_scalars<T><<<1, 512, 0, s>>>(k, b, nb, 0, 0.0, rec);

@@ -38,8 +38,19 @@ CASES = {
     "scr_lowr_f32s": ("linear", 3, 777, 2.0, 1, "f32s", 3),
     "scr_ragged_f32s": ("cubic", 17, 1000, 0.3, 3, "f32s", 2),
     "scr_rmax_f32s": ("cubic", 1024, 1000, 0.3, 2, "f32s", 11),
+    # the paper's large-scale model: coupled drift, sensor (x - 100)^3
+    "e1_f64": ("paper_e1", 3, 700, 0.3, 2, "f64", 14),
+    "e1_f32": ("paper_e1", 10, 1000, 0.3, 2, "f32", 12),
+    "e1_bf16": ("paper_e1", 100, 2048, 0.3, 2, "bf16", 13),
+    "e1_rmax_bf16": ("paper_e1", 1000, 512, 0.3, 3, "bf16", 15),
+    "e1_odd_f32s": ("paper_e1", 65, 777, 0.3, 2, "f32s", 16),
 }
 TOL = {"f64": 1e-10, "f32": 1e-5, "bf16": 1e-5, "f32s": 1e-5}
+# The large-scale model's sensor (x - 100)^3 is near -1e6: the oracle evaluates
+# h.dy - dt/2 |h|^2 directly, with terms near 1e10 per coordinate, so its own rounding is
+# about r 1e10 2^-53 ~ 1e-5 on log-weights of 1e5..1e6 (the library uses the centred form);
+# its FP64 bar is therefore 1e-9 relative.
+CASE_TOL = {"e1_f64": 1e-9}
 
 
 def _make(case, restart_interval=0, ess_frac=0.0, scrambled=True, restart_init="gauss"):
@@ -100,7 +111,7 @@ def test_step_local_parity(yy_lib, name):
     from oracle import filter as F
     case = CASES[name]
     prec = case[5]
-    tol = TOL[prec]
+    tol = CASE_TOL.get(name, TOL[prec])
     flt, p, poly, scr = _make(case)
     u, _ = flt.get_nodes()
     st, dy = _oracle_state(p, u, 2, case[6])

@@ -114,7 +114,7 @@ def test_boundary_mask_rule():
     assert m.tolist() == [True, True, False, False]
 
 
-@pytest.mark.parametrize("model", ["cubic", "linear"])
+@pytest.mark.parametrize("model", ["cubic", "linear", "paper_e1"])
 def test_divergence_closed_form_vs_complex_step(model):
     """Section 6: sum_k Im f_k(x + i h e_k) / h, h = 1e-20, against the closed forms."""
     rng = np.random.default_rng(0)
@@ -122,3 +122,21 @@ def test_divergence_closed_form_vs_complex_step(model):
     cs = mdl.complex_step_divergence(model, x, a=-0.5)
     cf = mdl.divergence(model, x, a=-0.5)
     assert np.allclose(cs, cf, rtol=1e-14, atol=1e-14)
+
+
+def test_paper_e1_model_hand_values_and_matrix_form():
+    """The large-scale test's drift with its matrices written out (upper bidiagonal: the
+    superdiagonal couples x_d to x_{d+1}); sensor (x - 100)^3."""
+    x = np.array([[1.0, 2.0]])
+    # A x = (-0.5 + 0.2, -1.0), A1 x = (-0.3 + 0.6, -0.6)
+    f = mdl.drift("paper_e1", x)
+    assert f[0, 0] == pytest.approx(np.sin(1.0) * -0.3 + np.sin(2.0) * 0.3, abs=1e-15)
+    assert f[0, 1] == pytest.approx(np.sin(2.0) * -1.0 + np.sin(4.0) * -0.6, abs=1e-15)
+    rng = np.random.default_rng(3)
+    r = 9
+    A = np.diag(np.full(r, -0.5)) + np.diag(np.full(r - 1, 0.1), k=1)
+    A1 = np.diag(np.full(r, -0.3)) + np.diag(np.full(r - 1, 0.3), k=1)
+    xs = rng.normal(size=(5, r))
+    ref = np.sin(xs) * (xs @ A.T) + np.sin(2 * xs) * (xs @ A1.T)
+    assert np.allclose(mdl.drift("paper_e1", xs), ref, rtol=0, atol=1e-14)
+    assert mdl.sensor("paper_e1", np.array([[0.0, 101.0]])).tolist() == [[-1e6, 1.0]]
