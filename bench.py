@@ -10,8 +10,10 @@ Prints ONE JSON line (rank 0).
 
 Under torchrun (N > 1) every rank runs an independent trajectory of the same workload
 (different seed); the path shards by trajectory with no collective, so the value is the
-sum of trajectory-steps per second over ranks (weak scaling).  --impl reference times the
-FP64 CPU oracle on a bounded sample of the same workload (rank 0 only).
+sum of trajectory-steps per second over ranks (weak scaling).  --shard rows instead splits
+one filter's target rows across the ranks (all-gathers of rows and records every step;
+strong scaling).  --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload (rank 0 only).
 """
 from __future__ import annotations
 
@@ -335,6 +337,52 @@ def _comparators(w, K, W, tr, device, fp32_steps, est):
     return out
 
 
+def run_sharded(args):
+    """One trajectory of the workload with its target rows split across the ranks (NCCL
+    all-gathers of the rows and records every step); value = filter steps/s of that one
+    filter (strong scaling)."""
+    import torch
+    from paper_2509_16896_gb300 import binding, sharded
+    rank, ws, local, dist = _dist()
+    device = f"cuda:{local}"
+    torch.cuda.set_device(device)
+    w = WORKLOADS[args.workload]
+    prec = args.precision or w.precision
+    W, K = args.warmup, args.steps
+    tr = simulate(w.model, w.r, W + K, w.dt, seed=w.seed)
+    cfg = binding.config_from_workload(w, precision=prec, screen_type=args.screen_type or w.screen_type)
+    sf = sharded.ShardedFilter(cfg, dist, device)
+    sf.init_nodes(sobol_poly_params(w.r, w.seed), sobol_scramble_params(w.r, w.seed), np.zeros(w.r))
+    dys = torch.tensor(tr.dy, dtype=torch.float64, device=device)
+    for k in range(W):
+        sf.step(dys[k])
+    est = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        clk.mark_start()
+        t0 = time.perf_counter()
+        for k in range(W, W + K):
+            sf.step(dys[k])
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        clk.mark_end()
+    t_max = max_over_ranks(t, dist, device)
+    mean, var, ess, z = sf.estimate()
+    if rank == 0:
+        out = {"metric": METRIC, "value": round(K / t_max, 4), "unit": "filter steps/s", "n_gpus": ws, "steps": K,
+               "warmup": W, "ms_per_step": round(1e3 * t_max / K, 4), "higher_is_better": True, "scaling": "strong",
+               "vs_baseline": None, "dtype": prec, "data": "synthetic (seeded Euler-Maruyama cubic sensor, scrambled Sobol nodes)",
+               "config": dict(_config(w, prec, args.screen_type or w.screen_type), partition="target rows split, "
+                              "source set replicated; per step all-gather of rows and records"),
+               "clocks": clk.summary(), "timing": "host wall clock around the K steps (NCCL in the loop)"}
+        print(json.dumps(out), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_yy(args):
     import torch
     rank, ws, local, dist = _dist()
@@ -377,7 +425,18 @@ def run_yy(args):
         if args.fp32_steps > 0:
             sub.update(_comparators(w2, K2, W, tr2, device, args.fp32_steps, est2))
         del f2
+        sub["schedules"] = compare_schedules(w2, device, predicts_per_build=3)
         subs["cubic_r100_n16384"] = sub
+        we = WORKLOADS["paper_e1_r1000_n2000"]
+        re_, fe, tre, _ = measure_single(we, "bf16", we.screen_type, 0, we.steps, W, device, we.seed)
+        re_.pop("est")
+        del fe
+        subs["paper_e1_r1000_n2000"] = {
+            "metric": "filter steps/s", "value": round(re_["value"], 3), "unit": "filter steps/s", "steps": we.steps,
+            "config": _config(we, "bf16", we.screen_type), **{k: v for k, v in re_.items() if k != "value"},
+            "paper_context": {"note": "the paper's own time for this workload (1000 steps, r = 1000, n = 2000), "
+                                      "MATLAB R2023b on an i9-12900K with one RTX 4090; context only",
+                              "seconds_per_1000_steps": 150.54, "steps_per_s": 6.64, "rmse": 1.609}}
         subs["batched_256"] = measure_batch(max(W, 8), min(K, 20), device, "bf16", None, 0)
     if rank != 0:
         if dist is not None:
@@ -422,6 +481,27 @@ def run_yy(args):
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def compare_schedules(w, device, predicts_per_build: int):
+    """The materialised schedule (the paper's offline operator, online log-domain product)
+    against the recomputed prediction on workload w's state after a few steps: the
+    library's tuner times recompute, build and apply and reports its choice for
+    `predicts_per_build` predictions per node set."""
+    import torch
+    from paper_2509_16896_gb300 import binding
+    cfg = binding.config_from_workload(w, precision="bf16", materialise=1)
+    f = binding.Filter(cfg, device=device)
+    f.init_nodes(sobol_poly_params(w.r, w.seed), sobol_scramble_params(w.r, w.seed), np.zeros(w.r))
+    tr = simulate(w.model, w.r, 3, w.dt, seed=w.seed)
+    f.run_steps(torch.tensor(tr.dy, dtype=torch.float64, device=device))
+    torch.cuda.synchronize()
+    choice, (re, bu, ap) = f.tune_materialise(predicts_per_build, reps=3)
+    op_gb = w.n_scales * ((w.n + 255) // 256 * 256) ** 2 * 4 / 1e9
+    f.close()
+    return {"predicts_per_build": predicts_per_build, "recompute_ms": round(re, 4), "build_ms": round(bu, 4),
+            "apply_ms": round(ap, 4), "materialised_chosen": bool(choice), "operator_gb": round(op_gb, 2),
+            "apply_gbs": round(op_gb / (ap / 1e3), 1)}
 
 
 class OracleSample:
@@ -650,7 +730,9 @@ def main():
     ap.add_argument("--mlp-epochs", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-sublines", dest="sublines", action="store_false",
-                    help="skip the r = 100 and batched sub-lines of the default workload")
+                    help="skip the r = 100, batched and large-scale sub-lines of the default workload")
+    ap.add_argument("--shard", default="trajectories", choices=["trajectories", "rows"],
+                    help="N > 1: independent trajectories per rank (default) or one filter's target rows split")
     ap.add_argument("--screen-type", default=None, choices=["bf16", "fp8"],
                     help="operands of the screen's Gram product (default: the workload's)")
     ap.add_argument("--screen-prefix", type=int, default=0,
@@ -660,6 +742,8 @@ def main():
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         run_reference(args)
+    elif args.shard == "rows":
+        run_sharded(args)
     elif args.workload == "batched_256":
         run_batch(args)
     elif args.workload == "cubic_r50_n8192":

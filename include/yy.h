@@ -155,6 +155,11 @@ typedef struct {
     int32_t noise_u_zero;      /* DIAG: leading coordinates without state noise, 0..r */
     double noise_u, noise_u_kappa;   /* DIAG: U_d(x) = noise_u (1 + noise_u_kappa sin^2 x_d); > 0, >= 0 */
     double noise_v, noise_v_kappa;   /* DIAG: V_d(x) = noise_v (1 + noise_v_kappa sin^2 x_d); > 0, >= 0 */
+    int32_t materialise;       /* float precisions, single filters: 0 = the prediction recomputes its
+                                * kernel sums every step; 1 = the workspace also holds the
+                                * materialised per-scale log-operator (N n_pad^2 floats) and
+                                * yy_tune_materialise chooses between the two schedules (recompute
+                                * until it is called); 2 = always the materialised operator */
 } yy_config;
 
 /* Bytes of device workspace that yy_create needs for cfg (0 if cfg is invalid). */
@@ -421,6 +426,26 @@ YY_EXPORT yy_status yy_weighted_moments_static(const float* d_u, int64_t n, int3
  * no counterpart in the paper: it lets a caller bound how long a stalled launch can hold
  * the GPU, and lets a test make a wait expire. */
 YY_EXPORT yy_status yy_set_wait_limit(yy_filter* f, double seconds);
+
+/* The materialised schedule of the prediction (the paper's offline operator and online
+ * matrix-vector product, Sections "Algorithm for Kolmogorov Equation" and "CPU/GPU
+ * Parallel Acceleration", in its log-domain form, Section "Log-Domain Computation"):
+ * per scale j the matrix A_j(i, s) = -|u_i - tau_j f_i - u_s|^2 / (2 tau_j) (the pair part of
+ * log K_{tau_j}, float32, [N][n_pad][n_pad]) is built once per node set -- on the device at
+ * the first prediction after a restart or a state change, so graphs replay it correctly --
+ * and each prediction is the log-sum-exp product L_j(i) = C_j - tau_j div f_i +
+ * LSE_s(A_j(i, s) + ell_s), combined across scales as in yy_predict.  The paper applies
+ * one combined operator; with the negative coefficients of the multi-scale kernel its
+ * logarithm is not defined everywhere, so the scales are kept apart (results equal the
+ * recomputed ones within float32 rounding).
+ * yy_tune_materialise times, on the handle's current state (reps launches each), the
+ * recomputed prediction, the build and the apply, and chooses the materialised schedule
+ * when build + m apply < m recompute, m = predicts_per_build (the predictions a node set
+ * serves between restarts: the restart interval when restarts are by interval only).
+ * h_ms (host double [3], may be NULL) receives the three times in ms, *h_choice 1 when the
+ * materialised schedule was chosen.  Needs cfg.materialise >= 1.  Synchronous. */
+YY_EXPORT yy_status yy_tune_materialise(yy_filter* f, int32_t predicts_per_build, int32_t reps, double* h_ms,
+                                        int32_t* h_choice);
 
 /* Kernel launches issued by this handle so far (for launch accounting). */
 YY_EXPORT int64_t yy_launch_count(const yy_filter* f);

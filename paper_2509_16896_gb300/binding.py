@@ -46,7 +46,7 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train",
            "yy_mlp_set_input_norm", "yy_get_screen", "yy_batch_set_routing",
            "yy_set_wait_limit", "yy_set_shard", "yy_shard_rows", "yy_update_shard", "yy_merge_shards",
-           "yy_merge_records_host", "yy_init_nodes_lds")
+           "yy_merge_records_host", "yy_init_nodes_lds", "yy_tune_materialise")
 
 
 class YYError(RuntimeError):
@@ -65,7 +65,8 @@ class YYConfig(ctypes.Structure):
                 ("restart_rule", ctypes.c_int32), ("screen_prefix", ctypes.c_int32),
                 ("screen_type", ctypes.c_int32), ("noise", ctypes.c_int32), ("noise_u_zero", ctypes.c_int32),
                 ("noise_u", ctypes.c_double), ("noise_u_kappa", ctypes.c_double),
-                ("noise_v", ctypes.c_double), ("noise_v_kappa", ctypes.c_double)]
+                ("noise_v", ctypes.c_double), ("noise_v_kappa", ctypes.c_double),
+                ("materialise", ctypes.c_int32)]
 
 
 def _declare(L: ctypes.CDLL) -> None:
@@ -116,6 +117,7 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_merge_shards": (I32, [P, P, P, I32]),
         "yy_merge_records_host": (I32, [P, I32, I32, P]),
         "yy_init_nodes_lds": (I32, [P, I32, P, P]),
+        "yy_tune_materialise": (I32, [P, I32, I32, P, P]),
         "yy_get_box": (I32, [P, P, P]),
         "yy_set_restart_mlp": (I32, [P, P]),
         "yy_mlp_param_count": (I64, [I32, I32]),
@@ -168,7 +170,7 @@ def make_config(model: str, r: int, n: int, dt: float, R: float, n_scales: int,
                 precision: str, restart_interval: int = 0, ess_frac: float = 0.0,
                 model_a: float = -0.5, restart_init: str = "gauss", prior_mean: float = 0.0,
                 prior_var: float = 1.0, restart_rule: str = "plain", screen_prefix: int = 0,
-                screen_type: str = "bf16", noise: dict | None = None) -> YYConfig:
+                screen_type: str = "bf16", noise: dict | None = None, materialise: int = 0) -> YYConfig:
     """noise: None (unit noise) or diagonal noise coefficients {u, u_kappa, u_zero, v, v_kappa}
     (include/yy.h, yy_noise)."""
     nz = noise or {}
@@ -180,7 +182,8 @@ def make_config(model: str, r: int, n: int, dt: float, R: float, n_scales: int,
                     screen_prefix=screen_prefix, screen_type=SCREEN_TYPE[screen_type],
                     noise=1 if noise else 0, noise_u_zero=int(nz.get("u_zero", 0)),
                     noise_u=float(nz.get("u", 1.0)), noise_u_kappa=float(nz.get("u_kappa", 0.0)),
-                    noise_v=float(nz.get("v", 1.0)), noise_v_kappa=float(nz.get("v_kappa", 0.0)))
+                    noise_v=float(nz.get("v", 1.0)), noise_v_kappa=float(nz.get("v_kappa", 0.0)),
+                    materialise=materialise)
 
 
 def config_from_workload(w, precision: str | None = None, **over) -> YYConfig:
@@ -325,6 +328,14 @@ class Filter:
 
     def launches(self) -> int:
         return int(self.lib.yy_launch_count(self.h))
+
+    def tune_materialise(self, predicts_per_build: int, reps: int = 3):
+        """Times recompute, build and apply; returns (choice 0/1, (ms recompute, build, apply))."""
+        ms = np.zeros(3)
+        ch = ctypes.c_int32()
+        _check("yy_tune_materialise", self.lib.yy_tune_materialise(self.h, predicts_per_build, reps, _ptr(ms),
+                                                                   ctypes.byref(ch)))
+        return ch.value, tuple(ms)
 
     def set_wait_limit(self, seconds: float) -> None:
         _check("yy_set_wait_limit", self.lib.yy_set_wait_limit(self.h, float(seconds)))

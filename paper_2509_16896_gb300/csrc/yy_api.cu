@@ -104,6 +104,7 @@ bool cfg_valid(const yy_config* c) {
             return false;
         if (c->noise_u_zero < 0 || c->noise_u_zero > c->r) return false;
     }
+    if (c->materialise < 0 || c->materialise > 2) return false;
     return true;
 }
 
@@ -112,7 +113,9 @@ bool cfg_valid(const yy_config* c) {
 // update does not separate from state-dependent b(x)).
 bool cfg_supported(const yy_config* c) {
     if (c->noise == YY_NOISE_DIAG)
-        return (c->precision == YY_PREC_FP32 || c->precision == YY_PREC_FP64) && c->model != YY_MODEL_PAPER_E1;
+        return (c->precision == YY_PREC_FP32 || c->precision == YY_PREC_FP64) && c->model != YY_MODEL_PAPER_E1 &&
+               c->materialise == 0;
+    if (c->materialise != 0) return c->precision != YY_PREC_FP64;   // the operator is float32
     return true;
 }
 
@@ -162,6 +165,8 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
         b.minv = cv.take<T>(nr * sizeof(T));
         b.hld = cv.take<T>(n_pad * sizeof(T));
     }
+    if (c->materialise != 0 && c->precision != YY_PREC_FP64)
+        b.op = cv.take<float>((size_t)c->n_scales * (size_t)n_pad * (size_t)n_pad * sizeof(float));
     b.dimc = cv.take<T>(5 * (size_t)r_pad * sizeof(T));
     b.next_centre = cv.take<double>(r_pad * sizeof(double));
     b.next_half = cv.take<double>(r_pad * sizeof(double));
@@ -169,8 +174,9 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.part = cv.take<double>(part_bytes(r_pad));
     b.part_list = cv.take<int>((size_t)kNumPartBlocks * sizeof(int));
     b.stats = cv.take<DevStats>(sizeof(DevStats));
-    if (c->precision == YY_PREC_BF16) {
+    if (c->precision == YY_PREC_BF16 || c->precision == YY_PREC_FP32_SCREEN)
         b.nu_chunk = cv.take<float>((size_t)n_pad * (r_pad / kColAlign) * sizeof(float));
+    if (c->precision == YY_PREC_BF16) {
         b.tc_q = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_q1 = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_q1t = cv.take<float>((size_t)n_pad * sizeof(float));
@@ -306,9 +312,13 @@ yy_status cuda_status(cudaError_t e) { return e == cudaSuccess ? YY_OK : YY_ERR_
 __global__ void k_set_stats(DevStats* st, double lognorm, long long step) {
     st->lognorm = lognorm;
     st->step = step;
+    st->op_stale = 1;   // the centre may have moved
 }
 
-__global__ void k_init_cref(DevStats* st, double c_ref) { st->c_ref = c_ref; }
+__global__ void k_init_cref(DevStats* st, double c_ref) {
+    st->c_ref = c_ref;
+    st->op_stale = 1;   // a new node set
+}
 
 // The first `count` primes (trial division by the primes found so far).
 std::vector<uint32_t> first_primes_host(int count) {
@@ -429,6 +439,7 @@ yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t bytes, void*
     f->row1 = cfg->n;
     f->shard_rank = 0;
     f->shard_count = 1;
+    f->use_op = (cfg->materialise == 2);
     multiscale_coefficients(cfg->n_scales, f->coef);
     if (f->fp64) carve<double>(cfg, f->ws, &f->bd);
     else carve<float>(cfg, f->ws, &f->bf);
@@ -491,6 +502,12 @@ yy_status yy_predict(yy_filter* f) {
         e = cudaMemsetAsync(&f->bd.stats->clamps, 0, sizeof(unsigned), f->stream);
         if (e == cudaSuccess) e = launch_ksum_simt<double>(f->kd, f->bd, f->stream);
         f->launches += 1;
+    } else if (f->use_op) {
+        // materialised schedule: rebuild on the device if the node set moved, then apply
+        e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
+        if (e == cudaSuccess) e = launch_op_build(f->kf, f->bf, false, f->stream);
+        if (e == cudaSuccess) e = launch_op_apply(f->kf, f->bf, f->stream);
+        f->launches += 2;
     } else if (f->cfg.precision == YY_PREC_FP32) {
         e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
         if (e == cudaSuccess) e = launch_ksum_simt<float>(f->kf, f->bf, f->stream);
@@ -735,6 +752,44 @@ yy_status yy_get_clamps(yy_filter* f, int64_t* h_clamps) {
 }
 
 int64_t yy_launch_count(const yy_filter* f) { return f ? f->launches : 0; }
+
+yy_status yy_tune_materialise(yy_filter* f, int32_t predicts_per_build, int32_t reps, double* h_ms,
+                               int32_t* h_choice) {
+    if (!f || predicts_per_build < 1 || reps < 1) return YY_ERR_ARG;
+    if (f->cfg.materialise == 0 || f->fp64 || !f->bf.op) return YY_ERR_UNSUPPORTED;
+    if (!f->nodes_ready || f->predicted || f->shard_updated) return YY_ERR_STATE;
+    cudaEvent_t ev[6];
+    for (auto& x : ev)
+        if (cudaEventCreate(&x) != cudaSuccess) return YY_ERR_CUDA;
+    const bool keep = f->use_op;
+    cudaError_t e = cudaSuccess;
+    // recomputed prediction
+    f->use_op = false;
+    cudaEventRecord(ev[0], f->stream);
+    for (int q = 0; q < reps && e == cudaSuccess; ++q) e = (yy_predict(f) == YY_OK) ? cudaSuccess : cudaErrorUnknown;
+    cudaEventRecord(ev[1], f->stream);
+    // build (forced) and apply
+    for (int q = 0; q < reps && e == cudaSuccess; ++q) e = launch_op_build(f->kf, f->bf, true, f->stream);
+    cudaEventRecord(ev[2], f->stream);
+    for (int q = 0; q < reps && e == cudaSuccess; ++q) e = launch_op_apply(f->kf, f->bf, f->stream);
+    cudaEventRecord(ev[3], f->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev[3]);
+    float t_re = 0.f, t_build = 0.f, t_apply = 0.f;
+    if (e == cudaSuccess) {
+        cudaEventElapsedTime(&t_re, ev[0], ev[1]);
+        cudaEventElapsedTime(&t_build, ev[1], ev[2]);
+        cudaEventElapsedTime(&t_apply, ev[2], ev[3]);
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    f->launches += (int64_t)reps * 2;
+    f->predicted = false;   // the timing predictions leave the weights as they were
+    if (e != cudaSuccess) { f->use_op = keep; return YY_ERR_CUDA; }
+    const double re = t_re / reps, bu = t_build / reps, ap = t_apply / reps;
+    f->use_op = (f->cfg.materialise == 2) || (bu + predicts_per_build * ap < predicts_per_build * re);
+    if (h_ms) { h_ms[0] = re; h_ms[1] = bu; h_ms[2] = ap; }
+    if (h_choice) *h_choice = f->use_op ? 1 : 0;
+    return YY_OK;
+}
 
 yy_status yy_set_wait_limit(yy_filter* f, double seconds) {
     if (!f || !(seconds > 0.0) || seconds > 3600.0) return YY_ERR_ARG;

@@ -30,6 +30,7 @@ struct yy_filter {
     int shard_rank, shard_count;  // 0, 1 for a whole filter
     bool shard_updated;           // yy_update_shard ran; yy_merge_shards completes the step
     int node_kind;                // yy_nodes of the last node generation
+    bool use_op;                  // the prediction applies the materialised operator
 };
 
 namespace yy {

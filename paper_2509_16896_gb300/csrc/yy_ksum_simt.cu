@@ -18,6 +18,8 @@
 // step; each of the 256 threads holds a 4x4 block of (S1, S2) accumulators and, per
 // target and scale, an online (max, sum) of the exponentials, merged across the 16
 // threads of a target group at the end.
+#include <algorithm>
+
 #include "yy_combine.cuh"
 
 namespace yy {
@@ -31,8 +33,12 @@ template <> __device__ __forceinline__ double exp_fast<double>(double x) { retur
 }  // namespace
 
 // SCREEN (float32 only): before a source tile is evaluated, the squared distance of each
-// of its pairs over the first k1 coordinates -- a lower bound of the full |u_i - u_s|^2,
-// formed exactly as the full sum's first terms -- is compared with rho_i^2, where
+// of its pairs over the first k1 coordinates -- a lower bound of the full |u_i - u_s|^2 --
+// is bounded from below through its Gram form q_i + q_s - 2 G (q the norms over those
+// coordinates from the preparation pass, G = sum u_i u_s by one FMA per coordinate), less
+// the rounding allowance 3 gamma_k1 (q_i + q_s) of the FMA chain (gamma_k = k 2^-24 /
+// (1 - k 2^-24); 2 |u_i||u_s| <= q_i + q_s) and 1e-5 (q_i + q_s) for the norms' own
+// rounding, and compared with rho_i^2, where
 //     rho_i = max_j [tau_j |f_i| + sqrt(2 tau_j max(0, lmax - (ell_i - tau_j |f_i|^2 / 2) + T))],
 // lmax the largest live source log-weight, ell_i - tau_j |f_i|^2 / 2 the exact self term of
 // row i (a lower bound of its largest term) and T = ln n + 20.  By the triangle inequality
@@ -45,7 +51,10 @@ template <> __device__ __forceinline__ double exp_fast<double>(double x) { retur
 // NOISE (diagonal noise coefficients): the squared distance and the drift's inner product
 // take the target's metric a(x_i)^+, S1 = sum_d m_d D_d^2, S2 = sum_d m_d D_d f_d, with
 // |f_i|^2 in the same metric (nf) and -1/2 log det_+ a(x_i) added in the combination.
-template <typename T, int N, bool SCREEN = false, bool NOISE = false>
+// OPBUILD (float32): the materialised operator -- every pair's score without the source
+// weight, A_j(i, s) = -S1 / (2 tau_j) + S2 - tau_j |f_i|^2 / 2, is written to b.op instead of
+// being accumulated.
+template <typename T, int N, bool SCREEN = false, bool NOISE = false, bool OPBUILD = false>
 __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>& b, int rk, int bid, int k1 = 0) {
     __shared__ T At[BK][BM];   // u of targets
     __shared__ T Ft[BK][BM];   // f of targets
@@ -60,6 +69,9 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
     T rowc[TM][N];          // -(tau_j / 2) |f_i|^2
     T mx[TM][N], sm[TM][N];
     T rho2[TM];             // SCREEN: squared screening radius of each row
+    T q1t[TM];              // SCREEN: first-pass norms of the target rows
+    __shared__ T q1s[SCREEN ? BN : 1];   // SCREEN: first-pass norms of the tile's sources
+    const T gam = SCREEN ? T(3.03) * (T)k1 * T(5.9604645e-8) + T(1e-5) : T(0);   // rounding allowance per (q_i + q_s)
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
         const long long i = i0 + ty * TM + a;
@@ -71,6 +83,11 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
             sm[a][j] = T(0);
         }
         rho2[a] = T(-1);   // no candidates (padded or masked rows)
+        if constexpr (SCREEN) {   // first-pass norm of the target row
+            q1t[a] = T(0);
+            if (i < k.n)
+                for (int c = 0; c < k1 / 64; ++c) q1t[a] += b.nu_chunk[(size_t)i * (k.r_pad / 64) + c];
+        }
         if constexpr (SCREEN) {
             if (i < k.n && !b.mask[i]) {
                 const T li = b.logw[i];
@@ -101,9 +118,15 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
         if (tid < BN) {
             const long long s = s0 + tid;
             lsrc[tid] = (s < k.n && !b.mask[s]) ? b.logw[s] : T(-INFINITY);
+            if constexpr (SCREEN) {
+                T q = T(0);
+                if (s < k.n)
+                    for (int c = 0; c < k1 / 64; ++c) q += b.nu_chunk[(size_t)s * (k.r_pad / 64) + c];
+                q1s[tid] = q;
+            }
         }
         if constexpr (SCREEN) {
-            // first pass: partial squared distances over coordinates [0, k1)
+            // first pass: Gram products G over coordinates [0, k1)
             for (int d0 = 0; d0 < k1; d0 += BK) {
                 __syncthreads();
 #pragma unroll
@@ -124,18 +147,18 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
 #pragma unroll
                     for (int a = 0; a < TM; ++a)
 #pragma unroll
-                        for (int c = 0; c < TN; ++c) {
-                            const T dlt = av[a] - bv[c];
-                            S1[a][c] = fma(dlt, dlt, S1[a][c]);
-                        }
+                        for (int c = 0; c < TN; ++c) S1[a][c] = fma(av[a], bv[c], S1[a][c]);
                 }
             }
             int any = 0;
 #pragma unroll
             for (int a = 0; a < TM; ++a)
 #pragma unroll
-                for (int c = 0; c < TN; ++c)
-                    any |= (S1[a][c] <= rho2[a] && lsrc[tx * TN + c] != T(-INFINITY)) ? 1 : 0;
+                for (int c = 0; c < TN; ++c) {
+                    const T qq = q1t[a] + q1s[tx * TN + c];
+                    const T lower = qq - T(2) * S1[a][c] - gam * qq;   // lower bound of the partial |u_i - u_s|^2
+                    any |= (lower <= rho2[a] && lsrc[tx * TN + c] != T(-INFINITY)) ? 1 : 0;
+                }
             if (!__syncthreads_or(any)) continue;   // every pair of the tile is negligible
 #pragma unroll
             for (int a = 0; a < TM; ++a)
@@ -179,6 +202,24 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
                     }
             }
         }
+        if constexpr (OPBUILD) {
+            const size_t plane = (size_t)k.n_pad * (size_t)k.n_pad;
+#pragma unroll
+            for (int a = 0; a < TM; ++a) {
+                const long long i = i0 + ty * TM + a;
+#pragma unroll
+                for (int j = 0; j < N; ++j) {
+                    float4 v;
+                    v.x = (float)(fma(-S1[a][0], k.inv2tau[j], S2[a][0]) + rowc[a][j]);
+                    v.y = (float)(fma(-S1[a][1], k.inv2tau[j], S2[a][1]) + rowc[a][j]);
+                    v.z = (float)(fma(-S1[a][2], k.inv2tau[j], S2[a][2]) + rowc[a][j]);
+                    v.w = (float)(fma(-S1[a][3], k.inv2tau[j], S2[a][3]) + rowc[a][j]);
+                    *reinterpret_cast<float4*>(b.op + j * plane + (size_t)i * k.n_pad + s0 + tx * TN) = v;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         // scores and online log-sum-exp for this source tile
         T ls[TN];
 #pragma unroll
@@ -205,6 +246,7 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
         __syncthreads();
     }
 
+    if constexpr (OPBUILD) return;
     // merge the 16 threads that share a target group (lanes differing in the low 4 bits)
 #pragma unroll
     for (int a = 0; a < TM; ++a)
@@ -246,6 +288,92 @@ __global__ void __launch_bounds__(256) k_ksum_scr32(Consts<float> k, Bufs<float>
     ksum_simt_body<float, N, true>(k, b, rk, (int)(k.row0 / BM) + blockIdx.x, k1);
 }
 
+// Materialised operator: built only when the node set moved since the last build (the flag
+// is set by restarts and state changes, cleared by the apply), unless forced.
+template <int N>
+__global__ void __launch_bounds__(256) k_op_build(Consts<float> k, Bufs<float> b, int rk, int force) {
+    if (!force && b.stats->op_stale == 0) return;
+    ksum_simt_body<float, N, false, false, true>(k, b, rk, (int)(k.row0 / BM) + blockIdx.x);
+}
+
+// L_j(i) = log sum_s exp(A_j(i, s) + ell_s) over live sources, one warp per target row
+// (float4 loads of the row, an online (max, sum) per lane, a warp merge), then the signed
+// combination of the scales with the identity term.
+template <int N>
+__global__ void __launch_bounds__(256) k_op_apply(Consts<float> k, Bufs<float> b) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) b.stats->op_stale = 0;
+    const int lane = threadIdx.x & 31;
+    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    const size_t plane = (size_t)k.n_pad * (size_t)k.n_pad;
+    for (long long i = k.row0 + warp; i < k.row1; i += nwarps) {
+        float mx[N], sm[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const float4* row = reinterpret_cast<const float4*>(b.op + j * plane + (size_t)i * k.n_pad);
+            float m = -INFINITY, s = 0.f;
+            for (long long q = lane; q * 4 < k.n; q += 32) {
+                const float4 a = row[q];
+                const float av[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const long long src = q * 4 + c;
+                    if (src >= k.n || b.mask[src]) continue;
+                    const float v = av[c] + b.logw[src];
+                    if (v == -INFINITY) continue;
+                    if (v > m) { s = (m == -INFINITY) ? 1.f : s * exp_fast<float>(m - v) + 1.f; m = v; }
+                    else s += exp_fast<float>(v - m);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const float m2 = __shfl_xor_sync(0xffffffffu, m, o), s2 = __shfl_xor_sync(0xffffffffu, s, o);
+                if (m2 != -INFINITY) {
+                    if (m == -INFINITY) { m = m2; s = s2; }
+                    else if (m2 > m) { s = s * exp_fast<float>(m - m2) + s2; m = m2; }
+                    else s += s2 * exp_fast<float>(m2 - m);
+                }
+            }
+            mx[j] = m;
+            sm[j] = s;
+        }
+        if (lane == 0)
+            b.logw_pred[i] = b.mask[i] ? -INFINITY
+                                       : combine_scales<float, N>(k, mx, sm, b.divf[i], b.logw[i], b.stats->c_ref,
+                                                                  &b.stats->clamps);
+    }
+}
+
+cudaError_t launch_op_build(const Consts<float>& k, const Bufs<float>& b, bool force, cudaStream_t s) {
+    if (!b.op) return cudaErrorInvalidValue;
+    const int rk = ((k.r + BK - 1) / BK) * BK;
+    const unsigned grid = (unsigned)((k.row1 - k.row0 + BM - 1) / BM);
+    if (grid == 0) return cudaSuccess;
+    switch (k.N) {
+        case 1: k_op_build<1><<<grid, 256, 0, s>>>(k, b, rk, force ? 1 : 0); break;
+        case 2: k_op_build<2><<<grid, 256, 0, s>>>(k, b, rk, force ? 1 : 0); break;
+        case 3: k_op_build<3><<<grid, 256, 0, s>>>(k, b, rk, force ? 1 : 0); break;
+        case 4: k_op_build<4><<<grid, 256, 0, s>>>(k, b, rk, force ? 1 : 0); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_op_apply(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s) {
+    if (!b.op) return cudaErrorInvalidValue;
+    const long long rows = k.row1 - k.row0;
+    const unsigned grid = (unsigned)std::min<long long>((rows + 7) / 8, 152 * 8);   // 8 rows per block of 8 warps
+    if (grid == 0) return cudaSuccess;
+    switch (k.N) {
+        case 1: k_op_apply<1><<<grid, 256, 0, s>>>(k, b); break;
+        case 2: k_op_apply<2><<<grid, 256, 0, s>>>(k, b); break;
+        case 3: k_op_apply<3><<<grid, 256, 0, s>>>(k, b); break;
+        case 4: k_op_apply<4><<<grid, 256, 0, s>>>(k, b); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // Largest live source log-weight (the screen's lmax), one block.
 __global__ void __launch_bounds__(1024) k_live_lmax(Consts<float> k, Bufs<float> b) {
     __shared__ float red[32];
@@ -262,13 +390,15 @@ __global__ void __launch_bounds__(1024) k_live_lmax(Consts<float> k, Bufs<float>
     }
 }
 
-// Screened float32 form: first pass over k1 coordinates (multiple of 16, 16 <= k1 <= r
-// rounded up to 16), then exact evaluation of every tile that keeps a candidate.
+// Screened float32 form: first pass over k1 coordinates (a multiple of 64, 64 <= k1 <= r
+// rounded up to 64: the first-pass norms come in chunks of 64), then exact evaluation of
+// every tile that keeps a candidate.
 cudaError_t launch_ksum_scr32(const Consts<float>& k, const Bufs<float>& b, int k1, cudaStream_t s) {
+    if (!b.nu_chunk) return cudaErrorInvalidValue;
     const int rk = ((k.r + BK - 1) / BK) * BK;
-    k1 = ((k1 + BK - 1) / BK) * BK;
-    if (k1 < BK) k1 = BK;
-    if (k1 > rk) k1 = rk;
+    k1 = ((k1 + 63) / 64) * 64;
+    if (k1 < 64) k1 = 64;
+    if (k1 > k.r_pad) k1 = k.r_pad;
     const unsigned grid = (unsigned)((k.row1 - k.row0 + BM - 1) / BM);   // the handle's target blocks
     if (grid == 0) return cudaSuccess;
     k_live_lmax<<<1, 1024, 0, s>>>(k, b);

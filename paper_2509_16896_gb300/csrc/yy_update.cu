@@ -566,6 +566,7 @@ __device__ __forceinline__ void restart_commit_body(const Consts<T>& k, const Bu
         b.stats->restarts += 1;
         b.stats->restart_flag = 0;
         b.stats->last_restarted = 1;
+        b.stats->op_stale = 1;   // the nodes moved: a materialised operator is rebuilt
     }
 }
 

@@ -43,8 +43,9 @@ def combination_err_ok(gpu, ref, Lj, coef, logw, tol, eps=2.0 ** -24):
     ref = np.asarray(ref, dtype=np.float64)
     assert np.array_equal(np.isneginf(gpu), np.isneginf(ref))
     N = Lj.shape[1]
-    terms = np.concatenate([np.exp(Lj - ref[:, None]) * coef[:N], (coef[N] * np.exp(logw - ref))[:, None]], axis=1)
-    with np.errstate(invalid="ignore", divide="ignore"):
+    with np.errstate(invalid="ignore", divide="ignore", over="ignore"):
+        terms = np.concatenate([np.exp(Lj - ref[:, None]) * coef[:N], (coef[N] * np.exp(logw - ref))[:, None]],
+                               axis=1)
         kappa = np.abs(terms).sum(1) / np.abs(terms.sum(1))
     fin = np.isfinite(ref)
     big = np.max(np.abs(np.where(np.isfinite(Lj), Lj, 0.0)), axis=1)
