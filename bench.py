@@ -428,12 +428,12 @@ def run_yy(args):
         sub["schedules"] = compare_schedules(w2, device, predicts_per_build=3)
         subs["cubic_r100_n16384"] = sub
         we = WORKLOADS["paper_e1_r1000_n2000"]
-        re_, fe, tre, _ = measure_single(we, "bf16", we.screen_type, 0, we.steps, W, device, we.seed)
+        re_, fe, tre, _ = measure_single(we, we.precision, we.screen_type, 0, we.steps, W, device, we.seed)
         re_.pop("est")
         del fe
         subs["paper_e1_r1000_n2000"] = {
             "metric": "filter steps/s", "value": round(re_["value"], 3), "unit": "filter steps/s", "steps": we.steps,
-            "config": _config(we, "bf16", we.screen_type), **{k: v for k, v in re_.items() if k != "value"},
+            "config": _config(we, we.precision, we.screen_type), **{k: v for k, v in re_.items() if k != "value"},
             "paper_context": {"note": "the paper's own time for this workload (1000 steps, r = 1000, n = 2000), "
                                       "MATLAB R2023b on an i9-12900K with one RTX 4090; context only",
                               "seconds_per_1000_steps": 150.54, "steps_per_s": 6.64, "rmse": 1.609}}

@@ -55,11 +55,14 @@ WORKLOADS: dict[str, Workload] = {
 # drift sin(x) (A x) + sin(2x) (A1 x), sensor (x - 100)^3, x_0 ~ N(0, I), dt = 0.01, 1000
 # steps, Sobol nodes, R = 0.3, restart every second step, at the paper's pairs of dimension
 # and node count.  The paper gives no kernel order; two bandwidths are used, as for the
-# other workloads, and no ESS trigger (the paper restarts on the interval only).
+# other workloads, and no ESS trigger (the paper restarts on the interval only).  The
+# sensor's log-likelihood spreads the weights over 1e5 nats or more, so a rigorous screen
+# keeps nearly every pair of the low-weight rows: these small node sets run the plain
+# float32 form (the routing the batch autotuner applies to such members).
 for _i, (_r, _n) in enumerate([(10, 100), (50, 300), (100, 500), (300, 800), (600, 1000), (1000, 2000)]):
     _name = f"paper_e1_r{_r}_n{_n}"
     WORKLOADS[_name] = Workload(_name, "paper_e1", r=_r, n=_n, steps=1000, n_scales=2, restart_interval=2,
-                                ess_frac=0.0, seed=20 + _i, precision="bf16")
+                                ess_frac=0.0, seed=20 + _i, precision="f32")
 
 
 def get_workload(name: str) -> Workload:
