@@ -2,18 +2,21 @@
  * yy.h -- C ABI of libyy, the GB300 (sm_103a) online stage of the improved Yau--Yau
  * filter (arXiv 2509.16896).
  *
- * The filtering problem (Section 2.1, eq. NonlinearFilter) is
+ * The paper is cited by section title.  The filtering problem ("Continuous-Time Nonlinear
+ * Filtering Problem", eq. NonlinearFilter) is
  *     dX = f(X) dt + dV,   dY = h(X) dt + dW,   X in R^r, Y in R^m,
  * with unit-covariance Brownian motions.  The library carries the unnormalised
  * conditional density as log-weights on n scrambled-Sobol nodes in a box
  * [c - R, c + R]^r and advances it one observation step at a time:
- *     yy_predict   prediction by the N-scale kernel operator (Sections 4.1-4.3,
- *                  eq. general_kernel) in log-sum-exp form (Section 7, Prediction Step)
- *     yy_update    Ito-corrected likelihood update (Section 2.2, Online stage), log-domain
- *                  normalisation (Section 7, Normalization), posterior mean (Section 2.2,
- *                  step 4), variance and effective sample size
+ *     yy_predict   prediction by the N-scale kernel operator ("Solving Kolmogorov Equations
+ *                  via Low-Discrepancy Sampling and Kernel Approximation", eq.
+ *                  general_kernel) in log-sum-exp form ("Log-Domain Computation")
+ *     yy_update    Ito-corrected likelihood update ("Procedure for the Improved Yau-Yau
+ *                  Algorithm", online stage), log-domain normalisation ("Log-Domain
+ *                  Computation"), posterior mean (the procedure's step 4), variance and
+ *                  effective sample size
  *     yy_estimate  copies the estimates to the host
- *     yy_restart   local resampling-restart (Section 5)
+ *     yy_restart   local resampling-restart ("Local Resampling-Restart Mechanism")
  *
  * Conventions shared by every entry point
  *   - Memory.  Device memory is owned by the caller: it passes one device workspace of at
@@ -30,8 +33,8 @@
  *     yy_estimate returns.
  *   - Models.  m = r; h is componentwise.  YY_MODEL_CUBIC: f(x) = cos x, h(x) = x^3.
  *     YY_MODEL_LINEAR: f(x) = a x, h(x) = x.  YY_MODEL_PAPER_E1 (the paper's large-scale
- *     scalability test, Section 9 "Large-Scale Scalability Test"): f(x) = sin(x) (A x) +
- *     sin(2x) (A1 x) elementwise with A, A1 upper bidiagonal (diagonal -0.5 / -0.3,
+ *     scalability test, "Large-Scale Scalability Test"): f(x) = sin(x) (A x) + sin(2x) (A1 x)
+ *     elementwise with A, A1 upper bidiagonal (diagonal -0.5 / -0.3,
  *     superdiagonal 0.1 / 0.3), h(x) = (x - 100)^3.
  *   - Layout.  Node coordinates are float32 box coordinates u (x = c + u), rows of
  *     r values, row-major; host arrays passed in or out are dense [n][r].
@@ -90,12 +93,13 @@ typedef enum { YY_NODES_SOBOL = 0, YY_NODES_HALTON = 1, YY_NODES_FAURE = 2 } yy_
  * float32 rounding).  Not accepted by batches. */
 typedef enum { YY_PREC_FP64 = 0, YY_PREC_FP32 = 1, YY_PREC_BF16 = 2, YY_PREC_FP32_SCREEN = 3 } yy_precision;
 
-/* Log-weights after a restart (Section 5 only says the filter restarts at x_hat):
+/* Log-weights after a restart ("Local Resampling-Restart Mechanism" only says that the
+ * filter restarts at x_hat):
  * GAUSS = log N(x; x_hat, diag(max(v_hat, (R/4)^2))), UNIFORM = equal weights. */
 typedef enum { YY_RESTART_INIT_GAUSS = 0, YY_RESTART_INIT_UNIFORM = 1 } yy_restart_init;
 
-/* Where a restart puts the new box.  PLAIN: centre x_hat, half-widths unchanged (Section
- * 5).  LEARNED: centre x_hat + delta and half-widths R exp(lambda) from the restart-proposal
+/* Where a restart puts the new box.  PLAIN: centre x_hat, half-widths unchanged ("Local
+ * Resampling-Restart Mechanism").  LEARNED: centre x_hat + delta and half-widths R exp(lambda) from the restart-proposal
  * network attached with yy_set_restart_mlp (a library addition, not in the paper); it falls
  * back to PLAIN when no network is attached, when an output is not finite, when a
  * half-width leaves [R/8, 8R], or when the box would not contain x_hat. */
@@ -174,10 +178,11 @@ YY_EXPORT yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t by
 /* Releases the host handle (the workspace stays the caller's). NULL is accepted. */
 YY_EXPORT yy_status yy_destroy(yy_filter* f);
 
-/* Node generation (Appendix A, Sobol Sequence; Section 2.2, step 1): generates the n
- * scrambled Sobol points on the device and maps them to the box, then evaluates the
- * prior log-weights log sigma_0 (Section 4.2, step 4) and the Dirichlet mask (Section
- * 4.2, step 3).
+/* Node generation ("Sobol Sequence" in the appendix "Low-Discrepancy Sequence Sampling";
+ * step 1 of "Procedure for the Improved Yau-Yau Algorithm"): generates the n scrambled
+ * Sobol points on the device and maps them to the box, then evaluates the prior
+ * log-weights log sigma_0 and the Dirichlet mask ("Algorithm for Kolmogorov Equation",
+ * steps 4 and 3).
  *   h_poly      host uint32 [r][YY_SOBOL_POLY_WORDS]: per dimension the degree s of its
  *               primitive polynomial (0 = identity dimension), the inner coefficients a
  *               (a_1 most significant), then m_1..m_s.
@@ -207,7 +212,8 @@ YY_EXPORT yy_status yy_init_nodes_lds(yy_filter* f, int32_t kind, const double* 
  * (device uint32 [count][r], caller-owned).  Same generator as yy_init_nodes. */
 YY_EXPORT yy_status yy_sobol_bits(yy_filter* f, uint32_t* d_bits, int64_t first, int64_t count);
 
-/* Prediction (Section 4, eq. general_kernel; Section 7, Prediction Step):
+/* Prediction ("Solving Kolmogorov Equations via Low-Discrepancy Sampling and Kernel
+ * Approximation", eq. general_kernel; the prediction step of "Log-Domain Computation"):
  *   ell_pred(i) = log( sum_j c_j e^{L_j(i)} + c_{N+1} e^{ell(i)} ),
  *   L_j(i) = log sum_{s unmasked} K_{dt/s_j}(x_i, x_s) w_q e^{ell(s)},
  * K the first-order kernel of eq. kernel, w_q = prod_d 2 R_d / n, c the solution of the
@@ -221,7 +227,8 @@ YY_EXPORT yy_status yy_sobol_bits(yy_filter* f, uint32_t* d_bits, int64_t first,
  * many candidates are screened again with all coordinates. */
 YY_EXPORT yy_status yy_predict(yy_filter* f);
 
-/* Correction and estimate (Section 2.2 Online stage and step 4; Section 7):
+/* Correction and estimate ("Procedure for the Improved Yau-Yau Algorithm", online stage
+ * and step 4; "Log-Domain Computation"):
  *   ell'(i) = ell_pred(i) + h(x_i).dy - dt/2 |h(x_i)|^2,  Lambda = LSE ell',
  *   normalised weights, x_hat = sum w x, v_hat = sum w (x - x_hat)^2, ESS = 1/sum w^2,
  *   Z += Lambda, then the restart test.
@@ -235,8 +242,8 @@ YY_EXPORT yy_status yy_update(yy_filter* f, const double* d_dy);
 YY_EXPORT yy_status yy_estimate(yy_filter* f, double* h_mean, double* h_var, double* h_ess,
                       double* h_lognorm);
 
-/* Local resampling-restart (Section 5): re-centres the box at x_hat, keeps the reference
- * node set (translation), re-evaluates the drift at the new nodes and re-initialises the
+/* Local resampling-restart ("Local Resampling-Restart Mechanism"): re-centres the box at
+ * x_hat, keeps the reference node set (translation), re-evaluates the drift at the new nodes and re-initialises the
  * log-weights (cfg.restart_init).  mode: yy_restart_mode.  h_did_restart: NULL (stay
  * asynchronous) or a host int32 that receives 1 if a restart happened (synchronises). */
 YY_EXPORT yy_status yy_restart(yy_filter* f, int32_t mode, int32_t* h_did_restart);
@@ -351,7 +358,8 @@ YY_EXPORT yy_status yy_batch_graph_launch(yy_batch* bt);
  * each), the routing thresholds {3e-4, 1e-3, 3e-3, 1e-2, 3e-2, 1e-1, never} (filters whose
  * fraction exceeds it use the FP32 form, which is faster when most pairs are within reach
  * of the kernel, i.e. at low r) with bn = 256 and grid = 2 x SM count, then bn in
- * {256, 128} x grid in {1, 2, 4} x SM count with the best routing, and keeps the fastest.  If cache_path is not NULL the choice is recorded there keyed by
+ * {256, 128} x grid in {1, 2, 4} x SM count with the best routing, and keeps the fastest.
+ * If cache_path is not NULL the choice is recorded there keyed by
  * the batch's shape and reused instead of timing.  yy_batch_get_routing reports the
  * per-filter choice (0 = tensor-core screen, 1 = FP32 form; host int32 [B]). */
 YY_EXPORT yy_status yy_batch_set_schedule(yy_batch* bt, int32_t bn, int32_t grid);
@@ -409,7 +417,8 @@ YY_EXPORT yy_status yy_get_clamps(yy_filter* f, int64_t* h_clamps);
  * If every log-weight is -inf the output reads LSE = -inf with weight sum, ESS, mean and
  * variance 0 (the call is asynchronous, so this is reported in the output, not as a code).
  * Limits: 1 <= r <= YY_NOALLOC_MAX_DIM and n >= 1; anything else returns YY_ERR_ARG
- * before any launch.  YY_ERR_CUDA reports a failure of this call's own launches only.  Scratch lives in a fixed device array of about 2 MB inside the
+ * before any launch.  YY_ERR_CUDA reports a failure of this call's own launches only.
+ * Scratch lives in a fixed device array of about 2 MB inside the
  * library, held by every GPU that loads it until the process exits.  The first call on a
  * device looks up that array's device address; make it before any stream capture.  All
  * calls share the array: calls that overlap on the GPU race and must be serialised by
@@ -486,7 +495,8 @@ YY_EXPORT yy_status yy_set_shard(yy_filter* f, int32_t rank, int32_t count);
 /* First row of the handle's chunk and the chunk length n_pad / count (rows); host int64. */
 YY_EXPORT yy_status yy_shard_rows(const yy_filter* f, int64_t* h_row0, int64_t* h_chunk);
 
-/* Likelihood update of the shard's rows (Section 2.2, Online stage; Section 7).  Writes
+/* Likelihood update of the shard's rows ("Procedure for the Improved Yau-Yau Algorithm",
+ * online stage; "Log-Domain Computation").  Writes
  *   d_rows_out    device float [chunk] (double for FP64 precision): the chunk's log-weights
  *                 ell'_i - lam_g, normalised by the shard's own log-sum-exp lam_g (-inf for
  *                 padding rows)

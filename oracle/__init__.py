@@ -6,14 +6,17 @@ does.  The oracle shares no code with the CUDA path: it reads only the seeded in
 ``synth`` and follows the paper's definitions step by step in float64.
 
 Modules (each cites the passage it follows):
-    coeffs   multi-scale kernel coefficients, generalised Vandermonde system (Sec. 4.3.3)
+    coeffs   multi-scale kernel coefficients, generalised Vandermonde system
+             ("High-Order Kernel Construction")
     sobol    Sobol points (Gray code, Appendix A) and the affine scramble
     model    drift, divergence and sensor of the two workload models; complex-step
-             divergence (Section 6)
-    filter   one filter step: kernel prediction (Sec. 4, Sec. 7), Ito-corrected update
-             (Sec. 2.2), log-domain normalisation, estimate, ESS, restart (Sec. 5)
+             divergence ("Numerical Divergence Calculation")
+    filter   one filter step: kernel prediction ("Solving Kolmogorov Equations ...",
+             "Log-Domain Computation"), Ito-corrected update
+             ("Procedure for the Improved Yau-Yau Algorithm"), log-domain normalisation,
+             estimate, ESS, restart ("Local Resampling-Restart Mechanism")
     kalman   exact discrete Kalman filter for the Euler-discretised linear model
-    metrics  RMSE and ME (Section 9, "Error Metrics")
+    metrics  RMSE and ME ("Numerical Experiments", error metrics)
     mlp      FP64 reference of the restart-proposal MLP (forward, backward, Adam)
 
 Pins: every function is checked by ``tests/test_oracle_*.py`` against closed forms,

@@ -1,4 +1,4 @@
-"""Coefficients of the N-scale kernel (Section 4.3.3, eq. general_kernel).
+"""Coefficients of the N-scale kernel ("High-Order Kernel Construction", eq. general_kernel).
 
 Scales s_j = 2^(j-1), j = 1..N, and eliminated error orders mu_k = 3/2, 2, 5/2, ...
 (the example given after the expansion of L_{dt/s_j}).  The N+1 constraints are

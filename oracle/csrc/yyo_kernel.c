@@ -9,7 +9,7 @@
  *
  *     L_tau(i) = log( sum_{s unmasked} K_tau(x_i, x_s) * w_q * exp(ell_s) )
  *
- * with the first-order kernel of Theorem 4.1 (eq. kernel, Section 4.3.1),
+ * with the first-order kernel (eq. kernel, "First-Order Kernel Construction"),
  *
  *     log K_tau(x, y) = -(r/2) log(2 pi tau) - |x - y|^2 / (2 tau)
  *                       - (y - x) . f(x) - (tau/2) (2 div f(x) + |f(x)|^2),
@@ -22,7 +22,7 @@
  * eigenvalues); here a(x) is diagonal, passed as minv[i][d] = 1/a_d(x_i) (0 where
  * a_d(x_i) = 0) and hld[i] = 1/2 sum log a_d(x_i) over the positive a_d.  And w_q = prod_d (2 R_d) / n is the quadrature
  * volume per node that turns the integral into a sum over the nodes (the "Delta y"
- * factor of that Remark).  The sum is a log-sum-exp (Section 7, Prediction Step),
+ * factor of that Remark).  The sum is a log-sum-exp ("Log-Domain Computation", Prediction Step),
  * taken by the two-pass definition max + log sum exp(a - max).  Differences x - y are
  * formed directly; nothing is expanded into Gram products.
  */

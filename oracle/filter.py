@@ -1,22 +1,26 @@
 """One step of the improved Yau--Yau filter in float64, in the paper's order.
 
-Per step k (Section 2.2, "Procedure"; log-domain forms of Section 7):
+Per step k ("Procedure for the Improved Yau-Yau Algorithm"; log-domain forms of "Log-Domain
+Computation"):
   1. prediction  ell_pred(i) = log( sum_j c_j e^{L_j(i)} + c_{N+1} e^{ell(i)} ), the N-scale
-     kernel of eq. general_kernel applied to the weights (Sections 4.1-4.3), with
+     kernel of eq. general_kernel applied to the weights ("Solving Kolmogorov Equations
+     via Low-Discrepancy Sampling and Kernel Approximation"), with
      L_j(i) = LSE over unmasked sources of log K_{dt/s_j}(x_i, x_s) + log w_q + ell(s)
      (computed by the C core, see csrc/yyo_kernel.c); the identity term carries no
-     quadrature factor.  Targets on the Dirichlet boundary get -inf (Section 4.2, step 3).
+     quadrature factor.  Targets on the Dirichlet boundary get -inf ("Algorithm for Kolmogorov
+     Equation", step 3).
      Negative coefficients are handled by a signed log-sum-exp; a non-positive total
      gives -inf and is counted.
-  2. correction  ell'(i) = ell_pred(i) + h(x_i).dy_k - dt/2 |h(x_i)|^2 (Section 2.2
-     "Online stage", Section 7 "Observation Update").
-  3. normalisation  Lambda_k = LSE_i ell'(i), ell_hat = ell' - Lambda_k (Section 7
-     "Normalization"); running log-normaliser Z_k = Z_{k-1} + Lambda_k, Z_0 = 0 (the prior
+  2. correction  ell'(i) = ell_pred(i) + h(x_i).dy_k - dt/2 |h(x_i)|^2 (online stage of
+     "Procedure for the Improved Yau-Yau Algorithm"; observation update of "Log-Domain
+     Computation").
+  3. normalisation  Lambda_k = LSE_i ell'(i), ell_hat = ell' - Lambda_k (normalisation in
+     "Log-Domain Computation"); running log-normaliser Z_k = Z_{k-1} + Lambda_k, Z_0 = 0 (the prior
      weights are normalised at initialisation).
-  4. estimate  x_hat = sum w_hat x (Section 2.2, step 4); variance
-     v_hat = sum w_hat (x - x_hat)^2; ESS = 1 / sum w_hat^2.
-  5. restart  (Section 5): when ESS < rho n, or iota >= 2 and k mod iota == 0, the box is
-     re-centred at x_hat, the reference nodes are translated (the same u), and the
+  4. estimate  x_hat = sum w_hat x ("Procedure for the Improved Yau-Yau Algorithm", step 4);
+     variance v_hat = sum w_hat (x - x_hat)^2; ESS = 1 / sum w_hat^2.
+  5. restart  ("Local Resampling-Restart Mechanism"): when ESS < rho n, or iota >= 2 and
+     k mod iota == 0, the box is re-centred at x_hat, the reference nodes are translated (the same u), and the
      weights are re-initialised from N(c, diag(max(v_hat, v_min))), v_min = (R/4)^2,
      c the new centre, or uniformly.  Z is left unchanged by a restart.  With the learned
      rule (a library addition, see oracle/mlp.py) the centre is x_hat + delta and the
@@ -78,12 +82,14 @@ class Prepared:
 
 
 def log_wq(half: np.ndarray, n: int) -> float:
-    """Quadrature volume per node of the box with these half-widths (Sec. 4.1 Remark)."""
+    """Quadrature volume per node of the box with these half-widths ("Discrete Solution-Mapping
+    Operator Construction", remark)."""
     return float(np.sum(np.log(2.0 * half)) - np.log(n))
 
 
 def boundary_mask(u: np.ndarray, R: np.ndarray) -> np.ndarray:
-    """Nodes within omega = 1e-12 R of a face of [-R, R]^r (Section 4.2, step 3)."""
+    """Nodes within omega = 1e-12 R of a face of [-R, R]^r ("Algorithm for Kolmogorov
+    Equation", step 3)."""
     uu = np.abs(u.astype(np.float64))
     return np.any(uu >= R[None, :] - 1e-12 * R[None, :], axis=1)
 
@@ -109,7 +115,7 @@ def normalise(logw: np.ndarray) -> tuple[float, np.ndarray]:
 
 
 def prior_logw(p: Problem, x: np.ndarray) -> np.ndarray:
-    """log sigma_0(x_i) for x_0 ~ N(mu0, s0^2 I) (Section 4.2, step 4)."""
+    """log sigma_0(x_i) for x_0 ~ N(mu0, s0^2 I) ("Algorithm for Kolmogorov Equation", step 4)."""
     d = x - p.prior_mean
     return -0.5 * np.sum(d * d, axis=1) / p.prior_var - 0.5 * p.r * np.log(2 * np.pi * p.prior_var)
 

@@ -3,7 +3,7 @@
 Model (componentwise, unit noise): x_k = (1 + a dt) x_{k-1} + sqrt(dt) xi_k,
 dy_k = dt x_k + sqrt(dt) eta_k, x_0 ~ N(m0, P0).  The components are independent, so
 the filter is r scalar filters.  This is the discrete counterpart of the Kalman--Bucy
-filter the paper compares against in Section 9.3.
+filter the paper compares against in "Linear Filtering Benchmark".
 """
 from __future__ import annotations
 

@@ -1,4 +1,4 @@
-"""Error metrics of Section 9 ("Error Metrics"):
+"""Error metrics of "Numerical Experiments" (error metrics):
 RMSE = sqrt( sum_k |x_hat_k - x_k|^2 / (K r) ),  ME = (1/K) sum_k sqrt(|x_hat_k - x_k|^2 / r)."""
 from __future__ import annotations
 

@@ -1,5 +1,6 @@
 """FP64 reference of the restart-proposal network (a library addition; the paper's
-restart, Section 5, re-centres the box at the estimate with a fixed half-width).
+restart, "Local Resampling-Restart Mechanism", re-centres the box at the estimate with a fixed
+half-width).
 
 Network: features z = [x_hat - c; sqrt(v_hat); dy / sqrt(dt)] in R^{3r} (c the centre of the box the
 estimate was computed in, so the first block is how far the posterior moved inside it), normalised per

@@ -2,12 +2,13 @@
 
 cubic    : f(x) = cos(x) componentwise, div f = -sum_d sin(x_d), h(x) = x^3
 linear   : f(x) = a x,                  div f = a r,              h(x) = x
-paper_e1 : the large-scale scalability test of Section 9 ("Large-Scale Scalability Test"):
+paper_e1 : the large-scale scalability test of "Large-Scale Scalability Test":
            f(x) = sin(x) * (A x) + sin(2x) * (A1 x) elementwise, A and A1 upper bidiagonal
            with diagonal -0.5 / -0.3 and superdiagonal 0.1 / 0.3, h(x) = (x - 100)^3;
            div f = sum_d [cos(x_d) (A x)_d - 0.5 sin(x_d) + 2 cos(2 x_d) (A1 x)_d - 0.3 sin(2 x_d)]
 
-``complex_step_divergence`` is the complex-step formula of Section 6 (eq. boxed there):
+``complex_step_divergence`` is the complex-step formula of "Numerical Divergence Calculation"
+(the boxed formula there):
 div f(x) ~= sum_k Im f_k(x + i h e_k) / h, used to cross-check the closed forms.
 """
 from __future__ import annotations

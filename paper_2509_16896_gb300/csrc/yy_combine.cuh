@@ -1,5 +1,5 @@
 // Per-target combination of the N kernel terms with the identity term of eq.
-// general_kernel (Section 4.3.3), in log space, relative to c_ref:
+// general_kernel ("High-Order Kernel Construction"), in log space, relative to c_ref:
 //   ell_pred(i) - c_ref = log( sum_j c_j e^{L_j(i) - c_ref} + c_{N+1} e^{ell(i) - c_ref} ),
 //   L_j(i) - c_ref = (C_j - c_ref) - tau_j div f(x_i) - hld_i + m_j + log s_j,
 // where (m_j, s_j) is the online log-sum-exp state of the scaled kernel scores over the

@@ -1,5 +1,5 @@
-// Drift of the cubic sensor model (Section 9.1), f_d(x) = cos x_d, and sin x_d (for the
-// divergence), in float32 at x_d = c_d + u from per-dimension constants of the box:
+// Drift of the cubic sensor model ("Large-Scale Scalability Test"), f_d(x) = cos x_d, and
+// sin x_d (for the divergence), in float32 at x_d = c_d + u from per-dimension constants of the box:
 //     cos(c + u) = cos c cos u - sin c sin u,    sin(c + u) = sin c cos u + cos c sin u,
 // with cos c, sin c taken once per dimension in float64 and cos u, sin u from their Taylor
 // polynomials through u^8 and u^9 (Horner in u^2).  For |u| <= kPolyMaxU = 0.6 the

@@ -5,7 +5,7 @@
 //                    + LSE_s [ -|u_i - tau_j f_i - u_s|^2 / (2 tau_j) + ell_s ],
 //   C_j = -(r/2) log(2 pi tau_j) + log w_q,
 // which is log sum_s K_{tau_j}(x_i, x_s) w_q e^{ell_s} for the first-order kernel of
-// eq. kernel (Section 4.3.1) after completing the square:
+// eq. kernel ("First-Order Kernel Construction") after completing the square:
 //   -|x-y|^2/(2 tau) - (y-x).f(x) - tau(div f + |f|^2/2) = -|x - tau f(x) - y|^2/(2 tau) - tau div f.
 // Differences are formed first: with D = u_i - u_s, S1 = |D|^2 and S2 = D.f_i,
 //   |u_i - tau f_i - u_s|^2 = S1 - 2 tau S2 + tau^2 |f_i|^2,

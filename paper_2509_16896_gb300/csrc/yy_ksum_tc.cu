@@ -1,7 +1,8 @@
 // Prediction step on the 5th-generation tensor cores (sm_103a): Gram screening on tcgen05
 // (BF16 or e4m3 operands) + exact float32 evaluation of the surviving pairs.
 //
-// The kernel sum of the prediction (Section 4, eq. general_kernel; Section 7) is, per
+// The kernel sum of the prediction ("Solving Kolmogorov Equations via Low-Discrepancy Sampling
+// and Kernel Approximation", eq. general_kernel; "Log-Domain Computation") is, per
 // target i and scale j, a log-sum-exp over sources s of
 //     score_j(i, s) = -|u_i - tau_j f_i - u_s|^2 / (2 tau_j) + ell_s.
 // In high dimension almost every term is smaller than the largest one by hundreds of

@@ -1,6 +1,6 @@
 // Restart-proposal network: a 3-layer perceptron trained and run on the GPU with the
-// library's own kernels (a library addition; the paper's restart, Section 5, uses a fixed
-// box at the estimate).
+// library's own kernels (a library addition; the paper's restart, "Local Resampling-Restart
+// Mechanism", uses a fixed box at the estimate).
 //
 //   z = [x_hat; sqrt(v_hat); dy / sqrt(dt)] (3r), zn = clamp((z - mu) / s, -4, 4) (per-feature
 //   statistics of the training set)  ->  relu(W1 zn + b1) (H)  ->  relu(W2 . + b2) (H)

@@ -1,14 +1,17 @@
 // Per-node preparation: drift, divergence and norms at x = c + u, Dirichlet mask, bf16
 // copy of u, and the initial or restart log-weights.
 //
-//   f(x)      cubic: cos x (componentwise); linear: a x              (Section 9.1 / 9.3)
+//   f(x)      cubic: cos x (componentwise); linear: a x  ("Large-Scale Scalability Test",
+//             "Linear Filtering Benchmark");
 //             large-scale test: sin(x) (A x) + sin(2x) (A1 x), A and A1 upper bidiagonal
 //   div f(x)  cubic: -sum_d sin x_d;       linear: a r;
 //             large-scale test: sum_d cos(x_d)(A x)_d - 0.5 sin x_d + 2 cos(2 x_d)(A1 x)_d - 0.3 sin 2x_d
-//   mask      |u_d| >= R_d - 1e-12 R_d for some d (Section 4.2, step 3), tested in float64
-//   prior     log sigma_0(x) = -|x - mu0|^2 / (2 s0^2) + const (Section 4.2, step 4)
+//   mask      |u_d| >= R_d - 1e-12 R_d for some d, tested in float64 ("Algorithm for
+//             Kolmogorov Equation", step 3)
+//   prior     log sigma_0(x) = -|x - mu0|^2 / (2 s0^2) + const (same algorithm, step 4)
 //   restart   log N(x; x_hat, diag(max(v_hat, (R/4)^2))) + const, or uniform
-//             (Section 5; the density is this library's reading of "re-initialise")
+//             ("Local Resampling-Restart Mechanism"; the density is this library's reading
+//             of "re-initialise")
 // Constants that cancel in the normalisation that follows are dropped.
 //
 // One warp per node row; lane l holds float2 l + 32 q of the row for q = 0 .. r_pad / 64 - 1

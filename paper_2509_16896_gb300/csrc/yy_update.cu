@@ -1,5 +1,6 @@
-// Correction, normalisation, estimate and restart test (Section 2.2 "Online stage" and
-// step 4, Section 7 "Observation Update" and "Normalization", Section 5).
+// Correction, normalisation, estimate and restart test: the online stage and step 4 of
+// "Procedure for the Improved Yau-Yau Algorithm", the observation update and normalisation
+// of "Log-Domain Computation", and "Local Resampling-Restart Mechanism".
 //
 // The Ito-corrected log-likelihood h(x).dy - dt/2 |h(x)|^2 is split as
 //     lambda(c) + sum_d dh_d (g_d - dt/2 dh_d),   dh_d = h(c_d + u_d) - h(c_d),

@@ -9,7 +9,8 @@ This package holds no arithmetic of the filter itself.  It produces:
   Gray-code point construction and the scrambling are implemented separately by the
   oracle and by the CUDA path.
 * ``trajectory``    -- Euler--Maruyama simulation of the filtering problem
-  dX = f(X)dt + dV, dY = h(X)dt + dW (the problem statement of Section 2.1),
+  dX = f(X)dt + dV, dY = h(X)dt + dW (the problem statement of
+  "Continuous-Time Nonlinear Filtering Problem"),
   producing the true states and the observation increments dy_k.
 * ``configs``       -- the named workloads (sizes, step counts, seeds).
 

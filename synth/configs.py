@@ -51,7 +51,7 @@ WORKLOADS: dict[str, Workload] = {
                                 n_scales=2, seed=5, precision="bf16"),
 }
 
-# The paper's large-scale scalability test (Section 9, "Large-Scale Scalability Test"):
+# The paper's large-scale scalability test ("Large-Scale Scalability Test"):
 # drift sin(x) (A x) + sin(2x) (A1 x), sensor (x - 100)^3, x_0 ~ N(0, I), dt = 0.01, 1000
 # steps, Sobol nodes, R = 0.3, restart every second step, at the paper's pairs of dimension
 # and node count.  The paper gives no kernel order; two bandwidths are used, as for the

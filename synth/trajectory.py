@@ -1,9 +1,9 @@
 """Euler--Maruyama truth and observation increments for the filtering problem.
 
-The problem (Section 2.1, eq. NonlinearFilter) is dX = f(X)dt + dV, dY = h(X)dt + dW with
-unit-covariance Brownian motions.  The experiments discretise both SDEs with
-Euler--Maruyama at the filter step dt (Section 9.1, "Setup").  The observation of step k
-uses the state after the step:
+The problem ("Continuous-Time Nonlinear Filtering Problem", eq. NonlinearFilter) is
+dX = f(X)dt + dV, dY = h(X)dt + dW with unit-covariance Brownian motions.  The experiments
+discretise both SDEs with Euler--Maruyama at the filter step dt ("Large-Scale Scalability
+Test", setup).  The observation of step k uses the state after the step:
 
     x_k  = x_{k-1} + f(x_{k-1}) dt + sqrt(dt) xi_k,
     dy_k = h(x_k) dt + sqrt(dt) eta_k,            xi_k, eta_k ~ N(0, I).

@@ -80,7 +80,7 @@ def test_nodes_bit_exact(yy_lib, name):
 
 def test_unscrambled_corner_node_is_masked(yy_lib):
     """Unscrambled point 0 maps to R (2^-32 - 1), which rounds to -R in float32: on the
-    face, so it is masked as source and target (Section 4.2, step 3)."""
+    face, so it is masked as source and target ("Algorithm for Kolmogorov Equation", step 3)."""
     from oracle import filter as F
     flt, p, poly, scr = _make(CASES["ragged_f32"], scrambled=False)
     u, mask = flt.get_nodes()

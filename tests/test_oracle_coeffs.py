@@ -1,4 +1,5 @@
-"""Pins for the multi-scale kernel coefficients (Section 4.3.2-4.3.3)."""
+"""Pins for the multi-scale kernel coefficients ("Second-Order Kernel Construction" and
+"High-Order Kernel Construction")."""
 import math
 import os
 

@@ -103,7 +103,7 @@ def test_restart_rules():
     assert F.restart_due(p, 49.9, 1) and not F.restart_due(p, 50.0, 1)
     assert F.restart_due(p, 80.0, 4) and not F.restart_due(p, 80.0, 3)
     p1 = _problem(n=100, restart_interval=1, ess_frac=0.0)
-    assert not F.restart_due(p1, 1.0, 2)   # iota = 1: no restart (Section 5 remark)
+    assert not F.restart_due(p1, 1.0, 2)   # iota = 1: no restart (restart remark)
 
 
 def test_restart_translates_reference_nodes_and_uniform_init():

@@ -1,4 +1,5 @@
-"""Pins for the oracle's kernel sums (Sections 4.1-4.3, Section 7 prediction)."""
+"""Pins for the oracle's kernel sums ("Solving Kolmogorov Equations via Low-Discrepancy
+Sampling and Kernel Approximation", "Log-Domain Computation" prediction)."""
 import math
 
 import numpy as np
@@ -65,7 +66,8 @@ def test_linear_drift_gaussian_closed_form(r, n, R, dt, tol):
 
 
 def test_zero_drift_kernel_integrates_to_one():
-    """f = 0: sum_s K(x_i, x_s) w_q ~ int K dy = 1 (Theorem 4.1) away from the faces."""
+    """f = 0: sum_s K(x_i, x_s) w_q ~ int K dy = 1 (the first-order kernel theorem)
+    away from the faces."""
     p = _problem("linear", 1, 4096, 2.0, N=1, dt=0.01, a=0.0)
     u = _nodes(1, 4096, 2.0, seed=3)
     prep = F.prepare(p, u, np.zeros(1))
@@ -106,7 +108,8 @@ def test_masked_target_is_minus_inf_and_masked_source_excluded():
 
 
 def test_boundary_mask_rule():
-    """Nodes within omega = 1e-12 R of a face are on the boundary (Section 4.2, step 3)."""
+    """Nodes within omega = 1e-12 R of a face are on the boundary ("Algorithm for Kolmogorov
+    Equation", step 3)."""
     R = np.array([0.3, 0.3])
     u = np.array([[0.3, 0.0], [0.0, -0.3], [0.2999, 0.1], [np.float32(0.3) * (1 - 2 ** -23), 0.0]],
                  dtype=np.float32)
@@ -116,7 +119,8 @@ def test_boundary_mask_rule():
 
 @pytest.mark.parametrize("model", ["cubic", "linear", "paper_e1"])
 def test_divergence_closed_form_vs_complex_step(model):
-    """Section 6: sum_k Im f_k(x + i h e_k) / h, h = 1e-20, against the closed forms."""
+    """Complex-step divergence ("Numerical Divergence Calculation"): sum_k Im f_k(x + i h e_k) / h, h = 1e-20, against
+    the closed forms."""
     rng = np.random.default_rng(0)
     x = rng.normal(size=(20, 7))
     cs = mdl.complex_step_divergence(model, x, a=-0.5)
