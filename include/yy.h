@@ -436,6 +436,19 @@ YY_EXPORT yy_status yy_weighted_moments_static(const float* d_u, int64_t n, int3
  * the GPU, and lets a test make a wait expire. */
 YY_EXPORT yy_status yy_set_wait_limit(yy_filter* f, double seconds);
 
+/* Whether the tensor-core prediction (YY_PREC_BF16) may run on pairs of CTAs (on = 1) or
+ * on single CTAs (on = 0, the default).  A pair is a 2-CTA cluster on two SMs: each CTA
+ * holds 128 target rows and stages half of every 256-wide source tile, and one
+ * tcgen05.mma.cta_group::2 per K step computes both CTAs' Gram blocks, so each source tile
+ * is fetched into shared memory once per 256 targets instead of once per 128 (a library
+ * design, not in the paper).  Pairs are used when allowed and when the device can place
+ * the clusters; both forms take the same screening decisions and give the same predicted
+ * weights up to float32 rounding.  h_pairs (host int32, may be NULL) receives the number
+ * of CTA pairs (clusters) of the handle's current schedule, 0 when it uses single CTAs.
+ * Rebuilds the work list (synchronous) if nodes exist; call it outside stream capture.
+ * YY_ERR_ARG for on not in {0, 1}. */
+YY_EXPORT yy_status yy_set_cta_pair(yy_filter* f, int32_t on, int32_t* h_pairs);
+
 /* The materialised schedule of the prediction (the paper's offline operator and online
  * matrix-vector product, Sections "Algorithm for Kolmogorov Equation" and "CPU/GPU
  * Parallel Acceleration", in its log-domain form, Section "Log-Domain Computation"):

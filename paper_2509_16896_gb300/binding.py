@@ -46,7 +46,7 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train",
            "yy_mlp_set_input_norm", "yy_get_screen", "yy_batch_set_routing",
            "yy_set_wait_limit", "yy_set_shard", "yy_shard_rows", "yy_update_shard", "yy_merge_shards",
-           "yy_merge_records_host", "yy_init_nodes_lds", "yy_tune_materialise")
+           "yy_merge_records_host", "yy_init_nodes_lds", "yy_tune_materialise", "yy_set_cta_pair")
 
 
 class YYError(RuntimeError):
@@ -118,6 +118,7 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_merge_records_host": (I32, [P, I32, I32, P]),
         "yy_init_nodes_lds": (I32, [P, I32, P, P]),
         "yy_tune_materialise": (I32, [P, I32, I32, P, P]),
+        "yy_set_cta_pair": (I32, [P, I32, P]),
         "yy_get_box": (I32, [P, P, P]),
         "yy_set_restart_mlp": (I32, [P, P]),
         "yy_mlp_param_count": (I64, [I32, I32]),
@@ -339,6 +340,13 @@ class Filter:
 
     def set_wait_limit(self, seconds: float) -> None:
         _check("yy_set_wait_limit", self.lib.yy_set_wait_limit(self.h, float(seconds)))
+
+    def set_cta_pair(self, on: bool) -> int:
+        """Allow (True) or forbid the tensor-core prediction on 2-CTA clusters; returns
+        the number of CTA pairs of the current schedule (0: single CTAs)."""
+        pairs = ctypes.c_int32(0)
+        _check("yy_set_cta_pair", self.lib.yy_set_cta_pair(self.h, 1 if on else 0, ctypes.byref(pairs)))
+        return pairs.value
 
     # ---- one filter across devices (target rows split) ------------------------------
     def set_shard(self, rank: int, count: int) -> None:

@@ -24,22 +24,32 @@ constexpr unsigned long long kDefaultWaitNs = 4000000000ull;   // 4 s
 // holding row 128 a on (L_a = nst - a / 2 tiles of 256), split into tc_sym_splits(L_a)
 // ranges; items are assigned longest first to the least loaded CTA.  Otherwise every
 // target tile is split into S ranges (S minimising the makespan) dealt round-robin.
+// CTA pairs (when allowed, the handle's first row starts a 256-row super-tile -- always:
+// shard chunks are whole super-tiles -- and the device can place 2-CTA clusters): the same
+// construction over super-tiles p (target tiles 2p and 2p + 1, both with L = nst - p), one
+// work list per cluster.  A last tile of odd index gets its pair partner from the padding
+// rows (n_pad is a multiple of 256), which the kernel treats as out of range.
 // Copied into the workspace; synchronous (set-up only).
 yy_status build_tc_schedule(yy_filter* f) {
     int dev = 0, sms = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // the handle's target tiles (all of them, or its shard's chunk)
-    const long long t_lo = f->row0 / 128, t_hi = (f->row1 + 127) / 128;
+    long long t_lo = f->row0 / 128, t_hi = (f->row1 + 127) / 128;
+    const int max_cl = f->pair_ok ? tc_pair_max_clusters() : 0;
+    const bool pair = max_cl > 0 && t_lo % 2 == 0 && (t_hi + 1) / 2 * 256 <= f->n_pad;
+    const int span = pair ? 2 : 1;   // target tiles per item
+    const int units = pair ? std::min(max_cl, sms / 2) : std::min(sms, kMaxTcGrid);
+    if (pair) { t_lo /= 2; t_hi = (t_hi + 1) / 2; }   // super-tiles
     const long long tiles = t_hi - t_lo;
     const int nst = (int)(f->n_pad / 256);
-    const int grid = (int)std::min<long long>(std::min(sms, kMaxTcGrid), tiles * 8);
+    const int grid = (int)std::min<long long>(units, tiles * 8);
     std::vector<std::vector<int4>> per(grid);
     int S = 1;
     if (f->kf.tc_sym) {
         struct It { double cost; int t, q, S; };
         std::vector<It> all;
         for (long long t = t_lo; t < t_hi; ++t) {
-            const int L = nst - (int)(t / 2);
+            const int L = nst - (int)(span == 2 ? t : t / 2);
             const int St = tc_sym_splits(L);
             for (int q = 0; q < St; ++q)
                 all.push_back({(double)((L * (q + 1)) / St - (L * q) / St) + 1.0, (int)t, q, St});
@@ -72,8 +82,9 @@ yy_status build_tc_schedule(yy_filter* f) {
                             f->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(f->stream);
     if (e != cudaSuccess) return YY_ERR_CUDA;
-    f->bf.tc_grid = grid;
+    f->bf.tc_grid = pair ? 2 * grid : grid;   // CTAs
     f->bf.tc_splits = S;
+    f->bf.tc_pair = pair ? 1 : 0;
     return YY_OK;
 }
 
@@ -434,6 +445,7 @@ yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t bytes, void*
     f->ws_bytes = bytes;
     f->fp64 = (cfg->precision == YY_PREC_FP64);
     f->wait_ns = kDefaultWaitNs;
+    f->pair_ok = false;
     f->kf.wait_ns = f->kd.wait_ns = kDefaultWaitNs;
     f->row0 = 0;
     f->row1 = cfg->n;
@@ -798,6 +810,18 @@ yy_status yy_set_wait_limit(yy_filter* f, double seconds) {
     f->wait_ns = ns;
     f->kf.wait_ns = ns;
     f->kd.wait_ns = ns;
+    return YY_OK;
+}
+
+yy_status yy_set_cta_pair(yy_filter* f, int32_t on, int32_t* h_pairs) {
+    if (!f || (on != 0 && on != 1)) return YY_ERR_ARG;
+    f->pair_ok = (on == 1);
+    if (f->cfg.precision == YY_PREC_BF16 && f->nodes_ready) {
+        const yy_status st = build_tc_schedule(f);
+        if (st != YY_OK) return st;
+    }
+    if (h_pairs)
+        *h_pairs = (f->cfg.precision == YY_PREC_BF16 && f->nodes_ready && f->bf.tc_pair) ? f->bf.tc_grid / 2 : 0;
     return YY_OK;
 }
 

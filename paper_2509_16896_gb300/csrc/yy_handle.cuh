@@ -31,6 +31,7 @@ struct yy_filter {
     bool shard_updated;           // yy_update_shard ran; yy_merge_shards completes the step
     int node_kind;                // yy_nodes of the last node generation
     bool use_op;                  // the prediction applies the materialised operator
+    bool pair_ok;                 // the tensor-core prediction may run on CTA pairs (yy_set_cta_pair)
 };
 
 namespace yy {

@@ -144,6 +144,7 @@ struct Bufs {
     int* tc_cta_start;    // [tc_grid + 1]
     int tc_grid;          // persistent CTAs of the single-filter prediction
     int tc_splits;        // source splits per target tile
+    int tc_pair;          // 1: the work list is per 2-CTA cluster (items are pairs of target tiles)
 };
 
 // Device-side descriptor of one trajectory of a batch (kernels index it by blockIdx.y).
@@ -190,6 +191,7 @@ cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStr
 size_t tc_scratch_bytes(long long n_pad);
 cudaError_t prepare_ksum_tc();
 int tc_choose_splits(long long tiles, int nst, int grid);
+int tc_pair_max_clusters();
 int tc_max_split();
 
 template <typename T>

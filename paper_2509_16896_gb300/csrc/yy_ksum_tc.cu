@@ -75,26 +75,35 @@ constexpr int kEscThresh = 8;    // candidates of one warp in one tile above whi
 constexpr int kExactBudget = 64; // exact pairs one warp evaluates per item in the first pass
 
 // Shape-dependent constants.  BN = 256: 4 stages, 512 TMEM columns, one CTA per SM.
-// BN = 128: 3 stages (96 KB), 256 TMEM columns, so two CTAs fit on one SM.
-template <int BN>
+// BN = 128: 3 stages (96 KB), 256 TMEM columns, so two CTAs fit on one SM.  PAIR (BN = 256
+// only): the two CTAs of a cluster share each source tile, each staging half of it (128
+// rows) next to its own 128 target rows, so a stage is 32 KB and the same shared memory
+// holds 6 of them; the expected bytes of a stage on the even CTA's barrier cover both.
+template <int BN, bool PAIR = false>
 struct Cfg {
-    static constexpr int STAGES = (BN == 256) ? 4 : 3;
-    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGES = PAIR ? 6 : ((BN == 256) ? 4 : 3);
+    static constexpr int B_BYTES = (PAIR ? BN / 2 : BN) * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr uint32_t TX_BYTES = (PAIR ? 2u : 1u) * (uint32_t)STAGE_BYTES;
+    static constexpr int MMA_M = PAIR ? 2 * BM : BM;
+    // buffers of the per-tile source values (q, column bounds, chunk maxima): a ring of its
+    // own, so that a tile's values are staged well before its accumulator is ready
+    static constexpr int QB = (BN == 256) ? 4 : 2;
     static constexpr uint32_t TMEM_COLS = 2 * BN;   // two accumulators of BN fp32 columns
     static constexpr int HALF = BN / 2;   // columns of one epilogue warp
     // ring | row- and column-direction q values per accumulator | candidate masks per
     // epilogue warp | marking bitmaps | row states exchanged between the two warps of a lane
     // quarter | barriers
-    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 4 * BN * 4 + 2 * 16 * 4 + 2 * EPI_WARPS * HALF * 4 +
-                                      EPI_WARPS * 2 * kEscWords * 4 + 128 * kMaxScales * 2 * 4 + 2 * (BN / 32) * 4 + 256;
+    static constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 2 * QB * BN * 4 + QB * 16 * 4 +
+                                      2 * EPI_WARPS * HALF * 4 + EPI_WARPS * 2 * kEscWords * 4 +
+                                      128 * kMaxScales * 2 * 4 + QB * (BN / 32) * 4 + 384;
     // kind::f16 instruction descriptor: D fp32 (bits 4-5 = 1), A bf16 (bits 7-9 = 1),
     // B bf16 (bits 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                                      ((uint32_t)(BM >> 4) << 24);
+                                      ((uint32_t)(MMA_M >> 4) << 24);
     // kind::f8f6f4 instruction descriptor: D fp32 (bits 4-5 = 1), A and B e4m3 (bits 7-9 and
     // 10-12 = 0), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-    static constexpr uint32_t IDESC8 = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    static constexpr uint32_t IDESC8 = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(MMA_M >> 4) << 24);
 };
 
 }  // namespace tc
@@ -104,12 +113,19 @@ namespace {
 using namespace ptx;
 
 // Bounded wait: false when the limit expired (status recorded) or another role aborted.
+// CL: acquire at cluster scope (waits after which the other CTA of a pair's shared memory
+// is read).
+template <bool CL = false>
+__device__ __forceinline__ bool try_wait_sc(uint64_t* bar, uint32_t parity) {
+    return CL ? mbar_try_wait_cluster(bar, parity) : mbar_try_wait(bar, parity);
+}
+template <bool CL = false>
 __device__ __forceinline__ bool wait_bounded(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
                                              unsigned int* status, unsigned long long limit_ns) {
-    if (mbar_try_wait(bar, parity)) return true;
+    if (try_wait_sc<CL>(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (try_wait_sc<CL>(bar, parity)) return true;
         if (*abort_flag) return false;
         if (globaltimer() - t0 > limit_ns) {
             *abort_flag = 1;
@@ -507,14 +523,29 @@ __device__ __forceinline__ float* part_slot(const Bufs<float>& b, long long i, i
 // for pass 2 instead of evaluating them; after pass 1 of the item the three roles meet at
 // an mbarrier, and pass 2 recomputes the marked tiles over all coordinates and screens them
 // again (only the marking warps use the result).  With nk1 = nk there is one pass.
-template <int N, int BN>
+//
+// PAIR: the grid is made of 2-CTA clusters (one CTA per SM) and work item p of a cluster
+// is the pair of target tiles 2p (even CTA) and 2p + 1 (odd CTA), which have the same
+// source range.  Each CTA stages its own 128 target rows and half of each source tile;
+// the even CTA's MMA thread issues tcgen05.mma.cta_group::2 (M = 256) once both halves
+// have landed on its barrier, and its commits arrive on the barriers of both CTAs.  The
+// even CTA's MMA waits until the epilogues of both CTAs have released an accumulator
+// (the odd CTA's arrive remotely).  Tiles to be screened again are the union of both
+// CTAs' marks.  Everything else -- screening, exact evaluation, row states -- is per CTA
+// and identical to the single-CTA kernel.
+template <int N, int BN, bool PAIR>
 // One CTA per SM; with 10 warps two of the four SM sub-partitions hold three warps each, so
 // the register budget is 168 per thread.
 __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     k_ksum_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ Consts<float> k0, const __grid_constant__ Bufs<float> b0, TcWork w) {
     using namespace tc;
-    using C = Cfg<BN>;
+    using C = Cfg<BN, PAIR>;
+    static_assert(!PAIR || BN == 256, "CTA pairs share 256-wide source tiles");
+    // the waits after which a CTA reads the other CTA's marks acquire at cluster scope; the
+    // pipeline waits (ring, accumulators, q buffers) order only asynchronous copies and
+    // tensor-core work and stay at CTA scope
+    constexpr bool CL = PAIR;
     constexpr int STAGES = C::STAGES;
     constexpr int STAGE_BYTES = C::STAGE_BYTES;
     extern __shared__ uint8_t smem_raw[];
@@ -522,11 +553,12 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     constexpr int HALF = C::HALF;
     // q_s of the tile's sources and, for symmetric blocks, the column-direction values,
     // staged by the producer per accumulator: [2][BN] each
-    float* qbuf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);
-    float* qtbuf = qbuf + 2 * BN;
-    float* qinfo = qtbuf + 2 * BN;                                       // [2][16]: the tile's chunk maxima
-    float* qmbuf = qinfo + 2 * 16;                                       // [2][BN / 32]: smallest q_s per 32
-    uint32_t* cms = reinterpret_cast<uint32_t*>(qmbuf + 2 * (BN / 32));  // [EPI_WARPS][HALF / 32][32]
+    constexpr int QB = C::QB;
+    float* qbuf = reinterpret_cast<float*>(smem + STAGES * STAGE_BYTES);   // [QB][BN]
+    float* qtbuf = qbuf + QB * BN;                                         // [QB][BN]
+    float* qinfo = qtbuf + QB * BN;                                        // [QB][16]: the tile's chunk maxima
+    float* qmbuf = qinfo + QB * 16;                                        // [QB][BN / 32]: smallest q_s per 32
+    uint32_t* cms = reinterpret_cast<uint32_t*>(qmbuf + QB * (BN / 32));   // [EPI_WARPS][HALF / 32][32]
     uint32_t* tcms = cms + EPI_WARPS * HALF;                             // [EPI_WARPS][HALF / 32][32]
     uint32_t* escm = tcms + EPI_WARPS * HALF;                            // [EPI_WARPS][2][kEscWords]
     float* xch = reinterpret_cast<float*>(escm + EPI_WARPS * 2 * kEscWords);   // [128 rows][kMaxScales][2]
@@ -539,14 +571,20 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     uint64_t* escb = drain + 1;
     uint64_t* xfull = escb + 1;    // [4]: the second warp of lane quarter q stored its row states
     uint64_t* xfree = xfull + 4;   // [4]: the first warp of lane quarter q has read them
-    uint64_t* qfull = xfree + 4;   // [2]: the q values of the tile in accumulator a landed
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(qfull + 2);
+    uint64_t* qfull = xfree + 4;   // [QB]: the source values of a tile landed in q buffer b
+    uint64_t* qempty = qfull + QB; // [QB]: the epilogue is done with q buffer b
+    // [2] (pairs, even CTA): accumulator a released by the epilogues of both CTAs; the MMA
+    // waits on it (single CTAs: on tempty)
+    uint64_t* tpair = qempty + QB;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tpair + 2);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const bool batched = (w.tr != nullptr);
-    const int it_begin = w.cta_start[blockIdx.x];
-    const int it_end = w.cta_start[blockIdx.x + 1];
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;   // 0: even CTA (issues the MMAs)
+    const int unit = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;   // work list index
+    const int it_begin = w.cta_start[unit];
+    const int it_end = w.cta_start[unit + 1];
     // status word for timeouts: the first filter of this CTA (none if the CTA has no work)
     unsigned int* status = (it_end <= it_begin) ? nullptr
                            : batched ? &w.tr[w.items[it_begin].x].b.stats->status : &b0.stats->status;
@@ -554,22 +592,37 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     DevStats* const ctr = batched ? w.tr[0].b.stats : b0.stats;   // launch-wide counter
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-        for (int a = 0; a < 2; ++a) { mbar_init(&tfull[a], 1); mbar_init(&tempty[a], EPI_WARPS); }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&tfull[a], 1);
+            mbar_init(&tempty[a], EPI_WARPS);
+            mbar_init(&tpair[a], 2 * EPI_WARPS);   // both CTAs' epilogue warps
+        }
         mbar_init(drain, 1);
-        mbar_init(escb, EPI_WARPS);
+        mbar_init(escb, PAIR ? 2 * EPI_WARPS : EPI_WARPS);   // a pair's marks are read by both
         for (int a = 0; a < 4; ++a) { mbar_init(&xfull[a], 1); mbar_init(&xfree[a], 1); }
-        for (int a = 0; a < 2; ++a) mbar_init(&qfull[a], 1);
+        for (int a = 0; a < QB; ++a) { mbar_init(&qfull[a], 1); mbar_init(&qempty[a], EPI_WARPS); }
         *abort_flag = 0;
         mbar_fence_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, C::TMEM_COLS);
-        tmem_relinquish();
+        if (PAIR) {   // one warp of each CTA; both receive the same column
+            tmem_alloc_pair(tmem_slot, C::TMEM_COLS);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(tmem_slot, C::TMEM_COLS);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if (PAIR) cluster_sync();   // both CTAs' barriers initialised before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // the other CTA's copies of the barriers and marks a pair uses (shared::cluster)
+    const uint32_t full_lead = PAIR ? mapa_shared(full, 0) : 0u;      // the even CTA's ring barriers
+    const uint32_t tpair_lead = PAIR ? mapa_shared(tpair, 0) : 0u;
+    const uint32_t escb_peer = PAIR ? mapa_shared(escb, rank ^ 1u) : 0u;
+    const uint32_t escm_peer = PAIR ? mapa_shared(escm, rank ^ 1u) : 0u;
 
     // per-item view: descriptors, maps, first target row, source tile range, split, chunks
     // of all coordinates (nk) and of the first pass (nk1; nk when the range does not fit
@@ -584,7 +637,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             kp = &w.tr[it.x].k; bp = &w.tr[it.x].b;
             ma = &w.maps[2 * it.x]; mb = &w.maps[2 * it.x + 1];
         }
-        i0 = (long long)it.y * BM;
+        i0 = PAIR ? (long long)it.y * (2 * BM) + (long long)rank * BM : (long long)it.y * BM;
         split = it.z;
         nsplit = it.w;
         // symmetric screen: only source tiles from the one holding the tile's first row on
@@ -600,10 +653,17 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     auto esc_bit = [&](int e, uint32_t par, int j) -> bool {
         return (escm[(e * 2 + par) * kEscWords + (j >> 5)] >> (j & 31)) & 1u;
     };
+    // a pair screens again the union of both CTAs' marks
     auto esc_any = [&](uint32_t par, int j) -> bool {
         bool m = false;
 #pragma unroll
         for (int e = 0; e < EPI_WARPS; ++e) m |= esc_bit(e, par, j);
+        if (PAIR && !m) {
+#pragma unroll
+            for (int e = 0; e < EPI_WARPS; ++e)
+                m |= (ld_shared_cluster_u32(escm_peer + (uint32_t)(((e * 2 + (int)par) * kEscWords + (j >> 5)) * 4)) >>
+                      (j & 31)) & 1u;
+        }
         return m;
     };
 
@@ -612,40 +672,51 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             // ---- TMA producer -------------------------------------------------------
             int last_phase[STAGES];
             for (int s = 0; s < STAGES; ++s) last_phase[s] = -1;
-            int last_qphase[2] = {-1, -1};
+            int last_qphase[QB];
+            for (int a = 0; a < QB; ++a) last_qphase[a] = -1;
             uint32_t it = 0, npre = 0, tp = 0;
             bool ok = true;
-            // one tile: its coordinate chunks into the ring (gated by the ring's slots only,
-            // so they stream in while the epilogue still holds the accumulator), then its q
-            // values into the accumulator's buffer once the epilogue has released it
+            // one tile: its source values into the next q buffer (free once the epilogue is
+            // done with the tile QB back, so they are staged well ahead), then its
+            // coordinate chunks into the ring (gated by the ring's slots only, so they
+            // stream in while the epilogue still holds the accumulator)
             auto load_tile = [&](const Consts<float>* kp, const Bufs<float>* bp, const CUtensorMap* ma,
                                  const CUtensorMap* mb, long long i0, int t, int nkb, bool prefix) -> bool {
-                const int acc = (int)(tp & 1u);
-                const uint32_t aph = (tp >> 1) & 1u;
+                const int qs = (int)(tp % QB);
+                const uint32_t qph = (tp / QB) & 1u;
                 ++tp;
+                if (!wait_bounded(&qempty[qs], qph ^ 1u, abort_flag, status, w.wait_ns)) return false;
+                const uint32_t qb = (uint32_t)(BN * sizeof(float));
+                const uint32_t ib = (uint32_t)((BN / 128) * 8 * sizeof(float));
+                const uint32_t qmb = (uint32_t)((BN / 32) * sizeof(float));
+                mbar_arrive_expect_tx(&qfull[qs], (kp->tc_sym ? 2 * qb : qb) + ib + qmb);
+                bulk_load(qbuf + qs * BN, (prefix ? bp->tc_q1 : bp->tc_q) + (size_t)t * BN, qb, &qfull[qs]);
+                bulk_load(qinfo + qs * 16, bp->tc_cinfo + (size_t)t * (BN / 128) * 8, ib, &qfull[qs]);
+                bulk_load(qmbuf + qs * (BN / 32), (prefix ? bp->tc_qmin1 : bp->tc_qmin) + (size_t)t * (BN / 32), qmb,
+                          &qfull[qs]);
+                if (kp->tc_sym)
+                    bulk_load(qtbuf + qs * BN, (prefix ? bp->tc_qt1 : bp->tc_qt) + (size_t)t * BN, qb, &qfull[qs]);
+                last_qphase[qs] = (int)qph;
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
                     const int s = (int)(it % STAGES);
                     const uint32_t ph = (it / STAGES) & 1u;
                     if (!wait_bounded(&empty[s], ph ^ 1u, abort_flag, status, w.wait_ns)) return false;
-                    mbar_arrive_expect_tx(&full[s], STAGE_BYTES);
                     uint8_t* dA = smem + s * STAGE_BYTES;
                     const int x = kb * (kp->tc_fp8 ? 128 : BK);   // 128 bytes of coordinates per stage
-                    tma_load_2d(ma, &full[s], dA, x, (int)i0);
-                    tma_load_2d(mb, &full[s], dA + A_BYTES, x, t * BN);
+                    if (PAIR) {
+                        // this CTA's 128 target rows and source rows t BN + 128 rank .. +127
+                        // (the 128-row map serves both), counted on the even CTA's barrier
+                        if (rank == 0) mbar_arrive_expect_tx(&full[s], C::TX_BYTES);
+                        const uint32_t fb = full_lead + (uint32_t)(s * 8);
+                        tma_load_2d_pair(ma, fb, dA, x, (int)i0);
+                        tma_load_2d_pair(ma, fb, dA + A_BYTES, x, t * BN + (int)rank * BM);
+                    } else {
+                        mbar_arrive_expect_tx(&full[s], C::TX_BYTES);
+                        tma_load_2d(ma, &full[s], dA, x, (int)i0);
+                        tma_load_2d(mb, &full[s], dA + A_BYTES, x, t * BN);
+                    }
                     last_phase[s] = (int)ph;
                 }
-                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status, w.wait_ns)) return false;
-                const uint32_t qb = (uint32_t)(BN * sizeof(float));
-                const uint32_t ib = (uint32_t)((BN / 128) * 8 * sizeof(float));
-                const uint32_t qmb = (uint32_t)((BN / 32) * sizeof(float));
-                mbar_arrive_expect_tx(&qfull[acc], (kp->tc_sym ? 2 * qb : qb) + ib + qmb);
-                bulk_load(qbuf + acc * BN, (prefix ? bp->tc_q1 : bp->tc_q) + (size_t)t * BN, qb, &qfull[acc]);
-                bulk_load(qinfo + acc * 16, bp->tc_cinfo + (size_t)t * (BN / 128) * 8, ib, &qfull[acc]);
-                bulk_load(qmbuf + acc * (BN / 32), (prefix ? bp->tc_qmin1 : bp->tc_qmin) + (size_t)t * (BN / 32), qmb,
-                          &qfull[acc]);
-                if (kp->tc_sym)
-                    bulk_load(qtbuf + acc * BN, (prefix ? bp->tc_qt1 : bp->tc_qt) + (size_t)t * BN, qb, &qfull[acc]);
-                last_qphase[acc] = (int)aph;
                 return true;
             };
             for (int idx = it_begin; idx < it_end && ok; ++idx) {
@@ -657,27 +728,42 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 for (int t = t0; t < t1 && ok; ++t) ok = load_tile(kp, bp, ma, mb, i0, t, nk1, pre);
                 if (ok && pre) {
                     const uint32_t par = npre++ & 1u;
-                    if (!wait_bounded(escb, par, abort_flag, status, w.wait_ns)) { ok = false; break; }
+                    if (!wait_bounded<CL>(escb, par, abort_flag, status, w.wait_ns)) { ok = false; break; }
                     for (int t = t0; t < t1 && ok; ++t)
                         if (esc_any(par, t - t0)) ok = load_tile(kp, bp, ma, mb, i0, t, nk, false);
                 }
             }
             if (!ok) {   // let our own copies land before shared memory is released
-                for (int s = 0; s < STAGES; ++s)
-                    if (last_phase[s] >= 0) wait_drain(&full[s], (uint32_t)last_phase[s]);
-                for (int a = 0; a < 2; ++a)
+                if (!PAIR) {
+                    for (int s = 0; s < STAGES; ++s)
+                        if (last_phase[s] >= 0) wait_drain(&full[s], (uint32_t)last_phase[s]);
+                } else {
+                    // a pair's ring barriers count both CTAs' copies (the odd CTA's cannot be
+                    // waited on at all, and the even CTA's barrier may wait for the odd CTA's
+                    // half that never comes): give this CTA's own copies time to land (a
+                    // copy takes microseconds); both CTAs then leave together
+                    const unsigned long long tq = globaltimer();
+                    while (globaltimer() - tq < 1000000ull) {}
+                }
+                for (int a = 0; a < QB; ++a)
                     if (last_qphase[a] >= 0) wait_drain(&qfull[a], (uint32_t)last_qphase[a]);
             }
         }
     } else if (warp == 1) {
-        if (lane == 0 && status) {
-            // ---- MMA issuer -----------------------------------------------------------
+        if (lane == 0 && status && rank == 0) {
+            // ---- MMA issuer (the even CTA of a pair issues for both) -------------------
             uint32_t it = 0, tcount = 0, npre = 0;
             bool ok = true;
+            // the ring slot / accumulator is free again in every CTA that staged into it
+            auto commit_all = [&](uint64_t* bar) {
+                if (PAIR) mma_commit_pair_mc(bar, (uint16_t)3);
+                else mma_commit(bar);
+            };
             auto mma_tile = [&](int nkb, bool fp8) -> bool {
                 const int acc = (int)(tcount & 1u);
                 const uint32_t aph = (tcount >> 1) & 1u;
-                if (!wait_bounded(&tempty[acc], aph ^ 1u, abort_flag, status, w.wait_ns)) return false;
+                uint64_t* rel = PAIR ? &tpair[acc] : &tempty[acc];
+                if (!wait_bounded(rel, aph ^ 1u, abort_flag, status, w.wait_ns)) return false;
                 tc_fence_after();
                 const uint32_t d_tmem = tmem + (uint32_t)(acc * BN);
                 for (int kb = 0; kb < nkb; ++kb, ++it) {
@@ -690,18 +776,28 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     // four instructions per stage either way: K = 16 bf16 or 32 e4m3, 32 bytes
                     if (fp8) {
 #pragma unroll
-                        for (int kk = 0; kk < BK / UK; ++kk)
-                            mma_f8(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0a + kk * 32), C::IDESC8,
-                                   (kb | kk) != 0 ? 1u : 0u);
+                        for (int kk = 0; kk < BK / UK; ++kk) {
+                            if (PAIR)
+                                mma_f8_pair(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0a + kk * 32), C::IDESC8,
+                                            (kb | kk) != 0 ? 1u : 0u);
+                            else
+                                mma_f8(d_tmem, sw128_desc(a0 + kk * 32), sw128_desc(b0a + kk * 32), C::IDESC8,
+                                       (kb | kk) != 0 ? 1u : 0u);
+                        }
                     } else {
 #pragma unroll
-                        for (int kk = 0; kk < BK / UK; ++kk)
-                            mma_bf16(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0a + kk * UK * 2), C::IDESC,
-                                     (kb | kk) != 0 ? 1u : 0u);
+                        for (int kk = 0; kk < BK / UK; ++kk) {
+                            if (PAIR)
+                                mma_bf16_pair(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0a + kk * UK * 2),
+                                              C::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                            else
+                                mma_bf16(d_tmem, sw128_desc(a0 + kk * UK * 2), sw128_desc(b0a + kk * UK * 2),
+                                         C::IDESC, (kb | kk) != 0 ? 1u : 0u);
+                        }
                     }
-                    mma_commit(&empty[s]);
+                    commit_all(&empty[s]);
                 }
-                mma_commit(&tfull[acc]);
+                commit_all(&tfull[acc]);
                 ++tcount;
                 return true;
             };
@@ -714,17 +810,19 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 unsigned long long nesc = 0;
                 if (ok && nk1 < nk) {
                     const uint32_t par = npre++ & 1u;
-                    if (!wait_bounded(escb, par, abort_flag, status, w.wait_ns)) { ok = false; break; }
+                    if (!wait_bounded<CL>(escb, par, abort_flag, status, w.wait_ns)) { ok = false; break; }
                     for (int t = t0; t < t1 && ok; ++t)
                         if (esc_any(par, t - t0)) { ok = mma_tile(nk, kp->tc_fp8 != 0); ++nesc; }
                 }
-                if (ok) {
-                    atomicAdd(&bp->stats->tc_blk, (unsigned long long)(t1 - t0));
-                    if (nesc) atomicAdd(&bp->stats->tc_esc, nesc);
+                if (ok) {   // counted in blocks of 128 targets x BN sources (a pair MMA is two)
+                    const unsigned long long per = PAIR ? 2ull : 1ull;
+                    atomicAdd(&bp->stats->tc_blk, per * (unsigned long long)(t1 - t0));
+                    if (nesc) atomicAdd(&bp->stats->tc_esc, per * nesc);
                 }
             }
             // all MMAs issued by this thread have completed once drain fires
-            mma_commit(drain);
+            if (PAIR) mma_commit_pair(drain);
+            else mma_commit(drain);
             wait_drain(drain, 0);
         }
     } else if (status) {
@@ -732,6 +830,13 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
         // warp pair (q, h): TMEM lane quarter q (its 32 target rows), columns h HALF ..
         // h HALF + HALF - 1 of every tile; each warp keeps its own online log-sum-exp of its
         // rows over its columns, and the pair merges them at the end of an item
+        // a wait whose outcome every lane of the warp shares (the lanes go on to aligned
+        // TMEM loads and warp barriers together, or all leave); cl: acquire at cluster scope
+        auto wait_warp = [&](uint64_t* bar, uint32_t parity, bool cl = false) -> bool {
+            const bool got = cl ? wait_bounded<true>(bar, parity, abort_flag, status, w.wait_ns)
+                                : wait_bounded<false>(bar, parity, abort_flag, status, w.wait_ns);
+            return __all_sync(0xffffffffu, got);
+        };
         const int ew = warp - 2;       // epilogue warp index 0..7
         const int q = warp & 3;        // TMEM lane quarter (fixed by the warp's rank in its warpgroup)
         const int h = ew >> 2;         // column half
@@ -851,10 +956,16 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                     }
                 }
             };
-            auto release = [&](int acc) {
+            // this warp is done with accumulator acc and q buffer qs
+            auto release = [&](int acc, int qs) {
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[acc]);
+                if (lane == 0) {
+                    mbar_arrive(&qempty[qs]);
+                    // the TMEM loads completed (wait::ld) and are fenced before this signal
+                    if (PAIR) mbar_arrive_remote(tpair_lead + (uint32_t)(acc * 8));
+                    else mbar_arrive(&tempty[acc]);
+                }
             };
             // column direction of a symmetric block: target c (a column) from source i (a
             // row of this item); exact score with the drift at the target, added to the
@@ -897,24 +1008,29 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             auto tile = [&](int t, int mode) -> bool {
                 const int acc = (int)(tcount & 1u);
                 const uint32_t aph = (tcount >> 1) & 1u;
+                const int qs = (int)(tcount % QB);
+                const uint32_t qph = (tcount / QB) & 1u;
                 ++tcount;
                 const long long c0 = (long long)t * BN + h * HALF;   // first source of this warp
                 const long long cchunk = c0 / 128;
                 const int hm = !k.tc_sym ? 1 : (cchunk < a_chunk ? 0 : (cchunk == a_chunk ? 1 : 2));
                 if (mode == 3 || hm == 0) {
-                    if (!wait_bounded(&tfull[acc], aph, abort_flag, status, w.wait_ns)) return false;
+                    // unused here, but a q buffer is handed back only once its copy landed (the
+                    // producer re-arms its barrier next)
+                    if (!wait_warp(&qfull[qs], qph)) return false;
+                    if (!wait_warp(&tfull[acc], aph)) return false;
                     tc_fence_after();
-                    release(acc);
+                    release(acc, qs);
                     return true;
                 }
                 const bool first_pass = (mode == 1);
                 const float nu_s = first_pass ? nu1_i : nu_i;
                 // this warp's columns of the staged q values and the tile's chunk maxima
-                // (producer, per accumulator)
-                const float* qw = qbuf + acc * BN + h * HALF;
-                const float* qtw = qtbuf + acc * BN + h * HALF;   // q_c - (rho_c^2 + err_c)
-                const float* ci = qinfo + acc * 16;
-                if (!wait_bounded(&qfull[acc], aph, abort_flag, status, w.wait_ns)) return false;
+                // (producer, per tile, q buffer qs)
+                const float* qw = qbuf + qs * BN + h * HALF;
+                const float* qtw = qtbuf + qs * BN + h * HALF;   // q_c - (rho_c^2 + err_c)
+                const float* ci = qinfo + qs * 16;
+                if (!wait_warp(&qfull[qs], qph)) return false;
                 const float rnu_s = first_pass ? rnu1_i : rnu_i;
                 // the tile's threshold, from its chunk maxima
                 auto tile_theta = [&]() -> float {
@@ -933,7 +1049,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 // candidate only if q_s - 2 G <= max(theta_i, Rmax - nu_i), Rmax the largest
                 // column bound of this warp's chunk
                 const float rmax_c = ci[(BN == 256 ? h : 0) * 8 + (first_pass ? 4 : 3)];
-                if (!wait_bounded(&tfull[acc], aph, abort_flag, status, w.wait_ns)) return false;
+                if (!wait_warp(&tfull[acc], aph)) return false;
                 tc_fence_after();
                 const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN + h * HALF);
                 if (k.r <= 64) {
@@ -971,7 +1087,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                         }
                         theta = tile_theta();
                     }
-                    release(acc);
+                    release(acc, qs);
                     return true;
                 }
                 // long rows: 32 columns per TMEM load.  First test: with q_min the smallest
@@ -980,7 +1096,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 // covers; only a lane that passes it (some lane of the warp) computes the
                 // smallest q_s - 2 G, and only when that passes theta_any the candidate masks
                 int cnt = 0;
-                const float* qmw = qmbuf + acc * (BN / 32) + h * (HALF / 32);
+                const float* qmw = qmbuf + qs * (BN / 32) + h * (HALF / 32);
                 // the threshold from the item's maxima bounds every tile's from above
                 // (screen_theta grows with lmax, numax and rnumax; the margin covers
                 // rounding); the tile's own is computed only for a lane that passes with it
@@ -1065,7 +1181,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                         nzm |= 1u << ch;
                     }
                 }
-                release(acc);
+                release(acc, qs);
                 if (use_l0 && l0_chunks >= 16 && 2 * l0_pass > l0_chunks) use_l0 = false;
                 const int tot = (int)__reduce_add_sync(0xffffffffu, (unsigned)cnt);
                 if (tot == 0) return true;
@@ -1084,8 +1200,15 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             for (int t = t0; t < t1 && ok; ++t) ok = tile(t, pre ? 1 : 0);
             if (ok && pre) {
                 __syncwarp();
-                if (lane == 0) mbar_arrive(escb);
-                if (!wait_bounded(escb, par, abort_flag, status, w.wait_ns)) ok = false;
+                if (lane == 0) {
+                    if (PAIR) {   // this warp's marks are read by both CTAs
+                        mbar_arrive_cluster(mapa_shared(escb, rank));
+                        mbar_arrive_cluster(escb_peer);
+                    } else {
+                        mbar_arrive(escb);
+                    }
+                }
+                if (!wait_warp(escb, par, CL)) ok = false;
                 for (int t = t0; t < t1 && ok; ++t)
                     if (esc_any(par, t - t0)) ok = tile(t, esc_bit(ew, par, t - t0) ? 2 : 3);
             }
@@ -1093,7 +1216,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
             // shared memory (bounded hand-shakes, so an aborted partner cannot block)
             const uint32_t xph = nitem & 1u;
             if (ok && h == 1) {
-                if (nitem > 0 && !wait_bounded(&xfree[q], xph ^ 1u, abort_flag, status, w.wait_ns)) ok = false;
+                if (nitem > 0 && !wait_warp(&xfree[q], xph ^ 1u)) ok = false;
                 if (ok) {
 #pragma unroll
                     for (int j = 0; j < N; ++j) { xrow[2 * j] = mx[j]; xrow[2 * j + 1] = sm[j]; }
@@ -1102,7 +1225,7 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
                 }
             }
             if (ok && h == 0) {
-                if (!wait_bounded(&xfull[q], xph, abort_flag, status, w.wait_ns)) ok = false;
+                if (!wait_warp(&xfull[q], xph)) ok = false;
                 if (ok) {
 #pragma unroll
                     for (int j = 0; j < N; ++j) {
@@ -1138,10 +1261,14 @@ __global__ void __launch_bounds__(tc::NUM_THREADS, 1)
     }
     tc_fence_before();
     __syncthreads();
+    // a pair leaves together: no remote arrive, mark read or MMA into this CTA's TMEM is
+    // outstanding once both CTAs are here
+    if (PAIR) cluster_sync();
     tc_fence_after();
     if (warp == 1) {
         __syncwarp();
-        tmem_dealloc(tmem, C::TMEM_COLS);
+        if (PAIR) tmem_dealloc_pair(tmem, C::TMEM_COLS);
+        else tmem_dealloc(tmem, C::TMEM_COLS);
     }
     // the last CTA to finish runs the first-pass controller of every filter of the launch
     if (threadIdx.x == 0) {
@@ -1239,21 +1366,19 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-template <int N, int BN>
-void* kernel_ptr() { return reinterpret_cast<void*>(k_ksum_tc<N, BN>); }
-
-template <int BN>
+template <int BN, bool PAIR>
 cudaError_t set_attr_all() {
     cudaError_t e = cudaSuccess;
-    const int sm = tc::Cfg<BN>::SMEM_BYTES;
+    const int sm = tc::Cfg<BN, PAIR>::SMEM_BYTES;
     // the block must be launchable at its size (registers per thread x threads)
     cudaFuncAttributes fa;
-    if ((e = cudaFuncGetAttributes(&fa, k_ksum_tc<3, BN>)) != cudaSuccess) return e;
+    if ((e = cudaFuncGetAttributes(&fa, k_ksum_tc<3, BN, PAIR>)) != cudaSuccess) return e;
     if (fa.maxThreadsPerBlock < tc::NUM_THREADS) return cudaErrorLaunchOutOfResources;
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<1, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<2, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<3, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<4, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    const auto a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<1, BN, PAIR>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<2, BN, PAIR>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<3, BN, PAIR>, a, sm);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ksum_tc<4, BN, PAIR>, a, sm);
     return e;
 }
 
@@ -1263,13 +1388,47 @@ cudaError_t launch_bn(int N, unsigned grid, const CUtensorMap& a, const CUtensor
     if (grid == 0) return cudaSuccess;
     const int sm = tc::Cfg<BN>::SMEM_BYTES;
     switch (N) {
-        case 1: k_ksum_tc<1, BN><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
-        case 2: k_ksum_tc<2, BN><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
-        case 3: k_ksum_tc<3, BN><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
-        case 4: k_ksum_tc<4, BN><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
+        case 1: k_ksum_tc<1, BN, false><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
+        case 2: k_ksum_tc<2, BN, false><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
+        case 3: k_ksum_tc<3, BN, false><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
+        case 4: k_ksum_tc<4, BN, false><<<grid, tc::NUM_THREADS, sm, s>>>(a, bm, k, b, w); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+// Launch configuration of the pair kernel: `clusters` 2-CTA clusters, one CTA per SM.
+cudaLaunchConfig_t pair_config(unsigned clusters, cudaStream_t s, cudaLaunchAttribute* at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * clusters);
+    cfg.blockDim = dim3(tc::NUM_THREADS);
+    cfg.dynamicSmemBytes = tc::Cfg<256, true>::SMEM_BYTES;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+template <int N>
+cudaError_t launch_pair_n(unsigned clusters, const CUtensorMap& a, const Consts<float>& k, const Bufs<float>& b,
+                          const TcWork& w, cudaStream_t s) {
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = pair_config(clusters, s, at);
+    return cudaLaunchKernelEx(&cfg, k_ksum_tc<N, 256, true>, a, a, k, b, w);
+}
+cudaError_t launch_pair(int N, unsigned clusters, const CUtensorMap& a, const Consts<float>& k, const Bufs<float>& b,
+                        const TcWork& w, cudaStream_t s) {
+    if (clusters == 0) return cudaSuccess;
+    switch (N) {
+        case 1: return launch_pair_n<1>(clusters, a, k, b, w, s);
+        case 2: return launch_pair_n<2>(clusters, a, k, b, w, s);
+        case 3: return launch_pair_n<3>(clusters, a, k, b, w, s);
+        case 4: return launch_pair_n<4>(clusters, a, k, b, w, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
@@ -1293,9 +1452,23 @@ bool make_tc_map(void* map_out, const void* base, long long rows, int cols, int 
 // when a BF16 handle or batch is created, so that no attribute call happens during
 // stream capture).
 cudaError_t prepare_ksum_tc() {
-    cudaError_t e = set_attr_all<256>();
-    if (e == cudaSuccess) e = set_attr_all<128>();
+    cudaError_t e = set_attr_all<256, false>();
+    if (e == cudaSuccess) e = set_attr_all<128, false>();
+    if (e == cudaSuccess) e = set_attr_all<256, true>();
     return e;
+}
+
+// How many 2-CTA clusters of the pair kernel can be resident at once on the current
+// device (0 when clusters of its size cannot be placed).  Host-side set-up only.
+int tc_pair_max_clusters() {
+    cudaLaunchAttribute at[1];
+    const cudaLaunchConfig_t cfg = pair_config(1, nullptr, at);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_ksum_tc<3, 256, true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
 }
 
 // Single filter: the work list (items, cta_start) was built by the handle
@@ -1315,7 +1488,9 @@ cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStr
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     const TcWork w{nullptr, nullptr, b.tc_items, b.tc_cta_start, 1, k.wait_ns};
-    e = launch_bn<256>(k.N, (unsigned)b.tc_grid, ma, mb, k, b, w, s);
+    // tc_grid counts CTAs; a paired schedule has tc_grid / 2 work lists, one per cluster
+    e = b.tc_pair ? launch_pair(k.N, (unsigned)(b.tc_grid / 2), ma, k, b, w, s)
+                  : launch_bn<256>(k.N, (unsigned)b.tc_grid, ma, mb, k, b, w, s);
     if (e != cudaSuccess) return e;
     int l = k.tc_sym ? 3 : 2;
     if (b.tc_splits > 1 || k.tc_sym) {
