@@ -38,9 +38,12 @@ from synth.configs import batched_workloads  # noqa: E402
 
 DEFAULT_WORKLOAD = "cubic_r1000_n65536"
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of the prediction
-# kernel, from one ncu capture of the workload, keyed by workload and screen operands.  An
-# entry is removed whenever the kernel changes after its capture.
-NCU_TRAFFIC = {("cubic_r1000_n65536", "fp8"): 39.31392e6 + 0.466432e6}
+# kernel, from one ncu capture of the workload, keyed by workload, screen operands and
+# whether the kernel ran on CTA pairs.  An entry is removed whenever the kernel changes
+# after its capture.
+NCU_TRAFFIC = {("cubic_r1000_n65536", "fp8", False): 39.31776e6 + 0.551424e6}
+# --cta-pair: the tensor-core prediction on 2-CTA clusters (yy_set_cta_pair)
+CTA_PAIR = False
 METRIC = "filter steps/s & kernel pair-evals/s at r=1000: mixed vs FP32, same RMSE"
 
 
@@ -175,6 +178,8 @@ def _make_filter(w, precision, seed, device, stream=None, screen_prefix=0, scree
     cfg = binding.config_from_workload(w, precision=precision, screen_prefix=screen_prefix, screen_type=screen_type)
     flt = binding.Filter(cfg, device=device, stream=stream)
     flt.init_nodes(sobol_poly_params(w.r, seed), sobol_scramble_params(w.r, seed), np.zeros(w.r))
+    if precision == "bf16":
+        flt.set_cta_pair(CTA_PAIR)
     return flt
 
 
@@ -271,7 +276,8 @@ def measure_single(w, prec, screen_type, screen_prefix, K, W, device, seed, dist
         last, nxt, tiles, resc = flt.screen()
         screen = {"operands": screen_type, "first_pass_stages": last, "stage_coords": stage,
                   "stages": ((w.r + 63) // 64 * 64 + stage - 1) // stage, "tiles": tiles,
-                  "rescreened": resc, "exact_pairs": exact}
+                  "rescreened": resc, "exact_pairs": exact,
+                  "cta_pairs": flt.set_cta_pair(CTA_PAIR)}   # 2-CTA clusters of the schedule (0: single CTAs)
         flops = _gram_flops(w.r, last, stage, tiles, resc)
         peak, note = _tensor_peak(screen_type)
         roof = {"bound": "tensor", "achieved": round(flops / (pred_ms / 1e3) / 1e12, 3), "peak": peak,
@@ -468,8 +474,8 @@ def run_yy(args):
                 "h2d_bytes_per_step": 8 * w.r, "d2h_bytes_per_step": 8 * (2 * w.r + 2) + 56},
         "gpu_launches": res["gpu_launches"],
         "screen": res["screen"],
-        "roofline": dict(res["roofline"], traffic=NCU_TRAFFIC.get((w.name, args.screen_type)) if prec == "bf16"
-                         else None),
+        "roofline": dict(res["roofline"], traffic=NCU_TRAFFIC.get((w.name, args.screen_type, CTA_PAIR))
+                         if prec == "bf16" else None),
     }
     if args.fp32_steps > 0 and prec == "bf16":
         out.update(_comparators(w, K, W, tr, device, args.fp32_steps, res["est"]))
@@ -737,7 +743,11 @@ def main():
                     help="operands of the screen's Gram product (default: the workload's)")
     ap.add_argument("--screen-prefix", type=int, default=0,
                     help="BF16 screen: first-pass coordinate chunks of 64 (0 = chosen on the device)")
+    ap.add_argument("--cta-pair", action="store_true",
+                    help="BF16 screen on 2-CTA clusters (tcgen05.mma.cta_group::2); single CTAs by default")
     args = ap.parse_args()
+    global CTA_PAIR
+    CTA_PAIR = args.cta_pair
     if args.warmup < 3 and args.impl == "yy":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

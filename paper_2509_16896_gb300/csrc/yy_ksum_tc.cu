@@ -150,17 +150,6 @@ __device__ __forceinline__ void wait_drain(uint64_t* bar, uint32_t parity) {
     while (!mbar_try_wait(bar, parity))
         if (globaltimer() - t0 > tc::kTimeoutNs) return;
 }
-// a * b + c on two float lanes at once (one packed FMA, each lane rounded as fmaf)
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    uint64_t av, bv, cv, dv;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(av) : "f"(a.x), "f"(a.y));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(bv) : "f"(b.x), "f"(b.y));
-    asm("mov.b64 %0, {%1, %2};" : "=l"(cv) : "f"(c.x), "f"(c.y));
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(dv) : "l"(av), "l"(bv), "l"(cv));
-    float2 d;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(d.x), "=f"(d.y) : "l"(dv));
-    return d;
-}
 // the largest of three floats (exact)
 __device__ __forceinline__ float fmax3(float a, float b, float c) {
     float d;

@@ -162,10 +162,10 @@ __device__ __forceinline__ void prep_rows(const Consts<T>& k, const Bufs<T>& b, 
                     const int d = 64 * q + 2 * lane;
                     const float2 cc = *reinterpret_cast<const float2*>(s_cc + d);
                     const float2 sc = *reinterpret_cast<const float2*>(s_sc + d);
-                    float f0, f1, sn0, sn1;
-                    cubic_drift_narrow(uu[q].x, cc.x, sc.x, &f0, &sn0);
-                    cubic_drift_narrow(uu[q].y, cc.y, sc.y, &f1, &sn1);
-                    div -= sn0 + sn1;
+                    float2 f2, s2;   // both coordinates in packed pairs (same values as one by one)
+                    cubic_drift_narrow2(uu[q], cc, sc, &f2, &s2);
+                    const float f0 = f2.x, f1 = f2.y;
+                    div -= s2.x + s2.y;
                     nf = fmaf(f0, f0, fmaf(f1, f1, nf));
                     if constexpr (mode == kPrepRestart) {
                         const float2 iv = *reinterpret_cast<const float2*>(s_iv + d);
