@@ -365,10 +365,14 @@ __device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& 
     }
     double* p = b.part + (size_t)bid * (4 + 2 * k.r_pad);
     if (tid == 0) { p[0] = W; p[1] = Q; }
+    // only partials with weight are merged (finalize_scalars lists them), so a block
+    // without weight -- most of them when the posterior is concentrated -- writes no moments
+    if (W > 0.0) {
 #pragma unroll
-    for (int q = 0; q < kMomDims; ++q) {
-        const int d = tid + 256 * q;
-        if (d < k.r_pad) { p[4 + d] = mu[q]; p[4 + k.r_pad + d] = M2[q]; }
+        for (int q = 0; q < kMomDims; ++q) {
+            const int d = tid + 256 * q;
+            if (d < k.r_pad) { p[4 + d] = mu[q]; p[4 + k.r_pad + d] = M2[q]; }
+        }
     }
 }
 
