@@ -325,6 +325,7 @@ __device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& 
             T S[kMomDims], muc[kMomDims], m2[kMomDims];
 #pragma unroll
             for (int q = 0; q < kMomDims; ++q) { S[q] = T(0); m2[q] = T(0); }
+#pragma unroll 4   // several rows' loads in flight; the sums still run in row order
             for (int l = 0; l < cnt; ++l) {
                 const float* ur = b.u + (size_t)(c0 + s_rows[l]) * k.r_pad;
                 const T wl = s_w[l];
@@ -336,6 +337,7 @@ __device__ __forceinline__ void moments_body(const Consts<T>& k, const Bufs<T>& 
             }
 #pragma unroll
             for (int q = 0; q < kMomDims; ++q) muc[q] = S[q] / (T)Wc;
+#pragma unroll 4
             for (int l = 0; l < cnt; ++l) {
                 const float* ur = b.u + (size_t)(c0 + s_rows[l]) * k.r_pad;
                 const T wl = s_w[l];
@@ -442,55 +444,48 @@ __device__ __forceinline__ void finalize_scalars_body(const Consts<T>& k, const 
     }
 }
 
-// Per coordinate: mean and variance merged from the block partials with Chan's rule;
-// x_hat = c + mean.  8 coordinates per block and 32 groups of partials (group g takes the
-// listed partials g, g + 32, ...); the 32 group results are merged pairwise in a tree.
-__device__ __forceinline__ void chan_merge(double& W, double& mu, double& M2, double W2, double mu2, double M22) {
-    if (!(W2 > 0.0)) return;
-    if (!(W > 0.0)) { W = W2; mu = mu2; M2 = M22; return; }
-    const double Wn = W + W2;
-    const double delta = mu2 - mu;
-    mu = fma(delta, W2 / Wn, mu);
-    M2 += M22 + delta * delta * (W * W2 / Wn);
-    W = Wn;
-}
-
+// Per coordinate: mean and variance from the block partials with weight (finalize_scalars'
+// list), one warp per coordinate, 8 per block, in two reductions: the mean of the block
+// means weighted by W_b (one division), then M2 = sum of M2_b + W_b (mu_b - mu)^2 about it
+// (the parallel-axis identity: the same quantity as merging the partials pairwise, without a
+// float64 division per partial, slow on this part); x_hat = c + mean.
 // rec != NULL: the shard's merged mean and M2 of u go to its record instead of x_hat, v_hat.
 template <typename T>
 __device__ __forceinline__ void finalize_dims_body(const Consts<T>& k, const Bufs<T>& b, int nb, int bid,
                                                    double* rec = nullptr) {
-    __shared__ double g_w[32][8], g_mu[32][8], g_m2[32][8];
     (void)nb;
-    const int c8 = threadIdx.x & 7, g = threadIdx.x >> 3;
-    const int d = bid * 8 + c8;
-    const int np = b.stats->part_count;   // partials with weight (finalize_scalars' list)
-    double W = 0.0, mu = 0.0, M2 = 0.0;
-    if (d < k.r)
-        for (int jj = g; jj < np; jj += 32) {
-            const double* p = b.part + (size_t)b.part_list[jj] * (4 + 2 * k.r_pad);
-            chan_merge(W, mu, M2, p[0], p[4 + d], p[4 + k.r_pad + d]);
-        }
-    g_w[g][c8] = W;
-    g_mu[g][c8] = mu;
-    g_m2[g][c8] = M2;
-    __syncthreads();
-    for (int s = 16; s > 0; s >>= 1) {
-        if (g < s) {
-            double Wa = g_w[g][c8], ma = g_mu[g][c8], Ma = g_m2[g][c8];
-            chan_merge(Wa, ma, Ma, g_w[g + s][c8], g_mu[g + s][c8], g_m2[g + s][c8]);
-            g_w[g][c8] = Wa;
-            g_mu[g][c8] = ma;
-            g_m2[g][c8] = Ma;
-        }
-        __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int d = bid * 8 + (int)(threadIdx.x >> 5);
+    if (d >= k.r) return;
+    const int np = b.stats->part_count;
+    const size_t stride = 4 + 2 * (size_t)k.r_pad;
+    double W = 0.0, WM = 0.0;
+    for (int jj = lane; jj < np; jj += 32) {
+        const double* p = b.part + (size_t)b.part_list[jj] * stride;
+        W += p[0];
+        WM = fma(p[0], p[4 + d], WM);
     }
-    if (g == 0 && d < k.r && rec) {
-        rec[4 + d] = g_mu[0][c8];
-        rec[4 + k.r + d] = g_m2[0][c8];
-    } else if (g == 0 && d < k.r) {
-        const double Wt = g_w[0][c8];
-        const double mean = b.centre[d] + g_mu[0][c8];
-        const double var = (Wt > 0.0) ? g_m2[0][c8] / Wt : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        W += __shfl_xor_sync(0xffffffffu, W, o);
+        WM += __shfl_xor_sync(0xffffffffu, WM, o);
+    }
+    const double mu = (W > 0.0) ? WM / W : 0.0;
+    double M2 = 0.0;
+    for (int jj = lane; jj < np; jj += 32) {
+        const double* p = b.part + (size_t)b.part_list[jj] * stride;
+        const double dm = p[4 + d] - mu;
+        M2 += fma(p[0] * dm, dm, p[4 + k.r_pad + d]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) M2 += __shfl_xor_sync(0xffffffffu, M2, o);
+    if (lane != 0) return;
+    if (rec) {
+        rec[4 + d] = mu;
+        rec[4 + k.r + d] = M2;
+    } else {
+        const double mean = b.centre[d] + mu;
+        const double var = (W > 0.0) ? M2 / W : 0.0;
         b.mean[d] = mean;
         b.var[d] = var;
         if (!isfinite(mean) || !isfinite(var)) atomicOr(&b.stats->status, kStatusNonFinite);
