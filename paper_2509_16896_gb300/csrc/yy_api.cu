@@ -46,11 +46,20 @@ yy_status build_tc_schedule(yy_filter* f) {
     std::vector<std::vector<int4>> per(grid);
     int S = 1;
     if (f->kf.tc_sym) {
+        // range length: 64 source tiles, or shorter (down to 8) where a CTA's share of the
+        // blocks is small, so that every CTA gets about four items to balance with; taken
+        // per CTA (a cluster holds two), so that both forms split alike and take the same
+        // screening decisions
+        double work = 0.0;
+        for (long long t = t_lo; t < t_hi; ++t) work += span * (double)(nst - (int)(span == 2 ? t : t / 2));
+        const int ctas = span * grid;
+        const int len = (int)std::max(8.0, std::min(64.0, work / ctas / 4.0));
+        f->kf.tc_split_len = len;
         struct It { double cost; int t, q, S; };
         std::vector<It> all;
         for (long long t = t_lo; t < t_hi; ++t) {
             const int L = nst - (int)(span == 2 ? t : t / 2);
-            const int St = tc_sym_splits(L);
+            const int St = tc_sym_splits(L, len);
             for (int q = 0; q < St; ++q)
                 all.push_back({(double)((L * (q + 1)) / St - (L * q) / St) + 1.0, (int)t, q, St});
             S = std::max(S, St);
@@ -257,6 +266,7 @@ void fill_consts(yy_filter* f, Consts<T>* k, const double* halfwidth) {
     k->tc_prefix = c.screen_prefix > 0 ? c.screen_prefix : 0;
     // symmetric blocks need the long-row epilogue (r > 64)
     k->tc_sym = (c.precision == YY_PREC_BF16 && c.r > 64) ? 1 : 0;
+    k->tc_split_len = 64;
     // Screen operands.  BF16: |dG| <= 2^-6 |u_i||u_s| (unit roundoff 2^-9 per operand, 4x
     // slack).  FP8 e4m3 of s u, s the largest power of two with s 8 max R <= 448 (a learned
     // box is at most 8 times wider): per product (2 2^-4 + 2^-8) |a b| = 0.129 |a b|, plus

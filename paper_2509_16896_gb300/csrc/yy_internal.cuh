@@ -68,6 +68,7 @@ struct Consts {
     T cj_off[kMaxScales];    // C_j - C_ref, C_j = -(r/2) log(2 pi tau_j) + log w_q
     int tc_prefix;           // fixed first-pass stages of the tensor-core screen (0 = adaptive)
     int tc_sym;              // screen over the upper block triangle, both directions per block
+    int tc_split_len;        // symmetric screen: source tiles per work item (set with the work list)
     int tc_fp8;              // screen operands FP8 e4m3 (else BF16)
     int tc_r8;               // FP8: coordinates per row of the e4m3 copy (multiple of 128)
     float tc_s;              // FP8: power-of-two scale of the coordinates in the e4m3 copy
@@ -161,9 +162,10 @@ struct Traj {
 };
 
 // Source splits of target tile a of the symmetric screen: its L source tiles in ranges of
-// about 64 (at most 8), so that the work list balances.
-__host__ __device__ __forceinline__ int tc_sym_splits(int L) {
-    const int s = (L + 63) / 64;
+// about len (at most 8 ranges), so that the work list balances; len is the filter's
+// tc_split_len (64, or shorter when the work per CTA is small).
+__host__ __device__ __forceinline__ int tc_sym_splits(int L, int len) {
+    const int s = (L + len - 1) / len;
     return s < 1 ? 1 : (s > 8 ? 8 : s);
 }
 

@@ -1284,7 +1284,7 @@ __device__ __forceinline__ void tc_merge_body(const Consts<float>& k, const Bufs
     const int nst = (int)(k.n_pad / 256);
     for (long long i = k.row0 + bid * (long long)blockDim.x + threadIdx.x; i < k.row1; i += (long long)nblk * blockDim.x) {
         if (b.mask[i]) { b.logw_pred[i] = -INFINITY; continue; }
-        const int ns = k.tc_sym ? tc_sym_splits(nst - (int)(i / 256)) : nsplit;
+        const int ns = k.tc_sym ? tc_sym_splits(nst - (int)(i / 256), k.tc_split_len) : nsplit;
         float mx[N], sm[N];
 #pragma unroll
         for (int j = 0; j < N; ++j) {
