@@ -21,14 +21,13 @@
 // comes from the angle-addition form of yy_drift.cuh; in float64 from sincos.
 #include "yy_internal.cuh"
 #include "yy_drift.cuh"
+#include "yy_prep_dims.cuh"
 
 #include <cuda_fp8.h>
 
 #include <type_traits>
 
 namespace yy {
-
-enum PrepMode { kPrepOnly = 0, kPrepInit = 1, kPrepRestart = 2 };
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -72,38 +71,6 @@ template <>
 __device__ __forceinline__ float exp_w<float>(float x) { return expf(x); }
 template <>
 __device__ __forceinline__ double exp_w<double>(double x) { return exp(x); }
-
-// Per-dimension constants of one preparation pass: the centre split into a T-precision
-// head and tail (x = c_hi + (u + c_lo) loses only the final rounding), for a Gaussian
-// restart 1 / (2 max(v_hat_d, (R_d / 4)^2)), and cos c_d, sin c_d (NaN cosine where the
-// half-width is too wide for the polynomials of yy_drift.cuh).
-template <typename T>
-__device__ __forceinline__ void prep_dims_body(const Consts<T>& k, const Bufs<T>& b, int mode, int init_kind,
-                                               int bid, int nblk) {
-    if (mode == kPrepRestart && b.stats->restart_flag == 0) return;
-    const double* cen = (mode == kPrepRestart) ? b.next_centre : b.centre;
-    const double* half = (mode == kPrepRestart) ? b.next_half : b.halfwidth;
-    const int rp = k.r_pad;
-    for (int d = bid * blockDim.x + threadIdx.x; d < rp; d += nblk * blockDim.x) {
-        T hi = T(0), lo = T(0), iv = T(0), cc = T(0), sc = T(0);   // padded: u = 0 gives f = 0
-        if (d < k.r) {
-            const double c = cen[d];
-            hi = (T)c;
-            lo = (T)(c - (double)hi);
-            if (mode == kPrepRestart && init_kind == YY_RESTART_INIT_GAUSS) {
-                const double R4 = 0.25 * half[d];
-                iv = (T)(0.5 / fmax(b.var[d], R4 * R4));
-            }
-            cc = (half[d] <= kPolyMaxU) ? (T)cos(c) : (T)NAN;
-            sc = (T)sin(c);
-        }
-        b.dimc[d] = hi;
-        b.dimc[rp + d] = lo;
-        b.dimc[2 * rp + d] = iv;
-        b.dimc[3 * rp + d] = cc;
-        b.dimc[4 * rp + d] = sc;
-    }
-}
 
 // The pass proper, compiled per mode and per "first" (node-only quantities too), so that
 // the restart pass carries none of the other modes' float64 arithmetic.
@@ -400,6 +367,14 @@ cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, boo
     k_prep<T><<<(unsigned)prep_grid(k.n_pad), 256, 0, s>>>(k, b, mode, first ? 1 : 0, prior_mean, prior_var);
     return cudaGetLastError();
 }
+
+// The rows only (the per-dimension constants already written, as by the restart head).
+template <typename T>
+cudaError_t launch_prep_rows(const Consts<T>& k, const Bufs<T>& b, int mode, cudaStream_t s) {
+    k_prep<T><<<(unsigned)prep_grid(k.n_pad), 256, 0, s>>>(k, b, mode, 0, 0.0, 1.0);
+    return cudaGetLastError();
+}
+template cudaError_t launch_prep_rows<float>(const Consts<float>&, const Bufs<float>&, int, cudaStream_t);
 
 template <typename T>
 cudaError_t launch_prep(const Consts<T>& k, const Bufs<T>& b, bool init_weights, bool first,

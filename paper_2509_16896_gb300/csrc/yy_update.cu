@@ -26,6 +26,7 @@
 // (prefix kb_) runs it for trajectory blockIdx.y of a Traj array, so that one launch
 // covers a whole batch of ragged filters.
 #include "yy_internal.cuh"
+#include "yy_prep_dims.cuh"
 
 namespace yy {
 
@@ -619,6 +620,18 @@ __global__ void __launch_bounds__(256) k_finalize_dims(Consts<T> k, Bufs<T> b, i
 }
 template <typename T>
 __global__ void k_restart_begin(DevStats* st, int mode) { restart_begin_body(st, mode); }
+// Float filters without a learned proposal: the restart decision, the box at x_hat and the
+// restart pass's per-dimension constants in one block (the three steps of k_restart_begin,
+// k_restart_box and k_prep_dims; each reads what the one before wrote).
+template <typename T>
+__global__ void __launch_bounds__(256) k_restart_head(Consts<T> k, Bufs<T> b, int mode, int init_kind,
+                                                      double base_R) {
+    restart_begin_body(b.stats, mode);
+    __syncthreads();
+    restart_box_body<T>(k, b, nullptr, base_R);
+    __syncthreads();
+    prep_dims_body<T>(k, b, kPrepRestart, init_kind, 0, 1);
+}
 template <typename T>
 __global__ void k_restart_commit(Consts<T> k, Bufs<T> b) { restart_commit_body<T>(k, b); }
 template <typename T>
@@ -760,6 +773,8 @@ template <typename T>
 cudaError_t launch_prep_mode(const Consts<T>& k, const Bufs<T>& b, int mode, bool first,
                              double prior_mean, double prior_var, int init_kind, cudaStream_t s);
 template <typename T>
+cudaError_t launch_prep_rows(const Consts<T>& k, const Bufs<T>& b, int mode, cudaStream_t s);
+template <typename T>
 cudaError_t launch_prep_restart_batch(const Traj<T>* d_traj, int B, long long n_pad_max, cudaStream_t s);
 
 // Restart sequence (every kernel is a no-op unless the restart flag is set): begin, the
@@ -770,6 +785,16 @@ cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int i
                            struct ::yy_mlp* net, cudaStream_t s, int* launches) {
     if (mode == YY_RESTART_NEVER) return cudaSuccess;
     const int nb = kNumPartBlocks;
+    if (!net && sizeof(T) == 4) {   // float, plain or Gaussian restart: head, rows, weights, commit
+        k_restart_head<T><<<1, 256, 0, s>>>(k, b, mode, init_kind, base_R);
+        cudaError_t e = launch_prep_rows<T>(k, b, 2 /*restart*/, s);
+        if (e != cudaSuccess) return e;
+        k_lse_merge<<<1, 256, 0, s>>>(b.part, prep_grid(k.n_pad), b.stats, 1);
+        k_subtract<T><<<nb, 256, 0, s>>>(k, b, 1);
+        k_restart_commit<T><<<1, 256, 0, s>>>(k, b);
+        if (launches) *launches += 5;
+        return cudaGetLastError();
+    }
     int l = 0;
     k_restart_begin<T><<<1, 32, 0, s>>>(b.stats, mode);
     const float* out = nullptr;
