@@ -216,6 +216,10 @@ __device__ __forceinline__ void lse_partials_body(const Consts<T>& k, const Bufs
     }
 }
 
+// The partials' maxima and sums are float64; the rescale factors e^(m_b - M) in [0, 1]
+// are taken in the filter's working precision T (a float64 exponential per partial is
+// costly on this part, and float filters carry their log-weights in float).
+template <typename T>
 __device__ __forceinline__ void lse_merge_body(const double* __restrict__ part, int nb, DevStats* st, int conditional,
                                                int report = 1) {
     if (conditional && st->restart_flag == 0) return;
@@ -240,7 +244,8 @@ __device__ __forceinline__ void lse_merge_body(const double* __restrict__ part, 
     if (M != -INFINITY)
         for (int i = threadIdx.x; i < nb; i += blockDim.x) {
             const double mb = part[2 * i];
-            if (mb != -INFINITY) s += part[2 * i + 1] * exp(mb - M);
+            if (mb != -INFINITY)
+                s += part[2 * i + 1] * (sizeof(T) == 4 ? (double)expf((float)(mb - M)) : exp(mb - M));
         }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -600,8 +605,9 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_lse_partials(Consts<T> k, Bufs<T> b, int conditional) {
     lse_partials_body<T>(k, b, conditional, blockIdx.x, gridDim.x);
 }
+template <typename T>
 __global__ void k_lse_merge(const double* __restrict__ part, int nb, DevStats* st, int conditional, int report = 1) {
-    lse_merge_body(part, nb, st, conditional, report);
+    lse_merge_body<T>(part, nb, st, conditional, report);
 }
 template <typename T>
 __global__ void k_subtract(Consts<T> k, Bufs<T> b, int conditional) {
@@ -658,7 +664,7 @@ __global__ void __launch_bounds__(256) kb_loglik(const Traj<T>* __restrict__ tr)
 template <typename T>
 __global__ void kb_lse_merge(const Traj<T>* __restrict__ tr, int nb, int conditional) {
     const Traj<T>& t = tr[blockIdx.y];
-    lse_merge_body(t.b.part, nb, t.b.stats, conditional);
+    lse_merge_body<T>(t.b.part, nb, t.b.stats, conditional);
 }
 template <typename T>
 __global__ void __launch_bounds__(256) kb_moments(const Traj<T>* __restrict__ tr) {
@@ -725,7 +731,7 @@ cudaError_t launch_update(const Consts<T>& k, const Bufs<T>& b, const double* dy
     k_obs_prep<T><<<1, 256, 0, s>>>(k, b, dy);
     if (k.noise == YY_NOISE_DIAG) k_loglik<T, true><<<nbl, 256, 0, s>>>(k, b);
     else k_loglik<T><<<nbl, 256, 0, s>>>(k, b);
-    k_lse_merge<<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0);
+    k_lse_merge<T><<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0);
     k_moments<T><<<nb, 256, 0, s>>>(k, b);
     k_finalize_scalars<T><<<1, 512, 0, s>>>(k, b, nb, restart_interval, ess_frac);
     k_finalize_dims<T><<<(k.r + 7) / 8, 256, 0, s>>>(k, b, nb);
@@ -744,7 +750,7 @@ cudaError_t launch_update_shard(const Consts<T>& k, const Bufs<T>& b, const doub
     k_obs_prep<T><<<1, 256, 0, s>>>(k, b, dy);
     if (k.noise == YY_NOISE_DIAG) k_loglik<T, true><<<nbl, 256, 0, s>>>(k, b);
     else k_loglik<T><<<nbl, 256, 0, s>>>(k, b);
-    k_lse_merge<<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0, 0);
+    k_lse_merge<T><<<1, 256, 0, s>>>(b.part, nbl, b.stats, 0, 0);
     k_moments<T><<<nb, 256, 0, s>>>(k, b);
     k_finalize_scalars<T><<<1, 512, 0, s>>>(k, b, nb, 0, 0.0, rec);
     k_finalize_dims<T><<<(k.r + 7) / 8, 256, 0, s>>>(k, b, nb, rec);
@@ -757,7 +763,7 @@ cudaError_t launch_normalise_only(const Consts<T>& k, const Bufs<T>& b, cudaStre
                                   int* launches) {
     const int nb = kNumPartBlocks;
     k_lse_partials<T><<<nb, 256, 0, s>>>(k, b, 0);
-    k_lse_merge<<<1, 256, 0, s>>>(b.part, nb, b.stats, 0);
+    k_lse_merge<T><<<1, 256, 0, s>>>(b.part, nb, b.stats, 0);
     k_subtract<T><<<nb, 256, 0, s>>>(k, b, 0);
     if (launches) *launches += 3;
     return cudaGetLastError();
@@ -789,7 +795,7 @@ cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int i
         k_restart_head<T><<<1, 256, 0, s>>>(k, b, mode, init_kind, base_R);
         cudaError_t e = launch_prep_rows<T>(k, b, 2 /*restart*/, s);
         if (e != cudaSuccess) return e;
-        k_lse_merge<<<1, 256, 0, s>>>(b.part, prep_grid(k.n_pad), b.stats, 1);
+        k_lse_merge<T><<<1, 256, 0, s>>>(b.part, prep_grid(k.n_pad), b.stats, 1);
         k_subtract<T><<<nb, 256, 0, s>>>(k, b, 1);
         k_restart_commit<T><<<1, 256, 0, s>>>(k, b);
         if (launches) *launches += 5;
@@ -810,7 +816,7 @@ cudaError_t launch_restart(const Consts<T>& k, const Bufs<T>& b, int mode, int i
     e = launch_prep_mode<T>(k, b, 2 /*restart*/, false, 0.0, 1.0, init_kind, s);
     if (e != cudaSuccess) return e;
     // the preparation pass wrote the log-sum-exp partials of the new weights
-    k_lse_merge<<<1, 256, 0, s>>>(b.part, prep_grid(k.n_pad), b.stats, 1);
+    k_lse_merge<T><<<1, 256, 0, s>>>(b.part, prep_grid(k.n_pad), b.stats, 1);
     k_subtract<T><<<nb, 256, 0, s>>>(k, b, 1);
     k_restart_commit<T><<<1, 256, 0, s>>>(k, b);
     if (launches) *launches += 7 + l + (net ? 1 : 0);
