@@ -196,6 +196,10 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
     b.stats = cv.take<DevStats>(sizeof(DevStats));
     if (c->precision == YY_PREC_BF16 || c->precision == YY_PREC_FP32_SCREEN)
         b.nu_chunk = cv.take<float>((size_t)n_pad * (r_pad / kColAlign) * sizeof(float));
+    // plain form of a filter with fewer than two target blocks of 64 per SM: its source
+    // ranges' partial states
+    if ((c->precision == YY_PREC_FP32 || c->precision == YY_PREC_FP64) && n_pad < 2 * 152 * 64)
+        b.simt_part = cv.take<T>((size_t)n_pad * kSimtMaxSplit * kMaxScales * 2 * sizeof(T));
     if (c->precision == YY_PREC_BF16) {
         b.tc_q = cv.take<float>((size_t)n_pad * sizeof(float));
         b.tc_q1 = cv.take<float>((size_t)n_pad * sizeof(float));
@@ -522,8 +526,9 @@ yy_status yy_predict(yy_filter* f) {
     cudaError_t e;
     if (f->fp64) {
         e = cudaMemsetAsync(&f->bd.stats->clamps, 0, sizeof(unsigned), f->stream);
-        if (e == cudaSuccess) e = launch_ksum_simt<double>(f->kd, f->bd, f->stream);
-        f->launches += 1;
+        int l = 0;
+        if (e == cudaSuccess) e = launch_ksum_simt<double>(f->kd, f->bd, f->stream, &l);
+        f->launches += l;
     } else if (f->use_op) {
         // materialised schedule: rebuild on the device if the node set moved, then apply
         e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
@@ -532,8 +537,9 @@ yy_status yy_predict(yy_filter* f) {
         f->launches += 2;
     } else if (f->cfg.precision == YY_PREC_FP32) {
         e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
-        if (e == cudaSuccess) e = launch_ksum_simt<float>(f->kf, f->bf, f->stream);
-        f->launches += 1;
+        int l = 0;
+        if (e == cudaSuccess) e = launch_ksum_simt<float>(f->kf, f->bf, f->stream, &l);
+        f->launches += l;
     } else if (f->cfg.precision == YY_PREC_FP32_SCREEN) {
         // first pass over 64 k coordinates: k = screen_prefix, else half of the 64-chunks
         const int nk = f->r_pad / kColAlign;

@@ -16,6 +16,7 @@ constexpr int kMaxScales = YY_MAX_SCALES;
 constexpr int kRowAlign = 256;       // node rows are padded to a multiple of this
 constexpr int kColAlign = 64;        // coordinates per row are padded to a multiple of this
 constexpr int kNumPartBlocks = 304;  // blocks of the reduction passes (2 per SM)
+constexpr int kSimtMaxSplit = 8;     // source ranges per target block of the plain form
 
 // Device status word bits (sticky until the handle is recreated).
 constexpr uint32_t kStatusNonFinite = 1u << 0;
@@ -141,6 +142,8 @@ struct Bufs {
     float* tc_tile_numax; // [n_pad / 128] max |u_s|^2 per chunk of 128 sources
     float* tc_tile_numax1;// [n_pad / 128] the same over the first-pass coordinates
     float* tc_part;       // [n_pad][8][4][2] partial (max, sum) of split work items
+    T* simt_part;         // [n_pad][kSimtMaxSplit][kMaxScales][2] plain form: partial (max, sum)
+                          // of each source range (filters with few target blocks only)
     int4* tc_items;       // single-filter work list (target tile, split, nsplit)
     int* tc_cta_start;    // [tc_grid + 1]
     int tc_grid;          // persistent CTAs of the single-filter prediction
@@ -184,7 +187,7 @@ cudaError_t launch_prep(const Consts<T>& k, const Bufs<T>& b, bool init_weights,
                         double prior_mean, double prior_var, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s);
+cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s, int* launches = nullptr);
 cudaError_t launch_ksum_scr32(const Consts<float>& k, const Bufs<float>& b, int k1, cudaStream_t s);
 cudaError_t launch_op_build(const Consts<float>& k, const Bufs<float>& b, bool force, cudaStream_t s);
 cudaError_t launch_op_apply(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s);

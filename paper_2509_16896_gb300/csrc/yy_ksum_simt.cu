@@ -54,8 +54,12 @@ template <> __device__ __forceinline__ double exp_fast<double>(double x) { retur
 // OPBUILD (float32): the materialised operator -- every pair's score without the source
 // weight, A_j(i, s) = -S1 / (2 tau_j) + S2 - tau_j |f_i|^2 / 2, is written to b.op instead of
 // being accumulated.
+// split / nsplit (plain form of a filter with few target blocks): this block sweeps only the
+// split-th of nsplit equal ranges of source tiles and stores its rows' partial (max, sum)
+// per scale in b.simt_part; k_simt_merge combines the ranges.
 template <typename T, int N, bool SCREEN = false, bool NOISE = false, bool OPBUILD = false>
-__device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>& b, int rk, int bid, int k1 = 0) {
+__device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>& b, int rk, int bid, int k1 = 0,
+                                               int split = 0, int nsplit = 1) {
     __shared__ T At[BK][BM];   // u of targets
     __shared__ T Ft[BK][BM];   // f of targets
     __shared__ T Bt[BK][BN];   // u of sources
@@ -109,7 +113,10 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
         }
     }
 
-    for (long long s0 = 0; s0 < k.n; s0 += BN) {
+    const long long src_tiles = (k.n + BN - 1) / BN;
+    const long long s_begin = (src_tiles * split / nsplit) * BN;
+    const long long s_end = std::min<long long>(k.n, (src_tiles * (split + 1) / nsplit) * BN);
+    for (long long s0 = s_begin; s0 < s_end; s0 += BN) {
         T S1[TM][TN], S2[TM][TN];
 #pragma unroll
         for (int a = 0; a < TM; ++a)
@@ -267,6 +274,20 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
             sm[a][j] = s;
         }
     if (tx != 0) return;
+    if (nsplit > 1) {   // this range's states; the merge applies the combination
+#pragma unroll
+        for (int a = 0; a < TM; ++a) {
+            const long long i = i0 + ty * TM + a;
+            if (i >= k.n) continue;
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                T* ps = b.simt_part + (((size_t)i * kSimtMaxSplit + split) * kMaxScales + j) * 2;
+                ps[0] = mx[a][j];
+                ps[1] = sm[a][j];
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < TM; ++a) {
         const long long i = i0 + ty * TM + a;
@@ -279,8 +300,35 @@ __device__ __forceinline__ void ksum_simt_body(const Consts<T>& k, const Bufs<T>
 }
 
 template <typename T, int N, bool NOISE = false>
-__global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int rk) {
-    ksum_simt_body<T, N, false, NOISE>(k, b, rk, (int)(k.row0 / BM) + blockIdx.x);
+__global__ void __launch_bounds__(256) k_ksum_simt(Consts<T> k, Bufs<T> b, int rk, int nsplit) {
+    ksum_simt_body<T, N, false, NOISE>(k, b, rk, (int)(k.row0 / BM) + (int)(blockIdx.x / nsplit), 0,
+                                       (int)(blockIdx.x % nsplit), nsplit);
+}
+
+// Merges the source ranges' (max, sum) states of every row and applies the multi-scale
+// combination (the plain form with nsplit > 1).
+template <typename T, int N, bool NOISE = false>
+__global__ void __launch_bounds__(256) k_simt_merge(Consts<T> k, Bufs<T> b, int nsplit) {
+    const long long i = k.row0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= k.row1 || i >= k.n) return;
+    if (b.mask[i]) { b.logw_pred[i] = T(-INFINITY); return; }
+    T mx[N], sm[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        T m = T(-INFINITY), s = T(0);
+        for (int q = 0; q < nsplit; ++q) {
+            const T* ps = b.simt_part + (((size_t)i * kSimtMaxSplit + q) * kMaxScales + j) * 2;
+            const T m2 = ps[0], s2 = ps[1];
+            if (m2 == T(-INFINITY)) continue;
+            if (m == T(-INFINITY)) { m = m2; s = s2; }
+            else if (m2 > m) { s = s * exp_fast<T>(m - m2) + s2; m = m2; }
+            else { s += s2 * exp_fast<T>(m2 - m); }
+        }
+        mx[j] = m;
+        sm[j] = s;
+    }
+    const T hld = NOISE ? b.hld[i] : T(0);
+    b.logw_pred[i] = combine_scales<T, N>(k, mx, sm, b.divf[i], b.logw[i], b.stats->c_ref, &b.stats->clamps, hld);
 }
 
 template <int N>
@@ -439,31 +487,47 @@ cudaError_t launch_ksum_simt_batch(const Traj<T>* d_traj, int B, int N, long lon
 template cudaError_t launch_ksum_simt_batch<float>(const Traj<float>*, int, int, long long, int, cudaStream_t, int*);
 template cudaError_t launch_ksum_simt_batch<double>(const Traj<double>*, int, int, long long, int, cudaStream_t, int*);
 
+// Source ranges per target block of the plain form: enough blocks for two per SM (at most
+// kSimtMaxSplit ranges, none beyond the source tiles), when the filter has few target
+// blocks and the workspace holds the partial states.
+int simt_splits(long long n_pad, long long tiles, bool has_part) {
+    if (!has_part || tiles <= 0) return 1;
+    long long sp = (2 * 152 + tiles - 1) / tiles;
+    sp = std::min<long long>(sp, kSimtMaxSplit);
+    sp = std::min<long long>(sp, n_pad / BN);
+    return (int)std::max<long long>(sp, 1);
+}
+
 template <typename T>
-cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s) {
+cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t s, int* launches) {
     const int rk = ((k.r + BK - 1) / BK) * BK;
-    const unsigned grid = (unsigned)((k.row1 - k.row0 + BM - 1) / BM);   // the handle's target blocks
-    if (grid == 0) return cudaSuccess;
-    if (k.noise == YY_NOISE_DIAG) {
-        switch (k.N) {
-            case 1: k_ksum_simt<T, 1, true><<<grid, 256, 0, s>>>(k, b, rk); break;
-            case 2: k_ksum_simt<T, 2, true><<<grid, 256, 0, s>>>(k, b, rk); break;
-            case 3: k_ksum_simt<T, 3, true><<<grid, 256, 0, s>>>(k, b, rk); break;
-            case 4: k_ksum_simt<T, 4, true><<<grid, 256, 0, s>>>(k, b, rk); break;
-            default: return cudaErrorInvalidValue;
-        }
-        return cudaGetLastError();
-    }
+    const long long tiles = (k.row1 - k.row0 + BM - 1) / BM;   // the handle's target blocks
+    if (tiles == 0) return cudaSuccess;
+    const int nsplit = simt_splits(k.n_pad, tiles, b.simt_part != nullptr);
+    const unsigned grid = (unsigned)(tiles * nsplit);
+    const bool noise = (k.noise == YY_NOISE_DIAG);
+#define YY_SIMT(NN)                                                                                     \
+    case NN:                                                                                            \
+        if (noise) k_ksum_simt<T, NN, true><<<grid, 256, 0, s>>>(k, b, rk, nsplit);                     \
+        else k_ksum_simt<T, NN><<<grid, 256, 0, s>>>(k, b, rk, nsplit);                                \
+        if (nsplit > 1) {                                                                               \
+            const unsigned mg = (unsigned)((k.row1 - k.row0 + 255) / 256);                              \
+            if (noise) k_simt_merge<T, NN, true><<<mg, 256, 0, s>>>(k, b, nsplit);                      \
+            else k_simt_merge<T, NN><<<mg, 256, 0, s>>>(k, b, nsplit);                                 \
+        }                                                                                               \
+        break;
     switch (k.N) {
-        case 1: k_ksum_simt<T, 1><<<grid, 256, 0, s>>>(k, b, rk); break;
-        case 2: k_ksum_simt<T, 2><<<grid, 256, 0, s>>>(k, b, rk); break;
-        case 3: k_ksum_simt<T, 3><<<grid, 256, 0, s>>>(k, b, rk); break;
-        case 4: k_ksum_simt<T, 4><<<grid, 256, 0, s>>>(k, b, rk); break;
+        YY_SIMT(1)
+        YY_SIMT(2)
+        YY_SIMT(3)
+        YY_SIMT(4)
         default: return cudaErrorInvalidValue;
     }
+#undef YY_SIMT
+    if (launches) *launches += (nsplit > 1) ? 2 : 1;
     return cudaGetLastError();
 }
-template cudaError_t launch_ksum_simt<float>(const Consts<float>&, const Bufs<float>&, cudaStream_t);
-template cudaError_t launch_ksum_simt<double>(const Consts<double>&, const Bufs<double>&, cudaStream_t);
+template cudaError_t launch_ksum_simt<float>(const Consts<float>&, const Bufs<float>&, cudaStream_t, int*);
+template cudaError_t launch_ksum_simt<double>(const Consts<double>&, const Bufs<double>&, cudaStream_t, int*);
 
 }  // namespace yy
