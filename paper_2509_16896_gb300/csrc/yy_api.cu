@@ -186,7 +186,10 @@ size_t carve(const yy_config* c, char* base, Bufs<T>* out) {
         b.hld = cv.take<T>(n_pad * sizeof(T));
     }
     if (c->materialise != 0 && c->precision != YY_PREC_FP64)
+    {
         b.op = cv.take<float>((size_t)c->n_scales * (size_t)n_pad * (size_t)n_pad * sizeof(float));
+        b.op_lsrc = cv.take<float>((size_t)n_pad * sizeof(float));
+    }
     b.dimc = cv.take<T>(5 * (size_t)r_pad * sizeof(T));
     b.next_centre = cv.take<double>(r_pad * sizeof(double));
     b.next_half = cv.take<double>(r_pad * sizeof(double));
@@ -471,6 +474,7 @@ yy_status yy_create(const yy_config* cfg, void* d_workspace, size_t bytes, void*
     else carve<float>(cfg, f->ws, &f->bf);
     cudaError_t e = cudaSuccess;
     if (cfg->precision == YY_PREC_BF16) e = prepare_ksum_tc();
+    if (e == cudaSuccess && cfg->materialise && !f->fp64) e = prepare_op_apply();
     if (e == cudaSuccess) e = cudaMemsetAsync(d_workspace, 0, need, f->stream);
     if (e != cudaSuccess) { delete f; return YY_ERR_CUDA; }
     *out = f;
@@ -534,7 +538,7 @@ yy_status yy_predict(yy_filter* f) {
         e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
         if (e == cudaSuccess) e = launch_op_build(f->kf, f->bf, false, f->stream);
         if (e == cudaSuccess) e = launch_op_apply(f->kf, f->bf, f->stream);
-        f->launches += 2;
+        f->launches += 3;   // build (returns at once unless the node set moved), source terms, apply
     } else if (f->cfg.precision == YY_PREC_FP32) {
         e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
         int l = 0;

@@ -113,6 +113,7 @@ struct Bufs {
     T* obs_l;             // [r_pad] noise coefficients: h(c) dy - dt/2 h(c)^2 per coordinate
     T* obs_ibc;           // [r_pad] noise coefficients: 1 / b_d(c)
     float* op;            // [N][n_pad][n_pad] materialised pair parts of log K_{tau_j} (materialise >= 1)
+    float* op_lsrc;       // [n_pad] source terms of the materialised apply (log2 e ell_s, -inf if not live)
     T* minv;              // [n_pad][r_pad] noise coefficients: a(x)^+ (diagonal) at every node
     T* hld;               // [n_pad] noise coefficients: 1/2 log det_+ a(x)
     T* dimc;              // [5][r_pad] per-dimension constants of the preparation pass:
@@ -191,6 +192,7 @@ cudaError_t launch_ksum_simt(const Consts<T>& k, const Bufs<T>& b, cudaStream_t 
 cudaError_t launch_ksum_scr32(const Consts<float>& k, const Bufs<float>& b, int k1, cudaStream_t s);
 cudaError_t launch_op_build(const Consts<float>& k, const Bufs<float>& b, bool force, cudaStream_t s);
 cudaError_t launch_op_apply(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s);
+cudaError_t prepare_op_apply();
 cudaError_t launch_ksum_tc(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s,
                            int* launches);
 size_t tc_scratch_bytes(long long n_pad);

@@ -21,6 +21,7 @@
 #include <algorithm>
 
 #include "yy_combine.cuh"
+#include "yy_tcgen05.cuh"
 
 namespace yy {
 
@@ -344,51 +345,210 @@ __global__ void __launch_bounds__(256) k_op_build(Consts<float> k, Bufs<float> b
     ksum_simt_body<float, N, false, false, true>(k, b, rk, (int)(k.row0 / BM) + blockIdx.x);
 }
 
-// L_j(i) = log sum_s exp(A_j(i, s) + ell_s) over live sources, one warp per target row
-// (float4 loads of the row, an online (max, sum) per lane, a warp merge), then the signed
-// combination of the scales with the identity term.
+// The apply works in base 2: with v = A + ell, e^(v - m) = 2^(v log2 e - m log2 e).
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+// 2^x by the hardware approximation (PTX ex2.approx.ftz.f32): its results below 2^-126 are
+// flushed to zero, which here are terms below 2^-126 of the running maximum.
+__device__ __forceinline__ float ex2_hw(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// No term yet: a finite stand-in for -inf in the apply's running maxima, so that
+// 2^(v - m) and the merges need no test (2^(-inf - kOpNone) = 0, 2^(kOpNone - v) = 0 for
+// any score v the operator can produce, 2^(kOpNone - kOpNone) = 1 with both sums zero).
+constexpr float kOpNone = -3.402823466e38f;
+
+// Source terms of the apply in base 2: log2 e ell_s for live sources, -inf for masked nodes
+// and for the padding beyond n.
+__global__ void __launch_bounds__(256) k_op_src(Consts<float> k, Bufs<float> b) {
+    const long long s = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= k.n_pad) return;
+    b.op_lsrc[s] = (s < k.n && !b.mask[s]) ? b.logw[s] * kLog2e : -INFINITY;
+}
+
+// Online base-2 (max, sum) over four scores A log2 e + l.  Every streamed operator entry
+// is finite (the build writes whole 64-column source tiles of the zero-initialised
+// workspace), so a -inf source term gives a -inf score.  One rescale per group of four
+// when its largest score is a new maximum.
+__device__ __forceinline__ void op_lse4(float& m, float& s, const float4 a, const float4 l) {
+    const float v0 = fmaf(a.x, kLog2e, l.x), v1 = fmaf(a.y, kLog2e, l.y);
+    const float v2 = fmaf(a.z, kLog2e, l.z), v3 = fmaf(a.w, kLog2e, l.w);
+    const float vm = fmaxf(fmaxf(v0, v1), fmaxf(v2, v3));
+    if (vm > m) { s *= ex2_hw(m - vm); m = vm; }
+    s += (ex2_hw(v0 - m) + ex2_hw(v1 - m)) + (ex2_hw(v2 - m) + ex2_hw(v3 - m));
+}
+
+// Merge of two base-2 (max, sum) states.
+__device__ __forceinline__ void op_merge(float& m, float& s, float m2, float s2) {
+    const float mm = fmaxf(m, m2);
+    s = s * ex2_hw(m - mm) + s2 * ex2_hw(m2 - mm);
+    m = mm;
+}
+
+namespace {
+constexpr int kOpCW = 2048;   // columns of one plane in a stage of the apply's ring
+constexpr unsigned long long kOpDrainNs = 4000000000ull;   // bound of the exit drain (4 s)
+template <int N> constexpr int op_stages() { return 8 / N > 2 ? 8 / N : 2; }
+template <int N> constexpr size_t op_smem_bytes() {
+    return (size_t)op_stages<N>() * N * kOpCW * sizeof(float) + 2 * op_stages<N>() * sizeof(uint64_t);
+}
+// Untiled bulk copy global -> shared (both addresses 16-byte aligned, size a multiple of
+// 16) completing on an mbarrier.
+__device__ __forceinline__ void op_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    uint64_t g;
+    asm volatile("cvta.to.global.u64 %0, %1;" : "=l"(g) : "l"(reinterpret_cast<uint64_t>(src)));
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     ptx::smem_u32(dst)),
+                 "l"(g), "r"(bytes), "r"(ptx::smem_u32(bar))
+                 : "memory");
+}
+// Wait for a phase, bounded by limit_ns: on expiry the block's abort flag and the status
+// word's timeout bit are set; a raised abort flag ends the wait as well.
+__device__ __forceinline__ bool op_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                        unsigned int* status, unsigned long long limit_ns) {
+    if (ptx::mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = ptx::globaltimer();
+    while (true) {
+        if (ptx::mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (ptx::globaltimer() - t0 > limit_ns) {
+            *abort_flag = 1;
+            atomicOr(status, kStatusTimeout);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+}  // namespace
+
+// L_j(i) = log sum_s exp(A_j(i, s) + ell_s) over live sources, then the signed combination
+// of the scales with the identity term.  A block owns one target row at a time (rows are
+// strided over the grid, so every block gets the same share).  Warp 8 streams the row's N
+// planes through a ring of shared-memory stages with bulk async copies (kOpCW columns of
+// every plane per stage); warps 0-7 take float4 groups of each stage, keep an online base-2
+// (max, sum) per scale, release the stage, and merge their 256 states at the end of the
+// row.  Every wait is bounded by the handle's limit; after a timeout the consumers keep
+// the same barrier sequence without computing, and the producer waits (bounded) for its
+// copies in flight before it exits.
 template <int N>
-__global__ void __launch_bounds__(256) k_op_apply(Consts<float> k, Bufs<float> b) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) b.stats->op_stale = 0;
-    const int lane = threadIdx.x & 31;
-    const long long warp = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+__global__ void __launch_bounds__(288) k_op_apply(Consts<float> k, Bufs<float> b) {
+    constexpr int S = op_stages<N>();
+    extern __shared__ __align__(128) unsigned char op_smem[];
+    float* stage = reinterpret_cast<float*>(op_smem);
+    uint64_t* full = reinterpret_cast<uint64_t*>(op_smem + (size_t)S * N * kOpCW * sizeof(float));
+    uint64_t* empty = full + S;
+    __shared__ float red_m[2][N][8], red_s[2][N][8];
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    if (tid == 0) {
+        for (int q = 0; q < S; ++q) {
+            ptx::mbar_init(&full[q], 1);
+            ptx::mbar_init(&empty[q], 8);
+        }
+        ptx::mbar_fence_init();
+        abort_flag = 0;
+        if (blockIdx.x == 0) b.stats->op_stale = 0;
+    }
+    __syncthreads();
+    volatile int* ab = &abort_flag;
+    unsigned int* status = &b.stats->status;
+    const long long n4 = (k.n + 3) / 4 * 4;   // columns streamed per row: a multiple of 16 bytes
+    const int chunks = (int)((n4 + kOpCW - 1) / kOpCW);
     const size_t plane = (size_t)k.n_pad * (size_t)k.n_pad;
-    for (long long i = k.row0 + warp; i < k.row1; i += nwarps) {
-        float mx[N], sm[N];
+    const float4* lsrc = reinterpret_cast<const float4*>(b.op_lsrc);
+
+    if (wid == 8) {   // producer
+        if (lane != 0) return;
+        uint32_t it = 0;
+        for (long long i = k.row0 + blockIdx.x; i < k.row1 && !*ab; i += gridDim.x) {
+            for (int c = 0; c < chunks; ++c) {
+                const uint32_t slot = it % S, ph = (it / S) & 1u;
+                if (!op_wait(&empty[slot], ph ^ 1u, ab, status, k.wait_ns)) break;
+                const long long c0 = (long long)c * kOpCW;
+                const uint32_t bytes = (uint32_t)((n4 - c0 < kOpCW ? n4 - c0 : kOpCW) * sizeof(float));
+                ptx::mbar_arrive_expect_tx(&full[slot], N * bytes);
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    op_bulk_load(stage + ((size_t)slot * N + j) * kOpCW, b.op + j * plane + (size_t)i * k.n_pad + c0,
+                                 bytes, &full[slot]);
+                ++it;
+            }
+        }
+        // the last S stages issued have landed before the block's shared memory is released
+        for (uint32_t t = it > (uint32_t)S ? it - S : 0u; t < it; ++t) {
+            const unsigned long long t0 = ptx::globaltimer();
+            while (!ptx::mbar_try_wait(&full[t % S], (t / S) & 1u))
+                if (ptx::globaltimer() - t0 > kOpDrainNs) break;
+        }
+        return;
+    }
+
+    uint32_t it = 0;
+    int par = 0;
+    for (long long i = k.row0 + blockIdx.x; i < k.row1; i += gridDim.x, par ^= 1) {
+        float m[N], s[N];
+#pragma unroll
+        for (int j = 0; j < N; ++j) { m[j] = kOpNone; s[j] = 0.f; }
+        for (int c = 0; c < chunks; ++c, ++it) {
+            const uint32_t slot = it % S, ph = (it / S) & 1u;
+            if (!*ab && op_wait(&full[slot], ph, ab, status, k.wait_ns)) {
+                const long long g0 = (long long)c * (kOpCW / 4);
+                const int groups = (int)((n4 / 4 - g0) < kOpCW / 4 ? (n4 / 4 - g0) : kOpCW / 4);
+                const float4* st = reinterpret_cast<const float4*>(stage + (size_t)slot * N * kOpCW);
+                if (groups == kOpCW / 4) {   // a full stage: two groups per thread
+                    const float4 l0 = __ldg(lsrc + g0 + tid), l1 = __ldg(lsrc + g0 + tid + 256);
+                    float4 a0[N], a1[N];
+#pragma unroll
+                    for (int j = 0; j < N; ++j) {
+                        a0[j] = st[j * (kOpCW / 4) + tid];
+                        a1[j] = st[j * (kOpCW / 4) + tid + 256];
+                    }
+#pragma unroll
+                    for (int j = 0; j < N; ++j) {
+                        op_lse4(m[j], s[j], a0[j], l0);
+                        op_lse4(m[j], s[j], a1[j], l1);
+                    }
+                } else {
+                    for (int g = tid; g < groups; g += 256) {
+                        const float4 l = __ldg(lsrc + g0 + g);
+#pragma unroll
+                        for (int j = 0; j < N; ++j) op_lse4(m[j], s[j], st[j * (kOpCW / 4) + g], l);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&empty[slot]);
+        }
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const float4* row = reinterpret_cast<const float4*>(b.op + j * plane + (size_t)i * k.n_pad);
-            float m = -INFINITY, s = 0.f;
-            for (long long q = lane; q * 4 < k.n; q += 32) {
-                const float4 a = row[q];
-                const float av[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const long long src = q * 4 + c;
-                    if (src >= k.n || b.mask[src]) continue;
-                    const float v = av[c] + b.logw[src];
-                    if (v == -INFINITY) continue;
-                    if (v > m) { s = (m == -INFINITY) ? 1.f : s * exp_fast<float>(m - v) + 1.f; m = v; }
-                    else s += exp_fast<float>(v - m);
-                }
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const float m2 = __shfl_xor_sync(0xffffffffu, m, o), s2 = __shfl_xor_sync(0xffffffffu, s, o);
-                if (m2 != -INFINITY) {
-                    if (m == -INFINITY) { m = m2; s = s2; }
-                    else if (m2 > m) { s = s * exp_fast<float>(m - m2) + s2; m = m2; }
-                    else s += s2 * exp_fast<float>(m2 - m);
-                }
-            }
-            mx[j] = m;
-            sm[j] = s;
+            for (int o = 16; o > 0; o >>= 1)
+                op_merge(m[j], s[j], __shfl_xor_sync(0xffffffffu, m[j], o), __shfl_xor_sync(0xffffffffu, s[j], o));
+            if (lane == 0) { red_m[par][j][wid] = m[j]; red_s[par][j][wid] = s[j]; }
         }
-        if (lane == 0)
-            b.logw_pred[i] = b.mask[i] ? -INFINITY
-                                       : combine_scales<float, N>(k, mx, sm, b.divf[i], b.logw[i], b.stats->c_ref,
-                                                                  &b.stats->clamps);
+        // One barrier of the 8 consumer warps per row: the next row writes the other parity,
+        // and a row two ahead writes this one only after the next row's barrier, which warp 0
+        // reaches after reading this row's states.
+        consumer_sync();
+        if (wid == 0 && !*ab) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                m[j] = lane < 8 ? red_m[par][j][lane] : kOpNone;
+                s[j] = lane < 8 ? red_s[par][j][lane] : 0.f;
+#pragma unroll
+                for (int o = 4; o > 0; o >>= 1)
+                    op_merge(m[j], s[j], __shfl_xor_sync(0xffffffffu, m[j], o), __shfl_xor_sync(0xffffffffu, s[j], o));
+                m[j] = m[j] == kOpNone ? -INFINITY : m[j] * kLn2;   // natural log of the row's largest term
+            }
+            if (lane == 0)
+                b.logw_pred[i] = b.mask[i] ? -INFINITY
+                                           : combine_scales<float, N>(k, m, s, b.divf[i], b.logw[i], b.stats->c_ref,
+                                                                      &b.stats->clamps);
+        }
     }
 }
 
@@ -407,17 +567,39 @@ cudaError_t launch_op_build(const Consts<float>& k, const Bufs<float>& b, bool f
     return cudaGetLastError();
 }
 
+namespace {
+int g_op_resident[5] = {0, 0, 0, 0, 0};   // blocks of k_op_apply<N> resident on the device at once
+}
+
+cudaError_t prepare_op_apply() {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const void* fns[4] = {(const void*)k_op_apply<1>, (const void*)k_op_apply<2>, (const void*)k_op_apply<3>,
+                          (const void*)k_op_apply<4>};
+    const size_t smem[4] = {op_smem_bytes<1>(), op_smem_bytes<2>(), op_smem_bytes<3>(), op_smem_bytes<4>()};
+    for (int j = 0; j < 4 && e == cudaSuccess; ++j) {
+        int per = 0;
+        e = cudaFuncSetAttribute(fns[j], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem[j]);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fns[j], 288, smem[j]);
+        g_op_resident[j + 1] = std::max(1, sms * per);
+    }
+    return e;
+}
+
 cudaError_t launch_op_apply(const Consts<float>& k, const Bufs<float>& b, cudaStream_t s) {
     if (!b.op) return cudaErrorInvalidValue;
+    if (k.N < 1 || k.N > 4 || g_op_resident[k.N] == 0) return cudaErrorInvalidValue;
     const long long rows = k.row1 - k.row0;
-    const unsigned grid = (unsigned)std::min<long long>((rows + 7) / 8, 152 * 8);   // 8 rows per block of 8 warps
-    if (grid == 0) return cudaSuccess;
+    if (rows <= 0) return cudaSuccess;
+    // one row per block at a time; the grid is what the device holds at once
+    const unsigned grid = (unsigned)std::min<long long>(rows, g_op_resident[k.N]);
+    k_op_src<<<(unsigned)((k.n_pad + 255) / 256), 256, 0, s>>>(k, b);
     switch (k.N) {
-        case 1: k_op_apply<1><<<grid, 256, 0, s>>>(k, b); break;
-        case 2: k_op_apply<2><<<grid, 256, 0, s>>>(k, b); break;
-        case 3: k_op_apply<3><<<grid, 256, 0, s>>>(k, b); break;
-        case 4: k_op_apply<4><<<grid, 256, 0, s>>>(k, b); break;
-        default: return cudaErrorInvalidValue;
+        case 1: k_op_apply<1><<<grid, 288, op_smem_bytes<1>(), s>>>(k, b); break;
+        case 2: k_op_apply<2><<<grid, 288, op_smem_bytes<2>(), s>>>(k, b); break;
+        case 3: k_op_apply<3><<<grid, 288, op_smem_bytes<3>(), s>>>(k, b); break;
+        default: k_op_apply<4><<<grid, 288, op_smem_bytes<4>(), s>>>(k, b); break;
     }
     return cudaGetLastError();
 }

@@ -48,6 +48,29 @@ def test_materialised_prediction_step_local(yy_lib, prec):
         assert rel_err((pred.astype(np.float64) + off)[rows], ref[rows]) <= 1e-5, rep
 
 
+@pytest.mark.parametrize("prec,r,n,N", [("f32", 7, 3001, 3), ("bf16", 33, 5002, 1), ("f32", 12, 2053, 4),
+                                         ("bf16", 16, 515, 2)])
+def test_materialised_prediction_ragged(yy_lib, prec, r, n, N):
+    """Node counts that end inside a group of four columns and inside a block of rows, at
+    every scale count: every row against the oracle, for the build and the reuse."""
+    from oracle import filter as F
+    f = _make(r, n, N, prec, 2, 3, 11)
+    u, _ = f.get_nodes()
+    p = oracle_problem("cubic", r, n, 0.01, 0.3, N, restart_interval=3)
+    tr = simulate("cubic", r, 2, 0.01, seed=11)
+    st = F.init_state(p, u, np.zeros(r))
+    _, st = F.step(p, st, tr.dy[0], n_threads=os.cpu_count() or 1)
+    f.set_state(st.centre, st.logw.astype(np.float32), st.lognorm, st.k)
+    ref, _ = F.predict(p, F.prepare(p, u, st.centre), st.logw.astype(np.float32).astype(np.float64),
+                       0, n, n_threads=os.cpu_count() or 1)
+    for rep in range(2):
+        f.predict()
+        pred, off = f.get_log_weights()
+        full = pred.astype(np.float64) + off
+        assert np.array_equal(np.isneginf(full), np.isneginf(ref)), rep
+        assert rel_err(full, ref) <= 1e-5, rep
+
+
 def test_materialised_whole_run_and_graph(yy_lib):
     import torch
     from oracle import filter as F
