@@ -469,6 +469,25 @@ YY_EXPORT yy_status yy_set_cta_pair(yy_filter* f, int32_t on, int32_t* h_pairs);
 YY_EXPORT yy_status yy_tune_materialise(yy_filter* f, int32_t predicts_per_build, int32_t reps, double* h_ms,
                                         int32_t* h_choice);
 
+/* Routing of a BF16 filter's prediction (no counterpart in the paper; the paper evaluates
+ * every pair): the screened tensor-core form of yy_predict, or the plain float32 form of
+ * YY_PREC_FP32 (every pair, same results within float32 rounding).  The screen wins where
+ * it proves most pairs negligible; where the weights spread over many nats (the paper's
+ * large-scale workload) nearly every pair survives it and the plain form is faster.
+ * yy_set_route: plain = 1 routes to the plain form, 0 back to the screen (the default).
+ * The plain form reads the drift f of every node, which the preparation pass then stores
+ * (recomputed here for the current nodes when it was not stored).
+ * yy_tune_route times, on the handle's current state, reps predictions of each form (after
+ * one untimed prediction of each) and keeps the faster; h_ms (host double [2], may be NULL)
+ * receives the screened and plain times in ms, *h_route (may be NULL) 1 when the plain form
+ * was chosen.  The timing predictions leave the weights as they were; they do advance the
+ * adaptive first-pass controller of the screen.  Synchronous.  A captured graph keeps the
+ * route it was captured with.
+ * Both: YY_ERR_UNSUPPORTED unless the precision is YY_PREC_BF16, YY_ERR_STATE between a
+ * prediction and its update, YY_ERR_ARG for plain not in {0, 1} or reps < 1. */
+YY_EXPORT yy_status yy_set_route(yy_filter* f, int32_t plain);
+YY_EXPORT yy_status yy_tune_route(yy_filter* f, int32_t reps, double* h_ms, int32_t* h_route);
+
 /* Kernel launches issued by this handle so far (for launch accounting). */
 YY_EXPORT int64_t yy_launch_count(const yy_filter* f);
 

@@ -46,7 +46,8 @@ EXPORTS = ("yy_workspace_bytes", "yy_create", "yy_destroy", "yy_init_nodes", "yy
            "yy_mlp_get_params", "yy_mlp_forward", "yy_mlp_loss_grad", "yy_mlp_train",
            "yy_mlp_set_input_norm", "yy_get_screen", "yy_batch_set_routing",
            "yy_set_wait_limit", "yy_set_shard", "yy_shard_rows", "yy_update_shard", "yy_merge_shards",
-           "yy_merge_records_host", "yy_init_nodes_lds", "yy_tune_materialise", "yy_set_cta_pair")
+           "yy_merge_records_host", "yy_init_nodes_lds", "yy_tune_materialise", "yy_set_cta_pair",
+           "yy_set_route", "yy_tune_route")
 
 
 class YYError(RuntimeError):
@@ -118,6 +119,8 @@ def _declare(L: ctypes.CDLL) -> None:
         "yy_merge_records_host": (I32, [P, I32, I32, P]),
         "yy_init_nodes_lds": (I32, [P, I32, P, P]),
         "yy_tune_materialise": (I32, [P, I32, I32, P, P]),
+        "yy_set_route": (I32, [P, I32]),
+        "yy_tune_route": (I32, [P, I32, P, P]),
         "yy_set_cta_pair": (I32, [P, I32, P]),
         "yy_get_box": (I32, [P, P, P]),
         "yy_set_restart_mlp": (I32, [P, P]),
@@ -337,6 +340,18 @@ class Filter:
         _check("yy_tune_materialise", self.lib.yy_tune_materialise(self.h, predicts_per_build, reps, _ptr(ms),
                                                                    ctypes.byref(ch)))
         return ch.value, tuple(ms)
+
+    def set_route(self, plain: bool) -> None:
+        """BF16 filters: predictions on the plain float32 form (True) or the screen (False)."""
+        _check("yy_set_route", self.lib.yy_set_route(self.h, 1 if plain else 0))
+
+    def tune_route(self, reps: int = 3):
+        """Times the screened and the plain prediction and keeps the faster; returns
+        (route 0 screen / 1 plain, (ms screened, ms plain))."""
+        ms = np.zeros(2)
+        rt = ctypes.c_int32()
+        _check("yy_tune_route", self.lib.yy_tune_route(self.h, reps, _ptr(ms), ctypes.byref(rt)))
+        return rt.value, tuple(ms)
 
     def set_wait_limit(self, seconds: float) -> None:
         _check("yy_set_wait_limit", self.lib.yy_set_wait_limit(self.h, float(seconds)))

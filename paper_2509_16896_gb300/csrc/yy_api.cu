@@ -539,7 +539,7 @@ yy_status yy_predict(yy_filter* f) {
         if (e == cudaSuccess) e = launch_op_build(f->kf, f->bf, false, f->stream);
         if (e == cudaSuccess) e = launch_op_apply(f->kf, f->bf, f->stream);
         f->launches += 3;   // build (returns at once unless the node set moved), source terms, apply
-    } else if (f->cfg.precision == YY_PREC_FP32) {
+    } else if (f->cfg.precision == YY_PREC_FP32 || f->route_plain) {
         e = cudaMemsetAsync(&f->bf.stats->clamps, 0, sizeof(unsigned), f->stream);
         int l = 0;
         if (e == cudaSuccess) e = launch_ksum_simt<float>(f->kf, f->bf, f->stream, &l);
@@ -820,6 +820,80 @@ yy_status yy_tune_materialise(yy_filter* f, int32_t predicts_per_build, int32_t 
     f->use_op = (f->cfg.materialise == 2) || (bu + predicts_per_build * ap < predicts_per_build * re);
     if (h_ms) { h_ms[0] = re; h_ms[1] = bu; h_ms[2] = ap; }
     if (h_choice) *h_choice = f->use_op ? 1 : 0;
+    return YY_OK;
+}
+
+// Routes a BF16 filter's predictions to the plain float32 form (or back).  The plain form
+// reads the stored drift f; a filter that did not store it gets it for its current nodes
+// from the preparation pass, and stores it from then on.  Back on the screen, the drift is
+// recomputed from u inside the screen again (except for the model whose drift is always
+// stored).
+static yy_status route_to(yy_filter* f, bool plain) {
+    const int screen_store_f = (f->cfg.model == YY_MODEL_PAPER_E1) ? 1 : 0;
+    cudaError_t e = cudaSuccess;
+    if (plain && !f->bf.store_f) {
+        f->bf.store_f = 1;
+        if (f->nodes_ready) {
+            e = launch_prep<float>(f->kf, f->bf, false, false, 0.0, 1.0, f->stream);
+            f->launches += 1;
+        }
+    } else if (!plain) {
+        f->bf.store_f = screen_store_f;
+    }
+    f->route_plain = plain;
+    return cuda_status(e);
+}
+
+yy_status yy_set_route(yy_filter* f, int32_t plain) {
+    if (!f || (plain != 0 && plain != 1)) return YY_ERR_ARG;
+    if (f->cfg.precision != YY_PREC_BF16) return YY_ERR_UNSUPPORTED;
+    if (f->predicted || f->shard_updated) return YY_ERR_STATE;
+    return route_to(f, plain == 1);
+}
+
+yy_status yy_tune_route(yy_filter* f, int32_t reps, double* h_ms, int32_t* h_route) {
+    if (!f || reps < 1) return YY_ERR_ARG;
+    if (f->cfg.precision != YY_PREC_BF16) return YY_ERR_UNSUPPORTED;
+    if (!f->nodes_ready || f->predicted || f->shard_updated) return YY_ERR_STATE;
+    const bool keep_op = f->use_op;
+    f->use_op = false;   // the two forms compared are the recomputing ones
+    cudaEvent_t ev[4];
+    for (auto& x : ev)
+        if (cudaEventCreate(&x) != cudaSuccess) { f->use_op = keep_op; return YY_ERR_CUDA; }
+    yy_status st = route_to(f, true);   // f of the current nodes, stored
+    auto predicts = [&](int m) {
+        for (int q = 0; q < m && st == YY_OK; ++q) st = yy_predict(f);
+    };
+    predicts(1);
+    cudaEventRecord(ev[0], f->stream);
+    predicts(reps);
+    cudaEventRecord(ev[1], f->stream);
+    // the screen as it runs when chosen (drift recomputed inside it); f stays valid in
+    // memory, since the timing leaves the nodes as they are
+    f->bf.store_f = (f->cfg.model == YY_MODEL_PAPER_E1) ? 1 : 0;
+    f->route_plain = false;
+    predicts(1);
+    cudaEventRecord(ev[2], f->stream);
+    predicts(reps);
+    cudaEventRecord(ev[3], f->stream);
+    cudaError_t e = st == YY_OK ? cudaEventSynchronize(ev[3]) : cudaSuccess;
+    float t_plain = 0.f, t_screen = 0.f;
+    if (st == YY_OK && e == cudaSuccess) {
+        cudaEventElapsedTime(&t_plain, ev[0], ev[1]);
+        cudaEventElapsedTime(&t_screen, ev[2], ev[3]);
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    f->predicted = false;   // the timing predictions leave the weights as they were
+    f->use_op = keep_op;
+    if (st != YY_OK) return st;
+    if (e != cudaSuccess) return YY_ERR_CUDA;
+    const bool plain = t_plain < t_screen;
+    if (plain) {   // f is still that of the current nodes
+        f->bf.store_f = 1;
+        f->route_plain = true;
+    }
+    if (h_ms) { h_ms[0] = t_screen / reps; h_ms[1] = t_plain / reps; }
+    if (h_route) *h_route = plain ? 1 : 0;
     return YY_OK;
 }
 

@@ -32,6 +32,7 @@ struct yy_filter {
     int node_kind;                // yy_nodes of the last node generation
     bool use_op;                  // the prediction applies the materialised operator
     bool pair_ok;                 // the tensor-core prediction may run on CTA pairs (yy_set_cta_pair)
+    bool route_plain = false;   // BF16: predictions on the plain float32 form (yy_set_route)
 };
 
 namespace yy {
