@@ -885,8 +885,10 @@ yy_status yy_tune_route(yy_filter* f, int32_t reps, double* h_ms, int32_t* h_rou
     for (auto& x : ev) cudaEventDestroy(x);
     f->predicted = false;   // the timing predictions leave the weights as they were
     f->use_op = keep_op;
-    if (st != YY_OK) return st;
-    if (e != cudaSuccess) return YY_ERR_CUDA;
+    if (st != YY_OK || e != cudaSuccess) {   // back on the screen, the default route
+        route_to(f, false);
+        return st != YY_OK ? st : YY_ERR_CUDA;
+    }
     const bool plain = t_plain < t_screen;
     if (plain) {   // f is still that of the current nodes
         f->bf.store_f = 1;
